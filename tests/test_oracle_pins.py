@@ -1,0 +1,300 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the
+mathematics, independent of the oracle's own formulas (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import bruteforce
+from oracle.geometry import (contacts, fine_sets, limiting_points, mobius_angles, peanut,
+                             radius_rule, shield_ellipse)
+from oracle.kernel import stokeslet
+from oracle.params import PACKING, PAIR_SMALL
+from oracle.system import System
+
+
+# ---------------------------------------------------------------- kernel
+def test_stokeslet_symmetry_and_stokes_equations():
+    """S(x,y) = S(y,x) = S(x,y)^T, and a single Stokeslet field is
+    divergence-free and satisfies mu Lap u = grad p with the Stokeslet
+    pressure p = (x-y).F / (2 pi |x-y|^2) (checked by finite differences)."""
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-3, 3, (5, 2))
+    Y = rng.uniform(-3, 3, (4, 2))
+    S = stokeslet(X, Y)
+    St = stokeslet(Y, X)
+    assert np.allclose(S, St.T, atol=1e-15)
+    for m in range(5):
+        blk = S[2 * m:2 * m + 2, 0:2]
+        assert np.allclose(blk, blk.T, atol=1e-15)
+    F = np.array([0.7, -1.3])
+    y0 = np.array([[0.1, -0.2]])
+    u = lambda x: (stokeslet(np.atleast_2d(x), y0) @ F)
+    x0 = np.array([1.3, 0.4])
+    h = 1e-4
+    ex, ey = np.array([h, 0]), np.array([0, h])
+    div = (u(x0 + ex)[0] - u(x0 - ex)[0] + u(x0 + ey)[1] - u(x0 - ey)[1]) / (2 * h)
+    assert abs(div) < 1e-8
+    lap = (u(x0 + ex) + u(x0 - ex) + u(x0 + ey) + u(x0 - ey) - 4 * u(x0)) / h ** 2
+    p = lambda x: (x - y0[0]) @ F / (2 * math.pi * np.sum((x - y0[0]) ** 2))
+    gp = np.array([(p(x0 + ex) - p(x0 - ex)) / (2 * h), (p(x0 + ey) - p(x0 - ey)) / (2 * h)])
+    assert np.allclose(lap, gp, atol=1e-5)
+
+
+# ------------------------------------------------------- closed forms
+@pytest.mark.parametrize("a", [1.0, 0.8, 1.2])
+def test_single_disk_resistance_closed_form(a):
+    """Translation: a Stokeslet F plus a potential dipole at the centre moves
+    the circle rigidly with V = F (1/2 - log a) / (4 pi mu), so the force on
+    the fluid is F = 4 pi mu V / (1/2 - log a) (= 8 pi mu V for the unit
+    disk; singular at a = sqrt(e), Remark r:uinfty).  Rotation: a rotlet gives
+    t = 4 pi mu a^2 omega and zero force."""
+    s = System(np.zeros((1, 2)), np.array([a]), PACKING, "resistance")
+    ft, info = s.solve(np.array([[1.0, -0.5, 0.0]]), tol=1e-13)
+    F = 4 * math.pi / (0.5 - math.log(a))
+    assert np.allclose(ft[0], [F, -0.5 * F, 0.0], rtol=1e-10, atol=1e-10 * F)
+    ft, _ = s.solve(np.array([[0.0, 0.0, 1.0]]), tol=1e-13)
+    assert np.allclose(ft[0], [0, 0, 4 * math.pi * a * a], rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("a", [1.0, 0.9])
+def test_single_disk_mobility_closed_form(a):
+    """Inverse of the above: v = f (1/2 - log a)/(4 pi mu), omega = t/(4 pi mu a^2)."""
+    s = System(np.zeros((1, 2)), np.array([a]), PACKING, "mobility")
+    v, _ = s.solve(np.array([[0.3, 1.1, -2.0]]), tol=1e-13)
+    m = (0.5 - math.log(a)) / (4 * math.pi)
+    assert np.allclose(v[0], [0.3 * m, 1.1 * m, -2.0 / (4 * math.pi * a * a)], rtol=1e-10, atol=1e-12)
+
+
+# ------------------------------------------------------- algebra of Alg. 3
+@pytest.mark.parametrize("problem", ["resistance", "mobility"])
+def test_isolated_pair_matvec_is_identity(problem):
+    """For P = 2 the Step 2b subtraction cancels every pair-internal term:
+    the two-body system matrix of an isolated pair is exactly I (Sec. 3.5,
+    'approximately the identity', exact in Algorithm 3's algebra)."""
+    pk = w.two_disks(1e-2)
+    s = System(pk.centres, pk.radii, PACKING, problem)
+    assert len(s.pairs) == 1
+    mu = w.smooth_surface_vector(2, PACKING.Mc, 7).reshape(2, -1)
+    u = s.matvec(mu)
+    # rounding of the large cancelling terms in the literal form
+    assert np.max(np.abs(u - mu)) < 1e-9 * np.max(np.abs(mu))
+
+
+def test_no_contacts_reduces_to_one_body_system():
+    """Without close pairs Algorithm 3 is the one-body preconditioned system,
+    eq. (resistance): identity diagonal blocks and S^(ik) P^+ off-diagonal."""
+    c = np.array([[0.0, 0.0], [2.6, 0.4], [-0.3, 2.7]])
+    s = System(c, np.ones(3), PACKING, "resistance")
+    assert s.pairs == []
+    mu = w.smooth_surface_vector(3, PACKING.Mc, 3).reshape(3, -1)
+    u = s.matvec(mu)
+    ob = s.ob[0]
+    pinv = ob.pinv.VSi @ ob.pinv.Ut
+    for i in range(3):
+        ref = mu[i].copy()
+        for k in range(3):
+            if k != i:
+                ref = ref + stokeslet(s.X[i], s.Y[k]) @ (pinv @ mu[k])
+        assert np.allclose(u[i], ref, atol=1e-11)
+
+
+def test_gmres_matches_dense_solve():
+    """GMRES on Algorithm 3 agrees with a dense direct solve of the same
+    square 2 M_c P system (matrix assembled column by column)."""
+    c = np.array([[0.0, 0.0], [2.02, 0.0], [4.3, 0.5], [1.0, 2.3]])
+    p = PACKING.with_(Nc=32, Mc=40, Rc=0.6, Nfp=60, Nell=20, Mp=80)
+    s = System(c, np.ones(4), p, "mobility")
+    n = 4 * 2 * p.Mc
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = s.matvec(e.reshape(4, -1)).ravel()
+    b = s.rhs_mobility(w.forces_torques(4, 9)).ravel()
+    x_dense = np.linalg.solve(A, b)
+    _, info = s.solve(w.forces_torques(4, 9), tol=1e-13)
+    # unit-vector columns are non-smooth inputs: the literal form's cancelling
+    # terms leave ~1e-7 rounding in the assembled matrix
+    assert np.linalg.norm(info["mu"].ravel() - x_dense) < 1e-5 * np.linalg.norm(x_dense)
+
+
+# ------------------------------------------------------- physics
+def test_two_disk_resistance_matrix_symmetric_positive_definite():
+    """Lorentz reciprocity: the 6x6 resistance matrix of two close disks is
+    symmetric; it is positive definite once the pair is small enough that the
+    w = 0 problem of Remark r:uinfty is not near its singular scale (radius
+    0.3, gap 3e-4).  Mirror symmetry about the line of centres zeros the
+    coupling between motion along the line and the other modes."""
+    a = 0.3
+    c = a * np.array([[0.0, 0.0], [2.001, 0.0]])
+    s = System(c, a * np.ones(2), PACKING, "resistance")
+    R = np.zeros((6, 6))
+    for j in range(6):
+        e = np.zeros(6)
+        e[j] = 1.0
+        R[:, j] = s.solve(e.reshape(2, 3), tol=1e-12)[0].ravel()
+    assert np.linalg.norm(R - R.T) < 1e-8 * np.linalg.norm(R)
+    assert np.linalg.eigvalsh(0.5 * (R + R.T)).min() > 0
+    along, other = [0, 3], [1, 2, 4, 5]
+    assert np.max(np.abs(R[np.ix_(along, other)])) < 1e-8 * np.abs(R).max()
+    # lubrication: squeeze resistance far above the isolated-disk value
+    assert R[0, 0] > 100 * 4 * math.pi / (0.5 - math.log(a))
+
+
+def test_squeeze_resistance_grows_as_gap_shrinks():
+    fx = []
+    for gap in (1e-1, 1e-2, 1e-3):
+        pk = w.two_disks(gap)
+        s = System(pk.centres, pk.radii, PACKING, "resistance")
+        fx.append(s.solve(np.array([[1.0, 0, 0], [-1.0, 0, 0]]), tol=1e-12)[0][0, 0])
+    assert fx[0] < fx[1] < fx[2]
+    # 2D squeeze flow between cylinders: force ~ delta^(-3/2)
+    slope = math.log(fx[2] / fx[1]) / math.log(10)
+    assert 1.3 < slope < 1.7
+
+
+def test_zero_net_force_under_pure_rotation():
+    s = System(np.zeros((1, 2)), np.ones(1), PACKING, "resistance")
+    ft, _ = s.solve(np.array([[0.0, 0.0, 2.5]]), tol=1e-13)
+    assert np.all(np.abs(ft[0, :2]) < 1e-11)
+
+
+@pytest.mark.parametrize("gap,tol", [(1e-1, 1e-8), (1e-2, 1e-4)])
+def test_two_way_consistency(gap, tol):
+    """Mobility output fed to the resistance solve returns the input forces
+    (Sec. 6.1, 'two-way error'), to a level set by the boundary residual."""
+    pk = w.two_disks(gap)
+    ft = np.array([[1.0, 0.3, 0.2], [-1.0, -0.3, -0.5]])
+    v, _ = System(pk.centres, pk.radii, PACKING, "mobility").solve(ft, tol=1e-12)
+    ft2, _ = System(pk.centres, pk.radii, PACKING, "resistance").solve(v, tol=1e-12)
+    assert np.max(np.abs(ft2 - ft)) < tol
+
+
+def test_isolated_pair_equals_fine_brute_force():
+    """For an isolated pair the two-body scheme is the pair's fine MFS: its
+    forces match a dense global fine solve (no compression, no
+    preconditioning), which pins Z, E and the force extraction."""
+    pk = w.two_disks(1e-2)
+    vel = np.array([[1.0, 0.3, 0.2], [-0.5, -0.3, 0.4]])
+    p = PACKING.with_(Nfp=100)
+    fb = bruteforce.solve(pk.centres, pk.radii, p, "resistance", vel)
+    ft, _ = System(pk.centres, pk.radii, p, "resistance").solve(vel, tol=1e-13)
+    assert np.linalg.norm(ft - fb) < 1e-8 * np.linalg.norm(fb)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("problem,geom,tol", [
+    ("resistance", "chain", 5e-6), ("mobility", "chain", 5e-6), ("mobility", "triangle", 5e-4)])
+def test_three_disks_against_fine_brute_force(problem, geom, tol):
+    """Three disks with two or three close contacts: the pairwise-corrected,
+    peanut-compressed solution approaches the dense fine MFS.  (A closed
+    triangle under resistance traps a fluid pocket -- a three-body effect
+    that pair corrections do not carry, cf. Remark 'Clustering' -- so it is
+    not used.)"""
+    geoms = {"chain": np.array([[0, 0], [2.01, 0], [4.02, 0.3]]),
+             "triangle": np.array([[0, 0], [2.01, 0], [1.005, 2.01 * np.sqrt(3) / 2]])}
+    c = geoms[geom]
+    data = np.array([[1.0, 0.3, 0.2], [-0.5, -0.3, 0.4], [-0.5, 0.0, -0.1]])
+    fb = bruteforce.solve(c, np.ones(3), PACKING, problem, data)
+    out, _ = System(c, np.ones(3), PACKING, problem).solve(data, tol=1e-12)
+    assert np.linalg.norm(out - fb) < tol * np.linalg.norm(fb)
+
+
+# ------------------------------------------------------- geometry
+def test_accumulation_radius_and_limiting_points():
+    """R_acc(delta) = 1 + delta/2 - sqrt(delta + delta^2/4) (Sec. 5) is the
+    limiting point of two unit circles: the point inverse to itself under
+    reflection in both circles (image accumulation)."""
+    for delta in (1e-3, 1e-2, 0.1):
+        p1, p2 = limiting_points(2 + delta, 1.0, 1.0)
+        racc = 1 + delta / 2 - math.sqrt(delta + delta ** 2 / 4)
+        assert abs(p1 - racc) < 1e-14 and abs(p2 - racc) < 1e-14
+    d, r1, r2 = 2.05, 0.8, 1.2
+    p1, p2 = limiting_points(d, r1, r2)
+    # mutual inverses in circle 1 (centre 0) and circle 2 (centre d)
+    assert abs((d - p2) * p1 - r1 ** 2) < 1e-12
+    assert abs((d - p1) * p2 - r2 ** 2) < 1e-12
+
+
+def test_shield_ellipse_foci_and_tip():
+    """Ellipse with foci 0 and a, rightmost point a + gamma (1 - a); nodes kept
+    only outside the proxy circle."""
+    a, Rf, gamma = 0.969, 0.9309, 0.3
+    alpha = math.acosh(1 + 2 * gamma * (1 - a) / a)
+    z_all = 0.5 * a * (1 + np.cos(np.linspace(0, 2 * np.pi, 50) + 1j * alpha))
+    s = np.abs(z_all) + np.abs(z_all - a)
+    assert np.allclose(s, s[0], atol=1e-12)
+    assert abs(0.5 * a * (1 + math.cosh(alpha)) - (a + gamma * (1 - a))) < 1e-14
+    z = shield_ellipse(a, 1.0, Rf, 80, gamma)
+    assert len(z) > 0 and np.all(np.abs(z) > Rf)
+
+
+def test_fine_sets_counts_and_orientation():
+    p = PAIR_SMALL
+    pk = w.two_disks(1e-3)
+    fs = fine_sets(pk.centres[0], 1.0, pk.centres[1], 1.0, p)
+    assert fs["n_enh1"] == fs["n_enh2"] > 0
+    assert fs["Y1"].shape[0] == p.Nfp + fs["n_enh1"]
+    assert fs["X1"].shape[0] == math.ceil(p.af * p.Nfp) + int(p.aell * p.Nell)
+    # enhancing sources lie between the centre and the partner
+    enh = fs["Y1"][p.Nfp:]
+    assert np.all(enh[:, 0] > 0)
+    # proxies on radius R_f, not rotated
+    assert np.allclose(np.hypot(*fs["Y1"][:p.Nfp].T), radius_rule(p.Nfp))
+    assert np.allclose(fs["Y1"][0], [radius_rule(p.Nfp), 0.0])
+    # Moebius nodes cluster toward the partner
+    mob = fs["X1"][math.ceil(p.af * p.Nfp):]
+    assert np.sum(mob[:, 0] > 0.9) > 4 * np.sum(mob[:, 0] < -0.9)
+    # a wide gap keeps no ellipse sources (R_acc <= R_f)
+    fs2 = fine_sets([0, 0], 1.0, [2.15, 0], 1.0, PACKING)
+    assert fs2["n_enh1"] == 0
+
+
+def test_mobius_map_fixed_points():
+    t = mobius_angles(8, 0.6)
+    assert abs(t[0] - math.pi) < 1e-15           # theta = 0 -> pi
+    assert abs((t[4] % (2 * math.pi))) < 1e-12   # theta = pi -> 2 pi = 0
+
+
+def test_peanut_is_the_rolling_disk_envelope():
+    """Every peanut node lies on one of the four arcs, outside both disks, and
+    a disk of radius rho placed against the curve at that node touches but
+    does not overlap the pair; nodes are uniform in arc length and the
+    length is 6 pi - 8 atan2(h, d/2) for unit disks and rho = 1."""
+    for gap in (1e-3, 0.15):
+        d = 2 + gap
+        c1, c2 = np.array([0.3, -0.2]), np.array([0.3, -0.2]) + d * np.array([math.cos(0.7), math.sin(0.7)])
+        z = peanut(c1, 1.0, c2, 1.0, 1.0, 400)
+        d1 = np.hypot(*(z - c1).T)
+        d2 = np.hypot(*(z - c2).T)
+        assert np.all(d1 >= 1 - 1e-12) and np.all(d2 >= 1 - 1e-12)
+        on_disk = (np.abs(d1 - 1) < 1e-12) | (np.abs(d2 - 1) < 1e-12)
+        # waist nodes: distance exactly 1 from a rolling centre at distance 2 from both
+        h = math.sqrt(4 - (d / 2) ** 2)
+        mid = 0.5 * (c1 + c2)
+        n = np.array([-(c2 - c1)[1], (c2 - c1)[0]]) / d
+        wu, wd = mid + h * n, mid - h * n
+        on_waist = (np.abs(np.hypot(*(z - wu).T) - 1) < 1e-12) | (np.abs(np.hypot(*(z - wd).T) - 1) < 1e-12)
+        assert np.all(on_disk | on_waist)
+        seg = np.hypot(*(np.roll(z, -1, axis=0) - z).T)
+        L = 6 * math.pi - 8 * math.atan2(h, d / 2)
+        assert abs(seg.sum() - L) < 1e-3
+        assert np.std(seg) < 1e-3 * seg.mean()
+
+
+def test_params_reject_nonpositive_source_radius():
+    with pytest.raises(ValueError):
+        PACKING.with_(Nc=24)
+
+
+def test_contacts_brute_force():
+    pk = w.packing_p100()
+    cs = contacts(pk.centres, pk.radii, 0.2)
+    ref = set()
+    for i in range(pk.P):
+        for k in range(i + 1, pk.P):
+            if np.hypot(*(pk.centres[i] - pk.centres[k])) - 2 <= 0.2:
+                ref.add((i, k))
+    assert set(cs) == ref and len(cs) > 10
