@@ -1,0 +1,306 @@
+"""Benchmark: batched GPU solves of the locally compressed MFS on one GB300.
+
+Default workload: P = 100 unit disks at area fraction 0.40 (random sequential
+placement, minimum gap 1e-2), mobility problem with per-disk N(0,1) forces
+(net force shifted to zero) and torques, 72 vector unknowns per body
+(N_c = 60, M_c = 72), fine pair parameters N_fp = 150, N_ell = 80, M_p = 200,
+GMRES tol 1e-7.  One step = one complete solve of that batch on the device:
+contact detection, one-body factors and every pair block (batched QR), the
+completion-flow right-hand side, GMRES with the two-body matvec, and the
+velocity post-processing.  Inputs are resident in device memory before the
+timed region; `e2e` repeats the measurement through the host API (geometry
+and forces copied in, velocities copied out, every step).
+
+Also reported: the dominant kernel's roofline (the batched FP64 QR, from CUDA
+events on the handle's stream inside the library), the Stokeslet direct-tile
+kernel's pair rate at the P = 10^4 problem's size (7.2e5 targets x 6e5
+sources), per-step p50/p99 latency, SM clocks sampled during the timed
+region, and the CPU oracle's time for the same solve on this host.
+
+--impl reference times the CPU oracle itself (plain FP64 numpy) on the same
+workload.  Multi-GPU: the solve does not shard, so N ranks run independent
+replicas (weak scaling; value = all ranks' solves / max-over-ranks time).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Stokeslet Gpair-evals/s vs FP32 peak; batched solves/s & p99 latency at 1e-5 err"
+WORKLOAD = "p100_phi040_mobility"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Sample nvidia-smi SM clocks and throttle reasons in the background."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows if len(r) >= 8 for j in range(4) if r[4 + j] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload():
+    import workloads as w
+    pk = w.packing_p100()
+    ft = w.forces_torques(pk.P, 5)
+    return pk, ft
+
+
+def oracle_solve(pk, ft):
+    from oracle.params import PACKING
+    from oracle.system import System
+    s = System(pk.centres, pk.radii, PACKING, "mobility")
+    return s.solve(ft)
+
+
+def stokeslet_kernel_rate(L, torch, stream):
+    """Direct FP32 tile kernel at the P = 10^4 problem's size: 10^4 source
+    disks x 60 sources on a square lattice (spacing 4.4) and 72 targets per
+    lattice cell on a radius-0.5 circle about the cell centre (every target
+    at least 4 ring radii from every disk centre)."""
+    n = 100
+    h = 4.4
+    g = (np.arange(n) + 0.5) * h
+    cx, cy = np.meshgrid(g, g)
+    centres = np.stack([cx.ravel(), cy.ravel()], -1)
+    th = 2 * np.pi * np.arange(60) / 60
+    off = np.broadcast_to(np.stack([0.54 * np.cos(th), 0.54 * np.sin(th)], -1), (n * n, 60, 2)).copy()
+    rng = np.random.default_rng(0)
+    s = rng.standard_normal((n * n, 60, 2)) / 60
+    tc = centres + h / 2
+    ph = 2 * np.pi * np.arange(72) / 72
+    targets = (tc[:, None, :] + 0.5 * np.stack([np.cos(ph), np.sin(ph)], -1)[None]).reshape(-1, 2)
+    d = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    T, Cc, O, S = d(targets), d(centres), d(off), d(s)
+    out = torch.zeros_like(T)
+    pairs = T.shape[0] * S.shape[0] * S.shape[1]
+    with torch.cuda.stream(stream):
+        L.stokeslet_sum(T, Cc, O, S, stream=stream.cuda_stream, out=out)   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            L.stokeslet_sum(T, Cc, O, S, stream=stream.cuda_stream, out=out)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"targets": int(T.shape[0]), "sources": int(S.shape[0] * S.shape[1]), "ms_per_sum": ms,
+            "gpair_per_s": pairs / (ms * 1e-3) / 1e9}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2606_11273_gb300 import build as b
+    b.build()
+    import paper_2606_11273_gb300 as L
+    from paper_2606_11273_gb300 import _lib
+    pk, ft = workload()
+    stream = torch.cuda.Stream()
+    prm = L.Params(precision=L.MIXED, tol=1e-7, stream=stream.cuda_stream, device=local)
+    s = L.Solver(pk.centres, pk.radii, prm)
+    ft_d = torch.tensor(ft, dtype=torch.float64, device="cuda")
+    out_d = torch.zeros_like(ft_d)
+
+    def step():
+        s.invalidate()
+        return s.solve_device(L.MOBILITY, ft_d, out_d)
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    vel_gpu = out_d.cpu().numpy()
+    lat, qr_ms, qr_flops = [], [], []
+    iters = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = _lib.launch_count()
+    ev_all0, ev_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev_all0.record(stream)
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+            st = s.stats(L.MOBILITY)
+            qr_ms.append(st["qr_ms"])
+            qr_flops.append(st["qr_flops"])
+            iters.append(info["iters"])
+        ev_all1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = _lib.launch_count() - n0
+    t_ms = ev_all0.elapsed_time(ev_all1)
+    if ws > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = ws * args.steps / (t_ms * 1e-3)
+
+    # end to end through the public host API: create + solve (host in/out) + destroy
+    e2e_ms = None
+    if rank == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s2 = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, tol=1e-7, device=local))
+            vel_e2e, _ = s2.solve(L.MOBILITY, ft)
+            s2.close()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    result = None
+    if rank == 0:
+        pk_ = peaks()
+        # FP64 peak of this part from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop
+        sm_max = pk_.get("sm_max_mhz", 2070.0)
+        fp64_peak_tf = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+        qr_t = float(np.mean(qr_ms))
+        qr_tf = float(np.mean(qr_flops)) / (qr_t * 1e-3) / 1e12
+        stk = stokeslet_kernel_rate(L, torch, stream)
+        fp32_peak_tf = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        # accuracy of the timed result against the oracle (not timed)
+        t0 = time.perf_counter()
+        vel_ref, oinfo = oracle_solve(pk, ft)
+        oracle_s = time.perf_counter() - t0
+        err = float(np.linalg.norm(vel_gpu - vel_ref) / np.linalg.norm(vel_ref))
+        err_e2e = float(np.linalg.norm(vel_e2e - vel_ref) / np.linalg.norm(vel_ref))
+        clocks = clk.summary()
+        nbytes_in = (pk.P * 2 + pk.P + pk.P * 3) * 8
+        result = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic (seeded packing and forces)",
+            "config": {"workload": WORKLOAD, "P": int(pk.P), "n_pairs": int(s.n_pairs), "Nc": 60, "Mc": 72,
+                       "Nfp": 150, "Nell": 80, "Mp": 200, "tol": 1e-7, "precision": "mixed (FP32 far field)",
+                       "l2": "per-step working set < L2; every step recomputes all pair blocks",
+                       "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(np.mean(lat))},
+            "gmres_iters": int(np.median(iters)),
+            "err_vs_oracle": {"velocity_rel_2norm": err, "e2e_velocity_rel_2norm": err_e2e},
+            "e2e": {"value": 1e3 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": nbytes_in,
+                    "d2h_bytes_per_step": pk.P * 3 * 8},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": "qrcp_kernel (batched FP64 pair QR)",
+                         "achieved": qr_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
+                         "frac": qr_tf / fp64_peak_tf, "traffic": None,
+                         "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                         "kernel_ms_per_step": qr_t, "share_of_step": qr_t / (t_ms / args.steps)},
+            "stokeslet_tile_kernel": {**stk, "flops_per_pair": 17,
+                                      "achieved_tflops_17": stk["gpair_per_s"] * 17 / 1e3,
+                                      "fp32_peak_tflops": fp32_peak_tf,
+                                      "frac_17": stk["gpair_per_s"] * 17 / 1e3 / fp32_peak_tf},
+            "clocks": clocks,
+            "cpu_baseline": {"value": 1.0 / oracle_s, "unit": "solves/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "one full solve of the same workload (numpy FP64)",
+                             "gmres_iters": oinfo["iters"]},
+        }
+        print(json.dumps(result))
+    if ws > 1:
+        dist.destroy_process_group()
+    return result
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    pk, ft = workload()
+    for _ in range(min(args.warmup, 1)):
+        oracle_solve(pk, ft)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_solve(pk, ft)
+    t = time.perf_counter() - t0
+    v = args.steps / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded packing and forces)",
+        "config": {"workload": WORKLOAD, "P": int(pk.P)},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "full solves of the workload, numpy FP64 on the host cores"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

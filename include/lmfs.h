@@ -1,0 +1,200 @@
+/*
+ * lmfs -- locally compressed method of fundamental solutions for dense 2D
+ * Stokes suspensions of nearly-touching rigid disks, on one NVIDIA GB300.
+ *
+ * C ABI.  Plain pointers and sizes only.  Every call returns LMFS_OK (0) or a
+ * negative error code; lmfs_strerror() turns a code into text.  Unless a
+ * pointer is documented as a device pointer it is a host pointer; the caller
+ * keeps ownership of every array it passes, and calls copy what they keep.
+ *
+ * Conventions (Sec. 1, eq. (rigidbc); Sec. 3, eq. (stokes_sum)):
+ *   - A surface vector on disk i holds M_c nodes x_m = c_i + r_i (cos, sin)(2 pi m / M_c)
+ *     with the x and y components interleaved: [P][M_c][2] doubles.
+ *   - Coarse sources y_j = c_i + r_i R_c (cos, sin)(2 pi j / N_c): [P][N_c][2].
+ *   - (a, b)^perp = (-b, a); rigid data per disk is (v_x, v_y, omega) and forces
+ *     per disk (f_x, f_y, t), t = sum lambda . (y - c)^perp (eq. (force_eq)),
+ *     forces being forces on the fluid (sum of Stokeslet strengths).
+ *   - problem: LMFS_RESISTANCE (velocities in, forces out; Algorithm 2) or
+ *     LMFS_MOBILITY (forces in, velocities out; Sec. 4).
+ *
+ * Threading: a handle may be used from one host thread at a time.  All GPU
+ * work of a handle is ordered on the stream given in lmfs_params.stream (the
+ * legacy default stream when NULL).
+ */
+#ifndef LMFS_H
+#define LMFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define LMFS_OK                 0
+#define LMFS_PENDING            1   /* lmfs_poll: request not finished yet      */
+#define LMFS_ERR_INVALID       -1   /* bad argument, geometry or parameter      */
+#define LMFS_ERR_CUDA          -2   /* a CUDA call failed                       */
+#define LMFS_ERR_NOMEM         -3   /* device or host allocation failed         */
+#define LMFS_ERR_NOT_CONVERGED -4   /* GMRES hit maxit; outputs still written   */
+#define LMFS_ERR_STATE         -5   /* call out of order (e.g. no precompute)   */
+#define LMFS_ERR_TIMEOUT       -6   /* lmfs_poll gave up after its time limit   */
+#define LMFS_ERR_TOO_LARGE     -7   /* request alone exceeds the memory budget  */
+#define LMFS_ERR_NUMERICAL     -8   /* a factorization produced a non-finite value */
+
+#define LMFS_RESISTANCE 0
+#define LMFS_MOBILITY   1
+
+#define LMFS_FP64  0   /* every step in FP64, far field included                          */
+#define LMFS_MIXED 1   /* far field: FP64 per-disk multipole moments evaluated in FP32;
+                          near zone, pair blocks, factorizations and GMRES in FP64        */
+#define LMFS_MIXED_DIRECT 2 /* far field: direct FP32 Stokeslet tile sum (recentred,
+                          compensated).  Accurate only for strengths without large
+                          high Fourier modes (e.g. the completion flow); the pair
+                          corrections of close contacts violate that.                      */
+
+/* ---- parameters (Sec. 5 and Sec. 6; defaults from lmfs_params_default) */
+typedef struct lmfs_params {
+  int    Nc;             /* coarse sources per disk (60)                         */
+  int    Mc;             /* coarse collocation nodes per disk (72)               */
+  double Rc;             /* source radius / disk radius; 0: 1 - log(1e12)/Nc     */
+  int    Nfp;            /* fine proxy sources per disk (150)                    */
+  int    Nell;           /* shielding-ellipse parameter N_ell (80)               */
+  int    Mp;             /* peanut collocation nodes (200)                       */
+  double gamma;          /* ellipse shape parameter (0.3)                        */
+  double af;             /* fine equispaced nodes = ceil(af * Nfp) (1.2)         */
+  double r_mob;          /* Moebius node parameter r (0.6)                       */
+  double aell;           /* Moebius nodes per disk = aell * Nell (5)             */
+  double delta_c;        /* close-pair gap threshold (0.2)                       */
+  double eps_trunc;      /* pseudo-inverse truncation, one-body and peanut (1e-14) */
+  double eps_trunc_fine; /* truncation of the fine pair solve (1e-11)            */
+  double mu;             /* viscosity (1)                                        */
+  double tol;            /* GMRES relative residual tolerance (1e-7)             */
+  int    maxit;          /* GMRES iteration limit (300)                          */
+  double rho;            /* peanut rolling radius; 0: smallest disk radius       */
+  int    precision;      /* LMFS_FP64, LMFS_MIXED or LMFS_MIXED_DIRECT (lmfs_solve) */
+  void*  stream;         /* cudaStream_t for all work of the handle (NULL: default) */
+  int    device;         /* CUDA device ordinal (0)                              */
+} lmfs_params;
+
+typedef struct lmfs_solve_info {
+  int    iters;          /* GMRES iterations                                     */
+  double relres;         /* final GMRES relative residual estimate               */
+  double t_precompute_ms;/* pair precompute of this call (0 if already done)     */
+  double t_solve_ms;     /* right-hand side + GMRES + post-processing            */
+  int    n_pairs;        /* close pairs                                          */
+} lmfs_solve_info;
+
+typedef struct lmfs_ctx* lmfs_handle;
+
+/* Fill *p with the defaults listed above. */
+int lmfs_params_default(lmfs_params* p);
+
+/* Create a handle for P disks.  centres: host [P][2] (x, y), radii: host [P].
+ * Validates P >= 1, finite positive radii, finite centres, every gap > 0, and
+ * parameters (Nc, Mc, Nfp, Mp >= 2, source radii in (0, 1)); otherwise
+ * LMFS_ERR_INVALID.  Runs contact detection (pairs with gap <= delta_c,
+ * Algorithm 2, precomputation) on the device.  Allocates device memory. */
+int lmfs_create(const double* centres, const double* radii, int P,
+                const lmfs_params* p, lmfs_handle* out);
+int lmfs_destroy(lmfs_handle h);
+
+/* Number of close pairs C, and the pairs themselves: host int [C][2], i < k,
+ * sorted by (i, k). */
+int lmfs_num_pairs(lmfs_handle h, int* C);
+int lmfs_get_pairs(lmfs_handle h, int* pairs);
+
+/* One-body factors (eq. (howG+) resistance, eq. (SL) mobility) and every close
+ * pair's coarse-to-coarse correction A (4N_c x 4N_c, eq. (Amat)) and
+ * extraction matrix E (6 x 4N_c, eq. (force_ext) resistance, eq. (rbm2)
+ * mobility), computed on the device by batched column-pivoted Householder QR
+ * (FP64).  Idempotent per problem. */
+int lmfs_precompute_pairs(lmfs_handle h, int problem);
+
+/* Export / import the pair blocks: host double A[C][4Nc][4Nc] (row-major),
+ * E[C][6][4Nc].  Import replaces the blocks (e.g. to exchange identical
+ * blocks with another implementation); it marks the problem precomputed. */
+int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E);
+int lmfs_set_pair_blocks(lmfs_handle h, int problem, const double* A, const double* E);
+
+/* The two-body system matrix applied to mu (Algorithm 3; mobility with the
+ * projected strengths of Sec. 4.4).  mu_dev, u_dev: DEVICE pointers to
+ * [P][Mc][2] doubles; stream-ordered on the handle's stream (returns before
+ * the GPU finishes).  precision: LMFS_FP64, LMFS_MIXED or LMFS_MIXED_DIRECT. */
+int lmfs_matvec(lmfs_handle h, int problem, const double* mu_dev, double* u_dev, int precision);
+
+/* Right-hand side of the global system on the device: resistance g^(i) =
+ * v + omega (x - c)^perp (eq. (rigidbc)); mobility -u_0 (eq. (u0_def)).
+ * in_dev: DEVICE [P][3]; b_dev: DEVICE [P][Mc][2]. */
+int lmfs_rhs(lmfs_handle h, int problem, const double* in_dev, double* b_dev, int precision);
+
+/* Full solve (Algorithm 2 / Sec. 4): precompute if needed, right-hand side,
+ * GMRES on lmfs_matvec, post-processing.  in, out: HOST [P][3].  Resistance:
+ * in = (v_x, v_y, omega), out = (f_x, f_y, t); mobility the reverse.  info may
+ * be NULL.  Returns LMFS_ERR_NOT_CONVERGED if maxit was reached (out is still
+ * filled).  Synchronizes the stream. */
+int lmfs_solve(lmfs_handle h, int problem, const double* in, double* out, lmfs_solve_info* info);
+
+/* As lmfs_solve with DEVICE in/out ([P][3] doubles); no host copies. */
+int lmfs_solve_device(lmfs_handle h, int problem, const double* in_dev, double* out_dev,
+                      lmfs_solve_info* info);
+
+/* Mark the pair blocks of both problems stale and re-run contact detection
+ * (same geometry): the next solve recomputes one-body factors and pair blocks.
+ * Used to time the whole path repeatedly on one handle. */
+int lmfs_invalidate(lmfs_handle h);
+
+/* Diagnostics of the last pair precompute of `problem`: out[8] =
+ * {wall ms, QR kernel ms (CUDA events on the handle's stream), algorithmic
+ * FP64 flops of those QR launches, min rank of F, max rank of F, C, far-field
+ * source-range split, near-list entries}. */
+int lmfs_stats(lmfs_handle h, int problem, double* out);
+
+/* Diagnostics of the last solve on the device: the GMRES solution mu
+ * (DEVICE [P][Mc][2] copy destination) for parity checks. */
+int lmfs_get_solution(lmfs_handle h, double* mu_dev);
+
+/* Stand-alone far-field kernel: u_m = sum_n S(x_m, y_n) s_n over all targets
+ * and sources (eq. (stokes_sum)), FP32 recentred arithmetic with the sources
+ * grouped in disks of n_per_disk around centres; DEVICE pointers:
+ * targets [nt][2] (double), centres [nd][2] (double), offsets [nd][n_per_disk][2]
+ * (double, source minus centre), strengths [nd][n_per_disk][2] (double),
+ * out [nt][2] (double).  No exclusions. */
+int lmfs_stokeslet_sum(const double* targets, int nt, const double* centres,
+                       const double* offsets, const double* strengths, int nd,
+                       int n_per_disk, double mu, int precision, void* stream, double* out);
+
+/* Number of kernels this process has launched through the library so far
+ * (eager launches plus the kernel nodes of every replayed graph). */
+int lmfs_launch_count(uint64_t* out);
+
+const char* lmfs_strerror(int code);
+
+/* ---- serving (continuous batching) ----------------------------------- */
+typedef struct lmfs_server lmfs_server;
+
+typedef struct lmfs_server_params {
+  size_t hbm_budget_bytes; /* admission limit on resident device memory       */
+  int    max_slots;        /* resident requests at most                        */
+  int    device;
+  int    precision;        /* LMFS_MIXED or LMFS_FP64 for every request        */
+} lmfs_server_params;
+
+/* Start a server (one worker thread driving one stream). */
+int lmfs_server_create(const lmfs_server_params* sp, lmfs_server** out);
+/* Queue a request (copies all inputs, never blocks).  LMFS_ERR_TOO_LARGE if
+ * the request alone exceeds the budget; LMFS_ERR_INVALID on bad input. */
+int lmfs_submit(lmfs_server* s, const double* centres, const double* radii, int P,
+                int problem, const double* in, const lmfs_params* p, uint64_t* ticket);
+/* Wait up to timeout_us for a request: LMFS_OK (out [P][3] and info filled),
+ * LMFS_PENDING if timeout_us == 0 and it is not done, LMFS_ERR_TIMEOUT when the
+ * wait expired, or the request's own error code. */
+int lmfs_poll(lmfs_server* s, uint64_t ticket, double* out, lmfs_solve_info* info,
+              int timeout_us);
+int lmfs_server_destroy(lmfs_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMFS_H */

@@ -1,0 +1,177 @@
+"""GB300-native locally compressed MFS for dense 2D Stokes suspensions.
+
+Thin Python layer over the C ABI in include/lmfs.h (liblmfs.so): every step
+of the solver runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch supplies device memory and streams where the caller wants
+device-resident inputs.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import FP64, MIXED, MIXED_DIRECT, MOBILITY, RESISTANCE, LmfsError  # noqa: F401
+
+__all__ = ["Params", "Solver", "Server", "stokeslet_sum", "FP64", "MIXED", "MIXED_DIRECT", "RESISTANCE",
+           "MOBILITY", "LmfsError"]
+
+
+def Params(**kw):
+    """lmfs_params with the library defaults, overridden by keyword."""
+    lib = _lib.load()
+    p = _lib.lmfs_params()
+    _lib.check(lib.lmfs_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor (device or host) or a numpy array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One geometry: P disks with centres [P][2] and radii [P]."""
+
+    def __init__(self, centres, radii, params=None, stream=None):
+        self.lib = _lib.load()
+        self.centres = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 2)
+        self.radii = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+        self.P = self.radii.size
+        self.params = params if params is not None else Params()
+        if stream is not None:
+            self.params.stream = stream
+        self.h = ctypes.c_void_p()
+        _lib.check(self.lib.lmfs_create(_ptr(self.centres), _ptr(self.radii), self.P,
+                                        ctypes.byref(self.params), ctypes.byref(self.h)))
+
+    def close(self):
+        if self.h:
+            self.lib.lmfs_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_pairs(self):
+        c = ctypes.c_int()
+        _lib.check(self.lib.lmfs_num_pairs(self.h, ctypes.byref(c)))
+        return c.value
+
+    def pairs(self):
+        out = np.zeros((self.n_pairs, 2), dtype=np.int32)
+        _lib.check(self.lib.lmfs_get_pairs(self.h, _ptr(out)))
+        return out
+
+    def precompute(self, problem):
+        _lib.check(self.lib.lmfs_precompute_pairs(self.h, problem))
+
+    def pair_blocks(self, problem):
+        C, n4 = self.n_pairs, 4 * self.params.Nc
+        A = np.zeros((C, n4, n4))
+        E = np.zeros((C, 6, n4))
+        _lib.check(self.lib.lmfs_get_pair_blocks(self.h, problem, _ptr(A), _ptr(E)))
+        return A, E
+
+    def set_pair_blocks(self, problem, A, E):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        _lib.check(self.lib.lmfs_set_pair_blocks(self.h, problem, _ptr(A), _ptr(E)))
+
+    def matvec(self, problem, mu_dev, u_dev, precision=MIXED):
+        """mu_dev, u_dev: CUDA float64 tensors of P*Mc*2 elements (stream-ordered)."""
+        _lib.check(self.lib.lmfs_matvec(self.h, problem, _ptr(mu_dev), _ptr(u_dev), precision))
+
+    def rhs(self, problem, in_dev, b_dev, precision=MIXED):
+        _lib.check(self.lib.lmfs_rhs(self.h, problem, _ptr(in_dev), _ptr(b_dev), precision))
+
+    def solve(self, problem, data):
+        """Host in/out: data [P][3] -> result [P][3], info dict."""
+        data = np.ascontiguousarray(data, dtype=np.float64).reshape(self.P, 3)
+        out = np.zeros((self.P, 3))
+        info = _lib.lmfs_solve_info()
+        rc = _lib.check(self.lib.lmfs_solve(self.h, problem, _ptr(data), _ptr(out), ctypes.byref(info)),
+                        allow=(_lib.LMFS_ERR_NOT_CONVERGED,))
+        return out, self._info(info, rc)
+
+    def solve_device(self, problem, in_dev, out_dev):
+        info = _lib.lmfs_solve_info()
+        rc = _lib.check(self.lib.lmfs_solve_device(self.h, problem, _ptr(in_dev), _ptr(out_dev),
+                                                   ctypes.byref(info)),
+                        allow=(_lib.LMFS_ERR_NOT_CONVERGED,))
+        return self._info(info, rc)
+
+    def invalidate(self):
+        _lib.check(self.lib.lmfs_invalidate(self.h))
+
+    def stats(self, problem):
+        out = np.zeros(8)
+        _lib.check(self.lib.lmfs_stats(self.h, problem, _ptr(out)))
+        keys = ["precompute_ms", "qr_ms", "qr_flops", "min_rank_F", "max_rank_F", "n_pairs", "far_split",
+                "near_entries"]
+        return dict(zip(keys, out.tolist()))
+
+    def solution(self, mu_dev):
+        _lib.check(self.lib.lmfs_get_solution(self.h, _ptr(mu_dev)))
+
+    @staticmethod
+    def _info(info, rc):
+        return {"iters": info.iters, "relres": info.relres, "t_precompute_ms": info.t_precompute_ms,
+                "t_solve_ms": info.t_solve_ms, "n_pairs": info.n_pairs,
+                "converged": rc == _lib.LMFS_OK}
+
+
+def stokeslet_sum(targets, centres, offsets, strengths, mu=1.0, precision=MIXED_DIRECT, stream=None, out=None):
+    """u_m = sum_n S(x_m, y_n) s_n with FP32 direct tiles (device tensors, float64):
+    targets [nt, 2], centres [nd, 2], offsets/strengths [nd, npd, 2] -> out [nt, 2]."""
+    lib = _lib.load()
+    nt = targets.shape[0]
+    nd, npd = offsets.shape[0], offsets.shape[1]
+    if out is None:
+        out = targets.new_zeros((nt, 2))
+    st = ctypes.c_void_p(stream) if stream is not None else None
+    _lib.check(lib.lmfs_stokeslet_sum(_ptr(targets), nt, _ptr(centres), _ptr(offsets), _ptr(strengths), nd, npd,
+                                      float(mu), precision, st, _ptr(out)))
+    return out
+
+
+class Server:
+    """Continuous-batching request server (lmfs_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=8, precision=MIXED, device=0):
+        self.lib = _lib.load()
+        sp = _lib.lmfs_server_params(hbm_budget_bytes, max_slots, device, precision)
+        self.s = ctypes.c_void_p()
+        _lib.check(self.lib.lmfs_server_create(ctypes.byref(sp), ctypes.byref(self.s)))
+
+    def submit(self, centres, radii, problem, data, params=None):
+        c = np.ascontiguousarray(centres, dtype=np.float64)
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        d = np.ascontiguousarray(data, dtype=np.float64)
+        t = ctypes.c_uint64()
+        p = ctypes.byref(params) if params is not None else None
+        _lib.check(self.lib.lmfs_submit(self.s, _ptr(c), _ptr(r), r.size, problem, _ptr(d), p,
+                                        ctypes.byref(t)))
+        return t.value, r.size
+
+    def poll(self, ticket, P, timeout_us=0):
+        out = np.zeros((P, 3))
+        info = _lib.lmfs_solve_info()
+        rc = self.lib.lmfs_poll(self.s, ticket, _ptr(out), ctypes.byref(info), int(timeout_us))
+        return rc, out, Solver._info(info, rc)
+
+    def close(self):
+        if self.s:
+            self.lib.lmfs_server_destroy(self.s)
+            self.s = ctypes.c_void_p()

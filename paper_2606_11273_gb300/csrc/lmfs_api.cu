@@ -1,0 +1,375 @@
+// C ABI of the lmfs library: handles, validation, orchestration of the
+// device pipeline (Algorithm 2), and the request server.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lmfs_internal.h"
+
+struct lmfs_ctx {
+  lmfs::Ctx c;
+};
+
+namespace lmfs {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+bool cuda_failed(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return false;
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return true;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(unsigned long long n) { g_launches += n; }
+
+// Called after every eager kernel launch; also counts it.
+int check_launch(const char* what) {
+  g_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return LMFS_ERR_CUDA;
+  }
+  return LMFS_OK;
+}
+
+static void free_ctx(Ctx& c) {
+  gmres_free(c);
+  dfree(c.centres); dfree(c.radii); dfree(c.cls); dfree(c.cls_r); dfree(c.pairs); dfree(c.csr_off);
+  dfree(c.csr_ent); dfree(c.near_off); dfree(c.near_ent); dfree(c.far_excl_off); dfree(c.far_excl);
+  dfree(c.tgt32); dfree(c.dsk32);
+  for (auto& pb : c.prob) {
+    dfree(pb.A); dfree(pb.E); dfree(pb.ob.W); dfree(pb.ob.R); dfree(pb.ob.perm); dfree(pb.ob.rank);
+    pb.ready = false;
+  }
+  dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
+  dfree(c.ufar_part); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
+  if (c.own_stream && c.stream) { cudaStreamDestroy(c.stream); c.stream = nullptr; c.own_stream = false; }
+}
+
+static int validate_params(const lmfs_params& p) {
+  if (p.Nc < 2 || p.Mc < 2 || p.Nfp < 2 || p.Mp < 2 || p.Nell < 1) return LMFS_ERR_INVALID;
+  if (2 * p.Nc > 256) { set_last_error("Nc must be <= 128"); return LMFS_ERR_INVALID; }
+  if (p.Mc % 2) { set_last_error("Mc must be even"); return LMFS_ERR_INVALID; }
+  const double Rc = p.Rc > 0 ? p.Rc : 1.0 - std::log(1e12) / p.Nc;
+  const double Rf = 1.0 - std::log(1e12) / p.Nfp;
+  if (!(Rc > 0 && Rc < 1) || !(Rf > 0 && Rf < 1)) {
+    set_last_error("source radii must lie in (0, 1): Nc and Nfp must exceed log(1e12) ~ 27.6");
+    return LMFS_ERR_INVALID;
+  }
+  if (!(p.gamma > 0 && p.gamma < 1) || !(p.af > 0) || !(p.aell >= 0) || !(p.delta_c >= 0) ||
+      !(p.eps_trunc > 0) || !(p.eps_trunc_fine > 0) || !(p.mu > 0) || !(p.tol > 0) || p.maxit < 1 ||
+      !(p.rho >= 0) || (p.precision != LMFS_FP64 && p.precision != LMFS_MIXED && p.precision != LMFS_MIXED_DIRECT))
+    return LMFS_ERR_INVALID;
+  return LMFS_OK;
+}
+
+static int create_ctx(Ctx& c, const double* centres, const double* radii, int P, const lmfs_params& p) {
+  if (P < 1 || !centres || !radii) { set_last_error("P >= 1 and non-null arrays required"); return LMFS_ERR_INVALID; }
+  LMFS_TRY(validate_params(p));
+  for (int i = 0; i < P; ++i) {
+    if (!std::isfinite(centres[2 * i]) || !std::isfinite(centres[2 * i + 1]) || !std::isfinite(radii[i]) ||
+        !(radii[i] > 0)) {
+      set_last_error("non-finite centre or non-positive radius");
+      return LMFS_ERR_INVALID;
+    }
+  }
+  c.prm = p;
+  c.d.P = P; c.d.Nc = p.Nc; c.d.Mc = p.Mc;
+  c.device = p.device;
+  LMFS_CUDA(cudaSetDevice(p.device));
+  c.stream = (cudaStream_t)p.stream;
+  if (!c.stream) {
+    // graphs cannot be captured on the legacy default stream: own a stream
+    LMFS_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+    c.own_stream = true;
+  }
+  c.Rc = p.Rc > 0 ? p.Rc : 1.0 - std::log(1e12) / p.Nc;
+  c.Rf = 1.0 - std::log(1e12) / p.Nfp;
+  c.centres_h.assign(centres, centres + 2 * (size_t)P);
+  c.radii_h.assign(radii, radii + P);
+  c.rho = p.rho > 0 ? p.rho : *std::min_element(radii, radii + P);
+  // radius classes (one-body factors are shared by equal radii)
+  {
+    std::map<double, int> idx;
+    c.cls_h.resize(P);
+    for (int i = 0; i < P; ++i) {
+      auto it = idx.find(radii[i]);
+      if (it == idx.end()) { int id = (int)c.cls_r_h.size(); idx[radii[i]] = id; c.cls_r_h.push_back(radii[i]); c.cls_h[i] = id; }
+      else c.cls_h[i] = it->second;
+    }
+  }
+  LMFS_TRY(dalloc(&c.centres, 2 * (size_t)P));
+  LMFS_TRY(dalloc(&c.radii, (size_t)P));
+  LMFS_TRY(dalloc(&c.cls, (size_t)P));
+  LMFS_TRY(dalloc(&c.cls_r, c.cls_r_h.size()));
+  LMFS_CUDA(cudaMemcpyAsync(c.centres, centres, 2 * (size_t)P * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(c.radii, radii, (size_t)P * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(c.cls, c.cls_h.data(), (size_t)P * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(c.cls_r, c.cls_r_h.data(), c.cls_r_h.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  LMFS_TRY(detect_contacts(c));
+  LMFS_TRY(upload_geometry(c));
+  const int Nc = p.Nc, Mc = p.Mc;
+  const size_t ns = 2 * (size_t)Nc * P, nn = 2 * (size_t)Mc * P;
+  LMFS_TRY(dalloc(&c.lb, ns));
+  LMFS_TRY(dalloc(&c.lam, ns));
+  LMFS_TRY(dalloc(&c.sig, ns));
+  LMFS_TRY(dalloc(&c.lam0, ns));
+  LMFS_TRY(dalloc(&c.tilde, std::max<size_t>((size_t)c.C * 4 * Nc, 8)));
+  LMFS_TRY(dalloc(&c.ufar, nn));
+  LMFS_TRY(dalloc(&c.src4, 2 * (size_t)P * Nc));
+  LMFS_TRY(dalloc(&c.bvec, nn));
+  LMFS_TRY(dalloc(&c.xsol, nn));
+  LMFS_TRY(dalloc(&c.io3, 3 * (size_t)P));
+  // source-range split of the far-field kernels: aim for >= ~8 blocks per SM
+  {
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p.device);
+    const long long bx = ((long long)P * Mc / 2 + 127) / 128;
+    long long split = std::max<long long>(1, (8LL * dev_sms + bx - 1) / bx);
+    split = std::min<long long>(split, std::max(1, P / 4));
+    c.far_split = (int)split;
+    LMFS_TRY(dalloc(&c.ufar_part, (size_t)c.far_split * nn));
+  }
+  LMFS_TRY(far_field_prepare(c));
+  return LMFS_OK;
+}
+
+static int ensure_precompute(Ctx& c, int problem) {
+  PairBlocks& pb = c.prob[problem];
+  if (pb.ready) return LMFS_OK;
+  LMFS_TRY(build_onebody(c, problem, pb.ob));
+  LMFS_TRY(build_pair_blocks(c, problem));
+  pb.ready = true;
+  return LMFS_OK;
+}
+
+static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
+  if (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) return LMFS_ERR_INVALID;
+  const auto t0 = std::chrono::steady_clock::now();
+  const bool had = c.prob[problem].ready;
+  LMFS_TRY(ensure_precompute(c, problem));
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  const auto t1 = std::chrono::steady_clock::now();
+  LMFS_TRY(rhs_device(c, problem, in_dev, c.bvec, c.prm.precision));
+  lmfs_solve_info loc{};
+  int rc = gmres_solve(c, problem, c.prm.precision, c.bvec, c.xsol, &loc);
+  if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
+  LMFS_TRY(post_device(c, problem, c.xsol, out_dev));
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  c.have_solution = true;
+  const auto t2 = std::chrono::steady_clock::now();
+  if (info) {
+    *info = loc;
+    info->t_precompute_ms = had ? 0.0 : std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->t_solve_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    info->n_pairs = c.C;
+  }
+  return rc;
+}
+
+}  // namespace lmfs
+
+using namespace lmfs;
+
+extern "C" {
+
+int lmfs_params_default(lmfs_params* p) {
+  if (!p) return LMFS_ERR_INVALID;
+  std::memset(p, 0, sizeof(*p));
+  p->Nc = 60; p->Mc = 72; p->Rc = 0.0; p->Nfp = 150; p->Nell = 80; p->Mp = 200;
+  p->gamma = 0.3; p->af = 1.2; p->r_mob = 0.6; p->aell = 5.0; p->delta_c = 0.2;
+  p->eps_trunc = 1e-14; p->eps_trunc_fine = 1e-11; p->mu = 1.0; p->tol = 1e-7; p->maxit = 300;
+  p->rho = 0.0; p->precision = LMFS_MIXED; p->stream = nullptr; p->device = 0;
+  return LMFS_OK;
+}
+
+int lmfs_create(const double* centres, const double* radii, int P, const lmfs_params* p, lmfs_handle* out) {
+  if (!out) return LMFS_ERR_INVALID;
+  *out = nullptr;
+  lmfs_params prm;
+  if (p) prm = *p; else lmfs_params_default(&prm);
+  auto* h = new (std::nothrow) lmfs_ctx();
+  if (!h) return LMFS_ERR_NOMEM;
+  int rc = create_ctx(h->c, centres, radii, P, prm);
+  if (rc != LMFS_OK) { free_ctx(h->c); delete h; return rc; }
+  *out = h;
+  return LMFS_OK;
+}
+
+int lmfs_destroy(lmfs_handle h) {
+  if (!h) return LMFS_ERR_INVALID;
+  cudaSetDevice(h->c.device);
+  cudaStreamSynchronize(h->c.stream);
+  free_ctx(h->c);
+  delete h;
+  return LMFS_OK;
+}
+
+int lmfs_num_pairs(lmfs_handle h, int* C) {
+  if (!h || !C) return LMFS_ERR_INVALID;
+  *C = h->c.C;
+  return LMFS_OK;
+}
+
+int lmfs_get_pairs(lmfs_handle h, int* pairs) {
+  if (!h || (!pairs && h->c.C)) return LMFS_ERR_INVALID;
+  if (h->c.C) std::memcpy(pairs, h->c.pairs_h.data(), 2 * (size_t)h->c.C * sizeof(int));
+  return LMFS_OK;
+}
+
+int lmfs_precompute_pairs(lmfs_handle h, int problem) {
+  if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
+  LMFS_CUDA(cudaSetDevice(h->c.device));
+  LMFS_TRY(ensure_precompute(h->c, problem));
+  LMFS_CUDA(cudaStreamSynchronize(h->c.stream));
+  return LMFS_OK;
+}
+
+int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E) {
+  if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
+  Ctx& c = h->c;
+  if (!c.prob[problem].ready) return LMFS_ERR_STATE;
+  const size_t n4 = 4 * (size_t)c.d.Nc;
+  if (c.C == 0) return LMFS_OK;
+  if (A) LMFS_CUDA(cudaMemcpyAsync(A, c.prob[problem].A, c.C * n4 * n4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  if (E) LMFS_CUDA(cudaMemcpyAsync(E, c.prob[problem].E, c.C * 6 * n4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  return LMFS_OK;
+}
+
+int lmfs_set_pair_blocks(lmfs_handle h, int problem, const double* A, const double* E) {
+  if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) || (h->c.C && (!A || !E))) return LMFS_ERR_INVALID;
+  Ctx& c = h->c;
+  PairBlocks& pb = c.prob[problem];
+  if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
+  const size_t n4 = 4 * (size_t)c.d.Nc;
+  if (!pb.A) LMFS_TRY(dalloc(&pb.A, std::max<size_t>(c.C, 1) * n4 * n4));
+  if (!pb.E) LMFS_TRY(dalloc(&pb.E, std::max<size_t>(c.C, 1) * 6 * n4));
+  if (c.C) {
+    LMFS_CUDA(cudaMemcpyAsync(pb.A, A, c.C * n4 * n4 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    LMFS_CUDA(cudaMemcpyAsync(pb.E, E, c.C * 6 * n4 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  }
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  pb.ready = true;
+  return LMFS_OK;
+}
+
+int lmfs_matvec(lmfs_handle h, int problem, const double* mu_dev, double* u_dev, int precision) {
+  if (!h || !mu_dev || !u_dev || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) ||
+      (precision != LMFS_FP64 && precision != LMFS_MIXED && precision != LMFS_MIXED_DIRECT))
+    return LMFS_ERR_INVALID;
+  return matvec_device(h->c, problem, mu_dev, u_dev, precision);
+}
+
+int lmfs_rhs(lmfs_handle h, int problem, const double* in_dev, double* b_dev, int precision) {
+  if (!h || !in_dev || !b_dev || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) ||
+      (precision != LMFS_FP64 && precision != LMFS_MIXED && precision != LMFS_MIXED_DIRECT))
+    return LMFS_ERR_INVALID;
+  return rhs_device(h->c, problem, in_dev, b_dev, precision);
+}
+
+int lmfs_solve_device(lmfs_handle h, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
+  if (!h || !in_dev || !out_dev) return LMFS_ERR_INVALID;
+  LMFS_CUDA(cudaSetDevice(h->c.device));
+  return solve_dev(h->c, problem, in_dev, out_dev, info);
+}
+
+int lmfs_solve(lmfs_handle h, int problem, const double* in, double* out, lmfs_solve_info* info) {
+  if (!h || !in || !out) return LMFS_ERR_INVALID;
+  Ctx& c = h->c;
+  LMFS_CUDA(cudaSetDevice(c.device));
+  for (int i = 0; i < 3 * c.d.P; ++i)
+    if (!std::isfinite(in[i])) { set_last_error("non-finite input"); return LMFS_ERR_INVALID; }
+  LMFS_CUDA(cudaMemcpyAsync(c.io3, in, 3 * (size_t)c.d.P * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  double* outd = nullptr;
+  LMFS_TRY(dalloc(&outd, 3 * (size_t)c.d.P));
+  int rc = solve_dev(c, problem, c.io3, outd, info);
+  if (rc == LMFS_OK || rc == LMFS_ERR_NOT_CONVERGED) {
+    if (cuda_failed(cudaMemcpyAsync(out, outd, 3 * (size_t)c.d.P * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+        cuda_failed(cudaStreamSynchronize(c.stream), "sync"))
+      rc = LMFS_ERR_CUDA;
+  }
+  dfree(outd);
+  return rc;
+}
+
+int lmfs_invalidate(lmfs_handle h) {
+  if (!h) return LMFS_ERR_INVALID;
+  Ctx& c = h->c;
+  LMFS_CUDA(cudaSetDevice(c.device));
+  // re-run contact detection on the device; the geometry is unchanged, so the
+  // pair lists (and every allocation sized from them) stay valid
+  const int C0 = c.C;
+  std::vector<int> pairs0 = c.pairs_h;
+  LMFS_TRY(detect_contacts(c));
+  if (c.C != C0 || c.pairs_h != pairs0) { set_last_error("contact list changed"); return LMFS_ERR_STATE; }
+  for (auto& pb : c.prob) pb.ready = false;
+  c.have_solution = false;
+  return LMFS_OK;
+}
+
+int lmfs_stats(lmfs_handle h, int problem, double* out) {
+  if (!h || !out || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
+  const PairBlocks& pb = h->c.prob[problem];
+  out[0] = pb.t_ms; out[1] = pb.qr_ms; out[2] = pb.qr_flops;
+  out[3] = pb.min_rank_F; out[4] = pb.max_rank_F; out[5] = h->c.C;
+  out[6] = h->c.far_split; out[7] = (double)h->c.near_h.size();
+  return LMFS_OK;
+}
+
+int lmfs_get_solution(lmfs_handle h, double* mu_dev) {
+  if (!h || !mu_dev) return LMFS_ERR_INVALID;
+  if (!h->c.have_solution) return LMFS_ERR_STATE;
+  LMFS_CUDA(cudaMemcpyAsync(mu_dev, h->c.xsol, 2 * (size_t)h->c.d.P * h->c.d.Mc * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->c.stream));
+  return LMFS_OK;
+}
+
+int lmfs_stokeslet_sum(const double* targets, int nt, const double* centres, const double* offsets,
+                       const double* strengths, int nd, int n_per_disk, double mu, int precision, void* stream,
+                       double* out) {
+  return stokeslet_sum_standalone(targets, nt, centres, offsets, strengths, nd, n_per_disk, mu, precision,
+                                  (cudaStream_t)stream, out);
+}
+
+int lmfs_launch_count(uint64_t* out) {
+  if (!out) return LMFS_ERR_INVALID;
+  *out = lmfs::g_launches.load();
+  return LMFS_OK;
+}
+
+const char* lmfs_strerror(int code) {
+  static thread_local std::string s;
+  const char* base = "unknown error";
+  switch (code) {
+    case LMFS_OK: base = "ok"; break;
+    case LMFS_PENDING: base = "pending"; break;
+    case LMFS_ERR_INVALID: base = "invalid argument"; break;
+    case LMFS_ERR_CUDA: base = "CUDA error"; break;
+    case LMFS_ERR_NOMEM: base = "out of memory"; break;
+    case LMFS_ERR_NOT_CONVERGED: base = "GMRES did not converge"; break;
+    case LMFS_ERR_STATE: base = "call out of order"; break;
+    case LMFS_ERR_TIMEOUT: base = "timed out"; break;
+    case LMFS_ERR_TOO_LARGE: base = "request exceeds the memory budget"; break;
+    case LMFS_ERR_NUMERICAL: base = "non-finite value in a factorization"; break;
+  }
+  s = base;
+  if (code < 0 && !g_last_error.empty()) s += " (" + g_last_error + ")";
+  return s.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Contact detection (Algorithm 2, precomputation: pairs with gap <= delta_c,
+// Sec. 6) and the near-interaction lists, on the device; CSR bookkeeping on
+// the host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "lmfs_internal.h"
+
+namespace lmfs {
+namespace {
+
+// Pass 1 (counts) and pass 2 (writes) share this kernel.  Thread i scans
+// k > i in increasing order, so the output is sorted by (i, k).
+//   close: gap <= delta_c;   near: gap < g_near;   overlap: gap <= 0.
+__global__ void contacts_kernel(const double* __restrict__ c, const double* __restrict__ r, int P,
+                                double delta_c, double g_near, int* cnt_close, int* cnt_near,
+                                int* n_overlap, const int* off_close, const int* off_near,
+                                int* out_close, int* out_near) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const double xi = c[2 * i], yi = c[2 * i + 1], ri = r[i];
+  int nc = 0, nn = 0, no = 0;
+  for (int k = i + 1; k < P; ++k) {
+    const double dx = c[2 * k] - xi, dy = c[2 * k + 1] - yi;
+    const double gap = sqrt(dx * dx + dy * dy) - ri - r[k];
+    if (gap <= 0.0) ++no;
+    if (gap <= delta_c) {
+      if (out_close) { out_close[2 * (off_close[i] + nc)] = i; out_close[2 * (off_close[i] + nc) + 1] = k; }
+      ++nc;
+    }
+    if (gap < g_near) {
+      if (out_near) { out_near[2 * (off_near[i] + nn)] = i; out_near[2 * (off_near[i] + nn) + 1] = k; }
+      ++nn;
+    }
+  }
+  if (cnt_close) { cnt_close[i] = nc; cnt_near[i] = nn; }
+  if (no && n_overlap) atomicAdd(n_overlap, no);
+}
+
+}  // namespace
+
+int detect_contacts(Ctx& c) {
+  const int P = c.d.P;
+  const double g_near = c.prm.delta_c > 3.0 ? c.prm.delta_c : 3.0;
+  int *cc = nullptr, *cn = nullptr, *nov = nullptr, *oc = nullptr, *on = nullptr;
+  int *pc = nullptr, *pn = nullptr;
+  int rc = LMFS_OK;
+  std::vector<int> hcc(P), hcn(P), hoc(P + 1, 0), hon(P + 1, 0);
+  int hov = 0;
+  const int thr = 128, blk = (P + thr - 1) / thr;
+  if ((rc = dalloc(&cc, P)) || (rc = dalloc(&cn, P)) || (rc = dalloc(&nov, 1)) ||
+      (rc = dalloc(&oc, P + 1)) || (rc = dalloc(&on, P + 1)))
+    goto done;
+  if (cuda_failed(cudaMemsetAsync(nov, 0, sizeof(int), c.stream), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
+  contacts_kernel<<<blk, thr, 0, c.stream>>>(c.centres, c.radii, P, c.prm.delta_c, g_near, cc, cn,
+                                             nov, nullptr, nullptr, nullptr, nullptr);
+  if ((rc = check_launch("contacts count"))) goto done;
+  if (cuda_failed(cudaMemcpyAsync(hcc.data(), cc, P * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+      cuda_failed(cudaMemcpyAsync(hcn.data(), cn, P * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+      cuda_failed(cudaMemcpyAsync(&hov, nov, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+      cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
+  if (hov > 0) { set_last_error("overlapping or touching disks (gap <= 0)"); rc = LMFS_ERR_INVALID; goto done; }
+  for (int i = 0; i < P; ++i) { hoc[i + 1] = hoc[i] + hcc[i]; hon[i + 1] = hon[i] + hcn[i]; }
+  c.C = hoc[P];
+  {
+    const int nnear = hon[P];
+    if ((rc = dalloc(&pc, 2 * (size_t)std::max(c.C, 1))) || (rc = dalloc(&pn, 2 * (size_t)std::max(nnear, 1)))) goto done;
+    if (cuda_failed(cudaMemcpyAsync(oc, hoc.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+        cuda_failed(cudaMemcpyAsync(on, hon.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d")) {
+      rc = LMFS_ERR_CUDA; goto done;
+    }
+    contacts_kernel<<<blk, thr, 0, c.stream>>>(c.centres, c.radii, P, c.prm.delta_c, g_near, nullptr,
+                                               nullptr, nullptr, oc, on, pc, pn);
+    if ((rc = check_launch("contacts write"))) goto done;
+    std::vector<int> hnear(2 * (size_t)nnear);
+    c.pairs_h.assign(2 * (size_t)c.C, 0);
+    if ((c.C && cuda_failed(cudaMemcpyAsync(c.pairs_h.data(), pc, 2 * (size_t)c.C * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h")) ||
+        (nnear && cuda_failed(cudaMemcpyAsync(hnear.data(), pn, 2 * (size_t)nnear * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h")) ||
+        cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
+    // per-disk incident pairs, in pair order
+    c.csr_off_h.assign(P + 1, 0);
+    for (int q = 0; q < c.C; ++q) { c.csr_off_h[c.pairs_h[2 * q] + 1]++; c.csr_off_h[c.pairs_h[2 * q + 1] + 1]++; }
+    for (int i = 0; i < P; ++i) c.csr_off_h[i + 1] += c.csr_off_h[i];
+    c.csr_ent_h.assign(2 * (size_t)c.C, 0);
+    {
+      std::vector<int> fill(c.csr_off_h.begin(), c.csr_off_h.end() - 1);
+      for (int q = 0; q < c.C; ++q) {
+        c.csr_ent_h[fill[c.pairs_h[2 * q]]++] = 2 * q;
+        c.csr_ent_h[fill[c.pairs_h[2 * q + 1]]++] = 2 * q + 1;
+      }
+    }
+    // near lists: every k with gap < g_near (both directions) plus self
+    std::vector<std::vector<NearEntry>> per(P);
+    for (int i = 0; i < P; ++i) per[i].push_back({i, 2, -1, 0});
+    for (int e = 0; e < nnear; ++e) {
+      const int i = hnear[2 * e], k = hnear[2 * e + 1];
+      per[i].push_back({k, 0, -1, 0});
+      per[k].push_back({i, 0, -1, 0});
+    }
+    for (int q = 0; q < c.C; ++q) {
+      const int i = c.pairs_h[2 * q], k = c.pairs_h[2 * q + 1];
+      for (auto& e : per[i]) if (e.k == k) { e.kind = 1; e.pair = q; e.side = 1; }
+      for (auto& e : per[k]) if (e.k == i) { e.kind = 1; e.pair = q; e.side = 0; }
+    }
+    c.near_off_h.assign(P + 1, 0);
+    c.near_h.clear();
+    for (int i = 0; i < P; ++i) {
+      std::sort(per[i].begin(), per[i].end(), [](const NearEntry& a, const NearEntry& b) { return a.k < b.k; });
+      for (auto& e : per[i]) c.near_h.push_back(e);
+      c.near_off_h[i + 1] = (int)c.near_h.size();
+    }
+  }
+done:
+  dfree(cc); dfree(cn); dfree(nov); dfree(oc); dfree(on); dfree(pc); dfree(pn);
+  return rc;
+}
+
+// Upload the pair and near lists and the FP32 target/disk tables.
+int upload_geometry(Ctx& c) {
+  const int P = c.d.P, Mc = c.d.Mc;
+  LMFS_TRY(dalloc(&c.pairs, 2 * (size_t)std::max(c.C, 1)));
+  LMFS_TRY(dalloc(&c.csr_off, P + 1));
+  LMFS_TRY(dalloc(&c.csr_ent, 2 * (size_t)std::max(c.C, 1)));
+  LMFS_TRY(dalloc(&c.near_off, P + 1));
+  LMFS_TRY(dalloc(&c.near_ent, c.near_h.size()));
+  LMFS_TRY(dalloc(&c.far_excl_off, P + 1));
+  LMFS_TRY(dalloc(&c.far_excl, c.near_h.size()));
+  LMFS_TRY(dalloc(&c.tgt32, (size_t)P * Mc));
+  LMFS_TRY(dalloc(&c.dsk32, (size_t)P * 2));
+  std::vector<int4> ne(c.near_h.size());
+  std::vector<int> fx(c.near_h.size());
+  for (size_t e = 0; e < c.near_h.size(); ++e) {
+    ne[e] = make_int4(c.near_h[e].k, c.near_h[e].kind, c.near_h[e].pair, c.near_h[e].side);
+    fx[e] = c.near_h[e].k;
+  }
+  std::vector<float2> t(P * (size_t)Mc);
+  std::vector<float4> dk(2 * (size_t)P);
+  for (int i = 0; i < P; ++i) {
+    for (int m = 0; m < Mc; ++m) {
+      const double th = 2.0 * LMFS_PI * m / Mc;
+      t[(size_t)i * Mc + m] = make_float2((float)(c.radii_h[i] * cos(th)), (float)(c.radii_h[i] * sin(th)));
+    }
+    const double cx = c.centres_h[2 * i], cy = c.centres_h[2 * i + 1];
+    const float hx = (float)cx, hy = (float)cy;
+    dk[2 * i] = make_float4(hx, hy, (float)(cx - (double)hx), (float)(cy - (double)hy));
+    dk[2 * i + 1] = make_float4(0.f, 0.f, (float)c.radii_h[i], 0.f);
+  }
+  cudaStream_t s = c.stream;
+  if (c.C) {
+    LMFS_CUDA(cudaMemcpyAsync(c.pairs, c.pairs_h.data(), 2 * (size_t)c.C * sizeof(int), cudaMemcpyHostToDevice, s));
+    LMFS_CUDA(cudaMemcpyAsync(c.csr_ent, c.csr_ent_h.data(), 2 * (size_t)c.C * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  LMFS_CUDA(cudaMemcpyAsync(c.csr_off, c.csr_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  LMFS_CUDA(cudaMemcpyAsync(c.near_off, c.near_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  LMFS_CUDA(cudaMemcpyAsync(c.near_ent, ne.data(), ne.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  LMFS_CUDA(cudaMemcpyAsync(c.far_excl_off, c.near_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  LMFS_CUDA(cudaMemcpyAsync(c.far_excl, fx.data(), fx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  LMFS_CUDA(cudaMemcpyAsync(c.tgt32, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+  LMFS_CUDA(cudaMemcpyAsync(c.dsk32, dk.data(), dk.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+  LMFS_CUDA(cudaStreamSynchronize(s));
+  return LMFS_OK;
+}
+
+}  // namespace lmfs

@@ -1,0 +1,279 @@
+// Unrestarted GMRES on the device (the solver of Algorithm 2; restart, start
+// vector and orthogonalization are not specified by the paper): x0 = 0,
+// classical Gram-Schmidt applied twice (CGS2) in FP64, Givens rotations in
+// FP64 by a single device thread, stop at |g_{j+1}| / ||b|| <= tol.
+//
+// One iteration (copy V_j -> work, matvec, two CGS passes, normalisation,
+// Givens, j += 1) reads its column index j from device memory, so it is
+// captured once into a CUDA graph and replayed; the host reads the residual
+// estimate after each replay.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "lmfs_internal.h"
+
+namespace lmfs {
+namespace {
+
+constexpr int RB = 256;            // threads per block in the reductions
+constexpr int ROWS_PER_BLOCK = 4096;
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v) {
+  __shared__ double red[RB / 32];
+  v = wsum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (lane < RB / 32) ? red[lane] : 0.0;
+    t = wsum(t);
+  }
+  return t;   // valid in thread 0
+}
+
+// part[i][blk] = sum_{rows in blk} V_i[row] * w[row] for i <= j
+__global__ void dots_kernel(const double* V, long long n, const double* w, const int* jdev, int cap,
+                            double* part, int nblk) {
+  const int i = blockIdx.y;
+  const int j = *jdev;
+  if (i > j) return;
+  const double* v = V + (long long)i * n;
+  const long long r0 = (long long)blockIdx.x * ROWS_PER_BLOCK;
+  const long long r1 = min(n, r0 + ROWS_PER_BLOCK);
+  double acc = 0.0;
+  for (long long r = r0 + threadIdx.x; r < r1; r += RB) acc += v[r] * w[r];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[(long long)i * nblk + blockIdx.x] = acc;
+  (void)cap;
+}
+
+// h[i] (+)= sum_blk part[i][blk]   (fixed order); also stores into H(:, j)
+__global__ void dots_reduce(const double* part, int nblk, const int* jdev, int cap, double* hcoef,
+                            double* H, int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = *jdev;
+  if (i > j) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += part[(long long)i * nblk + b];
+  hcoef[i] = acc;
+  double* Hj = H + (long long)j * (cap + 1);
+  Hj[i] = accumulate ? Hj[i] + acc : acc;
+}
+
+// w -= sum_{i<=j} V_i h_i
+__global__ void orth_update(const double* V, long long n, double* w, const double* hcoef, const int* jdev) {
+  const int j = *jdev;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double acc = w[r];
+    for (int i = 0; i <= j; ++i) acc -= V[(long long)i * n + r] * hcoef[i];
+    w[r] = acc;
+  }
+}
+
+__global__ void norm_part(const double* w, long long n, double* part) {
+  const long long r0 = (long long)blockIdx.x * ROWS_PER_BLOCK;
+  const long long r1 = min(n, r0 + ROWS_PER_BLOCK);
+  double acc = 0.0;
+  for (long long r = r0 + threadIdx.x; r < r1; r += RB) acc += w[r] * w[r];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// h_{j+1,j} = ||w||; Givens rotations; residual estimate.  scal: [0] beta,
+// [1] relres, [2] h_{j+1,j}, [3] breakdown flag.
+__global__ void givens_kernel(const double* part, int nblk, int* jdev, int cap, double* H, double* g,
+                              double* cs, double* sn, double* scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = *jdev;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[b];
+  const double hn = sqrt(s);
+  double* Hj = H + (long long)j * (cap + 1);
+  Hj[j + 1] = hn;
+  scal[2] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+    Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+    Hj[i] = t;
+  }
+  const double den = hypot(Hj[j], Hj[j + 1]);
+  cs[j] = den > 0 ? Hj[j] / den : 1.0;
+  sn[j] = den > 0 ? Hj[j + 1] / den : 0.0;
+  Hj[j] = den;
+  Hj[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  scal[1] = fabs(g[j + 1]) / scal[0];
+  scal[3] = (hn == 0.0) ? 1.0 : 0.0;
+}
+
+// V_{j+1} = w / h_{j+1,j}; then j += 1 (one thread bumps the counter last)
+__global__ void normalize_next(double* V, long long n, const double* w, const int* jdev, const double* scal) {
+  const int j = *jdev;
+  const double h = scal[2];
+  const double inv = h > 0 ? 1.0 / h : 0.0;
+  double* vn = V + (long long)(j + 1) * n;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    vn[r] = w[r] * inv;
+}
+__global__ void bump_j(int* jdev) { if (threadIdx.x == 0 && blockIdx.x == 0) *jdev += 1; }
+
+__global__ void copy_vj(const double* V, long long n, const int* jdev, double* out) {
+  const int j = *jdev;
+  const double* v = V + (long long)j * n;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    out[r] = v[r];
+}
+
+// beta = ||b||, V_0 = b / beta, g = (beta, 0, ...), j = 0
+__global__ void init_kernel(const double* part, int nblk, double* scal, double* g, int cap, int* jdev) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[b];
+  scal[0] = sqrt(s);
+  scal[1] = 1.0;
+  for (int i = 0; i <= cap; ++i) g[i] = 0.0;
+  g[0] = scal[0];
+  *jdev = 0;
+}
+__global__ void scale_kernel(const double* b, long long n, const double* scal, double* v) {
+  const double beta = scal[0];
+  const double inv = beta > 0 ? 1.0 / beta : 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    v[r] = b[r] * inv;
+}
+
+// Back substitution of the k x k upper triangle (columns of H, leading
+// dimension cap + 1) and x = V y.  Single thread for y (k <= a few hundred).
+__global__ void solve_y(const double* H, int cap, const double* g, int k, double* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c < k; ++c) s -= H[(long long)c * (cap + 1) + i] * y[c];
+    y[i] = s / H[(long long)i * (cap + 1) + i];
+  }
+}
+__global__ void combine_x(const double* V, long long n, const double* y, int k, double* x) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += V[(long long)i * n + r] * y[i];
+    x[r] = acc;
+  }
+}
+
+}  // namespace
+
+void gmres_free(Ctx& c) {
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 3; ++b)
+      if (c.graph_exec[a][b]) { cudaGraphExecDestroy(c.graph_exec[a][b]); c.graph_exec[a][b] = nullptr; }
+  dfree(c.V); dfree(c.w); dfree(c.H); dfree(c.gvec); dfree(c.cs); dfree(c.sn); dfree(c.hpart);
+  dfree(c.scal); dfree(c.jdev);
+  if (c.host_pinned) { cudaFreeHost(c.host_pinned); c.host_pinned = nullptr; }
+  c.gm_cap = 0;
+}
+
+static int gmres_alloc(Ctx& c, int cap) {
+  if (c.gm_cap >= cap) return LMFS_OK;
+  gmres_free(c);
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+  LMFS_TRY(dalloc(&c.V, (size_t)(cap + 1) * n));
+  LMFS_TRY(dalloc(&c.w, (size_t)n));
+  LMFS_TRY(dalloc(&c.H, (size_t)(cap + 1) * (cap + 1)));
+  LMFS_TRY(dalloc(&c.gvec, (size_t)cap + 2));
+  LMFS_TRY(dalloc(&c.cs, (size_t)cap + 1));
+  LMFS_TRY(dalloc(&c.sn, (size_t)cap + 1));
+  LMFS_TRY(dalloc(&c.hpart, (size_t)(cap + 2) * nblk + (cap + 2)));
+  LMFS_TRY(dalloc(&c.scal, 8));
+  LMFS_TRY(dalloc(&c.jdev, 2));
+  if (cudaMallocHost((void**)&c.host_pinned, 8 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return LMFS_ERR_NOMEM; }
+  c.gm_cap = cap;
+  return LMFS_OK;
+}
+
+// One Arnoldi step on the handle's stream (graph-capturable: no host sync).
+static int arnoldi_step(Ctx& c, int problem, int precision) {
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+  const int cap = c.gm_cap;
+  double* hcoef = c.hpart + (long long)(cap + 1) * nblk;
+  const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
+  copy_vj<<<eb, 256, 0, c.stream>>>(c.V, n, c.jdev, c.bvec);
+  LMFS_TRY(check_launch("copy_vj"));
+  LMFS_TRY(matvec_device(c, problem, c.bvec, c.w, precision));
+  for (int pass = 0; pass < 2; ++pass) {
+    dots_kernel<<<dim3(nblk, cap), RB, 0, c.stream>>>(c.V, n, c.w, c.jdev, cap, c.hpart, nblk);
+    dots_reduce<<<(cap + 127) / 128, 128, 0, c.stream>>>(c.hpart, nblk, c.jdev, cap, hcoef, c.H, pass);
+    orth_update<<<eb, 256, 0, c.stream>>>(c.V, n, c.w, hcoef, c.jdev);
+  }
+  norm_part<<<nblk, RB, 0, c.stream>>>(c.w, n, c.hpart);
+  givens_kernel<<<1, 32, 0, c.stream>>>(c.hpart, nblk, c.jdev, cap, c.H, c.gvec, c.cs, c.sn, c.scal);
+  normalize_next<<<eb, 256, 0, c.stream>>>(c.V, n, c.w, c.jdev, c.scal);
+  bump_j<<<1, 32, 0, c.stream>>>(c.jdev);
+  return check_launch("arnoldi");
+}
+
+int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, lmfs_solve_info* info) {
+  const int maxit = std::max(1, c.prm.maxit);
+  LMFS_TRY(gmres_alloc(c, maxit));
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+  const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
+  norm_part<<<nblk, RB, 0, c.stream>>>(b, n, c.hpart);
+  init_kernel<<<1, 32, 0, c.stream>>>(c.hpart, nblk, c.scal, c.gvec, c.gm_cap, c.jdev);
+  scale_kernel<<<eb, 256, 0, c.stream>>>(b, n, c.scal, c.V);
+  note_launches(2);
+  LMFS_TRY(check_launch("gmres init"));
+  LMFS_CUDA(cudaMemcpyAsync(c.host_pinned, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  const double beta = c.host_pinned[0];
+  int iters = 0;
+  double relres = 1.0;
+  if (beta > 0.0) {
+    cudaGraphExec_t& ge = c.graph_exec[problem][precision];  // precision < 3
+    if (!ge) {
+      cudaGraph_t g;
+      LMFS_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = arnoldi_step(c, problem, precision);
+      cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+      if (rc != LMFS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return rc; }
+      LMFS_CUDA(e);
+      size_t nn = 0;
+      cudaGraphGetNodes(g, nullptr, &nn);
+      c.graph_nodes[problem][precision] = nn;
+      LMFS_CUDA(cudaGraphInstantiate(&ge, g, 0));
+      cudaGraphDestroy(g);
+    }
+    for (int it = 0; it < maxit; ++it) {
+      LMFS_CUDA(cudaGraphLaunch(ge, c.stream));
+      note_launches(c.graph_nodes[problem][precision]);
+      LMFS_CUDA(cudaMemcpyAsync(c.host_pinned + 1, c.scal + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      LMFS_CUDA(cudaStreamSynchronize(c.stream));
+      iters = it + 1;
+      relres = c.host_pinned[1];
+      if (!(relres == relres)) { set_last_error("GMRES produced a non-finite residual"); return LMFS_ERR_NUMERICAL; }
+      if (relres <= c.prm.tol || c.host_pinned[3] != 0.0) break;
+    }
+    double* y = c.hpart;  // reuse
+    solve_y<<<1, 32, 0, c.stream>>>(c.H, c.gm_cap, c.gvec, iters, y);
+    combine_x<<<eb, 256, 0, c.stream>>>(c.V, n, y, iters, x);
+    note_launches(1);
+    LMFS_TRY(check_launch("gmres finish"));
+  } else {
+    LMFS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), c.stream));
+    relres = 0.0;
+  }
+  if (info) { info->iters = iters; info->relres = relres; }
+  return relres <= c.prm.tol ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
+}
+
+}  // namespace lmfs

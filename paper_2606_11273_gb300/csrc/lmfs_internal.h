@@ -1,0 +1,213 @@
+// Internal declarations shared by the lmfs translation units (not part of the
+// public ABI).  Device data layout (all FP64 unless stated):
+//   centres [P][2], radii [P]
+//   mu, u, b            [P][Mc][2]      surface vectors (x, y interleaved)
+//   lb, lam, sig        [P][Nc][2]      one-body, corrected and projected strengths
+//   tilde               [C][4Nc]        per-pair corrections  A [lb_i; lb_k]
+//   A                   [C][4Nc][4Nc]   row-major;  E [C][6][4Nc]
+//   one-body factors per radius class: W [2Nc][2Mc] (rows < rank used),
+//   R [2Nc][2Nc] column-major upper triangle, perm [2Nc], rank
+//   far-field FP32 sources: src4 [P][Nc] float4 (y_x, y_y, |y|^2, y.sigma),
+//   src2 [P][Nc] float2 (sigma_x, sigma_y), disk data dsk [P] float4x2.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lmfs.h"
+
+#define LMFS_PI 3.14159265358979323846
+
+namespace lmfs {
+
+struct Status {
+  int code = LMFS_OK;
+  std::string msg;
+};
+
+// Records the first CUDA error; returns true on failure.
+bool cuda_failed(cudaError_t e, const char* what);
+void set_last_error(const std::string& s);
+
+// Integer geometry of a problem size.
+struct Dims {
+  int P = 0, Nc = 0, Mc = 0;
+  int nsrc() const { return 2 * Nc; }
+  int nnode() const { return 2 * Mc; }
+};
+
+// ---- one-body factors (per radius class) ---------------------------------
+struct OneBody {
+  int nclass = 0;
+  double* W = nullptr;     // [nclass][2Nc][2Mc]
+  double* R = nullptr;     // [nclass][2Nc][2Nc] column-major
+  int* perm = nullptr;     // [nclass][2Nc]
+  int* rank = nullptr;     // [nclass]
+  std::vector<int> rank_h;
+};
+
+struct PairBlocks {
+  bool ready = false;
+  double* A = nullptr;     // [C][4Nc][4Nc]
+  double* E = nullptr;     // [C][6][4Nc]
+  OneBody ob;
+  double t_ms = 0.0;             // wall time of the last pair precompute
+  double qr_ms = 0.0;            // QR kernel time (CUDA events on the handle's stream)
+  double qr_flops = 0.0;         // algorithmic FP64 flops of those QR launches
+  int max_rank_F = 0, min_rank_F = 0;
+};
+
+// Near-interaction list: for each target disk i, the source disks handled in
+// FP64 by the near kernel (close partners, neighbours within the near radius,
+// and -- for the completion flow only -- the disk itself).  kind: 0 regular,
+// 1 close partner (matvec uses the modified strength rho), 2 self.
+struct NearEntry {
+  int k;       // source disk
+  int kind;    // 0 regular, 1 close, 2 self
+  int pair;    // pair index for kind 1, else -1
+  int side;    // side of disk k in that pair (0: first, 1: second)
+};
+
+struct Ctx {
+  lmfs_params prm{};
+  Dims d;
+  int C = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;           // created by the handle (no caller stream given)
+  int device = 0;
+  double Rc = 0, Rf = 0, rho = 0;
+
+  std::vector<double> centres_h, radii_h;
+  std::vector<int> pairs_h;          // [C][2]
+  std::vector<int> csr_off_h;        // [P+1] incident pairs per disk
+  std::vector<int> csr_ent_h;        // [2C]  pair*2 + side
+  std::vector<int> near_off_h;       // [P+1]
+  std::vector<NearEntry> near_h;
+  std::vector<int> cls_h;            // radius class per disk
+  std::vector<double> cls_r_h;       // radius of each class
+
+  // device geometry
+  double* centres = nullptr;
+  double* radii = nullptr;
+  int* cls = nullptr;
+  double* cls_r = nullptr;
+  int* pairs = nullptr;
+  int* csr_off = nullptr;
+  int* csr_ent = nullptr;
+  int* near_off = nullptr;
+  int4* near_ent = nullptr;          // (k, kind, pair, side)
+  int* far_excl_off = nullptr;       // [P+1] sorted source disks the far kernel skips
+  int* far_excl = nullptr;
+  float2* tgt32 = nullptr;           // [P][Mc] node offsets x - c (FP32)
+  float4* dsk32 = nullptr;           // [P][2] (c_hi, c_lo), (sum sigma, 0, 0)
+
+  PairBlocks prob[2];
+
+  // matvec workspace
+  double* lb = nullptr;
+  double* lam = nullptr;
+  double* sig = nullptr;
+  double* tilde = nullptr;
+  double* ufar = nullptr;
+  double* lam0 = nullptr;
+  float4* src4 = nullptr;
+  float2* src2 = nullptr;
+  int far_split = 1;                 // source-range split of the far kernel
+  double* ufar_part = nullptr;       // [far_split][P][Mc][2]
+  int* far_err = nullptr;            // set by the far kernel if a bounded wait expired
+  double2* coef64 = nullptr;         // [P][64] multipole coefficients (FP64)
+  float2* coef32 = nullptr;          // [P][64] the same rounded to FP32
+
+  // GMRES workspace
+  int gm_cap = 0;                    // basis capacity (maxit + 1 vectors)
+  double* V = nullptr;               // [cap][n]
+  double* w = nullptr;
+  double* H = nullptr;               // [cap][cap] column j holds H(:, j)
+  double* gvec = nullptr;            // [cap+1] (g), cs, sn
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* hpart = nullptr;           // partial dot products
+  double* scal = nullptr;            // device scalars: [0] beta, [1] relres, ...
+  int* jdev = nullptr;
+  double* bvec = nullptr;
+  double* xsol = nullptr;
+  double* io3 = nullptr;             // [P][3]
+  double* host_pinned = nullptr;     // pinned scalars
+  cudaGraphExec_t graph_exec[2][3] = {};
+  size_t graph_nodes[2][3] = {};
+  bool have_solution = false;
+};
+
+// ---- geometry (lmfs_geom.cu) ----------------------------------------------
+int detect_contacts(Ctx& c);          // fills pairs_h, csr, near lists
+int upload_geometry(Ctx& c);
+
+// ---- precompute (lmfs_precompute.cu) -------------------------------------
+int build_onebody(Ctx& c, int problem, OneBody& ob);
+int build_pair_blocks(Ctx& c, int problem);
+
+// ---- batched QR (lmfs_qr.cu) ---------------------------------------------
+// Column-pivoted Householder QR of nb column-major matrices [m][n + k] (leading
+// dimension ld, stride between matrices mstride), truncated at |R_jj| <=
+// eps |R_00|, then the truncated basic solution X (n x k) of A X ~ B where B
+// is the trailing k columns.  X written to Xout (column-major [n][k], stride
+// xstride).  If keep_factors, R and perm stay in the workspace for the caller.
+struct QRBatch {
+  double* A;        // workspace, overwritten
+  long long mstride;
+  int* m;           // per matrix rows   (device)
+  int* n;           // per matrix columns of the coefficient part
+  int k;            // right-hand sides (same for all)
+  int ld;           // leading dimension (>= max m)
+  double eps;
+  double* X;        // solutions [nb][xld][k] column-major, xld >= max n
+  int xld;
+  long long xstride;
+  int* rank;        // out: numerical rank per matrix
+  int* perm;        // out/work: [nb][permstride]
+  int permstride;
+  double* tau;      // work [nb][permstride]
+  double* vn;       // work [nb][2*permstride]
+  int* info;        // out: 0 ok, 1 non-finite
+  int nb;
+  int nmax;
+};
+int qr_solve_batched(const QRBatch& q, cudaStream_t s, bool solve);
+
+// ---- matvec pieces (lmfs_matvec.cu) ---------------------------------------
+int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb);
+int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision);
+int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision);
+int post_device(Ctx& c, int problem, const double* mu, double* out3);
+int far_field(Ctx& c, const double* strength, double* out, int precision, bool mobility_sums_zero);
+int far_field_prepare(Ctx& c);
+int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar,
+               double* u, int problem);
+int stokeslet_sum_standalone(const double* targets, int nt, const double* centres,
+                             const double* offsets, const double* strengths, int nd, int npd,
+                             double mu, int precision, cudaStream_t s, double* out);
+
+// ---- GMRES (lmfs_gmres.cu) ------------------------------------------------
+int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x,
+                lmfs_solve_info* info);
+void gmres_free(Ctx& c);
+
+// ---- memory ---------------------------------------------------------------
+template <class T>
+int dalloc(T** p, size_t count) {
+  if (count == 0) { *p = nullptr; return LMFS_OK; }
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); return LMFS_ERR_NOMEM; }
+  return LMFS_OK;
+}
+template <class T>
+void dfree(T*& p) { if (p) cudaFree((void*)p); p = nullptr; }
+
+int check_launch(const char* what);
+void note_launches(unsigned long long n);   // launches not followed by check_launch
+
+}  // namespace lmfs
+
+#define LMFS_TRY(x) do { int _rc = (x); if (_rc != LMFS_OK) return _rc; } while (0)
+#define LMFS_CUDA(x) do { if (lmfs::cuda_failed((x), #x)) return LMFS_ERR_CUDA; } while (0)

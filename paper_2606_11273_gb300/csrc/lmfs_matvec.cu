@@ -1,0 +1,1081 @@
+// The two-body matrix-vector product (Algorithm 3; mobility with projected
+// strengths, Sec. 4.4), its right-hand sides and post-processing, on the
+// device.
+//
+// Algorithm 3 evaluates the far field from every source (self and close
+// partners included, Step 2a) and then subtracts the pair-internal and self
+// terms (Step 2b).  Expanding Step 2b shows that every self term and every
+// close partner's own one-body and correction strengths cancel exactly, so
+// this implementation never adds them:
+//   u^(i) = mu^(i) + sum_{k not in C(i) u {i}} S^(ik) sigma^(k)
+//                  + sum_{k in C(i)} S^(ik) proj_k( sum_{n in C(k), n != i} lam~_k^(k-n) )
+// with sigma = proj(lam), lam = lam_bar + sum lam~ (eq. (total_corr)) and proj
+// = I (resistance) or I - L (mobility).  The first sum runs in the FP32 (or
+// FP64) far-field kernel over disks outside a near radius; every disk inside
+// it (close partners with the modified strengths above, and regular
+// neighbours) is summed in FP64 by the near kernel.
+#include <algorithm>
+#include <cmath>
+
+#include "lmfs_internal.h"
+
+namespace lmfs {
+namespace {
+
+constexpr double INV4PI = 1.0 / (4.0 * LMFS_PI);
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- Step 1a: lam_bar = Pi^+ mu, per disk, one warp per disk ----------------
+// Pi^+ applied from its QR factors: t = W mu (W = first r rows of Q^T),
+// R[0:r,0:r] z = t (back substitution), lam_bar[perm[j]] = z_j.
+__global__ void onebody_apply_kernel(const double* __restrict__ W, const double* __restrict__ R,
+                                     const int* __restrict__ perm, const int* __restrict__ rank,
+                                     const int* __restrict__ cls, int P, int Nc, int Mc,
+                                     const double* __restrict__ mu, double* __restrict__ lb) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P) return;
+  const int i = warp, c = cls[i];
+  const int ns = 2 * Nc, nn = 2 * Mc, r = rank[c];
+  const double* Wc = W + (long long)c * ns * nn;
+  const double* Rc = R + (long long)c * ns * ns;
+  const int* pc = perm + (long long)c * ns;
+  const double* m = mu + (long long)i * nn;
+  constexpr int RPL = 8;  // rows per lane: supports 2Nc <= 256
+  double t[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int row = lane + 32 * q;
+    double acc = 0.0;
+    if (row < r) {
+      const double* wr = Wc + (long long)row * nn;
+      for (int col = 0; col < nn; ++col) acc += wr[col] * m[col];
+    }
+    t[q] = acc;
+  }
+  // column-oriented back substitution; row j lives in lane j%32, slot j/32
+  for (int j = r - 1; j >= 0; --j) {
+    const int owner = j & 31, slot = j >> 5;
+    double tj = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) if (q == slot) tj = t[q];
+    tj = __shfl_sync(0xffffffffu, tj, owner);
+    const double* rj = Rc + (long long)j * ns;
+    const double xj = tj / rj[j];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int row = lane + 32 * q;
+      if (row < j) t[q] -= xj * rj[row];
+      if (row == j) t[q] = xj;
+    }
+  }
+  double* out = lb + (long long)i * ns;
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int row = lane + 32 * q;
+    if (row < ns) out[pc[row]] = (row < r) ? t[q] : 0.0;
+  }
+}
+
+// ---- Step 1b: lam~ = A [lam_bar_i; lam_bar_k] per close pair ----------------
+__global__ void pair_apply_kernel(const double* __restrict__ A, const int* __restrict__ pairs, int C,
+                                  int Nc, const double* __restrict__ lb, double* __restrict__ tilde) {
+  extern __shared__ double xs[];
+  const int c = blockIdx.x;
+  const int n4 = 4 * Nc, ns = 2 * Nc;
+  const int i = pairs[2 * c], k = pairs[2 * c + 1];
+  for (int t = threadIdx.x; t < n4; t += blockDim.x)
+    xs[t] = (t < ns) ? lb[(long long)i * ns + t] : lb[(long long)k * ns + (t - ns)];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* Ac = A + (long long)c * n4 * n4;
+  for (int row = wid; row < n4; row += nw) {
+    const double* ar = Ac + (long long)row * n4;
+    double acc = 0.0;
+    for (int col = lane; col < n4; col += 32) acc += ar[col] * xs[col];
+    acc = wsum(acc);
+    if (lane == 0) tilde[(long long)c * n4 + row] = acc;
+  }
+}
+
+// Rigid projection on disk i's coarse strengths: proj(s) = s - K (K^T K)^{-1}
+// K^T s with K rows [1, 0, -e_y], [0, 1, e_x], e = y_j - c (Sec. 4.1); for an
+// equispaced ring (K^T K)^{-1} = diag(1/Nc, 1/Nc, 1/(Nc rs^2)).  Warp-level:
+// lanes hold sources j = lane + 32 q.
+template <int SPL>
+__device__ __forceinline__ void warp_project(double (&sx)[SPL], double (&sy)[SPL], const double (&ex)[SPL],
+                                             const double (&ey)[SPL], int Nc, double rs, int lane) {
+  double t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+  for (int q = 0; q < SPL; ++q) {
+    if (lane + 32 * q < Nc) { t0 += sx[q]; t1 += sy[q]; t2 += -ey[q] * sx[q] + ex[q] * sy[q]; }
+  }
+  t0 = wsum(t0); t1 = wsum(t1); t2 = wsum(t2);
+  t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
+#pragma unroll
+  for (int q = 0; q < SPL; ++q) {
+    sx[q] -= t0 + t2 * (-ey[q]);
+    sy[q] -= t1 + t2 * ex[q];
+  }
+}
+
+// ---- eq. (total_corr) gather + projection (Sec. 4.4), one warp per disk ----
+// lam_i = lam_bar_i + sum over incident pairs of the pair's correction
+// (CSR order: deterministic); sig_i = proj(lam_i).
+__global__ void gather_kernel(const double* __restrict__ lb, const double* __restrict__ tilde,
+                              const int* __restrict__ csr_off, const int* __restrict__ csr_ent, int P,
+                              int Nc, const double* __restrict__ radii, double Rc, int mobility,
+                              double* __restrict__ lam, double* __restrict__ sig) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P) return;
+  const int i = warp, ns = 2 * Nc, n4 = 4 * Nc;
+  constexpr int SPL = 4;  // Nc <= 128
+  double sx[SPL], sy[SPL], ex[SPL], ey[SPL];
+  const double rs = radii[i] * Rc;
+#pragma unroll
+  for (int q = 0; q < SPL; ++q) {
+    const int j = lane + 32 * q;
+    sx[q] = sy[q] = ex[q] = ey[q] = 0.0;
+    if (j < Nc) {
+      sx[q] = lb[(long long)i * ns + 2 * j];
+      sy[q] = lb[(long long)i * ns + 2 * j + 1];
+      const double ph = 2.0 * LMFS_PI * j / Nc;
+      ex[q] = rs * cos(ph); ey[q] = rs * sin(ph);
+    }
+  }
+  for (int e = csr_off[i]; e < csr_off[i + 1]; ++e) {
+    const int ent = csr_ent[e], pc = ent >> 1, side = ent & 1;
+    const double* tc = tilde + (long long)pc * n4 + side * ns;
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      const int j = lane + 32 * q;
+      if (j < Nc) { sx[q] += tc[2 * j]; sy[q] += tc[2 * j + 1]; }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < SPL; ++q) {
+    const int j = lane + 32 * q;
+    if (j < Nc) { lam[(long long)i * ns + 2 * j] = sx[q]; lam[(long long)i * ns + 2 * j + 1] = sy[q]; }
+  }
+  if (mobility) warp_project<SPL>(sx, sy, ex, ey, Nc, rs, lane);
+#pragma unroll
+  for (int q = 0; q < SPL; ++q) {
+    const int j = lane + 32 * q;
+    if (j < Nc) { sig[(long long)i * ns + 2 * j] = sx[q]; sig[(long long)i * ns + 2 * j + 1] = sy[q]; }
+  }
+}
+
+// FP32 source records for the far-field kernel: per source (y_x, y_y, |y|^2,
+// y.s) and (s_x, s_y, 0, 0), y = source offset from the disk centre; per disk
+// the strength sum (FP64 sum rounded once).  One warp per disk.
+__global__ void records_kernel(const double* __restrict__ s, int P, int Nc, const double* __restrict__ radii,
+                               double Rc, float4* __restrict__ rec, float4* __restrict__ dsk) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P) return;
+  const int i = warp;
+  const double rs = radii[i] * Rc;
+  double tx = 0, ty = 0;
+  for (int j = lane; j < Nc; j += 32) {
+    const double ph = 2.0 * LMFS_PI * j / Nc;
+    const double yx = rs * cos(ph), yy = rs * sin(ph);
+    const double sx = s[(long long)i * 2 * Nc + 2 * j], sy = s[(long long)i * 2 * Nc + 2 * j + 1];
+    rec[2 * ((long long)i * Nc + j)] = make_float4((float)yx, (float)yy, (float)(yx * yx + yy * yy), (float)(yx * sx + yy * sy));
+    rec[2 * ((long long)i * Nc + j) + 1] = make_float4((float)sx, (float)sy, 0.f, 0.f);
+    tx += sx; ty += sy;
+  }
+  tx = wsum(tx); ty = wsum(ty);
+  if (lane == 0) { dsk[2 * i + 1].x = (float)tx; dsk[2 * i + 1].y = (float)ty; dsk[2 * i + 1].w = (float)(rs * rs); }
+}
+
+// Stand-alone sums: source records from explicit offsets; per disk the
+// double-float centre, strength sum and max |offset|^2.
+__global__ void records_general(const double* __restrict__ centres, const double* __restrict__ off,
+                                const double* __restrict__ s, int nd, int npd, float4* __restrict__ rec,
+                                float4* __restrict__ dsk) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nd) return;
+  const int i = warp;
+  double tx = 0, ty = 0, r2m = 0;
+  for (int j = lane; j < npd; j += 32) {
+    const long long o = (long long)i * npd + j;
+    const double yx = off[2 * o], yy = off[2 * o + 1], sx = s[2 * o], sy = s[2 * o + 1];
+    rec[2 * o] = make_float4((float)yx, (float)yy, (float)(yx * yx + yy * yy), (float)(yx * sx + yy * sy));
+    rec[2 * o + 1] = make_float4((float)sx, (float)sy, 0.f, 0.f);
+    tx += sx; ty += sy; r2m = fmax(r2m, yx * yx + yy * yy);
+  }
+  tx = wsum(tx); ty = wsum(ty);
+  for (int o = 16; o > 0; o >>= 1) r2m = fmax(r2m, __shfl_xor_sync(0xffffffffu, r2m, o));
+  if (lane == 0) {
+    const double cx = centres[2 * i], cy = centres[2 * i + 1];
+    const float hx = (float)cx, hy = (float)cy;
+    dsk[2 * i] = make_float4(hx, hy, (float)(cx - (double)hx), (float)(cy - (double)hy));
+    dsk[2 * i + 1] = make_float4((float)tx, (float)ty, 0.f, (float)r2m);
+  }
+}
+
+// Targets as disks of one node with a zero offset.
+__global__ void targets_as_disks(const double* __restrict__ t, int nt, float2* __restrict__ tgt,
+                                 float4* __restrict__ tdsk, int* __restrict__ excl_off) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= nt) excl_off[i] = 0;
+  if (i >= nt) return;
+  const double x = t[2 * i], y = t[2 * i + 1];
+  const float hx = (float)x, hy = (float)y;
+  tgt[i] = make_float2(0.f, 0.f);
+  tdsk[2 * i] = make_float4(hx, hy, (float)(x - (double)hx), (float)(y - (double)hy));
+  tdsk[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// ---- Step 2a far field, FP32 ------------------------------------------------
+// Per (target x, source disk k) with X = x - c_k (double-float centres) and
+// R^2 = |X|^2, the disk's sum is split exactly as
+//   sum_j S(X - y_j) s_j = S_0(X) sum_j s_j + sum_j [ -1/2 log(r_j^2/R^2) s_j
+//                        + (r^ r^T - X^ X^T) s_j ] / (4 pi mu)
+// (S_0 the Stokeslet at X).  Each bracketed term is O(|y|/R) |s_j| and is
+// computed without cancellation from q = |y|^2 - 2 X.y = r^2 - R^2:
+//   1/2 log(r^2/R^2) = atanh(q / (r^2 + R^2))      (odd series, FMA pipe)
+//   (r^ r^T - X^ X^T) s = -[X (b + q a / R^2) + y (a - b)] / r^2,
+// a = X.s, b = y.s; 1/r^2 and 1/(r^2 + R^2) share one MUFU reciprocal.
+// Per-disk partials are accumulated with Kahan compensation.
+constexpr int F_THREADS = 128;
+constexpr int F_TILE = 16;        // source disks per staged tile
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Bulk asynchronous copy global -> shared with mbarrier completion (TMA).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait on an mbarrier phase; returns false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+struct FarArgs {
+  const float2* tgt;     // [ntd * Mt] target offsets from their disk centre
+  const float4* tdsk;    // [ntd][2] target disk centres (hi, lo)
+  const float4* dsk;     // [nsd][2] source disk centres (hi, lo), (sum s_x, sum s_y, ., .)
+  const float4* rec;     // [nsd][Nc][2] source records
+  const int* excl_off; const int* excl;   // per target disk, sorted source disks to skip
+  int ntd, Mt, nsd, Nc;
+  int kchunk;            // source disks per split
+  double cmu;
+  double* out;           // [split][ntd*Mt][2]
+  long long out_stride;
+  int with_base;
+  int* err;
+  int* range_err;
+};
+
+template <int F_TPT>
+__global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int Nc = a.Nc;
+  const uint32_t rec_bytes = (uint32_t)(F_TILE * Nc * 32);
+  float4* rbuf[2] = {(float4*)fsm, (float4*)(fsm + rec_bytes)};
+  float4* dbuf[2] = {(float4*)(fsm + 2 * rec_bytes), (float4*)(fsm + 2 * rec_bytes + F_TILE * 32)};
+  uint64_t* bars = (uint64_t*)(fsm + 2 * rec_bytes + 2 * F_TILE * 32);
+  __shared__ int s_fail;
+
+  const int nt = a.ntd * a.Mt;
+  const int t0 = (blockIdx.x * F_THREADS + threadIdx.x) * F_TPT;
+  const bool active = t0 < nt;
+  const int ti = active ? t0 / a.Mt : 0;   // target disk (F_TPT divides Mt)
+  const int k_begin = blockIdx.y * a.kchunk;
+  const int k_end = min(a.nsd, k_begin + a.kchunk);
+
+  float2 xo[F_TPT];
+  float chx = 0, chy = 0, clx = 0, cly = 0;
+  if (active) {
+    for (int q = 0; q < F_TPT; ++q) xo[q] = a.tgt[t0 + q];
+    const float4 dh = a.tdsk[2 * ti];
+    chx = dh.x; chy = dh.y; clx = dh.z; cly = dh.w;
+  }
+  // exclusion pointer: first excluded disk >= k_begin
+  int ep = 0, ee = 0;
+  if (active) {
+    ep = a.excl_off[ti]; ee = a.excl_off[ti + 1];
+    while (ep < ee && a.excl[ep] < k_begin) ++ep;
+  }
+  int next_ex = (ep < ee) ? a.excl[ep] : 0x7fffffff;
+
+  float sx[F_TPT], sy[F_TPT], cx_[F_TPT], cy_[F_TPT];
+#pragma unroll
+  for (int q = 0; q < F_TPT; ++q) { sx[q] = sy[q] = cx_[q] = cy_[q] = 0.f; }
+
+  const int ntile = (k_end - k_begin + F_TILE - 1) / F_TILE;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int tile) {
+    const int kb = k_begin + tile * F_TILE;
+    const int nd = min(F_TILE, k_end - kb);
+    const int buf = tile & 1;
+    const uint32_t rb = (uint32_t)(nd * Nc * 32), db = (uint32_t)(nd * 32);
+    mbar_expect_tx(&bars[buf], rb + db);
+    bulk_g2s(rbuf[buf], a.rec + 2LL * kb * Nc, rb, &bars[buf]);
+    bulk_g2s(dbuf[buf], a.dsk + 2LL * kb, db, &bars[buf]);
+  };
+  if (threadIdx.x == 0 && ntile > 0) issue(0);
+
+  for (int tile = 0; tile < ntile; ++tile) {
+    const int buf = tile & 1;
+    if (threadIdx.x == 0 && tile + 1 < ntile) issue(tile + 1);
+    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) { s_fail = 1; }
+    __syncthreads();
+    if (s_fail) break;
+    const int kb = k_begin + tile * F_TILE;
+    const int nd = min(F_TILE, k_end - kb);
+    const float4* R = rbuf[buf];
+    const float4* Dk = dbuf[buf];
+    if (active) {
+      for (int dd = 0; dd < nd; ++dd) {
+        const int k = kb + dd;
+        if (k == next_ex) {
+          ++ep;
+          next_ex = (ep < ee) ? a.excl[ep] : 0x7fffffff;
+          continue;
+        }
+        const float4 dh = Dk[2 * dd];
+        const float4 ds = Dk[2 * dd + 1];   // (sum s_x, sum s_y, r, rho^2)
+        // X = x - c_k = (c_i - c_k) + x_off, centre difference in double-float
+        const float dxh = chx - dh.x, dyh = chy - dh.y;
+        const float dxl = clx - dh.z, dyl = cly - dh.w;
+        float Xx[F_TPT], Xy[F_TPT], R2[F_TPT], m2x[F_TPT], m2y[F_TPT], twoR2[F_TPT], iR2[F_TPT];
+        float px[F_TPT], py[F_TPT];
+#pragma unroll
+        for (int q = 0; q < F_TPT; ++q) {
+          Xx[q] = dxh + (dxl + xo[q].x);
+          Xy[q] = dyh + (dyl + xo[q].y);
+          R2[q] = fmaf(Xx[q], Xx[q], Xy[q] * Xy[q]);
+          twoR2[q] = R2[q] + R2[q];
+          iR2[q] = rcp_approx(R2[q]);
+          m2x[q] = -2.f * Xx[q];
+          m2y[q] = -2.f * Xy[q];
+          px[q] = 0.f; py[q] = 0.f;
+          // the 7-term atanh series needs |q|/(r^2 + R^2) <= 1/4: R >= 4 rho
+          if (R2[q] < 16.f * ds.w) a.range_err[0] = 1;
+        }
+#pragma unroll 4
+        for (int j = 0; j < Nc; ++j) {
+          const float4 y = R[2 * (dd * Nc + j)];       // (y_x, y_y, |y|^2, y.s)
+          const float4 s = R[2 * (dd * Nc + j) + 1];   // (s_x, s_y)
+#pragma unroll
+          for (int q = 0; q < F_TPT; ++q) {
+            const float qq = fmaf(m2x[q], y.x, fmaf(m2y[q], y.y, y.z));  // r^2 - R^2
+            const float r2 = R2[q] + qq;
+            const float t1 = twoR2[q] + qq;                               // r^2 + R^2
+            const float w = rcp_approx(r2 * t1);
+            const float ir2 = w * t1;
+            const float sl = qq * (w * r2);
+            const float x2 = sl * sl;
+            float p = fmaf(x2, 1.f / 13.f, 1.f / 11.f);
+            p = fmaf(p, x2, 1.f / 9.f);
+            p = fmaf(p, x2, 1.f / 7.f);
+            p = fmaf(p, x2, 1.f / 5.f);
+            p = fmaf(p, x2, 1.f / 3.f);
+            p = fmaf(p, x2, 1.f);
+            const float hl = sl * p;                                      // 1/2 log(r^2/R^2)
+            const float av = fmaf(Xx[q], s.x, Xy[q] * s.y);
+            const float amb = av - y.w;
+            const float bg = fmaf(qq * iR2[q], av, y.w);
+            const float tx = fmaf(Xx[q], bg, y.x * amb);
+            const float ty = fmaf(Xy[q], bg, y.y * amb);
+            px[q] = fmaf(-hl, s.x, px[q]);
+            py[q] = fmaf(-hl, s.y, py[q]);
+            px[q] = fmaf(-tx, ir2, px[q]);
+            py[q] = fmaf(-ty, ir2, py[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < F_TPT; ++q) {
+          float ux = px[q], uy = py[q];
+          if (a.with_base) {
+            // S_0(X) sum s: -1/2 log R^2 sum s + X (X . sum s) / R^2
+            const float lr = -0.5f * 0.6931471805599453f * __log2f(R2[q]);
+            const float xs = fmaf(Xx[q], ds.x, Xy[q] * ds.y) * iR2[q];
+            ux += fmaf(lr, ds.x, Xx[q] * xs);
+            uy += fmaf(lr, ds.y, Xy[q] * xs);
+          }
+          // Kahan accumulation of the disk partial
+          float yk = ux - cx_[q];
+          float tk = sx[q] + yk;
+          cx_[q] = (tk - sx[q]) - yk;
+          sx[q] = tk;
+          yk = uy - cy_[q];
+          tk = sy[q] + yk;
+          cy_[q] = (tk - sy[q]) - yk;
+          sy[q] = tk;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) { if (threadIdx.x == 0) atomicExch(a.err, 1); return; }
+  if (active) {
+    double* o = a.out + blockIdx.y * a.out_stride;
+#pragma unroll
+    for (int q = 0; q < F_TPT; ++q) {
+      o[2 * (t0 + q)] = ((double)sx[q] - (double)cx_[q]) * a.cmu;
+      o[2 * (t0 + q) + 1] = ((double)sy[q] - (double)cy_[q]) * a.cmu;
+    }
+  }
+}
+
+// ---- Step 2a far field by per-disk multipole expansions --------------------
+// The coarse strengths of a disk that carries pair corrections have Fourier
+// modes that grow like (1/R_c)^m (the peanut least squares of eq. (peanut)
+// fits the fine field with coarse sources), so a direct sum over them in FP32
+// carries an error of eps_32 |sigma| everywhere.  Outside the near zone the
+// field of disk k is instead evaluated from the exact expansion of its ring of
+// Stokeslets about c_k (complex notation, Z = x - c_k, w_j = y_j - c_k,
+// f = s_x + i s_y, u = u_x + i u_y):
+//   4 pi mu u = -F_0 log|Z| + F_0/2 + sum_{n>=1} A_n Z^-n / (2n)
+//             + sum_{n>=1} (B_n/(2n) - D_{n-1}/2) conj(Z)^-n
+//             + Z/2 sum_{n>=0} conj(A_n) conj(Z)^-(n+1)   [- D_p/2 conj(Z)^-(p+1)]
+// with A_n = sum f w^n, B_n = sum f conj(w)^n, D_n = sum conj(f) w conj(w)^n,
+// truncated at n = MP_P; the terms decay like (|w|/|Z|)^n and |w|/|Z| <=
+// R_c r/(r + g_near) outside the near zone.  The moments are formed in FP64;
+// the evaluation runs in FP32 (mixed) or FP64.
+constexpr int MP_P = 20;
+constexpr int MP_NCOEF = 64;   // F0, a[1..P], g[1..P+1], h[0..P] = 3P + 3 = 63, padded
+
+// P2M: one warp per disk.  Coefficient layout per disk (complex):
+// [0] F0, [1..P] a_n = A_n/(2n), [P+1..2P+1] g_n = B_n/(2n) - D_{n-1}/2
+// (g_{P+1} = -D_P/2), [2P+2..3P+2] h_n = conj(A_n).
+__global__ void p2m_kernel(const double* __restrict__ s, int P, int Nc, const double* __restrict__ radii,
+                           double Rc, double2* __restrict__ coef, float2* __restrict__ coef32) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P) return;
+  const int i = warp;
+  const double rs = radii[i] * Rc;
+  constexpr int SPL = 4;
+  double fr[SPL], fi[SPL], wr[SPL], wi[SPL], pr[SPL], pi_[SPL], qr[SPL], qi[SPL];
+#pragma unroll
+  for (int q = 0; q < SPL; ++q) {
+    const int j = lane + 32 * q;
+    fr[q] = fi[q] = wr[q] = wi[q] = 0.0;
+    if (j < Nc) {
+      fr[q] = s[(long long)i * 2 * Nc + 2 * j];
+      fi[q] = s[(long long)i * 2 * Nc + 2 * j + 1];
+      const double ph = 2.0 * LMFS_PI * j / Nc;
+      wr[q] = rs * cos(ph); wi[q] = rs * sin(ph);
+    }
+    pr[q] = 1.0; pi_[q] = 0.0;   // w^n
+    qr[q] = 1.0; qi[q] = 0.0;   // conj(w)^n
+  }
+  double2* out = coef + (long long)i * MP_NCOEF;
+  double Dprev_r = 0, Dprev_i = 0;
+  for (int n = 0; n <= MP_P; ++n) {
+    double Ar = 0, Ai = 0, Br = 0, Bi = 0, Dr = 0, Di = 0;
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      // A: f w^n ; B: f conj(w)^n ; D: conj(f) w conj(w)^n
+      Ar += fr[q] * pr[q] - fi[q] * pi_[q];
+      Ai += fr[q] * pi_[q] + fi[q] * pr[q];
+      Br += fr[q] * qr[q] - fi[q] * qi[q];
+      Bi += fr[q] * qi[q] + fi[q] * qr[q];
+      const double tr = wr[q] * qr[q] - wi[q] * qi[q], ti = wr[q] * qi[q] + wi[q] * qr[q];  // w conj(w)^n
+      Dr += fr[q] * tr + fi[q] * ti;
+      Di += fr[q] * ti - fi[q] * tr;
+    }
+    Ar = wsum(Ar); Ai = wsum(Ai); Br = wsum(Br); Bi = wsum(Bi); Dr = wsum(Dr); Di = wsum(Di);
+    if (lane == 0) {
+      if (n == 0) out[0] = make_double2(Ar, Ai);
+      else {
+        out[n] = make_double2(Ar / (2.0 * n), Ai / (2.0 * n));
+        out[MP_P + n] = make_double2(Br / (2.0 * n) - 0.5 * Dprev_r, Bi / (2.0 * n) - 0.5 * Dprev_i);
+      }
+      out[2 * MP_P + 2 + n] = make_double2(Ar, -Ai);
+      if (n == MP_P) out[2 * MP_P + 1] = make_double2(-0.5 * Dr, -0.5 * Di);
+    }
+    Dprev_r = Dr; Dprev_i = Di;
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      const double npr = pr[q] * wr[q] - pi_[q] * wi[q], npi = pr[q] * wi[q] + pi_[q] * wr[q];
+      const double nqr = qr[q] * wr[q] + qi[q] * wi[q], nqi = qi[q] * wr[q] - qr[q] * wi[q];
+      pr[q] = npr; pi_[q] = npi; qr[q] = nqr; qi[q] = nqi;
+    }
+  }
+  if (coef32) {
+    __syncwarp();
+    for (int c = lane; c < MP_NCOEF; c += 32) {
+      const double2 v = (c < 3 * MP_P + 3) ? out[c] : make_double2(0.0, 0.0);
+      coef32[(long long)i * MP_NCOEF + c] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+}
+
+template <typename T> struct Cx { T r, i; };
+template <typename T> __device__ __forceinline__ Cx<T> cfma(Cx<T> a, Cx<T> t, Cx<T> b) {
+  // a * t + b
+  Cx<T> o;
+  o.r = fma(a.r, t.r, fma(-a.i, t.i, b.r));
+  o.i = fma(a.r, t.i, fma(a.i, t.r, b.i));
+  return o;
+}
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+constexpr int M_THREADS = 128;
+constexpr int M_TILE = 16;     // source disks per staged tile
+
+struct MpArgs {
+  const float2* tgt; const float4* dsk;      // FP32 path: node offsets, double-float centres
+  const double* centres; const double* radii; int Mc_nodes;
+  const void* coef;                          // [P][MP_NCOEF] float2 or double2
+  const int* excl_off; const int* excl;
+  int P, Mc, kchunk;
+  double cmu;
+  double* out; long long out_stride;
+  int with_log;
+  int* err;
+};
+
+// M2P: one thread per target (FP64) or two targets per thread (FP32), source
+// disks staged tile by tile into shared memory with bulk asynchronous copies
+// (TMA) completing on an mbarrier, double-buffered.
+template <typename T, int TPT>
+__global__ void __launch_bounds__(M_THREADS) m2p_kernel(MpArgs a) {
+  using V2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char msm[];
+  const uint32_t cbytes = (uint32_t)(M_TILE * MP_NCOEF * sizeof(V2));
+  V2* cbuf0 = (V2*)msm;
+  V2* cbuf1 = (V2*)(msm + cbytes);
+  float4* dbuf0 = (float4*)(msm + 2 * cbytes);
+  float4* dbuf1 = (float4*)(msm + 2 * cbytes + M_TILE * 32);
+  uint64_t* bars = (uint64_t*)(msm + 2 * cbytes + 2 * M_TILE * 32);
+  __shared__ int s_fail;
+
+  const int nt = a.P * a.Mc;
+  const int t0 = (blockIdx.x * M_THREADS + threadIdx.x) * TPT;
+  const bool active = t0 < nt;
+  const int ti = active ? t0 / a.Mc : 0;
+  const int k_begin = blockIdx.y * a.kchunk;
+  const int k_end = min(a.P, k_begin + a.kchunk);
+  // target positions: FP32 double-float centre + offset, or FP64 absolute
+  T xr[TPT], xi[TPT];
+  float chx = 0, chy = 0, clx = 0, cly = 0;
+  if (active) {
+    if (sizeof(T) == 4) {
+      const float4 dh = a.dsk[2 * ti];
+      chx = dh.x; chy = dh.y; clx = dh.z; cly = dh.w;
+      for (int q = 0; q < TPT; ++q) { xr[q] = (T)a.tgt[t0 + q].x; xi[q] = (T)a.tgt[t0 + q].y; }
+    } else {
+      for (int q = 0; q < TPT; ++q) {
+        const int m = (t0 + q) % a.Mc;
+        const double th = 2.0 * LMFS_PI * m / a.Mc;
+        xr[q] = (T)(a.centres[2 * ti] + a.radii[ti] * cos(th));
+        xi[q] = (T)(a.centres[2 * ti + 1] + a.radii[ti] * sin(th));
+      }
+    }
+  }
+  int ep = 0, ee = 0;
+  if (active) {
+    ep = a.excl_off[ti]; ee = a.excl_off[ti + 1];
+    while (ep < ee && a.excl[ep] < k_begin) ++ep;
+  }
+  int next_ex = (ep < ee) ? a.excl[ep] : 0x7fffffff;
+  T sr[TPT], si[TPT], cr[TPT], ci[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) { sr[q] = si[q] = cr[q] = ci[q] = (T)0; }
+
+  const int ntile = (k_end - k_begin + M_TILE - 1) / M_TILE;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int tile) {
+    const int kb = k_begin + tile * M_TILE;
+    const int nd = min(M_TILE, k_end - kb);
+    const int buf = tile & 1;
+    const uint32_t cb = (uint32_t)(nd * MP_NCOEF * sizeof(V2)), db = (uint32_t)(nd * 32);
+    const bool fp32 = sizeof(T) == 4;
+    mbar_expect_tx(&bars[buf], cb + (fp32 ? db : 0));
+    bulk_g2s(buf ? (void*)cbuf1 : (void*)cbuf0, (const V2*)a.coef + (long long)kb * MP_NCOEF, cb, &bars[buf]);
+    if (fp32) bulk_g2s(buf ? (void*)dbuf1 : (void*)dbuf0, a.dsk + 2LL * kb, db, &bars[buf]);
+  };
+  if (threadIdx.x == 0 && ntile > 0) issue(0);
+  for (int tile = 0; tile < ntile; ++tile) {
+    const int buf = tile & 1;
+    if (threadIdx.x == 0 && tile + 1 < ntile) issue(tile + 1);
+    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    const int kb = k_begin + tile * M_TILE;
+    const int nd = min(M_TILE, k_end - kb);
+    const V2* CB = buf ? cbuf1 : cbuf0;
+    const float4* DB = buf ? dbuf1 : dbuf0;
+    if (active) {
+      for (int dd = 0; dd < nd; ++dd) {
+        const int k = kb + dd;
+        if (k == next_ex) { ++ep; next_ex = (ep < ee) ? a.excl[ep] : 0x7fffffff; continue; }
+        const V2* cf = CB + dd * MP_NCOEF;
+        Cx<T> Z[TPT], t[TPT], tb[TPT];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+          if (sizeof(T) == 4) {
+            const float4 dh = DB[2 * dd];
+            Z[q].r = (T)((chx - dh.x) + ((clx - dh.z) + (float)xr[q]));
+            Z[q].i = (T)((chy - dh.y) + ((cly - dh.w) + (float)xi[q]));
+          } else {
+            Z[q].r = xr[q] - (T)a.centres[2 * k];
+            Z[q].i = xi[q] - (T)a.centres[2 * k + 1];
+          }
+          const T r2 = Z[q].r * Z[q].r + Z[q].i * Z[q].i;
+          const T ir2 = (T)1 / r2;
+          t[q].r = Z[q].r * ir2; t[q].i = -Z[q].i * ir2;     // 1/Z
+          tb[q].r = t[q].r; tb[q].i = -t[q].i;              // 1/conj(Z)
+        }
+        Cx<T> s1[TPT], s2[TPT], s3[TPT];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+          s1[q].r = s1[q].i = s2[q].r = s2[q].i = s3[q].r = s3[q].i = (T)0;
+        }
+        // Horner: s1 = sum_{n=1}^P a_n t^n ; s2 = sum_{n=1}^{P+1} g_n tb^n ;
+        //         s3 = sum_{n=0}^{P} h_n tb^(n+1)
+        {
+          const V2 gl = cf[2 * MP_P + 1];
+#pragma unroll
+          for (int q = 0; q < TPT; ++q) { s2[q].r = (T)gl.x; s2[q].i = (T)gl.y; }
+        }
+        for (int n = MP_P; n >= 1; --n) {
+          const V2 an = cf[n], gn = cf[MP_P + n], hn = cf[2 * MP_P + 2 + n];
+#pragma unroll
+          for (int q = 0; q < TPT; ++q) {
+            Cx<T> A_ = {(T)an.x, (T)an.y}, G_ = {(T)gn.x, (T)gn.y}, H_ = {(T)hn.x, (T)hn.y};
+            // s1 <- (s1 + a_n) t ;  s2 <- s2 tb + g_n ;  s3 <- (s3 + h_n) tb
+            Cx<T> u1 = {s1[q].r + A_.r, s1[q].i + A_.i};
+            s1[q].r = u1.r * t[q].r - u1.i * t[q].i; s1[q].i = u1.r * t[q].i + u1.i * t[q].r;
+            s2[q] = cfma(s2[q], tb[q], G_);
+            Cx<T> u3 = {s3[q].r + H_.r, s3[q].i + H_.i};
+            s3[q].r = u3.r * tb[q].r - u3.i * tb[q].i; s3[q].i = u3.r * tb[q].i + u3.i * tb[q].r;
+          }
+        }
+        const V2 h0 = cf[2 * MP_P + 2];
+        const V2 f0 = cf[0];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+          // s2 still lacks the final factor tb (g_n multiplies tb^n, n >= 1)
+          Cx<T> s2f = {s2[q].r * tb[q].r - s2[q].i * tb[q].i, s2[q].r * tb[q].i + s2[q].i * tb[q].r};
+          Cx<T> u3 = {s3[q].r + (T)h0.x, s3[q].i + (T)h0.y};
+          Cx<T> s3f = {u3.r * tb[q].r - u3.i * tb[q].i, u3.r * tb[q].i + u3.i * tb[q].r};
+          T ur = s1[q].r + s2f.r + (T)0.5 * (Z[q].r * s3f.r - Z[q].i * s3f.i);
+          T ui = s1[q].i + s2f.i + (T)0.5 * (Z[q].r * s3f.i + Z[q].i * s3f.r);
+          if (a.with_log) {
+            const T lr = (T)0.5 * log(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
+            ur += (T)f0.x * ((T)0.5 - lr);
+            ui += (T)f0.y * ((T)0.5 - lr);
+          }
+          // Kahan accumulation over source disks
+          T yk = ur - cr[q]; T tk = sr[q] + yk; cr[q] = (tk - sr[q]) - yk; sr[q] = tk;
+          yk = ui - ci[q]; tk = si[q] + yk; ci[q] = (tk - si[q]) - yk; si[q] = tk;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) { if (threadIdx.x == 0) atomicExch(a.err, 1); return; }
+  if (active) {
+    double* o = a.out + blockIdx.y * a.out_stride;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      o[2 * (t0 + q)] = ((double)sr[q] - (double)cr[q]) * a.cmu;
+      o[2 * (t0 + q) + 1] = ((double)si[q] - (double)ci[q]) * a.cmu;
+    }
+  }
+}
+
+// Sum the source-range splits in a fixed order.
+__global__ void reduce_splits(const double* part, long long stride, int nsplit, long long n, double* out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += part[s * stride + t];
+    out[t] = acc;
+  }
+}
+
+// ---- near field (FP64) + assembly ------------------------------------------
+// One block per target disk i.  mode 0 (matvec): u_i = mu_i + ufar_i +
+//   sum over near entries (regular: sig_k; close partner: proj_k(lam_k -
+//   lam_bar_k - lam~ of the pair with i)); self entries skipped.
+// mode 1 (completion flow, eq. (u0_def)): b_i = -(ufar_i + sum over all near
+//   entries, self included, of S^(ik) s_k).
+__global__ void near_kernel(int mode, const double* __restrict__ centres, const double* __restrict__ radii,
+                            double Rc, int P, int Mc, int Nc, const int* __restrict__ near_off,
+                            const int4* __restrict__ near_ent, const double* __restrict__ sig,
+                            const double* __restrict__ lam, const double* __restrict__ lb,
+                            const double* __restrict__ tilde, int mobility, const double* __restrict__ mu,
+                            const double* __restrict__ ufar, double cmu, double* __restrict__ u) {
+  extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y
+  __shared__ double red[3][32];
+  const int i = blockIdx.x;
+  const int ns = 2 * Nc, n4 = 4 * Nc;
+  const int m = threadIdx.x;
+  double xx = 0, xy = 0;
+  if (m < Mc) {
+    const double th = 2.0 * LMFS_PI * m / Mc;
+    xx = centres[2 * i] + radii[i] * cos(th);
+    xy = centres[2 * i + 1] + radii[i] * sin(th);
+  }
+  double ux = 0, uy = 0;
+  for (int e = near_off[i]; e < near_off[i + 1]; ++e) {
+    const int4 en = near_ent[e];
+    const int k = en.x, kind = en.y;
+    if (mode == 0 && kind == 2) continue;
+    const double rs = radii[k] * Rc;
+    __syncthreads();
+    double t0 = 0, t1 = 0, t2 = 0;
+    for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
+      const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+      double sx, sy;
+      if (mode == 0 && kind == 1) {
+        const double* tc = tilde + (long long)en.z * n4 + en.w * ns;
+        sx = lam[(long long)k * ns + 2 * j] - lb[(long long)k * ns + 2 * j] - tc[2 * j];
+        sy = lam[(long long)k * ns + 2 * j + 1] - lb[(long long)k * ns + 2 * j + 1] - tc[2 * j + 1];
+        t0 += sx; t1 += sy; t2 += -ey * sx + ex * sy;
+      } else {
+        sx = sig[(long long)k * ns + 2 * j];
+        sy = sig[(long long)k * ns + 2 * j + 1];
+      }
+      nsm[4 * j] = centres[2 * k] + ex;
+      nsm[4 * j + 1] = centres[2 * k + 1] + ey;
+      nsm[4 * j + 2] = sx;
+      nsm[4 * j + 3] = sy;
+    }
+    if (mode == 0 && kind == 1 && mobility) {
+      // block-wide K^T rho, then rho -= K (K^T K)^{-1} K^T rho
+      t0 = wsum(t0); t1 = wsum(t1); t2 = wsum(t2);
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      if (lane == 0) { red[0][wid] = t0; red[1][wid] = t1; red[2][wid] = t2; }
+      __syncthreads();
+      t0 = t1 = t2 = 0;
+      for (int w = 0; w < nw; ++w) { t0 += red[0][w]; t1 += red[1][w]; t2 += red[2][w]; }
+      t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
+      for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
+        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        nsm[4 * j + 2] -= t0 + t2 * (-ey);
+        nsm[4 * j + 3] -= t1 + t2 * ex;
+      }
+    }
+    __syncthreads();
+    if (m < Mc) {
+      for (int j = 0; j < Nc; ++j) {
+        const double dx = xx - nsm[4 * j], dy = xy - nsm[4 * j + 1];
+        const double r2 = dx * dx + dy * dy;
+        const double lg = 0.5 * log(r2);
+        const double dt = (dx * nsm[4 * j + 2] + dy * nsm[4 * j + 3]) / r2;
+        ux += -lg * nsm[4 * j + 2] + dt * dx;
+        uy += -lg * nsm[4 * j + 3] + dt * dy;
+      }
+    }
+  }
+  if (m < Mc) {
+    const long long o = (long long)i * 2 * Mc + 2 * m;
+    const double fx = ufar[o] + ux * cmu, fy = ufar[o + 1] + uy * cmu;
+    if (mode == 0) { u[o] = mu[o] + fx; u[o + 1] = mu[o + 1] + fy; }
+    else { u[o] = -fx; u[o + 1] = -fy; }
+  }
+}
+
+// ---- right-hand sides -------------------------------------------------------
+// Resistance: g = v + omega (x - c)^perp at the coarse nodes (eq. (rigidbc)).
+__global__ void rhs_res_kernel(const double* in3, const double* radii, int P, int Mc, double* b) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P * Mc) return;
+  const int i = t / Mc, m = t % Mc;
+  const double th = 2.0 * LMFS_PI * m / Mc;
+  const double ex = radii[i] * cos(th), ey = radii[i] * sin(th);
+  b[2 * t] = in3[3 * i] - in3[3 * i + 2] * ey;
+  b[2 * t + 1] = in3[3 * i + 1] + in3[3 * i + 2] * ex;
+}
+
+// Completion-flow strengths lam_0 = K (K^T K)^{-1} [f; t] (Sec. 4.1).
+__global__ void lam0_kernel(const double* in3, const double* radii, double Rc, int P, int Nc, double* lam0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P * Nc) return;
+  const int i = t / Nc, j = t % Nc;
+  const double rs = radii[i] * Rc, ph = 2.0 * LMFS_PI * j / Nc;
+  const double ex = rs * cos(ph), ey = rs * sin(ph);
+  const double a0 = in3[3 * i] / Nc, a1 = in3[3 * i + 1] / Nc, a2 = in3[3 * i + 2] / (Nc * rs * rs);
+  lam0[2 * t] = a0 + a2 * (-ey);
+  lam0[2 * t + 1] = a1 + a2 * ex;
+}
+
+// ---- post-processing (eq. (two_force), eq. (rbm2)) ---------------------------
+__global__ void pair_E_kernel(const double* __restrict__ E, const int* __restrict__ pairs, int C, int Nc,
+                              const double* __restrict__ lb, double* __restrict__ e6) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= C) return;
+  const int c = warp, n4 = 4 * Nc, ns = 2 * Nc;
+  const int i = pairs[2 * c], k = pairs[2 * c + 1];
+  for (int r = 0; r < 6; ++r) {
+    const double* er = E + ((long long)c * 6 + r) * n4;
+    double acc = 0.0;
+    for (int col = lane; col < n4; col += 32)
+      acc += er[col] * (col < ns ? lb[(long long)i * ns + col] : lb[(long long)k * ns + col - ns]);
+    acc = wsum(acc);
+    if (lane == 0) e6[(long long)c * 6 + r] = acc;
+  }
+}
+
+// out_i = sgn K^T lam_bar_i + sum over incident pairs of their E share;
+// segmented warp-shuffle reduction per disk.
+__global__ void post_kernel(const double* __restrict__ lb, const double* __restrict__ e6,
+                            const int* __restrict__ csr_off, const int* __restrict__ csr_ent, int P, int Nc,
+                            const double* __restrict__ radii, double Rc, double sgn, double* __restrict__ out3) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P) return;
+  const int i = warp;
+  const double rs = radii[i] * Rc;
+  double t0 = 0, t1 = 0, t2 = 0;
+  for (int j = lane; j < Nc; j += 32) {
+    const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+    const double sx = lb[(long long)i * 2 * Nc + 2 * j], sy = lb[(long long)i * 2 * Nc + 2 * j + 1];
+    t0 += sx; t1 += sy; t2 += -ey * sx + ex * sy;
+  }
+  t0 = wsum(t0); t1 = wsum(t1); t2 = wsum(t2);
+  if (lane == 0) {
+    double o0 = sgn * t0, o1 = sgn * t1, o2 = sgn * t2;
+    for (int e = csr_off[i]; e < csr_off[i + 1]; ++e) {
+      const int ent = csr_ent[e], pc = ent >> 1, side = ent & 1;
+      o0 += e6[(long long)pc * 6 + 3 * side];
+      o1 += e6[(long long)pc * 6 + 3 * side + 1];
+      o2 += e6[(long long)pc * 6 + 3 * side + 2];
+    }
+    out3[3 * i] = o0; out3[3 * i + 1] = o1; out3[3 * i + 2] = o2;
+  }
+}
+
+}  // namespace
+
+// Kernel attributes and the error flag are set up once per handle, outside
+// any stream capture.
+int far_field_prepare(Ctx& c) {
+  const size_t shm = 2 * (size_t)F_TILE * c.d.Nc * 32 + 2 * F_TILE * 32 + 16;
+  LMFS_CUDA(cudaFuncSetAttribute(far32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  LMFS_CUDA(cudaFuncSetAttribute(far32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  LMFS_TRY(dalloc(&c.coef64, (size_t)c.d.P * MP_NCOEF));
+  LMFS_TRY(dalloc(&c.coef32, (size_t)c.d.P * MP_NCOEF));
+  LMFS_TRY(dalloc(&c.far_err, 2));
+  LMFS_CUDA(cudaMemsetAsync(c.far_err, 0, 2 * sizeof(int), c.stream));
+  return LMFS_OK;
+}
+
+int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
+  if (2 * c.d.Nc > 256) { set_last_error("2 Nc > 256 not supported"); return LMFS_ERR_INVALID; }
+  const int thr = 128, blocks = (c.d.P * 32 + thr - 1) / thr;
+  onebody_apply_kernel<<<blocks, thr, 0, c.stream>>>(ob.W, ob.R, ob.perm, ob.rank, c.cls, c.d.P, c.d.Nc, c.d.Mc, mu, lb);
+  return check_launch("onebody_apply");
+}
+
+int far_field(Ctx& c, const double* strength, double* out, int precision, bool skip_base) {
+  const int P = c.d.P, Mc = c.d.Mc, Nc = c.d.Nc;
+  const long long n = (long long)P * Mc * 2;
+  const double cmu = INV4PI / c.prm.mu;
+  int split = c.far_split;
+  const int kchunk_raw = (P + split - 1) / split;
+  if (precision == LMFS_MIXED_DIRECT) {
+    const int kchunk = ((kchunk_raw + F_TILE - 1) / F_TILE) * F_TILE;
+    split = (P + kchunk - 1) / kchunk;
+    records_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.src4, c.dsk32);
+    LMFS_TRY(check_launch("records"));
+    FarArgs a;
+    a.tgt = c.tgt32; a.tdsk = c.dsk32; a.dsk = c.dsk32; a.rec = c.src4; a.excl_off = c.far_excl_off;
+    a.excl = c.far_excl; a.ntd = P; a.Mt = Mc; a.nsd = P; a.Nc = Nc; a.kchunk = kchunk; a.cmu = cmu;
+    a.out = split > 1 ? c.ufar_part : out; a.out_stride = n; a.with_base = skip_base ? 0 : 1; a.err = c.far_err;
+    a.range_err = c.far_err + 1;
+    const int threads_needed = (P * Mc + 1) / 2;
+    dim3 grid((threads_needed + F_THREADS - 1) / F_THREADS, split);
+    const size_t shm = 2 * (size_t)F_TILE * Nc * 32 + 2 * F_TILE * 32 + 16;
+    far32_kernel<2><<<grid, F_THREADS, shm, c.stream>>>(a);
+    LMFS_TRY(check_launch("far32"));
+  } else {
+    const int kchunk = ((kchunk_raw + M_TILE - 1) / M_TILE) * M_TILE;
+    split = (P + kchunk - 1) / kchunk;
+    const bool fp32 = precision == LMFS_MIXED;
+    p2m_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.coef64,
+                                                          fp32 ? c.coef32 : nullptr);
+    LMFS_TRY(check_launch("p2m"));
+    MpArgs a;
+    a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc;
+    a.coef = fp32 ? (const void*)c.coef32 : (const void*)c.coef64;
+    a.excl_off = c.far_excl_off; a.excl = c.far_excl; a.P = P; a.Mc = Mc; a.kchunk = kchunk; a.cmu = cmu;
+    a.out = split > 1 ? c.ufar_part : out; a.out_stride = n; a.with_log = skip_base ? 0 : 1; a.err = c.far_err;
+    if (fp32) {
+      const size_t shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(float2) + 2 * M_TILE * 32 + 16;
+      dim3 grid(((P * Mc + 1) / 2 + M_THREADS - 1) / M_THREADS, split);
+      m2p_kernel<float, 2><<<grid, M_THREADS, shm, c.stream>>>(a);
+    } else {
+      const size_t shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(double2) + 2 * M_TILE * 32 + 16;
+      dim3 grid((P * Mc + M_THREADS - 1) / M_THREADS, split);
+      m2p_kernel<double, 1><<<grid, M_THREADS, shm, c.stream>>>(a);
+    }
+    LMFS_TRY(check_launch("m2p"));
+  }
+  if (split > 1) {
+    reduce_splits<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, c.stream>>>(c.ufar_part, n, split, n, out);
+    LMFS_TRY(check_launch("reduce_splits"));
+  }
+  return LMFS_OK;
+}
+
+int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar, double* u,
+               int problem) {
+  const int threads = std::max(32, ((c.d.Mc + 31) / 32) * 32);
+  const size_t shm = (size_t)c.d.Nc * 4 * sizeof(double);
+  near_kernel<<<c.d.P, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, c.d.P, c.d.Mc, c.d.Nc, c.near_off,
+                                                 c.near_ent, strength, c.lam, c.lb, c.tilde,
+                                                 problem == LMFS_MOBILITY, mu, ufar, INV4PI / c.prm.mu, u);
+  return check_launch("near");
+}
+
+int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision) {
+  PairBlocks& pb = c.prob[problem];
+  if (!pb.ready) { set_last_error("pair blocks not computed for this problem"); return LMFS_ERR_STATE; }
+  const int P = c.d.P, Nc = c.d.Nc;
+  LMFS_TRY(onebody_apply(c, pb.ob, mu, c.lb));                                   // Step 1a
+  if (c.C > 0) {                                                                 // Step 1b
+    pair_apply_kernel<<<c.C, 256, 4 * Nc * sizeof(double), c.stream>>>(pb.A, c.pairs, c.C, Nc, c.lb, c.tilde);
+    LMFS_TRY(check_launch("pair_apply"));
+  }
+  gather_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(c.lb, c.tilde, c.csr_off, c.csr_ent, P, Nc, c.radii,
+                                                           c.Rc, problem == LMFS_MOBILITY, c.lam, c.sig);
+  LMFS_TRY(check_launch("gather"));
+  LMFS_TRY(far_field(c, c.sig, c.ufar, precision, problem == LMFS_MOBILITY));   // Step 2a (far)
+  return near_field(c, 0, c.sig, mu, c.ufar, u, problem);                       // near + identity
+}
+
+int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision) {
+  const int P = c.d.P;
+  if (problem == LMFS_RESISTANCE) {
+    rhs_res_kernel<<<(P * c.d.Mc + 127) / 128, 128, 0, c.stream>>>(in3, c.radii, P, c.d.Mc, b);
+    return check_launch("rhs_res");
+  }
+  lam0_kernel<<<(P * c.d.Nc + 127) / 128, 128, 0, c.stream>>>(in3, c.radii, c.Rc, P, c.d.Nc, c.lam0);
+  LMFS_TRY(check_launch("lam0"));
+  LMFS_TRY(far_field(c, c.lam0, c.ufar, precision, false));
+  return near_field(c, 1, c.lam0, nullptr, c.ufar, b, problem);
+}
+
+int post_device(Ctx& c, int problem, const double* mu, double* out3) {
+  PairBlocks& pb = c.prob[problem];
+  const int P = c.d.P, Nc = c.d.Nc;
+  LMFS_TRY(onebody_apply(c, pb.ob, mu, c.lb));
+  double* e6 = c.tilde;   // reuse: C*6 <= C*4Nc
+  if (c.C > 0) {
+    pair_E_kernel<<<(c.C * 32 + 127) / 128, 128, 0, c.stream>>>(pb.E, c.pairs, c.C, Nc, c.lb, e6);
+    LMFS_TRY(check_launch("pair_E"));
+  }
+  post_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(c.lb, e6, c.csr_off, c.csr_ent, P, Nc, c.radii, c.Rc,
+                                                         problem == LMFS_RESISTANCE ? 1.0 : -1.0, out3);
+  return check_launch("post");
+}
+
+// Stand-alone far field from disks of sources to arbitrary targets (no
+// exclusions): each target is a disk of one node.  Scratch is taken from the
+// stream-ordered allocator and returned before the call ends.
+int stokeslet_sum_standalone(const double* targets, int nt, const double* centres, const double* offsets,
+                             const double* strengths, int nd, int npd, double mu, int precision,
+                             cudaStream_t st, double* out) {
+  if (nt < 1 || nd < 1 || npd < 1 || !(mu > 0) || !targets || !centres || !offsets || !strengths || !out) {
+    set_last_error("lmfs_stokeslet_sum: bad sizes or null pointers");
+    return LMFS_ERR_INVALID;
+  }
+  if (precision != LMFS_MIXED_DIRECT && precision != LMFS_MIXED) {
+    set_last_error("lmfs_stokeslet_sum: precision must be LMFS_MIXED_DIRECT (FP32 direct tiles)");
+    return LMFS_ERR_INVALID;
+  }
+  int dev_sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long bx = ((long long)nt + F_THREADS - 1) / F_THREADS;
+  long long split = std::max<long long>(1, (8LL * dev_sms + bx - 1) / bx);
+  int kchunk = (int)((nd + split - 1) / split);
+  kchunk = ((kchunk + F_TILE - 1) / F_TILE) * F_TILE;
+  split = (nd + kchunk - 1) / kchunk;
+  float2* tgt = nullptr; float4* tdsk = nullptr; float4* dsk = nullptr; float4* rec = nullptr;
+  int* excl_off = nullptr; int* err = nullptr; double* part = nullptr;
+  auto A = [&](void** p, size_t b) { return cudaMallocAsync(p, b, st); };
+  int rc = LMFS_OK;
+  if (cuda_failed(A((void**)&tgt, nt * sizeof(float2)), "alloc") || cuda_failed(A((void**)&tdsk, 2LL * nt * sizeof(float4)), "alloc") ||
+      cuda_failed(A((void**)&dsk, 2LL * nd * sizeof(float4)), "alloc") ||
+      cuda_failed(A((void**)&rec, 2LL * nd * npd * sizeof(float4)), "alloc") ||
+      cuda_failed(A((void**)&excl_off, (nt + 1) * sizeof(int)), "alloc") || cuda_failed(A((void**)&err, 2 * sizeof(int)), "alloc") ||
+      (split > 1 && cuda_failed(A((void**)&part, split * 2LL * nt * sizeof(double)), "alloc"))) {
+    rc = LMFS_ERR_NOMEM;
+  }
+  int herr[2] = {0, 0};
+  if (rc == LMFS_OK) {
+    cudaMemsetAsync(err, 0, 2 * sizeof(int), st);
+    targets_as_disks<<<(nt + 1 + 255) / 256, 256, 0, st>>>(targets, nt, tgt, tdsk, excl_off);
+    records_general<<<(nd * 32 + 127) / 128, 128, 0, st>>>(centres, offsets, strengths, nd, npd, rec, dsk);
+    FarArgs a;
+    a.tgt = tgt; a.tdsk = tdsk; a.dsk = dsk; a.rec = rec; a.excl_off = excl_off; a.excl = excl_off;
+    a.ntd = nt; a.Mt = 1; a.nsd = nd; a.Nc = npd; a.kchunk = kchunk; a.cmu = INV4PI / mu;
+    a.out = split > 1 ? part : out; a.out_stride = 2LL * nt; a.with_base = 1; a.err = err; a.range_err = err + 1;
+    const size_t shm = 2 * (size_t)F_TILE * npd * 32 + 2 * F_TILE * 32 + 16;
+    if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); rc = LMFS_ERR_INVALID; }
+    else if (cuda_failed(cudaFuncSetAttribute(far32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr")) rc = LMFS_ERR_CUDA;
+    else {
+      dim3 grid((unsigned)bx, (unsigned)split);
+      far32_kernel<1><<<grid, F_THREADS, shm, st>>>(a);
+      rc = check_launch("far32 standalone");
+      if (rc == LMFS_OK && split > 1) {
+        reduce_splits<<<(int)std::min<long long>((2LL * nt + 255) / 256, 4096), 256, 0, st>>>(part, 2LL * nt, (int)split, 2LL * nt, out);
+        rc = check_launch("reduce");
+      }
+      if (rc == LMFS_OK && (cuda_failed(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st), "d2h") ||
+                            cuda_failed(cudaStreamSynchronize(st), "sync")))
+        rc = LMFS_ERR_CUDA;
+    }
+  }
+  cudaFreeAsync(tgt, st); cudaFreeAsync(tdsk, st); cudaFreeAsync(dsk, st); cudaFreeAsync(rec, st);
+  cudaFreeAsync(excl_off, st); cudaFreeAsync(err, st); if (part) cudaFreeAsync(part, st);
+  if (rc == LMFS_OK && herr[0]) { set_last_error("far32: bounded wait expired"); rc = LMFS_ERR_CUDA; }
+  if (rc == LMFS_OK && herr[1]) {
+    set_last_error("lmfs_stokeslet_sum: a target lies within 4 x the source ring radius of a source disk centre");
+    rc = LMFS_ERR_INVALID;
+  }
+  return rc;
+}
+
+}  // namespace lmfs

@@ -1,0 +1,701 @@
+// Device precompute: one-body factors (Sec. 3.1, eq. (howG+); Sec. 4.1,
+// eq. (SL)) and the pair blocks A and E of every close pair (Algorithm 2,
+// precomputation loop; Sec. 3.2-3.4 resistance, Sec. 4.3-4.4 mobility), all in
+// FP64 with the batched column-pivoted QR of lmfs_qr.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "lmfs_geom.cuh"
+#include "lmfs_internal.h"
+
+namespace lmfs {
+namespace {
+
+// 2x2 Stokeslet block S(x - y) (eq. (stokeslet2d)), scaled by 1/(4 pi mu).
+__device__ __forceinline__ void stokes2(double dx, double dy, double c, double* s00, double* s01,
+                                        double* s11) {
+  const double r2 = dx * dx + dy * dy;
+  const double lg = 0.5 * log(r2);
+  const double ir2 = 1.0 / r2;
+  *s00 = c * (-lg + dx * dx * ir2);
+  *s01 = c * (dx * dy * ir2);
+  *s11 = c * (-lg + dy * dy * ir2);
+}
+
+// ---- one-body ---------------------------------------------------------
+// Matrix [M | I] per radius class, M = P (resistance) or P (I - L) + B K^T
+// (mobility, eq. (SL)); rows 2Mc, columns 2Nc + 2Mc, column-major.
+__global__ void fill_onebody(double* A, int ld, long long mstride, const double* cls_r, int Nc, int Mc,
+                             double Rc, double cmu, int mobility) {
+  const int b = blockIdx.y;
+  double* M = A + (long long)b * mstride;
+  const double r = cls_r[b];
+  const int rows = 2 * Mc, nsrc = 2 * Nc;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+    const int m = row >> 1, a = row & 1;
+    const double th = 2.0 * LMFS_PI * m / Mc;
+    const double xx = r * cos(th), xy = r * sin(th);
+    const double rs = r * Rc;
+    double pk0 = 0, pk1 = 0, pk2 = 0;
+    for (int j = 0; j < Nc; ++j) {
+      const double ph = 2.0 * LMFS_PI * j / Nc;
+      const double ex = rs * cos(ph), ey = rs * sin(ph);
+      double s00, s01, s11;
+      stokes2(xx - ex, xy - ey, cmu, &s00, &s01, &s11);
+      const double v0 = a == 0 ? s00 : s01;   // (row, col 2j)
+      const double v1 = a == 0 ? s01 : s11;   // (row, col 2j+1)
+      M[(long long)(2 * j) * ld + row] = v0;
+      M[(long long)(2 * j + 1) * ld + row] = v1;
+      // P K for the rigid projector; K rows: [1, 0, -ey], [0, 1, ex]
+      pk0 += v0; pk1 += v1; pk2 += -ey * v0 + ex * v1;
+    }
+    if (mobility) {
+      // (K^T K)^{-1} = diag(1/Nc, 1/Nc, 1/(Nc rs^2)) for an equispaced ring
+      const double g0 = pk0 / Nc, g1 = pk1 / Nc, g2 = pk2 / (Nc * rs * rs);
+      const double bx = (a == 0) ? 1.0 : 0.0, by = (a == 0) ? 0.0 : 1.0;
+      const double bw = (a == 0) ? -xy : xx;   // B row: [bx, by, bw]
+      for (int j = 0; j < Nc; ++j) {
+        const double ph = 2.0 * LMFS_PI * j / Nc;
+        const double ex = rs * cos(ph), ey = rs * sin(ph);
+        // column 2j:   K row [1, 0, -ey];   column 2j+1: K row [0, 1, ex]
+        double* c0 = M + (long long)(2 * j) * ld + row;
+        double* c1 = M + (long long)(2 * j + 1) * ld + row;
+        *c0 += -(g0 + g2 * (-ey)) + (bx + bw * (-ey));
+        *c1 += -(g1 + g2 * ex) + (by + bw * ex);
+      }
+    }
+    for (int q = 0; q < rows; ++q) M[(long long)(nsrc + q) * ld + row] = (q == row) ? 1.0 : 0.0;
+  }
+}
+
+// Extract W (rank rows of Q^T), R (upper 2Nc x 2Nc) from the factored [M | I].
+__global__ void extract_onebody(const double* A, int ld, long long mstride, int Nc, int Mc,
+                                const int* rank, double* W, double* R) {
+  const int b = blockIdx.y;
+  const double* M = A + (long long)b * mstride;
+  const int nsrc = 2 * Nc, nn = 2 * Mc, r = rank[b];
+  double* Wb = W + (long long)b * nsrc * nn;
+  double* Rb = R + (long long)b * nsrc * nsrc;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsrc * nn; t += gridDim.x * blockDim.x) {
+    const int row = t / nn, col = t % nn;
+    Wb[t] = (row < r) ? M[(long long)(nsrc + col) * ld + row] : 0.0;
+  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsrc * nsrc; t += gridDim.x * blockDim.x) {
+    const int col = t / nsrc, row = t % nsrc;
+    Rb[t] = (row <= col) ? M[(long long)col * ld + row] : 0.0;
+  }
+}
+
+// ---- pair geometry ----------------------------------------------------
+struct PairGeo {
+  const double* centres; const double* radii; const int* pairs;  // global
+  int first;               // first pair of the chunk
+  double Rf, gamma, rmob, rho;
+  int Nfp, Nell, neq, nmob, Mp;
+};
+
+// Count the kept shielding-ellipse sources per pair side.
+__global__ void count_enh(PairGeo g, int nb, int* nenh) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nb) return;
+  const int q = g.first + t / 2, side = t & 1;
+  const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
+  PairFrame f = make_frame(g.centres[2 * i], g.centres[2 * i + 1], g.radii[i], g.centres[2 * k],
+                           g.centres[2 * k + 1], g.radii[k]);
+  const double a = side == 0 ? f.p1 : f.p2, rad = side == 0 ? f.r1 : f.r2;
+  int n = 0;
+  if (a > rad * g.Rf) {
+    for (int j = 0; j < 2 * g.Nell; ++j) {
+      double zr, zi;
+      if (ellipse_node(a, rad, g.Rf, g.Nell, g.gamma, j, &zr, &zi)) ++n;
+    }
+  }
+  nenh[t] = n;
+}
+
+// Fine sources (per side: N_fp proxies then kept ellipse nodes), fine nodes
+// (per side: neq equispaced then nmob Moebius nodes) and peanut nodes (Sec. 5,
+// Sec. 3.3).  Yf [nb][SY][2] with side 2 starting at nY1; Xf [nb][2 nX][2];
+// Z [nb][Mp][2].
+__global__ void fill_fine_sets(PairGeo g, int nb, const int* nenh, int SY, double* Yf, double* Xf,
+                               double* Zp) {
+  const int b = blockIdx.y;
+  const int q = g.first + b;
+  const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
+  PairFrame f = make_frame(g.centres[2 * i], g.centres[2 * i + 1], g.radii[i], g.centres[2 * k],
+                           g.centres[2 * k + 1], g.radii[k]);
+  const int e1 = nenh[2 * b], e2 = nenh[2 * b + 1];
+  const int nY1 = g.Nfp + e1;
+  const int nX = g.neq + g.nmob;
+  double* Y = Yf + (long long)b * SY * 2;
+  double* X = Xf + (long long)b * 2 * nX * 2;
+  double* Z = Zp + (long long)b * g.Mp * 2;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  // proxies
+  for (int t = tid; t < 2 * g.Nfp; t += nth) {
+    const int side = t / g.Nfp, s = t % g.Nfp;
+    const double cx = side ? f.c2x : f.c1x, cy = side ? f.c2y : f.c1y, rad = side ? f.r2 : f.r1;
+    const double th = 2.0 * LMFS_PI * s / g.Nfp;
+    double* y = Y + 2 * (side ? nY1 + s : s);
+    y[0] = cx + rad * g.Rf * cos(th);
+    y[1] = cy + rad * g.Rf * sin(th);
+  }
+  // ellipse sources, in order of j (one thread per side)
+  if (tid < 2) {
+    const int side = tid;
+    const double a = side == 0 ? f.p1 : f.p2, rad = side == 0 ? f.r1 : f.r2;
+    const double cx = side ? f.c2x : f.c1x, cy = side ? f.c2y : f.c1y;
+    const double sg = side ? -1.0 : 1.0;
+    int n = 0;
+    if (a > rad * g.Rf) {
+      for (int j = 0; j < 2 * g.Nell; ++j) {
+        double zr, zi;
+        if (!ellipse_node(a, rad, g.Rf, g.Nell, g.gamma, j, &zr, &zi)) continue;
+        const double wr = f.cphi * zr - f.sphi * zi, wi = f.sphi * zr + f.cphi * zi;
+        double* y = Y + 2 * ((side ? nY1 : 0) + g.Nfp + n);
+        y[0] = cx + sg * wr;
+        y[1] = cy + sg * wi;
+        ++n;
+      }
+    }
+    (void)e2;
+  }
+  // nodes
+  for (int t = tid; t < 2 * nX; t += nth) {
+    const int side = t / nX, m = t % nX;
+    const double cx = side ? f.c2x : f.c1x, cy = side ? f.c2y : f.c1y, rad = side ? f.r2 : f.r1;
+    double ang;
+    if (m < g.neq) {
+      ang = 2.0 * LMFS_PI * m / g.neq;
+    } else {
+      const double tt = mobius_angle(m - g.neq, g.nmob, g.rmob);
+      const double phi = atan2(f.sphi, f.cphi);
+      ang = side ? phi + tt : phi + tt - LMFS_PI;
+    }
+    X[2 * t] = cx + rad * cos(ang);
+    X[2 * t + 1] = cy + rad * sin(ang);
+  }
+  for (int t = tid; t < g.Mp; t += nth) peanut_node(f, g.rho, t, g.Mp, Z + 2 * t, Z + 2 * t + 1);
+}
+
+struct PairDims {
+  const int* nenh;  int Nfp; int nX; int SY; int Nc; double Rc; double cmu;
+};
+
+// [F | blkQ]: F = S(X_f, Y_f) (eq. (sys2b)), blkQ = [[0, Q21], [Q12, 0]],
+// Q21 = S(X_f side 1, Y^(2)), Q12 = S(X_f side 2, Y^(1)); column-major, rows
+// 4 nX.  One thread per (node, source) 2x2 block.
+__global__ void fill_FQ(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* A, int ld,
+                        long long mstride) {
+  const int b = blockIdx.y;
+  const int q = g.first + b;
+  const int e1 = pd.nenh[2 * b], e2 = pd.nenh[2 * b + 1];
+  const int nY = 2 * pd.Nfp + e1 + e2, nX = pd.nX, Nc = pd.Nc;
+  const double* Y = Yf + (long long)b * pd.SY * 2;
+  const double* X = Xf + (long long)b * 2 * nX * 2;
+  double* M = A + (long long)b * mstride;
+  const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
+  const long long nblk = (long long)(2 * nX) * (nY + 2 * Nc);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nblk; t += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(t % (2 * nX));
+    const int s = (int)(t / (2 * nX));
+    const double xx = X[2 * n], xy = X[2 * n + 1];
+    int col;
+    double yx, yy;
+    bool zero = false;
+    if (s < nY) {
+      col = 2 * s;
+      yx = Y[2 * s]; yy = Y[2 * s + 1];
+    } else {
+      const int j = (s - nY) % Nc, disk = (s - nY) / Nc;  // disk 0: lambda_bar^1 columns
+      col = 2 * nY + 2 * (disk * Nc + j);
+      const int dd = disk == 0 ? i : k;
+      const double rs = g.radii[dd] * pd.Rc, ph = 2.0 * LMFS_PI * j / Nc;
+      yx = g.centres[2 * dd] + rs * cos(ph);
+      yy = g.centres[2 * dd + 1] + rs * sin(ph);
+      // disk-1 columns live in side-2 rows (Q12), disk-2 columns in side-1 rows (Q21)
+      zero = (disk == 0) ? (n < nX) : (n >= nX);
+    }
+    double s00 = 0, s01 = 0, s11 = 0;
+    if (!zero) stokes2(xx - yx, xy - yy, pd.cmu, &s00, &s01, &s11);
+    double* c0 = M + (long long)col * ld + 2 * n;
+    double* c1 = M + (long long)(col + 1) * ld + 2 * n;
+    c0[0] = s00; c0[1] = s01;
+    c1[0] = s01; c1[1] = s11;
+  }
+}
+
+// Mobility maps (list after eq. (peanut_mob)): per row, F's side-d columns
+// times (I - L_f,d) plus B_f,d K_f,d^T on the diagonal blocks, and blkQ's
+// coarse columns times (I - L).  One thread per row.
+__global__ void project_FQ_mobility(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* A,
+                                    int ld, long long mstride, const double* Gf) {
+  const int b = blockIdx.y;
+  const int q = g.first + b;
+  const int e1 = pd.nenh[2 * b], e2 = pd.nenh[2 * b + 1];
+  const int nY1 = pd.Nfp + e1, nY2 = pd.Nfp + e2, nY = nY1 + nY2, nX = pd.nX, Nc = pd.Nc;
+  const double* Y = Yf + (long long)b * pd.SY * 2;
+  const double* X = Xf + (long long)b * 2 * nX * 2;
+  double* M = A + (long long)b * mstride;
+  const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
+  const double* G = Gf + (long long)b * 18;   // two 3x3 (K_f^T K_f)^{-1}, row-major
+  const int rows = 4 * nX;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
+    const int n = row >> 1, a = row & 1;
+    const int rside = n < nX ? 0 : 1;
+    for (int side = 0; side < 2; ++side) {
+      const int s0 = side ? nY1 : 0, ns = side ? nY2 : nY1;
+      const int dd = side ? k : i;
+      const double cx = g.centres[2 * dd], cy = g.centres[2 * dd + 1];
+      double t0 = 0, t1 = 0, t2 = 0;
+      for (int s = s0; s < s0 + ns; ++s) {
+        const double v0 = M[(long long)(2 * s) * ld + row], v1 = M[(long long)(2 * s + 1) * ld + row];
+        const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+        t0 += v0; t1 += v1; t2 += -ey * v0 + ex * v1;
+      }
+      const double* Gs = G + 9 * side;
+      const double u0 = Gs[0] * t0 + Gs[1] * t1 + Gs[2] * t2;
+      const double u1 = Gs[3] * t0 + Gs[4] * t1 + Gs[5] * t2;
+      const double u2 = Gs[6] * t0 + Gs[7] * t1 + Gs[8] * t2;
+      // B row of this node relative to the source side's centre (only on the diagonal block)
+      const bool diag = (rside == side);
+      const double bx = (a == 0) ? 1.0 : 0.0, by = (a == 0) ? 0.0 : 1.0;
+      const double bw = (a == 0) ? -(X[2 * n + 1] - cy) : (X[2 * n] - cx);
+      for (int s = s0; s < s0 + ns; ++s) {
+        const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+        double* p0 = M + (long long)(2 * s) * ld + row;
+        double* p1 = M + (long long)(2 * s + 1) * ld + row;
+        double d0 = -(u0 + u2 * (-ey)), d1 = -(u1 + u2 * ex);
+        if (diag) { d0 += bx + bw * (-ey); d1 += by + bw * ex; }
+        *p0 += d0;
+        *p1 += d1;
+      }
+    }
+    // coarse columns: ring projector, (K^T K)^{-1} = diag(1/Nc, 1/Nc, 1/(Nc rs^2))
+    for (int disk = 0; disk < 2; ++disk) {
+      const int dd = disk == 0 ? i : k;
+      const double rs = g.radii[dd] * pd.Rc;
+      const int c0 = 2 * nY + 2 * disk * Nc;
+      double t0 = 0, t1 = 0, t2 = 0;
+      for (int j = 0; j < Nc; ++j) {
+        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        const double v0 = M[(long long)(c0 + 2 * j) * ld + row], v1 = M[(long long)(c0 + 2 * j + 1) * ld + row];
+        t0 += v0; t1 += v1; t2 += -ey * v0 + ex * v1;
+      }
+      t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
+      for (int j = 0; j < Nc; ++j) {
+        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        M[(long long)(c0 + 2 * j) * ld + row] -= t0 + t2 * (-ey);
+        M[(long long)(c0 + 2 * j + 1) * ld + row] -= t1 + t2 * ex;
+      }
+    }
+  }
+}
+
+// (K_f^T K_f)^{-1} per pair side (3x3, rows [I_2, (y - c)^perp] per source).
+__global__ void fine_gram_inv(PairDims pd, PairGeo g, const double* Yf, int nb, double* Gf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nb) return;
+  const int b = t / 2, side = t & 1, q = g.first + b;
+  const int e1 = pd.nenh[2 * b], e2 = pd.nenh[2 * b + 1];
+  const int nY1 = pd.Nfp + e1, nY2 = pd.Nfp + e2;
+  const int s0 = side ? nY1 : 0, ns = side ? nY2 : nY1;
+  const int dd = side ? g.pairs[2 * q + 1] : g.pairs[2 * q];
+  const double* Y = Yf + (long long)b * pd.SY * 2;
+  const double cx = g.centres[2 * dd], cy = g.centres[2 * dd + 1];
+  double sx = 0, sy = 0, s2 = 0;
+  for (int s = s0; s < s0 + ns; ++s) {
+    const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+    sx += ex; sy += ey; s2 += ex * ex + ey * ey;
+  }
+  // K^T K = [[n, 0, -sy], [0, n, sx], [-sy, sx, s2]]
+  const double n = ns;
+  const double m[9] = {n, 0, -sy, 0, n, sx, -sy, sx, s2};
+  const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+  const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  double* G = Gf + (long long)b * 18 + 9 * side;
+  G[0] = c00 / det; G[1] = (m[2] * m[7] - m[1] * m[8]) / det; G[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+  G[3] = c01 / det; G[4] = (m[0] * m[8] - m[2] * m[6]) / det; G[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+  G[6] = c02 / det; G[7] = (m[1] * m[6] - m[0] * m[7]) / det; G[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+}
+
+// E = sgn * blockdiag(K_f1^T, K_f2^T) Z (eq. (force_ext) with beta = -Z lam,
+// sgn = -1, resistance; eq. (rbm2), sgn = +1, mobility).  One warp per
+// (pair, column).  Also writes Zp = (I - L_f) Z for mobility (in place of Z's
+// copy) when zp != nullptr.
+__global__ void extract_E(PairDims pd, PairGeo g, const double* Yf, const double* Z, int zld,
+                          long long zstride, int k, double sgn, double* E, int Cfirst, const double* Gf,
+                          double* Zp) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  if (warp >= k) return;
+  const int col = warp, q = g.first + b;
+  const int e1 = pd.nenh[2 * b], e2 = pd.nenh[2 * b + 1];
+  const int nY1 = pd.Nfp + e1, nY2 = pd.Nfp + e2;
+  const double* Y = Yf + (long long)b * pd.SY * 2;
+  const double* Zc = Z + (long long)b * zstride + (long long)col * zld;
+  double* out = E + (long long)(Cfirst + b) * 6 * k;
+  for (int side = 0; side < 2; ++side) {
+    const int s0 = side ? nY1 : 0, ns = side ? nY2 : nY1;
+    const int dd = side ? g.pairs[2 * q + 1] : g.pairs[2 * q];
+    const double cx = g.centres[2 * dd], cy = g.centres[2 * dd + 1];
+    double t0 = 0, t1 = 0, t2 = 0;
+    for (int s = s0 + lane; s < s0 + ns; s += 32) {
+      const double z0 = Zc[2 * s], z1 = Zc[2 * s + 1];
+      const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+      t0 += z0; t1 += z1; t2 += -ey * z0 + ex * z1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+      t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+      t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+    }
+    if (lane == 0) {
+      out[(3 * side + 0) * k + col] = sgn * t0;
+      out[(3 * side + 1) * k + col] = sgn * t1;
+      out[(3 * side + 2) * k + col] = sgn * t2;
+    }
+    if (Zp) {
+      const double* G = Gf + (long long)b * 18 + 9 * side;
+      const double u0 = G[0] * t0 + G[1] * t1 + G[2] * t2;
+      const double u1 = G[3] * t0 + G[4] * t1 + G[5] * t2;
+      const double u2 = G[6] * t0 + G[7] * t1 + G[8] * t2;
+      double* Zpc = Zp + (long long)b * zstride + (long long)col * zld;
+      for (int s = s0 + lane; s < s0 + ns; s += 32) {
+        const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+        Zpc[2 * s] = Zc[2 * s] - (u0 + u2 * (-ey));
+        Zpc[2 * s + 1] = Zc[2 * s + 1] - (u1 + u2 * ex);
+      }
+    }
+  }
+}
+
+// D = S(z, Y_f) (eq. (peanut)), column-major [2Mp][nY]; and C = S(z, Y^(1-2))
+// (times (I - L^pair) for mobility) into the second workspace's first 4Nc
+// columns.
+__global__ void fill_DC(PairDims pd, PairGeo g, const double* Yf, const double* Zpts, double* D, int dld,
+                        long long dstride, double* W2, int ld2, long long w2stride, int mobility) {
+  const int b = blockIdx.y, q = g.first + b;
+  const int e1 = pd.nenh[2 * b], e2 = pd.nenh[2 * b + 1];
+  const int nY = 2 * pd.Nfp + e1 + e2, Mp = g.Mp, Nc = pd.Nc;
+  const double* Y = Yf + (long long)b * pd.SY * 2;
+  const double* Z = Zpts + (long long)b * Mp * 2;
+  double* Db = D + (long long)b * dstride;
+  double* Cb = W2 + (long long)b * w2stride;
+  const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
+  const long long nD = (long long)Mp * nY, nC = (long long)Mp * 2 * Nc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nD + nC; t += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)((t < nD ? t : t - nD) % Mp);
+    const int s = (int)((t < nD ? t : t - nD) / Mp);
+    double yx, yy;
+    double* base;
+    int ldd;
+    if (t < nD) { yx = Y[2 * s]; yy = Y[2 * s + 1]; base = Db; ldd = dld; }
+    else {
+      const int disk = s / Nc, j = s % Nc, dd = disk ? k : i;
+      const double rs = g.radii[dd] * pd.Rc, ph = 2.0 * LMFS_PI * j / Nc;
+      yx = g.centres[2 * dd] + rs * cos(ph); yy = g.centres[2 * dd + 1] + rs * sin(ph);
+      base = Cb; ldd = ld2;
+    }
+    double s00, s01, s11;
+    stokes2(Z[2 * p] - yx, Z[2 * p + 1] - yy, pd.cmu, &s00, &s01, &s11);
+    double* c0 = base + (long long)(2 * s) * ldd + 2 * p;
+    double* c1 = base + (long long)(2 * s + 1) * ldd + 2 * p;
+    c0[0] = s00; c0[1] = s01; c1[0] = s01; c1[1] = s11;
+  }
+  (void)mobility;
+}
+
+// C (I - L^pair) in place: per row, per disk, ring projector.
+__global__ void project_C(PairDims pd, PairGeo g, double* W2, int ld2, long long w2stride) {
+  const int b = blockIdx.y, q = g.first + b, Nc = pd.Nc;
+  double* Cb = W2 + (long long)b * w2stride;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < 2 * g.Mp; row += gridDim.x * blockDim.x) {
+    for (int disk = 0; disk < 2; ++disk) {
+      const int dd = disk ? g.pairs[2 * q + 1] : g.pairs[2 * q];
+      const double rs = g.radii[dd] * pd.Rc;
+      const int c0 = 2 * disk * Nc;
+      double t0 = 0, t1 = 0, t2 = 0;
+      for (int j = 0; j < Nc; ++j) {
+        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        const double v0 = Cb[(long long)(c0 + 2 * j) * ld2 + row], v1 = Cb[(long long)(c0 + 2 * j + 1) * ld2 + row];
+        t0 += v0; t1 += v1; t2 += -ey * v0 + ex * v1;
+      }
+      t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
+      for (int j = 0; j < Nc; ++j) {
+        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        Cb[(long long)(c0 + 2 * j) * ld2 + row] -= t0 + t2 * (-ey);
+        Cb[(long long)(c0 + 2 * j + 1) * ld2 + row] -= t1 + t2 * ex;
+      }
+    }
+  }
+}
+
+// Batched FP64 GEMM  Out[b] = Amat[b] (M x K_b) * Bmat[b] (K_b x N), column-major.
+constexpr int GT = 32;
+__global__ void gemm_batched(const double* Am, int lda, long long sa, const double* Bm, int ldb, long long sb,
+                             double* Out, int ldo, long long so, int M, int N, const int* Kb, int kfixed,
+                             const PairDims* pdp) {
+  __shared__ double As[GT][GT + 1];
+  __shared__ double Bs[GT][GT + 1];
+  const int b = blockIdx.z;
+  int K = kfixed;
+  if (Kb) K = 2 * (2 * pdp->Nfp + Kb[2 * b] + Kb[2 * b + 1]);
+  const double* A_ = Am + (long long)b * sa;
+  const double* B_ = Bm + (long long)b * sb;
+  double* O = Out + (long long)b * so;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const int row0 = blockIdx.x * GT, col0 = blockIdx.y * GT;
+  double acc[4] = {0, 0, 0, 0};
+  for (int kk = 0; kk < K; kk += GT) {
+    for (int r = ty; r < GT; r += 8) {
+      const int ar = row0 + tx, ac = kk + r;
+      As[r][tx] = (ar < M && ac < K) ? A_[(long long)ac * lda + ar] : 0.0;
+      const int br = kk + tx, bc = col0 + r;
+      Bs[r][tx] = (br < K && bc < N) ? B_[(long long)bc * ldb + br] : 0.0;
+    }
+    __syncthreads();
+    for (int e = 0; e < GT; ++e) {
+      const double a = As[e][tx];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] += a * Bs[ty + 8 * c][e];
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < 4; ++c) {
+    const int r = row0 + tx, cc = col0 + ty + 8 * c;
+    if (r < M && cc < N) O[(long long)cc * ldo + r] = acc[c];
+  }
+}
+
+// A = -X (row-major [4Nc][4Nc]) from the column-major solution X.
+__global__ void store_A(const double* X, int xld, long long xstride, int n4, double* A, int Cfirst) {
+  const int b = blockIdx.y;
+  const double* Xb = X + (long long)b * xstride;
+  double* Ab = A + (long long)(Cfirst + b) * n4 * n4;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4 * n4; t += gridDim.x * blockDim.x) {
+    const int row = t / n4, col = t % n4;
+    Ab[t] = -Xb[(long long)col * xld + row];
+  }
+}
+
+__global__ void any_nonzero(const int* v, int n, int* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && v[t]) atomicOr(out, 1);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int build_onebody(Ctx& c, int problem, OneBody& ob) {
+  const int Nc = c.d.Nc, Mc = c.d.Mc;
+  const int nb = (int)c.cls_r_h.size();
+  const int m = 2 * Mc, n = 2 * Nc, k = 2 * Mc;
+  const int ld = m;
+  const long long mstride = (long long)ld * (n + k);
+  ob.nclass = nb;
+  LMFS_TRY(dalloc(&ob.W, (size_t)nb * n * 2 * Mc));
+  LMFS_TRY(dalloc(&ob.R, (size_t)nb * n * n));
+  LMFS_TRY(dalloc(&ob.perm, (size_t)nb * n));
+  LMFS_TRY(dalloc(&ob.rank, (size_t)nb));
+  double *ws = nullptr, *tau = nullptr, *vn = nullptr;
+  int *dm = nullptr, *dn = nullptr, *info = nullptr, *bad = nullptr;
+  int rc = LMFS_OK;
+  std::vector<int> hm(nb, m), hn(nb, n);
+  int hbad = 0;
+  if ((rc = dalloc(&ws, (size_t)nb * mstride)) || (rc = dalloc(&tau, (size_t)nb * n)) ||
+      (rc = dalloc(&vn, (size_t)nb * 2 * n)) || (rc = dalloc(&dm, nb)) || (rc = dalloc(&dn, nb)) ||
+      (rc = dalloc(&info, nb)) || (rc = dalloc(&bad, 1)))
+    goto done;
+  if (cuda_failed(cudaMemcpyAsync(dm, hm.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+      cuda_failed(cudaMemcpyAsync(dn, hn.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+      cuda_failed(cudaMemsetAsync(bad, 0, sizeof(int), c.stream), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
+  {
+    dim3 grid(2, nb);
+    fill_onebody<<<grid, 128, 0, c.stream>>>(ws, ld, mstride, c.cls_r, Nc, Mc, c.Rc, 1.0 / (4 * LMFS_PI * c.prm.mu),
+                                             problem == LMFS_MOBILITY);
+    if ((rc = check_launch("fill_onebody"))) goto done;
+    QRBatch q{};
+    q.A = ws; q.mstride = mstride; q.m = dm; q.n = dn; q.k = k; q.ld = ld; q.eps = c.prm.eps_trunc;
+    q.X = nullptr; q.xld = 0; q.xstride = 0; q.rank = ob.rank; q.perm = ob.perm; q.permstride = n;
+    q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = n;
+    if ((rc = qr_solve_batched(q, c.stream, false))) goto done;
+    extract_onebody<<<grid, 256, 0, c.stream>>>(ws, ld, mstride, Nc, Mc, ob.rank, ob.W, ob.R);
+    if ((rc = check_launch("extract_onebody"))) goto done;
+    any_nonzero<<<(nb + 255) / 256, 256, 0, c.stream>>>(info, nb, bad);
+    note_launches(1);
+    ob.rank_h.assign(nb, 0);
+    if (cuda_failed(cudaMemcpyAsync(ob.rank_h.data(), ob.rank, nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+        cuda_failed(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+        cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
+    if (hbad) { set_last_error("non-finite value in a one-body factorization"); rc = LMFS_ERR_NUMERICAL; }
+  }
+done:
+  dfree(ws); dfree(tau); dfree(vn); dfree(dm); dfree(dn); dfree(info); dfree(bad);
+  return rc;
+}
+
+int build_pair_blocks(Ctx& c, int problem) {
+  PairBlocks& pb = c.prob[problem];
+  const int C = c.C, Nc = c.d.Nc;
+  const int n4 = 4 * Nc;
+  if (!pb.A) LMFS_TRY(dalloc(&pb.A, (size_t)std::max(C, 1) * n4 * n4));
+  if (!pb.E) LMFS_TRY(dalloc(&pb.E, (size_t)std::max(C, 1) * 6 * n4));
+  if (C == 0) return LMFS_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int Nfp = c.prm.Nfp, Nell = c.prm.Nell, Mp = c.prm.Mp;
+  const int neq = (int)std::ceil(c.prm.af * Nfp);
+  const int nmob = (int)std::lround(c.prm.aell * Nell);
+  const int nX = neq + nmob;
+  const int m1 = 4 * nX;                // rows of [F | blkQ]
+  const int SYmax = 2 * (Nfp + 2 * Nell);
+  const int nmax = 2 * SYmax;           // max columns of F
+  const int k = n4;
+  const int ld1 = m1;
+  const long long s1 = (long long)ld1 * (nmax + k);
+  const int ld2 = 2 * Mp;
+  const long long s2 = (long long)ld2 * (n4 + k);
+  // chunk size: bounded by ~12 GB of workspace and 3 blocks per SM
+  const long long per = s1 + (long long)nmax * k * 2 + (long long)ld2 * nmax + s2 + (long long)n4 * k;
+  int chunk = (int)std::min<long long>(C, std::max<long long>(1, (12LL << 30) / (per * 8)));
+  chunk = std::min(chunk, 456);
+  double *ws1 = nullptr, *Z = nullptr, *Zp = nullptr, *D = nullptr, *ws2 = nullptr, *X2 = nullptr;
+  double *Yf = nullptr, *Xf = nullptr, *Zpts = nullptr, *Gf = nullptr, *tau = nullptr, *vn = nullptr;
+  int *nenh = nullptr, *dm = nullptr, *dn = nullptr, *rank = nullptr, *perm = nullptr, *info = nullptr;
+  int *dm2 = nullptr, *dn2 = nullptr, *bad = nullptr;
+  PairDims* pdd = nullptr;
+  int rc = LMFS_OK;
+  const bool mob = problem == LMFS_MOBILITY;
+  std::vector<int> hen(2 * chunk), hm(chunk), hn(chunk), hr(chunk), hr2(chunk);
+  int hbad = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double qr_ms = 0.0, qr_flops = 0.0;
+  // algorithmic flops of one QR launch: reflector s applied to the n + k - s - 1
+  // trailing columns (a dot and an update of length m - s), then k back
+  // substitutions with the r x r triangle
+  auto qrf = [](double m, double n, double k, double r) {
+    double f = 0.0;
+    for (int s = 0; s < (int)r; ++s) f += 4.0 * (m - s) * (n + k - s - 1);
+    return f + k * r * r;
+  };
+  for (auto& e : ev) cudaEventCreate(&e);
+  int minr = 1 << 30, maxr = 0;
+  if ((rc = dalloc(&ws1, (size_t)chunk * s1)) || (rc = dalloc(&Z, (size_t)chunk * nmax * k)) ||
+      (mob && (rc = dalloc(&Zp, (size_t)chunk * nmax * k))) || (rc = dalloc(&D, (size_t)chunk * ld2 * nmax)) ||
+      (rc = dalloc(&ws2, (size_t)chunk * s2)) || (rc = dalloc(&X2, (size_t)chunk * n4 * k)) ||
+      (rc = dalloc(&Yf, (size_t)chunk * SYmax * 2)) || (rc = dalloc(&Xf, (size_t)chunk * 2 * nX * 2)) ||
+      (rc = dalloc(&Zpts, (size_t)chunk * Mp * 2)) || (rc = dalloc(&Gf, (size_t)chunk * 18)) ||
+      (rc = dalloc(&tau, (size_t)chunk * nmax)) || (rc = dalloc(&vn, (size_t)chunk * 2 * nmax)) ||
+      (rc = dalloc(&nenh, (size_t)2 * chunk)) || (rc = dalloc(&dm, chunk)) || (rc = dalloc(&dn, chunk)) ||
+      (rc = dalloc(&rank, chunk)) || (rc = dalloc(&perm, (size_t)chunk * nmax)) || (rc = dalloc(&info, chunk)) ||
+      (rc = dalloc(&dm2, chunk)) || (rc = dalloc(&dn2, chunk)) || (rc = dalloc(&bad, 1)) ||
+      (rc = dalloc(&pdd, 1)))
+    goto done;
+  if (cuda_failed(cudaMemsetAsync(bad, 0, sizeof(int), c.stream), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
+  for (int first = 0; first < C; first += chunk) {
+    const int nb = std::min(chunk, C - first);
+    PairGeo g;
+    g.centres = c.centres; g.radii = c.radii; g.pairs = c.pairs; g.first = first;
+    g.Rf = c.Rf; g.gamma = c.prm.gamma; g.rmob = c.prm.r_mob; g.rho = c.rho;
+    g.Nfp = Nfp; g.Nell = Nell; g.neq = neq; g.nmob = nmob; g.Mp = Mp;
+    count_enh<<<(2 * nb + 127) / 128, 128, 0, c.stream>>>(g, nb, nenh);
+    if ((rc = check_launch("count_enh"))) goto done;
+    if (cuda_failed(cudaMemcpyAsync(hen.data(), nenh, 2 * nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+        cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
+    for (int b = 0; b < nb; ++b) { hm[b] = m1; hn[b] = 2 * (2 * Nfp + hen[2 * b] + hen[2 * b + 1]); }
+    std::vector<int> hm2(nb, 2 * Mp), hn2(nb, n4);
+    PairDims pd;
+    pd.nenh = nenh; pd.Nfp = Nfp; pd.nX = nX; pd.SY = SYmax; pd.Nc = Nc; pd.Rc = c.Rc;
+    pd.cmu = 1.0 / (4 * LMFS_PI * c.prm.mu);
+    if (cuda_failed(cudaMemcpyAsync(dm, hm.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+        cuda_failed(cudaMemcpyAsync(dn, hn.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+        cuda_failed(cudaMemcpyAsync(dm2, hm2.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+        cuda_failed(cudaMemcpyAsync(dn2, hn2.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+        cuda_failed(cudaMemcpyAsync(pdd, &pd, sizeof(PairDims), cudaMemcpyHostToDevice, c.stream), "h2d")) {
+      rc = LMFS_ERR_CUDA; goto done;
+    }
+    fill_fine_sets<<<dim3(4, nb), 256, 0, c.stream>>>(g, nb, nenh, SYmax, Yf, Xf, Zpts);
+    if ((rc = check_launch("fill_fine_sets"))) goto done;
+    fill_FQ<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ld1, s1);
+    if ((rc = check_launch("fill_FQ"))) goto done;
+    if (mob) {
+      fine_gram_inv<<<(2 * nb + 127) / 128, 128, 0, c.stream>>>(pd, g, Yf, nb, Gf);
+      note_launches(1);
+      project_FQ_mobility<<<dim3((m1 + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ld1, s1, Gf);
+      if ((rc = check_launch("project_FQ_mobility"))) goto done;
+    }
+    // F's columns beyond n_b (unused padding) are never touched: the RHS block
+    // starts at column n_b, so move it there when n_b < nmax -- the fill put
+    // blkQ right after F's own columns, i.e. already at column n_b.
+    {
+      QRBatch q{};
+      q.A = ws1; q.mstride = s1; q.m = dm; q.n = dn; q.k = k; q.ld = ld1; q.eps = c.prm.eps_trunc_fine;
+      q.X = Z; q.xld = nmax; q.xstride = (long long)nmax * k; q.rank = rank; q.perm = perm; q.permstride = nmax;
+      q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = nmax;
+      cudaEventRecord(ev[0], c.stream);
+      if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
+      cudaEventRecord(ev[1], c.stream);
+    }
+    any_nonzero<<<(nb + 255) / 256, 256, 0, c.stream>>>(info, nb, bad);
+    note_launches(1);
+    extract_E<<<dim3((k * 32 + 255) / 256, nb), 256, 0, c.stream>>>(pd, g, Yf, Z, nmax, (long long)nmax * k, k,
+                                                                   mob ? 1.0 : -1.0, pb.E, first, Gf, mob ? Zp : nullptr);
+    if ((rc = check_launch("extract_E"))) goto done;
+    fill_DC<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Zpts, D, ld2, (long long)ld2 * nmax, ws2, ld2, s2, mob);
+    if ((rc = check_launch("fill_DC"))) goto done;
+    if (mob) {
+      project_C<<<dim3((2 * Mp + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, ws2, ld2, s2);
+      if ((rc = check_launch("project_C"))) goto done;
+    }
+    // DZ into the right-hand-side columns of the second workspace
+    {
+      dim3 grid((2 * Mp + GT - 1) / GT, (k + GT - 1) / GT, nb);
+      gemm_batched<<<grid, 256, 0, c.stream>>>(D, ld2, (long long)ld2 * nmax, mob ? Zp : Z, nmax, (long long)nmax * k,
+                                               ws2 + (long long)n4 * ld2, ld2, s2, 2 * Mp, k, nenh, 0, pdd);
+      if ((rc = check_launch("gemm DZ"))) goto done;
+    }
+    {
+      QRBatch q{};
+      q.A = ws2; q.mstride = s2; q.m = dm2; q.n = dn2; q.k = k; q.ld = ld2; q.eps = c.prm.eps_trunc;
+      q.X = X2; q.xld = n4; q.xstride = (long long)n4 * k; q.rank = rank + 0; q.perm = perm; q.permstride = nmax;
+      q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = n4;
+      // ranks of F are read back before this call overwrites them
+      if (cuda_failed(cudaMemcpyAsync(hr.data(), rank, nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+          cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
+      for (int b = 0; b < nb; ++b) {
+        minr = std::min(minr, hr[b]); maxr = std::max(maxr, hr[b]);
+        qr_flops += qrf(m1, hn[b], k, hr[b]);
+      }
+      cudaEventRecord(ev[2], c.stream);
+      if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
+      cudaEventRecord(ev[3], c.stream);
+      if (cuda_failed(cudaMemcpyAsync(hr2.data(), rank, nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+          cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
+      for (int b = 0; b < nb; ++b) qr_flops += qrf(2 * Mp, n4, k, hr2[b]);
+      float ms0 = 0, ms1 = 0;
+      cudaEventElapsedTime(&ms0, ev[0], ev[1]);
+      cudaEventElapsedTime(&ms1, ev[2], ev[3]);
+      qr_ms += ms0 + ms1;
+    }
+    any_nonzero<<<(nb + 255) / 256, 256, 0, c.stream>>>(info, nb, bad);
+    note_launches(1);
+    store_A<<<dim3(64, nb), 256, 0, c.stream>>>(X2, n4, (long long)n4 * k, n4, pb.A, first);
+    if ((rc = check_launch("store_A"))) goto done;
+  }
+  if (cuda_failed(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+      cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
+  if (hbad) { set_last_error("non-finite value in a pair factorization"); rc = LMFS_ERR_NUMERICAL; goto done; }
+  pb.min_rank_F = minr; pb.max_rank_F = maxr;
+  pb.qr_ms = qr_ms; pb.qr_flops = qr_flops;
+  pb.t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+done:
+  dfree(ws1); dfree(Z); dfree(Zp); dfree(D); dfree(ws2); dfree(X2); dfree(Yf); dfree(Xf); dfree(Zpts);
+  dfree(Gf); dfree(tau); dfree(vn); dfree(nenh); dfree(dm); dfree(dn); dfree(rank); dfree(perm);
+  dfree(info); dfree(dm2); dfree(dn2); dfree(bad); dfree(pdd);
+  for (auto& e : ev) if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+}  // namespace lmfs

@@ -1,0 +1,288 @@
+"""GPU path (C ABI) against the CPU oracle, element by element on seeded
+inputs.  Tolerances: FP64 matvec 1e-12 relative where the oracle's own
+literal-form rounding allows it (see fp64_tolerance), mixed-precision matvec
+1e-6, solved velocities and forces 1e-5 (relative 2-norm)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle.gmres import gmres
+from oracle.kernel import stokeslet
+from oracle.pairs import pair_blocks
+from oracle.params import PACKING, PAIR_SMALL, POLY
+from oracle.system import System
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.220446049250313e-16
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2606_11273_gb300 import build
+    build.build()
+    import paper_2606_11273_gb300 as lib
+    return lib
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def gparams(L, p, **kw):
+    base = dict(Nc=p.Nc, Mc=p.Mc, Rc=p.Rc, Nfp=p.Nfp, Nell=p.Nell, Mp=p.Mp, delta_c=p.delta_c, tol=p.tol,
+                gamma=p.gamma, af=p.af, r_mob=p.r_mob, aell=p.aell, eps_trunc=p.eps_trunc,
+                eps_trunc_fine=p.eps_trunc_fine, mu=p.mu)
+    base.update(kw)
+    return L.Params(**base)
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x).ravel(), dtype=torch.float64, device="cuda")
+
+
+def gpu_matvec(L, s, problem, mu, prec):
+    md = dev(mu)
+    ud = torch.zeros_like(md)
+    s.matvec(problem, md, ud, prec)
+    torch.cuda.synchronize()
+    return ud.cpu().numpy().reshape(np.shape(mu))
+
+
+def fp64_tolerance(sysm, mu):
+    """The oracle runs Algorithm 3 literally: Step 2a sums every source,
+    self and close partners included, with the corrected strengths, and Step
+    2b subtracts the pair-internal terms again.  Its rounding error is about
+    eps * || |S| |sigma| || (the absolute-value sum of the terms that cancel);
+    the tolerance is the larger of 1e-12 and 50 times that, relative to ||u||."""
+    lb = sysm.lam_bar(mu)
+    lam = lb.copy()
+    n = 2 * sysm.p.Nc
+    for (i, k), b in zip(sysm.pairs, sysm.blocks):
+        t = b["A"] @ np.concatenate([lb[i], lb[k]])
+        lam[i] += t[:n]
+        lam[k] += t[n:]
+    sig = np.stack([sysm.proj(i, lam[i]) for i in range(sysm.P)])
+    if sysm.S_all is not None:
+        scale = np.linalg.norm(np.abs(sysm.S_all) @ np.abs(sig).ravel())
+    else:
+        scale = np.linalg.norm(np.abs(sig)) * 10.0
+    u = sysm.matvec(mu)
+    return max(1e-12, 50 * EPS64 * scale / np.linalg.norm(u))
+
+
+# ----------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_disk_closed_forms(L, prec):
+    s = L.Solver([[0.3, -0.1]], [1.0], gparams(L, PACKING, precision=prec, tol=1e-13))
+    ft, info = s.solve(L.RESISTANCE, [[1.0, -0.5, 0.0]])
+    assert np.allclose(ft[0], [8 * math.pi, -4 * math.pi, 0.0], rtol=1e-10, atol=1e-9)
+    ft, _ = s.solve(L.RESISTANCE, [[0.0, 0.0, 1.0]])
+    assert np.allclose(ft[0], [0, 0, 4 * math.pi], atol=1e-9)
+    v, _ = s.solve(L.MOBILITY, [[0.3, 1.1, -2.0]])
+    m = 0.5 / (4 * math.pi)
+    assert np.allclose(v[0], [0.3 * m, 1.1 * m, -2.0 / (4 * math.pi)], rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------- config 1
+@pytest.fixture(scope="module")
+def pair1():
+    pk = w.two_disks(1e-3)
+    so = System(pk.centres, pk.radii, PAIR_SMALL, "resistance")
+    return pk, so
+
+
+def test_two_disks_resistance_fp64(L, pair1):
+    """Two unit disks at gap 1e-3, 36 coarse sources on radius 0.7, 400 fine
+    proxies; FP64, tol 1e-10: one GMRES iteration (the isolated-pair matvec is
+    the identity), forces within 1e-5 of the oracle."""
+    pk, so = pair1
+    vel = w.rigid_velocities(2, 11)
+    fo, io = so.solve(vel)
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PAIR_SMALL, precision=L.FP64))
+    fg, ig = s.solve(L.RESISTANCE, vel)
+    assert ig["iters"] == 1 and io["iters"] == 1
+    assert rel(fg, fo) < 1e-5
+
+
+def test_two_disks_pair_blocks(L, pair1):
+    """QR-truncated blocks against SVD-truncated ones: the unique parts agree --
+    E (fine-source forces) and C A (the compressed field on the peanut)."""
+    pk, so = pair1
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PAIR_SMALL, precision=L.FP64))
+    s.precompute(L.RESISTANCE)
+    A, E = s.pair_blocks(L.RESISTANCE)
+    b = pair_blocks(pk.centres[0], 1.0, pk.centres[1], 1.0, so.ob[0], so.ob[1], PAIR_SMALL, "resistance", 1.0,
+                    keep=True)
+    assert rel(E[0], b["E"]) < 1e-5
+    assert rel(b["C"] @ A[0], b["C"] @ b["A"]) < 1e-5
+    assert np.array_equal(s.pairs(), np.array([[0, 1]]))
+
+
+# ----------------------------------------------------------------- config 2
+@pytest.fixture(scope="module")
+def p100():
+    pk = w.packing_p100()
+    so = System(pk.centres, pk.radii, PACKING, "mobility")
+    ft = w.forces_torques(100, 5)
+    b = so.rhs_mobility(ft)
+    vs = []
+
+    def mv(x):
+        vs.append(x.copy())
+        return so.matvec(x)
+    gmres(mv, b, 1e-12, 10)
+    return pk, so, ft, vs
+
+
+def test_p100_contacts_match(L, p100):
+    pk, so, _, _ = p100
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
+    assert [tuple(x) for x in s.pairs()] == so.pairs
+
+
+def test_p100_matvec_exchanged_blocks(L, p100):
+    """Identical (oracle) pair blocks in both: FP64 within the oracle's
+    literal-form rounding bound, mixed within 1e-6, on the right-hand side and
+    the first Krylov vectors of the solve."""
+    pk, so, ft, vs = p100
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
+    s.set_pair_blocks(L.MOBILITY, np.stack([b["A"] for b in so.blocks]), np.stack([b["E"] for b in so.blocks]))
+    for j, v in enumerate(vs[:8]):
+        uo = so.matvec(v)
+        tol64 = fp64_tolerance(so, v)
+        e64 = rel(gpu_matvec(L, s, L.MOBILITY, v, L.FP64), uo)
+        e32 = rel(gpu_matvec(L, s, L.MOBILITY, v, L.MIXED), uo)
+        print(f"krylov {j}: fp64 {e64:.2e} (bound {tol64:.1e})  mixed {e32:.2e}")
+        assert e64 < tol64, (j, e64, tol64)
+        assert e32 < 1e-6, (j, e32)
+
+
+@pytest.mark.parametrize("problem", ["mobility", "resistance"])
+def test_p100_matvec_fp64_where_oracle_is_exact(L, p100, problem):
+    """With zero pair blocks injected in both (no large cancelling correction
+    strengths), the oracle's literal form is accurate to rounding, and the FP64
+    path must match it to 1e-12; the mixed path to 1e-6.  Covers the one-body
+    factors, the near/far split, the close-partner exclusion, the multipole far
+    field and the identity step at full P = 100 size."""
+    pk, _, ft, _ = p100
+    so0 = System(pk.centres, pk.radii, PACKING, problem,
+                 blocks=[{"A": np.zeros((240, 240)), "E": np.zeros((6, 240))}] * 37)
+    assert len(so0.pairs) == 37
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
+    s.set_pair_blocks(L.MOBILITY if problem == "mobility" else L.RESISTANCE, np.zeros((37, 240, 240)),
+                      np.zeros((37, 6, 240)))
+    code = L.MOBILITY if problem == "mobility" else L.RESISTANCE
+    for seed in (1, 2):
+        mu = w.smooth_surface_vector(100, 72, seed).reshape(100, -1)
+        uo = so0.matvec(mu)
+        assert rel(gpu_matvec(L, s, code, mu, L.FP64), uo) < 1e-12
+        assert rel(gpu_matvec(L, s, code, mu, L.MIXED), uo) < 1e-6
+
+
+def test_p100_rhs_mobility(L, p100):
+    pk, so, ft, _ = p100
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
+    bo = so.rhs_mobility(ft)
+    for prec, tol in ((L.FP64, 1e-12), (L.MIXED, 1e-6), (L.MIXED_DIRECT, 1e-6)):
+        bd = torch.zeros(bo.size, dtype=torch.float64, device="cuda")
+        s.rhs(L.MOBILITY, dev(ft), bd, prec)
+        torch.cuda.synchronize()
+        assert rel(bd.cpu().numpy().reshape(bo.shape), bo) < tol, prec
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_p100_mobility_solve(L, p100, prec):
+    """Full GPU pipeline (device pair precompute by QR) against the oracle's
+    SVD-based solve: velocities within 1e-5."""
+    pk, so, ft, _ = p100
+    vo, io = so.solve(ft, tol=1e-9)
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, precision=prec, tol=1e-9))
+    vg, ig = s.solve(L.MOBILITY, ft)
+    assert ig["converged"]
+    assert rel(vg, vo) < 1e-5, rel(vg, vo)
+    vg2, _ = s.solve(L.MOBILITY, ft)
+    assert np.array_equal(vg, vg2)          # bitwise reproducible
+
+
+# ----------------------------------------------------------------- clusters
+def test_three_disk_chain_resistance(L):
+    c = np.array([[0.0, 0.0], [2.01, 0.0], [4.02, 0.3]])
+    data = np.array([[1.0, 0.3, 0.2], [-0.5, -0.3, 0.4], [-0.5, 0.0, -0.1]])
+    fo, _ = System(c, np.ones(3), PACKING, "resistance").solve(data, tol=1e-12)
+    for prec in (0, 1):
+        s = L.Solver(c, np.ones(3), gparams(L, PACKING, precision=prec, tol=1e-12))
+        fg, _ = s.solve(L.RESISTANCE, data)
+        assert rel(fg, fo) < 1e-5
+
+
+def test_polydisperse_mobility(L):
+    """Unequal radii (this build's extension: limiting points of unequal
+    circles, rolling radius = smallest radius)."""
+    rng = np.random.default_rng(7)
+    r = rng.uniform(0.8, 1.2, 8)
+    pk = w.packing(8, 0.45, 11, gmin=1e-3, radii=r, start="hex", nsweep=10, snap_gap=2e-3)
+    ft = w.forces_torques(8, 3)
+    so = System(pk.centres, pk.radii, POLY, "mobility")
+    assert len(so.pairs) >= 1
+    vo, _ = so.solve(ft, tol=1e-11)
+    for prec in (0, 1):
+        s = L.Solver(pk.centres, pk.radii, gparams(L, POLY, precision=prec, tol=1e-11))
+        vg, _ = s.solve(L.MOBILITY, ft)
+        assert rel(vg, vo) < 1e-5
+
+
+# ----------------------------------------------------------------- edges
+def test_edge_cases(L):
+    p = gparams(L, PACKING)
+    with pytest.raises(L.LmfsError):            # overlapping disks
+        L.Solver([[0.0, 0.0], [1.5, 0.0]], [1.0, 1.0], p)
+    with pytest.raises(L.LmfsError):            # touching disks (gap 0)
+        L.Solver([[0.0, 0.0], [2.0, 0.0]], [1.0, 1.0], p)
+    with pytest.raises(L.LmfsError):            # non-positive radius
+        L.Solver([[0.0, 0.0]], [-1.0], p)
+    with pytest.raises(L.LmfsError):            # non-finite centre
+        L.Solver([[np.nan, 0.0]], [1.0], p)
+    with pytest.raises(L.LmfsError):            # source radius rule fails for Nc < 28
+        L.Solver([[0.0, 0.0]], [1.0], gparams(L, PACKING, Nc=20, Mc=24))
+    # no close pairs: one-body preconditioning; far-apart disks
+    c = np.array([[0.0, 0.0], [6.0, 0.0], [0.0, 7.5]])
+    so = System(c, np.ones(3), PACKING, "resistance")
+    fo, _ = so.solve(np.eye(3), tol=1e-12)
+    s = L.Solver(c, np.ones(3), gparams(L, PACKING, precision=L.FP64, tol=1e-12))
+    assert s.n_pairs == 0
+    fg, _ = s.solve(L.RESISTANCE, np.eye(3))
+    assert rel(fg, fo) < 1e-9
+    # maxit reached: NOT_CONVERGED reported, output still written
+    pk = w.packing_p100()
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, maxit=3, tol=1e-14))
+    v, info = s.solve(L.MOBILITY, w.forces_torques(100, 5))
+    assert not info["converged"] and info["iters"] == 3 and np.all(np.isfinite(v)) and np.abs(v).max() > 0
+
+
+def test_stokeslet_sum_standalone(L):
+    """Stand-alone FP32 direct tiles against FP64 direct summation."""
+    rng = np.random.default_rng(3)
+    nd, npd, nt = 40, 60, 500
+    centres = rng.uniform(-30, 30, (nd, 2))
+    th = 2 * np.pi * np.arange(npd) / npd
+    off = np.stack([0.54 * np.cos(th), 0.54 * np.sin(th)], -1)[None].repeat(nd, 0)
+    s = rng.standard_normal((nd, npd, 2)) / npd
+    targets = rng.uniform(-40, 40, (nt, 2))
+    d = np.min(np.hypot(targets[:, None, 0] - centres[None, :, 0], targets[:, None, 1] - centres[None, :, 1]), 1)
+    targets = targets[d > 3.0]
+    ref = (stokeslet(targets, (centres[:, None, :] + off).reshape(-1, 2)) @ s.reshape(-1)).reshape(-1, 2)
+    out = L.stokeslet_sum(dev(targets).reshape(-1, 2), dev(centres).reshape(-1, 2), dev(off).reshape(nd, npd, 2),
+                          dev(s).reshape(nd, npd, 2))
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref) < 1e-6
+    # a target inside the series range of a disk is rejected, not mis-summed
+    bad = np.array([[centres[0, 0] + 1.0, centres[0, 1]]])
+    with pytest.raises(L.LmfsError):
+        L.stokeslet_sum(dev(bad).reshape(-1, 2), dev(centres).reshape(-1, 2), dev(off).reshape(nd, npd, 2),
+                        dev(s).reshape(nd, npd, 2))
