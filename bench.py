@@ -289,13 +289,59 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_profile_case(case):
+    """Small, bounded cases for ncu captures (a few launches of one kernel)."""
+    import torch
+    from paper_2606_11273_gb300 import build as b
+    b.build()
+    import paper_2606_11273_gb300 as L
+    stream = torch.cuda.Stream()
+    if case in ("qr", "matvec"):
+        pk, ft = workload()
+        s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))
+        s.precompute(L.MOBILITY)
+        if case == "qr":
+            s.invalidate()
+            s.precompute(L.MOBILITY)
+        else:
+            n = pk.P * 72 * 2
+            mu = torch.randn(n, dtype=torch.float64, device="cuda")
+            u = torch.zeros_like(mu)
+            for _ in range(3):
+                s.matvec(L.MOBILITY, mu, u, L.MIXED)
+        torch.cuda.synchronize()
+    elif case == "stokeslet":
+        # 2000 source disks x 60 sources, 2000 x 72 targets (1.7e10 pairs)
+        n = 45
+        h = 4.4
+        g = (np.arange(n) + 0.5) * h
+        cx, cy = np.meshgrid(g, g)
+        centres = np.stack([cx.ravel(), cy.ravel()], -1)[:2000]
+        th = 2 * np.pi * np.arange(60) / 60
+        off = np.broadcast_to(np.stack([0.54 * np.cos(th), 0.54 * np.sin(th)], -1), (2000, 60, 2)).copy()
+        s = np.random.default_rng(0).standard_normal((2000, 60, 2)) / 60
+        ph = 2 * np.pi * np.arange(72) / 72
+        targets = ((centres + h / 2)[:, None, :] + 0.5 * np.stack([np.cos(ph), np.sin(ph)], -1)[None]).reshape(-1, 2)
+        d = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+        T, Cc, O, S = d(targets), d(centres), d(off), d(s)
+        for _ in range(2):
+            L.stokeslet_sum(T, Cc, O, S, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+    print(f"profile case {case} done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile-case", default=None, choices=["qr", "matvec", "stokeslet"],
+                    help="run one small bounded case for an ncu capture and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -118,6 +118,18 @@ int lmfs_precompute_pairs(lmfs_handle h, int problem);
 int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E);
 int lmfs_set_pair_blocks(lmfs_handle h, int problem, const double* A, const double* E);
 
+/* Replace the one-body pseudo-inverse of every radius class by truncated SVD
+ * factors, applied as in eq. (howG+): lam_bar = V diag(1/sigma) (U^T mu).
+ * Host arrays per class (classes numbered in order of first appearance of
+ * each distinct radius; lmfs_num_classes gives nclass): Ut [nclass][2Nc][2Mc]
+ * (row-major, rows >= rank ignored), sigma [nclass][2Nc], V [nclass][2Nc][2Nc]
+ * (row-major, columns >= rank ignored), rank [nclass] in 1..2Nc.  Used to
+ * exchange identical factors with another implementation; the library's own
+ * factors come from column-pivoted QR. */
+int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double* sigma, const double* V,
+                     const int* rank);
+int lmfs_num_classes(lmfs_handle h, int* nclass);
+
 /* The two-body system matrix applied to mu (Algorithm 3; mobility with the
  * projected strengths of Sec. 4.4).  mu_dev, u_dev: DEVICE pointers to
  * [P][Mc][2] doubles; stream-ordered on the handle's stream (returns before

@@ -89,6 +89,15 @@ class Solver:
         E = np.ascontiguousarray(E, dtype=np.float64)
         _lib.check(self.lib.lmfs_set_pair_blocks(self.h, problem, _ptr(A), _ptr(E)))
 
+    def set_onebody(self, problem, Ut, sigma, V, rank):
+        """Truncated-SVD one-body factors per radius class: Ut [nclass, 2Nc, 2Mc],
+        sigma [nclass, 2Nc], V [nclass, 2Nc, 2Nc], rank [nclass]."""
+        Ut = np.ascontiguousarray(Ut, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        rank = np.ascontiguousarray(rank, dtype=np.int32)
+        _lib.check(self.lib.lmfs_set_onebody(self.h, problem, _ptr(Ut), _ptr(sigma), _ptr(V), _ptr(rank)))
+
     def matvec(self, problem, mu_dev, u_dev, precision=MIXED):
         """mu_dev, u_dev: CUDA float64 tensors of P*Mc*2 elements (stream-ordered)."""
         _lib.check(self.lib.lmfs_matvec(self.h, problem, _ptr(mu_dev), _ptr(u_dev), precision))

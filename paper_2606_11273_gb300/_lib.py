@@ -72,6 +72,8 @@ SIGNATURES = {
     "lmfs_precompute_pairs": (_i, [_vp, _i]),
     "lmfs_get_pair_blocks": (_i, [_vp, _i, _vp, _vp]),
     "lmfs_set_pair_blocks": (_i, [_vp, _i, _vp, _vp]),
+    "lmfs_set_onebody": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "lmfs_num_classes": (_i, [_vp, _P(_i)]),
     "lmfs_matvec": (_i, [_vp, _i, _vp, _vp, _i]),
     "lmfs_rhs": (_i, [_vp, _i, _vp, _vp, _i]),
     "lmfs_solve": (_i, [_vp, _i, _vp, _vp, _P(lmfs_solve_info)]),

@@ -52,7 +52,7 @@ static void free_ctx(Ctx& c) {
   dfree(c.csr_ent); dfree(c.near_off); dfree(c.near_ent); dfree(c.far_excl_off); dfree(c.far_excl);
   dfree(c.tgt32); dfree(c.dsk32);
   for (auto& pb : c.prob) {
-    dfree(pb.A); dfree(pb.E); dfree(pb.ob.W); dfree(pb.ob.R); dfree(pb.ob.perm); dfree(pb.ob.rank);
+    dfree(pb.A); dfree(pb.E); dfree(pb.ob.W); dfree(pb.ob.R); dfree(pb.ob.perm); dfree(pb.ob.rank); dfree(pb.ob.V);
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
@@ -265,6 +265,41 @@ int lmfs_set_pair_blocks(lmfs_handle h, int problem, const double* A, const doub
   }
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
   pb.ready = true;
+  return LMFS_OK;
+}
+
+int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double* sigma, const double* V,
+                     const int* rank) {
+  if (!h || !Ut || !sigma || !V || !rank || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY))
+    return LMFS_ERR_INVALID;
+  Ctx& c = h->c;
+  PairBlocks& pb = c.prob[problem];
+  if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
+  const int ns = 2 * c.d.Nc, nn = 2 * c.d.Mc, nc = pb.ob.nclass;
+  if (!pb.ob.V) LMFS_TRY(dalloc(&pb.ob.V, (size_t)nc * ns * ns));
+  // W = U^T rows, R = diag(sigma) (the back substitution divides by sigma), V dense
+  std::vector<double> R((size_t)nc * ns * ns, 0.0);
+  std::vector<int> perm((size_t)nc * ns), rk(rank, rank + nc);
+  for (int q = 0; q < nc; ++q) {
+    if (rk[q] < 1 || rk[q] > ns) return LMFS_ERR_INVALID;
+    for (int j = 0; j < ns; ++j) {
+      R[(size_t)q * ns * ns + (size_t)j * ns + j] = j < rk[q] ? sigma[(size_t)q * ns + j] : 1.0;
+      perm[(size_t)q * ns + j] = j;
+    }
+  }
+  LMFS_CUDA(cudaMemcpyAsync(pb.ob.W, Ut, (size_t)nc * ns * nn * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(pb.ob.R, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(pb.ob.V, V, (size_t)nc * ns * ns * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(pb.ob.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(pb.ob.rank, rk.data(), rk.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  pb.ob.rank_h = rk;
+  return LMFS_OK;
+}
+
+int lmfs_num_classes(lmfs_handle h, int* nclass) {
+  if (!h || !nclass) return LMFS_ERR_INVALID;
+  *nclass = (int)h->c.cls_r_h.size();
   return LMFS_OK;
 }
 

@@ -44,6 +44,7 @@ struct OneBody {
   double* R = nullptr;     // [nclass][2Nc][2Nc] column-major
   int* perm = nullptr;     // [nclass][2Nc]
   int* rank = nullptr;     // [nclass]
+  double* V = nullptr;     // optional [nclass][2Nc][2Nc]: lam_bar = V z instead of the perm scatter
   std::vector<int> rank_h;
 };
 

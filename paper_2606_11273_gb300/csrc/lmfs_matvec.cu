@@ -34,8 +34,8 @@ __device__ __forceinline__ double wsum(double v) {
 // R[0:r,0:r] z = t (back substitution), lam_bar[perm[j]] = z_j.
 __global__ void onebody_apply_kernel(const double* __restrict__ W, const double* __restrict__ R,
                                      const int* __restrict__ perm, const int* __restrict__ rank,
-                                     const int* __restrict__ cls, int P, int Nc, int Mc,
-                                     const double* __restrict__ mu, double* __restrict__ lb) {
+                                     const double* __restrict__ V, const int* __restrict__ cls, int P,
+                                     int Nc, int Mc, const double* __restrict__ mu, double* __restrict__ lb) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= P) return;
   const int i = warp, c = cls[i];
@@ -73,6 +73,30 @@ __global__ void onebody_apply_kernel(const double* __restrict__ W, const double*
     }
   }
   double* out = lb + (long long)i * ns;
+  if (V) {
+    // imported factors of the form V Sigma^+ U^T: lam_bar = V z (z_j = t_j, j < r)
+    const double* Vc = V + (long long)c * ns * ns;
+    double acc[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) acc[q] = 0.0;
+    for (int j = 0; j < r; ++j) {
+      double zj = 0.0;
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) if (q == (j >> 5)) zj = t[q];
+      zj = __shfl_sync(0xffffffffu, zj, j & 31);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int row = lane + 32 * q;
+        if (row < ns) acc[q] += Vc[(long long)row * ns + j] * zj;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int row = lane + 32 * q;
+      if (row < ns) out[row] = acc[q];
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     const int row = lane + 32 * q;
@@ -240,8 +264,8 @@ __global__ void targets_as_disks(const double* __restrict__ t, int nt, float2* _
 //   (r^ r^T - X^ X^T) s = -[X (b + q a / R^2) + y (a - b)] / r^2,
 // a = X.s, b = y.s; 1/r^2 and 1/(r^2 + R^2) share one MUFU reciprocal.
 // Per-disk partials are accumulated with Kahan compensation.
-constexpr int F_THREADS = 128;
-constexpr int F_TILE = 16;        // source disks per staged tile
+constexpr int F_THREADS = 256;
+constexpr int F_TILE = 8;         // source disks per staged tile
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
@@ -302,8 +326,10 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int Nc = a.Nc;
   const uint32_t rec_bytes = (uint32_t)(F_TILE * Nc * 32);
-  float4* rbuf[2] = {(float4*)fsm, (float4*)(fsm + rec_bytes)};
-  float4* dbuf[2] = {(float4*)(fsm + 2 * rec_bytes), (float4*)(fsm + 2 * rec_bytes + F_TILE * 32)};
+  float4* const rbuf0 = (float4*)fsm;
+  float4* const rbuf1 = (float4*)(fsm + rec_bytes);
+  float4* const dbuf0 = (float4*)(fsm + 2 * rec_bytes);
+  float4* const dbuf1 = (float4*)(fsm + 2 * rec_bytes + F_TILE * 32);
   uint64_t* bars = (uint64_t*)(fsm + 2 * rec_bytes + 2 * F_TILE * 32);
   __shared__ int s_fail;
 
@@ -314,12 +340,18 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
   const int k_begin = blockIdx.y * a.kchunk;
   const int k_end = min(a.nsd, k_begin + a.kchunk);
 
+  // per target: offset from its disk centre and that centre (double-float);
+  // targets of one thread share a disk unless every target is its own disk
   float2 xo[F_TPT];
-  float chx = 0, chy = 0, clx = 0, cly = 0;
-  if (active) {
-    for (int q = 0; q < F_TPT; ++q) xo[q] = a.tgt[t0 + q];
-    const float4 dh = a.tdsk[2 * ti];
-    chx = dh.x; chy = dh.y; clx = dh.z; cly = dh.w;
+  float chx[F_TPT], chy[F_TPT], clx[F_TPT], cly[F_TPT];
+#pragma unroll
+  for (int q = 0; q < F_TPT; ++q) {
+    xo[q] = make_float2(0.f, 0.f); chx[q] = chy[q] = clx[q] = cly[q] = 0.f;
+    if (active && t0 + q < nt) {
+      xo[q] = a.tgt[t0 + q];
+      const float4 dh = a.tdsk[2 * ((t0 + q) / a.Mt)];
+      chx[q] = dh.x; chy[q] = dh.y; clx[q] = dh.z; cly[q] = dh.w;
+    }
   }
   // exclusion pointer: first excluded disk >= k_begin
   int ep = 0, ee = 0;
@@ -347,8 +379,8 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
     const int buf = tile & 1;
     const uint32_t rb = (uint32_t)(nd * Nc * 32), db = (uint32_t)(nd * 32);
     mbar_expect_tx(&bars[buf], rb + db);
-    bulk_g2s(rbuf[buf], a.rec + 2LL * kb * Nc, rb, &bars[buf]);
-    bulk_g2s(dbuf[buf], a.dsk + 2LL * kb, db, &bars[buf]);
+    bulk_g2s(buf ? rbuf1 : rbuf0, a.rec + 2LL * kb * Nc, rb, &bars[buf]);
+    bulk_g2s(buf ? dbuf1 : dbuf0, a.dsk + 2LL * kb, db, &bars[buf]);
   };
   if (threadIdx.x == 0 && ntile > 0) issue(0);
 
@@ -360,8 +392,8 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
     if (s_fail) break;
     const int kb = k_begin + tile * F_TILE;
     const int nd = min(F_TILE, k_end - kb);
-    const float4* R = rbuf[buf];
-    const float4* Dk = dbuf[buf];
+    const float4* R = buf ? rbuf1 : rbuf0;
+    const float4* Dk = buf ? dbuf1 : dbuf0;
     if (active) {
       for (int dd = 0; dd < nd; ++dd) {
         const int k = kb + dd;
@@ -373,14 +405,12 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
         const float4 dh = Dk[2 * dd];
         const float4 ds = Dk[2 * dd + 1];   // (sum s_x, sum s_y, r, rho^2)
         // X = x - c_k = (c_i - c_k) + x_off, centre difference in double-float
-        const float dxh = chx - dh.x, dyh = chy - dh.y;
-        const float dxl = clx - dh.z, dyl = cly - dh.w;
         float Xx[F_TPT], Xy[F_TPT], R2[F_TPT], m2x[F_TPT], m2y[F_TPT], twoR2[F_TPT], iR2[F_TPT];
         float px[F_TPT], py[F_TPT];
 #pragma unroll
         for (int q = 0; q < F_TPT; ++q) {
-          Xx[q] = dxh + (dxl + xo[q].x);
-          Xy[q] = dyh + (dyl + xo[q].y);
+          Xx[q] = (chx[q] - dh.x) + ((clx[q] - dh.z) + xo[q].x);
+          Xy[q] = (chy[q] - dh.y) + ((cly[q] - dh.w) + xo[q].y);
           R2[q] = fmaf(Xx[q], Xx[q], Xy[q] * Xy[q]);
           twoR2[q] = R2[q] + R2[q];
           iR2[q] = rcp_approx(R2[q]);
@@ -450,6 +480,7 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
     double* o = a.out + blockIdx.y * a.out_stride;
 #pragma unroll
     for (int q = 0; q < F_TPT; ++q) {
+      if (t0 + q >= nt) break;
       o[2 * (t0 + q)] = ((double)sx[q] - (double)cx_[q]) * a.cmu;
       o[2 * (t0 + q) + 1] = ((double)sy[q] - (double)cy_[q]) * a.cmu;
     }
@@ -903,7 +934,7 @@ int far_field_prepare(Ctx& c) {
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
   if (2 * c.d.Nc > 256) { set_last_error("2 Nc > 256 not supported"); return LMFS_ERR_INVALID; }
   const int thr = 128, blocks = (c.d.P * 32 + thr - 1) / thr;
-  onebody_apply_kernel<<<blocks, thr, 0, c.stream>>>(ob.W, ob.R, ob.perm, ob.rank, c.cls, c.d.P, c.d.Nc, c.d.Mc, mu, lb);
+  onebody_apply_kernel<<<blocks, thr, 0, c.stream>>>(ob.W, ob.R, ob.perm, ob.rank, ob.V, c.cls, c.d.P, c.d.Nc, c.d.Mc, mu, lb);
   return check_launch("onebody_apply");
 }
 
@@ -1027,7 +1058,7 @@ int stokeslet_sum_standalone(const double* targets, int nt, const double* centre
   int dev_sms = 152, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long bx = ((long long)nt + F_THREADS - 1) / F_THREADS;
+  const long long bx = ((long long)(nt + 1) / 2 + F_THREADS - 1) / F_THREADS;
   long long split = std::max<long long>(1, (8LL * dev_sms + bx - 1) / bx);
   int kchunk = (int)((nd + split - 1) / split);
   kchunk = ((kchunk + F_TILE - 1) / F_TILE) * F_TILE;
@@ -1054,10 +1085,10 @@ int stokeslet_sum_standalone(const double* targets, int nt, const double* centre
     a.out = split > 1 ? part : out; a.out_stride = 2LL * nt; a.with_base = 1; a.err = err; a.range_err = err + 1;
     const size_t shm = 2 * (size_t)F_TILE * npd * 32 + 2 * F_TILE * 32 + 16;
     if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); rc = LMFS_ERR_INVALID; }
-    else if (cuda_failed(cudaFuncSetAttribute(far32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr")) rc = LMFS_ERR_CUDA;
+    else if (cuda_failed(cudaFuncSetAttribute(far32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr")) rc = LMFS_ERR_CUDA;
     else {
       dim3 grid((unsigned)bx, (unsigned)split);
-      far32_kernel<1><<<grid, F_THREADS, shm, st>>>(a);
+      far32_kernel<2><<<grid, F_THREADS, shm, st>>>(a);
       rc = check_launch("far32 standalone");
       if (rc == LMFS_OK && split > 1) {
         reduce_splits<<<(int)std::min<long long>((2LL * nt + 255) / 256, 4096), 256, 0, st>>>(part, 2LL * nt, (int)split, 2LL * nt, out);

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "lmfs_internal.h"
 
 namespace lmfs {
@@ -69,17 +71,27 @@ __device__ void block_argmax(double val, int idx, double* redv, int* redi, doubl
 struct Args {
   double* A; long long mstride; const int* m; const int* n; int k; int ld; double eps;
   double* X; int xld; long long xstride; int* rank; int* perm; int permstride;
-  double* tau; double* vn; int* info; int solve;
+  double* tau; double* vn; int* info; int solve; int cs;
 };
 
+// One matrix per thread-block cluster of a.cs CTAs (a.cs = 1: a plain block).
+// Columns j are owned by warp (j mod (cs * QR_WARPS)) of the cluster; CTA 0
+// chooses the pivot, swaps columns and forms the Householder vector, then
+// every CTA applies it to its own columns.  Matrix data moves between CTAs
+// through global memory, so it is read with L2-only loads (__ldcg).
 __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double smem[];
-  const int b = blockIdx.x;
+  const int crank = (int)cluster.block_rank();
+  const int cs = q.cs;
+  const int b = blockIdx.x / cs;
   const int m = q.m[b], n = q.n[b], k = q.k, ld = q.ld;
   double* A = q.A + (long long)b * q.mstride;
   int* perm = q.perm + (long long)b * q.permstride;
   double* vn1 = q.vn + (long long)b * 2 * q.permstride;
   double* vn2 = vn1 + q.permstride;
+  double* tau_g = q.tau + (long long)b * q.permstride;
   double* sv = smem;                       // Householder vector, m entries
   double* red = smem + ld;                 // QR_WARPS
   int* redi = (int*)(red + QR_WARPS);      // QR_WARPS
@@ -88,100 +100,115 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
   __shared__ double s_beta, s_tau, s_r00, s_amb;
   __shared__ int s_stop, s_bad;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gw = crank * QR_WARPS + wid;          // warp id within the cluster
+  const int nw = cs * QR_WARPS;                   // warps in the cluster
   const double tol3z = sqrt(2.220446049250313e-16);
   const int ncol = n + k;
 
-  // initial column norms and identity permutation
-  for (int j = wid; j < n; j += QR_WARPS) {
+  // initial column norms and identity permutation (owner warps)
+  for (int j = gw; j < n; j += nw) {
     const double* col = A + (long long)j * ld;
     double s = 0.0;
-    for (int i = lane; i < m; i += 32) { double a = col[i]; s += a * a; }
+    for (int i = lane; i < m; i += 32) { double a = __ldcg(col + i); s += a * a; }
     s = warp_sum(s);
     if (lane == 0) { vn1[j] = sqrt(s); vn2[j] = sqrt(s); perm[j] = j; }
   }
   if (threadIdx.x == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; }
-  __syncthreads();
+  cluster.sync();
 
   const int smax = min(m, n);
   int rank = smax;
   for (int s = 0; s < smax; ++s) {
-    // 1. pivot: largest remaining partial column norm
-    double bv = -1.0; int bi = 0x7fffffff;
-    for (int j = s + threadIdx.x; j < n; j += QR_THREADS) {
-      double v = vn1[j];
-      if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
-    }
-    block_argmax(bv, bi, red, redi, &s_piv, &s_pidx);
-    const int p = s_pidx;
-    // 2. swap columns s and p
-    if (p != s) {
+    if (crank == 0) {
+      // 1. pivot: largest remaining partial column norm
+      double bv = -1.0; int bi = 0x7fffffff;
+      for (int j = s + threadIdx.x; j < n; j += QR_THREADS) {
+        double v = __ldcg(vn1 + j);
+        if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+      }
+      block_argmax(bv, bi, red, redi, &s_piv, &s_pidx);
+      const int p = s_pidx;
+      // 2. swap columns s and p
+      if (p != s) {
+        double* cs_ = A + (long long)s * ld;
+        double* cp_ = A + (long long)p * ld;
+        for (int i = threadIdx.x; i < m; i += QR_THREADS) {
+          double t = __ldcg(cs_ + i); cs_[i] = __ldcg(cp_ + i); cp_[i] = t;
+        }
+        if (threadIdx.x == 0) {
+          double t = __ldcg(vn1 + s); vn1[s] = __ldcg(vn1 + p); vn1[p] = t;
+          t = __ldcg(vn2 + s); vn2[s] = __ldcg(vn2 + p); vn2[p] = t;
+          int ti = __ldcg(perm + s); perm[s] = __ldcg(perm + p); perm[p] = ti;
+        }
+      }
+      __syncthreads();
+      // 3. Householder vector of A[s:m, s]
       double* cs_ = A + (long long)s * ld;
-      double* cp_ = A + (long long)p * ld;
-      for (int i = threadIdx.x; i < m; i += QR_THREADS) {
-        double t = cs_[i]; cs_[i] = cp_[i]; cp_[i] = t;
-      }
+      double part = 0.0;
+      for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) { double a = __ldcg(cs_ + i); part += a * a; }
+      const double sig2 = block_sum(part, red);
       if (threadIdx.x == 0) {
-        double t = vn1[s]; vn1[s] = vn1[p]; vn1[p] = t;
-        t = vn2[s]; vn2[s] = vn2[p]; vn2[p] = t;
-        int ti = perm[s]; perm[s] = perm[p]; perm[p] = ti;
+        const double alpha = __ldcg(cs_ + s);
+        const double nrm = sqrt(alpha * alpha + sig2);
+        if (s == 0) s_r00 = nrm;
+        if (!(nrm == nrm) || isinf(nrm)) s_bad = 1;
+        if (nrm <= q.eps * s_r00 || nrm == 0.0 || s_bad) {
+          s_stop = 1;
+        } else {
+          const double beta = (alpha >= 0.0) ? -nrm : nrm;
+          s_beta = beta;
+          s_tau = (beta - alpha) / beta;
+          s_amb = alpha - beta;          // alpha and -beta share a sign: no cancellation
+          cs_[s] = beta;
+          tau_g[s] = s_tau;
+        }
+      }
+      __syncthreads();
+      if (!s_stop) {
+        const double scale = 1.0 / s_amb;
+        for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) cs_[i] = __ldcg(cs_ + i) * scale;
       }
     }
-    __syncthreads();
-    // 3. Householder vector of A[s:m, s]
-    double* cs_ = A + (long long)s * ld;
-    double part = 0.0;
-    for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) { double a = cs_[i]; part += a * a; }
-    const double sig2 = block_sum(part, red);
-    if (threadIdx.x == 0) {
-      const double alpha = cs_[s];
-      const double nrm = sqrt(alpha * alpha + sig2);
-      if (s == 0) s_r00 = nrm;
-      if (!(nrm == nrm) || isinf(nrm)) s_bad = 1;
-      if (nrm <= q.eps * s_r00 || nrm == 0.0 || s_bad) {
-        s_stop = 1;
-      } else {
-        const double beta = (alpha >= 0.0) ? -nrm : nrm;
-        s_beta = beta;
-        s_tau = (beta - alpha) / beta;
-        s_amb = alpha - beta;          // alpha and -beta share a sign: no cancellation
-        cs_[s] = beta;
-      }
-    }
-    __syncthreads();
-    if (s_stop) { rank = s; break; }
+    cluster.sync();
+    // every CTA: read the decision and tau from CTA 0, stage v in shared memory
+    int stop;
+    double tau;
     {
-      const double scale = 1.0 / s_amb;
-      for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) {
-        double v = cs_[i] * scale;
-        cs_[i] = v;
-        sv[i] = v;
-      }
-      if (threadIdx.x == 0) { sv[s] = 1.0; q.tau[(long long)b * q.permstride + s] = s_tau; }
+      int* stop0 = cluster.map_shared_rank(&s_stop, 0);
+      double* tau0 = cluster.map_shared_rank(&s_tau, 0);
+      stop = *stop0;
+      tau = *tau0;
+    }
+    if (stop) { rank = s; break; }
+    {
+      const double* cs_ = A + (long long)s * ld;
+      for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) sv[i] = __ldcg(cs_ + i);
+      if (threadIdx.x == 0) sv[s] = 1.0;
     }
     __syncthreads();
-    // 4. apply H = I - tau v v^T to the trailing columns (coefficients and RHS)
-    const double tau = s_tau;
-    for (int j = s + 1 + wid; j < ncol; j += QR_WARPS) {
+    // 4. apply H = I - tau v v^T to this CTA's trailing columns
+    for (int j = s + 1 + ((gw - (s + 1)) % nw + nw) % nw; j < ncol; j += nw) {
       double* cj = A + (long long)j * ld;
       double w = 0.0;
-      for (int i = s + lane; i < m; i += 32) w += sv[i] * cj[i];
+      for (int i = s + lane; i < m; i += 32) w += sv[i] * __ldcg(cj + i);
       w = warp_sum(w) * tau;
-      for (int i = s + lane; i < m; i += 32) cj[i] -= w * sv[i];
+      for (int i = s + lane; i < m; i += 32) cj[i] = __ldcg(cj + i) - w * sv[i];
       if (j < n) {
         __syncwarp();
         // 5. downdate the partial column norm (LAPACK dlaqp2 rule)
-        double nv = vn1[j];
+        double nv = __ldcg(vn1 + j);
         bool recompute = false;
         if (nv != 0.0) {
-          double t = fabs(cj[s]) / nv;
+          double t = fabs(__ldcg(cj + s)) / nv;
           t = fmax(0.0, (1.0 + t) * (1.0 - t));
-          double t2 = t * (nv / vn2[j]) * (nv / vn2[j]);
+          const double v2 = __ldcg(vn2 + j);
+          double t2 = t * (nv / v2) * (nv / v2);
           if (t2 <= tol3z) recompute = true;
           else nv = nv * sqrt(t);
         }
         if (recompute) {
           double ss = 0.0;
-          for (int i = s + 1 + lane; i < m; i += 32) { double a = cj[i]; ss += a * a; }
+          for (int i = s + 1 + lane; i < m; i += 32) { double a = __ldcg(cj + i); ss += a * a; }
           ss = warp_sum(ss);
           nv = sqrt(ss);
           if (lane == 0) { vn1[j] = nv; vn2[j] = nv; }
@@ -190,37 +217,38 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
         }
       }
     }
-    __syncthreads();
+    cluster.sync();
   }
-  if (threadIdx.x == 0) {
+  // every CTA leaves the loop at the same s (the stop flag comes from CTA 0)
+  if (crank == 0 && threadIdx.x == 0) {
     q.rank[b] = rank;
     q.info[b] = s_bad;
   }
-  __syncthreads();
+  cluster.sync();
   if (!q.solve) return;
 
   // 6. back substitution R[0:r,0:r] x = (Q^T B)[0:r], one warp per RHS column,
   //    column-oriented (coalesced reads of R's columns); x overwrites B.
   double* X = q.X + (long long)b * q.xstride;
-  for (int c = wid; c < k; c += QR_WARPS) {
+  int bad = 0;
+  for (int c = gw; c < k; c += nw) {
     double* bc = A + (long long)(n + c) * ld;
     for (int j = rank - 1; j >= 0; --j) {
       const double* rj = A + (long long)j * ld;
-      const double xj = bc[j] / rj[j];
+      const double xj = __ldcg(bc + j) / __ldcg(rj + j);
       __syncwarp();
-      for (int i = lane; i < j; i += 32) bc[i] -= xj * rj[i];
+      for (int i = lane; i < j; i += 32) bc[i] = __ldcg(bc + i) - xj * __ldcg(rj + i);
       if (lane == 0) bc[j] = xj;
       __syncwarp();
     }
     double* xc = X + (long long)c * q.xld;
     for (int j = lane; j < n; j += 32) {
-      double v = (j < rank) ? bc[j] : 0.0;
-      if (!(v == v) || isinf(v)) atomicExch(&s_bad, 1);
-      xc[perm[j]] = v;
+      double v = (j < rank) ? __ldcg(bc + j) : 0.0;
+      if (!(v == v) || isinf(v)) bad = 1;
+      xc[__ldcg(perm + j)] = v;
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && s_bad) q.info[b] = 1;
+  if (bad) atomicExch(q.info + b, 1);
 }
 
 }  // namespace
@@ -237,7 +265,28 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
                                          (int)shm), "qr smem attribute"))
       return LMFS_ERR_CUDA;
   }
-  qrcp_kernel<<<q.nb, QR_THREADS, shm, st>>>(a);
+  // cluster size: spread few matrices over the SMs so that every SM holds up
+  // to two CTAs (the register limit of this kernel), up to the portable
+  // cluster limit of 8
+  int sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int cs = 1;
+  while (cs < 8 && q.nb * cs * 2 <= 2 * sms) cs *= 2;
+  a.cs = cs;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(q.nb * cs);
+  cfg.blockDim = dim3(QR_THREADS);
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cuda_failed(cudaLaunchKernelEx(&cfg, qrcp_kernel, a), "qrcp launch")) return LMFS_ERR_CUDA;
   return check_launch("qrcp_kernel");
 }
 

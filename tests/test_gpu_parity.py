@@ -46,6 +46,19 @@ def dev(x):
     return torch.tensor(np.ascontiguousarray(x).ravel(), dtype=torch.float64, device="cuda")
 
 
+def onebody_factors(ob, Nc):
+    """The oracle's truncated SVD of a one-body block as (U^T, sigma, V, rank)."""
+    ns = 2 * Nc
+    r = ob.pinv.rank
+    Ut = np.zeros((1, ns, ob.pinv.Ut.shape[1]))
+    Ut[0, :r] = ob.pinv.Ut
+    sig = np.ones((1, ns))
+    sig[0, :r] = ob.pinv.s[:r]
+    V = np.zeros((1, ns, ns))
+    V[0, :, :r] = ob.pinv.VSi * ob.pinv.s[:r]
+    return Ut, sig, V, np.array([r])
+
+
 def gpu_matvec(L, s, problem, mu, prec):
     md = dev(mu)
     ud = torch.zeros_like(md)
@@ -147,12 +160,13 @@ def test_p100_contacts_match(L, p100):
 
 
 def test_p100_matvec_exchanged_blocks(L, p100):
-    """Identical (oracle) pair blocks in both: FP64 within the oracle's
-    literal-form rounding bound, mixed within 1e-6, on the right-hand side and
-    the first Krylov vectors of the solve."""
+    """Identical (oracle) pair blocks and one-body factor in both: FP64 within
+    the oracle's literal-form rounding bound, mixed within 1e-6, on the
+    right-hand side and the first Krylov vectors of the solve."""
     pk, so, ft, vs = p100
     s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
     s.set_pair_blocks(L.MOBILITY, np.stack([b["A"] for b in so.blocks]), np.stack([b["E"] for b in so.blocks]))
+    s.set_onebody(L.MOBILITY, *onebody_factors(so.ob[0], PACKING.Nc))
     for j, v in enumerate(vs[:8]):
         uo = so.matvec(v)
         tol64 = fp64_tolerance(so, v)
@@ -165,19 +179,19 @@ def test_p100_matvec_exchanged_blocks(L, p100):
 
 @pytest.mark.parametrize("problem", ["mobility", "resistance"])
 def test_p100_matvec_fp64_where_oracle_is_exact(L, p100, problem):
-    """With zero pair blocks injected in both (no large cancelling correction
-    strengths), the oracle's literal form is accurate to rounding, and the FP64
-    path must match it to 1e-12; the mixed path to 1e-6.  Covers the one-body
-    factors, the near/far split, the close-partner exclusion, the multipole far
-    field and the identity step at full P = 100 size."""
+    """Identical one-body pseudo-inverse and zero pair blocks in both (no large
+    cancelling correction strengths): the oracle's literal form is then
+    accurate to rounding, and the FP64 path must match it to 1e-12, the mixed
+    path to 1e-6.  Covers the near/far split, the close-partner exclusion, the
+    multipole far field and the identity step at full P = 100 size."""
     pk, _, ft, _ = p100
     so0 = System(pk.centres, pk.radii, PACKING, problem,
                  blocks=[{"A": np.zeros((240, 240)), "E": np.zeros((6, 240))}] * 37)
     assert len(so0.pairs) == 37
     s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
-    s.set_pair_blocks(L.MOBILITY if problem == "mobility" else L.RESISTANCE, np.zeros((37, 240, 240)),
-                      np.zeros((37, 6, 240)))
     code = L.MOBILITY if problem == "mobility" else L.RESISTANCE
+    s.set_pair_blocks(code, np.zeros((37, 240, 240)), np.zeros((37, 6, 240)))
+    s.set_onebody(code, *onebody_factors(so0.ob[0], PACKING.Nc))     # identical one-body factors
     for seed in (1, 2):
         mu = w.smooth_surface_vector(100, 72, seed).reshape(100, -1)
         uo = so0.matvec(mu)

@@ -1,0 +1,84 @@
+"""Request server: continuous admission by memory budget, overlapping
+requests, bounded polls, and results that do not depend on what else runs."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2606_11273_gb300 import build
+    build.build()
+    import paper_2606_11273_gb300 as lib
+    return lib
+
+
+def requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n):
+        P = int(rng.integers(6, 40))
+        phi = float(rng.uniform(0.3, 0.5))
+        gmin = float(10 ** rng.uniform(-3, -1.5))
+        pk = w.packing(P, phi, 100 + q, gmin=gmin, start="square", nsweep=4, snap_gap=gmin)
+        problem = int(q % 2)
+        data = w.rigid_velocities(P, q) if problem == 0 else w.forces_torques(P, q)
+        out.append((pk, problem, data))
+    return out
+
+
+def params(L):
+    return L.Params(Nfp=100, Nell=40, Mp=120, tol=1e-9)
+
+
+def test_served_results_equal_alone(L):
+    """Each request's result in the mix is identical to the same solve run
+    alone (bitwise: no cross-request reductions, fixed reduction orders)."""
+    reqs = requests(8)
+    alone = []
+    for pk, problem, data in reqs:
+        s = L.Solver(pk.centres, pk.radii, params(L))
+        out, info = s.solve(problem, data)
+        assert info["converged"]
+        alone.append(out)
+        s.close()
+    srv = L.Server(hbm_budget_bytes=20 << 30, max_slots=4)
+    tickets = []
+    for (pk, problem, data) in reqs:
+        tickets.append(srv.submit(pk.centres, pk.radii, problem, data, params(L)))
+    for (t, P), ref in zip(tickets, alone):
+        rc, out, info = srv.poll(t, P, timeout_us=120_000_000)
+        assert rc == 0, L._lib.strerror(rc)
+        assert np.array_equal(out, ref)
+    srv.close()
+
+
+def test_admission_and_polling(L):
+    pk, problem, data = requests(1, seed=5)[0]
+    srv = L.Server(hbm_budget_bytes=1 << 20, max_slots=2)      # 1 MiB: nothing fits
+    with pytest.raises(L.LmfsError) as e:
+        srv.submit(pk.centres, pk.radii, problem, data, params(L))
+    assert e.value.code == L._lib.LMFS_ERR_TOO_LARGE
+    srv.close()
+    srv = L.Server(hbm_budget_bytes=8 << 30, max_slots=1)
+    big = w.packing_p100()
+    t0, P0 = srv.submit(big.centres, big.radii, L.MOBILITY, w.forces_torques(100, 1), params(L))
+    t1, P1 = srv.submit(pk.centres, pk.radii, problem, data, params(L))
+    # one slot: the second request waits; a zero-timeout poll returns at once
+    rc, _, _ = srv.poll(t1, P1, timeout_us=0)
+    assert rc in (L._lib.LMFS_PENDING, 0)
+    rc, _, _ = srv.poll(t0, P0, timeout_us=1)
+    assert rc in (L._lib.LMFS_ERR_TIMEOUT, 0)
+    for t, P in ((t0, P0), (t1, P1)):
+        rc, out, _ = srv.poll(t, P, timeout_us=300_000_000)
+        assert rc == 0 and np.all(np.isfinite(out))
+    assert srv.lib.lmfs_poll(srv.s, 999999, None, None, 0) == L._lib.LMFS_ERR_INVALID   # unknown ticket
+    srv.close()
