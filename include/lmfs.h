@@ -181,6 +181,27 @@ int lmfs_stokeslet_sum(const double* targets, int nt, const double* centres,
  * (eager launches plus the kernel nodes of every replayed graph). */
 int lmfs_launch_count(uint64_t* out);
 
+/* lmfs_stokeslet_sum without any device allocation, for callers that cannot
+ * let a library allocate during a call: applications that give the whole
+ * device budget to their own pool or arena, plugin hosts that require every
+ * allocation to go through their allocator, and latency-critical loops that
+ * cannot take an allocation's implicit synchronisation.  The paper has no
+ * counterpart: it is a packaging of the same FP32 direct tile sum.
+ *   Arguments as lmfs_stokeslet_sum (FP32 direct tiles; DEVICE pointers; out
+ *   is overwritten), with one source range per launch.
+ *   Scratch: a fixed 32 MiB array per device, reserved when the library's
+ *   module is loaded and held until the process exits.  A problem needs about
+ *   44 bytes per target + 32 bytes per source + 32 bytes per disk (each part
+ *   rounded up to 256 bytes); larger problems get LMFS_ERR_INVALID.
+ *   The first call on a device (with that device current) looks up the
+ *   array's device address; make that first call before any stream capture.
+ *   Every call reuses the same array and it keeps the last call's contents:
+ *   calls that overlap on the GPU race on it, so serialise them.
+ *   Synchronizes `stream` before returning (it reads the error flags). */
+int lmfs_stokeslet_sum_noalloc(const double* targets, int nt, const double* centres,
+                               const double* offsets, const double* strengths, int nd,
+                               int n_per_disk, double mu, void* stream, double* out);
+
 const char* lmfs_strerror(int code);
 
 /* ---- serving (continuous batching) ----------------------------------- */

@@ -82,6 +82,7 @@ SIGNATURES = {
     "lmfs_invalidate": (_i, [_vp]),
     "lmfs_stats": (_i, [_vp, _i, _vp]),
     "lmfs_stokeslet_sum": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _d, _i, _vp, _vp]),
+    "lmfs_stokeslet_sum_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _d, _vp, _vp]),
     "lmfs_strerror": (ctypes.c_char_p, [_i]),
     "lmfs_launch_count": (_i, [_P(ctypes.c_uint64)]),
     "lmfs_server_create": (_i, [_P(lmfs_server_params), _P(_vp)]),

@@ -387,6 +387,13 @@ int lmfs_launch_count(uint64_t* out) {
   return LMFS_OK;
 }
 
+int lmfs_stokeslet_sum_noalloc(const double* targets, int nt, const double* centres, const double* offsets,
+                               const double* strengths, int nd, int n_per_disk, double mu, void* stream,
+                               double* out) {
+  return stokeslet_sum_noalloc(targets, nt, centres, offsets, strengths, nd, n_per_disk, mu,
+                               (cudaStream_t)stream, out);
+}
+
 const char* lmfs_strerror(int code) {
   static thread_local std::string s;
   const char* base = "unknown error";

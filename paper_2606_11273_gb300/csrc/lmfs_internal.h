@@ -188,6 +188,8 @@ int near_field(Ctx& c, int mode, const double* strength, const double* mu, const
 int stokeslet_sum_standalone(const double* targets, int nt, const double* centres,
                              const double* offsets, const double* strengths, int nd, int npd,
                              double mu, int precision, cudaStream_t s, double* out);
+int stokeslet_sum_noalloc(const double* targets, int nt, const double* centres, const double* offsets,
+                          const double* strengths, int nd, int npd, double mu, cudaStream_t s, double* out);
 
 // ---- GMRES (lmfs_gmres.cu) ------------------------------------------------
 int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x,

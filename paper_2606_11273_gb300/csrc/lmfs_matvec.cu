@@ -16,6 +16,7 @@
 // neighbours) is summed in FP64 by the near kernel.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "lmfs_internal.h"
 
@@ -1107,6 +1108,95 @@ int stokeslet_sum_standalone(const double* targets, int nt, const double* centre
     rc = LMFS_ERR_INVALID;
   }
   return rc;
+}
+
+// ---- stand-alone sum without device allocation ------------------------------
+// Some callers cannot have a library allocate device memory during a call:
+// applications that hand the whole device budget to their own pool or arena,
+// plugin hosts that require every allocation to go through their allocator,
+// and latency-critical loops that cannot take the implicit synchronisation an
+// allocation may cause.  lmfs_stokeslet_sum_noalloc serves them: its scratch
+// lives in the fixed array below, reserved once per device when this module is
+// loaded and held until the process exits.  Every call reuses the same array,
+// so calls that overlap on the GPU (from different streams or threads) race on
+// it and must be serialised by the caller.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;   // 32 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[64] = {};   // device address of the array, per device ordinal
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+}  // namespace
+
+int stokeslet_sum_noalloc(const double* targets, int nt, const double* centres, const double* offsets,
+                          const double* strengths, int nd, int npd, double mu, cudaStream_t st, double* out) {
+  if (nt < 1 || nd < 1 || npd < 1 || !(mu > 0) || !targets || !centres || !offsets || !strengths || !out) {
+    set_last_error("lmfs_stokeslet_sum_noalloc: bad sizes or null pointers");
+    return LMFS_ERR_INVALID;
+  }
+  // scratch layout: target offsets, target centres, disk data, source records,
+  // exclusion offsets (all zero: nothing excluded), two error flags
+  const size_t b_tgt = align256((size_t)nt * sizeof(float2));
+  const size_t b_tdsk = align256(2 * (size_t)nt * sizeof(float4));
+  const size_t b_dsk = align256(2 * (size_t)nd * sizeof(float4));
+  const size_t b_rec = align256(2 * (size_t)nd * npd * sizeof(float4));
+  const size_t b_off = align256(((size_t)nt + 1) * sizeof(int));
+  const size_t b_err = align256(2 * sizeof(int));
+  const size_t need = b_tgt + b_tdsk + b_dsk + b_rec + b_off + b_err;
+  if (need > NOALLOC_SCRATCH_BYTES) {
+    set_last_error("lmfs_stokeslet_sum_noalloc: problem needs " + std::to_string(need) +
+                   " bytes of scratch, more than the fixed 33554432; use lmfs_stokeslet_sum");
+    return LMFS_ERR_INVALID;
+  }
+  const size_t shm = 2 * (size_t)F_TILE * npd * 32 + 2 * F_TILE * 32 + 16;
+  if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum_noalloc: too many sources per disk"); return LMFS_ERR_INVALID; }
+  int dev = 0;
+  LMFS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) { set_last_error("lmfs_stokeslet_sum_noalloc: device ordinal >= 64"); return LMFS_ERR_INVALID; }
+  unsigned char* base = nullptr;
+  {
+    // set-up on the first call on this device (with the device current): the
+    // host-side name of the array is not a device address, so look it up once
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      if (cuda_failed(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(no-alloc scratch)"))
+        return LMFS_ERR_CUDA;
+      g_noalloc_base[dev] = p;
+    }
+    base = (unsigned char*)g_noalloc_base[dev];
+  }
+  float2* tgt = (float2*)base;
+  float4* tdsk = (float4*)(base + b_tgt);
+  float4* dsk = (float4*)(base + b_tgt + b_tdsk);
+  float4* rec = (float4*)(base + b_tgt + b_tdsk + b_dsk);
+  int* excl_off = (int*)(base + b_tgt + b_tdsk + b_dsk + b_rec);
+  int* err = (int*)(base + b_tgt + b_tdsk + b_dsk + b_rec + b_off);
+  // the array keeps the previous call's contents: clear the error flags
+  LMFS_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), st));
+  targets_as_disks<<<(nt + 1 + 255) / 256, 256, 0, st>>>(targets, nt, tgt, tdsk, excl_off);
+  LMFS_TRY(check_launch("targets_as_disks"));
+  records_general<<<(nd * 32 + 127) / 128, 128, 0, st>>>(centres, offsets, strengths, nd, npd, rec, dsk);
+  LMFS_TRY(check_launch("records_general"));
+  FarArgs a;
+  a.tgt = tgt; a.tdsk = tdsk; a.dsk = dsk; a.rec = rec; a.excl_off = excl_off; a.excl = excl_off;
+  a.ntd = nt; a.Mt = 1; a.nsd = nd; a.Nc = npd; a.kchunk = nd; a.cmu = INV4PI / mu;
+  a.out = out; a.out_stride = 2LL * nt; a.with_base = 1; a.err = err; a.range_err = err + 1;
+  LMFS_CUDA(cudaFuncSetAttribute(far32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  const unsigned bx = (unsigned)(((long long)(nt + 1) / 2 + F_THREADS - 1) / F_THREADS);
+  far32_kernel<2><<<dim3(bx, 1), F_THREADS, shm, st>>>(a);   // one source range: no partial buffers
+  LMFS_TRY(check_launch("far32 no-alloc"));
+  int herr[2] = {0, 0};
+  LMFS_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+  LMFS_CUDA(cudaStreamSynchronize(st));
+  if (herr[0]) { set_last_error("far32: bounded wait expired"); return LMFS_ERR_CUDA; }
+  if (herr[1]) {
+    set_last_error("lmfs_stokeslet_sum_noalloc: a target lies within 4 x the source ring radius of a source disk centre");
+    return LMFS_ERR_INVALID;
+  }
+  return LMFS_OK;
 }
 
 }  // namespace lmfs
