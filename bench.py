@@ -95,11 +95,32 @@ def dist_env():
     return ws, rank, local
 
 
-def workload():
+WORKLOADS = {
+    # name: (problem, extra Params, tol)
+    "p100_phi040_mobility": ("mobility", {}, 1e-7),
+    "pair_gap1e-3_resistance": ("resistance", {"Nc": 36, "Mc": 72, "Rc": 0.7, "Nfp": 400}, 1e-10),
+    "p1000_poly_phi060_mobility": ("mobility", {"delta_c": 0.1}, 1e-7),
+    "p10000_phi065_mobility": ("mobility", {}, 1e-6),
+}
+
+
+def workload(name=WORKLOAD):
     import workloads as w
-    pk = w.packing_p100()
-    ft = w.forces_torques(pk.P, 5)
-    return pk, ft
+    if name == "p100_phi040_mobility":
+        pk = w.packing_p100()
+        data = w.forces_torques(pk.P, 5)
+    elif name == "pair_gap1e-3_resistance":
+        pk = w.two_disks(1e-3)
+        data = w.rigid_velocities(2, 11)
+    elif name == "p1000_poly_phi060_mobility":
+        pk = w.packing_p1000_poly()
+        data = w.forces_torques(pk.P, 6)
+    elif name == "p10000_phi065_mobility":
+        pk = w.packing_p10000()
+        data = w.forces_torques(pk.P, 7)
+    else:
+        raise ValueError(name)
+    return pk, data
 
 
 def oracle_solve(pk, ft):
@@ -289,6 +310,64 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_large(args):
+    """Non-default workloads: timings and full-size properties (no oracle solve)."""
+    import torch
+    from paper_2606_11273_gb300 import build as b
+    b.build()
+    import paper_2606_11273_gb300 as L
+    problem, extra, tol = WORKLOADS[args.workload]
+    code = L.MOBILITY if problem == "mobility" else L.RESISTANCE
+    t0 = time.perf_counter()
+    pk, data = workload(args.workload)
+    t_geom = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    res = {"workload": args.workload, "P": int(pk.P), "geometry_s": t_geom}
+    for prec in (L.MIXED, L.FP64) if args.workload != "p10000_phi065_mobility" else (L.MIXED,):
+        prm = L.Params(precision=prec, tol=tol, stream=stream.cuda_stream, **extra)
+        s = L.Solver(pk.centres, pk.radii, prm)
+        d_in = torch.tensor(data, dtype=torch.float64, device="cuda")
+        d_out = torch.zeros_like(d_in)
+        info = s.solve_device(code, d_in, d_out)          # includes the pair precompute
+        st = s.stats(code)
+        t1 = time.perf_counter()
+        info2 = s.solve_device(code, d_in, d_out)         # blocks resident
+        t_solve = time.perf_counter() - t1
+        n = pk.P * prm.Mc * 2
+        mu = torch.randn(n, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(mu)
+        s.matvec(code, mu, u, prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            s.matvec(code, mu, u, prec)
+        e1.record(stream)
+        e1.synchronize()
+        r = {"n_pairs": s.n_pairs, "precompute_ms": st["precompute_ms"], "qr_ms": st["qr_ms"],
+             "qr_tflops": st["qr_flops"] / (st["qr_ms"] * 1e-3) / 1e12, "rank_F": [st["min_rank_F"], st["max_rank_F"]],
+             "iters": info["iters"], "relres": info["relres"], "converged": info["converged"],
+             "solve_s_blocks_resident": t_solve, "matvec_ms": e0.elapsed_time(e1) / 3}
+        if prec == L.MIXED:
+            # full-size property: the mixed solution's residual under the FP64 operator
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            s.solution(x)
+            bvec = torch.zeros_like(x)
+            s.rhs(code, d_in, bvec, L.FP64)
+            ax = torch.zeros_like(x)
+            t2 = time.perf_counter()
+            s.matvec(code, x, ax, L.FP64)
+            torch.cuda.synchronize()
+            r["fp64_matvec_s"] = time.perf_counter() - t2
+            r["fp64_true_relres_of_mixed_solution"] = float((ax - bvec).norm() / bvec.norm())
+            mixed_out = d_out.cpu().numpy()
+        else:
+            r["rel_diff_fp64_vs_mixed"] = float(np.linalg.norm(d_out.cpu().numpy() - mixed_out) / np.linalg.norm(d_out.cpu().numpy()))
+        res["mixed" if prec == L.MIXED else "fp64"] = r
+        s.close()
+    print(json.dumps(res))
+
+
 def run_profile_case(case):
     """Small, bounded cases for ncu captures (a few launches of one kernel)."""
     import torch
@@ -296,7 +375,18 @@ def run_profile_case(case):
     b.build()
     import paper_2606_11273_gb300 as L
     stream = torch.cuda.Stream()
-    if case in ("qr", "matvec"):
+    if case in ("m2p_large", "matvec_large"):
+        # P = 10^4 packing with zero pair blocks (no precompute): far field only
+        pk, _ = workload("p10000_phi065_mobility")
+        s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))
+        C = s.n_pairs
+        s.set_pair_blocks(L.MOBILITY, np.zeros((C, 240, 240)), np.zeros((C, 6, 240)))
+        mu = torch.randn(pk.P * 144, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(mu)
+        for _ in range(2):
+            s.matvec(L.MOBILITY, mu, u, L.MIXED)
+        torch.cuda.synchronize()
+    elif case in ("qr", "matvec"):
         pk, ft = workload()
         s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))
         s.precompute(L.MOBILITY)
@@ -336,11 +426,16 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile-case", default=None, choices=["qr", "matvec", "stokeslet"],
+    ap.add_argument("--profile-case", default=None, choices=["qr", "matvec", "stokeslet", "m2p_large", "matvec_large"],
                     help="run one small bounded case for an ncu capture and exit")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="non-default workloads print timings and full-size checks, not the contract line")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)
+        return
+    if args.workload != WORKLOAD:
+        run_large(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -42,7 +42,12 @@ __global__ void contacts_kernel(const double* __restrict__ c, const double* __re
 
 int detect_contacts(Ctx& c) {
   const int P = c.d.P;
-  const double g_near = c.prm.delta_c > 3.0 ? c.prm.delta_c : 3.0;
+  // near zone: close pairs, plus every disk within gap 1.5 (the multipole far
+  // field converges there with at most 32 orders); never closer than 4 source
+  // ring radii to a centre, which the direct FP32 tile kernel's series needs
+  const double rmax = *std::max_element(c.radii_h.begin(), c.radii_h.end());
+  const double rmin = *std::min_element(c.radii_h.begin(), c.radii_h.end());
+  const double g_near = std::max({c.prm.delta_c, 1.5, 4.0 * c.Rc * rmax - rmin + 0.01});
   int *cc = nullptr, *cn = nullptr, *nov = nullptr, *oc = nullptr, *on = nullptr;
   int *pc = nullptr, *pn = nullptr;
   int rc = LMFS_OK;

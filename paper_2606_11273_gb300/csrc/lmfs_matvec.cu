@@ -503,12 +503,15 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
 // truncated at n = MP_P; the terms decay like (|w|/|Z|)^n and |w|/|Z| <=
 // R_c r/(r + g_near) outside the near zone.  The moments are formed in FP64;
 // the evaluation runs in FP32 (mixed) or FP64.
-constexpr int MP_P = 20;
-constexpr int MP_NCOEF = 64;   // F0, a[1..P], g[1..P+1], h[0..P] = 3P + 3 = 63, padded
+constexpr int MP_P = 32;
+// Coefficient slots per disk (complex): 2n -> a_n = A_n/(2n) and 2n+1 -> g_n
+// for n = 1..P+1 (a_{P+1} = 0), 2(P+2)+n -> h_n = conj(A_n) for n = 0..P;
+// slot 0 holds F_0, slot 1 holds (B, rho): rho = source ring radius and B a
+// bound with |c_n| <= B rho^n for every stored coefficient c_n (n >= 1),
+// which fixes the order needed at each target (adaptive truncation).
+constexpr int MP_NCOEF = 104;   // 3P + 5 = 101, padded to a multiple of 4
 
-// P2M: one warp per disk.  Coefficient layout per disk (complex):
-// [0] F0, [1..P] a_n = A_n/(2n), [P+1..2P+1] g_n = B_n/(2n) - D_{n-1}/2
-// (g_{P+1} = -D_P/2), [2P+2..3P+2] h_n = conj(A_n).
+// P2M: one warp per disk (moments in FP64).
 __global__ void p2m_kernel(const double* __restrict__ s, int P, int Nc, const double* __restrict__ radii,
                            double Rc, double2* __restrict__ coef, float2* __restrict__ coef32) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -532,6 +535,7 @@ __global__ void p2m_kernel(const double* __restrict__ s, int P, int Nc, const do
   }
   double2* out = coef + (long long)i * MP_NCOEF;
   double Dprev_r = 0, Dprev_i = 0;
+  double bound = 0.0, rpow = 1.0;   // max |c_n| / rho^n
   for (int n = 0; n <= MP_P; ++n) {
     double Ar = 0, Ai = 0, Br = 0, Bi = 0, Dr = 0, Di = 0;
 #pragma unroll
@@ -547,14 +551,25 @@ __global__ void p2m_kernel(const double* __restrict__ s, int P, int Nc, const do
     }
     Ar = wsum(Ar); Ai = wsum(Ai); Br = wsum(Br); Bi = wsum(Bi); Dr = wsum(Dr); Di = wsum(Di);
     if (lane == 0) {
-      if (n == 0) out[0] = make_double2(Ar, Ai);
-      else {
-        out[n] = make_double2(Ar / (2.0 * n), Ai / (2.0 * n));
-        out[MP_P + n] = make_double2(Br / (2.0 * n) - 0.5 * Dprev_r, Bi / (2.0 * n) - 0.5 * Dprev_i);
+      if (n == 0) {
+        out[0] = make_double2(Ar, Ai);
+      } else {
+        const double2 an = make_double2(Ar / (2.0 * n), Ai / (2.0 * n));
+        const double2 gn = make_double2(Br / (2.0 * n) - 0.5 * Dprev_r, Bi / (2.0 * n) - 0.5 * Dprev_i);
+        out[2 * n] = an;
+        out[2 * n + 1] = gn;
+        bound = fmax(bound, fmax(hypot(an.x, an.y), hypot(gn.x, gn.y)) / rpow);
       }
-      out[2 * MP_P + 2 + n] = make_double2(Ar, -Ai);
-      if (n == MP_P) out[2 * MP_P + 1] = make_double2(-0.5 * Dr, -0.5 * Di);
+      out[2 * (MP_P + 2) + n] = make_double2(Ar, -Ai);
+      bound = fmax(bound, hypot(Ar, Ai) * rs / (rpow * rs));   // |h_n| <= B rho^n
+      if (n == MP_P) {
+        out[2 * (MP_P + 1)] = make_double2(0.0, 0.0);
+        const double2 gl = make_double2(-0.5 * Dr, -0.5 * Di);
+        out[2 * (MP_P + 1) + 1] = gl;
+        bound = fmax(bound, hypot(gl.x, gl.y) / (rpow * rs));
+      }
     }
+    rpow *= rs;
     Dprev_r = Dr; Dprev_i = Di;
 #pragma unroll
     for (int q = 0; q < SPL; ++q) {
@@ -563,10 +578,11 @@ __global__ void p2m_kernel(const double* __restrict__ s, int P, int Nc, const do
       pr[q] = npr; pi_[q] = npi; qr[q] = nqr; qi[q] = nqi;
     }
   }
+  if (lane == 0) out[1] = make_double2(bound, rs);
+  __syncwarp();
   if (coef32) {
-    __syncwarp();
     for (int c = lane; c < MP_NCOEF; c += 32) {
-      const double2 v = (c < 3 * MP_P + 3) ? out[c] : make_double2(0.0, 0.0);
+      const double2 v = (c < 3 * MP_P + 5) ? out[c] : make_double2(0.0, 0.0);
       coef32[(long long)i * MP_NCOEF + c] = make_float2((float)v.x, (float)v.y);
     }
   }
@@ -697,41 +713,56 @@ __global__ void __launch_bounds__(M_THREADS) m2p_kernel(MpArgs a) {
           t[q].r = Z[q].r * ir2; t[q].i = -Z[q].i * ir2;     // 1/Z
           tb[q].r = t[q].r; tb[q].i = -t[q].i;              // 1/conj(Z)
         }
-        Cx<T> s1[TPT], s2[TPT], s3[TPT];
-#pragma unroll
-        for (int q = 0; q < TPT; ++q) {
-          s1[q].r = s1[q].i = s2[q].r = s2[q].i = s3[q].r = s3[q].i = (T)0;
-        }
-        // Horner: s1 = sum_{n=1}^P a_n t^n ; s2 = sum_{n=1}^{P+1} g_n tb^n ;
-        //         s3 = sum_{n=0}^{P} h_n tb^(n+1)
+        // order needed here: B x^(p+1) / (1 - x) <= tol * |leading term|, x = rho / R
+        int pe = 2;
         {
-          const V2 gl = cf[2 * MP_P + 1];
-#pragma unroll
-          for (int q = 0; q < TPT; ++q) { s2[q].r = (T)gl.x; s2[q].i = (T)gl.y; }
-        }
-        for (int n = MP_P; n >= 1; --n) {
-          const V2 an = cf[n], gn = cf[MP_P + n], hn = cf[2 * MP_P + 2 + n];
+          const V2 bd = cf[1];
+          const T B = (T)bd.x, rho = (T)bd.y;
 #pragma unroll
           for (int q = 0; q < TPT; ++q) {
-            Cx<T> A_ = {(T)an.x, (T)an.y}, G_ = {(T)gn.x, (T)gn.y}, H_ = {(T)hn.x, (T)hn.y};
-            // s1 <- (s1 + a_n) t ;  s2 <- s2 tb + g_n ;  s3 <- (s3 + h_n) tb
-            Cx<T> u1 = {s1[q].r + A_.r, s1[q].i + A_.i};
-            s1[q].r = u1.r * t[q].r - u1.i * t[q].i; s1[q].i = u1.r * t[q].i + u1.i * t[q].r;
-            s2[q] = cfma(s2[q], tb[q], G_);
-            Cx<T> u3 = {s3[q].r + H_.r, s3[q].i + H_.i};
-            s3[q].r = u3.r * tb[q].r - u3.i * tb[q].i; s3[q].i = u3.r * tb[q].i + u3.i * tb[q].r;
+            const T R = sqrt(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
+            const T x = rho / R;
+            const V2 a1 = cf[2];
+            const T lead = sqrt((T)a1.x * (T)a1.x + (T)a1.y * (T)a1.y) / R + B * x * (T)1e-6 + (T)1e-300;
+            const T tol = (sizeof(T) == 4) ? (T)1e-9 : (T)1e-16;
+            int need = MP_P;
+            if (B > (T)0 && x < (T)1) {
+              const T lim = tol * lead * ((T)1 - x) / B;
+              need = (lim >= (T)1) ? 1 : (int)ceil(log(lim) / log(x)) - 1;
+            }
+            pe = max(pe, min(need, MP_P));
+          }
+          pe = __reduce_max_sync(__activemask(), pe);   // lanes may skip different disks
+        }
+        Cx<T> s1[TPT], s2[TPT], s3[TPT];
+        {
+          const V2 ap = cf[2 * pe], gp = cf[2 * (pe + 1) + 1], hp = cf[2 * (MP_P + 2) + pe];
+#pragma unroll
+          for (int q = 0; q < TPT; ++q) {
+            s1[q].r = (T)ap.x; s1[q].i = (T)ap.y;
+            s2[q].r = (T)gp.x; s2[q].i = (T)gp.y;
+            s3[q].r = (T)hp.x; s3[q].i = (T)hp.y;
           }
         }
-        const V2 h0 = cf[2 * MP_P + 2];
+        // s1 = sum_{n=1}^{pe} a_n t^n, s2 = sum_{n=1}^{pe+1} g_n tb^n,
+        // s3 = sum_{n=0}^{pe} h_n tb^(n+1): Horner, one complex FMA per term
+        for (int n = pe; n >= 1; --n) {
+          const V2 an1 = cf[2 * (n - 1)], gn = cf[2 * n + 1], hn1 = cf[2 * (MP_P + 2) + n - 1];
+#pragma unroll
+          for (int q = 0; q < TPT; ++q) {
+            if (n > 1) s1[q] = cfma(s1[q], t[q], Cx<T>{(T)an1.x, (T)an1.y});
+            s2[q] = cfma(s2[q], tb[q], Cx<T>{(T)gn.x, (T)gn.y});
+            s3[q] = cfma(s3[q], tb[q], Cx<T>{(T)hn1.x, (T)hn1.y});
+          }
+        }
         const V2 f0 = cf[0];
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-          // s2 still lacks the final factor tb (g_n multiplies tb^n, n >= 1)
-          Cx<T> s2f = {s2[q].r * tb[q].r - s2[q].i * tb[q].i, s2[q].r * tb[q].i + s2[q].i * tb[q].r};
-          Cx<T> u3 = {s3[q].r + (T)h0.x, s3[q].i + (T)h0.y};
-          Cx<T> s3f = {u3.r * tb[q].r - u3.i * tb[q].i, u3.r * tb[q].i + u3.i * tb[q].r};
-          T ur = s1[q].r + s2f.r + (T)0.5 * (Z[q].r * s3f.r - Z[q].i * s3f.i);
-          T ui = s1[q].i + s2f.i + (T)0.5 * (Z[q].r * s3f.i + Z[q].i * s3f.r);
+          const Cx<T> s1f = {s1[q].r * t[q].r - s1[q].i * t[q].i, s1[q].r * t[q].i + s1[q].i * t[q].r};
+          const Cx<T> s2f = {s2[q].r * tb[q].r - s2[q].i * tb[q].i, s2[q].r * tb[q].i + s2[q].i * tb[q].r};
+          const Cx<T> s3f = {s3[q].r * tb[q].r - s3[q].i * tb[q].i, s3[q].r * tb[q].i + s3[q].i * tb[q].r};
+          T ur = s1f.r + s2f.r + (T)0.5 * (Z[q].r * s3f.r - Z[q].i * s3f.i);
+          T ui = s1f.i + s2f.i + (T)0.5 * (Z[q].r * s3f.i + Z[q].i * s3f.r);
           if (a.with_log) {
             const T lr = (T)0.5 * log(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
             ur += (T)f0.x * ((T)0.5 - lr);
@@ -923,6 +954,8 @@ __global__ void post_kernel(const double* __restrict__ lb, const double* __restr
 // any stream capture.
 int far_field_prepare(Ctx& c) {
   const size_t shm = 2 * (size_t)F_TILE * c.d.Nc * 32 + 2 * F_TILE * 32 + 16;
+  const size_t shm64 = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(double2) + 2 * M_TILE * 32 + 16;
+  LMFS_CUDA(cudaFuncSetAttribute(m2p_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm64));
   LMFS_CUDA(cudaFuncSetAttribute(far32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   LMFS_CUDA(cudaFuncSetAttribute(far32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   LMFS_TRY(dalloc(&c.coef64, (size_t)c.d.P * MP_NCOEF));
