@@ -496,6 +496,9 @@ int build_onebody(Ctx& c, int problem, OneBody& ob) {
   const int ld = m;
   const long long mstride = (long long)ld * (n + k);
   ob.nclass = nb;
+  // a rebuild (after lmfs_invalidate) replaces every factor, including
+  // imported SVD factors' V, which the QR form does not use
+  dfree(ob.W); dfree(ob.R); dfree(ob.perm); dfree(ob.rank); dfree(ob.V);
   LMFS_TRY(dalloc(&ob.W, (size_t)nb * n * 2 * Mc));
   LMFS_TRY(dalloc(&ob.R, (size_t)nb * n * n));
   LMFS_TRY(dalloc(&ob.perm, (size_t)nb * n));
