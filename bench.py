@@ -95,6 +95,23 @@ def dist_env():
     return ws, rank, local
 
 
+def job_time_ms(t_ms, ws, device="cpu"):
+    """Duration of the whole job's timed region: the maximum over ranks (the
+    replicas start together after a barrier; the job ends with the slowest)."""
+    if ws == 1:
+        return float(t_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps, ws, t_ms):
+    """Whole-job throughput: every rank's solves over the max-over-ranks time."""
+    return ws * steps / (t_ms * 1e-3)
+
+
 WORKLOADS = {
     # name: (problem, extra Params, tol)
     "p100_phi040_mobility": ("mobility", {}, 1e-7),
@@ -216,12 +233,8 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     launches = _lib.launch_count() - n0
-    t_ms = ev_all0.elapsed_time(ev_all1)
-    if ws > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = ws * args.steps / (t_ms * 1e-3)
+    t_ms = job_time_ms(ev_all0.elapsed_time(ev_all1), ws, device="cuda")
+    value = job_value(args.steps, ws, t_ms)
 
     # end to end through the public host API: create + solve (host in/out) + destroy
     e2e_ms = None
