@@ -1,6 +1,5 @@
 // Batched column-pivoted Householder QR with rank truncation, and the
-// truncated basic least-squares solution, in FP64 -- one thread block per
-// matrix, the matrix in global memory (column-major).
+// truncated basic least-squares solution, in FP64.
 //
 // This replaces the paper's truncated SVD pseudo-inverses (eq. (howG+),
 // eq. (bfm), eq. (Amat): singular values below eps * sigma_1 dropped) by the
@@ -8,25 +7,39 @@
 // norm and the factorization stops at the first |R_ss| <= eps |R_00|.  Both
 // give least-squares solutions with residuals at the truncation level; they
 // differ only in the numerically null directions.
+//
+// Two kernels per batch:
+//   qrcp_kernel     factors the coefficient columns [M] of each [M | B]
+//                   (one matrix per thread-block cluster, matrix in global
+//                   memory); reflectors stay below the diagonal, tau aside.
+//   apply_qt_kernel applies the r reflectors to B, a tile of KT right-hand
+//                   sides per CTA held in shared memory for the whole
+//                   sweep (each reflector arrives by a bulk asynchronous copy,
+//                   double-buffered), then either back-substitutes with R and
+//                   scatters the solution by the pivot order, or writes Q^T B
+//                   back in place.
+// Keeping B out of the pivoted sweep removes its columns from the per-reflector
+// global-memory traffic; the right-hand sides are then updated from shared
+// memory at the FP64 pipe's rate.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
 #include <cooperative_groups.h>
 
 #include "lmfs_internal.h"
+#include "lmfs_tma.cuh"
 
 namespace lmfs {
 namespace {
-
-constexpr int QR_THREADS = 512;
-constexpr int QR_WARPS = QR_THREADS / 32;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Block-wide sum; every thread gets the result.  red: QR_WARPS doubles.
+// Block-wide sum; every thread gets the result.  red: NW doubles.
+template <int NW>
 __device__ double block_sum(double v, double* red) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -35,7 +48,7 @@ __device__ double block_sum(double v, double* red) {
   __syncthreads();
   double t = 0.0;
   if (wid == 0) {
-    t = (lane < QR_WARPS) ? red[lane] : 0.0;
+    t = (lane < NW) ? red[lane] : 0.0;
     t = warp_sum(t);
     if (lane == 0) red[0] = t;
   }
@@ -45,6 +58,7 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // Block-wide argmax of val over indices; ties -> smallest index.
+template <int NW>
 __device__ void block_argmax(double val, int idx, double* redv, int* redi, double* outv, int* outi) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) {
@@ -56,8 +70,8 @@ __device__ void block_argmax(double val, int idx, double* redv, int* redi, doubl
   if (lane == 0) { redv[wid] = val; redi[wid] = idx; }
   __syncthreads();
   if (wid == 0) {
-    val = (lane < QR_WARPS) ? redv[lane] : -1.0;
-    idx = (lane < QR_WARPS) ? redi[lane] : 0x7fffffff;
+    val = (lane < NW) ? redv[lane] : -1.0;
+    idx = (lane < NW) ? redi[lane] : 0x7fffffff;
     for (int o = 16; o > 0; o >>= 1) {
       double ov = __shfl_xor_sync(0xffffffffu, val, o);
       int oi = __shfl_xor_sync(0xffffffffu, idx, o);
@@ -69,49 +83,55 @@ __device__ void block_argmax(double val, int idx, double* redv, int* redi, doubl
 }
 
 struct Args {
-  double* A; long long mstride; const int* m; const int* n; int k; int ld; double eps;
-  double* X; int xld; long long xstride; int* rank; int* perm; int permstride;
-  double* tau; double* vn; int* info; int solve; int cs;
+  double* A; long long mstride; const int* m; const int* n; int ld; double eps;
+  int* rank; int* perm; int permstride; double* tau; double* vn; int* info; int cs;
 };
 
-// One matrix per thread-block cluster of a.cs CTAs (a.cs = 1: a plain block).
-// Columns j are owned by warp (j mod (cs * QR_WARPS)) of the cluster; CTA 0
-// chooses the pivot, swaps columns and forms the Householder vector, then
-// every CTA applies it to its own columns.  Matrix data moves between CTAs
-// through global memory, so it is read with L2-only loads (__ldcg).
-__global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
+// One matrix per thread-block cluster of a.cs CTAs of T threads (a.cs = 1: a
+// plain block).  Columns j are owned by warp (j mod (cs * T / 32)) of the
+// cluster; CTA 0 chooses the pivot, swaps columns and forms the Householder
+// vector, then every CTA applies it to its own columns, two at a time.  Matrix
+// data moves between CTAs through global memory, so it is read with L2-only
+// loads (__ldcg).  Partial column norms are kept squared: the LAPACK dlaqp2
+// downdate nrm' = nrm sqrt((1 - t)(1 + t)), t = |a_sj| / nrm, becomes
+// nrm'^2 = nrm^2 - a_sj^2 (one fused multiply-add) with the same
+// recomputation test, so no division or square root is spent per column and
+// reflector; where the subtraction cancels, the test recomputes the norm.
+template <int T>
+__global__ void __launch_bounds__(T) qrcp_kernel(Args q) {
+  constexpr int NW = T / 32;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) double qsm[];
+  double* const smem = qsm;
   const int crank = (int)cluster.block_rank();
   const int cs = q.cs;
   const int b = blockIdx.x / cs;
-  const int m = q.m[b], n = q.n[b], k = q.k, ld = q.ld;
+  const int m = q.m[b], n = q.n[b], ld = q.ld;
   double* A = q.A + (long long)b * q.mstride;
   int* perm = q.perm + (long long)b * q.permstride;
-  double* vn1 = q.vn + (long long)b * 2 * q.permstride;
-  double* vn2 = vn1 + q.permstride;
+  double* vn1 = q.vn + (long long)b * 2 * q.permstride;   // squared partial norms
+  double* vn2 = vn1 + q.permstride;                       // squared norms at the last recompute
   double* tau_g = q.tau + (long long)b * q.permstride;
   double* sv = smem;                       // Householder vector, m entries
-  double* red = smem + ld;                 // QR_WARPS
-  int* redi = (int*)(red + QR_WARPS);      // QR_WARPS
+  double* red = smem + ld;                 // NW
+  int* redi = (int*)(red + NW);            // NW
   __shared__ double s_piv;
   __shared__ int s_pidx;
-  __shared__ double s_beta, s_tau, s_r00, s_amb;
+  __shared__ double s_tau, s_r00, s_amb;
   __shared__ int s_stop, s_bad;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int gw = crank * QR_WARPS + wid;          // warp id within the cluster
-  const int nw = cs * QR_WARPS;                   // warps in the cluster
+  const int gw = crank * NW + wid;          // warp id within the cluster
+  const int nw = cs * NW;                   // warps in the cluster
   const double tol3z = sqrt(2.220446049250313e-16);
-  const int ncol = n + k;
 
-  // initial column norms and identity permutation (owner warps)
+  // initial squared column norms and identity permutation (owner warps)
   for (int j = gw; j < n; j += nw) {
     const double* col = A + (long long)j * ld;
     double s = 0.0;
     for (int i = lane; i < m; i += 32) { double a = __ldcg(col + i); s += a * a; }
     s = warp_sum(s);
-    if (lane == 0) { vn1[j] = sqrt(s); vn2[j] = sqrt(s); perm[j] = j; }
+    if (lane == 0) { vn1[j] = s; vn2[j] = s; perm[j] = j; }
   }
   if (threadIdx.x == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; }
   cluster.sync();
@@ -122,17 +142,17 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
     if (crank == 0) {
       // 1. pivot: largest remaining partial column norm
       double bv = -1.0; int bi = 0x7fffffff;
-      for (int j = s + threadIdx.x; j < n; j += QR_THREADS) {
+      for (int j = s + threadIdx.x; j < n; j += T) {
         double v = __ldcg(vn1 + j);
         if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
       }
-      block_argmax(bv, bi, red, redi, &s_piv, &s_pidx);
+      block_argmax<NW>(bv, bi, red, redi, &s_piv, &s_pidx);
       const int p = s_pidx;
       // 2. swap columns s and p
       if (p != s) {
         double* cs_ = A + (long long)s * ld;
         double* cp_ = A + (long long)p * ld;
-        for (int i = threadIdx.x; i < m; i += QR_THREADS) {
+        for (int i = threadIdx.x; i < m; i += T) {
           double t = __ldcg(cs_ + i); cs_[i] = __ldcg(cp_ + i); cp_[i] = t;
         }
         if (threadIdx.x == 0) {
@@ -145,8 +165,8 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
       // 3. Householder vector of A[s:m, s]
       double* cs_ = A + (long long)s * ld;
       double part = 0.0;
-      for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) { double a = __ldcg(cs_ + i); part += a * a; }
-      const double sig2 = block_sum(part, red);
+      for (int i = s + 1 + threadIdx.x; i < m; i += T) { double a = __ldcg(cs_ + i); part += a * a; }
+      const double sig2 = block_sum<NW>(part, red);
       if (threadIdx.x == 0) {
         const double alpha = __ldcg(cs_ + s);
         const double nrm = sqrt(alpha * alpha + sig2);
@@ -156,7 +176,6 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
           s_stop = 1;
         } else {
           const double beta = (alpha >= 0.0) ? -nrm : nrm;
-          s_beta = beta;
           s_tau = (beta - alpha) / beta;
           s_amb = alpha - beta;          // alpha and -beta share a sign: no cancellation
           cs_[s] = beta;
@@ -166,7 +185,7 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
       __syncthreads();
       if (!s_stop) {
         const double scale = 1.0 / s_amb;
-        for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) cs_[i] = __ldcg(cs_ + i) * scale;
+        for (int i = s + 1 + threadIdx.x; i < m; i += T) cs_[i] = __ldcg(cs_ + i) * scale;
       }
     }
     cluster.sync();
@@ -182,38 +201,66 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
     if (stop) { rank = s; break; }
     {
       const double* cs_ = A + (long long)s * ld;
-      for (int i = s + 1 + threadIdx.x; i < m; i += QR_THREADS) sv[i] = __ldcg(cs_ + i);
+      for (int i = s + 1 + threadIdx.x; i < m; i += T) sv[i] = __ldcg(cs_ + i);
       if (threadIdx.x == 0) sv[s] = 1.0;
     }
     __syncthreads();
-    // 4. apply H = I - tau v v^T to this CTA's trailing columns
-    for (int j = s + 1 + ((gw - (s + 1)) % nw + nw) % nw; j < ncol; j += nw) {
-      double* cj = A + (long long)j * ld;
-      double w = 0.0;
-      for (int i = s + lane; i < m; i += 32) w += sv[i] * __ldcg(cj + i);
-      w = warp_sum(w) * tau;
-      for (int i = s + lane; i < m; i += 32) cj[i] = __ldcg(cj + i) - w * sv[i];
-      if (j < n) {
-        __syncwarp();
-        // 5. downdate the partial column norm (LAPACK dlaqp2 rule)
-        double nv = __ldcg(vn1 + j);
-        bool recompute = false;
-        if (nv != 0.0) {
-          double t = fabs(__ldcg(cj + s)) / nv;
-          t = fmax(0.0, (1.0 + t) * (1.0 - t));
-          const double v2 = __ldcg(vn2 + j);
-          double t2 = t * (nv / v2) * (nv / v2);
-          if (t2 <= tol3z) recompute = true;
-          else nv = nv * sqrt(t);
+    // 4. apply H = I - tau v v^T to this CTA's trailing columns, two per warp
+    //    at a time; 5. downdate their squared partial norms
+    const int jf = s + 1 + ((gw - (s + 1)) % nw + nw) % nw;
+    for (int j = jf; j < n; j += 2 * nw) {
+      const int j2 = j + nw;
+      const bool two = j2 < n;
+      double* c1 = A + (long long)j * ld;
+      double* c2 = A + (long long)(two ? j2 : j) * ld;
+      const double n1 = __ldcg(vn1 + j), r1 = __ldcg(vn2 + j);
+      const double n2 = two ? __ldcg(vn1 + j2) : 0.0, r2 = two ? __ldcg(vn2 + j2) : 0.0;
+      double d1 = 0.0, d2 = 0.0;
+      if (two) {
+        for (int i = s + lane; i < m; i += 32) {
+          const double vi = sv[i];
+          const double a1 = __ldcg(c1 + i), a2 = __ldcg(c2 + i);
+          d1 += vi * a1;
+          d2 += vi * a2;
         }
-        if (recompute) {
+      } else {
+        for (int i = s + lane; i < m; i += 32) d1 += sv[i] * __ldcg(c1 + i);
+      }
+      d1 = warp_sum(d1) * tau;
+      d2 = two ? warp_sum(d2) * tau : 0.0;
+      double as1 = 0.0, as2 = 0.0;             // updated A[s, j] (lane 0 holds row s)
+      if (two) {
+        for (int i = s + lane; i < m; i += 32) {
+          const double vi = sv[i];
+          const double a1 = __ldcg(c1 + i) - d1 * vi;
+          const double a2 = __ldcg(c2 + i) - d2 * vi;
+          c1[i] = a1;
+          c2[i] = a2;
+          if (i == s) { as1 = a1; as2 = a2; }
+        }
+      } else {
+        for (int i = s + lane; i < m; i += 32) {
+          const double a1 = __ldcg(c1 + i) - d1 * sv[i];
+          c1[i] = a1;
+          if (i == s) as1 = a1;
+        }
+      }
+      as1 = __shfl_sync(0xffffffffu, as1, 0);
+      as2 = __shfl_sync(0xffffffffu, as2, 0);
+      for (int h = 0; h < (two ? 2 : 1); ++h) {
+        const int jj = h ? j2 : j;
+        const double* cj = h ? c2 : c1;
+        const double nsq = h ? n2 : n1, rsq = h ? r2 : r1, a = fabs(h ? as2 : as1);
+        if (nsq == 0.0) continue;
+        const double rest = fma(-a, a, nsq);                // = nrm^2 (1 - t)(1 + t)
+        if (rest <= tol3z * rsq) {
+          __syncwarp();
           double ss = 0.0;
-          for (int i = s + 1 + lane; i < m; i += 32) { double a = __ldcg(cj + i); ss += a * a; }
+          for (int i = s + 1 + lane; i < m; i += 32) { double x = __ldcg(cj + i); ss += x * x; }
           ss = warp_sum(ss);
-          nv = sqrt(ss);
-          if (lane == 0) { vn1[j] = nv; vn2[j] = nv; }
+          if (lane == 0) { vn1[jj] = ss; vn2[jj] = ss; }
         } else if (lane == 0) {
-          vn1[j] = nv;
+          vn1[jj] = rest;
         }
       }
     }
@@ -224,59 +271,154 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(Args q) {
     q.rank[b] = rank;
     q.info[b] = s_bad;
   }
+  // after a truncation break the other CTAs may still be reading CTA 0's
+  // shared flags: no CTA exits before every distributed access is done
   cluster.sync();
-  if (!q.solve) return;
-
-  // 6. back substitution R[0:r,0:r] x = (Q^T B)[0:r], one warp per RHS column,
-  //    column-oriented (coalesced reads of R's columns); x overwrites B.
-  double* X = q.X + (long long)b * q.xstride;
-  int bad = 0;
-  for (int c = gw; c < k; c += nw) {
-    double* bc = A + (long long)(n + c) * ld;
-    for (int j = rank - 1; j >= 0; --j) {
-      const double* rj = A + (long long)j * ld;
-      const double xj = __ldcg(bc + j) / __ldcg(rj + j);
-      __syncwarp();
-      for (int i = lane; i < j; i += 32) bc[i] = __ldcg(bc + i) - xj * __ldcg(rj + i);
-      if (lane == 0) bc[j] = xj;
-      __syncwarp();
-    }
-    double* xc = X + (long long)c * q.xld;
-    for (int j = lane; j < n; j += 32) {
-      double v = (j < rank) ? __ldcg(bc + j) : 0.0;
-      if (!(v == v) || isinf(v)) bad = 1;
-      xc[__ldcg(perm + j)] = v;
-    }
-  }
-  if (bad) atomicExch(q.info + b, 1);
 }
 
-}  // namespace
+struct ArgsB {
+  double* A; long long mstride; const int* m; const int* n; int k; int ld;
+  const double* tau; int permstride; const int* rank; const int* perm;
+  double* X; int xld; long long xstride; int* info; int solve; int nmax;
+};
 
-int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
-  if (q.nb <= 0) return LMFS_OK;
-  Args a;
-  a.A = q.A; a.mstride = q.mstride; a.m = q.m; a.n = q.n; a.k = q.k; a.ld = q.ld; a.eps = q.eps;
-  a.X = q.X; a.xld = q.xld; a.xstride = q.xstride; a.rank = q.rank; a.perm = q.perm;
-  a.permstride = q.permstride; a.tau = q.tau; a.vn = q.vn; a.info = q.info; a.solve = solve ? 1 : 0;
-  size_t shm = (size_t)q.ld * sizeof(double) + QR_WARPS * (sizeof(double) + sizeof(int));
-  if (shm > 48 * 1024) {
-    if (cuda_failed(cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)shm), "qr smem attribute"))
-      return LMFS_ERR_CUDA;
+// Q^T B and the truncated solution for a tile of KT right-hand sides
+// (blockIdx.x) of matrix blockIdx.y; warp w owns right-hand side c0 + w.
+// Shared memory: the tile [KT][ldE], two reflector buffers [ldE], tau [nmax]
+// (ldE = ld rounded up to even, so that every copy is 16-byte aligned).
+template <int KT>
+__global__ void __launch_bounds__(KT * 32) apply_qt_kernel(ArgsB a) {
+  extern __shared__ __align__(16) double bsm[];
+  double* const smem = bsm;
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_fail;
+  const int b = blockIdx.y, c0 = blockIdx.x * KT;
+  const int m = a.m[b], n = a.n[b], r = a.rank[b], ld = a.ld;
+  const int ldE = (ld + 1) & ~1, mE = (m + 1) & ~1;
+  const int kt = min(KT, a.k - c0);
+  double* A = a.A + (long long)b * a.mstride;
+  double* Bs = smem;
+  double* vbuf[2] = {smem + (long long)KT * ldE, smem + (long long)(KT + 1) * ldE};
+  double* st = smem + (long long)(KT + 2) * ldE;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* col = Bs + (long long)w * ldE;
+  const bool own = w < kt;
+
+  for (int i = threadIdx.x; i < r; i += KT * 32) st[i] = a.tau[(long long)b * a.permstride + i];
+  if (own) {
+    const double* g = A + (long long)(n + c0 + w) * ld;
+    for (int i = lane; i < m; i += 32) col[i] = g[i];
   }
-  // cluster size: spread few matrices over the SMs so that every SM holds up
-  // to two CTAs (the register limit of this kernel), up to the portable
-  // cluster limit of 8
-  int sms = 152, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int cs = 1;
-  while (cs < 8 && q.nb * cs * 2 <= 2 * sms) cs *= 2;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // reflector s: rows s..m-1 of column s (row s is R_ss; the unit entry of v
+  // is applied explicitly), copied from the even row at or below s
+  auto issue = [&](int s) {
+    const int s0 = s & ~1, buf = s & 1;
+    const uint32_t bytes = (uint32_t)(mE - s0) * 8u;
+    mbar_expect_tx(&bars[buf], bytes);
+    bulk_g2s(vbuf[buf] + s0, A + (long long)s * ld + s0, bytes, &bars[buf]);
+  };
+  if (threadIdx.x == 0 && r > 0) issue(0);
+  for (int s = 0; s < r; ++s) {
+    const int buf = s & 1;
+    if (threadIdx.x == 0 && s + 1 < r) issue(s + 1);
+    if (!mbar_wait(&bars[buf], (uint32_t)((s >> 1) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    if (own) {
+      const double* v = vbuf[buf];
+      double d = (lane == 0) ? col[s] : 0.0;
+      for (int i = s + 1 + lane; i < m; i += 32) d += v[i] * col[i];
+      d = warp_sum(d) * st[s];
+      if (lane == 0) col[s] -= d;
+      for (int i = s + 1 + lane; i < m; i += 32) col[i] -= d * v[i];
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    // the copy issued for the next reflector may still be in flight: wait for
+    // it (bounded) before the shared memory goes away
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < r; ++s) {
+        if (mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1))) continue;
+        if (s + 1 < r) mbar_wait(&bars[(s + 1) & 1], (uint32_t)(((s + 1) >> 1) & 1));
+        break;
+      }
+      atomicOr(a.info + b, 2);
+    }
+    return;
+  }
+
+  if (!a.solve) {
+    if (own) {
+      double* g = A + (long long)(n + c0 + w) * ld;
+      for (int i = lane; i < m; i += 32) g[i] = col[i];
+    }
+    return;
+  }
+  // back substitution R[0:r,0:r] x = (Q^T B)[0:r], R's columns staged in
+  // chunks (upper parts only, with the reciprocal diagonal) in the reflector
+  // buffers, consumed from the last column down
+  double* Rs = vbuf[0];
+  double* rinv = st;                      // tau is no longer needed
+  const int cap = 2 * ldE;
+  int j = r - 1;
+  while (j >= 0) {
+    int ch = 0, used = 0;
+    while (j - ch >= 0 && ch < a.nmax && used + (j - ch + 1) <= cap) { used += j - ch + 1; ++ch; }
+    __syncthreads();                       // previous chunk consumed
+    {
+      int off = 0;
+      for (int q = 0; q < ch; ++q) {
+        const int jj = j - q;
+        const double* rc = A + (long long)jj * ld;
+        for (int i = threadIdx.x; i <= jj; i += KT * 32) Rs[off + i] = rc[i];
+        off += jj + 1;
+      }
+      for (int q = threadIdx.x; q < ch; q += KT * 32) rinv[q] = 1.0 / A[(long long)(j - q) * ld + (j - q)];
+    }
+    __syncthreads();
+    if (own) {
+      int off = 0;
+      for (int q = 0; q < ch; ++q) {
+        const int jj = j - q;
+        __syncwarp();
+        const double xj = col[jj] * rinv[q];
+        __syncwarp();
+        for (int i = lane; i < jj; i += 32) col[i] -= xj * Rs[off + i];
+        if (lane == 0) col[jj] = xj;
+        off += jj + 1;
+      }
+    }
+    j -= ch;
+  }
+  __syncwarp();
+  if (own) {
+    double* xc = a.X + (long long)b * a.xstride + (long long)(c0 + w) * a.xld;
+    const int* pb = a.perm + (long long)b * a.permstride;
+    int bad = 0;
+    for (int i = lane; i < n; i += 32) {
+      const double v = (i < r) ? col[i] : 0.0;
+      if (!(v == v) || isinf(v)) bad = 1;
+      xc[pb[i]] = v;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.info + b, 1);
+  }
+}
+
+template <int T>
+int launch_qrcp(const Args& a0, int nb, size_t shm, int cs, cudaStream_t st) {
+  Args a = a0;
   a.cs = cs;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(q.nb * cs);
-  cfg.blockDim = dim3(QR_THREADS);
+  cfg.gridDim = dim3(nb * cs);
+  cfg.blockDim = dim3(T);
   cfg.dynamicSmemBytes = shm;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -286,8 +428,135 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cuda_failed(cudaLaunchKernelEx(&cfg, qrcp_kernel, a), "qrcp launch")) return LMFS_ERR_CUDA;
+  if (cuda_failed(cudaLaunchKernelEx(&cfg, qrcp_kernel<T>, a), "qrcp launch")) return LMFS_ERR_CUDA;
   return check_launch("qrcp_kernel");
+}
+
+// Clusters of this configuration that fit on the device at once (0 if none).
+template <int T>
+int active_clusters(int nb, size_t shm, int cs) {
+  if (shm > 48 * 1024 &&
+      cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb * cs);
+  cfg.blockDim = dim3(T);
+  cfg.dynamicSmemBytes = shm;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int act = 0;
+  if (cudaOccupancyMaxActiveClusters(&act, qrcp_kernel<T>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return act;
+}
+
+template <int KT>
+int launch_apply(const ArgsB& a, int nb, size_t shm, cudaStream_t st) {
+  if (shm > 48 * 1024 &&
+      cuda_failed(cudaFuncSetAttribute(apply_qt_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm),
+                  "apply_qt smem attribute"))
+    return LMFS_ERR_CUDA;
+  dim3 grid((a.k + KT - 1) / KT, nb);
+  apply_qt_kernel<KT><<<grid, KT * 32, shm, st>>>(a);
+  return check_launch("apply_qt_kernel");
+}
+
+template <int KT>
+int apply_blocks_per_sm(size_t shm) {
+  if (shm > 48 * 1024 &&
+      cudaFuncSetAttribute(apply_qt_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_qt_kernel<KT>, KT * 32, shm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+}  // namespace
+
+int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
+  if (q.nb <= 0) return LMFS_OK;
+  int sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+  // ---- factorization: choose the CTA size and cluster size that finish the
+  // batch soonest -- waves of resident clusters x the work each CTA carries
+  Args a;
+  a.A = q.A; a.mstride = q.mstride; a.m = q.m; a.n = q.n; a.ld = q.ld; a.eps = q.eps;
+  a.rank = q.rank; a.perm = q.perm; a.permstride = q.permstride; a.tau = q.tau; a.vn = q.vn;
+  a.info = q.info; a.cs = 1;
+  {
+    double best = 1e300;
+    int bt = 512, bcs = 1;
+    for (int T : {512, 1024}) {
+      const size_t shm = (size_t)q.ld * sizeof(double) + (T / 32) * (sizeof(double) + sizeof(int));
+      for (int cs = 1; cs <= 8; ++cs) {
+        const int act = (T == 512) ? active_clusters<512>(q.nb, shm, cs) : active_clusters<1024>(q.nb, shm, cs);
+        if (act <= 0) continue;
+        const int waves = (q.nb + act - 1) / act;
+        // a small charge per cluster member for the two cluster barriers per reflector
+        const double cost = waves / (double)(cs * T) * (1.0 + 0.02 * cs);
+        if (cost < best * (1.0 - 1e-9)) { best = cost; bt = T; bcs = cs; }
+      }
+    }
+    const size_t shm = (size_t)q.ld * sizeof(double) + (bt / 32) * (sizeof(double) + sizeof(int));
+    const int rc = (bt == 512) ? launch_qrcp<512>(a, q.nb, shm, bcs, st) : launch_qrcp<1024>(a, q.nb, shm, bcs, st);
+    if (rc) return rc;
+  }
+  if (q.k <= 0) return LMFS_OK;
+  // the reflector copies start at even rows of columns ld apart: 16-byte
+  // alignment needs an even ld and matrix stride and an aligned base
+  if ((q.ld & 1) || (q.mstride & 1) || ((uintptr_t)q.A & 15)) {
+    set_last_error("QR workspace not 16-byte aligned per column");
+    return LMFS_ERR_INVALID;
+  }
+
+  // ---- right-hand sides: tile width from shared-memory capacity and waves
+  ArgsB ab;
+  ab.A = q.A; ab.mstride = q.mstride; ab.m = q.m; ab.n = q.n; ab.k = q.k; ab.ld = q.ld;
+  ab.tau = q.tau; ab.permstride = q.permstride; ab.rank = q.rank; ab.perm = q.perm;
+  ab.X = q.X; ab.xld = q.xld; ab.xstride = q.xstride; ab.info = q.info; ab.solve = solve ? 1 : 0;
+  ab.nmax = q.nmax;
+  const int ldE = (q.ld + 1) & ~1;
+  auto shm_of = [&](int kt) { return ((size_t)(kt + 2) * ldE + (size_t)std::max(q.nmax, 1)) * sizeof(double); };
+  double best = 1e300;
+  int bkt = 0;
+  for (int kt : {8, 4, 2, 1}) {
+    const size_t shm = shm_of(kt);
+    if (shm > 226 * 1024) continue;          // leaves room for the static shared variables
+    const int cps = kt == 8 ? apply_blocks_per_sm<8>(shm) : kt == 4 ? apply_blocks_per_sm<4>(shm)
+                  : kt == 2 ? apply_blocks_per_sm<2>(shm) : apply_blocks_per_sm<1>(shm);
+    if (cps <= 0) continue;
+    const long long ctas = (long long)q.nb * ((q.k + kt - 1) / kt);
+    const long long waves = (ctas + (long long)sms * cps - 1) / ((long long)sms * cps);
+    // co-resident CTAs share one SM's FP64 pipe; a grid smaller than the
+    // device spreads one CTA per SM
+    const long long share = std::min<long long>(cps, (ctas + sms - 1) / sms);
+    const double cost = (double)waves * kt * share;
+    if (cost < best * (1.0 - 1e-9)) { best = cost; bkt = kt; }
+  }
+  if (!bkt) { set_last_error("right-hand-side tile does not fit in shared memory"); return LMFS_ERR_INVALID; }
+  const size_t shm = shm_of(bkt);
+  switch (bkt) {
+    case 8: return launch_apply<8>(ab, q.nb, shm, st);
+    case 4: return launch_apply<4>(ab, q.nb, shm, st);
+    case 2: return launch_apply<2>(ab, q.nb, shm, st);
+    default: return launch_apply<1>(ab, q.nb, shm, st);
+  }
 }
 
 }  // namespace lmfs
