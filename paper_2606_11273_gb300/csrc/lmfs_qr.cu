@@ -33,9 +33,17 @@
 namespace lmfs {
 namespace {
 
+// Warp sum, result in every lane.  A halving tree in which only the lanes
+// that keep a partial sum add: 31 FP64 lane operations instead of 5 x 32, which
+// matters where the FP64 pipe is the bottleneck (2 lane operations per clock
+// per SM on this part).
 __device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  const int lane = threadIdx.x & 31;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane < o) v += t;
+  }
+  return __shfl_sync(0xffffffffu, v, 0);
 }
 
 // Block-wide sum; every thread gets the result.  red: NW doubles.
@@ -283,73 +291,76 @@ struct ArgsB {
 };
 
 // Q^T B and the truncated solution for a tile of KT right-hand sides
-// (blockIdx.x) of matrix blockIdx.y; warp w owns right-hand side c0 + w.
-// Shared memory: the tile [KT][ldE], two reflector buffers [ldE], tau [nmax]
+// (blockIdx.x) of matrix blockIdx.y; warp w owns right-hand side c0 + w and
+// applies every reflector to it from shared memory.  Reflectors arrive by bulk
+// asynchronous copies into NBUF rotating buffers, NBUF - 1 reflectors ahead
+// of the one being applied (two buffers suffice: the sweep is FP64-bound).
+// Shared memory: the tile [KT][ldE], NBUF reflector buffers [ldE], tau [nmax]
 // (ldE = ld rounded up to even, so that every copy is 16-byte aligned).
-template <int KT>
+template <int KT, int NBUF>
 __global__ void __launch_bounds__(KT * 32) apply_qt_kernel(ArgsB a) {
+  constexpr int NT = KT * 32;
   extern __shared__ __align__(16) double bsm[];
   double* const smem = bsm;
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[NBUF];
   __shared__ int s_fail;
   const int b = blockIdx.y, c0 = blockIdx.x * KT;
   const int m = a.m[b], n = a.n[b], r = a.rank[b], ld = a.ld;
   const int ldE = (ld + 1) & ~1, mE = (m + 1) & ~1;
   const int kt = min(KT, a.k - c0);
   double* A = a.A + (long long)b * a.mstride;
-  double* Bs = smem;
-  double* vbuf[2] = {smem + (long long)KT * ldE, smem + (long long)(KT + 1) * ldE};
-  double* st = smem + (long long)(KT + 2) * ldE;
+  double* const Bs = smem;
+  double* const V0 = smem + (long long)KT * ldE;          // buffer q at V0 + q * ldE
+  double* const st = smem + (long long)(KT + NBUF) * ldE;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* col = Bs + (long long)w * ldE;
   const bool own = w < kt;
 
-  for (int i = threadIdx.x; i < r; i += KT * 32) st[i] = a.tau[(long long)b * a.permstride + i];
+  for (int i = threadIdx.x; i < r; i += NT) st[i] = a.tau[(long long)b * a.permstride + i];
   if (own) {
     const double* g = A + (long long)(n + c0 + w) * ld;
     for (int i = lane; i < m; i += 32) col[i] = g[i];
   }
   if (threadIdx.x == 0) {
-    s_fail = 0;
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    s_fail = -1;
+    for (int q = 0; q < NBUF; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
   // reflector s: rows s..m-1 of column s (row s is R_ss; the unit entry of v
   // is applied explicitly), copied from the even row at or below s
   auto issue = [&](int s) {
-    const int s0 = s & ~1, buf = s & 1;
+    const int s0 = s & ~1, q = s % NBUF;
     const uint32_t bytes = (uint32_t)(mE - s0) * 8u;
-    mbar_expect_tx(&bars[buf], bytes);
-    bulk_g2s(vbuf[buf] + s0, A + (long long)s * ld + s0, bytes, &bars[buf]);
+    mbar_expect_tx(&bars[q], bytes);
+    bulk_g2s(V0 + (long long)q * ldE + s0, A + (long long)s * ld + s0, bytes, &bars[q]);
   };
-  if (threadIdx.x == 0 && r > 0) issue(0);
+  if (threadIdx.x == 0)
+    for (int s = 0; s < NBUF - 1 && s < r; ++s) issue(s);
   for (int s = 0; s < r; ++s) {
-    const int buf = s & 1;
-    if (threadIdx.x == 0 && s + 1 < r) issue(s + 1);
-    if (!mbar_wait(&bars[buf], (uint32_t)((s >> 1) & 1))) s_fail = 1;
+    const int q = s % NBUF;
+    // the buffer of reflector s + NBUF - 1 held reflector s - 1, whose
+    // readers all passed the barrier that ended the previous step
+    if (threadIdx.x == 0 && s + NBUF - 1 < r) issue(s + NBUF - 1);
+    if (!mbar_wait(&bars[q], (uint32_t)((s / NBUF) & 1))) s_fail = s;
     __syncthreads();
-    if (s_fail) break;
+    if (s_fail >= 0) break;
     if (own) {
-      const double* v = vbuf[buf];
+      const double* v = V0 + (long long)q * ldE;
       double d = (lane == 0) ? col[s] : 0.0;
       for (int i = s + 1 + lane; i < m; i += 32) d += v[i] * col[i];
-      d = warp_sum(d) * st[s];
+      d = warp_sum(d);
+      d = __shfl_sync(0xffffffffu, (lane == 0) ? d * st[s] : 0.0, 0);
       if (lane == 0) col[s] -= d;
       for (int i = s + 1 + lane; i < m; i += 32) col[i] -= d * v[i];
     }
     __syncthreads();
   }
-  if (s_fail) {
-    // the copy issued for the next reflector may still be in flight: wait for
-    // it (bounded) before the shared memory goes away
+  if (s_fail >= 0) {
+    // copies issued for reflectors s_fail .. s_fail + NBUF - 1 may still be in
+    // flight: wait for each (bounded) before the shared memory goes away
     if (threadIdx.x == 0) {
-      for (int s = 0; s < r; ++s) {
-        if (mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1))) continue;
-        if (s + 1 < r) mbar_wait(&bars[(s + 1) & 1], (uint32_t)(((s + 1) >> 1) & 1));
-        break;
-      }
+      for (int t = s_fail; t < r && t < s_fail + NBUF; ++t) mbar_wait(&bars[t % NBUF], (uint32_t)((t / NBUF) & 1));
       atomicOr(a.info + b, 2);
     }
     return;
@@ -365,9 +376,9 @@ __global__ void __launch_bounds__(KT * 32) apply_qt_kernel(ArgsB a) {
   // back substitution R[0:r,0:r] x = (Q^T B)[0:r], R's columns staged in
   // chunks (upper parts only, with the reciprocal diagonal) in the reflector
   // buffers, consumed from the last column down
-  double* Rs = vbuf[0];
+  double* Rs = V0;
   double* rinv = st;                      // tau is no longer needed
-  const int cap = 2 * ldE;
+  const int cap = NBUF * ldE;
   int j = r - 1;
   while (j >= 0) {
     int ch = 0, used = 0;
@@ -378,10 +389,10 @@ __global__ void __launch_bounds__(KT * 32) apply_qt_kernel(ArgsB a) {
       for (int q = 0; q < ch; ++q) {
         const int jj = j - q;
         const double* rc = A + (long long)jj * ld;
-        for (int i = threadIdx.x; i <= jj; i += KT * 32) Rs[off + i] = rc[i];
+        for (int i = threadIdx.x; i <= jj; i += NT) Rs[off + i] = rc[i];
         off += jj + 1;
       }
-      for (int q = threadIdx.x; q < ch; q += KT * 32) rinv[q] = 1.0 / A[(long long)(j - q) * ld + (j - q)];
+      for (int q = threadIdx.x; q < ch; q += NT) rinv[q] = 1.0 / A[(long long)(j - q) * ld + (j - q)];
     }
     __syncthreads();
     if (own) {
@@ -459,30 +470,49 @@ int active_clusters(int nb, size_t shm, int cs) {
   return act;
 }
 
-template <int KT>
+template <int KT, int NB>
 int launch_apply(const ArgsB& a, int nb, size_t shm, cudaStream_t st) {
   if (shm > 48 * 1024 &&
-      cuda_failed(cudaFuncSetAttribute(apply_qt_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm),
+      cuda_failed(cudaFuncSetAttribute(apply_qt_kernel<KT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm),
                   "apply_qt smem attribute"))
     return LMFS_ERR_CUDA;
   dim3 grid((a.k + KT - 1) / KT, nb);
-  apply_qt_kernel<KT><<<grid, KT * 32, shm, st>>>(a);
+  apply_qt_kernel<KT, NB><<<grid, KT * 32, shm, st>>>(a);
   return check_launch("apply_qt_kernel");
 }
 
-template <int KT>
+template <int KT, int NB>
 int apply_blocks_per_sm(size_t shm) {
   if (shm > 48 * 1024 &&
-      cudaFuncSetAttribute(apply_qt_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+      cudaFuncSetAttribute(apply_qt_kernel<KT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_qt_kernel<KT>, KT * 32, shm) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, apply_qt_kernel<KT, NB>, KT * 32, shm) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n;
+}
+
+// The (KT, NBUF) instantiations the host chooses from.
+struct ApplyCfg { int kt, nbuf; };
+constexpr ApplyCfg kApplyCfgs[] = {{8, 2}, {6, 2}, {4, 2}, {2, 2}, {1, 2}};
+
+template <int KT, int NB>
+int apply_dispatch(int kt, int nbuf, bool launch, const ArgsB& a, int nb, size_t shm, cudaStream_t st) {
+  if (kt == KT && nbuf == NB) return launch ? launch_apply<KT, NB>(a, nb, shm, st) : apply_blocks_per_sm<KT, NB>(shm);
+  return -1000;
+}
+
+// Occupancy (launch = false) or launch (launch = true) of instantiation (kt, nbuf).
+int apply_call(int kt, int nbuf, bool launch, const ArgsB& a, int nb, size_t shm, cudaStream_t st) {
+  int rc = -1000;
+#define LMFS_APPLY(K, V) if (rc == -1000) rc = apply_dispatch<K, V>(kt, nbuf, launch, a, nb, shm, st);
+  LMFS_APPLY(8, 2) LMFS_APPLY(6, 2) LMFS_APPLY(4, 2) LMFS_APPLY(2, 2) LMFS_APPLY(1, 2)
+#undef LMFS_APPLY
+  return rc == -1000 ? (launch ? LMFS_ERR_INVALID : 0) : rc;
 }
 
 }  // namespace
@@ -532,31 +562,28 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   ab.X = q.X; ab.xld = q.xld; ab.xstride = q.xstride; ab.info = q.info; ab.solve = solve ? 1 : 0;
   ab.nmax = q.nmax;
   const int ldE = (q.ld + 1) & ~1;
-  auto shm_of = [&](int kt) { return ((size_t)(kt + 2) * ldE + (size_t)std::max(q.nmax, 1)) * sizeof(double); };
+  auto shm_of = [&](const ApplyCfg& g) {
+    return ((size_t)(g.kt + g.nbuf) * ldE + (size_t)std::max(q.nmax, 1)) * sizeof(double);
+  };
+  // The sweep is bound by the SM's FP64 pipe once about eight warps (columns)
+  // share an SM (measured: 77 % pipe-busy at six, saturating near eight);
+  // below that a CTA takes the same time whatever its width.  Cost: waves x
+  // the larger of 8 and the columns sharing an SM.
   double best = 1e300;
-  int bkt = 0;
-  for (int kt : {8, 4, 2, 1}) {
-    const size_t shm = shm_of(kt);
+  ApplyCfg pick{0, 0};
+  for (const ApplyCfg& g : kApplyCfgs) {
+    const size_t shm = shm_of(g);
     if (shm > 226 * 1024) continue;          // leaves room for the static shared variables
-    const int cps = kt == 8 ? apply_blocks_per_sm<8>(shm) : kt == 4 ? apply_blocks_per_sm<4>(shm)
-                  : kt == 2 ? apply_blocks_per_sm<2>(shm) : apply_blocks_per_sm<1>(shm);
+    const int cps = apply_call(g.kt, g.nbuf, false, ab, q.nb, shm, st);
     if (cps <= 0) continue;
-    const long long ctas = (long long)q.nb * ((q.k + kt - 1) / kt);
+    const long long ctas = (long long)q.nb * ((q.k + g.kt - 1) / g.kt);
     const long long waves = (ctas + (long long)sms * cps - 1) / ((long long)sms * cps);
-    // co-resident CTAs share one SM's FP64 pipe; a grid smaller than the
-    // device spreads one CTA per SM
     const long long share = std::min<long long>(cps, (ctas + sms - 1) / sms);
-    const double cost = (double)waves * kt * share;
-    if (cost < best * (1.0 - 1e-9)) { best = cost; bkt = kt; }
+    const double cost = (double)waves * std::max(8.0, (double)(g.kt * share));
+    if (cost < best * (1.0 - 1e-9)) { best = cost; pick = g; }
   }
-  if (!bkt) { set_last_error("right-hand-side tile does not fit in shared memory"); return LMFS_ERR_INVALID; }
-  const size_t shm = shm_of(bkt);
-  switch (bkt) {
-    case 8: return launch_apply<8>(ab, q.nb, shm, st);
-    case 4: return launch_apply<4>(ab, q.nb, shm, st);
-    case 2: return launch_apply<2>(ab, q.nb, shm, st);
-    default: return launch_apply<1>(ab, q.nb, shm, st);
-  }
+  if (!pick.kt) { set_last_error("right-hand-side tile does not fit in shared memory"); return LMFS_ERR_INVALID; }
+  return apply_call(pick.kt, pick.nbuf, true, ab, q.nb, shm_of(pick), st);
 }
 
 }  // namespace lmfs
