@@ -223,34 +223,65 @@ __global__ void __launch_bounds__(T) qrcp_kernel(Args q) {
       double* c2 = A + (long long)(two ? j2 : j) * ld;
       const double n1 = __ldcg(vn1 + j), r1 = __ldcg(vn2 + j);
       const double n2 = two ? __ldcg(vn1 + j2) : 0.0, r2 = two ? __ldcg(vn2 + j2) : 0.0;
+      // four rows per lane and step: eight independent L2 loads in flight
       double d1 = 0.0, d2 = 0.0;
       if (two) {
-        for (int i = s + lane; i < m; i += 32) {
-          const double vi = sv[i];
-          const double a1 = __ldcg(c1 + i), a2 = __ldcg(c2 + i);
-          d1 += vi * a1;
-          d2 += vi * a2;
+        double e1 = 0.0, e2 = 0.0;
+        int i = s + lane;
+        for (; i + 96 < m; i += 128) {
+          const double a0 = __ldcg(c1 + i), a1 = __ldcg(c1 + i + 32), a2 = __ldcg(c1 + i + 64), a3 = __ldcg(c1 + i + 96);
+          const double b0 = __ldcg(c2 + i), b1 = __ldcg(c2 + i + 32), b2 = __ldcg(c2 + i + 64), b3 = __ldcg(c2 + i + 96);
+          const double v0 = sv[i], v1 = sv[i + 32], v2 = sv[i + 64], v3 = sv[i + 96];
+          d1 += v0 * a0; e1 += v1 * a1; d2 += v0 * b0; e2 += v1 * b1;
+          d1 += v2 * a2; e1 += v3 * a3; d2 += v2 * b2; e2 += v3 * b3;
         }
+        for (; i < m; i += 32) { const double vi = sv[i]; d1 += vi * __ldcg(c1 + i); d2 += vi * __ldcg(c2 + i); }
+        d1 += e1;
+        d2 += e2;
       } else {
-        for (int i = s + lane; i < m; i += 32) d1 += sv[i] * __ldcg(c1 + i);
+        double e1 = 0.0;
+        int i = s + lane;
+        for (; i + 96 < m; i += 128) {
+          const double a0 = __ldcg(c1 + i), a1 = __ldcg(c1 + i + 32), a2 = __ldcg(c1 + i + 64), a3 = __ldcg(c1 + i + 96);
+          d1 += sv[i] * a0; e1 += sv[i + 32] * a1; d1 += sv[i + 64] * a2; e1 += sv[i + 96] * a3;
+        }
+        for (; i < m; i += 32) d1 += sv[i] * __ldcg(c1 + i);
+        d1 += e1;
       }
       d1 = warp_sum(d1) * tau;
       d2 = two ? warp_sum(d2) * tau : 0.0;
-      double as1 = 0.0, as2 = 0.0;             // updated A[s, j] (lane 0 holds row s)
+      // row s is lane 0's first row: its updated value feeds the norm downdate
+      double as1 = 0.0, as2 = 0.0;
       if (two) {
-        for (int i = s + lane; i < m; i += 32) {
+        int i = s + lane;
+        for (; i + 96 < m; i += 128) {
+          const double a0 = __ldcg(c1 + i), a1 = __ldcg(c1 + i + 32), a2 = __ldcg(c1 + i + 64), a3 = __ldcg(c1 + i + 96);
+          const double b0 = __ldcg(c2 + i), b1 = __ldcg(c2 + i + 32), b2 = __ldcg(c2 + i + 64), b3 = __ldcg(c2 + i + 96);
+          const double v0 = sv[i], v1 = sv[i + 32], v2 = sv[i + 64], v3 = sv[i + 96];
+          const double x0 = a0 - d1 * v0, y0 = b0 - d2 * v0;
+          c1[i] = x0; c1[i + 32] = a1 - d1 * v1; c1[i + 64] = a2 - d1 * v2; c1[i + 96] = a3 - d1 * v3;
+          c2[i] = y0; c2[i + 32] = b1 - d2 * v1; c2[i + 64] = b2 - d2 * v2; c2[i + 96] = b3 - d2 * v3;
+          if (i == s) { as1 = x0; as2 = y0; }
+        }
+        for (; i < m; i += 32) {
           const double vi = sv[i];
-          const double a1 = __ldcg(c1 + i) - d1 * vi;
-          const double a2 = __ldcg(c2 + i) - d2 * vi;
-          c1[i] = a1;
-          c2[i] = a2;
-          if (i == s) { as1 = a1; as2 = a2; }
+          const double x0 = __ldcg(c1 + i) - d1 * vi, y0 = __ldcg(c2 + i) - d2 * vi;
+          c1[i] = x0;
+          c2[i] = y0;
+          if (i == s) { as1 = x0; as2 = y0; }
         }
       } else {
-        for (int i = s + lane; i < m; i += 32) {
-          const double a1 = __ldcg(c1 + i) - d1 * sv[i];
-          c1[i] = a1;
-          if (i == s) as1 = a1;
+        int i = s + lane;
+        for (; i + 96 < m; i += 128) {
+          const double a0 = __ldcg(c1 + i), a1 = __ldcg(c1 + i + 32), a2 = __ldcg(c1 + i + 64), a3 = __ldcg(c1 + i + 96);
+          const double x0 = a0 - d1 * sv[i];
+          c1[i] = x0; c1[i + 32] = a1 - d1 * sv[i + 32]; c1[i + 64] = a2 - d1 * sv[i + 64]; c1[i + 96] = a3 - d1 * sv[i + 96];
+          if (i == s) as1 = x0;
+        }
+        for (; i < m; i += 32) {
+          const double x0 = __ldcg(c1 + i) - d1 * sv[i];
+          c1[i] = x0;
+          if (i == s) as1 = x0;
         }
       }
       as1 = __shfl_sync(0xffffffffu, as1, 0);
@@ -530,21 +561,23 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   a.rank = q.rank; a.perm = q.perm; a.permstride = q.permstride; a.tau = q.tau; a.vn = q.vn;
   a.info = q.info; a.cs = 1;
   {
+    // 512-thread CTAs (two per SM); cluster size from the resident-cluster
+    // count: waves of clusters x the work each CTA carries, a small charge per
+    // member for the two cluster barriers per reflector, and at least two
+    // columns per warp
+    constexpr int T = 512;
+    const size_t shm = (size_t)q.ld * sizeof(double) + (T / 32) * (sizeof(double) + sizeof(int));
+    const int csmax = std::max(1, std::min(8, q.nmax / (2 * (T / 32))));
     double best = 1e300;
-    int bt = 512, bcs = 1;
-    for (int T : {512, 1024}) {
-      const size_t shm = (size_t)q.ld * sizeof(double) + (T / 32) * (sizeof(double) + sizeof(int));
-      for (int cs = 1; cs <= 8; ++cs) {
-        const int act = (T == 512) ? active_clusters<512>(q.nb, shm, cs) : active_clusters<1024>(q.nb, shm, cs);
-        if (act <= 0) continue;
-        const int waves = (q.nb + act - 1) / act;
-        // a small charge per cluster member for the two cluster barriers per reflector
-        const double cost = waves / (double)(cs * T) * (1.0 + 0.02 * cs);
-        if (cost < best * (1.0 - 1e-9)) { best = cost; bt = T; bcs = cs; }
-      }
+    int bcs = 1;
+    for (int cs = 1; cs <= csmax; ++cs) {
+      const int act = active_clusters<T>(q.nb, shm, cs);
+      if (act <= 0) continue;
+      const int waves = (q.nb + act - 1) / act;
+      const double cost = waves / (double)cs * (1.0 + 0.02 * cs);
+      if (cost < best * (1.0 - 1e-9)) { best = cost; bcs = cs; }
     }
-    const size_t shm = (size_t)q.ld * sizeof(double) + (bt / 32) * (sizeof(double) + sizeof(int));
-    const int rc = (bt == 512) ? launch_qrcp<512>(a, q.nb, shm, bcs, st) : launch_qrcp<1024>(a, q.nb, shm, bcs, st);
+    const int rc = launch_qrcp<T>(a, q.nb, shm, bcs, st);
     if (rc) return rc;
   }
   if (q.k <= 0) return LMFS_OK;
