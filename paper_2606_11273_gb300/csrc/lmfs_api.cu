@@ -277,7 +277,7 @@ int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double*
   if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
   const int ns = 2 * c.d.Nc, nn = 2 * c.d.Mc, nc = pb.ob.nclass;
   if (!pb.ob.V) LMFS_TRY(dalloc(&pb.ob.V, (size_t)nc * ns * ns));
-  // W = U^T rows, R = diag(sigma) (the back substitution divides by sigma), V dense
+  // W = U^T rows, R = diag(sigma) (the back substitution scales by 1/sigma), V dense
   std::vector<double> R((size_t)nc * ns * ns, 0.0);
   std::vector<int> perm((size_t)nc * ns), rk(rank, rank + nc);
   for (int q = 0; q < nc; ++q) {
@@ -287,7 +287,13 @@ int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double*
       perm[(size_t)q * ns + j] = j;
     }
   }
-  LMFS_CUDA(cudaMemcpyAsync(pb.ob.W, Ut, (size_t)nc * ns * nn * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  // the device keeps W column by column (Wt[col][row])
+  std::vector<double> Wt((size_t)nc * ns * nn);
+  for (int q = 0; q < nc; ++q)
+    for (int row = 0; row < ns; ++row)
+      for (int col = 0; col < nn; ++col)
+        Wt[(size_t)q * ns * nn + (size_t)col * ns + row] = Ut[(size_t)q * ns * nn + (size_t)row * nn + col];
+  LMFS_CUDA(cudaMemcpyAsync(pb.ob.W, Wt.data(), Wt.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   LMFS_CUDA(cudaMemcpyAsync(pb.ob.R, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   LMFS_CUDA(cudaMemcpyAsync(pb.ob.V, V, (size_t)nc * ns * ns * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   LMFS_CUDA(cudaMemcpyAsync(pb.ob.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));

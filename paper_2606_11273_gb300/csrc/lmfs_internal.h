@@ -40,7 +40,7 @@ struct Dims {
 // ---- one-body factors (per radius class) ---------------------------------
 struct OneBody {
   int nclass = 0;
-  double* W = nullptr;     // [nclass][2Nc][2Mc]
+  double* W = nullptr;     // [nclass][2Mc][2Nc]: Q^T rows stored column by column
   double* R = nullptr;     // [nclass][2Nc][2Nc] column-major
   int* perm = nullptr;     // [nclass][2Nc]
   int* rank = nullptr;     // [nclass]

@@ -31,79 +31,68 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// ---- Step 1a: lam_bar = Pi^+ mu, per disk, one warp per disk ----------------
-// Pi^+ applied from its QR factors: t = W mu (W = first r rows of Q^T),
-// R[0:r,0:r] z = t (back substitution), lam_bar[perm[j]] = z_j.
-__global__ void onebody_apply_kernel(const double* __restrict__ W, const double* __restrict__ R,
+// Warp sum into every lane where only the lanes keeping a partial sum add
+// (31 FP64 lane operations instead of 5 x 32).
+__device__ __forceinline__ double lsum(double v) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane < o) v += t;
+  }
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// ---- Step 1a: lam_bar = Pi^+ mu, one block per disk, one thread per row ----
+// Pi^+ applied from its QR factors: t = W mu (W = first r rows of Q^T, stored
+// column by column, Wt[col][row], so that the rows read together are
+// contiguous), R[0:r,0:r] z = t (column-oriented back substitution, one barrier
+// per column), lam_bar[perm[j]] = z_j.  With imported SVD factors (V set),
+// lam_bar = V z instead.
+__global__ void onebody_apply_kernel(const double* __restrict__ Wt, const double* __restrict__ R,
                                      const int* __restrict__ perm, const int* __restrict__ rank,
                                      const double* __restrict__ V, const int* __restrict__ cls, int P,
                                      int Nc, int Mc, const double* __restrict__ mu, double* __restrict__ lb) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= P) return;
-  const int i = warp, c = cls[i];
+  extern __shared__ double osm[];   // mu_i [nn], t [ns], 1/R_jj [ns], x [ns]
+  const int i = blockIdx.x, c = cls[i];
   const int ns = 2 * Nc, nn = 2 * Mc, r = rank[c];
-  const double* Wc = W + (long long)c * ns * nn;
+  const int row = threadIdx.x;
+  const double* Wc = Wt + (long long)c * ns * nn;
   const double* Rc = R + (long long)c * ns * ns;
-  const int* pc = perm + (long long)c * ns;
-  const double* m = mu + (long long)i * nn;
-  constexpr int RPL = 8;  // rows per lane: supports 2Nc <= 256
-  double t[RPL];
-#pragma unroll
-  for (int q = 0; q < RPL; ++q) {
-    const int row = lane + 32 * q;
-    double acc = 0.0;
-    if (row < r) {
-      const double* wr = Wc + (long long)row * nn;
-      for (int col = 0; col < nn; ++col) acc += wr[col] * m[col];
+  double* ms = osm;
+  double* ts = ms + nn;
+  double* ri = ts + ns;
+  double* xs = ri + ns;
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) ms[q] = mu[(long long)i * nn + q];
+  __syncthreads();
+  if (row < r) {
+    double a0 = 0.0, a1 = 0.0;
+    int col = 0;
+    for (; col + 1 < nn; col += 2) {
+      a0 += Wc[(long long)col * ns + row] * ms[col];
+      a1 += Wc[(long long)(col + 1) * ns + row] * ms[col + 1];
     }
-    t[q] = acc;
+    if (col < nn) a0 += Wc[(long long)col * ns + row] * ms[col];
+    ts[row] = a0 + a1;
+    ri[row] = 1.0 / Rc[(long long)row * ns + row];
   }
-  // column-oriented back substitution; row j lives in lane j%32, slot j/32
   for (int j = r - 1; j >= 0; --j) {
-    const int owner = j & 31, slot = j >> 5;
-    double tj = 0.0;
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) if (q == slot) tj = t[q];
-    tj = __shfl_sync(0xffffffffu, tj, owner);
-    const double* rj = Rc + (long long)j * ns;
-    const double xj = tj / rj[j];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const int row = lane + 32 * q;
-      if (row < j) t[q] -= xj * rj[row];
-      if (row == j) t[q] = xj;
-    }
+    __syncthreads();                     // t_j final, x_{j+1} written
+    const double xj = ts[j] * ri[j];
+    if (row < j) ts[row] -= xj * Rc[(long long)j * ns + row];
+    else if (row == j) xs[j] = xj;
   }
+  __syncthreads();
   double* out = lb + (long long)i * ns;
+  if (row >= ns) return;
   if (V) {
-    // imported factors of the form V Sigma^+ U^T: lam_bar = V z (z_j = t_j, j < r)
+    // imported factors of the form V Sigma^+ U^T
     const double* Vc = V + (long long)c * ns * ns;
-    double acc[RPL];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) acc[q] = 0.0;
-    for (int j = 0; j < r; ++j) {
-      double zj = 0.0;
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) if (q == (j >> 5)) zj = t[q];
-      zj = __shfl_sync(0xffffffffu, zj, j & 31);
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        const int row = lane + 32 * q;
-        if (row < ns) acc[q] += Vc[(long long)row * ns + j] * zj;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const int row = lane + 32 * q;
-      if (row < ns) out[row] = acc[q];
-    }
+    double acc = 0.0;
+    for (int j = 0; j < r; ++j) acc += Vc[(long long)row * ns + j] * xs[j];
+    out[row] = acc;
     return;
   }
-#pragma unroll
-  for (int q = 0; q < RPL; ++q) {
-    const int row = lane + 32 * q;
-    if (row < ns) out[pc[row]] = (row < r) ? t[q] : 0.0;
-  }
+  out[perm[(long long)c * ns + row]] = (row < r) ? xs[row] : 0.0;
 }
 
 // ---- Step 1b: lam~ = A [lam_bar_i; lam_bar_k] per close pair ----------------
@@ -481,14 +470,18 @@ constexpr int MP_P = 32;
 constexpr int MP_NCOEF = 104;   // 3P + 5 = 101, padded to a multiple of 4
 
 // P2M: one warp per disk (moments in FP64).
-__global__ void p2m_kernel(const double* __restrict__ s, int P, int Nc, const double* __restrict__ radii,
-                           double Rc, double2* __restrict__ coef, float2* __restrict__ coef32) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= P) return;
-  const int i = warp;
+__global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, int P, int Nc,
+                                                  const double* __restrict__ radii, double Rc,
+                                                  double2* __restrict__ coef, float2* __restrict__ coef32) {
+  // one block per disk; warp g forms the moments of orders n = g, g + 4, ...
+  __shared__ double mom[MP_P + 1][6];     // A_n, B_n, D_n (complex)
+  __shared__ double2 cf[MP_NCOEF];
+  __shared__ double bnd[MP_P + 1];
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const double rs = radii[i] * Rc;
-  constexpr int SPL = 4;
-  double fr[SPL], fi[SPL], wr[SPL], wi[SPL], pr[SPL], pi_[SPL], qr[SPL], qi[SPL];
+  constexpr int SPL = 4;                  // sources per lane: Nc <= 128
+  double fr[SPL], fi[SPL], wr[SPL], wi[SPL], pr[SPL], pi_[SPL], sr[SPL], si[SPL];
 #pragma unroll
   for (int q = 0; q < SPL; ++q) {
     const int j = lane + 32 * q;
@@ -499,61 +492,75 @@ __global__ void p2m_kernel(const double* __restrict__ s, int P, int Nc, const do
       const double ph = 2.0 * LMFS_PI * j / Nc;
       wr[q] = rs * cos(ph); wi[q] = rs * sin(ph);
     }
-    pr[q] = 1.0; pi_[q] = 0.0;   // w^n
-    qr[q] = 1.0; qi[q] = 0.0;   // conj(w)^n
+    pr[q] = 1.0; pi_[q] = 0.0;            // p = w^g
+    for (int k = 0; k < g; ++k) {
+      const double a = pr[q] * wr[q] - pi_[q] * wi[q], b = pr[q] * wi[q] + pi_[q] * wr[q];
+      pr[q] = a; pi_[q] = b;
+    }
+    const double w2r = wr[q] * wr[q] - wi[q] * wi[q], w2i = 2.0 * wr[q] * wi[q];
+    sr[q] = w2r * w2r - w2i * w2i; si[q] = 2.0 * w2r * w2i;   // step w^4
   }
-  double2* out = coef + (long long)i * MP_NCOEF;
-  double Dprev_r = 0, Dprev_i = 0;
-  double bound = 0.0, rpow = 1.0;   // max |c_n| / rho^n
-  for (int n = 0; n <= MP_P; ++n) {
+  for (int n = g; n <= MP_P; n += 4) {
     double Ar = 0, Ai = 0, Br = 0, Bi = 0, Dr = 0, Di = 0;
 #pragma unroll
     for (int q = 0; q < SPL; ++q) {
-      // A: f w^n ; B: f conj(w)^n ; D: conj(f) w conj(w)^n
+      // A: f w^n;  B: f conj(w^n);  D: conj(f) w conj(w^n)
       Ar += fr[q] * pr[q] - fi[q] * pi_[q];
       Ai += fr[q] * pi_[q] + fi[q] * pr[q];
-      Br += fr[q] * qr[q] - fi[q] * qi[q];
-      Bi += fr[q] * qi[q] + fi[q] * qr[q];
-      const double tr = wr[q] * qr[q] - wi[q] * qi[q], ti = wr[q] * qi[q] + wi[q] * qr[q];  // w conj(w)^n
+      Br += fr[q] * pr[q] + fi[q] * pi_[q];
+      Bi += fi[q] * pr[q] - fr[q] * pi_[q];
+      const double tr = wr[q] * pr[q] + wi[q] * pi_[q], ti = wi[q] * pr[q] - wr[q] * pi_[q];
       Dr += fr[q] * tr + fi[q] * ti;
       Di += fr[q] * ti - fi[q] * tr;
     }
-    Ar = wsum(Ar); Ai = wsum(Ai); Br = wsum(Br); Bi = wsum(Bi); Dr = wsum(Dr); Di = wsum(Di);
+    Ar = lsum(Ar); Ai = lsum(Ai); Br = lsum(Br); Bi = lsum(Bi); Dr = lsum(Dr); Di = lsum(Di);
     if (lane == 0) {
-      if (n == 0) {
-        out[0] = make_double2(Ar, Ai);
-      } else {
-        const double2 an = make_double2(Ar / (2.0 * n), Ai / (2.0 * n));
-        const double2 gn = make_double2(Br / (2.0 * n) - 0.5 * Dprev_r, Bi / (2.0 * n) - 0.5 * Dprev_i);
-        out[2 * n] = an;
-        out[2 * n + 1] = gn;
-        bound = fmax(bound, fmax(hypot(an.x, an.y), hypot(gn.x, gn.y)) / rpow);
-      }
-      out[2 * (MP_P + 2) + n] = make_double2(Ar, -Ai);
-      bound = fmax(bound, hypot(Ar, Ai) * rs / (rpow * rs));   // |h_n| <= B rho^n
-      if (n == MP_P) {
-        out[2 * (MP_P + 1)] = make_double2(0.0, 0.0);
-        const double2 gl = make_double2(-0.5 * Dr, -0.5 * Di);
-        out[2 * (MP_P + 1) + 1] = gl;
-        bound = fmax(bound, hypot(gl.x, gl.y) / (rpow * rs));
-      }
+      mom[n][0] = Ar; mom[n][1] = Ai; mom[n][2] = Br; mom[n][3] = Bi; mom[n][4] = Dr; mom[n][5] = Di;
     }
-    rpow *= rs;
-    Dprev_r = Dr; Dprev_i = Di;
 #pragma unroll
     for (int q = 0; q < SPL; ++q) {
-      const double npr = pr[q] * wr[q] - pi_[q] * wi[q], npi = pr[q] * wi[q] + pi_[q] * wr[q];
-      const double nqr = qr[q] * wr[q] + qi[q] * wi[q], nqi = qi[q] * wr[q] - qr[q] * wi[q];
-      pr[q] = npr; pi_[q] = npi; qr[q] = nqr; qi[q] = nqi;
+      const double a = pr[q] * sr[q] - pi_[q] * si[q], b = pr[q] * si[q] + pi_[q] * sr[q];
+      pr[q] = a; pi_[q] = b;
     }
   }
-  if (lane == 0) out[1] = make_double2(bound, rs);
-  __syncwarp();
-  if (coef32) {
-    for (int c = lane; c < MP_NCOEF; c += 32) {
-      const double2 v = (c < 3 * MP_P + 5) ? out[c] : make_double2(0.0, 0.0);
-      coef32[(long long)i * MP_NCOEF + c] = make_float2((float)v.x, (float)v.y);
+  __syncthreads();
+  // coefficients a_n = A_n / 2n, g_n = B_n / 2n - D_{n-1} / 2, h_n = conj(A_n)
+  // and the bound B >= |c_n| / rho^n over all of them
+  const int n = threadIdx.x;
+  if (n <= MP_P) {
+    const double Ar = mom[n][0], Ai = mom[n][1];
+    const double rp = pow(rs, (double)n);
+    double b = sqrt(Ar * Ar + Ai * Ai) / rp;
+    if (n == 0) {
+      cf[0] = make_double2(Ar, Ai);
+    } else {
+      const double2 an = make_double2(Ar / (2.0 * n), Ai / (2.0 * n));
+      const double2 gn = make_double2(mom[n][2] / (2.0 * n) - 0.5 * mom[n - 1][4],
+                                      mom[n][3] / (2.0 * n) - 0.5 * mom[n - 1][5]);
+      cf[2 * n] = an;
+      cf[2 * n + 1] = gn;
+      b = fmax(b, fmax(sqrt(an.x * an.x + an.y * an.y), sqrt(gn.x * gn.x + gn.y * gn.y)) / rp);
     }
+    cf[2 * (MP_P + 2) + n] = make_double2(Ar, -Ai);
+    if (n == MP_P) {
+      cf[2 * (MP_P + 1)] = make_double2(0.0, 0.0);
+      const double2 gl = make_double2(-0.5 * mom[n][4], -0.5 * mom[n][5]);
+      cf[2 * (MP_P + 1) + 1] = gl;
+      b = fmax(b, sqrt(gl.x * gl.x + gl.y * gl.y) / (rp * rs));
+    }
+    bnd[n] = b;
+  }
+  for (int c = 3 * MP_P + 5 + threadIdx.x; c < MP_NCOEF; c += blockDim.x) cf[c] = make_double2(0.0, 0.0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double B = 0.0;
+    for (int k = 0; k <= MP_P; ++k) B = fmax(B, bnd[k]);
+    cf[1] = make_double2(B, rs);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < MP_NCOEF; c += blockDim.x) {
+    coef[(long long)i * MP_NCOEF + c] = cf[c];
+    if (coef32) coef32[(long long)i * MP_NCOEF + c] = make_float2((float)cf[c].x, (float)cf[c].y);
   }
 }
 
@@ -766,22 +773,27 @@ __global__ void reduce_splits(const double* part, long long stride, int nsplit, 
 }
 
 // ---- near field (FP64) + assembly ------------------------------------------
-// One block per target disk i.  mode 0 (matvec): u_i = mu_i + ufar_i +
-//   sum over near entries (regular: sig_k; close partner: proj_k(lam_k -
-//   lam_bar_k - lam~ of the pair with i)); self entries skipped.
+// One block per target disk i, blockDim = G x Mt threads: thread (g, m) takes
+// target node m and the sources j in [g Nc / G, (g + 1) Nc / G) of every near
+// entry; the G partial sums are combined in a fixed order at the end.
+// mode 0 (matvec): u_i = mu_i + ufar_i + sum over near entries (regular:
+//   sig_k; close partner: proj_k(lam_k - lam_bar_k - lam~ of the pair with
+//   i)); self entries skipped.
 // mode 1 (completion flow, eq. (u0_def)): b_i = -(ufar_i + sum over all near
 //   entries, self included, of S^(ik) s_k).
 __global__ void near_kernel(int mode, const double* __restrict__ centres, const double* __restrict__ radii,
-                            double Rc, int P, int Mc, int Nc, const int* __restrict__ near_off,
+                            double Rc, int P, int Mc, int Nc, int G, const int* __restrict__ near_off,
                             const int4* __restrict__ near_ent, const double* __restrict__ sig,
                             const double* __restrict__ lam, const double* __restrict__ lb,
                             const double* __restrict__ tilde, int mobility, const double* __restrict__ mu,
                             const double* __restrict__ ufar, double cmu, double* __restrict__ u) {
-  extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y
+  extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y, then [G][Mt][2] partial sums
   __shared__ double red[3][32];
   const int i = blockIdx.x;
   const int ns = 2 * Nc, n4 = 4 * Nc;
-  const int m = threadIdx.x;
+  const int Mt = blockDim.x / G;
+  const int g = threadIdx.x / Mt, m = threadIdx.x % Mt;
+  const int j0 = g * Nc / G, j1 = (g + 1) * Nc / G;
   double xx = 0, xy = 0;
   if (m < Mc) {
     const double th = 2.0 * LMFS_PI * m / Mc;
@@ -830,7 +842,7 @@ __global__ void near_kernel(int mode, const double* __restrict__ centres, const 
     }
     __syncthreads();
     if (m < Mc) {
-      for (int j = 0; j < Nc; ++j) {
+      for (int j = j0; j < j1; ++j) {
         const double dx = xx - nsm[4 * j], dy = xy - nsm[4 * j + 1];
         const double r2 = dx * dx + dy * dy;
         const double lg = 0.5 * log(r2);
@@ -840,7 +852,15 @@ __global__ void near_kernel(int mode, const double* __restrict__ centres, const 
       }
     }
   }
-  if (m < Mc) {
+  // combine the G source groups in order
+  double* part = nsm + 4 * Nc;
+  __syncthreads();
+  part[2 * (g * Mt + m)] = ux;
+  part[2 * (g * Mt + m) + 1] = uy;
+  __syncthreads();
+  if (g == 0 && m < Mc) {
+    ux = 0; uy = 0;
+    for (int q = 0; q < G; ++q) { ux += part[2 * (q * Mt + m)]; uy += part[2 * (q * Mt + m) + 1]; }
     const long long o = (long long)i * 2 * Mc + 2 * m;
     const double fx = ufar[o] + ux * cmu, fy = ufar[o + 1] + uy * cmu;
     if (mode == 0) { u[o] = mu[o] + fx; u[o + 1] = mu[o + 1] + fy; }
@@ -935,9 +955,12 @@ int far_field_prepare(Ctx& c) {
 }
 
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
-  if (2 * c.d.Nc > 256) { set_last_error("2 Nc > 256 not supported"); return LMFS_ERR_INVALID; }
-  const int thr = 128, blocks = (c.d.P * 32 + thr - 1) / thr;
-  onebody_apply_kernel<<<blocks, thr, 0, c.stream>>>(ob.W, ob.R, ob.perm, ob.rank, ob.V, c.cls, c.d.P, c.d.Nc, c.d.Mc, mu, lb);
+  const int ns = 2 * c.d.Nc;
+  if (ns > 1024) { set_last_error("2 Nc > 1024 not supported"); return LMFS_ERR_INVALID; }
+  const int thr = std::max(32, ((ns + 31) / 32) * 32);
+  const size_t shm = ((size_t)2 * c.d.Mc + 3 * (size_t)ns) * sizeof(double);
+  onebody_apply_kernel<<<c.d.P, thr, shm, c.stream>>>(ob.W, ob.R, ob.perm, ob.rank, ob.V, c.cls, c.d.P, c.d.Nc,
+                                                      c.d.Mc, mu, lb);
   return check_launch("onebody_apply");
 }
 
@@ -966,8 +989,7 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
     const int kchunk = ((kchunk_raw + M_TILE - 1) / M_TILE) * M_TILE;
     split = (P + kchunk - 1) / kchunk;
     const bool fp32 = precision == LMFS_MIXED;
-    p2m_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.coef64,
-                                                          fp32 ? c.coef32 : nullptr);
+    p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.coef64, fp32 ? c.coef32 : nullptr);
     LMFS_TRY(check_launch("p2m"));
     MpArgs a;
     a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc;
@@ -994,9 +1016,12 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
 
 int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar, double* u,
                int problem) {
-  const int threads = std::max(32, ((c.d.Mc + 31) / 32) * 32);
-  const size_t shm = (size_t)c.d.Nc * 4 * sizeof(double);
-  near_kernel<<<c.d.P, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, c.d.P, c.d.Mc, c.d.Nc, c.near_off,
+  // target nodes x source groups: enough warps per SM to keep the FP64 pipe busy
+  const int Mt = std::max(32, ((c.d.Mc + 31) / 32) * 32);
+  const int G = std::max(1, std::min({4, 1024 / Mt, c.d.Nc}));
+  const int threads = G * Mt;
+  const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)threads * 2) * sizeof(double);
+  near_kernel<<<c.d.P, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, c.d.P, c.d.Mc, c.d.Nc, G, c.near_off,
                                                  c.near_ent, strength, c.lam, c.lb, c.tilde,
                                                  problem == LMFS_MOBILITY, mu, ufar, INV4PI / c.prm.mu, u);
   return check_launch("near");

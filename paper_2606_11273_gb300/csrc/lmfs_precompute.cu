@@ -70,7 +70,8 @@ __global__ void fill_onebody(double* A, int ld, long long mstride, const double*
   }
 }
 
-// Extract W (rank rows of Q^T), R (upper 2Nc x 2Nc) from the factored [M | I].
+// Extract W (rank rows of Q^T, stored column by column: Wt[col][row]) and R
+// (upper 2Nc x 2Nc, column-major) from the factored [M | I].
 __global__ void extract_onebody(const double* A, int ld, long long mstride, int Nc, int Mc,
                                 const int* rank, double* W, double* R) {
   const int b = blockIdx.y;
@@ -79,7 +80,7 @@ __global__ void extract_onebody(const double* A, int ld, long long mstride, int 
   double* Wb = W + (long long)b * nsrc * nn;
   double* Rb = R + (long long)b * nsrc * nsrc;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsrc * nn; t += gridDim.x * blockDim.x) {
-    const int row = t / nn, col = t % nn;
+    const int col = t / nsrc, row = t % nsrc;
     Wb[t] = (row < r) ? M[(long long)(nsrc + col) * ld + row] : 0.0;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsrc * nsrc; t += gridDim.x * blockDim.x) {
