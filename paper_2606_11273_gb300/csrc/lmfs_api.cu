@@ -56,7 +56,7 @@ static void free_ctx(Ctx& c) {
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
-  dfree(c.ufar_part); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
+  dfree(c.ufar_part); dfree(c.near_part); dfree(c.near_tgt); dfree(c.ring); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
   if (c.own_stream && c.stream) { cudaStreamDestroy(c.stream); c.stream = nullptr; c.own_stream = false; }
 }
 

@@ -129,6 +129,7 @@ int upload_geometry(Ctx& c) {
   LMFS_TRY(dalloc(&c.csr_ent, 2 * (size_t)std::max(c.C, 1)));
   LMFS_TRY(dalloc(&c.near_off, P + 1));
   LMFS_TRY(dalloc(&c.near_ent, c.near_h.size()));
+  LMFS_TRY(dalloc(&c.near_tgt, c.near_h.size()));
   LMFS_TRY(dalloc(&c.far_excl_off, P + 1));
   LMFS_TRY(dalloc(&c.far_excl, c.near_h.size()));
   LMFS_TRY(dalloc(&c.tgt32, (size_t)P * Mc));
@@ -159,6 +160,10 @@ int upload_geometry(Ctx& c) {
   LMFS_CUDA(cudaMemcpyAsync(c.csr_off, c.csr_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaMemcpyAsync(c.near_off, c.near_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaMemcpyAsync(c.near_ent, ne.data(), ne.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  std::vector<int> tg(c.near_h.size());
+  for (int i = 0; i < P; ++i)
+    for (int e = c.near_off_h[i]; e < c.near_off_h[i + 1]; ++e) tg[e] = i;
+  LMFS_CUDA(cudaMemcpyAsync(c.near_tgt, tg.data(), tg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaMemcpyAsync(c.far_excl_off, c.near_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaMemcpyAsync(c.far_excl, fx.data(), fx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaMemcpyAsync(c.tgt32, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice, s));

@@ -116,6 +116,10 @@ struct Ctx {
   float2* src2 = nullptr;
   int far_split = 1;                 // source-range split of the far kernel
   double* ufar_part = nullptr;       // [far_split][P][Mc][2]
+  int sms = 152;                     // multiprocessors of the handle's device
+  double2* ring = nullptr;           // [Nc] (cos, sin)(2 pi j / Nc) of the source rings
+  int* near_tgt = nullptr;           // target disk of each near entry
+  double* near_part = nullptr;       // [near entries][Mc][2] near-field sums per entry
   int* far_err = nullptr;            // set by the far kernel if a bounded wait expired
   double2* coef64 = nullptr;         // [P][64] multipole coefficients (FP64)
   float2* coef32 = nullptr;          // [P][64] the same rounded to FP32

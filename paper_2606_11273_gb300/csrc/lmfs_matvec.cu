@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "lmfs_internal.h"
 #include "lmfs_tma.cuh"
@@ -98,6 +99,7 @@ __global__ void onebody_apply_kernel(const double* __restrict__ Wt, const double
 // ---- Step 1b: lam~ = A [lam_bar_i; lam_bar_k] per close pair ----------------
 __global__ void pair_apply_kernel(const double* __restrict__ A, const int* __restrict__ pairs, int C,
                                   int Nc, const double* __restrict__ lb, double* __restrict__ tilde) {
+  // block (c, y) takes rows y, y + gridDim.y, ... of pair c (a warp per row)
   extern __shared__ double xs[];
   const int c = blockIdx.x;
   const int n4 = 4 * Nc, ns = 2 * Nc;
@@ -107,11 +109,11 @@ __global__ void pair_apply_kernel(const double* __restrict__ A, const int* __res
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* Ac = A + (long long)c * n4 * n4;
-  for (int row = wid; row < n4; row += nw) {
+  for (int row = blockIdx.y + gridDim.y * wid; row < n4; row += gridDim.y * nw) {
     const double* ar = Ac + (long long)row * n4;
     double acc = 0.0;
     for (int col = lane; col < n4; col += 32) acc += ar[col] * xs[col];
-    acc = wsum(acc);
+    acc = lsum(acc);
     if (lane == 0) tilde[(long long)c * n4 + row] = acc;
   }
 }
@@ -472,11 +474,13 @@ constexpr int MP_NCOEF = 104;   // 3P + 5 = 101, padded to a multiple of 4
 // P2M: one warp per disk (moments in FP64).
 __global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, int P, int Nc,
                                                   const double* __restrict__ radii, double Rc,
+                                                  const double2* __restrict__ ring,
                                                   double2* __restrict__ coef, float2* __restrict__ coef32) {
   // one block per disk; warp g forms the moments of orders n = g, g + 4, ...
   __shared__ double mom[MP_P + 1][6];     // A_n, B_n, D_n (complex)
   __shared__ double2 cf[MP_NCOEF];
   __shared__ double bnd[MP_P + 1];
+  __shared__ double rpw[MP_P + 1];        // rho^n
   const int i = blockIdx.x;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const double rs = radii[i] * Rc;
@@ -489,8 +493,8 @@ __global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, 
     if (j < Nc) {
       fr[q] = s[(long long)i * 2 * Nc + 2 * j];
       fi[q] = s[(long long)i * 2 * Nc + 2 * j + 1];
-      const double ph = 2.0 * LMFS_PI * j / Nc;
-      wr[q] = rs * cos(ph); wi[q] = rs * sin(ph);
+      const double2 cs = ring[j];
+      wr[q] = rs * cs.x; wi[q] = rs * cs.y;
     }
     pr[q] = 1.0; pi_[q] = 0.0;            // p = w^g
     for (int k = 0; k < g; ++k) {
@@ -500,7 +504,12 @@ __global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, 
     const double w2r = wr[q] * wr[q] - wi[q] * wi[q], w2i = 2.0 * wr[q] * wi[q];
     sr[q] = w2r * w2r - w2i * w2i; si[q] = 2.0 * w2r * w2i;   // step w^4
   }
+  double rp = 1.0;
+  for (int k = 0; k < g; ++k) rp *= rs;
+  const double rs4 = (rs * rs) * (rs * rs);
   for (int n = g; n <= MP_P; n += 4) {
+    if (lane == 0) rpw[n] = rp;
+    rp *= rs4;
     double Ar = 0, Ai = 0, Br = 0, Bi = 0, Dr = 0, Di = 0;
 #pragma unroll
     for (int q = 0; q < SPL; ++q) {
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, 
   const int n = threadIdx.x;
   if (n <= MP_P) {
     const double Ar = mom[n][0], Ai = mom[n][1];
-    const double rp = pow(rs, (double)n);
+    const double rp = rpw[n];
     double b = sqrt(Ar * Ar + Ai * Ai) / rp;
     if (n == 0) {
       cf[0] = make_double2(Ar, Ai);
@@ -772,100 +781,181 @@ __global__ void reduce_splits(const double* part, long long stride, int nsplit, 
   }
 }
 
+// ---- FP64 logarithm and reciprocal for the near field -----------------------
+// Written from the mathematics, for positive normal arguments:
+//  * reciprocal: an FP32 seed refined by two Newton-Raphson steps
+//    y <- y + y (1 - a y); each step squares the relative error
+//    (2^-22 -> 2^-44 -> below one FP64 rounding);
+//  * logarithm: x = 2^e f, f in [1, 2); f = c_k (1 + t) with c_k the centre of
+//    the k-th of 64 equal subintervals (c_0 = 1, so t = f - 1 exactly there),
+//    |t| <= 1/64; log x = e log 2 + log c_k + log1p(t), log1p(t) from its
+//    Taylor series to t^11 (the remainder is below 2^-53 |t|).  The table
+//    (c_k, 1/c_k, log c_k) is built per block in shared memory.
+constexpr int LOG_TAB = 64;
+
+__device__ __forceinline__ void log_table_init(double* tab) {
+  for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) {
+    const double c = (k == 0) ? 1.0 : 1.0 + (k + 0.5) / LOG_TAB;
+    tab[3 * k] = c;
+    tab[3 * k + 1] = 1.0 / c;
+    tab[3 * k + 2] = log(c);
+  }
+}
+
+__device__ __forceinline__ double log_pos(double x, const double* tab) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)(b >> 52) - 1023;
+  const int k = (int)((b >> 46) & (LOG_TAB - 1));
+  const double f = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  const double t = (f - tab[3 * k]) * tab[3 * k + 1];
+  // log1p(t) = t (1 - t/2 + t^2/3 - ... - t^10/11)
+  double p = -1.0 / 11.0;
+  p = fma(p, t, 1.0 / 10.0);
+  p = fma(p, t, -1.0 / 9.0);
+  p = fma(p, t, 1.0 / 8.0);
+  p = fma(p, t, -1.0 / 7.0);
+  p = fma(p, t, 1.0 / 6.0);
+  p = fma(p, t, -1.0 / 5.0);
+  p = fma(p, t, 1.0 / 4.0);
+  p = fma(p, t, -1.0 / 3.0);
+  p = fma(p, t, 1.0 / 2.0);
+  p = fma(p, -t, 1.0);
+  return fma((double)e, 0.69314718055994530942, fma(t, p, tab[3 * k + 2]));
+}
+
+__device__ __forceinline__ double rcp_pos(double a) {
+  double y = (double)rcp_approx((float)a);
+  y = fma(y, fma(-a, y, 1.0), y);
+  y = fma(y, fma(-a, y, 1.0), y);
+  return y;
+}
+
 // ---- near field (FP64) + assembly ------------------------------------------
-// One block per target disk i, blockDim = G x Mt threads: thread (g, m) takes
-// target node m and the sources j in [g Nc / G, (g + 1) Nc / G) of every near
-// entry; the G partial sums are combined in a fixed order at the end.
-// mode 0 (matvec): u_i = mu_i + ufar_i + sum over near entries (regular:
-//   sig_k; close partner: proj_k(lam_k - lam_bar_k - lam~ of the pair with
-//   i)); self entries skipped.
-// mode 1 (completion flow, eq. (u0_def)): b_i = -(ufar_i + sum over all near
-//   entries, self included, of S^(ik) s_k).
+// One block per near entry e = (target disk i, source disk k), so that every
+// block carries the same Mc x Nc pairs; thread (g, m), g < G, takes target
+// node m and the sources j in [g Nc / G, (g + 1) Nc / G).  The G partial sums
+// are combined in a fixed order and stored per entry; near_reduce adds each
+// disk's entries in list order and assembles
+//   mode 0 (matvec): u_i = mu_i + ufar_i + sum over near entries (regular:
+//     sig_k; close partner: proj_k(lam_k - lam_bar_k - lam~ of the pair with
+//     i)); self entries skipped;
+//   mode 1 (completion flow, eq. (u0_def)): b_i = -(ufar_i + sum over all near
+//     entries, self included, of S^(ik) s_k).
 __global__ void near_kernel(int mode, const double* __restrict__ centres, const double* __restrict__ radii,
-                            double Rc, int P, int Mc, int Nc, int G, const int* __restrict__ near_off,
-                            const int4* __restrict__ near_ent, const double* __restrict__ sig,
-                            const double* __restrict__ lam, const double* __restrict__ lb,
-                            const double* __restrict__ tilde, int mobility, const double* __restrict__ mu,
-                            const double* __restrict__ ufar, double cmu, double* __restrict__ u) {
-  extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y, then [G][Mt][2] partial sums
+                            double Rc, int Mc, int Nc, int G, const double2* __restrict__ ring,
+                            const int* __restrict__ near_tgt, const int4* __restrict__ near_ent,
+                            const double* __restrict__ sig, const double* __restrict__ lam,
+                            const double* __restrict__ lb, const double* __restrict__ tilde, int mobility,
+                            double* __restrict__ part) {
+  extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y, then [G][Mc][2] partial sums
   __shared__ double red[3][32];
-  const int i = blockIdx.x;
+  __shared__ double ltab[3 * LOG_TAB];
+  const int e = blockIdx.x;
+  const int4 en = near_ent[e];
+  const int i = near_tgt[e], k = en.x, kind = en.y;
+  if (mode == 0 && kind == 2) return;     // whole block: the self term cancels
+  log_table_init(ltab);
   const int ns = 2 * Nc, n4 = 4 * Nc;
-  const int Mt = blockDim.x / G;
-  const int g = threadIdx.x / Mt, m = threadIdx.x % Mt;
+  const int g = threadIdx.x / Mc, m = threadIdx.x % Mc;
+  const bool act = g < G;
   const int j0 = g * Nc / G, j1 = (g + 1) * Nc / G;
   double xx = 0, xy = 0;
-  if (m < Mc) {
+  if (act) {
     const double th = 2.0 * LMFS_PI * m / Mc;
     xx = centres[2 * i] + radii[i] * cos(th);
     xy = centres[2 * i + 1] + radii[i] * sin(th);
   }
-  double ux = 0, uy = 0;
-  for (int e = near_off[i]; e < near_off[i + 1]; ++e) {
-    const int4 en = near_ent[e];
-    const int k = en.x, kind = en.y;
-    if (mode == 0 && kind == 2) continue;
-    const double rs = radii[k] * Rc;
+  const double rs = radii[k] * Rc;
+  double t0 = 0, t1 = 0, t2 = 0;
+  for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
+    const double2 cs = ring[j];
+    const double ex = rs * cs.x, ey = rs * cs.y;
+    double sx, sy;
+    if (mode == 0 && kind == 1) {
+      const double* tc = tilde + (long long)en.z * n4 + en.w * ns;
+      sx = lam[(long long)k * ns + 2 * j] - lb[(long long)k * ns + 2 * j] - tc[2 * j];
+      sy = lam[(long long)k * ns + 2 * j + 1] - lb[(long long)k * ns + 2 * j + 1] - tc[2 * j + 1];
+      t0 += sx; t1 += sy; t2 += -ey * sx + ex * sy;
+    } else {
+      sx = sig[(long long)k * ns + 2 * j];
+      sy = sig[(long long)k * ns + 2 * j + 1];
+    }
+    nsm[4 * j] = centres[2 * k] + ex;
+    nsm[4 * j + 1] = centres[2 * k + 1] + ey;
+    nsm[4 * j + 2] = sx;
+    nsm[4 * j + 3] = sy;
+  }
+  if (mode == 0 && kind == 1 && mobility) {
+    // block-wide K^T rho, then rho -= K (K^T K)^{-1} K^T rho
+    t0 = wsum(t0); t1 = wsum(t1); t2 = wsum(t2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { red[0][wid] = t0; red[1][wid] = t1; red[2][wid] = t2; }
     __syncthreads();
-    double t0 = 0, t1 = 0, t2 = 0;
+    t0 = t1 = t2 = 0;
+    for (int w = 0; w < nw; ++w) { t0 += red[0][w]; t1 += red[1][w]; t2 += red[2][w]; }
+    t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
     for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
-      const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
-      double sx, sy;
-      if (mode == 0 && kind == 1) {
-        const double* tc = tilde + (long long)en.z * n4 + en.w * ns;
-        sx = lam[(long long)k * ns + 2 * j] - lb[(long long)k * ns + 2 * j] - tc[2 * j];
-        sy = lam[(long long)k * ns + 2 * j + 1] - lb[(long long)k * ns + 2 * j + 1] - tc[2 * j + 1];
-        t0 += sx; t1 += sy; t2 += -ey * sx + ex * sy;
-      } else {
-        sx = sig[(long long)k * ns + 2 * j];
-        sy = sig[(long long)k * ns + 2 * j + 1];
-      }
-      nsm[4 * j] = centres[2 * k] + ex;
-      nsm[4 * j + 1] = centres[2 * k + 1] + ey;
-      nsm[4 * j + 2] = sx;
-      nsm[4 * j + 3] = sy;
+      const double2 cs = ring[j];
+      const double ex = rs * cs.x, ey = rs * cs.y;
+      nsm[4 * j + 2] -= t0 + t2 * (-ey);
+      nsm[4 * j + 3] -= t1 + t2 * ex;
     }
-    if (mode == 0 && kind == 1 && mobility) {
-      // block-wide K^T rho, then rho -= K (K^T K)^{-1} K^T rho
-      t0 = wsum(t0); t1 = wsum(t1); t2 = wsum(t2);
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      if (lane == 0) { red[0][wid] = t0; red[1][wid] = t1; red[2][wid] = t2; }
-      __syncthreads();
-      t0 = t1 = t2 = 0;
-      for (int w = 0; w < nw; ++w) { t0 += red[0][w]; t1 += red[1][w]; t2 += red[2][w]; }
-      t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
-      for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
-        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
-        nsm[4 * j + 2] -= t0 + t2 * (-ey);
-        nsm[4 * j + 3] -= t1 + t2 * ex;
-      }
+  }
+  __syncthreads();
+  double ux = 0, uy = 0;
+  if (act) {
+    // two sources per step: independent dependency chains for the FP64 pipe
+    int j = j0;
+    for (; j + 1 < j1; j += 2) {
+      const double dx0 = xx - nsm[4 * j], dy0 = xy - nsm[4 * j + 1];
+      const double dx1 = xx - nsm[4 * j + 4], dy1 = xy - nsm[4 * j + 5];
+      const double r20 = dx0 * dx0 + dy0 * dy0, r21 = dx1 * dx1 + dy1 * dy1;
+      const double lg0 = 0.5 * log_pos(r20, ltab), lg1 = 0.5 * log_pos(r21, ltab);
+      const double dt0 = (dx0 * nsm[4 * j + 2] + dy0 * nsm[4 * j + 3]) * rcp_pos(r20);
+      const double dt1 = (dx1 * nsm[4 * j + 6] + dy1 * nsm[4 * j + 7]) * rcp_pos(r21);
+      ux += -lg0 * nsm[4 * j + 2] + dt0 * dx0;
+      uy += -lg0 * nsm[4 * j + 3] + dt0 * dy0;
+      ux += -lg1 * nsm[4 * j + 6] + dt1 * dx1;
+      uy += -lg1 * nsm[4 * j + 7] + dt1 * dy1;
     }
-    __syncthreads();
-    if (m < Mc) {
-      for (int j = j0; j < j1; ++j) {
-        const double dx = xx - nsm[4 * j], dy = xy - nsm[4 * j + 1];
-        const double r2 = dx * dx + dy * dy;
-        const double lg = 0.5 * log(r2);
-        const double dt = (dx * nsm[4 * j + 2] + dy * nsm[4 * j + 3]) / r2;
-        ux += -lg * nsm[4 * j + 2] + dt * dx;
-        uy += -lg * nsm[4 * j + 3] + dt * dy;
-      }
+    if (j < j1) {
+      const double dx = xx - nsm[4 * j], dy = xy - nsm[4 * j + 1];
+      const double r2 = dx * dx + dy * dy;
+      const double lg = 0.5 * log_pos(r2, ltab);
+      const double dt = (dx * nsm[4 * j + 2] + dy * nsm[4 * j + 3]) * rcp_pos(r2);
+      ux += -lg * nsm[4 * j + 2] + dt * dx;
+      uy += -lg * nsm[4 * j + 3] + dt * dy;
     }
   }
   // combine the G source groups in order
-  double* part = nsm + 4 * Nc;
+  double* gp = nsm + 4 * Nc;
+  if (act) { gp[2 * (g * Mc + m)] = ux; gp[2 * (g * Mc + m) + 1] = uy; }
   __syncthreads();
-  part[2 * (g * Mt + m)] = ux;
-  part[2 * (g * Mt + m) + 1] = uy;
-  __syncthreads();
-  if (g == 0 && m < Mc) {
+  if (g == 0) {
     ux = 0; uy = 0;
-    for (int q = 0; q < G; ++q) { ux += part[2 * (q * Mt + m)]; uy += part[2 * (q * Mt + m) + 1]; }
-    const long long o = (long long)i * 2 * Mc + 2 * m;
-    const double fx = ufar[o] + ux * cmu, fy = ufar[o + 1] + uy * cmu;
-    if (mode == 0) { u[o] = mu[o] + fx; u[o + 1] = mu[o + 1] + fy; }
-    else { u[o] = -fx; u[o + 1] = -fy; }
+    for (int q = 0; q < G; ++q) { ux += gp[2 * (q * Mc + m)]; uy += gp[2 * (q * Mc + m) + 1]; }
+    part[((long long)e * Mc + m) * 2] = ux;
+    part[((long long)e * Mc + m) * 2 + 1] = uy;
   }
+}
+
+// Per target node: the disk's near entries added in list order, and assembly.
+__global__ void near_reduce(int mode, const int* __restrict__ near_off, const int4* __restrict__ near_ent,
+                            const double* __restrict__ part, int P, int Mc, const double* __restrict__ mu,
+                            const double* __restrict__ ufar, double cmu, double* __restrict__ u) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P * Mc) return;
+  const int i = t / Mc, m = t % Mc;
+  double ax = 0.0, ay = 0.0;
+  for (int e = near_off[i]; e < near_off[i + 1]; ++e) {
+    if (mode == 0 && near_ent[e].y == 2) continue;
+    ax += part[((long long)e * Mc + m) * 2];
+    ay += part[((long long)e * Mc + m) * 2 + 1];
+  }
+  const long long o = 2LL * t;
+  const double fx = ufar[o] + ax * cmu, fy = ufar[o + 1] + ay * cmu;
+  if (mode == 0) { u[o] = mu[o] + fx; u[o + 1] = mu[o + 1] + fy; }
+  else { u[o] = -fx; u[o + 1] = -fy; }
 }
 
 // ---- right-hand sides -------------------------------------------------------
@@ -951,6 +1041,19 @@ int far_field_prepare(Ctx& c) {
   LMFS_TRY(dalloc(&c.coef32, (size_t)c.d.P * MP_NCOEF));
   LMFS_TRY(dalloc(&c.far_err, 2));
   LMFS_CUDA(cudaMemsetAsync(c.far_err, 0, 2 * sizeof(int), c.stream));
+  // near field: enough blocks for two per SM when the batch is small
+  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device);
+  {
+    std::vector<double2> ring(c.d.Nc);
+    for (int j = 0; j < c.d.Nc; ++j) {
+      const double ph = 2.0 * LMFS_PI * j / c.d.Nc;
+      ring[j] = make_double2(std::cos(ph), std::sin(ph));
+    }
+    LMFS_TRY(dalloc(&c.ring, (size_t)c.d.Nc));
+    LMFS_CUDA(cudaMemcpyAsync(c.ring, ring.data(), ring.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  }
+  LMFS_TRY(dalloc(&c.near_part, std::max<size_t>(1, c.near_h.size()) * c.d.Mc * 2));
   return LMFS_OK;
 }
 
@@ -989,7 +1092,7 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
     const int kchunk = ((kchunk_raw + M_TILE - 1) / M_TILE) * M_TILE;
     split = (P + kchunk - 1) / kchunk;
     const bool fp32 = precision == LMFS_MIXED;
-    p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.coef64, fp32 ? c.coef32 : nullptr);
+    p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.coef64, fp32 ? c.coef32 : nullptr);
     LMFS_TRY(check_launch("p2m"));
     MpArgs a;
     a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc;
@@ -1016,15 +1119,22 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
 
 int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar, double* u,
                int problem) {
-  // target nodes x source groups: enough warps per SM to keep the FP64 pipe busy
-  const int Mt = std::max(32, ((c.d.Mc + 31) / 32) * 32);
-  const int G = std::max(1, std::min({4, 1024 / Mt, c.d.Nc}));
-  const int threads = G * Mt;
-  const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)threads * 2) * sizeof(double);
-  near_kernel<<<c.d.P, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, c.d.P, c.d.Mc, c.d.Nc, G, c.near_off,
-                                                 c.near_ent, strength, c.lam, c.lb, c.tilde,
-                                                 problem == LMFS_MOBILITY, mu, ufar, INV4PI / c.prm.mu, u);
-  return check_launch("near");
+  // target nodes x source groups, about nine warps per block
+  const int Mc = c.d.Mc;
+  const int G = std::max(1, std::min({4, 1024 / Mc, c.d.Nc}));
+  const int threads = ((G * Mc + 31) / 32) * 32;
+  const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mc * 2) * sizeof(double);
+  const int ne = (int)c.near_h.size();
+  if (ne > 0) {
+    near_kernel<<<ne, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, c.near_tgt,
+                                                c.near_ent, strength, c.lam, c.lb, c.tilde,
+                                                problem == LMFS_MOBILITY, c.near_part);
+    LMFS_TRY(check_launch("near"));
+  }
+  const int n = c.d.P * Mc;
+  near_reduce<<<(n + 127) / 128, 128, 0, c.stream>>>(mode, c.near_off, c.near_ent, c.near_part, c.d.P, Mc, mu, ufar,
+                                                     INV4PI / c.prm.mu, u);
+  return check_launch("near_reduce");
 }
 
 int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision) {
@@ -1033,7 +1143,10 @@ int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precisio
   const int P = c.d.P, Nc = c.d.Nc;
   LMFS_TRY(onebody_apply(c, pb.ob, mu, c.lb));                                   // Step 1a
   if (c.C > 0) {                                                                 // Step 1b
-    pair_apply_kernel<<<c.C, 256, 4 * Nc * sizeof(double), c.stream>>>(pb.A, c.pairs, c.C, Nc, c.lb, c.tilde);
+    // rows of a pair over several blocks when the pairs alone leave SMs idle
+    const int ry = std::max(1, std::min(8, (2 * c.sms + c.C - 1) / c.C));
+    pair_apply_kernel<<<dim3(c.C, ry), 256, 4 * Nc * sizeof(double), c.stream>>>(pb.A, c.pairs, c.C, Nc, c.lb,
+                                                                                c.tilde);
     LMFS_TRY(check_launch("pair_apply"));
   }
   gather_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(c.lb, c.tilde, c.csr_off, c.csr_ent, P, Nc, c.radii,
