@@ -295,6 +295,145 @@ __global__ void project_FQ_mobility(PairDims pd, PairGeo g, const double* Yf, co
   }
 }
 
+// ---- equal-radius pairs: the half-turn symmetry ----------------------------
+// For r_i = r_k the rotation by pi about the pair's midpoint maps every point
+// set of the pair onto itself with the disks exchanged: proxy s of side 1 <->
+// proxy (s + N_fp/2) mod N_fp of side 2, shielding node n <-> n, equispaced
+// node m <-> (m + n_eq/2) mod n_eq, Moebius node m <-> m, coarse source j <->
+// (j + N_c/2) mod N_c (all counts even).  The 2x2 Stokeslet is even in x - y,
+// so in these image orders [F | blkQ] = [[A, B | 0, Q], [B, A | Q, 0]]
+// (mobility projections included: the rigid-body projector of a side is the
+// same in image order).  With U = [[I, I], [I, -I]] / sqrt(2) on rows, sources
+// and coarse columns, the least-squares problem splits into
+//   Zp = (A + B)^+ Q,  Zm = (A - B)^+ Q,
+//   Z  = 1/2 [[Zp - Zm, Zp + Zm], [Zp + Zm, Zp - Zm]],
+// two problems of half the rows and half the columns: a quarter of the QR
+// work.  Truncation is relative to each half's own largest column.
+__device__ __forceinline__ int sym_src(int b, int Nfp) { return b < Nfp ? (b + Nfp / 2) % Nfp : b; }
+
+// [A +- B | Q] for matrix 2b (+) and 2b + 1 (-): rows 2 nX (side-1 nodes),
+// columns 2 nY1 (side-1 sources) then 2 Nc (disk-2 coarse sources in image
+// order); column-major, leading dimension ld.
+__global__ void fill_FQ_sym(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* W, int ld,
+                            long long mstride) {
+  const int b = blockIdx.y;
+  const int q = g.first + b;
+  const int e1 = pd.nenh[2 * b];
+  const int nY1 = pd.Nfp + e1, nX = pd.nX, Nc = pd.Nc;
+  const double* Y = Yf + (long long)b * pd.SY * 2;
+  const double* X = Xf + (long long)b * 2 * nX * 2;
+  double* Mp = W + (long long)(2 * b) * mstride;
+  double* Mm = Mp + mstride;
+  const int k = g.pairs[2 * q + 1];
+  const long long nblk = (long long)nX * (nY1 + Nc);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nblk; t += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(t % nX);
+    const int s = (int)(t / nX);
+    const double xx = X[2 * n], xy = X[2 * n + 1];
+    double p00, p01, p11, m00, m01, m11;
+    int col;
+    if (s < nY1) {
+      col = 2 * s;
+      const int si = nY1 + sym_src(s, pd.Nfp);
+      double a00, a01, a11, b00, b01, b11;
+      stokes2(xx - Y[2 * s], xy - Y[2 * s + 1], pd.cmu, &a00, &a01, &a11);
+      stokes2(xx - Y[2 * si], xy - Y[2 * si + 1], pd.cmu, &b00, &b01, &b11);
+      p00 = a00 + b00; p01 = a01 + b01; p11 = a11 + b11;
+      m00 = a00 - b00; m01 = a01 - b01; m11 = a11 - b11;
+    } else {
+      const int j = s - nY1;
+      col = 2 * nY1 + 2 * j;                 // right-hand side right after this matrix's own columns
+      const int jj = (j + Nc / 2) % Nc;
+      const double rs = g.radii[k] * pd.Rc, ph = 2.0 * LMFS_PI * jj / Nc;
+      stokes2(xx - (g.centres[2 * k] + rs * cos(ph)), xy - (g.centres[2 * k + 1] + rs * sin(ph)), pd.cmu,
+              &p00, &p01, &p11);
+      m00 = p00; m01 = p01; m11 = p11;
+    }
+    double* c0 = Mp + (long long)col * ld + 2 * n;
+    double* c1 = Mp + (long long)(col + 1) * ld + 2 * n;
+    c0[0] = p00; c0[1] = p01; c1[0] = p01; c1[1] = p11;
+    c0 = Mm + (long long)col * ld + 2 * n;
+    c1 = Mm + (long long)(col + 1) * ld + 2 * n;
+    c0[0] = m00; c0[1] = m01; c1[0] = m01; c1[1] = m11;
+  }
+}
+
+// Mobility maps on the half problems: source columns times (I - L_f,1) plus
+// B_f,1 K_f,1^T (both halves), coarse columns times the ring projector.
+__global__ void project_FQ_mobility_sym(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* W,
+                                        int ld, long long mstride, const double* Gf) {
+  const int b = blockIdx.y;
+  const int q = g.first + b;
+  const int nY1 = pd.Nfp + pd.nenh[2 * b], nX = pd.nX, Nc = pd.Nc;
+  const double* Y = Yf + (long long)b * pd.SY * 2;
+  const double* X = Xf + (long long)b * 2 * nX * 2;
+  const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
+  const double* G = Gf + (long long)b * 18;   // side 1
+  const double cx = g.centres[2 * i], cy = g.centres[2 * i + 1];
+  const int rows = 2 * nX;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * rows; t += gridDim.x * blockDim.x) {
+    const int half = t / rows, row = t % rows;
+    double* M = W + (long long)(2 * b + half) * mstride;
+    const int n = row >> 1, a = row & 1;
+    double t0 = 0, t1 = 0, t2 = 0;
+    for (int s = 0; s < nY1; ++s) {
+      const double v0 = M[(long long)(2 * s) * ld + row], v1 = M[(long long)(2 * s + 1) * ld + row];
+      const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+      t0 += v0; t1 += v1; t2 += -ey * v0 + ex * v1;
+    }
+    const double u0 = G[0] * t0 + G[1] * t1 + G[2] * t2;
+    const double u1 = G[3] * t0 + G[4] * t1 + G[5] * t2;
+    const double u2 = G[6] * t0 + G[7] * t1 + G[8] * t2;
+    const double bx = (a == 0) ? 1.0 : 0.0, by = (a == 0) ? 0.0 : 1.0;
+    const double bw = (a == 0) ? -(X[2 * n + 1] - cy) : (X[2 * n] - cx);
+    for (int s = 0; s < nY1; ++s) {
+      const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+      M[(long long)(2 * s) * ld + row] += -(u0 + u2 * (-ey)) + bx + bw * (-ey);
+      M[(long long)(2 * s + 1) * ld + row] += -(u1 + u2 * ex) + by + bw * ex;
+    }
+    // coarse ring of disk 2 in image order, (K^T K)^{-1} = diag(1/Nc, 1/Nc, 1/(Nc rs^2))
+    const double rs = g.radii[k] * pd.Rc;
+    const long long c0 = 2LL * nY1;
+    double r0 = 0, r1 = 0, r2 = 0;
+    for (int j = 0; j < Nc; ++j) {
+      const int jj = (j + Nc / 2) % Nc;
+      const double ph = 2.0 * LMFS_PI * jj / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+      const double v0 = M[(c0 + 2 * j) * ld + row], v1 = M[(c0 + 2 * j + 1) * ld + row];
+      r0 += v0; r1 += v1; r2 += -ey * v0 + ex * v1;
+    }
+    r0 /= Nc; r1 /= Nc; r2 /= (Nc * rs * rs);
+    for (int j = 0; j < Nc; ++j) {
+      const int jj = (j + Nc / 2) % Nc;
+      const double ph = 2.0 * LMFS_PI * jj / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+      M[(c0 + 2 * j) * ld + row] -= r0 + r2 * (-ey);
+      M[(c0 + 2 * j + 1) * ld + row] -= r1 + r2 * ex;
+    }
+  }
+}
+
+// Z of every pair in its natural layout ([nY][4 Nc], column-major, ld zld)
+// from the half solutions Xh (matrix 2b: Zp, 2b + 1: Zm; [nmaxh][2 Nc]).
+__global__ void assemble_Z_sym(PairDims pd, const double* Xh, int xld, long long xstride, double* Z, int zld,
+                               long long zstride) {
+  const int b = blockIdx.y;
+  const int nY1 = pd.Nfp + pd.nenh[2 * b], Nc = pd.Nc;
+  const double* Xp = Xh + (long long)(2 * b) * xstride;
+  const double* Xm = Xp + xstride;
+  double* Zb = Z + (long long)b * zstride;
+  const long long n = 2LL * nY1 * 2 * Nc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t % (2 * nY1)), c = (int)(t / (2 * nY1));
+    const int s = r >> 1, beta = r & 1, j = c >> 1, gam = c & 1;
+    const double zp = Xp[(long long)c * xld + r], zm = Xm[(long long)c * xld + r];
+    const int r2 = 2 * (nY1 + sym_src(s, pd.Nfp)) + beta;
+    const int c1 = 2 * j + gam, c2 = 2 * Nc + 2 * ((j + Nc / 2) % Nc) + gam;
+    Zb[(long long)c1 * zld + r] = 0.5 * (zp - zm);
+    Zb[(long long)c2 * zld + r] = 0.5 * (zp + zm);
+    Zb[(long long)c1 * zld + r2] = 0.5 * (zp + zm);
+    Zb[(long long)c2 * zld + r2] = 0.5 * (zp - zm);
+  }
+}
+
 // (K_f^T K_f)^{-1} per pair side (3x3, rows [I_2, (y - c)^perp] per source).
 __global__ void fine_gram_inv(PairDims pd, PairGeo g, const double* Yf, int nb, double* Gf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -572,7 +711,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   PairDims* pdd = nullptr;
   int rc = LMFS_OK;
   const bool mob = problem == LMFS_MOBILITY;
-  std::vector<int> hen(2 * chunk), hm(chunk), hn(chunk), hr(chunk), hr2(chunk);
+  std::vector<int> hen(2 * chunk), hm(2 * chunk), hn(2 * chunk), hr(2 * chunk), hr2(chunk);
   int hbad = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double qr_ms = 0.0, qr_flops = 0.0;
@@ -592,8 +731,9 @@ int build_pair_blocks(Ctx& c, int problem) {
       (rc = dalloc(&Yf, (size_t)chunk * SYmax * 2)) || (rc = dalloc(&Xf, (size_t)chunk * 2 * nX * 2)) ||
       (rc = dalloc(&Zpts, (size_t)chunk * Mp * 2)) || (rc = dalloc(&Gf, (size_t)chunk * 18)) ||
       (rc = dalloc(&tau, (size_t)chunk * nmax)) || (rc = dalloc(&vn, (size_t)chunk * 2 * nmax)) ||
-      (rc = dalloc(&nenh, (size_t)2 * chunk)) || (rc = dalloc(&dm, chunk)) || (rc = dalloc(&dn, chunk)) ||
-      (rc = dalloc(&rank, chunk)) || (rc = dalloc(&perm, (size_t)chunk * nmax)) || (rc = dalloc(&info, chunk)) ||
+      (rc = dalloc(&nenh, (size_t)2 * chunk)) || (rc = dalloc(&dm, 2 * chunk)) || (rc = dalloc(&dn, 2 * chunk)) ||
+      (rc = dalloc(&rank, 2 * chunk)) || (rc = dalloc(&perm, (size_t)chunk * nmax)) ||
+      (rc = dalloc(&info, 2 * chunk)) ||
       (rc = dalloc(&dm2, chunk)) || (rc = dalloc(&dn2, chunk)) || (rc = dalloc(&bad, 1)) ||
       (rc = dalloc(&pdd, 1)))
     goto done;
@@ -608,13 +748,31 @@ int build_pair_blocks(Ctx& c, int problem) {
     if ((rc = check_launch("count_enh"))) goto done;
     if (cuda_failed(cudaMemcpyAsync(hen.data(), nenh, 2 * nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
         cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
-    for (int b = 0; b < nb; ++b) { hm[b] = m1; hn[b] = 2 * (2 * Nfp + hen[2 * b] + hen[2 * b + 1]); }
+    // equal radii everywhere in the chunk (and even point counts): the
+    // half-turn symmetry splits each fine problem into two halves
+    bool sym = (Nfp % 2 == 0) && (neq % 2 == 0) && (Nc % 2 == 0) && (Nc <= Mp);
+    for (int b = 0; b < nb && sym; ++b) {
+      const int q = first + b;
+      sym = c.radii_h[c.pairs_h[2 * q]] == c.radii_h[c.pairs_h[2 * q + 1]] && hen[2 * b] == hen[2 * b + 1];
+    }
+    const int nbq = sym ? 2 * nb : nb;                 // matrices in the fine QR batch
+    const int ldh = 2 * nX, kh = 2 * Nc, nmaxh = SYmax;
+    const long long sh = (long long)ldh * (nmaxh + kh);
+    for (int b = 0; b < nb; ++b) {
+      if (sym) {
+        hm[2 * b] = hm[2 * b + 1] = ldh;
+        hn[2 * b] = hn[2 * b + 1] = 2 * (Nfp + hen[2 * b]);
+      } else {
+        hm[b] = m1;
+        hn[b] = 2 * (2 * Nfp + hen[2 * b] + hen[2 * b + 1]);
+      }
+    }
     std::vector<int> hm2(nb, 2 * Mp), hn2(nb, n4);
     PairDims pd;
     pd.nenh = nenh; pd.Nfp = Nfp; pd.nX = nX; pd.SY = SYmax; pd.Nc = Nc; pd.Rc = c.Rc;
     pd.cmu = 1.0 / (4 * LMFS_PI * c.prm.mu);
-    if (cuda_failed(cudaMemcpyAsync(dm, hm.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
-        cuda_failed(cudaMemcpyAsync(dn, hn.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+    if (cuda_failed(cudaMemcpyAsync(dm, hm.data(), nbq * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+        cuda_failed(cudaMemcpyAsync(dn, hn.data(), nbq * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
         cuda_failed(cudaMemcpyAsync(dm2, hm2.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
         cuda_failed(cudaMemcpyAsync(dn2, hn2.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
         cuda_failed(cudaMemcpyAsync(pdd, &pd, sizeof(PairDims), cudaMemcpyHostToDevice, c.stream), "h2d")) {
@@ -622,18 +780,38 @@ int build_pair_blocks(Ctx& c, int problem) {
     }
     fill_fine_sets<<<dim3(4, nb), 256, 0, c.stream>>>(g, nb, nenh, SYmax, Yf, Xf, Zpts);
     if ((rc = check_launch("fill_fine_sets"))) goto done;
-    fill_FQ<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ld1, s1);
-    if ((rc = check_launch("fill_FQ"))) goto done;
     if (mob) {
       fine_gram_inv<<<(2 * nb + 127) / 128, 128, 0, c.stream>>>(pd, g, Yf, nb, Gf);
       note_launches(1);
-      project_FQ_mobility<<<dim3((m1 + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ld1, s1, Gf);
-      if ((rc = check_launch("project_FQ_mobility"))) goto done;
     }
-    // F's columns beyond n_b (unused padding) are never touched: the RHS block
-    // starts at column n_b, so move it there when n_b < nmax -- the fill put
-    // blkQ right after F's own columns, i.e. already at column n_b.
-    {
+    if (sym) {
+      // [A +- B | Q] of every pair (matrices 2b, 2b + 1), both halves solved
+      // in one batch; the half solutions go to D's space (filled only later)
+      fill_FQ_sym<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ldh, sh);
+      if ((rc = check_launch("fill_FQ_sym"))) goto done;
+      if (mob) {
+        project_FQ_mobility_sym<<<dim3((2 * ldh + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ldh, sh, Gf);
+        if ((rc = check_launch("project_FQ_mobility_sym"))) goto done;
+      }
+      QRBatch q{};
+      q.A = ws1; q.mstride = sh; q.m = dm; q.n = dn; q.k = kh; q.ld = ldh; q.eps = c.prm.eps_trunc_fine;
+      q.X = D; q.xld = nmaxh; q.xstride = (long long)nmaxh * kh; q.rank = rank; q.perm = perm;
+      q.permstride = nmaxh; q.tau = tau; q.vn = vn; q.info = info; q.nb = nbq; q.nmax = nmaxh;
+      cudaEventRecord(ev[0], c.stream);
+      if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
+      cudaEventRecord(ev[1], c.stream);
+      assemble_Z_sym<<<dim3(32, nb), 256, 0, c.stream>>>(pd, D, nmaxh, (long long)nmaxh * kh, Z, nmax,
+                                                         (long long)nmax * k);
+      if ((rc = check_launch("assemble_Z_sym"))) goto done;
+    } else {
+      fill_FQ<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ld1, s1);
+      if ((rc = check_launch("fill_FQ"))) goto done;
+      if (mob) {
+        project_FQ_mobility<<<dim3((m1 + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ld1, s1, Gf);
+        if ((rc = check_launch("project_FQ_mobility"))) goto done;
+      }
+      // the fill put blkQ right after F's own n_b columns, where the QR
+      // expects the right-hand sides
       QRBatch q{};
       q.A = ws1; q.mstride = s1; q.m = dm; q.n = dn; q.k = k; q.ld = ld1; q.eps = c.prm.eps_trunc_fine;
       q.X = Z; q.xld = nmax; q.xstride = (long long)nmax * k; q.rank = rank; q.perm = perm; q.permstride = nmax;
@@ -642,7 +820,7 @@ int build_pair_blocks(Ctx& c, int problem) {
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
       cudaEventRecord(ev[1], c.stream);
     }
-    any_nonzero<<<(nb + 255) / 256, 256, 0, c.stream>>>(info, nb, bad);
+    any_nonzero<<<(nbq + 255) / 256, 256, 0, c.stream>>>(info, nbq, bad);
     note_launches(1);
     extract_E<<<dim3((k * 32 + 255) / 256, nb), 256, 0, c.stream>>>(pd, g, Yf, Z, nmax, (long long)nmax * k, k,
                                                                    mob ? 1.0 : -1.0, pb.E, first, Gf, mob ? Zp : nullptr);
@@ -666,11 +844,13 @@ int build_pair_blocks(Ctx& c, int problem) {
       q.X = X2; q.xld = n4; q.xstride = (long long)n4 * k; q.rank = rank + 0; q.perm = perm; q.permstride = nmax;
       q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = n4;
       // ranks of F are read back before this call overwrites them
-      if (cuda_failed(cudaMemcpyAsync(hr.data(), rank, nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+      if (cuda_failed(cudaMemcpyAsync(hr.data(), rank, nbq * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
           cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
       for (int b = 0; b < nb; ++b) {
-        minr = std::min(minr, hr[b]); maxr = std::max(maxr, hr[b]);
-        qr_flops += qrf(m1, hn[b], k, hr[b]);
+        const int rF = sym ? hr[2 * b] + hr[2 * b + 1] : hr[b];
+        minr = std::min(minr, rF); maxr = std::max(maxr, rF);
+        if (sym) qr_flops += qrf(ldh, hn[2 * b], kh, hr[2 * b]) + qrf(ldh, hn[2 * b + 1], kh, hr[2 * b + 1]);
+        else qr_flops += qrf(m1, hn[b], k, hr[b]);
       }
       cudaEventRecord(ev[2], c.stream);
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
