@@ -434,6 +434,50 @@ __global__ void assemble_Z_sym(PairDims pd, const double* Xh, int xld, long long
   }
 }
 
+// The peanut system C A = -D Z has the same structure: peanut node p <-> p +
+// M_p/2, coarse source j <-> (j + N_c/2) on the other disk, and D Z is
+// symmetric once Z is.  Split halves [P +- R | S +- T] (rows: the first M_p/2
+// nodes, columns: disk-1 coarse sources) from the natural [C | D Z] (ld ldc):
+// P, S the disk-1 columns, R, T the disk-2 columns in image order.
+__global__ void split_C_sym(int Nc, int Mp, const double* W2, int ldc, long long cstride, double* H,
+                            long long hstride) {
+  const int b = blockIdx.y;
+  const double* Cb = W2 + (long long)b * cstride;
+  double* Hp = H + (long long)(2 * b) * hstride;
+  double* Hm = Hp + hstride;
+  const int n4 = 4 * Nc, rows = Mp;
+  const long long n = (long long)rows * n4;             // [C half | RHS half] columns: 2Nc + 2Nc
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t % rows), col = (int)(t / rows);
+    const int part = col / (2 * Nc), c = col % (2 * Nc);   // 0: C, 1: D Z
+    const int j = c >> 1, gam = c & 1;
+    const int c1 = part * n4 + c, c2 = part * n4 + 2 * Nc + 2 * ((j + Nc / 2) % Nc) + gam;
+    const double u = Cb[(long long)c1 * ldc + r], v = Cb[(long long)c2 * ldc + r];
+    Hp[(long long)col * rows + r] = u + v;
+    Hm[(long long)col * rows + r] = u - v;
+  }
+}
+
+// A = -1/2 [[Xp + Xm, Xp - Xm], [Xp - Xm, Xp + Xm]] in (disk 1, disk 2 image)
+// order, stored row-major [4Nc][4Nc] in the natural order.
+__global__ void assemble_A_sym(int Nc, const double* X, int xld, long long xstride, double* A, int Cfirst) {
+  const int b = blockIdx.y;
+  const int n4 = 4 * Nc, nh = 2 * Nc;
+  const double* Xp = X + (long long)(2 * b) * xstride;
+  const double* Xm = Xp + xstride;
+  double* Ab = A + (long long)(Cfirst + b) * n4 * n4;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nh * nh; t += gridDim.x * blockDim.x) {
+    const int r = t % nh, c = t / nh;                     // X column-major [nh][nh]
+    const double xp = Xp[(long long)c * xld + r], xm = Xm[(long long)c * xld + r];
+    const int r2 = nh + 2 * (((r >> 1) + Nc / 2) % Nc) + (r & 1);
+    const int c2 = nh + 2 * (((c >> 1) + Nc / 2) % Nc) + (c & 1);
+    Ab[(long long)r * n4 + c] = -0.5 * (xp + xm);
+    Ab[(long long)r * n4 + c2] = -0.5 * (xp - xm);
+    Ab[(long long)r2 * n4 + c] = -0.5 * (xp - xm);
+    Ab[(long long)r2 * n4 + c2] = -0.5 * (xp + xm);
+  }
+}
+
 // (K_f^T K_f)^{-1} per pair side (3x3, rows [I_2, (y - c)^perp] per source).
 __global__ void fine_gram_inv(PairDims pd, PairGeo g, const double* Yf, int nb, double* Gf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -711,7 +755,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   PairDims* pdd = nullptr;
   int rc = LMFS_OK;
   const bool mob = problem == LMFS_MOBILITY;
-  std::vector<int> hen(2 * chunk), hm(2 * chunk), hn(2 * chunk), hr(2 * chunk), hr2(chunk);
+  std::vector<int> hen(2 * chunk), hm(2 * chunk), hn(2 * chunk), hr(2 * chunk), hr2(2 * chunk);
   int hbad = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double qr_ms = 0.0, qr_flops = 0.0;
@@ -734,7 +778,7 @@ int build_pair_blocks(Ctx& c, int problem) {
       (rc = dalloc(&nenh, (size_t)2 * chunk)) || (rc = dalloc(&dm, 2 * chunk)) || (rc = dalloc(&dn, 2 * chunk)) ||
       (rc = dalloc(&rank, 2 * chunk)) || (rc = dalloc(&perm, (size_t)chunk * nmax)) ||
       (rc = dalloc(&info, 2 * chunk)) ||
-      (rc = dalloc(&dm2, chunk)) || (rc = dalloc(&dn2, chunk)) || (rc = dalloc(&bad, 1)) ||
+      (rc = dalloc(&dm2, 2 * chunk)) || (rc = dalloc(&dn2, 2 * chunk)) || (rc = dalloc(&bad, 1)) ||
       (rc = dalloc(&pdd, 1)))
     goto done;
   if (cuda_failed(cudaMemsetAsync(bad, 0, sizeof(int), c.stream), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
@@ -838,11 +882,29 @@ int build_pair_blocks(Ctx& c, int problem) {
                                                ws2 + (long long)n4 * ld2, ld2, s2, 2 * Mp, k, nenh, 0, pdd);
       if ((rc = check_launch("gemm DZ"))) goto done;
     }
+    const bool symC = sym && (Mp % 2 == 0);
+    const int nbc = symC ? 2 * nb : nb;
+    const long long shc = (long long)Mp * n4;             // half: Mp rows x (2Nc + 2Nc)
+    if (symC) {
+      split_C_sym<<<dim3(32, nb), 256, 0, c.stream>>>(Nc, Mp, ws2, ld2, s2, ws1, shc);
+      if ((rc = check_launch("split_C_sym"))) goto done;
+      std::vector<int> hmc(nbc, Mp), hnc(nbc, 2 * Nc);
+      if (cuda_failed(cudaMemcpyAsync(dm2, hmc.data(), nbc * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+          cuda_failed(cudaMemcpyAsync(dn2, hnc.data(), nbc * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d")) {
+        rc = LMFS_ERR_CUDA; goto done;
+      }
+    }
     {
       QRBatch q{};
-      q.A = ws2; q.mstride = s2; q.m = dm2; q.n = dn2; q.k = k; q.ld = ld2; q.eps = c.prm.eps_trunc;
-      q.X = X2; q.xld = n4; q.xstride = (long long)n4 * k; q.rank = rank + 0; q.perm = perm; q.permstride = nmax;
-      q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = n4;
+      if (symC) {
+        q.A = ws1; q.mstride = shc; q.m = dm2; q.n = dn2; q.k = 2 * Nc; q.ld = Mp; q.eps = c.prm.eps_trunc;
+        q.X = X2; q.xld = 2 * Nc; q.xstride = (long long)4 * Nc * Nc; q.rank = rank; q.perm = perm;
+        q.permstride = 2 * Nc; q.tau = tau; q.vn = vn; q.info = info; q.nb = nbc; q.nmax = 2 * Nc;
+      } else {
+        q.A = ws2; q.mstride = s2; q.m = dm2; q.n = dn2; q.k = k; q.ld = ld2; q.eps = c.prm.eps_trunc;
+        q.X = X2; q.xld = n4; q.xstride = (long long)n4 * k; q.rank = rank + 0; q.perm = perm; q.permstride = nmax;
+        q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = n4;
+      }
       // ranks of F are read back before this call overwrites them
       if (cuda_failed(cudaMemcpyAsync(hr.data(), rank, nbq * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
           cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
@@ -855,18 +917,23 @@ int build_pair_blocks(Ctx& c, int problem) {
       cudaEventRecord(ev[2], c.stream);
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
       cudaEventRecord(ev[3], c.stream);
-      if (cuda_failed(cudaMemcpyAsync(hr2.data(), rank, nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+      if (cuda_failed(cudaMemcpyAsync(hr2.data(), rank, nbc * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
           cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
-      for (int b = 0; b < nb; ++b) qr_flops += qrf(2 * Mp, n4, k, hr2[b]);
+      for (int b = 0; b < nbc; ++b) qr_flops += symC ? qrf(Mp, 2 * Nc, 2 * Nc, hr2[b]) : qrf(2 * Mp, n4, k, hr2[b]);
       float ms0 = 0, ms1 = 0;
       cudaEventElapsedTime(&ms0, ev[0], ev[1]);
       cudaEventElapsedTime(&ms1, ev[2], ev[3]);
       qr_ms += ms0 + ms1;
     }
-    any_nonzero<<<(nb + 255) / 256, 256, 0, c.stream>>>(info, nb, bad);
+    any_nonzero<<<(nbc + 255) / 256, 256, 0, c.stream>>>(info, nbc, bad);
     note_launches(1);
-    store_A<<<dim3(64, nb), 256, 0, c.stream>>>(X2, n4, (long long)n4 * k, n4, pb.A, first);
-    if ((rc = check_launch("store_A"))) goto done;
+    if (symC) {
+      assemble_A_sym<<<dim3(16, nb), 256, 0, c.stream>>>(Nc, X2, 2 * Nc, (long long)4 * Nc * Nc, pb.A, first);
+      if ((rc = check_launch("assemble_A_sym"))) goto done;
+    } else {
+      store_A<<<dim3(64, nb), 256, 0, c.stream>>>(X2, n4, (long long)n4 * k, n4, pb.A, first);
+      if ((rc = check_launch("store_A"))) goto done;
+    }
   }
   if (cuda_failed(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
       cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
