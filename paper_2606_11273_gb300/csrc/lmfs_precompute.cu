@@ -560,12 +560,14 @@ __global__ void extract_E(PairDims pd, PairGeo g, const double* Yf, const double
 // (times (I - L^pair) for mobility) into the second workspace's first 4Nc
 // columns.
 __global__ void fill_DC(PairDims pd, PairGeo g, const double* Yf, const double* Zpts, double* D, int dld,
-                        long long dstride, double* W2, int ld2, long long w2stride, int mobility) {
+                        long long dstride, double* W2, int ld2, long long w2stride, int Mp) {
+  // rows of the first Mp peanut nodes (all of them, or the first half when
+  // the symmetric split reads only those)
   const int b = blockIdx.y, q = g.first + b;
   const int e1 = pd.nenh[2 * b], e2 = pd.nenh[2 * b + 1];
-  const int nY = 2 * pd.Nfp + e1 + e2, Mp = g.Mp, Nc = pd.Nc;
+  const int nY = 2 * pd.Nfp + e1 + e2, Nc = pd.Nc;
   const double* Y = Yf + (long long)b * pd.SY * 2;
-  const double* Z = Zpts + (long long)b * Mp * 2;
+  const double* Z = Zpts + (long long)b * g.Mp * 2;
   double* Db = D + (long long)b * dstride;
   double* Cb = W2 + (long long)b * w2stride;
   const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
@@ -589,14 +591,13 @@ __global__ void fill_DC(PairDims pd, PairGeo g, const double* Yf, const double* 
     double* c1 = base + (long long)(2 * s + 1) * ldd + 2 * p;
     c0[0] = s00; c0[1] = s01; c1[0] = s01; c1[1] = s11;
   }
-  (void)mobility;
 }
 
 // C (I - L^pair) in place: per row, per disk, ring projector.
-__global__ void project_C(PairDims pd, PairGeo g, double* W2, int ld2, long long w2stride) {
+__global__ void project_C(PairDims pd, PairGeo g, double* W2, int ld2, long long w2stride, int Mp) {
   const int b = blockIdx.y, q = g.first + b, Nc = pd.Nc;
   double* Cb = W2 + (long long)b * w2stride;
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < 2 * g.Mp; row += gridDim.x * blockDim.x) {
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < 2 * Mp; row += gridDim.x * blockDim.x) {
     for (int disk = 0; disk < 2; ++disk) {
       const int dd = disk ? g.pairs[2 * q + 1] : g.pairs[2 * q];
       const double rs = g.radii[dd] * pd.Rc;
@@ -869,20 +870,23 @@ int build_pair_blocks(Ctx& c, int problem) {
     extract_E<<<dim3((k * 32 + 255) / 256, nb), 256, 0, c.stream>>>(pd, g, Yf, Z, nmax, (long long)nmax * k, k,
                                                                    mob ? 1.0 : -1.0, pb.E, first, Gf, mob ? Zp : nullptr);
     if ((rc = check_launch("extract_E"))) goto done;
-    fill_DC<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Zpts, D, ld2, (long long)ld2 * nmax, ws2, ld2, s2, mob);
+    // the symmetric split of the peanut system reads only the first half of
+    // the peanut nodes: fill, project and multiply only those rows
+    const bool symC = sym && (Mp % 2 == 0);
+    const int Mrow = symC ? Mp / 2 : Mp;
+    fill_DC<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Zpts, D, ld2, (long long)ld2 * nmax, ws2, ld2, s2, Mrow);
     if ((rc = check_launch("fill_DC"))) goto done;
     if (mob) {
-      project_C<<<dim3((2 * Mp + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, ws2, ld2, s2);
+      project_C<<<dim3((2 * Mrow + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, ws2, ld2, s2, Mrow);
       if ((rc = check_launch("project_C"))) goto done;
     }
     // DZ into the right-hand-side columns of the second workspace
     {
-      dim3 grid((2 * Mp + GT - 1) / GT, (k + GT - 1) / GT, nb);
+      dim3 grid((2 * Mrow + GT - 1) / GT, (k + GT - 1) / GT, nb);
       gemm_batched<<<grid, 256, 0, c.stream>>>(D, ld2, (long long)ld2 * nmax, mob ? Zp : Z, nmax, (long long)nmax * k,
-                                               ws2 + (long long)n4 * ld2, ld2, s2, 2 * Mp, k, nenh, 0, pdd);
+                                               ws2 + (long long)n4 * ld2, ld2, s2, 2 * Mrow, k, nenh, 0, pdd);
       if ((rc = check_launch("gemm DZ"))) goto done;
     }
-    const bool symC = sym && (Mp % 2 == 0);
     const int nbc = symC ? 2 * nb : nb;
     const long long shc = (long long)Mp * n4;             // half: Mp rows x (2Nc + 2Nc)
     if (symC) {
