@@ -163,6 +163,14 @@ int lmfs_invalidate(lmfs_handle h);
  * source-range split, near-list entries}. */
 int lmfs_stats(lmfs_handle h, int problem, double* out);
 
+/* The pair QR of the last precompute split into its two kernels (CUDA events
+ * on the handle's stream): out[4] = {factorization ms, its algorithmic FP64
+ * flops (sum over reflectors s < rank of 4 (m - s)(n - s - 1)), right-hand
+ * sides ms, their flops (4 (m - s) k per reflector plus k rank^2 for the back
+ * substitution)}.  HOST array; zeros before the first precompute.  No
+ * counterpart in the paper: a measurement hook. */
+int lmfs_qr_stats(lmfs_handle h, int problem, double* out);
+
 /* Diagnostics of the last solve on the device: the GMRES solution mu
  * (DEVICE [P][Mc][2] copy destination) for parity checks. */
 int lmfs_get_solution(lmfs_handle h, double* mu_dev);

@@ -129,7 +129,11 @@ class Solver:
         _lib.check(self.lib.lmfs_stats(self.h, problem, _ptr(out)))
         keys = ["precompute_ms", "qr_ms", "qr_flops", "min_rank_F", "max_rank_F", "n_pairs", "far_split",
                 "near_entries"]
-        return dict(zip(keys, out.tolist()))
+        d = dict(zip(keys, out.tolist()))
+        q = np.zeros(4)
+        _lib.check(self.lib.lmfs_qr_stats(self.h, problem, _ptr(q)))
+        d.update(zip(["factor_ms", "factor_flops", "rhs_ms", "rhs_flops"], q.tolist()))
+        return d
 
     def solution(self, mu_dev):
         _lib.check(self.lib.lmfs_get_solution(self.h, _ptr(mu_dev)))

@@ -81,6 +81,7 @@ SIGNATURES = {
     "lmfs_get_solution": (_i, [_vp, _vp]),
     "lmfs_invalidate": (_i, [_vp]),
     "lmfs_stats": (_i, [_vp, _i, _vp]),
+    "lmfs_qr_stats": (_i, [_vp, _i, _vp]),
     "lmfs_stokeslet_sum": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _d, _i, _vp, _vp]),
     "lmfs_stokeslet_sum_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _d, _vp, _vp]),
     "lmfs_strerror": (ctypes.c_char_p, [_i]),

@@ -372,6 +372,13 @@ int lmfs_stats(lmfs_handle h, int problem, double* out) {
   return LMFS_OK;
 }
 
+int lmfs_qr_stats(lmfs_handle h, int problem, double* out) {
+  if (!h || !out || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
+  const PairBlocks& pb = h->c.prob[problem];
+  out[0] = pb.fac_ms; out[1] = pb.fac_flops; out[2] = pb.rhs_ms; out[3] = pb.rhs_flops;
+  return LMFS_OK;
+}
+
 int lmfs_get_solution(lmfs_handle h, double* mu_dev) {
   if (!h || !mu_dev) return LMFS_ERR_INVALID;
   if (!h->c.have_solution) return LMFS_ERR_STATE;

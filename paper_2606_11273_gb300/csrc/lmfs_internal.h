@@ -56,6 +56,8 @@ struct PairBlocks {
   double t_ms = 0.0;             // wall time of the last pair precompute
   double qr_ms = 0.0;            // QR kernel time (CUDA events on the handle's stream)
   double qr_flops = 0.0;         // algorithmic FP64 flops of those QR launches
+  double fac_ms = 0.0, fac_flops = 0.0;   // of which the pivoted factorizations (qrcp_kernel)
+  double rhs_ms = 0.0, rhs_flops = 0.0;   // and the right-hand sides (apply_qt_kernel)
   int max_rank_F = 0, min_rank_F = 0;
 };
 
@@ -177,6 +179,7 @@ struct QRBatch {
   int* info;        // out: 0 ok, 1 non-finite
   int nb;
   int nmax;
+  cudaEvent_t* ev = nullptr;   // optional: 3 events recorded before, between and after the two kernels
 };
 int qr_solve_batched(const QRBatch& q, cudaStream_t s, bool solve);
 

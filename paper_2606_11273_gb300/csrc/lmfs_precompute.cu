@@ -758,8 +758,15 @@ int build_pair_blocks(Ctx& c, int problem) {
   const bool mob = problem == LMFS_MOBILITY;
   std::vector<int> hen(2 * chunk), hm(2 * chunk), hn(2 * chunk), hr(2 * chunk), hr2(2 * chunk);
   int hbad = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double qr_ms = 0.0, qr_flops = 0.0;
+  double fac_ms = 0.0, fac_flops = 0.0, rhs_ms = 0.0, rhs_flops = 0.0;
+  // split of qrf: the factorization's part, the rest being the right-hand sides
+  auto qrfA = [](double m, double n, double r) {
+    double f = 0.0;
+    for (int s = 0; s < (int)r; ++s) f += 4.0 * (m - s) * (n - s - 1);
+    return f;
+  };
   // algorithmic flops of one QR launch: reflector s applied to the n + k - s - 1
   // trailing columns (a dot and an update of length m - s), then k back
   // substitutions with the r x r triangle
@@ -842,9 +849,8 @@ int build_pair_blocks(Ctx& c, int problem) {
       q.A = ws1; q.mstride = sh; q.m = dm; q.n = dn; q.k = kh; q.ld = ldh; q.eps = c.prm.eps_trunc_fine;
       q.X = D; q.xld = nmaxh; q.xstride = (long long)nmaxh * kh; q.rank = rank; q.perm = perm;
       q.permstride = nmaxh; q.tau = tau; q.vn = vn; q.info = info; q.nb = nbq; q.nmax = nmaxh;
-      cudaEventRecord(ev[0], c.stream);
+      q.ev = ev;
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
-      cudaEventRecord(ev[1], c.stream);
       assemble_Z_sym<<<dim3(32, nb), 256, 0, c.stream>>>(pd, D, nmaxh, (long long)nmaxh * kh, Z, nmax,
                                                          (long long)nmax * k);
       if ((rc = check_launch("assemble_Z_sym"))) goto done;
@@ -861,9 +867,8 @@ int build_pair_blocks(Ctx& c, int problem) {
       q.A = ws1; q.mstride = s1; q.m = dm; q.n = dn; q.k = k; q.ld = ld1; q.eps = c.prm.eps_trunc_fine;
       q.X = Z; q.xld = nmax; q.xstride = (long long)nmax * k; q.rank = rank; q.perm = perm; q.permstride = nmax;
       q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = nmax;
-      cudaEventRecord(ev[0], c.stream);
+      q.ev = ev;
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
-      cudaEventRecord(ev[1], c.stream);
     }
     any_nonzero<<<(nbq + 255) / 256, 256, 0, c.stream>>>(info, nbq, bad);
     note_launches(1);
@@ -915,19 +920,29 @@ int build_pair_blocks(Ctx& c, int problem) {
       for (int b = 0; b < nb; ++b) {
         const int rF = sym ? hr[2 * b] + hr[2 * b + 1] : hr[b];
         minr = std::min(minr, rF); maxr = std::max(maxr, rF);
-        if (sym) qr_flops += qrf(ldh, hn[2 * b], kh, hr[2 * b]) + qrf(ldh, hn[2 * b + 1], kh, hr[2 * b + 1]);
-        else qr_flops += qrf(m1, hn[b], k, hr[b]);
+        for (int h = 0; h < (sym ? 2 : 1); ++h) {
+          const int mi = sym ? 2 * b + h : b;
+          const double mm = sym ? ldh : m1, kk = sym ? kh : k;
+          const double f = qrf(mm, hn[mi], kk, hr[mi]), fa = qrfA(mm, hn[mi], hr[mi]);
+          qr_flops += f; fac_flops += fa; rhs_flops += f - fa;
+        }
       }
-      cudaEventRecord(ev[2], c.stream);
+      q.ev = ev + 3;
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
-      cudaEventRecord(ev[3], c.stream);
       if (cuda_failed(cudaMemcpyAsync(hr2.data(), rank, nbc * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
           cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
-      for (int b = 0; b < nbc; ++b) qr_flops += symC ? qrf(Mp, 2 * Nc, 2 * Nc, hr2[b]) : qrf(2 * Mp, n4, k, hr2[b]);
-      float ms0 = 0, ms1 = 0;
-      cudaEventElapsedTime(&ms0, ev[0], ev[1]);
-      cudaEventElapsedTime(&ms1, ev[2], ev[3]);
-      qr_ms += ms0 + ms1;
+      for (int b = 0; b < nbc; ++b) {
+        const double mm = symC ? Mp : 2 * Mp, nn = symC ? 2 * Nc : n4, kk = symC ? 2 * Nc : k;
+        const double f = qrf(mm, nn, kk, hr2[b]), fa = qrfA(mm, nn, hr2[b]);
+        qr_flops += f; fac_flops += fa; rhs_flops += f - fa;
+      }
+      float a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+      cudaEventElapsedTime(&a0, ev[0], ev[1]);
+      cudaEventElapsedTime(&b0, ev[1], ev[2]);
+      cudaEventElapsedTime(&a1, ev[3], ev[4]);
+      cudaEventElapsedTime(&b1, ev[4], ev[5]);
+      fac_ms += a0 + a1; rhs_ms += b0 + b1;
+      qr_ms += a0 + b0 + a1 + b1;
     }
     any_nonzero<<<(nbc + 255) / 256, 256, 0, c.stream>>>(info, nbc, bad);
     note_launches(1);
@@ -944,6 +959,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   if (hbad) { set_last_error("non-finite value in a pair factorization"); rc = LMFS_ERR_NUMERICAL; goto done; }
   pb.min_rank_F = minr; pb.max_rank_F = maxr;
   pb.qr_ms = qr_ms; pb.qr_flops = qr_flops;
+  pb.fac_ms = fac_ms; pb.fac_flops = fac_flops; pb.rhs_ms = rhs_ms; pb.rhs_flops = rhs_flops;
   pb.t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 done:
   dfree(ws1); dfree(Z); dfree(Zp); dfree(D); dfree(ws2); dfree(X2); dfree(Yf); dfree(Xf); dfree(Zpts);

@@ -577,10 +577,15 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
       const double cost = waves / (double)cs * (1.0 + 0.02 * cs);
       if (cost < best * (1.0 - 1e-9)) { best = cost; bcs = cs; }
     }
+    if (q.ev) cudaEventRecord(q.ev[0], st);
     const int rc = launch_qrcp<T>(a, q.nb, shm, bcs, st);
     if (rc) return rc;
+    if (q.ev) cudaEventRecord(q.ev[1], st);
   }
-  if (q.k <= 0) return LMFS_OK;
+  if (q.k <= 0) {
+    if (q.ev) cudaEventRecord(q.ev[2], st);
+    return LMFS_OK;
+  }
   // the reflector copies start at even rows of columns ld apart: 16-byte
   // alignment needs an even ld and matrix stride and an aligned base
   if ((q.ld & 1) || (q.mstride & 1) || ((uintptr_t)q.A & 15)) {
@@ -616,7 +621,9 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
     if (cost < best * (1.0 - 1e-9)) { best = cost; pick = g; }
   }
   if (!pick.kt) { set_last_error("right-hand-side tile does not fit in shared memory"); return LMFS_ERR_INVALID; }
-  return apply_call(pick.kt, pick.nbuf, true, ab, q.nb, shm_of(pick), st);
+  const int rc = apply_call(pick.kt, pick.nbuf, true, ab, q.nb, shm_of(pick), st);
+  if (q.ev) cudaEventRecord(q.ev[2], st);
+  return rc;
 }
 
 }  // namespace lmfs
