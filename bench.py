@@ -88,6 +88,25 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
+# DRAM traffic of the pivoted-QR kernel (qrcp_kernel) per timed step -- its two
+# launches, the fine pair systems and the peanut systems of the P = 100 batch --
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; command
+# and figures in profiles/qrcp_kernel_p100_mobility.md).  Valid only for the
+# kernel source it was taken on: reported as null once lmfs_qr.cu changes.
+QRCP_TRAFFIC_BYTES = 23268326400 + 24799382784 + 14395136 + 2254336
+QRCP_TRAFFIC_SRC_SHA256 = "b34fd80cbe5cdcd050074b3dcef08db6c48e93d1acdc17f5d1ee738504fdbf6e"
+
+
+def qrcp_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2606_11273_gb300", "csrc", "lmfs_qr.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return QRCP_TRAFFIC_BYTES if h == QRCP_TRAFFIC_SRC_SHA256 else None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -208,7 +227,7 @@ def run_ours(args):
         info = step()
     torch.cuda.synchronize()
     vel_gpu = out_d.cpu().numpy()
-    lat, qr_ms, qr_flops = [], [], []
+    lat, qr_ms, qr_flops, fac, rhs = [], [], [], [], []
     iters = []
     if ws > 1:
         dist.barrier()
@@ -227,6 +246,8 @@ def run_ours(args):
             st = s.stats(L.MOBILITY)
             qr_ms.append(st["qr_ms"])
             qr_flops.append(st["qr_flops"])
+            fac.append((st["factor_ms"], st["factor_flops"]))
+            rhs.append((st["rhs_ms"], st["rhs_flops"]))
             iters.append(info["iters"])
         ev_all1.record(stream)
         torch.cuda.synchronize()
@@ -254,7 +275,8 @@ def run_ours(args):
         sm_max = pk_.get("sm_max_mhz", 2070.0)
         fp64_peak_tf = 152 * 2 * 2 * sm_max * 1e6 / 1e12
         qr_t = float(np.mean(qr_ms))
-        qr_tf = float(np.mean(qr_flops)) / (qr_t * 1e-3) / 1e12
+        fac_ms = float(np.mean([f[0] for f in fac])); fac_tf = float(np.mean([f[1] for f in fac])) / (fac_ms * 1e-3) / 1e12
+        rhs_ms = float(np.mean([f[0] for f in rhs])); rhs_tf = float(np.mean([f[1] for f in rhs])) / (rhs_ms * 1e-3) / 1e12
         stk = stokeslet_kernel_rate(L, torch, stream)
         fp32_peak_tf = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         # accuracy of the timed result against the oracle (not timed)
@@ -281,11 +303,16 @@ def run_ours(args):
             "e2e": {"value": 1e3 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": nbytes_in,
                     "d2h_bytes_per_step": pk.P * 3 * 8},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "qrcp_kernel (batched FP64 pair QR)",
-                         "achieved": qr_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
-                         "frac": qr_tf / fp64_peak_tf, "traffic": None,
+            "roofline": {"bound": "alu", "kernel": "qrcp_kernel (pivoted FP64 QR of the pair systems, 2 launches/step)",
+                         "achieved": fac_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
+                         "frac": fac_tf / fp64_peak_tf, "traffic": qrcp_traffic(),
+                         "traffic_note": "DRAM bytes of the step's qrcp launches from ncu, null if the kernel changed",
                          "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
-                         "kernel_ms_per_step": qr_t, "share_of_step": qr_t / (t_ms / args.steps)},
+                         "kernel_ms_per_step": fac_ms, "share_of_step": fac_ms / (t_ms / args.steps)},
+            "roofline_rhs": {"bound": "alu", "kernel": "apply_qt_kernel (Q^T B and back substitution)",
+                             "achieved": rhs_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
+                             "frac": rhs_tf / fp64_peak_tf, "kernel_ms_per_step": rhs_ms},
+            "qr_ms_per_step": qr_t,
             "stokeslet_tile_kernel": {**stk, "flops_per_pair": 17,
                                       "achieved_tflops_17": stk["gpair_per_s"] * 17 / 1e3,
                                       "fp32_peak_tflops": fp32_peak_tf,
