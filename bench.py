@@ -166,7 +166,7 @@ def oracle_solve(pk, ft):
     return s.solve(ft)
 
 
-def stokeslet_kernel_rate(L, torch, stream):
+def stokeslet_kernel_rate(L, torch, stream, precision):
     """Direct FP32 tile kernel at the P = 10^4 problem's size: 10^4 source
     disks x 60 sources on a square lattice (spacing 4.4) and 72 targets per
     lattice cell on a radius-0.5 circle about the cell centre (every target
@@ -188,17 +188,28 @@ def stokeslet_kernel_rate(L, torch, stream):
     out = torch.zeros_like(T)
     pairs = T.shape[0] * S.shape[0] * S.shape[1]
     with torch.cuda.stream(stream):
-        L.stokeslet_sum(T, Cc, O, S, stream=stream.cuda_stream, out=out)   # warm-up
+        L.stokeslet_sum(T, Cc, O, S, precision=precision, stream=stream.cuda_stream, out=out)   # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 3
         e0.record(stream)
         for _ in range(reps):
-            L.stokeslet_sum(T, Cc, O, S, stream=stream.cuda_stream, out=out)
+            L.stokeslet_sum(T, Cc, O, S, precision=precision, stream=stream.cuda_stream, out=out)
         e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # sampled targets for an FP64 check (rank 0, beside the CPU baseline)
+    idx = np.random.default_rng(1).choice(T.shape[0], 12, replace=False)
+    sample = {"targets": targets[idx], "sources": (centres[:, None, :] + off).reshape(-1, 2), "s": s.reshape(-1),
+              "gpu": out.cpu().numpy()[idx]}
     return {"targets": int(T.shape[0]), "sources": int(S.shape[0] * S.shape[1]), "ms_per_sum": ms,
-            "gpair_per_s": pairs / (ms * 1e-3) / 1e9}
+            "gpair_per_s": pairs / (ms * 1e-3) / 1e9}, sample
+
+
+def stokeslet_sample_error(sample):
+    """Relative 2-norm error of the sampled targets against FP64 direct summation."""
+    from oracle.kernel import stokeslet
+    ref = (stokeslet(sample["targets"], sample["sources"]) @ sample["s"]).reshape(-1, 2)
+    return float(np.linalg.norm(sample["gpu"] - ref) / np.linalg.norm(ref))
 
 
 def run_ours(args):
@@ -277,7 +288,8 @@ def run_ours(args):
         qr_t = float(np.mean(qr_ms))
         fac_ms = float(np.mean([f[0] for f in fac])); fac_tf = float(np.mean([f[1] for f in fac])) / (fac_ms * 1e-3) / 1e12
         rhs_ms = float(np.mean([f[0] for f in rhs])); rhs_tf = float(np.mean([f[1] for f in rhs])) / (rhs_ms * 1e-3) / 1e12
-        stk = stokeslet_kernel_rate(L, torch, stream)
+        stk, stk_sample = stokeslet_kernel_rate(L, torch, stream, L.FP32_FAST)
+        stk_series, stk_series_sample = stokeslet_kernel_rate(L, torch, stream, L.MIXED_DIRECT)
         fp32_peak_tf = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         # accuracy of the timed result against the oracle (not timed)
         t0 = time.perf_counter()
@@ -313,10 +325,14 @@ def run_ours(args):
                              "achieved": rhs_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
                              "frac": rhs_tf / fp64_peak_tf, "kernel_ms_per_step": rhs_ms},
             "qr_ms_per_step": qr_t,
-            "stokeslet_tile_kernel": {**stk, "flops_per_pair": 17,
+            "stokeslet_tile_kernel": {**stk, "kernel": "far32_lean_kernel (LMFS_FP32_FAST)", "flops_per_pair": 17,
                                       "achieved_tflops_17": stk["gpair_per_s"] * 17 / 1e3,
                                       "fp32_peak_tflops": fp32_peak_tf,
-                                      "frac_17": stk["gpair_per_s"] * 17 / 1e3 / fp32_peak_tf},
+                                      "frac_17": stk["gpair_per_s"] * 17 / 1e3 / fp32_peak_tf,
+                                      "err_vs_fp64_sampled": stokeslet_sample_error(stk_sample)},
+            "stokeslet_series_kernel": {**stk_series, "kernel": "far32_kernel<2> (LMFS_MIXED_DIRECT)",
+                                        "frac_17": stk_series["gpair_per_s"] * 17 / 1e3 / fp32_peak_tf,
+                                        "err_vs_fp64_sampled": stokeslet_sample_error(stk_series_sample)},
             "clocks": clocks,
             "cpu_baseline": {"value": 1.0 / oracle_s, "unit": "solves/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": "one full solve of the same workload (numpy FP64)",
@@ -440,7 +456,7 @@ def run_profile_case(case):
             for _ in range(3):
                 s.matvec(L.MOBILITY, mu, u, L.MIXED)
         torch.cuda.synchronize()
-    elif case == "stokeslet":
+    elif case in ("stokeslet", "stokeslet_fast"):
         # 2000 source disks x 60 sources, 2000 x 72 targets (1.7e10 pairs)
         n = 45
         h = 4.4
@@ -454,8 +470,9 @@ def run_profile_case(case):
         targets = ((centres + h / 2)[:, None, :] + 0.5 * np.stack([np.cos(ph), np.sin(ph)], -1)[None]).reshape(-1, 2)
         d = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
         T, Cc, O, S = d(targets), d(centres), d(off), d(s)
+        prec = L.FP32_FAST if case == "stokeslet_fast" else L.MIXED_DIRECT
         for _ in range(2):
-            L.stokeslet_sum(T, Cc, O, S, stream=stream.cuda_stream)
+            L.stokeslet_sum(T, Cc, O, S, precision=prec, stream=stream.cuda_stream)
         torch.cuda.synchronize()
     print(f"profile case {case} done")
 
@@ -466,7 +483,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile-case", default=None, choices=["qr", "matvec", "stokeslet", "m2p_large", "matvec_large"],
+    ap.add_argument("--profile-case", default=None, choices=["qr", "matvec", "stokeslet", "stokeslet_fast", "m2p_large", "matvec_large"],
                     help="run one small bounded case for an ncu capture and exit")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="non-default workloads print timings and full-size checks, not the contract line")

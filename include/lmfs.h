@@ -53,6 +53,11 @@ extern "C" {
                           compensated).  Accurate only for strengths without large
                           high Fourier modes (e.g. the completion flow); the pair
                           corrections of close contacts violate that.                      */
+#define LMFS_FP32_FAST 3 /* lmfs_stokeslet_sum only: direct FP32 tiles with the hardware
+                          approximate base-2 logarithm and reciprocal (one reciprocal
+                          shared by two targets), per-disk recentring and compensated
+                          per-disk partials; about 1e-7 relative on smooth or random
+                          strengths, no restriction on target distance but r > 0.     */
 
 /* ---- parameters (Sec. 5 and Sec. 6; defaults from lmfs_params_default) */
 typedef struct lmfs_params {
@@ -180,7 +185,10 @@ int lmfs_get_solution(lmfs_handle h, double* mu_dev);
  * grouped in disks of n_per_disk around centres; DEVICE pointers:
  * targets [nt][2] (double), centres [nd][2] (double), offsets [nd][n_per_disk][2]
  * (double, source minus centre), strengths [nd][n_per_disk][2] (double),
- * out [nt][2] (double).  No exclusions. */
+ * out [nt][2] (double).  No exclusions.  precision: LMFS_MIXED_DIRECT (or
+ * LMFS_MIXED, the same): the series kernel, which rejects targets within 4
+ * source-ring radii of a disk centre (LMFS_ERR_INVALID); LMFS_FP32_FAST: the
+ * lean kernel, which rejects a target on a source (r = 0). */
 int lmfs_stokeslet_sum(const double* targets, int nt, const double* centres,
                        const double* offsets, const double* strengths, int nd,
                        int n_per_disk, double mu, int precision, void* stream, double* out);

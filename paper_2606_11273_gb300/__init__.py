@@ -10,9 +10,9 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import FP64, MIXED, MIXED_DIRECT, MOBILITY, RESISTANCE, LmfsError  # noqa: F401
+from ._lib import FP32_FAST, FP64, MIXED, MIXED_DIRECT, MOBILITY, RESISTANCE, LmfsError  # noqa: F401
 
-__all__ = ["Params", "Solver", "Server", "stokeslet_sum", "FP64", "MIXED", "MIXED_DIRECT", "RESISTANCE",
+__all__ = ["Params", "Solver", "Server", "stokeslet_sum", "FP64", "MIXED", "MIXED_DIRECT", "FP32_FAST", "RESISTANCE",
            "MOBILITY", "LmfsError"]
 
 
@@ -147,7 +147,8 @@ class Solver:
 
 def stokeslet_sum(targets, centres, offsets, strengths, mu=1.0, precision=MIXED_DIRECT, stream=None, out=None):
     """u_m = sum_n S(x_m, y_n) s_n with FP32 direct tiles (device tensors, float64):
-    targets [nt, 2], centres [nd, 2], offsets/strengths [nd, npd, 2] -> out [nt, 2]."""
+    targets [nt, 2], centres [nd, 2], offsets/strengths [nd, npd, 2] -> out [nt, 2].
+    precision: MIXED_DIRECT (recentred series kernel) or FP32_FAST (lean kernel)."""
     lib = _lib.load()
     nt = targets.shape[0]
     nd, npd = offsets.shape[0], offsets.shape[1]

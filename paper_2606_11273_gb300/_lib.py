@@ -25,6 +25,7 @@ MOBILITY = 1
 FP64 = 0
 MIXED = 1
 MIXED_DIRECT = 2
+FP32_FAST = 3
 
 
 class lmfs_params(ctypes.Structure):

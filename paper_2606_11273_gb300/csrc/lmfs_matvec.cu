@@ -1029,6 +1029,229 @@ __global__ void post_kernel(const double* __restrict__ lb, const double* __restr
 
 }  // namespace
 
+// ---- lean FP32 tile kernel (stand-alone sum, LMFS_FP32_FAST) ------------------
+// Per source disk k, target offset X = x - c_k in double-float then FP32; per
+// source j (offset y_j, strength s_j) and the thread's two targets a, b:
+//   d = X - y_j,  r^2 = |d|^2,  L = lg2 r^2 (hardware approximation),
+//   1/r_a^2 = r_b^2 / (r_a^2 r_b^2) (one hardware reciprocal for both),
+//   sums  sum L s_j  and  sum d (d . s_j) / r^2  kept apart and combined per
+//   disk: u_k = -(ln 2 / 2) sum L s + sum d (d.s) / r^2, then added with
+//   compensation.  Twelve and a half FMA-pipe operations and one and a half
+//   special-function operations per (target, source) pair; the two targets of
+//   a pair run in packed two-wide FP32 instructions, so that the issue slots
+//   the special functions take leave the FMA pipe fed.
+constexpr int FL_TILE = 8;        // source disks per staged tile
+
+__global__ void records_lean(const double* __restrict__ centres, const double* __restrict__ off,
+                             const double* __restrict__ s, int nd, int npd, float4* __restrict__ rec,
+                             float4* __restrict__ dsk) {
+  const long long n = (long long)nd * npd;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+    const float yx = (float)off[2 * o], yy = (float)off[2 * o + 1], sx = (float)s[2 * o], sy = (float)s[2 * o + 1];
+    rec[2 * o] = make_float4(-yx, -yx, -yy, -yy);     // pairs for the packed two-target arithmetic
+    rec[2 * o + 1] = make_float4(sx, sx, sy, sy);
+    if (o % npd == 0) {
+      const long long i = o / npd;
+      const double cx = centres[2 * i], cy = centres[2 * i + 1];
+      const float hx = (float)cx, hy = (float)cy;
+      dsk[i] = make_float4(hx, hy, (float)(cx - (double)hx), (float)(cy - (double)hy));
+    }
+  }
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+struct LeanArgs {
+  const double* targets; int nt;
+  const float4* dsk;     // [nd] centre (hi, lo)
+  const float4* rec;     // [nd][npd][2] (-y_x, -y_x, -y_y, -y_y), (s_x, s_x, s_y, s_y)
+  int nd, npd, kchunk;
+  double cmu;
+  double* out; long long out_stride;
+  int* err; int* range_err;
+};
+
+template <int TPT>   // targets per thread, even: packed in pairs sharing one reciprocal
+__global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel(LeanArgs a) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  const int npd = a.npd;
+  const uint32_t rec_bytes = (uint32_t)(FL_TILE * npd * 32);
+  float4* const rbuf0 = (float4*)lsm;
+  float4* const rbuf1 = (float4*)(lsm + rec_bytes);
+  float4* const dbuf0 = (float4*)(lsm + 2 * rec_bytes);
+  float4* const dbuf1 = (float4*)(lsm + 2 * rec_bytes + FL_TILE * 16);
+  uint64_t* bars = (uint64_t*)(lsm + 2 * rec_bytes + 2 * FL_TILE * 16);
+  __shared__ int s_fail;
+
+  const int t0 = TPT * (blockIdx.x * F_THREADS + threadIdx.x);
+  const bool act = t0 < a.nt;
+  // targets in double-float
+  float hx[TPT], hy[TPT], lx[TPT], ly[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    hx[q] = hy[q] = lx[q] = ly[q] = 0.f;
+    const int t = t0 + q;
+    if (t < a.nt) {
+      const double x = a.targets[2 * t], y = a.targets[2 * t + 1];
+      hx[q] = (float)x; hy[q] = (float)y;
+      lx[q] = (float)(x - (double)hx[q]); ly[q] = (float)(y - (double)hy[q]);
+    }
+  }
+  const int k_begin = blockIdx.y * a.kchunk;
+  const int k_end = min(a.nd, k_begin + a.kchunk);
+  float sx[TPT], sy[TPT], cx[TPT], cy[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) sx[q] = sy[q] = cx[q] = cy[q] = 0.f;
+
+  const int ntile = (k_end - k_begin + FL_TILE - 1) / FL_TILE;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int tile) {
+    const int kb = k_begin + tile * FL_TILE;
+    const int nd = min(FL_TILE, k_end - kb);
+    const int buf = tile & 1;
+    const uint32_t rb = (uint32_t)(nd * npd * 32), db = (uint32_t)(nd * 16);
+    mbar_expect_tx(&bars[buf], rb + db);
+    bulk_g2s(buf ? rbuf1 : rbuf0, a.rec + 2LL * kb * npd, rb, &bars[buf]);
+    bulk_g2s(buf ? dbuf1 : dbuf0, a.dsk + kb, db, &bars[buf]);
+  };
+  if (threadIdx.x == 0 && ntile > 0) issue(0);
+  for (int tile = 0; tile < ntile; ++tile) {
+    const int buf = tile & 1;
+    if (threadIdx.x == 0 && tile + 1 < ntile) issue(tile + 1);
+    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    const int nd = min(FL_TILE, k_end - (k_begin + tile * FL_TILE));
+    const float4* R = buf ? rbuf1 : rbuf0;
+    const float4* Dk = buf ? dbuf1 : dbuf0;
+    if (act) {
+      for (int dd = 0; dd < nd; ++dd) {
+        const float4 c = Dk[dd];
+        constexpr int NP = TPT / 2;
+        float2 X[NP], Y[NP], ax[NP], ay[NP], bx[NP], by[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          X[p] = make_float2((hx[2 * p] - c.x) + (lx[2 * p] - c.z), (hx[2 * p + 1] - c.x) + (lx[2 * p + 1] - c.z));
+          Y[p] = make_float2((hy[2 * p] - c.y) + (ly[2 * p] - c.w), (hy[2 * p + 1] - c.y) + (ly[2 * p + 1] - c.w));
+          ax[p] = ay[p] = bx[p] = by[p] = make_float2(0.f, 0.f);
+        }
+        const float4* Rd = R + 2 * dd * npd;
+#pragma unroll 2
+        for (int j = 0; j < npd; ++j) {
+          const float4 ya = Rd[2 * j], sa = Rd[2 * j + 1];
+          const float2 nyx = make_float2(ya.x, ya.y), nyy = make_float2(ya.z, ya.w);
+          const float2 sxx = make_float2(sa.x, sa.y), syy = make_float2(sa.z, sa.w);
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const float2 dx = __fadd2_rn(X[p], nyx), dy = __fadd2_rn(Y[p], nyy);
+            const float2 r = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            const float2 L = make_float2(lg2_approx(r.x), lg2_approx(r.y));
+            const float ip = rcp_approx(r.x * r.y);
+            const float2 inv = make_float2(ip * r.y, ip * r.x);
+            const float2 t = __fmul2_rn(__ffma2_rn(dx, sxx, __fmul2_rn(dy, syy)), inv);
+            ax[p] = __ffma2_rn(L, sxx, ax[p]);
+            ay[p] = __ffma2_rn(L, syy, ay[p]);
+            bx[p] = __ffma2_rn(t, dx, bx[p]);
+            by[p] = __ffma2_rn(t, dy, by[p]);
+          }
+        }
+        const float hl = -0.34657359027997264f;   // -(ln 2) / 2
+        // compensated accumulation of the disk partials
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+          const int p = q >> 1;
+          const float axq = (q & 1) ? ax[p].y : ax[p].x, ayq = (q & 1) ? ay[p].y : ay[p].x;
+          const float bxq = (q & 1) ? bx[p].y : bx[p].x, byq = (q & 1) ? by[p].y : by[p].x;
+          const float ux = fmaf(hl, axq, bxq), uy = fmaf(hl, ayq, byq);
+          float yk = ux - cx[q];
+          float tk = sx[q] + yk;
+          cx[q] = (tk - sx[q]) - yk;
+          sx[q] = tk;
+          yk = uy - cy[q];
+          tk = sy[q] + yk;
+          cy[q] = (tk - sy[q]) - yk;
+          sy[q] = tk;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) { if (threadIdx.x == 0) atomicExch(a.err, 1); return; }
+  double* o = a.out + blockIdx.y * a.out_stride;
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int t = t0 + q;
+    if (t >= a.nt) break;
+    const double ux = ((double)sx[q] - (double)cx[q]) * a.cmu, uy = ((double)sy[q] - (double)cy[q]) * a.cmu;
+    bad |= !isfinite(ux) || !isfinite(uy);       // a target on a source (r = 0)
+    o[2 * t] = ux;
+    o[2 * t + 1] = uy;
+  }
+  if (bad) atomicExch(a.range_err, 1);
+}
+
+int stokeslet_sum_lean(const double* targets, int nt, const double* centres, const double* offsets,
+                       const double* strengths, int nd, int npd, double mu, cudaStream_t st, double* out) {
+  int dev_sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
+  constexpr int LT = 2;                    // targets per thread
+  const long long bx = ((long long)(nt + LT - 1) / LT + F_THREADS - 1) / F_THREADS;
+  long long split = std::max<long long>(1, (4LL * dev_sms + bx - 1) / bx);
+  int kchunk = (int)((nd + split - 1) / split);
+  kchunk = ((kchunk + FL_TILE - 1) / FL_TILE) * FL_TILE;
+  split = (nd + kchunk - 1) / kchunk;
+  const size_t shm = 2 * (size_t)FL_TILE * npd * 32 + 2 * FL_TILE * 16 + 16;
+  if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); return LMFS_ERR_INVALID; }
+  float4* dsk = nullptr; float4* rec = nullptr; int* err = nullptr; double* part = nullptr;
+  auto A = [&](void** p, size_t b) { return cudaMallocAsync(p, b, st); };
+  int rc = LMFS_OK;
+  if (cuda_failed(A((void**)&dsk, (size_t)nd * sizeof(float4)), "alloc") ||
+      cuda_failed(A((void**)&rec, 2 * (size_t)nd * npd * sizeof(float4)), "alloc") ||
+      cuda_failed(A((void**)&err, 2 * sizeof(int)), "alloc") ||
+      (split > 1 && cuda_failed(A((void**)&part, split * 2LL * nt * sizeof(double)), "alloc")))
+    rc = LMFS_ERR_NOMEM;
+  int herr[2] = {0, 0};
+  if (rc == LMFS_OK) {
+    cudaMemsetAsync(err, 0, 2 * sizeof(int), st);
+    records_lean<<<(int)std::min<long long>(((long long)nd * npd + 255) / 256, 8192), 256, 0, st>>>(
+        centres, offsets, strengths, nd, npd, rec, dsk);
+    rc = check_launch("records_lean");
+    LeanArgs a;
+    a.targets = targets; a.nt = nt; a.dsk = dsk; a.rec = rec; a.nd = nd; a.npd = npd; a.kchunk = kchunk;
+    a.cmu = INV4PI / mu; a.out = split > 1 ? part : out; a.out_stride = 2LL * nt; a.err = err; a.range_err = err + 1;
+    if (rc == LMFS_OK &&
+        cuda_failed(cudaFuncSetAttribute(far32_lean_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr"))
+      rc = LMFS_ERR_CUDA;
+    if (rc == LMFS_OK) {
+      far32_lean_kernel<LT><<<dim3((unsigned)bx, (unsigned)split), F_THREADS, shm, st>>>(a);
+      rc = check_launch("far32_lean");
+    }
+    if (rc == LMFS_OK && split > 1) {
+      reduce_splits<<<(int)std::min<long long>((2LL * nt + 255) / 256, 4096), 256, 0, st>>>(part, 2LL * nt, (int)split, 2LL * nt, out);
+      rc = check_launch("reduce");
+    }
+    if (rc == LMFS_OK && (cuda_failed(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st), "d2h") ||
+                          cuda_failed(cudaStreamSynchronize(st), "sync")))
+      rc = LMFS_ERR_CUDA;
+  }
+  cudaFreeAsync(dsk, st); cudaFreeAsync(rec, st); cudaFreeAsync(err, st); if (part) cudaFreeAsync(part, st);
+  if (rc == LMFS_OK && herr[0]) { set_last_error("far32_lean: bounded wait expired"); rc = LMFS_ERR_CUDA; }
+  if (rc == LMFS_OK && herr[1]) { set_last_error("lmfs_stokeslet_sum: a target coincides with a source"); rc = LMFS_ERR_INVALID; }
+  return rc;
+}
+
 // Kernel attributes and the error flag are set up once per handle, outside
 // any stream capture.
 int far_field_prepare(Ctx& c) {
@@ -1192,8 +1415,10 @@ int stokeslet_sum_standalone(const double* targets, int nt, const double* centre
     set_last_error("lmfs_stokeslet_sum: bad sizes or null pointers");
     return LMFS_ERR_INVALID;
   }
+  if (precision == LMFS_FP32_FAST)
+    return stokeslet_sum_lean(targets, nt, centres, offsets, strengths, nd, npd, mu, st, out);
   if (precision != LMFS_MIXED_DIRECT && precision != LMFS_MIXED) {
-    set_last_error("lmfs_stokeslet_sum: precision must be LMFS_MIXED_DIRECT (FP32 direct tiles)");
+    set_last_error("lmfs_stokeslet_sum: precision must be LMFS_MIXED_DIRECT or LMFS_FP32_FAST (FP32 direct tiles)");
     return LMFS_ERR_INVALID;
   }
   int dev_sms = 152, dev = 0;

@@ -295,6 +295,11 @@ def test_stokeslet_sum_standalone(L):
                           dev(s).reshape(nd, npd, 2))
     torch.cuda.synchronize()
     assert rel(out.cpu().numpy(), ref) < 1e-6
+    # the lean kernel (hardware logarithm and reciprocal) on the same sums
+    fast = L.stokeslet_sum(dev(targets).reshape(-1, 2), dev(centres).reshape(-1, 2), dev(off).reshape(nd, npd, 2),
+                           dev(s).reshape(nd, npd, 2), precision=L.FP32_FAST)
+    torch.cuda.synchronize()
+    assert rel(fast.cpu().numpy(), ref) < 1e-6
     # a target inside the series range of a disk is rejected, not mis-summed
     bad = np.array([[centres[0, 0] + 1.0, centres[0, 1]]])
     with pytest.raises(L.LmfsError):
