@@ -424,6 +424,95 @@ def run_large(args):
     print(json.dumps(res))
 
 
+def run_serving(args):
+    """Serving stream (Poisson arrivals, mixed disk counts and problems)
+    through the continuous-batching server in the mixed-precision form,
+    against the same requests solved one at a time in FP64 on the GPU.
+    Prints one JSON line (a side report; the contract line is the default run)."""
+    import torch
+    from paper_2606_11273_gb300 import build as b
+    b.build()
+    import paper_2606_11273_gb300 as L
+    import workloads as w
+    t0 = time.perf_counter()
+    stream = w.serving_stream(args.requests, seed=0, pmax=args.pmax)
+    t_gen = time.perf_counter() - t0
+    prm = lambda: L.Params(tol=1e-7)
+    # warm-up: load the library, first-use costs of CUDA
+    pk0 = w.packing(20, 0.4, 1, gmin=1e-2, start="square", nsweep=2)
+    s0 = L.Solver(pk0.centres, pk0.radii, prm()); s0.solve(L.MOBILITY, w.forces_torques(20, 1)); s0.close()
+    torch.cuda.synchronize()
+    # served, mixed precision: submit at the arrival times, poll without blocking
+    srv = L.Server(hbm_budget_bytes=150 << 30, max_slots=args.slots, precision=L.MIXED)
+    pending, done, lat = {}, {}, {}
+    q = 0
+    start = time.perf_counter()
+    with Clocks(0) as clk:
+        while q < len(stream) or pending:
+            now = time.perf_counter() - start
+            while q < len(stream) and stream[q][0] <= now:
+                t_arr, pk, problem, data = stream[q]
+                tk, P = srv.submit(pk.centres, pk.radii, problem, data, prm())
+                pending[q] = (tk, P, time.perf_counter())
+                q += 1
+            for k in list(pending):
+                tk, P, ts = pending[k]
+                rc, out, info = srv.poll(tk, P, timeout_us=0)
+                if rc != L._lib.LMFS_PENDING:
+                    lat[k] = time.perf_counter() - ts
+                    done[k] = (rc, out, info)
+                    del pending[k]
+            time.sleep(0.0005)
+    served_s = time.perf_counter() - start
+    srv.close()
+    # one at a time, FP64, same requests
+    ref, ref_info, seq_lat = {}, {}, []
+    t1 = time.perf_counter()
+    for k, (t_arr, pk, problem, data) in enumerate(stream):
+        ts = time.perf_counter()
+        so = L.Solver(pk.centres, pk.radii, L.Params(tol=1e-7, precision=L.FP64))
+        out, info = so.solve(problem, data)
+        so.close()
+        ref[k] = out
+        ref_info[k] = info
+        seq_lat.append(time.perf_counter() - ts)
+    seq_s = time.perf_counter() - t1
+    # the same arrivals served first come, first served by the one-at-a-time form
+    seq_done, seq_queue_lat = 0.0, []
+    for k, (t_arr, _, _, _) in enumerate(stream):
+        seq_done = max(seq_done, t_arr) + seq_lat[k]
+        seq_queue_lat.append(seq_done - t_arr)
+    ok = [k for k in done if done[k][0] == 0 and ref_info[k]["converged"]]
+    errs = [float(np.linalg.norm(done[k][1] - ref[k]) / np.linalg.norm(ref[k])) for k in ok]
+    bad = [k for k in done if done[k][0] != 0 or not ref_info[k]["converged"]]
+    lat_ms = np.array([lat[k] for k in sorted(lat)]) * 1e3
+    Ps = [x[1].P for x in stream]
+    print(json.dumps({
+        "serving": {"requests": len(stream), "P_range": [min(Ps), max(Ps)], "P_median": float(np.median(Ps)),
+                    "mean_arrival_gap_ms": 20.0, "hbm_budget_gb": 150, "slots": args.slots, "tol": 1e-7,
+                    "generation_s": t_gen},
+        "served_mixed": {"solves_per_s": len(stream) / served_s, "wall_s": served_s,
+                         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                                        "max": float(lat_ms.max())}},
+        "one_at_a_time_fp64": {"solves_per_s": len(stream) / seq_s, "wall_s": seq_s,
+                               "latency_ms": {"p50": float(np.percentile(seq_queue_lat, 50) * 1e3),
+                                              "p99": float(np.percentile(seq_queue_lat, 99) * 1e3),
+                                              "note": "same arrival times, first come first served"},
+                               "solve_ms": {"p50": float(np.percentile(seq_lat, 50) * 1e3),
+                                            "p99": float(np.percentile(seq_lat, 99) * 1e3)}},
+        "speedup": seq_s / served_s,
+        "not_converged": [{"P": stream[k][1].P, "problem": stream[k][2], "rc": int(done[k][0]),
+                           "iters": int(done[k][2]["iters"]), "fp64_iters": int(ref_info[k]["iters"]),
+                           "fp64_converged": bool(ref_info[k]["converged"])} for k in bad],
+        "iters_median": {"served": float(np.median([done[k][2]["iters"] for k in done])),
+                         "fp64": float(np.median([ref_info[k]["iters"] for k in ref_info]))},
+        "served_vs_fp64_rel_2norm": {"converged_pairs": len(errs),
+                                     "median": float(np.median(errs)) if errs else None,
+                                     "max": float(np.max(errs)) if errs else None,
+                                     "n_above_1e-5": int(sum(e > 1e-5 for e in errs))},
+        "clocks": clk.summary()}))
+
+
 def run_profile_case(case):
     """Small, bounded cases for ncu captures (a few launches of one kernel)."""
     import torch
@@ -485,11 +574,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile-case", default=None, choices=["qr", "matvec", "stokeslet", "stokeslet_fast", "m2p_large", "matvec_large"],
                     help="run one small bounded case for an ncu capture and exit")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving stream: served mixed precision against one-at-a-time FP64 (side report)")
+    ap.add_argument("--requests", type=int, default=64, help="serving: requests in the stream (config: 256)")
+    ap.add_argument("--pmax", type=int, default=5000, help="serving: largest disk count")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent request slots")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="non-default workloads print timings and full-size checks, not the contract line")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)
+        return
+    if args.serving:
+        run_serving(args)
         return
     if args.workload != WORKLOAD:
         run_large(args)

@@ -281,3 +281,25 @@ def smooth_surface_vector(P, Mc, seed, modes=4):
         out[:, :, 0] += a[:, 0, 0:1] * np.cos(m * th) + a[:, 0, 1:2] * np.sin(m * th)
         out[:, :, 1] += a[:, 1, 0:1] * np.cos(m * th) + a[:, 1, 1:2] * np.sin(m * th)
     return out
+
+
+def serving_stream(n, seed=0, pmin=50, pmax=5000, mean_gap_s=0.02):
+    """Seeded request stream: Poisson arrivals (mean mean_gap_s apart); each a
+    square-lattice packing with P log-uniform in [pmin, pmax], area fraction
+    uniform in [0.3, 0.65], minimum gap log-uniform in [1e-3, 1e-1] (the
+    closest pair snapped to it), resistance or mobility with probability 1/2,
+    inputs N(0, 1) as rigid_velocities / forces_torques.
+    Returns a list of (arrival_s, Packing, problem (0 resistance, 1 mobility),
+    inputs [P, 3])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out, t = [], 0.0
+    for q in range(n):
+        t += float(rng.exponential(mean_gap_s))
+        P = int(round(math.exp(rng.uniform(math.log(pmin), math.log(pmax)))))
+        phi = float(rng.uniform(0.3, 0.65))
+        gmin = float(10 ** rng.uniform(-3, -1))
+        problem = int(rng.integers(0, 2))
+        pk = packing(P, phi, 1000 + q, gmin=gmin, start="square", nsweep=3, snap_gap=gmin)
+        data = rigid_velocities(P, 5000 + q) if problem == 0 else forces_torques(P, 5000 + q)
+        out.append((t, pk, problem, data))
+    return out
