@@ -97,23 +97,25 @@ struct PairGeo {
   int Nfp, Nell, neq, nmob, Mp;
 };
 
-// Count the kept shielding-ellipse sources per pair side.
+// Count the kept shielding-ellipse sources per pair side: one warp per side.
 __global__ void count_enh(PairGeo g, int nb, int* nenh) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * nb) return;
-  const int q = g.first + t / 2, side = t & 1;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= 2 * nb) return;
+  const int q = g.first + w / 2, side = w & 1;
   const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
   PairFrame f = make_frame(g.centres[2 * i], g.centres[2 * i + 1], g.radii[i], g.centres[2 * k],
                            g.centres[2 * k + 1], g.radii[k]);
   const double a = side == 0 ? f.p1 : f.p2, rad = side == 0 ? f.r1 : f.r2;
   int n = 0;
   if (a > rad * g.Rf) {
-    for (int j = 0; j < 2 * g.Nell; ++j) {
+    for (int base = 0; base < 2 * g.Nell; base += 32) {
+      const int j = base + lane;
       double zr, zi;
-      if (ellipse_node(a, rad, g.Rf, g.Nell, g.gamma, j, &zr, &zi)) ++n;
+      const bool keep = j < 2 * g.Nell && ellipse_node(a, rad, g.Rf, g.Nell, g.gamma, j, &zr, &zi);
+      n += __popc(__ballot_sync(0xffffffffu, keep));
     }
   }
-  nenh[t] = n;
+  if (lane == 0) nenh[w] = n;
 }
 
 // Fine sources (per side: N_fp proxies then kept ellipse nodes), fine nodes
@@ -143,22 +145,27 @@ __global__ void fill_fine_sets(PairGeo g, int nb, const int* nenh, int SY, doubl
     y[0] = cx + rad * g.Rf * cos(th);
     y[1] = cy + rad * g.Rf * sin(th);
   }
-  // ellipse sources, in order of j (one thread per side)
-  if (tid < 2) {
-    const int side = tid;
+  // ellipse sources, kept ones in order of j: one warp per side, positions
+  // from the ballot of the lanes below
+  if (blockIdx.x == 0 && threadIdx.x < 64) {
+    const int side = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double a = side == 0 ? f.p1 : f.p2, rad = side == 0 ? f.r1 : f.r2;
     const double cx = side ? f.c2x : f.c1x, cy = side ? f.c2y : f.c1y;
     const double sg = side ? -1.0 : 1.0;
     int n = 0;
     if (a > rad * g.Rf) {
-      for (int j = 0; j < 2 * g.Nell; ++j) {
-        double zr, zi;
-        if (!ellipse_node(a, rad, g.Rf, g.Nell, g.gamma, j, &zr, &zi)) continue;
-        const double wr = f.cphi * zr - f.sphi * zi, wi = f.sphi * zr + f.cphi * zi;
-        double* y = Y + 2 * ((side ? nY1 : 0) + g.Nfp + n);
-        y[0] = cx + sg * wr;
-        y[1] = cy + sg * wi;
-        ++n;
+      for (int base = 0; base < 2 * g.Nell; base += 32) {
+        const int j = base + lane;
+        double zr = 0.0, zi = 0.0;
+        const bool keep = j < 2 * g.Nell && ellipse_node(a, rad, g.Rf, g.Nell, g.gamma, j, &zr, &zi);
+        const unsigned msk = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const double wr = f.cphi * zr - f.sphi * zi, wi = f.sphi * zr + f.cphi * zi;
+          double* y = Y + 2 * ((side ? nY1 : 0) + g.Nfp + n + __popc(msk & ((1u << lane) - 1u)));
+          y[0] = cx + sg * wr;
+          y[1] = cy + sg * wi;
+        }
+        n += __popc(msk);
       }
     }
     (void)e2;
@@ -362,6 +369,7 @@ __global__ void fill_FQ_sym(PairDims pd, PairGeo g, const double* Yf, const doub
 // B_f,1 K_f,1^T (both halves), coarse columns times the ring projector.
 __global__ void project_FQ_mobility_sym(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* W,
                                         int ld, long long mstride, const double* Gf) {
+  extern __shared__ double es[];            // [nY1][2] source offsets from the side-1 centre
   const int b = blockIdx.y;
   const int q = g.first + b;
   const int nY1 = pd.Nfp + pd.nenh[2 * b], nX = pd.nX, Nc = pd.Nc;
@@ -370,24 +378,30 @@ __global__ void project_FQ_mobility_sym(PairDims pd, PairGeo g, const double* Yf
   const int i = g.pairs[2 * q], k = g.pairs[2 * q + 1];
   const double* G = Gf + (long long)b * 18;   // side 1
   const double cx = g.centres[2 * i], cy = g.centres[2 * i + 1];
+  for (int s = threadIdx.x; s < nY1; s += blockDim.x) {
+    es[2 * s] = Y[2 * s] - cx;
+    es[2 * s + 1] = Y[2 * s + 1] - cy;
+  }
+  __syncthreads();
   const int rows = 2 * nX;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * rows; t += gridDim.x * blockDim.x) {
     const int half = t / rows, row = t % rows;
     double* M = W + (long long)(2 * b + half) * mstride;
     const int n = row >> 1, a = row & 1;
     double t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll 4
     for (int s = 0; s < nY1; ++s) {
       const double v0 = M[(long long)(2 * s) * ld + row], v1 = M[(long long)(2 * s + 1) * ld + row];
-      const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
-      t0 += v0; t1 += v1; t2 += -ey * v0 + ex * v1;
+      t0 += v0; t1 += v1; t2 += -es[2 * s + 1] * v0 + es[2 * s] * v1;
     }
     const double u0 = G[0] * t0 + G[1] * t1 + G[2] * t2;
     const double u1 = G[3] * t0 + G[4] * t1 + G[5] * t2;
     const double u2 = G[6] * t0 + G[7] * t1 + G[8] * t2;
     const double bx = (a == 0) ? 1.0 : 0.0, by = (a == 0) ? 0.0 : 1.0;
     const double bw = (a == 0) ? -(X[2 * n + 1] - cy) : (X[2 * n] - cx);
+#pragma unroll 4
     for (int s = 0; s < nY1; ++s) {
-      const double ex = Y[2 * s] - cx, ey = Y[2 * s + 1] - cy;
+      const double ex = es[2 * s], ey = es[2 * s + 1];
       M[(long long)(2 * s) * ld + row] += -(u0 + u2 * (-ey)) + bx + bw * (-ey);
       M[(long long)(2 * s + 1) * ld + row] += -(u1 + u2 * ex) + by + bw * ex;
     }
@@ -796,7 +810,7 @@ int build_pair_blocks(Ctx& c, int problem) {
     g.centres = c.centres; g.radii = c.radii; g.pairs = c.pairs; g.first = first;
     g.Rf = c.Rf; g.gamma = c.prm.gamma; g.rmob = c.prm.r_mob; g.rho = c.rho;
     g.Nfp = Nfp; g.Nell = Nell; g.neq = neq; g.nmob = nmob; g.Mp = Mp;
-    count_enh<<<(2 * nb + 127) / 128, 128, 0, c.stream>>>(g, nb, nenh);
+    count_enh<<<(2 * nb * 32 + 127) / 128, 128, 0, c.stream>>>(g, nb, nenh);
     if ((rc = check_launch("count_enh"))) goto done;
     if (cuda_failed(cudaMemcpyAsync(hen.data(), nenh, 2 * nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
         cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
@@ -842,7 +856,8 @@ int build_pair_blocks(Ctx& c, int problem) {
       fill_FQ_sym<<<dim3(64, nb), 256, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ldh, sh);
       if ((rc = check_launch("fill_FQ_sym"))) goto done;
       if (mob) {
-        project_FQ_mobility_sym<<<dim3((2 * ldh + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, Yf, Xf, ws1, ldh, sh, Gf);
+        project_FQ_mobility_sym<<<dim3((2 * ldh + 127) / 128, nb), 128, (size_t)SYmax * sizeof(double), c.stream>>>(
+            pd, g, Yf, Xf, ws1, ldh, sh, Gf);
         if ((rc = check_launch("project_FQ_mobility_sym"))) goto done;
       }
       QRBatch q{};
