@@ -1031,7 +1031,8 @@ __global__ void post_kernel(const double* __restrict__ lb, const double* __restr
 
 // ---- lean FP32 tile kernel (stand-alone sum, LMFS_FP32_FAST) ------------------
 // Per source disk k, target offset X = x - c_k in double-float then FP32; per
-// source j (offset y_j, strength s_j) and the thread's two targets a, b:
+// source j (offset y_j, strength s_j) and each pair (a, b) of the thread's four
+// targets:
 //   d = X - y_j,  r^2 = |d|^2,  L = lg2 r^2 (hardware approximation),
 //   1/r_a^2 = r_b^2 / (r_a^2 r_b^2) (one hardware reciprocal for both),
 //   sums  sum L s_j  and  sum d (d . s_j) / r^2  kept apart and combined per
@@ -1206,14 +1207,28 @@ int stokeslet_sum_lean(const double* targets, int nt, const double* centres, con
   int dev_sms = 152, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr int LT = 2;                    // targets per thread
+  constexpr int LT = 4;                    // targets per thread: two packed pairs
   const long long bx = ((long long)(nt + LT - 1) / LT + F_THREADS - 1) / F_THREADS;
-  long long split = std::max<long long>(1, (4LL * dev_sms + bx - 1) / bx);
+  const size_t shm = 2 * (size_t)FL_TILE * npd * 32 + 2 * FL_TILE * 16 + 16;
+  if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); return LMFS_ERR_INVALID; }
+  if (cuda_failed(cudaFuncSetAttribute(far32_lean_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr"))
+    return LMFS_ERR_CUDA;
+  // Split the source disks over blockIdx.y so that the blocks fill whole waves
+  // of the resident slots: every block runs equally long, so a partly filled
+  // last wave leaves SMs idle for a whole block's time.
+  int per_sm = 0;
+  if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far32_lean_kernel<LT>, F_THREADS, shm), "occupancy"))
+    return LMFS_ERR_CUDA;
+  const long long slots = (long long)std::max(1, per_sm) * dev_sms;
+  long long split = 1;
+  double best_fill = -1.0;
+  for (long long sp = 1; sp <= 16 && sp <= nd; ++sp) {
+    const double waves = (double)(bx * sp) / (double)slots, fill = waves / std::ceil(waves);
+    if (fill > best_fill + 0.01) { best_fill = fill; split = sp; }
+  }
   int kchunk = (int)((nd + split - 1) / split);
   kchunk = ((kchunk + FL_TILE - 1) / FL_TILE) * FL_TILE;
   split = (nd + kchunk - 1) / kchunk;
-  const size_t shm = 2 * (size_t)FL_TILE * npd * 32 + 2 * FL_TILE * 16 + 16;
-  if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); return LMFS_ERR_INVALID; }
   float4* dsk = nullptr; float4* rec = nullptr; int* err = nullptr; double* part = nullptr;
   auto A = [&](void** p, size_t b) { return cudaMallocAsync(p, b, st); };
   int rc = LMFS_OK;
@@ -1231,9 +1246,6 @@ int stokeslet_sum_lean(const double* targets, int nt, const double* centres, con
     LeanArgs a;
     a.targets = targets; a.nt = nt; a.dsk = dsk; a.rec = rec; a.nd = nd; a.npd = npd; a.kchunk = kchunk;
     a.cmu = INV4PI / mu; a.out = split > 1 ? part : out; a.out_stride = 2LL * nt; a.err = err; a.range_err = err + 1;
-    if (rc == LMFS_OK &&
-        cuda_failed(cudaFuncSetAttribute(far32_lean_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr"))
-      rc = LMFS_ERR_CUDA;
     if (rc == LMFS_OK) {
       far32_lean_kernel<LT><<<dim3((unsigned)bx, (unsigned)split), F_THREADS, shm, st>>>(a);
       rc = check_launch("far32_lean");
