@@ -134,16 +134,6 @@ static int create_ctx(Ctx& c, const double* centres, const double* radii, int P,
   LMFS_TRY(dalloc(&c.bvec, nn));
   LMFS_TRY(dalloc(&c.xsol, nn));
   LMFS_TRY(dalloc(&c.io3, 3 * (size_t)P));
-  // source-range split of the far-field kernels: aim for >= ~8 blocks per SM
-  {
-    int dev_sms = 152;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p.device);
-    const long long bx = ((long long)P * Mc / 2 + 127) / 128;
-    long long split = std::max<long long>(1, (8LL * dev_sms + bx - 1) / bx);
-    split = std::min<long long>(split, std::max(1, P / 4));
-    c.far_split = (int)split;
-    LMFS_TRY(dalloc(&c.ufar_part, (size_t)c.far_split * nn));
-  }
   LMFS_TRY(far_field_prepare(c));
   return LMFS_OK;
 }

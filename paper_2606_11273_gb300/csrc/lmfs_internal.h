@@ -10,6 +10,7 @@
 //   far-field FP32 sources: src4 [P][Nc] float4 (y_x, y_y, |y|^2, y.sigma),
 //   src2 [P][Nc] float2 (sigma_x, sigma_y), disk data dsk [P] float4x2.
 #pragma once
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -116,7 +117,10 @@ struct Ctx {
   double* lam0 = nullptr;
   float4* src4 = nullptr;
   float2* src2 = nullptr;
-  int far_split = 1;                 // source-range split of the far kernel
+  int far_split = 1;                 // largest source-range split of the far kernels
+  int split_direct = 1, kchunk_direct = 1;   // far32_kernel (LMFS_MIXED_DIRECT)
+  int split_m2p32 = 1, kchunk_m2p32 = 1;     // m2p_kernel<float> (LMFS_MIXED)
+  int split_m2p64 = 1, kchunk_m2p64 = 1;     // m2p_kernel<double> (LMFS_FP64)
   double* ufar_part = nullptr;       // [far_split][P][Mc][2]
   int sms = 152;                     // multiprocessors of the handle's device
   double2* ring = nullptr;           // [Nc] (cos, sin)(2 pi j / Nc) of the source rings
@@ -190,6 +194,27 @@ int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision)
 int post_device(Ctx& c, int problem, const double* mu, double* out3);
 int far_field(Ctx& c, const double* strength, double* out, int precision, bool mobility_sums_zero);
 int far_field_prepare(Ctx& c);
+
+// Source-range split of an all-pairs kernel whose blocks each sweep a chunk of
+// kchunk source disks (a whole number of tiles) for one tile of targets.  All
+// blocks run about equally long, so a launch of bx * split blocks on `slots`
+// resident blocks takes about ceil(bx * split / slots) x kchunk: a partly
+// filled last wave idles the other SMs for a whole block's time.  Returns the
+// split in [1, max_split] that minimises this (the smallest on ties) and its
+// chunk length; the split is the number of chunks that the rounding leaves.
+inline int wave_split(long long bx, long long slots, int nd, int tile, int max_split, int* kchunk_out) {
+  slots = std::max<long long>(1, slots);
+  int best_split = 1, best_chunk = ((nd + tile - 1) / tile) * tile;
+  long long best_cost = -1;
+  for (int sp = 1; sp <= std::max(1, max_split); ++sp) {
+    const int chunk = (((nd + sp - 1) / sp + tile - 1) / tile) * tile;
+    const int eff = (nd + chunk - 1) / chunk;
+    const long long cost = ((bx * eff + slots - 1) / slots) * (long long)chunk;
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_split = eff; best_chunk = chunk; }
+  }
+  *kchunk_out = best_chunk;
+  return best_split;
+}
 int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar,
                double* u, int problem);
 int stokeslet_sum_standalone(const double* targets, int nt, const double* centres,

@@ -1213,22 +1213,12 @@ int stokeslet_sum_lean(const double* targets, int nt, const double* centres, con
   if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); return LMFS_ERR_INVALID; }
   if (cuda_failed(cudaFuncSetAttribute(far32_lean_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr"))
     return LMFS_ERR_CUDA;
-  // Split the source disks over blockIdx.y so that the blocks fill whole waves
-  // of the resident slots: every block runs equally long, so a partly filled
-  // last wave leaves SMs idle for a whole block's time.
+  // split of the source disks over blockIdx.y that fills whole waves
   int per_sm = 0;
   if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far32_lean_kernel<LT>, F_THREADS, shm), "occupancy"))
     return LMFS_ERR_CUDA;
-  const long long slots = (long long)std::max(1, per_sm) * dev_sms;
-  long long split = 1;
-  double best_fill = -1.0;
-  for (long long sp = 1; sp <= 16 && sp <= nd; ++sp) {
-    const double waves = (double)(bx * sp) / (double)slots, fill = waves / std::ceil(waves);
-    if (fill > best_fill + 0.01) { best_fill = fill; split = sp; }
-  }
-  int kchunk = (int)((nd + split - 1) / split);
-  kchunk = ((kchunk + FL_TILE - 1) / FL_TILE) * FL_TILE;
-  split = (nd + kchunk - 1) / kchunk;
+  int kchunk = 1;
+  const long long split = wave_split(bx, (long long)std::max(1, per_sm) * dev_sms, nd, FL_TILE, 16, &kchunk);
   float4* dsk = nullptr; float4* rec = nullptr; int* err = nullptr; double* part = nullptr;
   auto A = [&](void** p, size_t b) { return cudaMallocAsync(p, b, st); };
   int rc = LMFS_OK;
@@ -1272,12 +1262,29 @@ int far_field_prepare(Ctx& c) {
   LMFS_CUDA(cudaFuncSetAttribute(m2p_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm64));
   LMFS_CUDA(cudaFuncSetAttribute(far32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   LMFS_CUDA(cudaFuncSetAttribute(far32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device);
+  {
+    // source-range splits that fill whole waves of each far kernel's resident blocks
+    const int P = c.d.P, Mc = c.d.Mc;
+    const size_t shm32 = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(float2) + 2 * M_TILE * 32 + 16;
+    int occ_d = 0, occ_32 = 0, occ_64 = 0;
+    LMFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, far32_kernel<2>, F_THREADS, shm));
+    LMFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_32, m2p_kernel<float, 2>, M_THREADS, shm32));
+    LMFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_64, m2p_kernel<double, 1>, M_THREADS, shm64));
+    const long long bx_d = ((long long)(P * Mc + 1) / 2 + F_THREADS - 1) / F_THREADS;
+    const long long bx_32 = ((long long)(P * Mc + 1) / 2 + M_THREADS - 1) / M_THREADS;
+    const long long bx_64 = ((long long)P * Mc + M_THREADS - 1) / M_THREADS;
+    constexpr int max_split = 16;
+    c.split_direct = wave_split(bx_d, (long long)std::max(1, occ_d) * c.sms, P, F_TILE, max_split, &c.kchunk_direct);
+    c.split_m2p32 = wave_split(bx_32, (long long)std::max(1, occ_32) * c.sms, P, M_TILE, max_split, &c.kchunk_m2p32);
+    c.split_m2p64 = wave_split(bx_64, (long long)std::max(1, occ_64) * c.sms, P, M_TILE, max_split, &c.kchunk_m2p64);
+    c.far_split = std::max(c.split_direct, std::max(c.split_m2p32, c.split_m2p64));
+    if (c.far_split > 1) LMFS_TRY(dalloc(&c.ufar_part, (size_t)c.far_split * 2 * Mc * P));
+  }
   LMFS_TRY(dalloc(&c.coef64, (size_t)c.d.P * MP_NCOEF));
   LMFS_TRY(dalloc(&c.coef32, (size_t)c.d.P * MP_NCOEF));
   LMFS_TRY(dalloc(&c.far_err, 2));
   LMFS_CUDA(cudaMemsetAsync(c.far_err, 0, 2 * sizeof(int), c.stream));
-  // near field: enough blocks for two per SM when the batch is small
-  cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, c.device);
   {
     std::vector<double2> ring(c.d.Nc);
     for (int j = 0; j < c.d.Nc; ++j) {
@@ -1306,11 +1313,10 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
   const int P = c.d.P, Mc = c.d.Mc, Nc = c.d.Nc;
   const long long n = (long long)P * Mc * 2;
   const double cmu = INV4PI / c.prm.mu;
-  int split = c.far_split;
-  const int kchunk_raw = (P + split - 1) / split;
+  int split = 1;
   if (precision == LMFS_MIXED_DIRECT) {
-    const int kchunk = ((kchunk_raw + F_TILE - 1) / F_TILE) * F_TILE;
-    split = (P + kchunk - 1) / kchunk;
+    const int kchunk = c.kchunk_direct;
+    split = c.split_direct;
     records_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.src4, c.dsk32);
     LMFS_TRY(check_launch("records"));
     FarArgs a;
@@ -1324,9 +1330,9 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
     far32_kernel<2><<<grid, F_THREADS, shm, c.stream>>>(a);
     LMFS_TRY(check_launch("far32"));
   } else {
-    const int kchunk = ((kchunk_raw + M_TILE - 1) / M_TILE) * M_TILE;
-    split = (P + kchunk - 1) / kchunk;
     const bool fp32 = precision == LMFS_MIXED;
+    const int kchunk = fp32 ? c.kchunk_m2p32 : c.kchunk_m2p64;
+    split = fp32 ? c.split_m2p32 : c.split_m2p64;
     p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.coef64, fp32 ? c.coef32 : nullptr);
     LMFS_TRY(check_launch("p2m"));
     MpArgs a;
@@ -1437,10 +1443,15 @@ int stokeslet_sum_standalone(const double* targets, int nt, const double* centre
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
   const long long bx = ((long long)(nt + 1) / 2 + F_THREADS - 1) / F_THREADS;
-  long long split = std::max<long long>(1, (8LL * dev_sms + bx - 1) / bx);
-  int kchunk = (int)((nd + split - 1) / split);
-  kchunk = ((kchunk + F_TILE - 1) / F_TILE) * F_TILE;
-  split = (nd + kchunk - 1) / kchunk;
+  const size_t shm_f = 2 * (size_t)F_TILE * npd * 32 + 2 * F_TILE * 32 + 16;
+  if (shm_f > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); return LMFS_ERR_INVALID; }
+  if (cuda_failed(cudaFuncSetAttribute(far32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_f), "attr"))
+    return LMFS_ERR_CUDA;
+  int per_sm = 0;
+  if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far32_kernel<2>, F_THREADS, shm_f), "occupancy"))
+    return LMFS_ERR_CUDA;
+  int kchunk = 1;
+  const long long split = wave_split(bx, (long long)std::max(1, per_sm) * dev_sms, nd, F_TILE, 16, &kchunk);
   float2* tgt = nullptr; float4* tdsk = nullptr; float4* dsk = nullptr; float4* rec = nullptr;
   int* excl_off = nullptr; int* err = nullptr; double* part = nullptr;
   auto A = [&](void** p, size_t b) { return cudaMallocAsync(p, b, st); };
