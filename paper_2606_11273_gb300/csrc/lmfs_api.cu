@@ -49,14 +49,17 @@ int check_launch(const char* what) {
 static void free_ctx(Ctx& c) {
   gmres_free(c);
   dfree(c.centres); dfree(c.radii); dfree(c.cls); dfree(c.cls_r); dfree(c.pairs); dfree(c.csr_off);
-  dfree(c.csr_ent); dfree(c.near_off); dfree(c.near_ent); dfree(c.far_excl_off); dfree(c.far_excl);
+  dfree(c.csr_ent);
+  for (NearSet& z : c.nz) {
+    dfree(z.off); dfree(z.ent); dfree(z.tgt); dfree(z.excl_off); dfree(z.excl); dfree(z.part);
+  }
   dfree(c.tgt32); dfree(c.dsk32);
   for (auto& pb : c.prob) {
     dfree(pb.A); dfree(pb.E); dfree(pb.ob.W); dfree(pb.ob.R); dfree(pb.ob.perm); dfree(pb.ob.rank); dfree(pb.ob.V);
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
-  dfree(c.ufar_part); dfree(c.near_part); dfree(c.near_tgt); dfree(c.ring); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
+  dfree(c.ufar_part); dfree(c.ring); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
   if (c.own_stream && c.stream) { cudaStreamDestroy(c.stream); c.stream = nullptr; c.own_stream = false; }
 }
 
@@ -358,7 +361,7 @@ int lmfs_stats(lmfs_handle h, int problem, double* out) {
   const PairBlocks& pb = h->c.prob[problem];
   out[0] = pb.t_ms; out[1] = pb.qr_ms; out[2] = pb.qr_flops;
   out[3] = pb.min_rank_F; out[4] = pb.max_rank_F; out[5] = h->c.C;
-  out[6] = h->c.far_split; out[7] = (double)h->c.near_h.size();
+  out[6] = h->c.far_split; out[7] = (double)h->c.nz[0].h.size();
   return LMFS_OK;
 }
 

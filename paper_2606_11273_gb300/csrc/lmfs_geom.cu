@@ -108,12 +108,16 @@ int detect_contacts(Ctx& c) {
       for (auto& e : per[i]) if (e.k == k) { e.kind = 1; e.pair = q; e.side = 1; }
       for (auto& e : per[k]) if (e.k == i) { e.kind = 1; e.pair = q; e.side = 0; }
     }
-    c.near_off_h.assign(P + 1, 0);
-    c.near_h.clear();
+    // zone 0: all of them; zone 1: self and close partners only
+    for (NearSet& z : c.nz) { z.off_h.assign(P + 1, 0); z.h.clear(); }
     for (int i = 0; i < P; ++i) {
       std::sort(per[i].begin(), per[i].end(), [](const NearEntry& a, const NearEntry& b) { return a.k < b.k; });
-      for (auto& e : per[i]) c.near_h.push_back(e);
-      c.near_off_h[i + 1] = (int)c.near_h.size();
+      for (auto& e : per[i]) {
+        c.nz[0].h.push_back(e);
+        if (e.kind != 0) c.nz[1].h.push_back(e);
+      }
+      c.nz[0].off_h[i + 1] = (int)c.nz[0].h.size();
+      c.nz[1].off_h[i + 1] = (int)c.nz[1].h.size();
     }
   }
 done:
@@ -127,18 +131,32 @@ int upload_geometry(Ctx& c) {
   LMFS_TRY(dalloc(&c.pairs, 2 * (size_t)std::max(c.C, 1)));
   LMFS_TRY(dalloc(&c.csr_off, P + 1));
   LMFS_TRY(dalloc(&c.csr_ent, 2 * (size_t)std::max(c.C, 1)));
-  LMFS_TRY(dalloc(&c.near_off, P + 1));
-  LMFS_TRY(dalloc(&c.near_ent, c.near_h.size()));
-  LMFS_TRY(dalloc(&c.near_tgt, c.near_h.size()));
-  LMFS_TRY(dalloc(&c.far_excl_off, P + 1));
-  LMFS_TRY(dalloc(&c.far_excl, c.near_h.size()));
   LMFS_TRY(dalloc(&c.tgt32, (size_t)P * Mc));
   LMFS_TRY(dalloc(&c.dsk32, (size_t)P * 2));
-  std::vector<int4> ne(c.near_h.size());
-  std::vector<int> fx(c.near_h.size());
-  for (size_t e = 0; e < c.near_h.size(); ++e) {
-    ne[e] = make_int4(c.near_h[e].k, c.near_h[e].kind, c.near_h[e].pair, c.near_h[e].side);
-    fx[e] = c.near_h[e].k;
+  cudaStream_t s = c.stream;
+  for (NearSet& z : c.nz) {
+    const size_t ne_n = std::max<size_t>(1, z.h.size());
+    LMFS_TRY(dalloc(&z.off, P + 1));
+    LMFS_TRY(dalloc(&z.ent, ne_n));
+    LMFS_TRY(dalloc(&z.tgt, ne_n));
+    LMFS_TRY(dalloc(&z.excl_off, P + 1));
+    LMFS_TRY(dalloc(&z.excl, ne_n));
+    std::vector<int4> ne(z.h.size());
+    std::vector<int> fx(z.h.size()), tg(z.h.size());
+    for (size_t e = 0; e < z.h.size(); ++e) {
+      ne[e] = make_int4(z.h[e].k, z.h[e].kind, z.h[e].pair, z.h[e].side);
+      fx[e] = z.h[e].k;
+    }
+    for (int i = 0; i < P; ++i)
+      for (int e = z.off_h[i]; e < z.off_h[i + 1]; ++e) tg[e] = i;
+    LMFS_CUDA(cudaMemcpyAsync(z.off, z.off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    LMFS_CUDA(cudaMemcpyAsync(z.excl_off, z.off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (!z.h.empty()) {
+      LMFS_CUDA(cudaMemcpyAsync(z.ent, ne.data(), ne.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+      LMFS_CUDA(cudaMemcpyAsync(z.tgt, tg.data(), tg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      LMFS_CUDA(cudaMemcpyAsync(z.excl, fx.data(), fx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    // pageable host vectors: each copy has taken its data when the call returns
   }
   std::vector<float2> t(P * (size_t)Mc);
   std::vector<float4> dk(2 * (size_t)P);
@@ -152,20 +170,11 @@ int upload_geometry(Ctx& c) {
     dk[2 * i] = make_float4(hx, hy, (float)(cx - (double)hx), (float)(cy - (double)hy));
     dk[2 * i + 1] = make_float4(0.f, 0.f, (float)c.radii_h[i], 0.f);
   }
-  cudaStream_t s = c.stream;
   if (c.C) {
     LMFS_CUDA(cudaMemcpyAsync(c.pairs, c.pairs_h.data(), 2 * (size_t)c.C * sizeof(int), cudaMemcpyHostToDevice, s));
     LMFS_CUDA(cudaMemcpyAsync(c.csr_ent, c.csr_ent_h.data(), 2 * (size_t)c.C * sizeof(int), cudaMemcpyHostToDevice, s));
   }
   LMFS_CUDA(cudaMemcpyAsync(c.csr_off, c.csr_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  LMFS_CUDA(cudaMemcpyAsync(c.near_off, c.near_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  LMFS_CUDA(cudaMemcpyAsync(c.near_ent, ne.data(), ne.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-  std::vector<int> tg(c.near_h.size());
-  for (int i = 0; i < P; ++i)
-    for (int e = c.near_off_h[i]; e < c.near_off_h[i + 1]; ++e) tg[e] = i;
-  LMFS_CUDA(cudaMemcpyAsync(c.near_tgt, tg.data(), tg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  LMFS_CUDA(cudaMemcpyAsync(c.far_excl_off, c.near_off_h.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  LMFS_CUDA(cudaMemcpyAsync(c.far_excl, fx.data(), fx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaMemcpyAsync(c.tgt32, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaMemcpyAsync(c.dsk32, dk.data(), dk.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
   LMFS_CUDA(cudaStreamSynchronize(s));

@@ -73,6 +73,20 @@ struct NearEntry {
   int side;    // side of disk k in that pair (0: first, 1: second)
 };
 
+// One near-interaction list with its device copies: per target disk the
+// source disks handled by the FP64 near kernel (and skipped by the far field),
+// the per-entry partial sums, and the far kernels' exclusion lists.
+struct NearSet {
+  std::vector<int> off_h;            // [P+1]
+  std::vector<NearEntry> h;
+  int* off = nullptr;                // [P+1]
+  int4* ent = nullptr;               // (k, kind, pair, side)
+  int* tgt = nullptr;                // target disk of each entry
+  int* excl_off = nullptr;           // [P+1] sorted source disks the far kernel skips
+  int* excl = nullptr;
+  double* part = nullptr;            // [entries][Mc][2] near-field sums per entry
+};
+
 struct Ctx {
   lmfs_params prm{};
   Dims d;
@@ -86,8 +100,6 @@ struct Ctx {
   std::vector<int> pairs_h;          // [C][2]
   std::vector<int> csr_off_h;        // [P+1] incident pairs per disk
   std::vector<int> csr_ent_h;        // [2C]  pair*2 + side
-  std::vector<int> near_off_h;       // [P+1]
-  std::vector<NearEntry> near_h;
   std::vector<int> cls_h;            // radius class per disk
   std::vector<double> cls_r_h;       // radius of each class
 
@@ -99,12 +111,14 @@ struct Ctx {
   int* pairs = nullptr;
   int* csr_off = nullptr;
   int* csr_ent = nullptr;
-  int* near_off = nullptr;
-  int4* near_ent = nullptr;          // (k, kind, pair, side)
-  int* far_excl_off = nullptr;       // [P+1] sorted source disks the far kernel skips
-  int* far_excl = nullptr;
   float2* tgt32 = nullptr;           // [P][Mc] node offsets x - c (FP32)
   float4* dsk32 = nullptr;           // [P][2] (c_hi, c_lo), (sum sigma, 0, 0)
+
+  // near zones: [0] every disk within the near gap (FP64 and direct FP32 far
+  // fields), [1] only the disk itself and its close partners (FP32 multipole
+  // far field, whose expansion is accurate to FP32 level from the close-pair
+  // gap on)
+  NearSet nz[2];
 
   PairBlocks prob[2];
 
@@ -124,8 +138,6 @@ struct Ctx {
   double* ufar_part = nullptr;       // [far_split][P][Mc][2]
   int sms = 152;                     // multiprocessors of the handle's device
   double2* ring = nullptr;           // [Nc] (cos, sin)(2 pi j / Nc) of the source rings
-  int* near_tgt = nullptr;           // target disk of each near entry
-  double* near_part = nullptr;       // [near entries][Mc][2] near-field sums per entry
   int* far_err = nullptr;            // set by the far kernel if a bounded wait expired
   double2* coef64 = nullptr;         // [P][64] multipole coefficients (FP64)
   float2* coef32 = nullptr;          // [P][64] the same rounded to FP32
@@ -216,7 +228,7 @@ inline int wave_split(long long bx, long long slots, int nd, int tile, int max_s
   return best_split;
 }
 int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar,
-               double* u, int problem);
+               double* u, int problem, int precision);
 int stokeslet_sum_standalone(const double* targets, int nt, const double* centres,
                              const double* offsets, const double* strengths, int nd, int npd,
                              double mu, int precision, cudaStream_t s, double* out);

@@ -1295,7 +1295,7 @@ int far_field_prepare(Ctx& c) {
     LMFS_CUDA(cudaMemcpyAsync(c.ring, ring.data(), ring.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
     LMFS_CUDA(cudaStreamSynchronize(c.stream));
   }
-  LMFS_TRY(dalloc(&c.near_part, std::max<size_t>(1, c.near_h.size()) * c.d.Mc * 2));
+  for (NearSet& z : c.nz) LMFS_TRY(dalloc(&z.part, std::max<size_t>(1, z.h.size()) * c.d.Mc * 2));
   return LMFS_OK;
 }
 
@@ -1309,8 +1309,13 @@ int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
   return check_launch("onebody_apply");
 }
 
+// The near zone that goes with a far-field precision: the FP32 multipole far
+// field takes every disk pair but the disk itself and its close partners.
+static const NearSet& zone(const Ctx& c, int precision) { return c.nz[precision == LMFS_MIXED ? 1 : 0]; }
+
 int far_field(Ctx& c, const double* strength, double* out, int precision, bool skip_base) {
   const int P = c.d.P, Mc = c.d.Mc, Nc = c.d.Nc;
+  const NearSet& z = zone(c, precision);
   const long long n = (long long)P * Mc * 2;
   const double cmu = INV4PI / c.prm.mu;
   int split = 1;
@@ -1320,8 +1325,8 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
     records_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.src4, c.dsk32);
     LMFS_TRY(check_launch("records"));
     FarArgs a;
-    a.tgt = c.tgt32; a.tdsk = c.dsk32; a.dsk = c.dsk32; a.rec = c.src4; a.excl_off = c.far_excl_off;
-    a.excl = c.far_excl; a.ntd = P; a.Mt = Mc; a.nsd = P; a.Nc = Nc; a.kchunk = kchunk; a.cmu = cmu;
+    a.tgt = c.tgt32; a.tdsk = c.dsk32; a.dsk = c.dsk32; a.rec = c.src4; a.excl_off = z.excl_off;
+    a.excl = z.excl; a.ntd = P; a.Mt = Mc; a.nsd = P; a.Nc = Nc; a.kchunk = kchunk; a.cmu = cmu;
     a.out = split > 1 ? c.ufar_part : out; a.out_stride = n; a.with_base = skip_base ? 0 : 1; a.err = c.far_err;
     a.range_err = c.far_err + 1;
     const int threads_needed = (P * Mc + 1) / 2;
@@ -1338,7 +1343,7 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
     MpArgs a;
     a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc;
     a.coef = fp32 ? (const void*)c.coef32 : (const void*)c.coef64;
-    a.excl_off = c.far_excl_off; a.excl = c.far_excl; a.P = P; a.Mc = Mc; a.kchunk = kchunk; a.cmu = cmu;
+    a.excl_off = z.excl_off; a.excl = z.excl; a.P = P; a.Mc = Mc; a.kchunk = kchunk; a.cmu = cmu;
     a.out = split > 1 ? c.ufar_part : out; a.out_stride = n; a.with_log = skip_base ? 0 : 1; a.err = c.far_err;
     if (fp32) {
       const size_t shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(float2) + 2 * M_TILE * 32 + 16;
@@ -1359,21 +1364,22 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
 }
 
 int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar, double* u,
-               int problem) {
+               int problem, int precision) {
+  const NearSet& z = zone(c, precision);
   // target nodes x source groups, about nine warps per block
   const int Mc = c.d.Mc;
   const int G = std::max(1, std::min({4, 1024 / Mc, c.d.Nc}));
   const int threads = ((G * Mc + 31) / 32) * 32;
   const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mc * 2) * sizeof(double);
-  const int ne = (int)c.near_h.size();
+  const int ne = (int)z.h.size();
   if (ne > 0) {
-    near_kernel<<<ne, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, c.near_tgt,
-                                                c.near_ent, strength, c.lam, c.lb, c.tilde,
-                                                problem == LMFS_MOBILITY, c.near_part);
+    near_kernel<<<ne, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, z.tgt,
+                                                z.ent, strength, c.lam, c.lb, c.tilde,
+                                                problem == LMFS_MOBILITY, z.part);
     LMFS_TRY(check_launch("near"));
   }
   const int n = c.d.P * Mc;
-  near_reduce<<<(n + 127) / 128, 128, 0, c.stream>>>(mode, c.near_off, c.near_ent, c.near_part, c.d.P, Mc, mu, ufar,
+  near_reduce<<<(n + 127) / 128, 128, 0, c.stream>>>(mode, z.off, z.ent, z.part, c.d.P, Mc, mu, ufar,
                                                      INV4PI / c.prm.mu, u);
   return check_launch("near_reduce");
 }
@@ -1394,7 +1400,7 @@ int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precisio
                                                            c.Rc, problem == LMFS_MOBILITY, c.lam, c.sig);
   LMFS_TRY(check_launch("gather"));
   LMFS_TRY(far_field(c, c.sig, c.ufar, precision, problem == LMFS_MOBILITY));   // Step 2a (far)
-  return near_field(c, 0, c.sig, mu, c.ufar, u, problem);                       // near + identity
+  return near_field(c, 0, c.sig, mu, c.ufar, u, problem, precision);            // near + identity
 }
 
 int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision) {
@@ -1406,7 +1412,7 @@ int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision)
   lam0_kernel<<<(P * c.d.Nc + 127) / 128, 128, 0, c.stream>>>(in3, c.radii, c.Rc, P, c.d.Nc, c.lam0);
   LMFS_TRY(check_launch("lam0"));
   LMFS_TRY(far_field(c, c.lam0, c.ufar, precision, false));
-  return near_field(c, 1, c.lam0, nullptr, c.ufar, b, problem);
+  return near_field(c, 1, c.lam0, nullptr, c.ufar, b, problem, precision);
 }
 
 int post_device(Ctx& c, int problem, const double* mu, double* out3) {
