@@ -10,30 +10,62 @@
 namespace lmfs {
 namespace {
 
-// Pass 1 (counts) and pass 2 (writes) share this kernel.  Thread i scans
-// k > i in increasing order, so the output is sorted by (i, k).
+// Uniform grid of square cells of side h >= 2 max radius + the largest gap
+// looked for, so that every such pair lies in the same or adjacent cells:
+// cell_start [ncell + 1] and cell_disk (disks sorted by cell) on the device.
+struct CellGrid {
+  const int* cell_start;
+  const int* cell_disk;
+  double x0, y0, h;
+  int nx, ny;
+};
+
+// Pass 1 (counts) and pass 2 (writes) share this kernel.  Thread i tests the
+// disks k > i of its own and the eight adjacent cells; in pass 2 it then
+// sorts its two output segments by k, so the lists come out sorted by (i, k)
+// whatever the cell order.
 //   close: gap <= delta_c;   near: gap < g_near;   overlap: gap <= 0.
-__global__ void contacts_kernel(const double* __restrict__ c, const double* __restrict__ r, int P,
+__global__ void contacts_kernel(const double* __restrict__ c, const double* __restrict__ r, int P, CellGrid grid,
                                 double delta_c, double g_near, int* cnt_close, int* cnt_near,
                                 int* n_overlap, const int* off_close, const int* off_near,
                                 int* out_close, int* out_near) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   const double xi = c[2 * i], yi = c[2 * i + 1], ri = r[i];
+  const int cx = min(grid.nx - 1, max(0, (int)floor((xi - grid.x0) / grid.h)));
+  const int cy = min(grid.ny - 1, max(0, (int)floor((yi - grid.y0) / grid.h)));
   int nc = 0, nn = 0, no = 0;
-  for (int k = i + 1; k < P; ++k) {
-    const double dx = c[2 * k] - xi, dy = c[2 * k + 1] - yi;
-    const double gap = sqrt(dx * dx + dy * dy) - ri - r[k];
-    if (gap <= 0.0) ++no;
-    if (gap <= delta_c) {
-      if (out_close) { out_close[2 * (off_close[i] + nc)] = i; out_close[2 * (off_close[i] + nc) + 1] = k; }
-      ++nc;
-    }
-    if (gap < g_near) {
-      if (out_near) { out_near[2 * (off_near[i] + nn)] = i; out_near[2 * (off_near[i] + nn) + 1] = k; }
-      ++nn;
+  for (int gy = max(0, cy - 1); gy <= min(grid.ny - 1, cy + 1); ++gy) {
+    for (int gx = max(0, cx - 1); gx <= min(grid.nx - 1, cx + 1); ++gx) {
+      const int cell = gy * grid.nx + gx;
+      for (int q = grid.cell_start[cell]; q < grid.cell_start[cell + 1]; ++q) {
+        const int k = grid.cell_disk[q];
+        if (k <= i) continue;
+        const double dx = c[2 * k] - xi, dy = c[2 * k + 1] - yi;
+        const double gap = sqrt(dx * dx + dy * dy) - ri - r[k];
+        if (gap <= 0.0) ++no;
+        if (gap <= delta_c) {
+          if (out_close) { out_close[2 * (off_close[i] + nc)] = i; out_close[2 * (off_close[i] + nc) + 1] = k; }
+          ++nc;
+        }
+        if (gap < g_near) {
+          if (out_near) { out_near[2 * (off_near[i] + nn)] = i; out_near[2 * (off_near[i] + nn) + 1] = k; }
+          ++nn;
+        }
+      }
     }
   }
+  // insertion sort of this disk's segments by partner index (a handful each)
+  auto sort_seg = [](int* seg, int len) {
+    for (int a = 1; a < len; ++a) {
+      const int key = seg[2 * a + 1];
+      int b = a - 1;
+      while (b >= 0 && seg[2 * b + 1] > key) { seg[2 * (b + 1) + 1] = seg[2 * b + 1]; --b; }
+      seg[2 * (b + 1) + 1] = key;
+    }
+  };
+  if (out_close) sort_seg(out_close + 2 * off_close[i], nc);
+  if (out_near) sort_seg(out_near + 2 * off_near[i], nn);
   if (cnt_close) { cnt_close[i] = nc; cnt_near[i] = nn; }
   if (no && n_overlap) atomicAdd(n_overlap, no);
 }
@@ -49,16 +81,56 @@ int detect_contacts(Ctx& c) {
   const double rmin = *std::min_element(c.radii_h.begin(), c.radii_h.end());
   const double g_near = std::max({c.prm.delta_c, 1.5, 4.0 * c.Rc * rmax - rmin + 0.01});
   int *cc = nullptr, *cn = nullptr, *nov = nullptr, *oc = nullptr, *on = nullptr;
-  int *pc = nullptr, *pn = nullptr;
+  int *pc = nullptr, *pn = nullptr, *gcs = nullptr, *gcd = nullptr;
   int rc = LMFS_OK;
+  // cell grid, binned on the host (a counting sort, O(P)); cells no smaller
+  // than 2 max radius + the larger of the two gaps, and at most about 4P of them
+  CellGrid grid{};
+  std::vector<int> cstart, cdisk;
+  {
+    double x0 = c.centres_h[0], x1 = x0, y0 = c.centres_h[1], y1 = y0;
+    for (int i = 1; i < P; ++i) {
+      x0 = std::min(x0, c.centres_h[2 * i]); x1 = std::max(x1, c.centres_h[2 * i]);
+      y0 = std::min(y0, c.centres_h[2 * i + 1]); y1 = std::max(y1, c.centres_h[2 * i + 1]);
+    }
+    double h = 2.0 * rmax + std::max(c.prm.delta_c, g_near);
+    h *= 1.0 + 1e-12;
+    auto cells = [&](double hh) {
+      return (std::floor((x1 - x0) / hh) + 1.0) * (std::floor((y1 - y0) / hh) + 1.0);
+    };
+    while (cells(h) > 4.0 * P + 16.0) h *= 1.25;
+    grid.x0 = x0; grid.y0 = y0; grid.h = h;
+    grid.nx = (int)std::floor((x1 - x0) / h) + 1;
+    grid.ny = (int)std::floor((y1 - y0) / h) + 1;
+    const int ncell = grid.nx * grid.ny;
+    std::vector<int> cell_of(P);
+    cstart.assign(ncell + 1, 0);
+    for (int i = 0; i < P; ++i) {
+      const int gx = std::min(grid.nx - 1, std::max(0, (int)std::floor((c.centres_h[2 * i] - x0) / h)));
+      const int gy = std::min(grid.ny - 1, std::max(0, (int)std::floor((c.centres_h[2 * i + 1] - y0) / h)));
+      cell_of[i] = gy * grid.nx + gx;
+      ++cstart[cell_of[i] + 1];
+    }
+    for (int q = 0; q < ncell; ++q) cstart[q + 1] += cstart[q];
+    cdisk.assign(P, 0);
+    std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+    for (int i = 0; i < P; ++i) cdisk[fill[cell_of[i]]++] = i;
+  }
   std::vector<int> hcc(P), hcn(P), hoc(P + 1, 0), hon(P + 1, 0);
   int hov = 0;
   const int thr = 128, blk = (P + thr - 1) / thr;
   if ((rc = dalloc(&cc, P)) || (rc = dalloc(&cn, P)) || (rc = dalloc(&nov, 1)) ||
-      (rc = dalloc(&oc, P + 1)) || (rc = dalloc(&on, P + 1)))
+      (rc = dalloc(&oc, P + 1)) || (rc = dalloc(&on, P + 1)) || (rc = dalloc(&gcs, cstart.size())) ||
+      (rc = dalloc(&gcd, cdisk.size())))
     goto done;
+  if (cuda_failed(cudaMemcpyAsync(gcs, cstart.data(), cstart.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+      cuda_failed(cudaMemcpyAsync(gcd, cdisk.data(), cdisk.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d")) {
+    rc = LMFS_ERR_CUDA; goto done;
+  }
+  grid.cell_start = gcs;
+  grid.cell_disk = gcd;
   if (cuda_failed(cudaMemsetAsync(nov, 0, sizeof(int), c.stream), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
-  contacts_kernel<<<blk, thr, 0, c.stream>>>(c.centres, c.radii, P, c.prm.delta_c, g_near, cc, cn,
+  contacts_kernel<<<blk, thr, 0, c.stream>>>(c.centres, c.radii, P, grid, c.prm.delta_c, g_near, cc, cn,
                                              nov, nullptr, nullptr, nullptr, nullptr);
   if ((rc = check_launch("contacts count"))) goto done;
   if (cuda_failed(cudaMemcpyAsync(hcc.data(), cc, P * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
@@ -75,7 +147,7 @@ int detect_contacts(Ctx& c) {
         cuda_failed(cudaMemcpyAsync(on, hon.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d")) {
       rc = LMFS_ERR_CUDA; goto done;
     }
-    contacts_kernel<<<blk, thr, 0, c.stream>>>(c.centres, c.radii, P, c.prm.delta_c, g_near, nullptr,
+    contacts_kernel<<<blk, thr, 0, c.stream>>>(c.centres, c.radii, P, grid, c.prm.delta_c, g_near, nullptr,
                                                nullptr, nullptr, oc, on, pc, pn);
     if ((rc = check_launch("contacts write"))) goto done;
     std::vector<int> hnear(2 * (size_t)nnear);
@@ -121,7 +193,7 @@ int detect_contacts(Ctx& c) {
     }
   }
 done:
-  dfree(cc); dfree(cn); dfree(nov); dfree(oc); dfree(on); dfree(pc); dfree(pn);
+  dfree(cc); dfree(cn); dfree(nov); dfree(oc); dfree(on); dfree(pc); dfree(pn); dfree(gcs); dfree(gcd);
   return rc;
 }
 

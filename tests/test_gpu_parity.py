@@ -305,3 +305,35 @@ def test_stokeslet_sum_standalone(L):
     with pytest.raises(L.LmfsError):
         L.stokeslet_sum(dev(bad).reshape(-1, 2), dev(centres).reshape(-1, 2), dev(off).reshape(nd, npd, 2),
                         dev(s).reshape(nd, npd, 2))
+
+
+@pytest.mark.parametrize("case", ["poly_2000", "sparse_outlier", "dense_3000"])
+def test_contacts_cell_grid_match_brute_force(L, case):
+    """The uniform-grid contact search returns exactly the brute-force pair
+    list (sorted by (i, k)), and the near zone the brute-force number of
+    directed entries, on polydisperse, sparse (one far outlier, which enlarges
+    the cells) and dense packings."""
+    from oracle.geometry import contacts
+    rng = np.random.default_rng(11)
+    if case == "poly_2000":
+        radii = rng.uniform(0.8, 1.2, 2000)
+        pk = w.packing(2000, 0.55, seed=5, radii=radii, nsweep=2, start="hex")
+        centres, radii = pk.centres, pk.radii
+    elif case == "dense_3000":
+        pk = w.packing(3000, 0.65, seed=6, nsweep=2)
+        centres, radii = pk.centres, pk.radii
+    else:
+        pk = w.packing(400, 0.4, seed=7, nsweep=2)
+        centres = np.vstack([pk.centres, [[5.0e4, -3.0e4]]])
+        radii = np.concatenate([pk.radii, [1.0]])
+    p = PACKING
+    s = L.Solver(centres, radii, gparams(L, p))
+    got = [tuple(int(v) for v in x) for x in s.pairs()]
+    assert got == contacts(centres, radii, p.delta_c)
+    # near zone: every pair with gap < g_near, both directions, plus self
+    g_near = max(p.delta_c, 1.5, 4.0 * p.Rc * radii.max() - radii.min() + 0.01)
+    d = np.hypot(centres[:, None, 0] - centres[None, :, 0], centres[:, None, 1] - centres[None, :, 1])
+    gap = d - radii[:, None] - radii[None, :]
+    np.fill_diagonal(gap, np.inf)
+    n_near = int((gap < g_near).sum()) + len(radii)
+    assert int(s.stats(L.MOBILITY)["near_entries"]) == n_near
