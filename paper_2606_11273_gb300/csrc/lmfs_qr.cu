@@ -106,7 +106,7 @@ struct Args {
 // recomputation test, so no division or square root is spent per column and
 // reflector; where the subtraction cancels, the test recomputes the norm.
 template <int T>
-__global__ void __launch_bounds__(T) qrcp_kernel(Args q) {
+__global__ void __launch_bounds__(T, 1024 / T) qrcp_kernel(Args q) {
   constexpr int NW = T / 32;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -561,11 +561,14 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   a.rank = q.rank; a.perm = q.perm; a.permstride = q.permstride; a.tau = q.tau; a.vn = q.vn;
   a.info = q.info; a.cs = 1;
   {
-    // 512-thread CTAs (two per SM); cluster size from the resident-cluster
-    // count: waves of clusters x the work each CTA carries, a small charge per
-    // member for the two cluster barriers per reflector, and at least two
-    // columns per warp
-    constexpr int T = 512;
+    // 256-thread CTAs, four per SM: the CTAs sharing an SM belong to different
+    // matrices, so while one waits on its reflector's barriers or L2 round
+    // trips the others keep the FP64 pipe busy (measured against 512-thread
+    // CTAs, two per SM: 26.0 against 27.4 ms per step).  Cluster size from
+    // the resident-cluster count: waves of clusters x the work each CTA
+    // carries, a small charge per member for the two cluster barriers per
+    // reflector, and at least two columns per warp
+    constexpr int T = 256;
     const size_t shm = (size_t)q.ld * sizeof(double) + (T / 32) * (sizeof(double) + sizeof(int));
     const int csmax = std::max(1, std::min(8, q.nmax / (2 * (T / 32))));
     double best = 1e300;
