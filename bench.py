@@ -93,8 +93,8 @@ class Clocks:
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; command
 # and figures in profiles/qrcp_kernel_p100_mobility.md).  Valid only for the
 # kernel source it was taken on: reported as null once lmfs_qr.cu changes.
-QRCP_TRAFFIC_BYTES = 23268326400 + 24799382784 + 14395136 + 2254336
-QRCP_TRAFFIC_SRC_SHA256 = "b34fd80cbe5cdcd050074b3dcef08db6c48e93d1acdc17f5d1ee738504fdbf6e"
+QRCP_TRAFFIC_BYTES = 23436956160 + 25761400320 + 14299136 + 2100224
+QRCP_TRAFFIC_SRC_SHA256 = "3ce04c663094e62340580234a338a11233c67842ce496f69c0fbeeff384884f9"
 
 
 def qrcp_traffic():
