@@ -228,9 +228,24 @@ typedef struct lmfs_server_params {
   int    max_slots;        /* resident requests at most                        */
   int    device;
   int    precision;        /* LMFS_MIXED or LMFS_FP64 for every request        */
+  int    engine;           /* LMFS_ENGINE_INTERLEAVED (0) or LMFS_ENGINE_STREAMS */
 } lmfs_server_params;
 
-/* Start a server (one worker thread driving one stream). */
+/* LMFS_ENGINE_INTERLEAVED: each admitted request is precomputed on its own
+ * thread and stream; then one engine thread advances every resident request's
+ * GMRES, one Arnoldi step at a time, and evaluates the far fields of all the
+ * requests that are ready in ONE launch over a (request, target block, source
+ * chunk) work list; a request joins the next launch as soon as its previous
+ * step is done, and leaves when it converges.
+ * LMFS_ENGINE_STREAMS: every request runs its whole solve on its own thread and
+ * stream (the requests' kernels overlap, each launch serves one request).
+ * Either way a request's result does not depend on the others: the same
+ * kernels compute the same values in the same order. */
+#define LMFS_ENGINE_INTERLEAVED 0
+#define LMFS_ENGINE_STREAMS 1
+
+/* Start a server: a dispatcher thread that admits queued requests, a thread per
+ * admitted request, and (interleaved engine) the engine thread. */
 int lmfs_server_create(const lmfs_server_params* sp, lmfs_server** out);
 /* Queue a request (copies all inputs, never blocks).  LMFS_ERR_TOO_LARGE if
  * the request alone exceeds the budget; LMFS_ERR_INVALID on bad input. */

@@ -163,9 +163,11 @@ def stokeslet_sum(targets, centres, offsets, strengths, mu=1.0, precision=MIXED_
 class Server:
     """Continuous-batching request server (lmfs_server_*)."""
 
-    def __init__(self, hbm_budget_bytes, max_slots=8, precision=MIXED, device=0):
+    def __init__(self, hbm_budget_bytes, max_slots=8, precision=MIXED, device=0, engine=0):
+        """engine: 0 = interleaved (one far-field launch for all ready
+        requests per Arnoldi step), 1 = one stream per request."""
         self.lib = _lib.load()
-        sp = _lib.lmfs_server_params(hbm_budget_bytes, max_slots, device, precision)
+        sp = _lib.lmfs_server_params(hbm_budget_bytes, max_slots, device, precision, engine)
         self.s = ctypes.c_void_p()
         _lib.check(self.lib.lmfs_server_create(ctypes.byref(sp), ctypes.byref(self.s)))
 

@@ -48,7 +48,7 @@ class lmfs_solve_info(ctypes.Structure):
 
 class lmfs_server_params(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
-                ("device", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("device", ctypes.c_int), ("precision", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class LmfsError(RuntimeError):

@@ -16,10 +16,6 @@
 
 #include "lmfs_internal.h"
 
-struct lmfs_ctx {
-  lmfs::Ctx c;
-};
-
 namespace lmfs {
 
 static thread_local std::string g_last_error;
@@ -172,6 +168,52 @@ static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev,
     info->n_pairs = c.C;
   }
   return rc;
+}
+
+// The solve in phases for the server's interleaved engine: the same steps as
+// lmfs_solve in the same order, with GMRES driven from outside one Arnoldi
+// step at a time (gmres_step_pre, the far field, gmres_step_post).
+int solve_begin(lmfs_handle h, int problem, const double* in, double* beta) {
+  if (!h || !in || !beta || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
+  Ctx& c = h->c;
+  LMFS_CUDA(cudaSetDevice(c.device));
+  for (int i = 0; i < 3 * c.d.P; ++i)
+    if (!std::isfinite(in[i])) { set_last_error("non-finite input"); return LMFS_ERR_INVALID; }
+  LMFS_CUDA(cudaMemcpyAsync(c.io3, in, 3 * (size_t)c.d.P * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  c.t_begin = std::chrono::steady_clock::now();
+  c.had_precompute = c.prob[problem].ready;
+  LMFS_TRY(ensure_precompute(c, problem));
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  c.t_pre = std::chrono::steady_clock::now();
+  LMFS_TRY(rhs_device(c, problem, c.io3, c.bvec, c.prm.precision));
+  return gmres_begin(c, problem, c.prm.precision, c.bvec, beta);
+}
+
+int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info) {
+  Ctx& c = h->c;
+  LMFS_CUDA(cudaSetDevice(c.device));
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  if (iters > 0) LMFS_TRY(gmres_finish(c, iters, c.xsol));
+  else LMFS_CUDA(cudaMemsetAsync(c.xsol, 0, n * sizeof(double), c.stream));
+  double* outd = nullptr;
+  LMFS_TRY(dalloc(&outd, 3 * (size_t)c.d.P));
+  int rc = post_device(c, problem, c.xsol, outd);
+  if (rc == LMFS_OK &&
+      (cuda_failed(cudaMemcpyAsync(out, outd, 3 * (size_t)c.d.P * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
+       cuda_failed(cudaStreamSynchronize(c.stream), "sync")))
+    rc = LMFS_ERR_CUDA;
+  dfree(outd);
+  if (rc != LMFS_OK) return rc;
+  c.have_solution = true;
+  const auto t2 = std::chrono::steady_clock::now();
+  if (info) {
+    info->iters = iters;
+    info->relres = relres;
+    info->t_precompute_ms = c.had_precompute ? 0.0 : std::chrono::duration<double, std::milli>(c.t_pre - c.t_begin).count();
+    info->t_solve_ms = std::chrono::duration<double, std::milli>(t2 - c.t_pre).count();
+    info->n_pairs = c.C;
+  }
+  return relres <= c.prm.tol ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
 }
 
 }  // namespace lmfs

@@ -174,7 +174,11 @@ __global__ void combine_x(const double* V, long long n, const double* y, int k, 
 void gmres_free(Ctx& c) {
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 3; ++b)
+    {
       if (c.graph_exec[a][b]) { cudaGraphExecDestroy(c.graph_exec[a][b]); c.graph_exec[a][b] = nullptr; }
+      if (c.step_pre[a][b]) { cudaGraphExecDestroy(c.step_pre[a][b]); c.step_pre[a][b] = nullptr; }
+      if (c.step_post[a][b]) { cudaGraphExecDestroy(c.step_post[a][b]); c.step_post[a][b] = nullptr; }
+    }
   dfree(c.V); dfree(c.w); dfree(c.H); dfree(c.gvec); dfree(c.cs); dfree(c.sn); dfree(c.hpart);
   dfree(c.scal); dfree(c.jdev);
   if (c.host_pinned) { cudaFreeHost(c.host_pinned); c.host_pinned = nullptr; }
@@ -200,16 +204,23 @@ static int gmres_alloc(Ctx& c, int cap) {
   return LMFS_OK;
 }
 
-// One Arnoldi step on the handle's stream (graph-capturable: no host sync).
-static int arnoldi_step(Ctx& c, int problem, int precision) {
+// One Arnoldi step on the handle's stream (graph-capturable: no host sync),
+// in two parts around the far field's evaluation.
+static int arnoldi_pre(Ctx& c, int problem, int precision) {
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
+  copy_vj<<<eb, 256, 0, c.stream>>>(c.V, n, c.jdev, c.bvec);
+  LMFS_TRY(check_launch("copy_vj"));
+  return matvec_pre(c, problem, c.bvec, precision);
+}
+
+static int arnoldi_post(Ctx& c, int problem, int precision) {
   const long long n = 2LL * c.d.P * c.d.Mc;
   const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
   const int cap = c.gm_cap;
   double* hcoef = c.hpart + (long long)(cap + 1) * nblk;
   const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
-  copy_vj<<<eb, 256, 0, c.stream>>>(c.V, n, c.jdev, c.bvec);
-  LMFS_TRY(check_launch("copy_vj"));
-  LMFS_TRY(matvec_device(c, problem, c.bvec, c.w, precision));
+  LMFS_TRY(matvec_post(c, problem, c.bvec, c.w, precision));
   for (int pass = 0; pass < 2; ++pass) {
     dots_kernel<<<dim3(nblk, cap), RB, 0, c.stream>>>(c.V, n, c.w, c.jdev, cap, c.hpart, nblk);
     dots_reduce<<<(cap + 127) / 128, 128, 0, c.stream>>>(c.hpart, nblk, c.jdev, cap, hcoef, c.H, pass);
@@ -222,9 +233,32 @@ static int arnoldi_step(Ctx& c, int problem, int precision) {
   return check_launch("arnoldi");
 }
 
-int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, lmfs_solve_info* info) {
-  const int maxit = std::max(1, c.prm.maxit);
-  LMFS_TRY(gmres_alloc(c, maxit));
+static int arnoldi_step(Ctx& c, int problem, int precision) {
+  LMFS_TRY(arnoldi_pre(c, problem, precision));
+  LMFS_TRY(matvec_far(c, problem, precision));
+  return arnoldi_post(c, problem, precision);
+}
+
+// Capture `fn` on the handle's stream into an executable graph.
+template <class F>
+static int capture(Ctx& c, F fn, cudaGraphExec_t* ge, size_t* nodes) {
+  cudaGraph_t g;
+  LMFS_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = fn();
+  cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+  if (rc != LMFS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return rc; }
+  LMFS_CUDA(e);
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  if (nodes) *nodes += nn;
+  const cudaError_t ei = cudaGraphInstantiate(ge, g, 0);
+  cudaGraphDestroy(g);
+  LMFS_CUDA(ei);
+  return LMFS_OK;
+}
+
+// First basis vector: v_0 = b / |b|; returns |b| (host synchronisation).
+static int gmres_init(Ctx& c, const double* b, double* beta) {
   const long long n = 2LL * c.d.P * c.d.Mc;
   const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
   const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
@@ -235,23 +269,61 @@ int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, 
   LMFS_TRY(check_launch("gmres init"));
   LMFS_CUDA(cudaMemcpyAsync(c.host_pinned, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
-  const double beta = c.host_pinned[0];
+  *beta = c.host_pinned[0];
+  return LMFS_OK;
+}
+
+int gmres_finish(Ctx& c, int iters, double* x) {
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
+  double* y = c.hpart;  // reuse
+  solve_y<<<1, 32, 0, c.stream>>>(c.H, c.gm_cap, c.gvec, iters, y);
+  combine_x<<<eb, 256, 0, c.stream>>>(c.V, n, y, iters, x);
+  note_launches(1);
+  return check_launch("gmres finish");
+}
+
+int gmres_begin(Ctx& c, int problem, int precision, const double* b, double* beta) {
+  LMFS_TRY(gmres_alloc(c, std::max(1, c.prm.maxit)));
+  LMFS_TRY(gmres_init(c, b, beta));
+  if (!c.step_pre[problem][precision]) {
+    c.step_nodes[problem][precision] = 0;
+    LMFS_TRY(capture(c, [&] { return arnoldi_pre(c, problem, precision); }, &c.step_pre[problem][precision],
+                     &c.step_nodes[problem][precision]));
+    LMFS_TRY(capture(c, [&] {
+      LMFS_TRY(arnoldi_post(c, problem, precision));
+      LMFS_CUDA(cudaMemcpyAsync(c.host_pinned + 1, c.scal + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      return LMFS_OK;
+    }, &c.step_post[problem][precision], &c.step_nodes[problem][precision]));
+    c.step_nodes[problem][precision] -= 1;   // the residual copy is not a kernel
+  }
+  return LMFS_OK;
+}
+
+int gmres_step_pre(Ctx& c, int problem, int precision) {
+  LMFS_CUDA(cudaGraphLaunch(c.step_pre[problem][precision], c.stream));
+  note_launches(c.step_nodes[problem][precision]);   // both graphs' kernels, counted once per step
+  return LMFS_OK;
+}
+
+int gmres_step_post(Ctx& c, int problem, int precision) {
+  LMFS_CUDA(cudaGraphLaunch(c.step_post[problem][precision], c.stream));
+  return LMFS_OK;
+}
+
+int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, lmfs_solve_info* info) {
+  const int maxit = std::max(1, c.prm.maxit);
+  LMFS_TRY(gmres_alloc(c, maxit));
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  double beta = 0.0;
+  LMFS_TRY(gmres_init(c, b, &beta));
   int iters = 0;
   double relres = 1.0;
   if (beta > 0.0) {
     cudaGraphExec_t& ge = c.graph_exec[problem][precision];  // precision < 3
     if (!ge) {
-      cudaGraph_t g;
-      LMFS_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
-      const int rc = arnoldi_step(c, problem, precision);
-      cudaError_t e = cudaStreamEndCapture(c.stream, &g);
-      if (rc != LMFS_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return rc; }
-      LMFS_CUDA(e);
-      size_t nn = 0;
-      cudaGraphGetNodes(g, nullptr, &nn);
-      c.graph_nodes[problem][precision] = nn;
-      LMFS_CUDA(cudaGraphInstantiate(&ge, g, 0));
-      cudaGraphDestroy(g);
+      c.graph_nodes[problem][precision] = 0;
+      LMFS_TRY(capture(c, [&] { return arnoldi_step(c, problem, precision); }, &ge, &c.graph_nodes[problem][precision]));
     }
     for (int it = 0; it < maxit; ++it) {
       LMFS_CUDA(cudaGraphLaunch(ge, c.stream));
@@ -263,11 +335,7 @@ int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, 
       if (!(relres == relres)) { set_last_error("GMRES produced a non-finite residual"); return LMFS_ERR_NUMERICAL; }
       if (relres <= c.prm.tol || c.host_pinned[3] != 0.0) break;
     }
-    double* y = c.hpart;  // reuse
-    solve_y<<<1, 32, 0, c.stream>>>(c.H, c.gm_cap, c.gvec, iters, y);
-    combine_x<<<eb, 256, 0, c.stream>>>(c.V, n, y, iters, x);
-    note_launches(1);
-    LMFS_TRY(check_launch("gmres finish"));
+    LMFS_TRY(gmres_finish(c, iters, x));
   } else {
     LMFS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), c.stream));
     relres = 0.0;

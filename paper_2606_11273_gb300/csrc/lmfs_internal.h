@@ -11,6 +11,7 @@
 //   src2 [P][Nc] float2 (sigma_x, sigma_y), disk data dsk [P] float4x2.
 #pragma once
 #include <algorithm>
+#include <chrono>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -159,7 +160,14 @@ struct Ctx {
   double* host_pinned = nullptr;     // pinned scalars
   cudaGraphExec_t graph_exec[2][3] = {};
   size_t graph_nodes[2][3] = {};
+  // the server's interleaved engine: an Arnoldi step as two graphs around the
+  // far field's evaluation (before: basis copy, Steps 1a-1b, moments; after:
+  // split sum, near field, orthogonalization, Givens, residual read-back)
+  cudaGraphExec_t step_pre[2][3] = {}, step_post[2][3] = {};
+  size_t step_nodes[2][3] = {};
   bool have_solution = false;
+  bool had_precompute = false;                                   // solve_begin / solve_finish
+  std::chrono::steady_clock::time_point t_begin, t_pre;
 };
 
 // ---- geometry (lmfs_geom.cu) ----------------------------------------------
@@ -202,6 +210,23 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t s, bool solve);
 // ---- matvec pieces (lmfs_matvec.cu) ---------------------------------------
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb);
 int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision);
+// matvec_device = matvec_pre + matvec_far + matvec_post
+int matvec_pre(Ctx& c, int problem, const double* mu, int precision);
+int matvec_far(Ctx& c, int problem, int precision);
+int matvec_post(Ctx& c, int problem, const double* mu, double* u, int precision);
+
+// Device buffers of the multi-handle far-field launch (argument records and
+// work items), grown on demand and owned by the caller.
+struct MultiFar {
+  void* args = nullptr;
+  size_t args_cap = 0;
+  int4* items = nullptr;
+  size_t items_cap = 0;
+};
+// matvec_far of n handles (LMFS_MIXED or LMFS_FP64) in one launch on `st`;
+// each handle's matvec_pre must be complete (the caller orders the streams).
+int far_multi_launch(Ctx* const* cs, const int* problems, int n, int precision, cudaStream_t st, MultiFar& buf);
+void multi_far_free(MultiFar& buf);
 int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision);
 int post_device(Ctx& c, int problem, const double* mu, double* out3);
 int far_field(Ctx& c, const double* strength, double* out, int precision, bool mobility_sums_zero);
@@ -239,6 +264,17 @@ int stokeslet_sum_noalloc(const double* targets, int nt, const double* centres, 
 int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x,
                 lmfs_solve_info* info);
 void gmres_free(Ctx& c);
+// gmres_solve in steps, for the server's interleaved engine (the same kernels
+// in the same order, so the same result):
+//   gmres_begin: basis, first vector, and the two step graphs; *beta = |b|;
+//   gmres_step_pre / far field (matvec_far, or far_multi_launch) /
+//   gmres_step_post: one Arnoldi step; step_post ends with an asynchronous
+//   copy of (relres, -, breakdown) to host_pinned[1..3];
+//   gmres_finish: x from the first `iters` basis vectors.
+int gmres_begin(Ctx& c, int problem, int precision, const double* b, double* beta);
+int gmres_step_pre(Ctx& c, int problem, int precision);
+int gmres_step_post(Ctx& c, int problem, int precision);
+int gmres_finish(Ctx& c, int iters, double* x);
 
 // ---- memory ---------------------------------------------------------------
 template <class T>
@@ -254,6 +290,21 @@ void dfree(T*& p) { if (p) cudaFree((void*)p); p = nullptr; }
 int check_launch(const char* what);
 void note_launches(unsigned long long n);   // launches not followed by check_launch
 
+}  // namespace lmfs
+
+struct lmfs_ctx {
+  lmfs::Ctx c;
+};
+
+namespace lmfs {
+// lmfs_solve in phases (lmfs_api.cu), for the server's interleaved engine:
+// solve_begin copies the input, precomputes, builds the right-hand side and
+// starts GMRES (*beta = |b|; 0 means x = 0); the caller then runs Arnoldi steps
+// (gmres_step_pre, far field, gmres_step_post) until convergence, breakdown or
+// maxit, and solve_finish forms x from `iters` basis vectors, post-processes,
+// and copies [P][3] to `out` (host).
+int solve_begin(lmfs_handle h, int problem, const double* in, double* beta);
+int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info);
 }  // namespace lmfs
 
 #define LMFS_TRY(x) do { int _rc = (x); if (_rc != LMFS_OK) return _rc; } while (0)

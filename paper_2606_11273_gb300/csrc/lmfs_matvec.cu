@@ -602,9 +602,10 @@ struct MpArgs {
 
 // M2P: one thread per target (FP64) or two targets per thread (FP32), source
 // disks staged tile by tile into shared memory with bulk asynchronous copies
-// (TMA) completing on an mbarrier, double-buffered.
+// (TMA) completing on an mbarrier, double-buffered.  One block of the launch
+// grid: target block bx, source chunk by.
 template <typename T, int TPT>
-__global__ void __launch_bounds__(M_THREADS) m2p_kernel(MpArgs a) {
+__device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
   using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char msm[];
   const uint32_t cbytes = (uint32_t)(M_TILE * MP_NCOEF * sizeof(V2));
@@ -616,10 +617,10 @@ __global__ void __launch_bounds__(M_THREADS) m2p_kernel(MpArgs a) {
   __shared__ int s_fail;
 
   const int nt = a.P * a.Mc;
-  const int t0 = (blockIdx.x * M_THREADS + threadIdx.x) * TPT;
+  const int t0 = (bx * M_THREADS + threadIdx.x) * TPT;
   const bool active = t0 < nt;
   const int ti = active ? t0 / a.Mc : 0;
-  const int k_begin = blockIdx.y * a.kchunk;
+  const int k_begin = by * a.kchunk;
   const int k_end = min(a.P, k_begin + a.kchunk);
   // target positions: FP32 double-float centre + offset, or FP64 absolute
   T xr[TPT], xi[TPT];
@@ -763,13 +764,30 @@ __global__ void __launch_bounds__(M_THREADS) m2p_kernel(MpArgs a) {
   }
   if (s_fail) { if (threadIdx.x == 0) atomicExch(a.err, 1); return; }
   if (active) {
-    double* o = a.out + blockIdx.y * a.out_stride;
+    double* o = a.out + by * a.out_stride;
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       o[2 * (t0 + q)] = ((double)sr[q] - (double)cr[q]) * a.cmu;
       o[2 * (t0 + q) + 1] = ((double)si[q] - (double)ci[q]) * a.cmu;
     }
   }
+}
+
+template <typename T, int TPT>
+__global__ void __launch_bounds__(M_THREADS) m2p_kernel(MpArgs a) {
+  m2p_block<T, TPT>(a, blockIdx.x, blockIdx.y);
+}
+
+// The far fields of several handles in one launch: block b runs work item
+// items[b] = (handle, target block, source chunk) of that handle's own m2p
+// grid, with the handle's arguments, so every output is computed exactly as
+// in the handle's own launch.
+template <typename T, int TPT>
+__global__ void __launch_bounds__(M_THREADS) m2p_multi_kernel(const MpArgs* __restrict__ args,
+                                                              const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const MpArgs a = args[it.x];
+  m2p_block<T, TPT>(a, it.y, it.z);
 }
 
 // Sum the source-range splits in a fixed order.
@@ -1313,54 +1331,130 @@ int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
 // field takes every disk pair but the disk itself and its close partners.
 static const NearSet& zone(const Ctx& c, int precision) { return c.nz[precision == LMFS_MIXED ? 1 : 0]; }
 
-int far_field(Ctx& c, const double* strength, double* out, int precision, bool skip_base) {
-  const int P = c.d.P, Mc = c.d.Mc, Nc = c.d.Nc;
-  const NearSet& z = zone(c, precision);
-  const long long n = (long long)P * Mc * 2;
-  const double cmu = INV4PI / c.prm.mu;
-  int split = 1;
+// The far field in three steps, so that the server can run the middle one
+// for several handles in one launch: moments (p2m) or FP32 records, the
+// evaluation at every target, and the sum of the source-range splits.
+static int far_pre(Ctx& c, const double* strength, int precision) {
+  const int P = c.d.P, Nc = c.d.Nc;
   if (precision == LMFS_MIXED_DIRECT) {
-    const int kchunk = c.kchunk_direct;
-    split = c.split_direct;
     records_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.src4, c.dsk32);
-    LMFS_TRY(check_launch("records"));
+    return check_launch("records");
+  }
+  p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.coef64,
+                                      precision == LMFS_MIXED ? c.coef32 : nullptr);
+  return check_launch("p2m");
+}
+
+static int far_split_of(const Ctx& c, int precision) {
+  return precision == LMFS_MIXED_DIRECT ? c.split_direct : precision == LMFS_MIXED ? c.split_m2p32 : c.split_m2p64;
+}
+
+// Arguments, grid and shared memory of a handle's multipole evaluation.
+static void mp_setup(const Ctx& c, int precision, double* out, bool skip_base, MpArgs& a, dim3& grid, size_t& shm) {
+  const int P = c.d.P, Mc = c.d.Mc;
+  const NearSet& z = zone(c, precision);
+  const bool fp32 = precision == LMFS_MIXED;
+  const int split = fp32 ? c.split_m2p32 : c.split_m2p64;
+  a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc;
+  a.coef = fp32 ? (const void*)c.coef32 : (const void*)c.coef64;
+  a.excl_off = z.excl_off; a.excl = z.excl; a.P = P; a.Mc = Mc;
+  a.kchunk = fp32 ? c.kchunk_m2p32 : c.kchunk_m2p64; a.cmu = INV4PI / c.prm.mu;
+  a.out = split > 1 ? c.ufar_part : out; a.out_stride = (long long)P * Mc * 2; a.with_log = skip_base ? 0 : 1;
+  a.err = c.far_err;
+  if (fp32) {
+    shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(float2) + 2 * M_TILE * 32 + 16;
+    grid = dim3(((P * Mc + 1) / 2 + M_THREADS - 1) / M_THREADS, split);
+  } else {
+    shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(double2) + 2 * M_TILE * 32 + 16;
+    grid = dim3((P * Mc + M_THREADS - 1) / M_THREADS, split);
+  }
+}
+
+static int far_main(Ctx& c, double* out, int precision, bool skip_base) {
+  const int P = c.d.P, Mc = c.d.Mc, Nc = c.d.Nc;
+  const long long n = (long long)P * Mc * 2;
+  if (precision == LMFS_MIXED_DIRECT) {
+    const NearSet& z = zone(c, precision);
+    const int split = c.split_direct;
     FarArgs a;
     a.tgt = c.tgt32; a.tdsk = c.dsk32; a.dsk = c.dsk32; a.rec = c.src4; a.excl_off = z.excl_off;
-    a.excl = z.excl; a.ntd = P; a.Mt = Mc; a.nsd = P; a.Nc = Nc; a.kchunk = kchunk; a.cmu = cmu;
+    a.excl = z.excl; a.ntd = P; a.Mt = Mc; a.nsd = P; a.Nc = Nc; a.kchunk = c.kchunk_direct; a.cmu = INV4PI / c.prm.mu;
     a.out = split > 1 ? c.ufar_part : out; a.out_stride = n; a.with_base = skip_base ? 0 : 1; a.err = c.far_err;
     a.range_err = c.far_err + 1;
     const int threads_needed = (P * Mc + 1) / 2;
     dim3 grid((threads_needed + F_THREADS - 1) / F_THREADS, split);
     const size_t shm = 2 * (size_t)F_TILE * Nc * 32 + 2 * F_TILE * 32 + 16;
     far32_kernel<2><<<grid, F_THREADS, shm, c.stream>>>(a);
-    LMFS_TRY(check_launch("far32"));
-  } else {
-    const bool fp32 = precision == LMFS_MIXED;
-    const int kchunk = fp32 ? c.kchunk_m2p32 : c.kchunk_m2p64;
-    split = fp32 ? c.split_m2p32 : c.split_m2p64;
-    p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.coef64, fp32 ? c.coef32 : nullptr);
-    LMFS_TRY(check_launch("p2m"));
-    MpArgs a;
-    a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc;
-    a.coef = fp32 ? (const void*)c.coef32 : (const void*)c.coef64;
-    a.excl_off = z.excl_off; a.excl = z.excl; a.P = P; a.Mc = Mc; a.kchunk = kchunk; a.cmu = cmu;
-    a.out = split > 1 ? c.ufar_part : out; a.out_stride = n; a.with_log = skip_base ? 0 : 1; a.err = c.far_err;
-    if (fp32) {
-      const size_t shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(float2) + 2 * M_TILE * 32 + 16;
-      dim3 grid(((P * Mc + 1) / 2 + M_THREADS - 1) / M_THREADS, split);
-      m2p_kernel<float, 2><<<grid, M_THREADS, shm, c.stream>>>(a);
-    } else {
-      const size_t shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(double2) + 2 * M_TILE * 32 + 16;
-      dim3 grid((P * Mc + M_THREADS - 1) / M_THREADS, split);
-      m2p_kernel<double, 1><<<grid, M_THREADS, shm, c.stream>>>(a);
-    }
-    LMFS_TRY(check_launch("m2p"));
+    return check_launch("far32");
   }
+  MpArgs a;
+  dim3 grid;
+  size_t shm = 0;
+  mp_setup(c, precision, out, skip_base, a, grid, shm);
+  if (precision == LMFS_MIXED) m2p_kernel<float, 2><<<grid, M_THREADS, shm, c.stream>>>(a);
+  else m2p_kernel<double, 1><<<grid, M_THREADS, shm, c.stream>>>(a);
+  return check_launch("m2p");
+}
+
+static int far_post(Ctx& c, double* out, int precision) {
+  const long long n = (long long)c.d.P * c.d.Mc * 2;
+  const int split = far_split_of(c, precision);
   if (split > 1) {
     reduce_splits<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, c.stream>>>(c.ufar_part, n, split, n, out);
-    LMFS_TRY(check_launch("reduce_splits"));
+    return check_launch("reduce_splits");
   }
   return LMFS_OK;
+}
+
+int far_field(Ctx& c, const double* strength, double* out, int precision, bool skip_base) {
+  LMFS_TRY(far_pre(c, strength, precision));
+  LMFS_TRY(far_main(c, out, precision, skip_base));
+  return far_post(c, out, precision);
+}
+
+int far_multi_launch(Ctx* const* cs, const int* problems, int n, int precision, cudaStream_t st, MultiFar& buf) {
+  if (n <= 0) return LMFS_OK;
+  if (precision != LMFS_MIXED && precision != LMFS_FP64) {
+    set_last_error("interleaved far field: precision must be LMFS_MIXED or LMFS_FP64");
+    return LMFS_ERR_INVALID;
+  }
+  std::vector<MpArgs> args(n);
+  std::vector<int4> items;
+  size_t shm = 0;
+  for (int r = 0; r < n; ++r) {
+    dim3 grid;
+    mp_setup(*cs[r], precision, cs[r]->ufar, problems[r] == LMFS_MOBILITY, args[r], grid, shm);
+    for (unsigned by = 0; by < grid.y; ++by)
+      for (unsigned bx = 0; bx < grid.x; ++bx) items.push_back(make_int4(r, (int)bx, (int)by, 0));
+  }
+  if (buf.args_cap < (size_t)n) {
+    if (buf.args) cudaFree(buf.args);
+    buf.args = nullptr; buf.args_cap = 0;
+    LMFS_CUDA(cudaMalloc(&buf.args, (size_t)n * sizeof(MpArgs)));
+    buf.args_cap = (size_t)n;
+  }
+  if (buf.items_cap < items.size()) {
+    if (buf.items) cudaFree(buf.items);
+    buf.items = nullptr; buf.items_cap = 0;
+    LMFS_CUDA(cudaMalloc((void**)&buf.items, items.size() * sizeof(int4)));
+    buf.items_cap = items.size();
+  }
+  // pageable sources: each copy has taken its data when the call returns
+  LMFS_CUDA(cudaMemcpyAsync(buf.args, args.data(), (size_t)n * sizeof(MpArgs), cudaMemcpyHostToDevice, st));
+  LMFS_CUDA(cudaMemcpyAsync(buf.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  if (precision == LMFS_MIXED) {
+    m2p_multi_kernel<float, 2><<<(unsigned)items.size(), M_THREADS, shm, st>>>((const MpArgs*)buf.args, buf.items);
+  } else {
+    LMFS_CUDA(cudaFuncSetAttribute(m2p_multi_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    m2p_multi_kernel<double, 1><<<(unsigned)items.size(), M_THREADS, shm, st>>>((const MpArgs*)buf.args, buf.items);
+  }
+  return check_launch("m2p multi");
+}
+
+void multi_far_free(MultiFar& buf) {
+  if (buf.args) cudaFree(buf.args);
+  if (buf.items) cudaFree(buf.items);
+  buf = MultiFar{};
 }
 
 int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar, double* u,
@@ -1384,7 +1478,9 @@ int near_field(Ctx& c, int mode, const double* strength, const double* mu, const
   return check_launch("near_reduce");
 }
 
-int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision) {
+// The matvec in three steps around the far field's evaluation (the server's
+// interleaved engine launches that step for several handles at once).
+int matvec_pre(Ctx& c, int problem, const double* mu, int precision) {
   PairBlocks& pb = c.prob[problem];
   if (!pb.ready) { set_last_error("pair blocks not computed for this problem"); return LMFS_ERR_STATE; }
   const int P = c.d.P, Nc = c.d.Nc;
@@ -1399,8 +1495,22 @@ int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precisio
   gather_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(c.lb, c.tilde, c.csr_off, c.csr_ent, P, Nc, c.radii,
                                                            c.Rc, problem == LMFS_MOBILITY, c.lam, c.sig);
   LMFS_TRY(check_launch("gather"));
-  LMFS_TRY(far_field(c, c.sig, c.ufar, precision, problem == LMFS_MOBILITY));   // Step 2a (far)
+  return far_pre(c, c.sig, precision);                                          // Step 2a: moments
+}
+
+int matvec_far(Ctx& c, int problem, int precision) {
+  return far_main(c, c.ufar, precision, problem == LMFS_MOBILITY);              // Step 2a: evaluation
+}
+
+int matvec_post(Ctx& c, int problem, const double* mu, double* u, int precision) {
+  LMFS_TRY(far_post(c, c.ufar, precision));
   return near_field(c, 0, c.sig, mu, c.ufar, u, problem, precision);            // near + identity
+}
+
+int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision) {
+  LMFS_TRY(matvec_pre(c, problem, mu, precision));
+  LMFS_TRY(matvec_far(c, problem, precision));
+  return matvec_post(c, problem, mu, u, precision);
 }
 
 int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision) {

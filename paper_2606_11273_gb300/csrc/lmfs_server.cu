@@ -1,10 +1,15 @@
-// Request server with continuous admission: requests queue on submit, a
+// Request server with continuous admission: requests queue on submit, and a
 // dispatcher admits them while a slot and enough of the device-memory budget
-// are free, and every admitted request runs on its own slot thread and CUDA
-// stream, so that requests that arrive while others are on the GPU start as
-// soon as capacity frees up and their kernels overlap on the device.  Results
-// do not depend on what else is running (no cross-request reductions; all
-// device reductions have a fixed order).
+// are free.  Every admitted request is precomputed on its own thread and CUDA
+// stream.  With the interleaved engine (the default) its GMRES then joins the
+// engine thread, which advances all resident requests one Arnoldi step at a
+// time and evaluates the far fields of every request that is ready in one
+// launch over a (request, target block, source chunk) work list; requests
+// join as they arrive and leave as they converge.  With the streams engine a
+// request's whole solve stays on its own thread and stream.  Results do not
+// depend on what else is running: each request's values come from the same
+// kernels in the same order (no cross-request reductions; all device
+// reductions have a fixed order).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -20,6 +25,18 @@
 #include "lmfs_internal.h"
 
 namespace {
+
+struct Request;
+
+// A request on the interleaved engine: its handle, stream and step state.
+struct Active {
+  std::shared_ptr<Request> rq;
+  lmfs_handle h = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_pre = nullptr, ev_step = nullptr;
+  int iters = 0;
+  bool in_flight = false;
+};
 
 struct Request {
   uint64_t ticket = 0;
@@ -47,6 +64,10 @@ struct lmfs_server {
   int running = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
+  // interleaved engine
+  std::thread engine;
+  std::condition_variable cv_engine;             // engine wakes on hand-off / stop
+  std::deque<std::unique_ptr<Active>> handoff;   // precomputed requests for the engine
 };
 
 namespace {
@@ -81,25 +102,7 @@ size_t estimate_bytes(const double* c, const double* r, int P, const lmfs_params
   return (size_t)(blocks + basis + vecs + ws + (64 << 20));
 }
 
-void run_request(lmfs_server* s, std::shared_ptr<Request> rq) {
-  cudaSetDevice(s->sp.device);
-  cudaStream_t st = nullptr;
-  int rc = LMFS_OK;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = LMFS_ERR_CUDA;
-  lmfs_handle h = nullptr;
-  if (rc == LMFS_OK) {
-    lmfs_params p = rq->prm;
-    p.stream = st;
-    p.device = s->sp.device;
-    p.precision = s->sp.precision;
-    rc = lmfs_create(rq->centres.data(), rq->radii.data(), rq->P, &p, &h);
-  }
-  if (rc == LMFS_OK) {
-    rq->out.assign(3 * (size_t)rq->P, 0.0);
-    rc = lmfs_solve(h, rq->problem, rq->in.data(), rq->out.data(), &rq->info);
-  }
-  if (h) lmfs_destroy(h);
-  if (st) cudaStreamDestroy(st);
+void complete(lmfs_server* s, const std::shared_ptr<Request>& rq, int rc) {
   std::lock_guard<std::mutex> lk(s->mu);
   rq->rc = rc;
   rq->t_end = std::chrono::steady_clock::now();
@@ -107,6 +110,144 @@ void run_request(lmfs_server* s, std::shared_ptr<Request> rq) {
   s->running -= 1;
   s->cv_done.notify_all();
   s->cv_dispatch.notify_all();
+}
+
+void release(Active& a) {
+  if (a.h) lmfs_destroy(a.h);
+  if (a.ev_pre) cudaEventDestroy(a.ev_pre);
+  if (a.ev_step) cudaEventDestroy(a.ev_step);
+  if (a.st) cudaStreamDestroy(a.st);
+  a.h = nullptr; a.ev_pre = a.ev_step = nullptr; a.st = nullptr;
+}
+
+// One admitted request: its handle on its own stream; then either the whole
+// solve here (streams engine) or the precompute, right-hand side and first
+// Krylov vector here and the Arnoldi steps on the engine.
+void run_request(lmfs_server* s, std::shared_ptr<Request> rq) {
+  cudaSetDevice(s->sp.device);
+  auto a = std::make_unique<Active>();
+  a->rq = rq;
+  int rc = LMFS_OK;
+  if (cudaStreamCreateWithFlags(&a->st, cudaStreamNonBlocking) != cudaSuccess) rc = LMFS_ERR_CUDA;
+  if (rc == LMFS_OK) {
+    lmfs_params p = rq->prm;
+    p.stream = a->st;
+    p.device = s->sp.device;
+    p.precision = s->sp.precision;
+    rc = lmfs_create(rq->centres.data(), rq->radii.data(), rq->P, &p, &a->h);
+  }
+  if (rc == LMFS_OK) rq->out.assign(3 * (size_t)rq->P, 0.0);
+  if (rc == LMFS_OK && s->sp.engine == LMFS_ENGINE_STREAMS) {
+    rc = lmfs_solve(a->h, rq->problem, rq->in.data(), rq->out.data(), &rq->info);
+  } else if (rc == LMFS_OK) {
+    double beta = 0.0;
+    rc = lmfs::solve_begin(a->h, rq->problem, rq->in.data(), &beta);
+    if (rc == LMFS_OK && beta > 0.0) {
+      if (cudaEventCreateWithFlags(&a->ev_pre, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a->ev_step, cudaEventDisableTiming) != cudaSuccess) {
+        rc = LMFS_ERR_CUDA;
+      } else {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->handoff.push_back(std::move(a));
+        s->cv_engine.notify_all();
+        return;                                   // the engine completes it
+      }
+    } else if (rc == LMFS_OK) {
+      rc = lmfs::solve_finish(a->h, rq->problem, 0, 0.0, rq->out.data(), &rq->info);   // b = 0: x = 0
+    }
+  }
+  release(*a);
+  complete(s, rq, rc);
+}
+
+// The interleaved engine.  Each pass: collect the requests whose last step has
+// finished, read their residuals, complete the converged ones, and advance the
+// rest together -- their pre-far parts on their own streams, the far field of
+// all of them in one launch on the engine stream, then their post-far parts
+// (near field, orthogonalization, residual) on their own streams again.
+void engine_loop(lmfs_server* s) {
+  cudaSetDevice(s->sp.device);
+  cudaStream_t est = nullptr;
+  cudaEvent_t ev_far = nullptr;
+  lmfs::MultiFar buf;
+  const bool ok = cudaStreamCreateWithFlags(&est, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&ev_far, cudaEventDisableTiming) == cudaSuccess;
+  const int prec = s->sp.precision;
+  std::vector<std::unique_ptr<Active>> act;
+  auto fail = [&](Active& a, int rc) { release(a); complete(s, a.rq, rc); };
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (act.empty()) s->cv_engine.wait(lk, [&] { return s->stop || !s->handoff.empty(); });
+      while (!s->handoff.empty()) { act.push_back(std::move(s->handoff.front())); s->handoff.pop_front(); }
+      if (s->stop && act.empty()) break;
+    }
+    // harvest finished steps
+    std::vector<Active*> ready;
+    for (auto& up : act) {
+      Active& a = *up;
+      if (!a.h) continue;
+      if (!ok) { fail(a, LMFS_ERR_CUDA); continue; }
+      if (a.in_flight) {
+        const cudaError_t q = cudaEventQuery(a.ev_step);
+        if (q == cudaErrorNotReady) continue;
+        a.in_flight = false;
+        if (q != cudaSuccess) { cudaGetLastError(); fail(a, LMFS_ERR_CUDA); continue; }
+        a.iters += 1;
+        const lmfs::Ctx& c = a.h->c;
+        const double relres = c.host_pinned[1];
+        if (!(relres == relres)) { fail(a, LMFS_ERR_NUMERICAL); continue; }
+        if (relres <= c.prm.tol || c.host_pinned[3] != 0.0 || a.iters >= std::max(1, c.prm.maxit)) {
+          const int rc = lmfs::solve_finish(a.h, a.rq->problem, a.iters, relres, a.rq->out.data(), &a.rq->info);
+          release(a);
+          complete(s, a.rq, rc);
+          continue;
+        }
+      }
+      ready.push_back(&a);
+    }
+    act.erase(std::remove_if(act.begin(), act.end(), [](const std::unique_ptr<Active>& a) { return !a->h; }),
+              act.end());
+    if (!ready.empty()) {
+      std::vector<lmfs::Ctx*> cs;
+      std::vector<int> problems;
+      int rc = LMFS_OK;
+      for (Active* a : ready) {
+        lmfs::Ctx& c = a->h->c;
+        if ((rc = lmfs::gmres_step_pre(c, a->rq->problem, prec)) != LMFS_OK) break;
+        if (cudaEventRecord(a->ev_pre, a->st) != cudaSuccess || cudaStreamWaitEvent(est, a->ev_pre, 0) != cudaSuccess) {
+          rc = LMFS_ERR_CUDA;
+          break;
+        }
+        cs.push_back(&c);
+        problems.push_back(a->rq->problem);
+      }
+      if (rc == LMFS_OK) rc = lmfs::far_multi_launch(cs.data(), problems.data(), (int)cs.size(), prec, est, buf);
+      if (rc == LMFS_OK && cudaEventRecord(ev_far, est) != cudaSuccess) rc = LMFS_ERR_CUDA;
+      for (Active* a : ready) {
+        int r = rc;
+        if (r == LMFS_OK && cudaStreamWaitEvent(a->st, ev_far, 0) != cudaSuccess) r = LMFS_ERR_CUDA;
+        if (r == LMFS_OK) r = lmfs::gmres_step_post(a->h->c, a->rq->problem, prec);
+        if (r == LMFS_OK && cudaEventRecord(a->ev_step, a->st) != cudaSuccess) r = LMFS_ERR_CUDA;
+        if (r == LMFS_OK) {
+          a->in_flight = true;
+        } else {
+          // nothing of this request is left in flight once its stream is idle
+          cudaStreamSynchronize(a->st);
+          cudaStreamSynchronize(est);
+          fail(*a, r);
+        }
+      }
+      act.erase(std::remove_if(act.begin(), act.end(), [](const std::unique_ptr<Active>& a) { return !a->h; }),
+                act.end());
+    } else if (!act.empty()) {
+      std::this_thread::sleep_for(std::chrono::microseconds(20));   // every resident request is in flight
+    }
+  }
+  if (est) cudaStreamSynchronize(est);
+  lmfs::multi_far_free(buf);
+  if (ev_far) cudaEventDestroy(ev_far);
+  if (est) cudaStreamDestroy(est);
 }
 
 void dispatch_loop(lmfs_server* s) {
@@ -134,12 +275,14 @@ extern "C" {
 
 int lmfs_server_create(const lmfs_server_params* sp, lmfs_server** out) {
   if (!sp || !out || sp->max_slots < 1 || sp->hbm_budget_bytes == 0 ||
-      (sp->precision != LMFS_FP64 && sp->precision != LMFS_MIXED))
+      (sp->precision != LMFS_FP64 && sp->precision != LMFS_MIXED) ||
+      (sp->engine != LMFS_ENGINE_INTERLEAVED && sp->engine != LMFS_ENGINE_STREAMS))
     return LMFS_ERR_INVALID;
   auto* s = new (std::nothrow) lmfs_server();
   if (!s) return LMFS_ERR_NOMEM;
   s->sp = *sp;
   s->dispatcher = std::thread(dispatch_loop, s);
+  if (s->sp.engine == LMFS_ENGINE_INTERLEAVED) s->engine = std::thread(engine_loop, s);
   *out = s;
   return LMFS_OK;
 }
@@ -196,9 +339,11 @@ int lmfs_server_destroy(lmfs_server* s) {
     s->cv_done.wait(lk, [&] { return s->running == 0; });
     s->stop = true;
     s->cv_dispatch.notify_all();
+    s->cv_engine.notify_all();
   }
   s->dispatcher.join();
   for (auto& t : s->slots) if (t.joinable()) t.join();
+  if (s->engine.joinable()) s->engine.join();
   delete s;
   return LMFS_OK;
 }

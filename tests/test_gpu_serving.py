@@ -35,28 +35,36 @@ def requests(n, seed=0):
     return out
 
 
-def params(L):
-    return L.Params(Nfp=100, Nell=40, Mp=120, tol=1e-9)
+def params(L, precision=None):
+    kw = dict(Nfp=100, Nell=40, Mp=120, tol=1e-9)
+    if precision is not None:
+        kw["precision"] = precision
+    return L.Params(**kw)
 
 
-def test_served_results_equal_alone(L):
+@pytest.mark.parametrize("engine,prec", [(0, "MIXED"), (1, "MIXED"), (0, "FP64")])
+def test_served_results_equal_alone(L, engine, prec):
     """Each request's result in the mix is identical to the same solve run
-    alone (bitwise: no cross-request reductions, fixed reduction orders)."""
-    reqs = requests(8)
+    alone (bitwise: no cross-request reductions, fixed reduction orders), with
+    the interleaved engine (one far-field launch for every ready request per
+    Arnoldi step) and with one stream per request."""
+    precision = getattr(L, prec)
+    reqs = requests(8 if prec == "MIXED" else 4)
     alone = []
     for pk, problem, data in reqs:
-        s = L.Solver(pk.centres, pk.radii, params(L))
+        s = L.Solver(pk.centres, pk.radii, params(L, precision))
         out, info = s.solve(problem, data)
         assert info["converged"]
         alone.append(out)
         s.close()
-    srv = L.Server(hbm_budget_bytes=20 << 30, max_slots=4)
+    srv = L.Server(hbm_budget_bytes=20 << 30, max_slots=4, precision=precision, engine=engine)
     tickets = []
     for (pk, problem, data) in reqs:
-        tickets.append(srv.submit(pk.centres, pk.radii, problem, data, params(L)))
+        tickets.append(srv.submit(pk.centres, pk.radii, problem, data, params(L, precision)))
     for (t, P), ref in zip(tickets, alone):
         rc, out, info = srv.poll(t, P, timeout_us=120_000_000)
         assert rc == 0, L._lib.strerror(rc)
+        assert info["iters"] > 0
         assert np.array_equal(out, ref)
     srv.close()
 
