@@ -443,7 +443,7 @@ def run_serving(args):
     s0 = L.Solver(pk0.centres, pk0.radii, prm()); s0.solve(L.MOBILITY, w.forces_torques(20, 1)); s0.close()
     torch.cuda.synchronize()
     # served, mixed precision: submit at the arrival times, poll without blocking
-    srv = L.Server(hbm_budget_bytes=150 << 30, max_slots=args.slots, precision=L.MIXED)
+    srv = L.Server(hbm_budget_bytes=150 << 30, max_slots=args.slots, precision=L.MIXED, engine=args.engine)
     pending, done, lat = {}, {}, {}
     q = 0
     start = time.perf_counter()
@@ -493,7 +493,7 @@ def run_serving(args):
     Ps = [x[1].P for x in stream]
     print(json.dumps({
         "serving": {"requests": len(stream), "P_range": [min(Ps), max(Ps)], "P_median": float(np.median(Ps)),
-                    "mean_arrival_gap_ms": 20.0, "hbm_budget_gb": 150, "slots": args.slots, "tol": 1e-7,
+                    "mean_arrival_gap_ms": 20.0, "hbm_budget_gb": 150, "slots": args.slots, "engine": ["interleaved", "streams"][args.engine], "tol": 1e-7,
                     "generation_s": t_gen},
         "served_mixed": {"solves_per_s": len(stream) / served_s, "wall_s": served_s,
                          "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
@@ -584,6 +584,8 @@ def main():
     ap.add_argument("--requests", type=int, default=64, help="serving: requests in the stream (config: 256)")
     ap.add_argument("--pmax", type=int, default=5000, help="serving: largest disk count")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent request slots")
+    ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
+                    help="serving: 0 = interleaved (one far-field launch for all ready requests), 1 = a stream per request")
     ap.add_argument("--baseline-requests", type=int, default=24,
                     help="serving: requests (from the start of the stream) solved one at a time in FP64")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
