@@ -274,15 +274,31 @@ int lmfs_precompute_pairs(lmfs_handle h, int problem) {
   return LMFS_OK;
 }
 
+// Per block, row-major <-> column-major (the same operation both ways).
+static void transpose_blocks(const double* in, double* out, int C, size_t n) {
+  for (int q = 0; q < C; ++q) {
+    const double* a = in + (size_t)q * n * n;
+    double* b = out + (size_t)q * n * n;
+    for (size_t i = 0; i < n; ++i)
+      for (size_t j = 0; j < n; ++j) b[j * n + i] = a[i * n + j];
+  }
+}
+
 int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E) {
   if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
   if (!c.prob[problem].ready) return LMFS_ERR_STATE;
   const size_t n4 = 4 * (size_t)c.d.Nc;
   if (c.C == 0) return LMFS_OK;
-  if (A) LMFS_CUDA(cudaMemcpyAsync(A, c.prob[problem].A, c.C * n4 * n4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  std::vector<double> colmajor;
+  if (A) {
+    colmajor.resize(c.C * n4 * n4);
+    LMFS_CUDA(cudaMemcpyAsync(colmajor.data(), c.prob[problem].A, c.C * n4 * n4 * sizeof(double), cudaMemcpyDeviceToHost,
+                              c.stream));
+  }
   if (E) LMFS_CUDA(cudaMemcpyAsync(E, c.prob[problem].E, c.C * 6 * n4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  if (A) transpose_blocks(colmajor.data(), A, c.C, n4);   // device storage is column by column
   return LMFS_OK;
 }
 
@@ -295,7 +311,9 @@ int lmfs_set_pair_blocks(lmfs_handle h, int problem, const double* A, const doub
   if (!pb.A) LMFS_TRY(dalloc(&pb.A, std::max<size_t>(c.C, 1) * n4 * n4));
   if (!pb.E) LMFS_TRY(dalloc(&pb.E, std::max<size_t>(c.C, 1) * 6 * n4));
   if (c.C) {
-    LMFS_CUDA(cudaMemcpyAsync(pb.A, A, c.C * n4 * n4 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    std::vector<double> colmajor(c.C * n4 * n4);
+    transpose_blocks(A, colmajor.data(), c.C, n4);          // device storage is column by column
+    LMFS_CUDA(cudaMemcpyAsync(pb.A, colmajor.data(), c.C * n4 * n4 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     LMFS_CUDA(cudaMemcpyAsync(pb.E, E, c.C * 6 * n4 * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   }
   LMFS_CUDA(cudaStreamSynchronize(c.stream));

@@ -97,24 +97,44 @@ __global__ void onebody_apply_kernel(const double* __restrict__ Wt, const double
 }
 
 // ---- Step 1b: lam~ = A [lam_bar_i; lam_bar_k] per close pair ----------------
-__global__ void pair_apply_kernel(const double* __restrict__ A, const int* __restrict__ pairs, int C,
-                                  int Nc, const double* __restrict__ lb, double* __restrict__ tilde) {
-  // block (c, y) takes rows y, y + gridDim.y, ... of pair c (a warp per row)
-  extern __shared__ double xs[];
+// A is stored column by column ([C][col][row]).  Block (c, y) takes rows
+// 32 y .. 32 y + 31 of pair c: warp g sums the columns of group g (a strided
+// eighth of them) for its lane's row, so every load of A is a coalesced
+// 256-byte row segment and x[col] is one shared-memory broadcast; the PA_G
+// partial sums are then added in a fixed order.  No shuffles: the FP64 pipe
+// does only the 4Nc multiply-adds per row and PA_G - 1 adds.
+constexpr int PA_G = 8;   // column groups (warps) per block
+
+__global__ void __launch_bounds__(PA_G * 32) pair_apply_kernel(const double* __restrict__ A, const int* __restrict__ pairs,
+                                                                int C, int Nc, const double* __restrict__ lb,
+                                                                double* __restrict__ tilde) {
+  __shared__ double xs[4 * 256];            // 4 Nc <= 1024 (checked by the caller)
+  __shared__ double part[PA_G][32];
   const int c = blockIdx.x;
   const int n4 = 4 * Nc, ns = 2 * Nc;
   const int i = pairs[2 * c], k = pairs[2 * c + 1];
   for (int t = threadIdx.x; t < n4; t += blockDim.x)
     xs[t] = (t < ns) ? lb[(long long)i * ns + t] : lb[(long long)k * ns + (t - ns)];
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int row = blockIdx.y * 32 + lane;
   const double* Ac = A + (long long)c * n4 * n4;
-  for (int row = blockIdx.y + gridDim.y * wid; row < n4; row += gridDim.y * nw) {
-    const double* ar = Ac + (long long)row * n4;
-    double acc = 0.0;
-    for (int col = lane; col < n4; col += 32) acc += ar[col] * xs[col];
-    acc = lsum(acc);
-    if (lane == 0) tilde[(long long)c * n4 + row] = acc;
+  double acc0 = 0.0, acc1 = 0.0;
+  if (row < n4) {
+    int col = g;
+    for (; col + PA_G < n4; col += 2 * PA_G) {
+      acc0 = fma(Ac[(long long)col * n4 + row], xs[col], acc0);
+      acc1 = fma(Ac[(long long)(col + PA_G) * n4 + row], xs[col + PA_G], acc1);
+    }
+    if (col < n4) acc0 = fma(Ac[(long long)col * n4 + row], xs[col], acc0);
+  }
+  part[g][lane] = acc0 + acc1;
+  __syncthreads();
+  if (g == 0 && row < n4) {
+    double s = part[0][lane];
+#pragma unroll
+    for (int q = 1; q < PA_G; ++q) s += part[q][lane];
+    tilde[(long long)c * n4 + row] = s;
   }
 }
 
@@ -1486,10 +1506,8 @@ int matvec_pre(Ctx& c, int problem, const double* mu, int precision) {
   const int P = c.d.P, Nc = c.d.Nc;
   LMFS_TRY(onebody_apply(c, pb.ob, mu, c.lb));                                   // Step 1a
   if (c.C > 0) {                                                                 // Step 1b
-    // rows of a pair over several blocks when the pairs alone leave SMs idle
-    const int ry = std::max(1, std::min(8, (2 * c.sms + c.C - 1) / c.C));
-    pair_apply_kernel<<<dim3(c.C, ry), 256, 4 * Nc * sizeof(double), c.stream>>>(pb.A, c.pairs, c.C, Nc, c.lb,
-                                                                                c.tilde);
+    if (4 * Nc > 1024) { set_last_error("4 Nc > 1024 not supported"); return LMFS_ERR_INVALID; }
+    pair_apply_kernel<<<dim3(c.C, (4 * Nc + 31) / 32), PA_G * 32, 0, c.stream>>>(pb.A, c.pairs, c.C, Nc, c.lb, c.tilde);
     LMFS_TRY(check_launch("pair_apply"));
   }
   gather_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(c.lb, c.tilde, c.csr_off, c.csr_ent, P, Nc, c.radii,

@@ -485,10 +485,11 @@ __global__ void assemble_A_sym(int Nc, const double* X, int xld, long long xstri
     const double xp = Xp[(long long)c * xld + r], xm = Xm[(long long)c * xld + r];
     const int r2 = nh + 2 * (((r >> 1) + Nc / 2) % Nc) + (r & 1);
     const int c2 = nh + 2 * (((c >> 1) + Nc / 2) % Nc) + (c & 1);
-    Ab[(long long)r * n4 + c] = -0.5 * (xp + xm);
-    Ab[(long long)r * n4 + c2] = -0.5 * (xp - xm);
-    Ab[(long long)r2 * n4 + c] = -0.5 * (xp - xm);
-    Ab[(long long)r2 * n4 + c2] = -0.5 * (xp + xm);
+    // A is stored column by column (element (row, col) at col * n4 + row)
+    Ab[(long long)c * n4 + r] = -0.5 * (xp + xm);
+    Ab[(long long)c2 * n4 + r] = -0.5 * (xp - xm);
+    Ab[(long long)c * n4 + r2] = -0.5 * (xp - xm);
+    Ab[(long long)c2 * n4 + r2] = -0.5 * (xp + xm);
   }
 }
 
@@ -675,7 +676,7 @@ __global__ void store_A(const double* X, int xld, long long xstride, int n4, dou
   const double* Xb = X + (long long)b * xstride;
   double* Ab = A + (long long)(Cfirst + b) * n4 * n4;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4 * n4; t += gridDim.x * blockDim.x) {
-    const int row = t / n4, col = t % n4;
+    const int row = t % n4, col = t / n4;       // A column by column, like X
     Ab[t] = -Xb[(long long)col * xld + row];
   }
 }
