@@ -55,7 +55,7 @@ static void free_ctx(Ctx& c) {
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
-  dfree(c.ufar_part); dfree(c.ring); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
+  dfree(c.ufar_part); dfree(c.ring); dfree(c.nodes); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
   if (c.own_stream && c.stream) { cudaStreamDestroy(c.stream); c.stream = nullptr; c.own_stream = false; }
 }
 
@@ -329,7 +329,10 @@ int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double*
   PairBlocks& pb = c.prob[problem];
   if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
   const int ns = 2 * c.d.Nc, nn = 2 * c.d.Mc, nc = pb.ob.nclass;
-  if (!pb.ob.V) LMFS_TRY(dalloc(&pb.ob.V, (size_t)nc * ns * ns));
+  if (!pb.ob.V) {
+    LMFS_TRY(dalloc(&pb.ob.V, (size_t)nc * ns * ns));
+    gmres_drop_graphs(c);                 // graphs captured without V
+  }
   // W = U^T rows, R = diag(sigma) (the back substitution scales by 1/sigma), V dense
   std::vector<double> R((size_t)nc * ns * ns, 0.0);
   std::vector<int> perm((size_t)nc * ns), rk(rank, rank + nc);

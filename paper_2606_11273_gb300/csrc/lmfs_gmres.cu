@@ -171,14 +171,17 @@ __global__ void combine_x(const double* V, long long n, const double* y, int k, 
 
 }  // namespace
 
-void gmres_free(Ctx& c) {
+void gmres_drop_graphs(Ctx& c) {
   for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 3; ++b)
-    {
+    for (int b = 0; b < 3; ++b) {
       if (c.graph_exec[a][b]) { cudaGraphExecDestroy(c.graph_exec[a][b]); c.graph_exec[a][b] = nullptr; }
       if (c.step_pre[a][b]) { cudaGraphExecDestroy(c.step_pre[a][b]); c.step_pre[a][b] = nullptr; }
       if (c.step_post[a][b]) { cudaGraphExecDestroy(c.step_post[a][b]); c.step_post[a][b] = nullptr; }
     }
+}
+
+void gmres_free(Ctx& c) {
+  gmres_drop_graphs(c);
   dfree(c.V); dfree(c.w); dfree(c.H); dfree(c.gvec); dfree(c.cs); dfree(c.sn); dfree(c.hpart);
   dfree(c.scal); dfree(c.jdev);
   if (c.host_pinned) { cudaFreeHost(c.host_pinned); c.host_pinned = nullptr; }

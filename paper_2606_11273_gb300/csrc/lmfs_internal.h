@@ -139,6 +139,7 @@ struct Ctx {
   double* ufar_part = nullptr;       // [far_split][P][Mc][2]
   int sms = 152;                     // multiprocessors of the handle's device
   double2* ring = nullptr;           // [Nc] (cos, sin)(2 pi j / Nc) of the source rings
+  double2* nodes = nullptr;          // [Mc] (cos, sin)(2 pi m / Mc) of the collocation nodes
   int* far_err = nullptr;            // set by the far kernel if a bounded wait expired
   double2* coef64 = nullptr;         // [P][64] multipole coefficients (FP64)
   float2* coef32 = nullptr;          // [P][64] the same rounded to FP32
@@ -264,6 +265,9 @@ int stokeslet_sum_noalloc(const double* targets, int nt, const double* centres, 
 int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x,
                 lmfs_solve_info* info);
 void gmres_free(Ctx& c);
+// The captured GMRES graphs hold the device addresses of every buffer the
+// matvec reads; drop them whenever one of those buffers is reallocated.
+void gmres_drop_graphs(Ctx& c);
 // gmres_solve in steps, for the server's interleaved engine (the same kernels
 // in the same order, so the same result):
 //   gmres_begin: basis, first vector, and the two step graphs; *beta = |b|;

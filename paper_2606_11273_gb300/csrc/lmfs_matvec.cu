@@ -164,8 +164,8 @@ __device__ __forceinline__ void warp_project(double (&sx)[SPL], double (&sy)[SPL
 // (CSR order: deterministic); sig_i = proj(lam_i).
 __global__ void gather_kernel(const double* __restrict__ lb, const double* __restrict__ tilde,
                               const int* __restrict__ csr_off, const int* __restrict__ csr_ent, int P,
-                              int Nc, const double* __restrict__ radii, double Rc, int mobility,
-                              double* __restrict__ lam, double* __restrict__ sig) {
+                              int Nc, const double* __restrict__ radii, double Rc, const double2* __restrict__ ring,
+                              int mobility, double* __restrict__ lam, double* __restrict__ sig) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= P) return;
   const int i = warp, ns = 2 * Nc, n4 = 4 * Nc;
@@ -179,8 +179,8 @@ __global__ void gather_kernel(const double* __restrict__ lb, const double* __res
     if (j < Nc) {
       sx[q] = lb[(long long)i * ns + 2 * j];
       sy[q] = lb[(long long)i * ns + 2 * j + 1];
-      const double ph = 2.0 * LMFS_PI * j / Nc;
-      ex[q] = rs * cos(ph); ey[q] = rs * sin(ph);
+      const double2 cs = ring[j];
+      ex[q] = rs * cs.x; ey[q] = rs * cs.y;
     }
   }
   for (int e = csr_off[i]; e < csr_off[i + 1]; ++e) {
@@ -209,15 +209,16 @@ __global__ void gather_kernel(const double* __restrict__ lb, const double* __res
 // y.s) and (s_x, s_y, 0, 0), y = source offset from the disk centre; per disk
 // the strength sum (FP64 sum rounded once).  One warp per disk.
 __global__ void records_kernel(const double* __restrict__ s, int P, int Nc, const double* __restrict__ radii,
-                               double Rc, float4* __restrict__ rec, float4* __restrict__ dsk) {
+                               double Rc, const double2* __restrict__ ring, float4* __restrict__ rec,
+                               float4* __restrict__ dsk) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= P) return;
   const int i = warp;
   const double rs = radii[i] * Rc;
   double tx = 0, ty = 0;
   for (int j = lane; j < Nc; j += 32) {
-    const double ph = 2.0 * LMFS_PI * j / Nc;
-    const double yx = rs * cos(ph), yy = rs * sin(ph);
+    const double2 cs = ring[j];
+    const double yx = rs * cs.x, yy = rs * cs.y;
     const double sx = s[(long long)i * 2 * Nc + 2 * j], sy = s[(long long)i * 2 * Nc + 2 * j + 1];
     rec[2 * ((long long)i * Nc + j)] = make_float4((float)yx, (float)yy, (float)(yx * yx + yy * yy), (float)(yx * sx + yy * sy));
     rec[2 * ((long long)i * Nc + j) + 1] = make_float4((float)sx, (float)sy, 0.f, 0.f);
@@ -611,6 +612,7 @@ constexpr int M_TILE = 16;     // source disks per staged tile
 struct MpArgs {
   const float2* tgt; const float4* dsk;      // FP32 path: node offsets, double-float centres
   const double* centres; const double* radii; int Mc_nodes;
+  const double2* nodes;                      // FP64 path: [Mc] (cos, sin)(2 pi m / Mc)
   const void* coef;                          // [P][MP_NCOEF] float2 or double2
   const int* excl_off; const int* excl;
   int P, Mc, kchunk;
@@ -652,10 +654,9 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
       for (int q = 0; q < TPT; ++q) { xr[q] = (T)a.tgt[t0 + q].x; xi[q] = (T)a.tgt[t0 + q].y; }
     } else {
       for (int q = 0; q < TPT; ++q) {
-        const int m = (t0 + q) % a.Mc;
-        const double th = 2.0 * LMFS_PI * m / a.Mc;
-        xr[q] = (T)(a.centres[2 * ti] + a.radii[ti] * cos(th));
-        xi[q] = (T)(a.centres[2 * ti + 1] + a.radii[ti] * sin(th));
+        const double2 cs = a.nodes[(t0 + q) % a.Mc];
+        xr[q] = (T)(a.centres[2 * ti] + a.radii[ti] * cs.x);
+        xi[q] = (T)(a.centres[2 * ti + 1] + a.radii[ti] * cs.y);
       }
     }
   }
@@ -881,7 +882,8 @@ __device__ __forceinline__ double rcp_pos(double a) {
 //     entries, self included, of S^(ik) s_k).
 __global__ void near_kernel(int mode, const double* __restrict__ centres, const double* __restrict__ radii,
                             double Rc, int Mc, int Nc, int G, const double2* __restrict__ ring,
-                            const int* __restrict__ near_tgt, const int4* __restrict__ near_ent,
+                            const double2* __restrict__ nodes, const int* __restrict__ near_tgt,
+                            const int4* __restrict__ near_ent,
                             const double* __restrict__ sig, const double* __restrict__ lam,
                             const double* __restrict__ lb, const double* __restrict__ tilde, int mobility,
                             double* __restrict__ part) {
@@ -899,9 +901,9 @@ __global__ void near_kernel(int mode, const double* __restrict__ centres, const 
   const int j0 = g * Nc / G, j1 = (g + 1) * Nc / G;
   double xx = 0, xy = 0;
   if (act) {
-    const double th = 2.0 * LMFS_PI * m / Mc;
-    xx = centres[2 * i] + radii[i] * cos(th);
-    xy = centres[2 * i + 1] + radii[i] * sin(th);
+    const double2 cs = nodes[m];
+    xx = centres[2 * i] + radii[i] * cs.x;
+    xy = centres[2 * i + 1] + radii[i] * cs.y;
   }
   const double rs = radii[k] * Rc;
   double t0 = 0, t1 = 0, t2 = 0;
@@ -1331,6 +1333,13 @@ int far_field_prepare(Ctx& c) {
     }
     LMFS_TRY(dalloc(&c.ring, (size_t)c.d.Nc));
     LMFS_CUDA(cudaMemcpyAsync(c.ring, ring.data(), ring.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+    std::vector<double2> nodes(c.d.Mc);
+    for (int m = 0; m < c.d.Mc; ++m) {
+      const double th = 2.0 * LMFS_PI * m / c.d.Mc;
+      nodes[m] = make_double2(std::cos(th), std::sin(th));
+    }
+    LMFS_TRY(dalloc(&c.nodes, (size_t)c.d.Mc));
+    LMFS_CUDA(cudaMemcpyAsync(c.nodes, nodes.data(), nodes.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
     LMFS_CUDA(cudaStreamSynchronize(c.stream));
   }
   for (NearSet& z : c.nz) LMFS_TRY(dalloc(&z.part, std::max<size_t>(1, z.h.size()) * c.d.Mc * 2));
@@ -1357,7 +1366,7 @@ static const NearSet& zone(const Ctx& c, int precision) { return c.nz[precision 
 static int far_pre(Ctx& c, const double* strength, int precision) {
   const int P = c.d.P, Nc = c.d.Nc;
   if (precision == LMFS_MIXED_DIRECT) {
-    records_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.src4, c.dsk32);
+    records_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.src4, c.dsk32);
     return check_launch("records");
   }
   p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.coef64,
@@ -1375,7 +1384,7 @@ static void mp_setup(const Ctx& c, int precision, double* out, bool skip_base, M
   const NearSet& z = zone(c, precision);
   const bool fp32 = precision == LMFS_MIXED;
   const int split = fp32 ? c.split_m2p32 : c.split_m2p64;
-  a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc;
+  a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc; a.nodes = c.nodes;
   a.coef = fp32 ? (const void*)c.coef32 : (const void*)c.coef64;
   a.excl_off = z.excl_off; a.excl = z.excl; a.P = P; a.Mc = Mc;
   a.kchunk = fp32 ? c.kchunk_m2p32 : c.kchunk_m2p64; a.cmu = INV4PI / c.prm.mu;
@@ -1487,7 +1496,7 @@ int near_field(Ctx& c, int mode, const double* strength, const double* mu, const
   const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mc * 2) * sizeof(double);
   const int ne = (int)z.h.size();
   if (ne > 0) {
-    near_kernel<<<ne, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, z.tgt,
+    near_kernel<<<ne, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, c.nodes, z.tgt,
                                                 z.ent, strength, c.lam, c.lb, c.tilde,
                                                 problem == LMFS_MOBILITY, z.part);
     LMFS_TRY(check_launch("near"));
@@ -1511,7 +1520,7 @@ int matvec_pre(Ctx& c, int problem, const double* mu, int precision) {
     LMFS_TRY(check_launch("pair_apply"));
   }
   gather_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(c.lb, c.tilde, c.csr_off, c.csr_ent, P, Nc, c.radii,
-                                                           c.Rc, problem == LMFS_MOBILITY, c.lam, c.sig);
+                                                           c.Rc, c.ring, problem == LMFS_MOBILITY, c.lam, c.sig);
   LMFS_TRY(check_launch("gather"));
   return far_pre(c, c.sig, precision);                                          // Step 2a: moments
 }

@@ -696,13 +696,17 @@ int build_onebody(Ctx& c, int problem, OneBody& ob) {
   const int ld = m;
   const long long mstride = (long long)ld * (n + k);
   ob.nclass = nb;
-  // a rebuild (after lmfs_invalidate) replaces every factor, including
-  // imported SVD factors' V, which the QR form does not use
-  dfree(ob.W); dfree(ob.R); dfree(ob.perm); dfree(ob.rank); dfree(ob.V);
-  LMFS_TRY(dalloc(&ob.W, (size_t)nb * n * 2 * Mc));
-  LMFS_TRY(dalloc(&ob.R, (size_t)nb * n * n));
-  LMFS_TRY(dalloc(&ob.perm, (size_t)nb * n));
-  LMFS_TRY(dalloc(&ob.rank, (size_t)nb));
+  // a rebuild (after lmfs_invalidate) recomputes the factors into the same
+  // buffers, so that the captured GMRES graphs, which hold their addresses,
+  // stay valid; imported SVD factors' V, which the QR form does not use, is
+  // dropped, and with it the graphs captured while it was in use
+  if (ob.V) { dfree(ob.V); gmres_drop_graphs(c); }
+  if (!ob.W) {
+    LMFS_TRY(dalloc(&ob.W, (size_t)nb * n * 2 * Mc));
+    LMFS_TRY(dalloc(&ob.R, (size_t)nb * n * n));
+    LMFS_TRY(dalloc(&ob.perm, (size_t)nb * n));
+    LMFS_TRY(dalloc(&ob.rank, (size_t)nb));
+  }
   double *ws = nullptr, *tau = nullptr, *vn = nullptr;
   int *dm = nullptr, *dn = nullptr, *info = nullptr, *bad = nullptr;
   int rc = LMFS_OK;

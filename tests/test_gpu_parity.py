@@ -337,3 +337,23 @@ def test_contacts_cell_grid_match_brute_force(L, case):
     np.fill_diagonal(gap, np.inf)
     n_near = int((gap < g_near).sum()) + len(radii)
     assert int(s.stats(L.MOBILITY)["near_entries"]) == n_near
+
+
+def test_resolve_after_invalidate_is_identical(L):
+    """Invalidate and solve again on the same handle, with device allocations
+    made in between so that freed addresses are not handed back: the GMRES
+    graphs captured on the first solve must still read the rebuilt one-body
+    factors and pair blocks, so the second result equals the first bitwise."""
+    pk = w.packing_p100()
+    ft = w.forces_torques(pk.P, 5)
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
+    first, info1 = s.solve(L.MOBILITY, ft)
+    assert info1["converged"]
+    hold = [torch.empty(1 << 20, dtype=torch.float64, device="cuda") for _ in range(4)]
+    for _ in range(2):
+        s.invalidate()
+        again, info2 = s.solve(L.MOBILITY, ft)
+        assert info2["iters"] == info1["iters"]
+        assert np.array_equal(again, first)
+    del hold
+    s.close()
