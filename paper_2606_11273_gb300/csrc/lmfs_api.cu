@@ -20,6 +20,52 @@ namespace lmfs {
 
 static thread_local std::string g_last_error;
 
+thread_local cudaStream_t g_alloc_stream = nullptr;
+thread_local bool g_alloc_scoped = false;
+
+cudaMemPool_t device_pool(int device) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  if (device < 0) return nullptr;
+  if ((int)pools.size() <= device) pools.resize(device + 1, nullptr);
+  if (!pools[device]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    unsigned long long keep = ~0ull;              // keep freed blocks for reuse
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[device] = pool;
+  }
+  return pools[device];
+}
+
+int dalloc_bytes(void** p, size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool = device_pool(dev);
+  cudaError_t e;
+  if (!pool) {
+    e = cudaMalloc(p, bytes);
+  } else if (g_alloc_scoped) {
+    e = cudaMallocFromPoolAsync(p, bytes, pool, g_alloc_stream);
+  } else {
+    e = cudaMallocFromPoolAsync(p, bytes, pool, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  }
+  if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); return LMFS_ERR_NOMEM; }
+  return LMFS_OK;
+}
+
+void dfree_bytes(void* p) {
+  if (!p) return;
+  if (g_alloc_scoped) cudaFreeAsync(p, g_alloc_stream);
+  else cudaFree(p);
+}
+
 void set_last_error(const std::string& s) { g_last_error = s; }
 
 bool cuda_failed(cudaError_t e, const char* what) {
@@ -96,6 +142,7 @@ static int create_ctx(Ctx& c, const double* centres, const double* radii, int P,
     LMFS_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
     c.own_stream = true;
   }
+  AllocScope as(c.stream);
   c.Rc = p.Rc > 0 ? p.Rc : 1.0 - std::log(1e12) / p.Nc;
   c.Rf = 1.0 - std::log(1e12) / p.Nfp;
   c.centres_h.assign(centres, centres + 2 * (size_t)P);
@@ -176,6 +223,7 @@ static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev,
 int solve_begin(lmfs_handle h, int problem, const double* in, double* beta) {
   if (!h || !in || !beta || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
+  AllocScope as(c.stream);
   LMFS_CUDA(cudaSetDevice(c.device));
   for (int i = 0; i < 3 * c.d.P; ++i)
     if (!std::isfinite(in[i])) { set_last_error("non-finite input"); return LMFS_ERR_INVALID; }
@@ -191,6 +239,7 @@ int solve_begin(lmfs_handle h, int problem, const double* in, double* beta) {
 
 int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info) {
   Ctx& c = h->c;
+  AllocScope as(c.stream);
   LMFS_CUDA(cudaSetDevice(c.device));
   const long long n = 2LL * c.d.P * c.d.Mc;
   if (iters > 0) LMFS_TRY(gmres_finish(c, iters, c.xsol));
@@ -249,7 +298,10 @@ int lmfs_destroy(lmfs_handle h) {
   if (!h) return LMFS_ERR_INVALID;
   cudaSetDevice(h->c.device);
   cudaStreamSynchronize(h->c.stream);
-  free_ctx(h->c);
+  {
+    AllocScope as(h->c.stream);
+    free_ctx(h->c);
+  }
   delete h;
   return LMFS_OK;
 }
@@ -269,6 +321,7 @@ int lmfs_get_pairs(lmfs_handle h, int* pairs) {
 int lmfs_precompute_pairs(lmfs_handle h, int problem) {
   if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   LMFS_CUDA(cudaSetDevice(h->c.device));
+  AllocScope as(h->c.stream);
   LMFS_TRY(ensure_precompute(h->c, problem));
   LMFS_CUDA(cudaStreamSynchronize(h->c.stream));
   return LMFS_OK;
@@ -287,6 +340,7 @@ static void transpose_blocks(const double* in, double* out, int C, size_t n) {
 int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E) {
   if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
+  AllocScope as(c.stream);
   if (!c.prob[problem].ready) return LMFS_ERR_STATE;
   const size_t n4 = 4 * (size_t)c.d.Nc;
   if (c.C == 0) return LMFS_OK;
@@ -305,6 +359,7 @@ int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E) {
 int lmfs_set_pair_blocks(lmfs_handle h, int problem, const double* A, const double* E) {
   if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) || (h->c.C && (!A || !E))) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
+  AllocScope as(c.stream);
   PairBlocks& pb = c.prob[problem];
   if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
   const size_t n4 = 4 * (size_t)c.d.Nc;
@@ -326,6 +381,7 @@ int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double*
   if (!h || !Ut || !sigma || !V || !rank || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY))
     return LMFS_ERR_INVALID;
   Ctx& c = h->c;
+  AllocScope as(c.stream);
   PairBlocks& pb = c.prob[problem];
   if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
   const int ns = 2 * c.d.Nc, nn = 2 * c.d.Mc, nc = pb.ob.nclass;
@@ -369,6 +425,7 @@ int lmfs_matvec(lmfs_handle h, int problem, const double* mu_dev, double* u_dev,
   if (!h || !mu_dev || !u_dev || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) ||
       (precision != LMFS_FP64 && precision != LMFS_MIXED && precision != LMFS_MIXED_DIRECT))
     return LMFS_ERR_INVALID;
+  AllocScope as(h->c.stream);
   return matvec_device(h->c, problem, mu_dev, u_dev, precision);
 }
 
@@ -376,18 +433,21 @@ int lmfs_rhs(lmfs_handle h, int problem, const double* in_dev, double* b_dev, in
   if (!h || !in_dev || !b_dev || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) ||
       (precision != LMFS_FP64 && precision != LMFS_MIXED && precision != LMFS_MIXED_DIRECT))
     return LMFS_ERR_INVALID;
+  AllocScope as(h->c.stream);
   return rhs_device(h->c, problem, in_dev, b_dev, precision);
 }
 
 int lmfs_solve_device(lmfs_handle h, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
   if (!h || !in_dev || !out_dev) return LMFS_ERR_INVALID;
   LMFS_CUDA(cudaSetDevice(h->c.device));
+  AllocScope as(h->c.stream);
   return solve_dev(h->c, problem, in_dev, out_dev, info);
 }
 
 int lmfs_solve(lmfs_handle h, int problem, const double* in, double* out, lmfs_solve_info* info) {
   if (!h || !in || !out) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
+  AllocScope as(c.stream);
   LMFS_CUDA(cudaSetDevice(c.device));
   for (int i = 0; i < 3 * c.d.P; ++i)
     if (!std::isfinite(in[i])) { set_last_error("non-finite input"); return LMFS_ERR_INVALID; }
@@ -407,6 +467,7 @@ int lmfs_solve(lmfs_handle h, int problem, const double* in, double* out, lmfs_s
 int lmfs_invalidate(lmfs_handle h) {
   if (!h) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
+  AllocScope as(c.stream);
   LMFS_CUDA(cudaSetDevice(c.device));
   // re-run contact detection on the device; the geometry is unchanged, so the
   // pair lists (and every allocation sized from them) stay valid

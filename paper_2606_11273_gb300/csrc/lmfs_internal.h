@@ -281,15 +281,35 @@ int gmres_step_post(Ctx& c, int problem, int precision);
 int gmres_finish(Ctx& c, int iters, double* x);
 
 // ---- memory ---------------------------------------------------------------
+// Device memory of the library comes from one stream-ordered pool per device
+// (cudaMemPoolCreate; freed blocks stay in the pool for reuse), allocated and
+// freed on the stream of the handle that an API call works for: repeated
+// solves, and handles created one after another, reuse memory without the
+// device-wide synchronisation of cudaMalloc / cudaFree.  AllocScope names that
+// stream for the calls made on this thread while it lives.  Without a scope
+// an allocation is made on the legacy stream and waited for, and a free is the
+// synchronous cudaFree (legal for pool memory), so every path stays ordered.
+cudaMemPool_t device_pool(int device);
+extern thread_local cudaStream_t g_alloc_stream;
+extern thread_local bool g_alloc_scoped;
+struct AllocScope {
+  cudaStream_t prev_stream;
+  bool prev_scoped;
+  explicit AllocScope(cudaStream_t s) : prev_stream(g_alloc_stream), prev_scoped(g_alloc_scoped) {
+    g_alloc_stream = s;
+    g_alloc_scoped = true;
+  }
+  ~AllocScope() { g_alloc_stream = prev_stream; g_alloc_scoped = prev_scoped; }
+};
+int dalloc_bytes(void** p, size_t bytes);
+void dfree_bytes(void* p);
 template <class T>
 int dalloc(T** p, size_t count) {
   if (count == 0) { *p = nullptr; return LMFS_OK; }
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); return LMFS_ERR_NOMEM; }
-  return LMFS_OK;
+  return dalloc_bytes((void**)p, count * sizeof(T));
 }
 template <class T>
-void dfree(T*& p) { if (p) cudaFree((void*)p); p = nullptr; }
+void dfree(T*& p) { if (p) dfree_bytes((void*)p); p = nullptr; }
 
 int check_launch(const char* what);
 void note_launches(unsigned long long n);   // launches not followed by check_launch
