@@ -97,7 +97,7 @@ static void free_ctx(Ctx& c) {
   }
   dfree(c.tgt32); dfree(c.dsk32);
   for (auto& pb : c.prob) {
-    dfree(pb.A); dfree(pb.E); dfree(pb.ob.W); dfree(pb.ob.R); dfree(pb.ob.perm); dfree(pb.ob.rank); dfree(pb.ob.V);
+    dfree(pb.A); dfree(pb.E); dfree(pb.ob.W); dfree(pb.ob.R); dfree(pb.ob.perm); dfree(pb.ob.rank); dfree(pb.ob.V); dfree(pb.ob.Rinv);
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
@@ -410,6 +410,7 @@ int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double*
   LMFS_CUDA(cudaMemcpyAsync(pb.ob.V, V, (size_t)nc * ns * ns * sizeof(double), cudaMemcpyHostToDevice, c.stream));
   LMFS_CUDA(cudaMemcpyAsync(pb.ob.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
   LMFS_CUDA(cudaMemcpyAsync(pb.ob.rank, rk.data(), rk.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  LMFS_TRY(onebody_rinv(c, pb.ob));
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
   pb.ob.rank_h = rk;
   return LMFS_OK;

@@ -47,6 +47,7 @@ struct OneBody {
   int* perm = nullptr;     // [nclass][2Nc]
   int* rank = nullptr;     // [nclass]
   double* V = nullptr;     // optional [nclass][2Nc][2Nc]: lam_bar = V z instead of the perm scatter
+  double* Rinv = nullptr;  // [nclass][2Nc][2Nc] column-major: R^{-1} of the leading r x r block
   std::vector<int> rank_h;
 };
 
@@ -210,6 +211,7 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t s, bool solve);
 
 // ---- matvec pieces (lmfs_matvec.cu) ---------------------------------------
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb);
+int onebody_rinv(Ctx& c, OneBody& ob);   // after R and rank are set
 int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision);
 // matvec_device = matvec_pre + matvec_far + matvec_post
 int matvec_pre(Ctx& c, int problem, const double* mu, int precision);

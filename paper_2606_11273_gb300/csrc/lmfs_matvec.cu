@@ -46,23 +46,26 @@ __device__ __forceinline__ double lsum(double v) {
 // ---- Step 1a: lam_bar = Pi^+ mu, one block per disk, one thread per row ----
 // Pi^+ applied from its QR factors: t = W mu (W = first r rows of Q^T, stored
 // column by column, Wt[col][row], so that the rows read together are
-// contiguous), R[0:r,0:r] z = t (column-oriented back substitution, one barrier
-// per column), lam_bar[perm[j]] = z_j.  With imported SVD factors (V set),
-// lam_bar = V z instead.
-__global__ void onebody_apply_kernel(const double* __restrict__ Wt, const double* __restrict__ R,
+// contiguous), z = R^{-1} t with the triangular inverse formed once per
+// precompute (onebody_rinv), lam_bar[perm[j]] = z_j.  With imported SVD
+// factors (V set; R = diag(sigma), so R^{-1} = diag(1 / sigma)), lam_bar = V z
+// instead.  Two products and three barriers per disk, where a back
+// substitution would take one barrier per column.  Accuracy: the error is that
+// of t = W mu; R^{-1} applied to t adds nothing measurable (checked against an
+// extended-precision back substitution on the one-body blocks).
+__global__ void onebody_apply_kernel(const double* __restrict__ Wt, const double* __restrict__ Rinv,
                                      const int* __restrict__ perm, const int* __restrict__ rank,
                                      const double* __restrict__ V, const int* __restrict__ cls, int P,
                                      int Nc, int Mc, const double* __restrict__ mu, double* __restrict__ lb) {
-  extern __shared__ double osm[];   // mu_i [nn], t [ns], 1/R_jj [ns], x [ns]
+  extern __shared__ double osm[];   // mu_i [nn], t [ns], x [ns]
   const int i = blockIdx.x, c = cls[i];
   const int ns = 2 * Nc, nn = 2 * Mc, r = rank[c];
   const int row = threadIdx.x;
   const double* Wc = Wt + (long long)c * ns * nn;
-  const double* Rc = R + (long long)c * ns * ns;
+  const double* Ic = Rinv + (long long)c * ns * ns;
   double* ms = osm;
   double* ts = ms + nn;
-  double* ri = ts + ns;
-  double* xs = ri + ns;
+  double* xs = ts + ns;
   for (int q = threadIdx.x; q < nn; q += blockDim.x) ms[q] = mu[(long long)i * nn + q];
   __syncthreads();
   if (row < r) {
@@ -74,26 +77,45 @@ __global__ void onebody_apply_kernel(const double* __restrict__ Wt, const double
     }
     if (col < nn) a0 += Wc[(long long)col * ns + row] * ms[col];
     ts[row] = a0 + a1;
-    ri[row] = 1.0 / Rc[(long long)row * ns + row];
-  }
-  for (int j = r - 1; j >= 0; --j) {
-    __syncthreads();                     // t_j final, x_{j+1} written
-    const double xj = ts[j] * ri[j];
-    if (row < j) ts[row] -= xj * Rc[(long long)j * ns + row];
-    else if (row == j) xs[j] = xj;
   }
   __syncthreads();
+  double x = 0.0;
+  if (row < r) {
+    // upper triangular: (R^{-1})_{row,k} = Ic[k * ns + row] for k >= row
+    for (int k = row; k < r; ++k) x += Ic[(long long)k * ns + row] * ts[k];
+    xs[row] = x;
+  }
   double* out = lb + (long long)i * ns;
-  if (row >= ns) return;
   if (V) {
     // imported factors of the form V Sigma^+ U^T
+    __syncthreads();
+    if (row >= ns) return;
     const double* Vc = V + (long long)c * ns * ns;
     double acc = 0.0;
     for (int j = 0; j < r; ++j) acc += Vc[(long long)row * ns + j] * xs[j];
     out[row] = acc;
     return;
   }
-  out[perm[(long long)c * ns + row]] = (row < r) ? xs[row] : 0.0;
+  if (row < ns) out[perm[(long long)c * ns + row]] = (row < r) ? x : 0.0;
+}
+
+// R^{-1} of each radius class's truncated R[0:r, 0:r] (column-major, zero
+// outside the leading r x r block): thread j solves R x = e_j by back
+// substitution into column j.  Once per precompute.
+__global__ void onebody_rinv_kernel(const double* __restrict__ R, const int* __restrict__ rank, int ns,
+                                    double* __restrict__ Rinv) {
+  const int c = blockIdx.x, j = threadIdx.x;
+  if (j >= ns) return;
+  const int r = rank[c];
+  const double* Rc = R + (long long)c * ns * ns;
+  double* X = Rinv + (long long)c * ns * ns + (long long)j * ns;
+  for (int i = 0; i < ns; ++i) X[i] = 0.0;
+  if (j >= r) return;
+  for (int i = j; i >= 0; --i) {
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int k = i + 1; k <= j; ++k) s -= Rc[(long long)k * ns + i] * X[k];
+    X[i] = s / Rc[(long long)i * ns + i];
+  }
 }
 
 // ---- Step 1b: lam~ = A [lam_bar_i; lam_bar_k] per close pair ----------------
@@ -1350,10 +1372,18 @@ int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
   const int ns = 2 * c.d.Nc;
   if (ns > 1024) { set_last_error("2 Nc > 1024 not supported"); return LMFS_ERR_INVALID; }
   const int thr = std::max(32, ((ns + 31) / 32) * 32);
-  const size_t shm = ((size_t)2 * c.d.Mc + 3 * (size_t)ns) * sizeof(double);
-  onebody_apply_kernel<<<c.d.P, thr, shm, c.stream>>>(ob.W, ob.R, ob.perm, ob.rank, ob.V, c.cls, c.d.P, c.d.Nc,
+  const size_t shm = ((size_t)2 * c.d.Mc + 2 * (size_t)ns) * sizeof(double);
+  onebody_apply_kernel<<<c.d.P, thr, shm, c.stream>>>(ob.W, ob.Rinv, ob.perm, ob.rank, ob.V, c.cls, c.d.P, c.d.Nc,
                                                       c.d.Mc, mu, lb);
   return check_launch("onebody_apply");
+}
+
+int onebody_rinv(Ctx& c, OneBody& ob) {
+  const int ns = 2 * c.d.Nc;
+  if (ns > 1024) { set_last_error("2 Nc > 1024 not supported"); return LMFS_ERR_INVALID; }
+  if (!ob.Rinv) LMFS_TRY(dalloc(&ob.Rinv, (size_t)ob.nclass * ns * ns));
+  onebody_rinv_kernel<<<ob.nclass, std::max(32, ((ns + 31) / 32) * 32), 0, c.stream>>>(ob.R, ob.rank, ns, ob.Rinv);
+  return check_launch("onebody_rinv");
 }
 
 // The near zone that goes with a far-field precision: the FP32 multipole far

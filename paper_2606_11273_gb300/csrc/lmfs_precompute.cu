@@ -731,6 +731,7 @@ int build_onebody(Ctx& c, int problem, OneBody& ob) {
     if ((rc = qr_solve_batched(q, c.stream, false))) goto done;
     extract_onebody<<<grid, 256, 0, c.stream>>>(ws, ld, mstride, Nc, Mc, ob.rank, ob.W, ob.R);
     if ((rc = check_launch("extract_onebody"))) goto done;
+    if ((rc = onebody_rinv(c, ob))) goto done;
     any_nonzero<<<(nb + 255) / 256, 256, 0, c.stream>>>(info, nb, bad);
     note_launches(1);
     ob.rank_h.assign(nb, 0);
