@@ -514,66 +514,71 @@ constexpr int MP_P = 32;
 // which fixes the order needed at each target (adaptive truncation).
 constexpr int MP_NCOEF = 104;   // 3P + 5 = 101, padded to a multiple of 4
 
-// P2M: one warp per disk (moments in FP64).
+// P2M: one block per disk, moments in FP64.  Thread (group, n) accumulates the
+// order-n moments over one third of the ring's sources; the powers come from
+// the ring table, w_j^n = rho^n e^{i n theta_j} = rho^n ring[n j mod Nc] and
+// w_j conj(w_j)^n = rho^(n+1) ring[(1 - n) j mod Nc], so a source costs twelve
+// fused multiply-adds and no cross-lane reduction; the three groups are then
+// added in a fixed order and scaled by the power of rho.
+constexpr int P2M_G = 3;
+
 __global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, int P, int Nc,
                                                   const double* __restrict__ radii, double Rc,
                                                   const double2* __restrict__ ring,
                                                   double2* __restrict__ coef, float2* __restrict__ coef32) {
-  // one block per disk; warp g forms the moments of orders n = g, g + 4, ...
   __shared__ double mom[MP_P + 1][6];     // A_n, B_n, D_n (complex)
   __shared__ double2 cf[MP_NCOEF];
   __shared__ double bnd[MP_P + 1];
   __shared__ double rpw[MP_P + 1];        // rho^n
+  __shared__ double fs[2 * 128];          // the disk's strengths (Nc <= 128)
+  __shared__ double2 rt[128];             // ring table
+  __shared__ double part[P2M_G][MP_P + 1][6];
   const int i = blockIdx.x;
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const double rs = radii[i] * Rc;
-  constexpr int SPL = 4;                  // sources per lane: Nc <= 128
-  double fr[SPL], fi[SPL], wr[SPL], wi[SPL], pr[SPL], pi_[SPL], sr[SPL], si[SPL];
-#pragma unroll
-  for (int q = 0; q < SPL; ++q) {
-    const int j = lane + 32 * q;
-    fr[q] = fi[q] = wr[q] = wi[q] = 0.0;
-    if (j < Nc) {
-      fr[q] = s[(long long)i * 2 * Nc + 2 * j];
-      fi[q] = s[(long long)i * 2 * Nc + 2 * j + 1];
-      const double2 cs = ring[j];
-      wr[q] = rs * cs.x; wi[q] = rs * cs.y;
-    }
-    pr[q] = 1.0; pi_[q] = 0.0;            // p = w^g
-    for (int k = 0; k < g; ++k) {
-      const double a = pr[q] * wr[q] - pi_[q] * wi[q], b = pr[q] * wi[q] + pi_[q] * wr[q];
-      pr[q] = a; pi_[q] = b;
-    }
-    const double w2r = wr[q] * wr[q] - wi[q] * wi[q], w2i = 2.0 * wr[q] * wi[q];
-    sr[q] = w2r * w2r - w2i * w2i; si[q] = 2.0 * w2r * w2i;   // step w^4
+  for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
+    fs[2 * j] = s[(long long)i * 2 * Nc + 2 * j];
+    fs[2 * j + 1] = s[(long long)i * 2 * Nc + 2 * j + 1];
+    rt[j] = ring[j];
   }
-  double rp = 1.0;
-  for (int k = 0; k < g; ++k) rp *= rs;
-  const double rs4 = (rs * rs) * (rs * rs);
-  for (int n = g; n <= MP_P; n += 4) {
-    if (lane == 0) rpw[n] = rp;
-    rp *= rs4;
+  __syncthreads();
+  if (threadIdx.x < P2M_G * (MP_P + 1)) {
+    const int n = threadIdx.x % (MP_P + 1), grp = threadIdx.x / (MP_P + 1);
+    const int j0 = grp * Nc / P2M_G, j1 = (grp + 1) * Nc / P2M_G;
+    const int na = n % Nc, nd = ((1 - n) % Nc + Nc) % Nc;
+    int ia = (int)(((long long)j0 * na) % Nc), id = (int)(((long long)j0 * nd) % Nc);
     double Ar = 0, Ai = 0, Br = 0, Bi = 0, Dr = 0, Di = 0;
+    for (int j = j0; j < j1; ++j) {
+      // A: f w^n;  B: f conj(w)^n;  D: conj(f) w conj(w)^n  (powers of rho applied below)
+      const double fr = fs[2 * j], fi = fs[2 * j + 1];
+      const double2 c = rt[ia], d = rt[id];
+      Ar = fma(fr, c.x, Ar); Ar = fma(-fi, c.y, Ar);
+      Ai = fma(fr, c.y, Ai); Ai = fma(fi, c.x, Ai);
+      Br = fma(fr, c.x, Br); Br = fma(fi, c.y, Br);
+      Bi = fma(fi, c.x, Bi); Bi = fma(-fr, c.y, Bi);
+      Dr = fma(fr, d.x, Dr); Dr = fma(fi, d.y, Dr);
+      Di = fma(fr, d.y, Di); Di = fma(-fi, d.x, Di);
+      ia += na; if (ia >= Nc) ia -= Nc;
+      id += nd; if (id >= Nc) id -= Nc;
+    }
+    double* pp = part[grp][n];
+    pp[0] = Ar; pp[1] = Ai; pp[2] = Br; pp[3] = Bi; pp[4] = Dr; pp[5] = Di;
+  }
+  __syncthreads();
+  if (threadIdx.x <= MP_P) {
+    const int n = threadIdx.x;
+    double rp = 1.0;
+    for (int k = 0; k < n; ++k) rp *= rs;
+    rpw[n] = rp;
+    double v[6];
 #pragma unroll
-    for (int q = 0; q < SPL; ++q) {
-      // A: f w^n;  B: f conj(w^n);  D: conj(f) w conj(w^n)
-      Ar += fr[q] * pr[q] - fi[q] * pi_[q];
-      Ai += fr[q] * pi_[q] + fi[q] * pr[q];
-      Br += fr[q] * pr[q] + fi[q] * pi_[q];
-      Bi += fi[q] * pr[q] - fr[q] * pi_[q];
-      const double tr = wr[q] * pr[q] + wi[q] * pi_[q], ti = wi[q] * pr[q] - wr[q] * pi_[q];
-      Dr += fr[q] * tr + fi[q] * ti;
-      Di += fr[q] * ti - fi[q] * tr;
+    for (int q = 0; q < 6; ++q) {
+      double t = part[0][n][q];
+      for (int grp = 1; grp < P2M_G; ++grp) t += part[grp][n][q];
+      v[q] = t;
     }
-    Ar = lsum(Ar); Ai = lsum(Ai); Br = lsum(Br); Bi = lsum(Bi); Dr = lsum(Dr); Di = lsum(Di);
-    if (lane == 0) {
-      mom[n][0] = Ar; mom[n][1] = Ai; mom[n][2] = Br; mom[n][3] = Bi; mom[n][4] = Dr; mom[n][5] = Di;
-    }
-#pragma unroll
-    for (int q = 0; q < SPL; ++q) {
-      const double a = pr[q] * sr[q] - pi_[q] * si[q], b = pr[q] * si[q] + pi_[q] * sr[q];
-      pr[q] = a; pi_[q] = b;
-    }
+    mom[n][0] = rp * v[0]; mom[n][1] = rp * v[1];
+    mom[n][2] = rp * v[2]; mom[n][3] = rp * v[3];
+    mom[n][4] = (rp * rs) * v[4]; mom[n][5] = (rp * rs) * v[5];
   }
   __syncthreads();
   // coefficients a_n = A_n / 2n, g_n = B_n / 2n - D_{n-1} / 2, h_n = conj(A_n)
@@ -909,7 +914,7 @@ __global__ void near_kernel(int mode, const double* __restrict__ centres, const 
                             const double* __restrict__ sig, const double* __restrict__ lam,
                             const double* __restrict__ lb, const double* __restrict__ tilde, int mobility,
                             double* __restrict__ part) {
-  extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y, then [G][Mc][2] partial sums
+  extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y, then [G][Mt][2] partial sums
   __shared__ double red[3][32];
   __shared__ double ltab[3 * LOG_TAB];
   const int e = blockIdx.x;
@@ -918,8 +923,10 @@ __global__ void near_kernel(int mode, const double* __restrict__ centres, const 
   if (mode == 0 && kind == 2) return;     // whole block: the self term cancels
   log_table_init(ltab);
   const int ns = 2 * Nc, n4 = 4 * Nc;
-  const int g = threadIdx.x / Mc, m = threadIdx.x % Mc;
-  const bool act = g < G;
+  // block y of the entry takes target nodes [y Mt, (y + 1) Mt)
+  const int Mt = (Mc + gridDim.y - 1) / gridDim.y;
+  const int g = threadIdx.x / Mt, ml = threadIdx.x % Mt, m = blockIdx.y * Mt + ml;
+  const bool act = g < G && m < Mc;
   const int j0 = g * Nc / G, j1 = (g + 1) * Nc / G;
   double xx = 0, xy = 0;
   if (act) {
@@ -991,11 +998,11 @@ __global__ void near_kernel(int mode, const double* __restrict__ centres, const 
   }
   // combine the G source groups in order
   double* gp = nsm + 4 * Nc;
-  if (act) { gp[2 * (g * Mc + m)] = ux; gp[2 * (g * Mc + m) + 1] = uy; }
+  if (act) { gp[2 * (g * Mt + ml)] = ux; gp[2 * (g * Mt + ml) + 1] = uy; }
   __syncthreads();
-  if (g == 0) {
+  if (g == 0 && m < Mc) {
     ux = 0; uy = 0;
-    for (int q = 0; q < G; ++q) { ux += gp[2 * (q * Mc + m)]; uy += gp[2 * (q * Mc + m) + 1]; }
+    for (int q = 0; q < G; ++q) { ux += gp[2 * (q * Mt + ml)]; uy += gp[2 * (q * Mt + ml) + 1]; }
     part[((long long)e * Mc + m) * 2] = ux;
     part[((long long)e * Mc + m) * 2 + 1] = uy;
   }
@@ -1519,14 +1526,18 @@ void multi_far_free(MultiFar& buf) {
 int near_field(Ctx& c, int mode, const double* strength, const double* mu, const double* ufar, double* u,
                int problem, int precision) {
   const NearSet& z = zone(c, precision);
-  // target nodes x source groups, about nine warps per block
+  // target nodes x source groups, about nine warps per block; with few
+  // entries, each entry's targets are split over Y blocks (and its sources
+  // over Y times as many groups) so that the launch covers the SMs
   const int Mc = c.d.Mc;
-  const int G = std::max(1, std::min({4, 1024 / Mc, c.d.Nc}));
-  const int threads = ((G * Mc + 31) / 32) * 32;
-  const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mc * 2) * sizeof(double);
   const int ne = (int)z.h.size();
+  const int Y = std::max(1, std::min(4, (2 * c.sms + std::max(ne, 1) - 1) / std::max(ne, 1)));
+  const int Mt = (Mc + Y - 1) / Y;
+  const int G = std::max(1, std::min({4 * Y, 1024 / Mt, c.d.Nc}));
+  const int threads = ((G * Mt + 31) / 32) * 32;
+  const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mt * 2) * sizeof(double);
   if (ne > 0) {
-    near_kernel<<<ne, threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, c.nodes, z.tgt,
+    near_kernel<<<dim3(ne, Y), threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, c.nodes, z.tgt,
                                                 z.ent, strength, c.lam, c.lb, c.tilde,
                                                 problem == LMFS_MOBILITY, z.part);
     LMFS_TRY(check_launch("near"));
