@@ -48,6 +48,7 @@ struct OneBody {
   int* rank = nullptr;     // [nclass]
   double* V = nullptr;     // optional [nclass][2Nc][2Nc]: lam_bar = V z instead of the perm scatter
   double* Rinv = nullptr;  // [nclass][2Nc][2Nc] column-major: R^{-1} of the leading r x r block
+  int* bad = nullptr;      // set if a factorization met a non-finite value
   std::vector<int> rank_h;
 };
 
@@ -177,7 +178,9 @@ int detect_contacts(Ctx& c);          // fills pairs_h, csr, near lists
 int upload_geometry(Ctx& c);
 
 // ---- precompute (lmfs_precompute.cu) -------------------------------------
-int build_onebody(Ctx& c, int problem, OneBody& ob);
+int build_onebody(Ctx& c, int problem, OneBody& ob);   // enqueue + finish on the handle's stream
+int onebody_enqueue(Ctx& c, int problem, OneBody& ob, cudaStream_t st);
+int onebody_finish(Ctx& c, OneBody& ob, cudaStream_t st);
 int build_pair_blocks(Ctx& c, int problem);
 
 // ---- batched QR (lmfs_qr.cu) ---------------------------------------------
@@ -211,7 +214,7 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t s, bool solve);
 
 // ---- matvec pieces (lmfs_matvec.cu) ---------------------------------------
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb);
-int onebody_rinv(Ctx& c, OneBody& ob);   // after R and rank are set
+int onebody_rinv(Ctx& c, OneBody& ob, cudaStream_t st);   // after R and rank are set
 int matvec_device(Ctx& c, int problem, const double* mu, double* u, int precision);
 // matvec_device = matvec_pre + matvec_far + matvec_post
 int matvec_pre(Ctx& c, int problem, const double* mu, int precision);

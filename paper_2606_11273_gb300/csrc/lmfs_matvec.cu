@@ -100,22 +100,30 @@ __global__ void onebody_apply_kernel(const double* __restrict__ Wt, const double
 }
 
 // R^{-1} of each radius class's truncated R[0:r, 0:r] (column-major, zero
-// outside the leading r x r block): thread j solves R x = e_j by back
-// substitution into column j.  Once per precompute.
+// outside the leading r x r block): block (j, class) solves R x = e_j by a
+// column-oriented back substitution, thread i holding row i of the running
+// right-hand side.  Once per precompute.
 __global__ void onebody_rinv_kernel(const double* __restrict__ R, const int* __restrict__ rank, int ns,
                                     double* __restrict__ Rinv) {
-  const int c = blockIdx.x, j = threadIdx.x;
-  if (j >= ns) return;
+  __shared__ double xk;
+  const int j = blockIdx.x, c = blockIdx.y, i = threadIdx.x;
   const int r = rank[c];
   const double* Rc = R + (long long)c * ns * ns;
   double* X = Rinv + (long long)c * ns * ns + (long long)j * ns;
-  for (int i = 0; i < ns; ++i) X[i] = 0.0;
-  if (j >= r) return;
-  for (int i = j; i >= 0; --i) {
-    double s = (i == j) ? 1.0 : 0.0;
-    for (int k = i + 1; k <= j; ++k) s -= Rc[(long long)k * ns + i] * X[k];
-    X[i] = s / Rc[(long long)i * ns + i];
+  if (j >= r) {
+    if (i < ns) X[i] = 0.0;
+    return;
   }
+  double si = (i == j) ? 1.0 : 0.0;
+  for (int k = j; k >= 0; --k) {
+    if (i == k) xk = si / Rc[(long long)k * ns + k];
+    __syncthreads();
+    const double x = xk;
+    if (i == k) X[k] = x;
+    else if (i < k) si -= Rc[(long long)k * ns + i] * x;
+    __syncthreads();
+  }
+  if (i > j && i < ns) X[i] = 0.0;
 }
 
 // ---- Step 1b: lam~ = A [lam_bar_i; lam_bar_k] per close pair ----------------
@@ -1385,11 +1393,11 @@ int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
   return check_launch("onebody_apply");
 }
 
-int onebody_rinv(Ctx& c, OneBody& ob) {
+int onebody_rinv(Ctx& c, OneBody& ob, cudaStream_t st) {
   const int ns = 2 * c.d.Nc;
   if (ns > 1024) { set_last_error("2 Nc > 1024 not supported"); return LMFS_ERR_INVALID; }
   if (!ob.Rinv) LMFS_TRY(dalloc(&ob.Rinv, (size_t)ob.nclass * ns * ns));
-  onebody_rinv_kernel<<<ob.nclass, std::max(32, ((ns + 31) / 32) * 32), 0, c.stream>>>(ob.R, ob.rank, ns, ob.Rinv);
+  onebody_rinv_kernel<<<dim3(ns, ob.nclass), std::max(32, ((ns + 31) / 32) * 32), 0, st>>>(ob.R, ob.rank, ns, ob.Rinv);
   return check_launch("onebody_rinv");
 }
 

@@ -689,7 +689,12 @@ __global__ void any_nonzero(const int* v, int n, int* out) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-int build_onebody(Ctx& c, int problem, OneBody& ob) {
+// The one-body factorization enqueued on `st` without a host wait (its
+// scratch is freed in stream order on st); onebody_finish drains st and checks
+// the result.  The pair precompute does not depend on it, so the handle runs
+// it on its side stream meanwhile.
+int onebody_enqueue(Ctx& c, int problem, OneBody& ob, cudaStream_t st) {
+  AllocScope as(st);
   const int Nc = c.d.Nc, Mc = c.d.Mc;
   const int nb = (int)c.cls_r_h.size();
   const int m = 2 * Mc, n = 2 * Nc, k = 2 * Mc;
@@ -706,43 +711,56 @@ int build_onebody(Ctx& c, int problem, OneBody& ob) {
     LMFS_TRY(dalloc(&ob.R, (size_t)nb * n * n));
     LMFS_TRY(dalloc(&ob.perm, (size_t)nb * n));
     LMFS_TRY(dalloc(&ob.rank, (size_t)nb));
+    LMFS_TRY(dalloc(&ob.bad, 1));
   }
   double *ws = nullptr, *tau = nullptr, *vn = nullptr;
-  int *dm = nullptr, *dn = nullptr, *info = nullptr, *bad = nullptr;
+  int *dm = nullptr, *dn = nullptr, *info = nullptr;
   int rc = LMFS_OK;
   std::vector<int> hm(nb, m), hn(nb, n);
-  int hbad = 0;
   if ((rc = dalloc(&ws, (size_t)nb * mstride)) || (rc = dalloc(&tau, (size_t)nb * n)) ||
       (rc = dalloc(&vn, (size_t)nb * 2 * n)) || (rc = dalloc(&dm, nb)) || (rc = dalloc(&dn, nb)) ||
-      (rc = dalloc(&info, nb)) || (rc = dalloc(&bad, 1)))
+      (rc = dalloc(&info, nb)))
     goto done;
-  if (cuda_failed(cudaMemcpyAsync(dm, hm.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
-      cuda_failed(cudaMemcpyAsync(dn, hn.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
-      cuda_failed(cudaMemsetAsync(bad, 0, sizeof(int), c.stream), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
+  if (cuda_failed(cudaMemcpyAsync(dm, hm.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st), "h2d") ||
+      cuda_failed(cudaMemcpyAsync(dn, hn.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st), "h2d") ||
+      cuda_failed(cudaMemsetAsync(ob.bad, 0, sizeof(int), st), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
   {
     dim3 grid(2, nb);
-    fill_onebody<<<grid, 128, 0, c.stream>>>(ws, ld, mstride, c.cls_r, Nc, Mc, c.Rc, 1.0 / (4 * LMFS_PI * c.prm.mu),
-                                             problem == LMFS_MOBILITY);
+    fill_onebody<<<grid, 128, 0, st>>>(ws, ld, mstride, c.cls_r, Nc, Mc, c.Rc, 1.0 / (4 * LMFS_PI * c.prm.mu),
+                                       problem == LMFS_MOBILITY);
     if ((rc = check_launch("fill_onebody"))) goto done;
     QRBatch q{};
     q.A = ws; q.mstride = mstride; q.m = dm; q.n = dn; q.k = k; q.ld = ld; q.eps = c.prm.eps_trunc;
     q.X = nullptr; q.xld = 0; q.xstride = 0; q.rank = ob.rank; q.perm = ob.perm; q.permstride = n;
     q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = n;
-    if ((rc = qr_solve_batched(q, c.stream, false))) goto done;
-    extract_onebody<<<grid, 256, 0, c.stream>>>(ws, ld, mstride, Nc, Mc, ob.rank, ob.W, ob.R);
+    if ((rc = qr_solve_batched(q, st, false))) goto done;
+    extract_onebody<<<grid, 256, 0, st>>>(ws, ld, mstride, Nc, Mc, ob.rank, ob.W, ob.R);
     if ((rc = check_launch("extract_onebody"))) goto done;
-    if ((rc = onebody_rinv(c, ob))) goto done;
-    any_nonzero<<<(nb + 255) / 256, 256, 0, c.stream>>>(info, nb, bad);
+    if ((rc = onebody_rinv(c, ob, st))) goto done;
+    any_nonzero<<<(nb + 255) / 256, 256, 0, st>>>(info, nb, ob.bad);
     note_launches(1);
-    ob.rank_h.assign(nb, 0);
-    if (cuda_failed(cudaMemcpyAsync(ob.rank_h.data(), ob.rank, nb * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
-        cuda_failed(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
-        cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
-    if (hbad) { set_last_error("non-finite value in a one-body factorization"); rc = LMFS_ERR_NUMERICAL; }
   }
 done:
-  dfree(ws); dfree(tau); dfree(vn); dfree(dm); dfree(dn); dfree(info); dfree(bad);
+  dfree(ws); dfree(tau); dfree(vn); dfree(dm); dfree(dn); dfree(info);
   return rc;
+}
+
+int onebody_finish(Ctx& c, OneBody& ob, cudaStream_t st) {
+  (void)c;
+  LMFS_CUDA(cudaStreamSynchronize(st));
+  const int nb = ob.nclass;
+  int hbad = 0;
+  ob.rank_h.assign(nb, 0);
+  LMFS_CUDA(cudaMemcpy(ob.rank_h.data(), ob.rank, nb * sizeof(int), cudaMemcpyDeviceToHost));
+  LMFS_CUDA(cudaMemcpy(&hbad, ob.bad, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hbad) { set_last_error("non-finite value in a one-body factorization"); return LMFS_ERR_NUMERICAL; }
+  return LMFS_OK;
+}
+
+int build_onebody(Ctx& c, int problem, OneBody& ob) {
+  const int rc = onebody_enqueue(c, problem, ob, c.stream);
+  const int rc1 = onebody_finish(c, ob, c.stream);
+  return rc != LMFS_OK ? rc : rc1;
 }
 
 int build_pair_blocks(Ctx& c, int problem) {
