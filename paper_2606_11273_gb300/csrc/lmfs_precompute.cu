@@ -92,6 +92,7 @@ __global__ void extract_onebody(const double* A, int ld, long long mstride, int 
 // ---- pair geometry ----------------------------------------------------
 struct PairGeo {
   const double* centres; const double* radii; const int* pairs;  // global
+  const double2* ring;     // [Nc] (cos, sin)(2 pi j / Nc): the coarse source ring
   int first;               // first pair of the chunk
   double Rf, gamma, rmob, rho;
   int Nfp, Nell, neq, nmob, Mp;
@@ -220,9 +221,10 @@ __global__ void fill_FQ(PairDims pd, PairGeo g, const double* Yf, const double* 
       const int j = (s - nY) % Nc, disk = (s - nY) / Nc;  // disk 0: lambda_bar^1 columns
       col = 2 * nY + 2 * (disk * Nc + j);
       const int dd = disk == 0 ? i : k;
-      const double rs = g.radii[dd] * pd.Rc, ph = 2.0 * LMFS_PI * j / Nc;
-      yx = g.centres[2 * dd] + rs * cos(ph);
-      yy = g.centres[2 * dd + 1] + rs * sin(ph);
+      const double rs = g.radii[dd] * pd.Rc;
+      const double2 cs = g.ring[j];
+      yx = g.centres[2 * dd] + rs * cs.x;
+      yy = g.centres[2 * dd + 1] + rs * cs.y;
       // disk-1 columns live in side-2 rows (Q12), disk-2 columns in side-1 rows (Q21)
       zero = (disk == 0) ? (n < nX) : (n >= nX);
     }
@@ -288,13 +290,15 @@ __global__ void project_FQ_mobility(PairDims pd, PairGeo g, const double* Yf, co
       const int c0 = 2 * nY + 2 * disk * Nc;
       double t0 = 0, t1 = 0, t2 = 0;
       for (int j = 0; j < Nc; ++j) {
-        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        const double2 cs = g.ring[j];
+        const double ex = rs * cs.x, ey = rs * cs.y;
         const double v0 = M[(long long)(c0 + 2 * j) * ld + row], v1 = M[(long long)(c0 + 2 * j + 1) * ld + row];
         t0 += v0; t1 += v1; t2 += -ey * v0 + ex * v1;
       }
       t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
       for (int j = 0; j < Nc; ++j) {
-        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        const double2 cs = g.ring[j];
+        const double ex = rs * cs.x, ey = rs * cs.y;
         M[(long long)(c0 + 2 * j) * ld + row] -= t0 + t2 * (-ey);
         M[(long long)(c0 + 2 * j + 1) * ld + row] -= t1 + t2 * ex;
       }
@@ -351,8 +355,9 @@ __global__ void fill_FQ_sym(PairDims pd, PairGeo g, const double* Yf, const doub
       const int j = s - nY1;
       col = 2 * nY1 + 2 * j;                 // right-hand side right after this matrix's own columns
       const int jj = (j + Nc / 2) % Nc;
-      const double rs = g.radii[k] * pd.Rc, ph = 2.0 * LMFS_PI * jj / Nc;
-      stokes2(xx - (g.centres[2 * k] + rs * cos(ph)), xy - (g.centres[2 * k + 1] + rs * sin(ph)), pd.cmu,
+      const double rs = g.radii[k] * pd.Rc;
+      const double2 cs = g.ring[jj];
+      stokes2(xx - (g.centres[2 * k] + rs * cs.x), xy - (g.centres[2 * k + 1] + rs * cs.y), pd.cmu,
               &p00, &p01, &p11);
       m00 = p00; m01 = p01; m11 = p11;
     }
@@ -411,14 +416,16 @@ __global__ void project_FQ_mobility_sym(PairDims pd, PairGeo g, const double* Yf
     double r0 = 0, r1 = 0, r2 = 0;
     for (int j = 0; j < Nc; ++j) {
       const int jj = (j + Nc / 2) % Nc;
-      const double ph = 2.0 * LMFS_PI * jj / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+      const double2 cs = g.ring[jj];
+      const double ex = rs * cs.x, ey = rs * cs.y;
       const double v0 = M[(c0 + 2 * j) * ld + row], v1 = M[(c0 + 2 * j + 1) * ld + row];
       r0 += v0; r1 += v1; r2 += -ey * v0 + ex * v1;
     }
     r0 /= Nc; r1 /= Nc; r2 /= (Nc * rs * rs);
     for (int j = 0; j < Nc; ++j) {
       const int jj = (j + Nc / 2) % Nc;
-      const double ph = 2.0 * LMFS_PI * jj / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+      const double2 cs = g.ring[jj];
+      const double ex = rs * cs.x, ey = rs * cs.y;
       M[(c0 + 2 * j) * ld + row] -= r0 + r2 * (-ey);
       M[(c0 + 2 * j + 1) * ld + row] -= r1 + r2 * ex;
     }
@@ -596,8 +603,9 @@ __global__ void fill_DC(PairDims pd, PairGeo g, const double* Yf, const double* 
     if (t < nD) { yx = Y[2 * s]; yy = Y[2 * s + 1]; base = Db; ldd = dld; }
     else {
       const int disk = s / Nc, j = s % Nc, dd = disk ? k : i;
-      const double rs = g.radii[dd] * pd.Rc, ph = 2.0 * LMFS_PI * j / Nc;
-      yx = g.centres[2 * dd] + rs * cos(ph); yy = g.centres[2 * dd + 1] + rs * sin(ph);
+      const double rs = g.radii[dd] * pd.Rc;
+      const double2 cs = g.ring[j];
+      yx = g.centres[2 * dd] + rs * cs.x; yy = g.centres[2 * dd + 1] + rs * cs.y;
       base = Cb; ldd = ld2;
     }
     double s00, s01, s11;
@@ -619,13 +627,15 @@ __global__ void project_C(PairDims pd, PairGeo g, double* W2, int ld2, long long
       const int c0 = 2 * disk * Nc;
       double t0 = 0, t1 = 0, t2 = 0;
       for (int j = 0; j < Nc; ++j) {
-        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        const double2 cs = g.ring[j];
+        const double ex = rs * cs.x, ey = rs * cs.y;
         const double v0 = Cb[(long long)(c0 + 2 * j) * ld2 + row], v1 = Cb[(long long)(c0 + 2 * j + 1) * ld2 + row];
         t0 += v0; t1 += v1; t2 += -ey * v0 + ex * v1;
       }
       t0 /= Nc; t1 /= Nc; t2 /= (Nc * rs * rs);
       for (int j = 0; j < Nc; ++j) {
-        const double ph = 2.0 * LMFS_PI * j / Nc, ex = rs * cos(ph), ey = rs * sin(ph);
+        const double2 cs = g.ring[j];
+        const double ex = rs * cs.x, ey = rs * cs.y;
         Cb[(long long)(c0 + 2 * j) * ld2 + row] -= t0 + t2 * (-ey);
         Cb[(long long)(c0 + 2 * j + 1) * ld2 + row] -= t1 + t2 * ex;
       }
@@ -831,7 +841,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   for (int first = 0; first < C; first += chunk) {
     const int nb = std::min(chunk, C - first);
     PairGeo g;
-    g.centres = c.centres; g.radii = c.radii; g.pairs = c.pairs; g.first = first;
+    g.centres = c.centres; g.radii = c.radii; g.pairs = c.pairs; g.first = first; g.ring = c.ring;
     g.Rf = c.Rf; g.gamma = c.prm.gamma; g.rmob = c.prm.r_mob; g.rho = c.rho;
     g.Nfp = Nfp; g.Nell = Nell; g.neq = neq; g.nmob = nmob; g.Mp = Mp;
     count_enh<<<(2 * nb * 32 + 127) / 128, 128, 0, c.stream>>>(g, nb, nenh);
