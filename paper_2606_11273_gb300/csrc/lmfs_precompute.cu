@@ -9,16 +9,19 @@
 
 #include "lmfs_geom.cuh"
 #include "lmfs_internal.h"
+#include "lmfs_fp64.cuh"
 
 namespace lmfs {
 namespace {
 
-// 2x2 Stokeslet block S(x - y) (eq. (stokeslet2d)), scaled by 1/(4 pi mu).
+// 2x2 Stokeslet block S(x - y) (eq. (stokeslet2d)), scaled by 1/(4 pi mu);
+// the table logarithm and Newton reciprocal of lmfs_fp64.cuh (ltab: the
+// block's log_table_init table).
 __device__ __forceinline__ void stokes2(double dx, double dy, double c, double* s00, double* s01,
-                                        double* s11) {
+                                        double* s11, const double* ltab) {
   const double r2 = dx * dx + dy * dy;
-  const double lg = 0.5 * log(r2);
-  const double ir2 = 1.0 / r2;
+  const double lg = 0.5 * log_pos(r2, ltab);
+  const double ir2 = rcp_pos(r2);
   *s00 = c * (-lg + dx * dx * ir2);
   *s01 = c * (dx * dy * ir2);
   *s11 = c * (-lg + dy * dy * ir2);
@@ -29,6 +32,9 @@ __device__ __forceinline__ void stokes2(double dx, double dy, double c, double* 
 // (mobility, eq. (SL)); rows 2Mc, columns 2Nc + 2Mc, column-major.
 __global__ void fill_onebody(double* A, int ld, long long mstride, const double* cls_r, int Nc, int Mc,
                              double Rc, double cmu, int mobility) {
+  __shared__ double ltab[3 * LOG_TAB];
+  log_table_init(ltab);
+  __syncthreads();
   const int b = blockIdx.y;
   double* M = A + (long long)b * mstride;
   const double r = cls_r[b];
@@ -43,7 +49,7 @@ __global__ void fill_onebody(double* A, int ld, long long mstride, const double*
       const double ph = 2.0 * LMFS_PI * j / Nc;
       const double ex = rs * cos(ph), ey = rs * sin(ph);
       double s00, s01, s11;
-      stokes2(xx - ex, xy - ey, cmu, &s00, &s01, &s11);
+      stokes2(xx - ex, xy - ey, cmu, &s00, &s01, &s11, ltab);
       const double v0 = a == 0 ? s00 : s01;   // (row, col 2j)
       const double v1 = a == 0 ? s01 : s11;   // (row, col 2j+1)
       M[(long long)(2 * j) * ld + row] = v0;
@@ -198,6 +204,9 @@ struct PairDims {
 // 4 nX.  One thread per (node, source) 2x2 block.
 __global__ void fill_FQ(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* A, int ld,
                         long long mstride) {
+  __shared__ double ltab[3 * LOG_TAB];
+  log_table_init(ltab);
+  __syncthreads();
   const int b = blockIdx.y;
   const int q = g.first + b;
   const int e1 = pd.nenh[2 * b], e2 = pd.nenh[2 * b + 1];
@@ -229,7 +238,7 @@ __global__ void fill_FQ(PairDims pd, PairGeo g, const double* Yf, const double* 
       zero = (disk == 0) ? (n < nX) : (n >= nX);
     }
     double s00 = 0, s01 = 0, s11 = 0;
-    if (!zero) stokes2(xx - yx, xy - yy, pd.cmu, &s00, &s01, &s11);
+    if (!zero) stokes2(xx - yx, xy - yy, pd.cmu, &s00, &s01, &s11, ltab);
     double* c0 = M + (long long)col * ld + 2 * n;
     double* c1 = M + (long long)(col + 1) * ld + 2 * n;
     c0[0] = s00; c0[1] = s01;
@@ -327,6 +336,9 @@ __device__ __forceinline__ int sym_src(int b, int Nfp) { return b < Nfp ? (b + N
 // order); column-major, leading dimension ld.
 __global__ void fill_FQ_sym(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* W, int ld,
                             long long mstride) {
+  __shared__ double ltab[3 * LOG_TAB];
+  log_table_init(ltab);
+  __syncthreads();
   const int b = blockIdx.y;
   const int q = g.first + b;
   const int e1 = pd.nenh[2 * b];
@@ -347,8 +359,8 @@ __global__ void fill_FQ_sym(PairDims pd, PairGeo g, const double* Yf, const doub
       col = 2 * s;
       const int si = nY1 + sym_src(s, pd.Nfp);
       double a00, a01, a11, b00, b01, b11;
-      stokes2(xx - Y[2 * s], xy - Y[2 * s + 1], pd.cmu, &a00, &a01, &a11);
-      stokes2(xx - Y[2 * si], xy - Y[2 * si + 1], pd.cmu, &b00, &b01, &b11);
+      stokes2(xx - Y[2 * s], xy - Y[2 * s + 1], pd.cmu, &a00, &a01, &a11, ltab);
+      stokes2(xx - Y[2 * si], xy - Y[2 * si + 1], pd.cmu, &b00, &b01, &b11, ltab);
       p00 = a00 + b00; p01 = a01 + b01; p11 = a11 + b11;
       m00 = a00 - b00; m01 = a01 - b01; m11 = a11 - b11;
     } else {
@@ -358,7 +370,7 @@ __global__ void fill_FQ_sym(PairDims pd, PairGeo g, const double* Yf, const doub
       const double rs = g.radii[k] * pd.Rc;
       const double2 cs = g.ring[jj];
       stokes2(xx - (g.centres[2 * k] + rs * cs.x), xy - (g.centres[2 * k + 1] + rs * cs.y), pd.cmu,
-              &p00, &p01, &p11);
+              &p00, &p01, &p11, ltab);
       m00 = p00; m01 = p01; m11 = p11;
     }
     double* c0 = Mp + (long long)col * ld + 2 * n;
@@ -583,6 +595,9 @@ __global__ void extract_E(PairDims pd, PairGeo g, const double* Yf, const double
 // columns.
 __global__ void fill_DC(PairDims pd, PairGeo g, const double* Yf, const double* Zpts, double* D, int dld,
                         long long dstride, double* W2, int ld2, long long w2stride, int Mp) {
+  __shared__ double ltab[3 * LOG_TAB];
+  log_table_init(ltab);
+  __syncthreads();
   // rows of the first Mp peanut nodes (all of them, or the first half when
   // the symmetric split reads only those)
   const int b = blockIdx.y, q = g.first + b;
@@ -609,7 +624,7 @@ __global__ void fill_DC(PairDims pd, PairGeo g, const double* Yf, const double* 
       base = Cb; ldd = ld2;
     }
     double s00, s01, s11;
-    stokes2(Z[2 * p] - yx, Z[2 * p + 1] - yy, pd.cmu, &s00, &s01, &s11);
+    stokes2(Z[2 * p] - yx, Z[2 * p + 1] - yy, pd.cmu, &s00, &s01, &s11, ltab);
     double* c0 = base + (long long)(2 * s) * ldd + 2 * p;
     double* c1 = base + (long long)(2 * s + 1) * ldd + 2 * p;
     c0[0] = s00; c0[1] = s01; c1[0] = s01; c1[1] = s11;
