@@ -29,51 +29,62 @@ __device__ __forceinline__ void stokes2(double dx, double dy, double c, double* 
 
 // ---- one-body ---------------------------------------------------------
 // Matrix [M | I] per radius class, M = P (resistance) or P (I - L) + B K^T
-// (mobility, eq. (SL)); rows 2Mc, columns 2Nc + 2Mc, column-major.
+// (mobility, eq. (SL)); rows 2Mc, columns 2Nc + 2Mc, column-major.  Block
+// (row, class), thread j: source j (positions from the node and ring
+// tables); the rigid-projection sums over j are added in a fixed order.
 __global__ void fill_onebody(double* A, int ld, long long mstride, const double* cls_r, int Nc, int Mc,
-                             double Rc, double cmu, int mobility) {
+                             double Rc, double cmu, int mobility, const double2* __restrict__ nodes,
+                             const double2* __restrict__ ring) {
   __shared__ double ltab[3 * LOG_TAB];
+  __shared__ double red[3][32];
   log_table_init(ltab);
   __syncthreads();
-  const int b = blockIdx.y;
+  const int row = blockIdx.x, b = blockIdx.y;
   double* M = A + (long long)b * mstride;
   const double r = cls_r[b];
   const int rows = 2 * Mc, nsrc = 2 * Nc;
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
-    const int m = row >> 1, a = row & 1;
-    const double th = 2.0 * LMFS_PI * m / Mc;
-    const double xx = r * cos(th), xy = r * sin(th);
-    const double rs = r * Rc;
-    double pk0 = 0, pk1 = 0, pk2 = 0;
-    for (int j = 0; j < Nc; ++j) {
-      const double ph = 2.0 * LMFS_PI * j / Nc;
-      const double ex = rs * cos(ph), ey = rs * sin(ph);
-      double s00, s01, s11;
-      stokes2(xx - ex, xy - ey, cmu, &s00, &s01, &s11, ltab);
-      const double v0 = a == 0 ? s00 : s01;   // (row, col 2j)
-      const double v1 = a == 0 ? s01 : s11;   // (row, col 2j+1)
-      M[(long long)(2 * j) * ld + row] = v0;
-      M[(long long)(2 * j + 1) * ld + row] = v1;
-      // P K for the rigid projector; K rows: [1, 0, -ey], [0, 1, ex]
-      pk0 += v0; pk1 += v1; pk2 += -ey * v0 + ex * v1;
-    }
-    if (mobility) {
-      // (K^T K)^{-1} = diag(1/Nc, 1/Nc, 1/(Nc rs^2)) for an equispaced ring
-      const double g0 = pk0 / Nc, g1 = pk1 / Nc, g2 = pk2 / (Nc * rs * rs);
-      const double bx = (a == 0) ? 1.0 : 0.0, by = (a == 0) ? 0.0 : 1.0;
-      const double bw = (a == 0) ? -xy : xx;   // B row: [bx, by, bw]
-      for (int j = 0; j < Nc; ++j) {
-        const double ph = 2.0 * LMFS_PI * j / Nc;
-        const double ex = rs * cos(ph), ey = rs * sin(ph);
-        // column 2j:   K row [1, 0, -ey];   column 2j+1: K row [0, 1, ex]
-        double* c0 = M + (long long)(2 * j) * ld + row;
-        double* c1 = M + (long long)(2 * j + 1) * ld + row;
-        *c0 += -(g0 + g2 * (-ey)) + (bx + bw * (-ey));
-        *c1 += -(g1 + g2 * ex) + (by + bw * ex);
-      }
-    }
-    for (int q = 0; q < rows; ++q) M[(long long)(nsrc + q) * ld + row] = (q == row) ? 1.0 : 0.0;
+  const int m = row >> 1, a = row & 1;
+  const double2 cn = nodes[m];
+  const double xx = r * cn.x, xy = r * cn.y;
+  const double rs = r * Rc;
+  double v0 = 0, v1 = 0, ex = 0, ey = 0;
+  double pk0 = 0, pk1 = 0, pk2 = 0;
+  const int j = threadIdx.x;
+  if (j < Nc) {
+    const double2 cs = ring[j];
+    ex = rs * cs.x; ey = rs * cs.y;
+    double s00, s01, s11;
+    stokes2(xx - ex, xy - ey, cmu, &s00, &s01, &s11, ltab);
+    v0 = a == 0 ? s00 : s01;   // (row, col 2j)
+    v1 = a == 0 ? s01 : s11;   // (row, col 2j+1)
+    // P K for the rigid projector; K rows: [1, 0, -ey], [0, 1, ex]
+    pk0 = v0; pk1 = v1; pk2 = -ey * v0 + ex * v1;
   }
+  if (mobility) {
+    // block sums of P K over the sources (warp sums, then warps in order)
+    for (int o = 16; o > 0; o >>= 1) {
+      pk0 += __shfl_xor_sync(0xffffffffu, pk0, o);
+      pk1 += __shfl_xor_sync(0xffffffffu, pk1, o);
+      pk2 += __shfl_xor_sync(0xffffffffu, pk2, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { red[0][wid] = pk0; red[1][wid] = pk1; red[2][wid] = pk2; }
+    __syncthreads();
+    double t0 = 0, t1 = 0, t2 = 0;
+    for (int w = 0; w < nw; ++w) { t0 += red[0][w]; t1 += red[1][w]; t2 += red[2][w]; }
+    // (K^T K)^{-1} = diag(1/Nc, 1/Nc, 1/(Nc rs^2)) for an equispaced ring
+    const double g0 = t0 / Nc, g1 = t1 / Nc, g2 = t2 / (Nc * rs * rs);
+    const double bx = (a == 0) ? 1.0 : 0.0, by = (a == 0) ? 0.0 : 1.0;
+    const double bw = (a == 0) ? -xy : xx;   // B row: [bx, by, bw]
+    // column 2j:   K row [1, 0, -ey];   column 2j+1: K row [0, 1, ex]
+    v0 += -(g0 + g2 * (-ey)) + (bx + bw * (-ey));
+    v1 += -(g1 + g2 * ex) + (by + bw * ex);
+  }
+  if (j < Nc) {
+    M[(long long)(2 * j) * ld + row] = v0;
+    M[(long long)(2 * j + 1) * ld + row] = v1;
+  }
+  for (int q = threadIdx.x; q < rows; q += blockDim.x) M[(long long)(nsrc + q) * ld + row] = (q == row) ? 1.0 : 0.0;
 }
 
 // Extract W (rank rows of Q^T, stored column by column: Wt[col][row]) and R
@@ -750,9 +761,10 @@ int onebody_enqueue(Ctx& c, int problem, OneBody& ob, cudaStream_t st) {
       cuda_failed(cudaMemcpyAsync(dn, hn.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st), "h2d") ||
       cuda_failed(cudaMemsetAsync(ob.bad, 0, sizeof(int), st), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
   {
+    const int thr = std::max(32, ((Nc + 31) / 32) * 32);   // Nc <= 128
+    fill_onebody<<<dim3(m, nb), thr, 0, st>>>(ws, ld, mstride, c.cls_r, Nc, Mc, c.Rc, 1.0 / (4 * LMFS_PI * c.prm.mu),
+                                              problem == LMFS_MOBILITY, c.nodes, c.ring);
     dim3 grid(2, nb);
-    fill_onebody<<<grid, 128, 0, st>>>(ws, ld, mstride, c.cls_r, Nc, Mc, c.Rc, 1.0 / (4 * LMFS_PI * c.prm.mu),
-                                       problem == LMFS_MOBILITY);
     if ((rc = check_launch("fill_onebody"))) goto done;
     QRBatch q{};
     q.A = ws; q.mstride = mstride; q.m = dm; q.n = dn; q.k = k; q.ld = ld; q.eps = c.prm.eps_trunc;
