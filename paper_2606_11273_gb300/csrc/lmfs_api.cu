@@ -93,7 +93,7 @@ static void free_ctx(Ctx& c) {
   dfree(c.centres); dfree(c.radii); dfree(c.cls); dfree(c.cls_r); dfree(c.pairs); dfree(c.csr_off);
   dfree(c.csr_ent);
   for (NearSet& z : c.nz) {
-    dfree(z.off); dfree(z.ent); dfree(z.tgt); dfree(z.excl_off); dfree(z.excl); dfree(z.part);
+    dfree(z.off); dfree(z.ent); dfree(z.tgt); dfree(z.excl_off); dfree(z.excl); dfree(z.part); dfree(z.work0);
   }
   dfree(c.tgt32); dfree(c.dsk32);
   for (auto& pb : c.prob) {

@@ -213,6 +213,13 @@ int upload_geometry(Ctx& c) {
     LMFS_TRY(dalloc(&z.tgt, ne_n));
     LMFS_TRY(dalloc(&z.excl_off, P + 1));
     LMFS_TRY(dalloc(&z.excl, ne_n));
+    std::vector<int> w0;
+    for (size_t e = 0; e < z.h.size(); ++e)
+      if (z.h[e].kind != 2) w0.push_back((int)e);
+    z.n_work0 = (int)w0.size();
+    LMFS_TRY(dalloc(&z.work0, std::max<size_t>(1, w0.size())));
+    if (!w0.empty())
+      LMFS_CUDA(cudaMemcpyAsync(z.work0, w0.data(), w0.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     std::vector<int4> ne(z.h.size());
     std::vector<int> fx(z.h.size()), tg(z.h.size());
     for (size_t e = 0; e < z.h.size(); ++e) {

@@ -88,6 +88,8 @@ struct NearSet {
   int* excl_off = nullptr;           // [P+1] sorted source disks the far kernel skips
   int* excl = nullptr;
   double* part = nullptr;            // [entries][Mc][2] near-field sums per entry
+  int* work0 = nullptr;              // the entries other than self, in list order (the matvec's launch)
+  int n_work0 = 0;
 };
 
 struct Ctx {

@@ -870,15 +870,15 @@ __global__ void reduce_splits(const double* part, long long stride, int nsplit, 
 //     entries, self included, of S^(ik) s_k).
 __global__ void near_kernel(int mode, const double* __restrict__ centres, const double* __restrict__ radii,
                             double Rc, int Mc, int Nc, int G, const double2* __restrict__ ring,
-                            const double2* __restrict__ nodes, const int* __restrict__ near_tgt,
-                            const int4* __restrict__ near_ent,
+                            const double2* __restrict__ nodes, const int* __restrict__ work,
+                            const int* __restrict__ near_tgt, const int4* __restrict__ near_ent,
                             const double* __restrict__ sig, const double* __restrict__ lam,
                             const double* __restrict__ lb, const double* __restrict__ tilde, int mobility,
                             double* __restrict__ part) {
   extern __shared__ double nsm[];   // [Nc][4]: y_x, y_y, s_x, s_y, then [G][Mt][2] partial sums
   __shared__ double red[3][32];
   __shared__ double ltab[3 * LOG_TAB];
-  const int e = blockIdx.x;
+  const int e = work ? work[blockIdx.x] : (int)blockIdx.x;   // the matvec launches the non-self entries only
   const int4 en = near_ent[e];
   const int i = near_tgt[e], k = en.x, kind = en.y;
   if (mode == 0 && kind == 2) return;     // whole block: the self term cancels
@@ -1491,14 +1491,17 @@ int near_field(Ctx& c, int mode, const double* strength, const double* mu, const
   // entries, each entry's targets are split over Y blocks (and its sources
   // over Y times as many groups) so that the launch covers the SMs
   const int Mc = c.d.Mc;
-  const int ne = (int)z.h.size();
+  // the matvec skips the self entries (their term cancels): a launch over the
+  // others only, so that no SM gets several working blocks while others idle
+  const int* work = mode == 0 ? z.work0 : nullptr;
+  const int ne = mode == 0 ? z.n_work0 : (int)z.h.size();
   const int Y = std::max(1, std::min(4, (2 * c.sms + std::max(ne, 1) - 1) / std::max(ne, 1)));
   const int Mt = (Mc + Y - 1) / Y;
   const int G = std::max(1, std::min({4 * Y, 1024 / Mt, c.d.Nc}));
   const int threads = ((G * Mt + 31) / 32) * 32;
   const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mt * 2) * sizeof(double);
   if (ne > 0) {
-    near_kernel<<<dim3(ne, Y), threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, c.nodes, z.tgt,
+    near_kernel<<<dim3(ne, Y), threads, shm, c.stream>>>(mode, c.centres, c.radii, c.Rc, Mc, c.d.Nc, G, c.ring, c.nodes, work, z.tgt,
                                                 z.ent, strength, c.lam, c.lb, c.tilde,
                                                 problem == LMFS_MOBILITY, z.part);
     LMFS_TRY(check_launch("near"));
