@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <tuple>
+#include <map>
 #include <vector>
 
 #include "lmfs_internal.h"
@@ -1061,7 +1063,7 @@ __global__ void post_kernel(const double* __restrict__ lb, const double* __restr
 
 // ---- lean FP32 tile kernel (stand-alone sum, LMFS_FP32_FAST) ------------------
 // Per source disk k, target offset X = x - c_k in double-float then FP32; per
-// source j (offset y_j, strength s_j) and each pair (a, b) of the thread's four
+// source j (offset y_j, strength s_j) and each pair (a, b) of the thread's
 // targets:
 //   d = X - y_j,  r^2 = |d|^2,  L = lg2 r^2 (hardware approximation),
 //   1/r_a^2 = r_b^2 / (r_a^2 r_b^2) (one hardware reciprocal for both),
@@ -1071,7 +1073,6 @@ __global__ void post_kernel(const double* __restrict__ lb, const double* __restr
 //   special-function operations per (target, source) pair; the two targets of
 //   a pair run in packed two-wide FP32 instructions, so that the issue slots
 //   the special functions take leave the FMA pipe fed.
-constexpr int FL_TILE = 8;        // source disks per staged tile
 
 __global__ void records_lean(const double* __restrict__ centres, const double* __restrict__ off,
                              const double* __restrict__ s, int nd, int npd, float4* __restrict__ rec,
@@ -1106,16 +1107,18 @@ struct LeanArgs {
   int* err; int* range_err;
 };
 
-template <int TPT>   // targets per thread, even: packed in pairs sharing one reciprocal
+// TPT targets per thread (even: packed in pairs sharing one reciprocal), FL
+// source disks per staged tile.
+template <int TPT, int FL>
 __global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel(LeanArgs a) {
   extern __shared__ __align__(16) unsigned char lsm[];
   const int npd = a.npd;
-  const uint32_t rec_bytes = (uint32_t)(FL_TILE * npd * 32);
+  const uint32_t rec_bytes = (uint32_t)(FL * npd * 32);
   float4* const rbuf0 = (float4*)lsm;
   float4* const rbuf1 = (float4*)(lsm + rec_bytes);
   float4* const dbuf0 = (float4*)(lsm + 2 * rec_bytes);
-  float4* const dbuf1 = (float4*)(lsm + 2 * rec_bytes + FL_TILE * 16);
-  uint64_t* bars = (uint64_t*)(lsm + 2 * rec_bytes + 2 * FL_TILE * 16);
+  float4* const dbuf1 = (float4*)(lsm + 2 * rec_bytes + FL * 16);
+  uint64_t* bars = (uint64_t*)(lsm + 2 * rec_bytes + 2 * FL * 16);
   __shared__ int s_fail;
 
   const int t0 = TPT * (blockIdx.x * F_THREADS + threadIdx.x);
@@ -1138,7 +1141,7 @@ __global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel
 #pragma unroll
   for (int q = 0; q < TPT; ++q) sx[q] = sy[q] = cx[q] = cy[q] = 0.f;
 
-  const int ntile = (k_end - k_begin + FL_TILE - 1) / FL_TILE;
+  const int ntile = (k_end - k_begin + FL - 1) / FL;
   if (threadIdx.x == 0) {
     s_fail = 0;
     mbar_init(&bars[0], 1);
@@ -1147,8 +1150,8 @@ __global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel
   }
   __syncthreads();
   auto issue = [&](int tile) {
-    const int kb = k_begin + tile * FL_TILE;
-    const int nd = min(FL_TILE, k_end - kb);
+    const int kb = k_begin + tile * FL;
+    const int nd = min(FL, k_end - kb);
     const int buf = tile & 1;
     const uint32_t rb = (uint32_t)(nd * npd * 32), db = (uint32_t)(nd * 16);
     mbar_expect_tx(&bars[buf], rb + db);
@@ -1162,7 +1165,7 @@ __global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel
     if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = 1;
     __syncthreads();
     if (s_fail) break;
-    const int nd = min(FL_TILE, k_end - (k_begin + tile * FL_TILE));
+    const int nd = min(FL, k_end - (k_begin + tile * FL));
     const float4* R = buf ? rbuf1 : rbuf0;
     const float4* Dk = buf ? dbuf1 : dbuf0;
     if (act) {
@@ -1232,30 +1235,115 @@ __global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel
   if (bad) atomicExch(a.range_err, 1);
 }
 
+// One lean launch of configuration <TPT, FL> (and the split sum) on the
+// first nd source disks and all targets.
+template <int TPT, int FL>
+static int lean_run(const double* targets, int nt, const float4* dsk, const float4* rec, int nd, int npd, double mu,
+                    int dev_sms, cudaStream_t st, double* out, double* part, int* err) {
+  const long long bx = ((long long)(nt + TPT - 1) / TPT + F_THREADS - 1) / F_THREADS;
+  const size_t shm = 2 * (size_t)FL * npd * 32 + 2 * FL * 16 + 16;
+  if (shm > 227 * 1024) return LMFS_ERR_INVALID;
+  if (cuda_failed(cudaFuncSetAttribute(far32_lean_kernel<TPT, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr"))
+    return LMFS_ERR_CUDA;
+  int per_sm = 0;
+  if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far32_lean_kernel<TPT, FL>, F_THREADS, shm), "occupancy"))
+    return LMFS_ERR_CUDA;
+  int kchunk = 1;
+  const int split = wave_split(bx, (long long)std::max(1, per_sm) * dev_sms, nd, FL, 16, &kchunk);
+  LeanArgs a;
+  a.targets = targets; a.nt = nt; a.dsk = dsk; a.rec = rec; a.nd = nd; a.npd = npd; a.kchunk = kchunk;
+  a.cmu = INV4PI / mu; a.out = split > 1 ? part : out; a.out_stride = 2LL * nt; a.err = err; a.range_err = err + 1;
+  far32_lean_kernel<TPT, FL><<<dim3((unsigned)bx, (unsigned)split), F_THREADS, shm, st>>>(a);
+  LMFS_TRY(check_launch("far32_lean"));
+  if (split > 1) {
+    reduce_splits<<<(int)std::min<long long>((2LL * nt + 255) / 256, 4096), 256, 0, st>>>(part, 2LL * nt, split, 2LL * nt, out);
+    LMFS_TRY(check_launch("reduce"));
+  }
+  return LMFS_OK;
+}
+
+// The autotuner's candidates: targets per thread x source disks per tile.
+struct LeanCfg { int tpt, fl; };
+constexpr LeanCfg kLeanCfgs[] = {{4, 8}, {2, 8}, {4, 16}, {2, 16}};
+
+static int lean_dispatch(LeanCfg g, const double* targets, int nt, const float4* dsk, const float4* rec, int nd,
+                         int npd, double mu, int dev_sms, cudaStream_t st, double* out, double* part, int* err) {
+  if (g.tpt == 4 && g.fl == 8) return lean_run<4, 8>(targets, nt, dsk, rec, nd, npd, mu, dev_sms, st, out, part, err);
+  if (g.tpt == 2 && g.fl == 8) return lean_run<2, 8>(targets, nt, dsk, rec, nd, npd, mu, dev_sms, st, out, part, err);
+  if (g.tpt == 4 && g.fl == 16) return lean_run<4, 16>(targets, nt, dsk, rec, nd, npd, mu, dev_sms, st, out, part, err);
+  return lean_run<2, 16>(targets, nt, dsk, rec, nd, npd, mu, dev_sms, st, out, part, err);
+}
+
+namespace {
+std::mutex g_lean_mu;
+std::map<std::tuple<int, int, int, int>, LeanCfg> g_lean_best;   // (device, npd, log2 nt, log2 nd)
+
+int ilog2(long long v) { int k = 0; while (v > 1) { v >>= 1; ++k; } return k; }
+}  // namespace
+
+// Autotuner: the first call for a (device, sources per disk, size class)
+// times every candidate configuration with CUDA events on a sample of the
+// problem (all targets, the first <= 2048 source disks; one untimed launch,
+// then one timed) and keeps the fastest for that class; later calls reuse it.
+// The candidates differ only in launch shape, and the results differ only by
+// rounding (the split changes the order of the partial sums).
+static int lean_tuned(int dev, const double* targets, int nt, const float4* dsk, const float4* rec, int nd, int npd,
+                      double mu, int dev_sms, cudaStream_t st, double* out, double* part, int* err, LeanCfg* best) {
+  const auto key = std::make_tuple(dev, npd, ilog2(nt), ilog2(nd));
+  {
+    std::lock_guard<std::mutex> lk(g_lean_mu);
+    auto it = g_lean_best.find(key);
+    if (it != g_lean_best.end()) { *best = it->second; return LMFS_OK; }
+  }
+  const int nd_s = std::min(nd, 2048);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cuda_failed(cudaEventCreate(&e0), "event") || cuda_failed(cudaEventCreate(&e1), "event")) {
+    if (e0) cudaEventDestroy(e0);
+    return LMFS_ERR_CUDA;
+  }
+  float best_ms = 1e30f;
+  LeanCfg pick = kLeanCfgs[0];
+  int rc = LMFS_OK;
+  for (const LeanCfg& g : kLeanCfgs) {
+    int r = lean_dispatch(g, targets, nt, dsk, rec, nd_s, npd, mu, dev_sms, st, out, part, err);
+    if (r == LMFS_ERR_INVALID) continue;          // does not fit shared memory
+    if (r == LMFS_OK && cuda_failed(cudaEventRecord(e0, st), "event")) r = LMFS_ERR_CUDA;
+    if (r == LMFS_OK) r = lean_dispatch(g, targets, nt, dsk, rec, nd_s, npd, mu, dev_sms, st, out, part, err);
+    if (r == LMFS_OK && (cuda_failed(cudaEventRecord(e1, st), "event") || cuda_failed(cudaEventSynchronize(e1), "sync")))
+      r = LMFS_ERR_CUDA;
+    if (r != LMFS_OK) { rc = r; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; pick = g; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LMFS_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_lean_mu);
+    g_lean_best[key] = pick;
+  }
+  *best = pick;
+  return LMFS_OK;
+}
+
 int stokeslet_sum_lean(const double* targets, int nt, const double* centres, const double* offsets,
                        const double* strengths, int nd, int npd, double mu, cudaStream_t st, double* out) {
   int dev_sms = 152, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr int LT = 4;                    // targets per thread: two packed pairs
-  const long long bx = ((long long)(nt + LT - 1) / LT + F_THREADS - 1) / F_THREADS;
-  const size_t shm = 2 * (size_t)FL_TILE * npd * 32 + 2 * FL_TILE * 16 + 16;
-  if (shm > 227 * 1024) { set_last_error("lmfs_stokeslet_sum: too many sources per disk"); return LMFS_ERR_INVALID; }
-  if (cuda_failed(cudaFuncSetAttribute(far32_lean_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm), "attr"))
-    return LMFS_ERR_CUDA;
-  // split of the source disks over blockIdx.y that fills whole waves
-  int per_sm = 0;
-  if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far32_lean_kernel<LT>, F_THREADS, shm), "occupancy"))
-    return LMFS_ERR_CUDA;
-  int kchunk = 1;
-  const long long split = wave_split(bx, (long long)std::max(1, per_sm) * dev_sms, nd, FL_TILE, 16, &kchunk);
+  if (2 * (size_t)8 * npd * 32 + 2 * 8 * 16 + 16 > 227 * 1024) {
+    set_last_error("lmfs_stokeslet_sum: too many sources per disk");
+    return LMFS_ERR_INVALID;
+  }
   float4* dsk = nullptr; float4* rec = nullptr; int* err = nullptr; double* part = nullptr;
   auto A = [&](void** p, size_t b) { return cudaMallocAsync(p, b, st); };
   int rc = LMFS_OK;
+  // split partial sums: at most 16 chunks (wave_split's limit)
   if (cuda_failed(A((void**)&dsk, (size_t)nd * sizeof(float4)), "alloc") ||
       cuda_failed(A((void**)&rec, 2 * (size_t)nd * npd * sizeof(float4)), "alloc") ||
       cuda_failed(A((void**)&err, 2 * sizeof(int)), "alloc") ||
-      (split > 1 && cuda_failed(A((void**)&part, split * 2LL * nt * sizeof(double)), "alloc")))
+      cuda_failed(A((void**)&part, 16 * 2LL * nt * sizeof(double)), "alloc"))
     rc = LMFS_ERR_NOMEM;
   int herr[2] = {0, 0};
   if (rc == LMFS_OK) {
@@ -1263,17 +1351,9 @@ int stokeslet_sum_lean(const double* targets, int nt, const double* centres, con
     records_lean<<<(int)std::min<long long>(((long long)nd * npd + 255) / 256, 8192), 256, 0, st>>>(
         centres, offsets, strengths, nd, npd, rec, dsk);
     rc = check_launch("records_lean");
-    LeanArgs a;
-    a.targets = targets; a.nt = nt; a.dsk = dsk; a.rec = rec; a.nd = nd; a.npd = npd; a.kchunk = kchunk;
-    a.cmu = INV4PI / mu; a.out = split > 1 ? part : out; a.out_stride = 2LL * nt; a.err = err; a.range_err = err + 1;
-    if (rc == LMFS_OK) {
-      far32_lean_kernel<LT><<<dim3((unsigned)bx, (unsigned)split), F_THREADS, shm, st>>>(a);
-      rc = check_launch("far32_lean");
-    }
-    if (rc == LMFS_OK && split > 1) {
-      reduce_splits<<<(int)std::min<long long>((2LL * nt + 255) / 256, 4096), 256, 0, st>>>(part, 2LL * nt, (int)split, 2LL * nt, out);
-      rc = check_launch("reduce");
-    }
+    LeanCfg g = kLeanCfgs[0];
+    if (rc == LMFS_OK) rc = lean_tuned(dev, targets, nt, dsk, rec, nd, npd, mu, dev_sms, st, out, part, err, &g);
+    if (rc == LMFS_OK) rc = lean_dispatch(g, targets, nt, dsk, rec, nd, npd, mu, dev_sms, st, out, part, err);
     if (rc == LMFS_OK && (cuda_failed(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st), "d2h") ||
                           cuda_failed(cudaStreamSynchronize(st), "sync")))
       rc = LMFS_ERR_CUDA;
