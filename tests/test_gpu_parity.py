@@ -357,3 +357,61 @@ def test_resolve_after_invalidate_is_identical(L):
         assert np.array_equal(again, first)
     del hold
     s.close()
+
+
+def test_p10000_matvec_sampled_rows(L):
+    """The P = 10^4 packing at full size (area fraction 0.65, ~10^4 close
+    pairs): FP64 and mixed matvecs against the oracle on 1008 sampled target
+    rows (7 disks x 72 nodes x 2), with identical one-body SVD factors and
+    zero pair blocks on both sides (the oracle's pair precompute at this size
+    is out of reach on the host).  Every source disk contributes to every
+    sampled row: the multipole far field over ~10^4 disks, the near zone and
+    the exclusion-form terms of the close partners.  FP64 within the oracle's
+    literal-form rounding bound on these rows (at least 1e-12), mixed 1e-6."""
+    pk = w.packing_p10000()
+    P = pk.P
+    n4 = 4 * PACKING.Nc
+    from oracle.geometry import contacts
+    C = len(contacts(pk.centres, pk.radii, PACKING.delta_c))
+    zero = {"A": np.zeros((n4, n4)), "E": np.zeros((6, n4))}
+    so = System(pk.centres, pk.radii, PACKING, "mobility", blocks=[zero] * C, dense_limit=0)
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
+    assert s.n_pairs == C
+    s.set_pair_blocks(L.MOBILITY, np.zeros((C, n4, n4)), np.zeros((C, 6, n4)))
+    s.set_onebody(L.MOBILITY, *onebody_factors(so.ob[0], PACKING.Nc))
+    # a smooth surface field, as in the P = 100 test: with iid noise the
+    # one-body pseudo-inverse makes strengths ~1e9 |mu| and the oracle's
+    # literal form (which adds and subtracts them) loses its accuracy
+    mu = w.smooth_surface_vector(P, PACKING.Mc, 17).reshape(P, -1)
+    rng = np.random.default_rng(17)
+    targets = np.sort(rng.choice(P, 7, replace=False))
+    uo = so.matvec(mu, targets)
+    # the oracle's own rounding on these rows (as fp64_tolerance, restricted
+    # to the sampled rows): its literal form adds the self and close-partner
+    # fields over all sources and subtracts them again
+    lb = so.lam_bar(mu)
+    sig = np.stack([so.proj(i, lb[i]) for i in range(P)]).reshape(-1, 2)
+    Xt = so.X[targets].reshape(-1, 2)
+    Ys = so.Y.reshape(-1, 2)
+    absum = np.zeros((Xt.shape[0], 2))
+    for a in range(0, Xt.shape[0], 32):
+        dx = Xt[a:a + 32, None, 0] - Ys[None, :, 0]
+        dy = Xt[a:a + 32, None, 1] - Ys[None, :, 1]
+        r2 = dx * dx + dy * dy
+        lg = 0.5 * np.log(r2)
+        sxx, sxy, syy = np.abs(-lg + dx * dx / r2), np.abs(dx * dy / r2), np.abs(-lg + dy * dy / r2)
+        absum[a:a + 32, 0] = (sxx * np.abs(sig[None, :, 0]) + sxy * np.abs(sig[None, :, 1])).sum(1)
+        absum[a:a + 32, 1] = (sxy * np.abs(sig[None, :, 0]) + syy * np.abs(sig[None, :, 1])).sum(1)
+    absum /= 4 * np.pi * PACKING.mu
+    tol64 = max(1e-12, 50 * EPS64 * np.linalg.norm(absum) / np.linalg.norm(uo))
+    e64 = rel(gpu_matvec(L, s, L.MOBILITY, mu, L.FP64)[targets], uo)
+    e32 = rel(gpu_matvec(L, s, L.MOBILITY, mu, L.MIXED)[targets], uo)
+    print(f"P = 10^4, {2 * PACKING.Mc * len(targets)} sampled rows: fp64 {e64:.2e} (bound {tol64:.1e})  "
+          f"mixed {e32:.2e}")
+    assert e64 < tol64
+    # the bound is loose here (the absolute sum over 6e5 sources includes the
+    # far field's own cancellation); the two sides agree to ~2e-12 on these
+    # rows, so also hold them within 50 times that
+    assert e64 < 1e-10
+    assert e32 < 1e-6
+    s.close()
