@@ -312,3 +312,26 @@ def test_squeeze_force_matches_reynolds_lubrication():
     lead = 1.5 * math.pi * 1.0 * 2.0 * (1.0 / 1e-3) ** 1.5
     assert f[0][0] == pytest.approx(lead, rel=5e-3)
     assert f[1][0] == pytest.approx(-f[0][0], rel=1e-10)
+
+
+def test_matvec_on_sampled_targets_equals_full_rows():
+    """The oracle's matvec evaluated on a subset of target disks (as the
+    full-size P = 10^4 check uses it) equals those rows of the full matvec:
+    Step 2a over every source, the Step 2b terms of pairs that touch a sampled
+    disk, and the identity step, with the dense far field (to rounding) and
+    with the chunked direct sum."""
+    p = PAIR_SMALL
+    c = np.array([[0.0, 0.0], [2.05, 0.0], [4.2, 0.3], [0.5, 2.3], [2.7, 2.2]])
+    r = np.ones(5)
+    mu = w.smooth_surface_vector(5, p.Mc, 3).reshape(5, -1)
+    dense = System(c, r, p, "mobility")
+    assert len(dense.pairs) >= 2
+    chunked = System(c, r, p, "mobility", blocks=dense.blocks, dense_limit=0)
+    full = dense.matvec(mu)
+    for targets in ([1], [0, 3], [2, 4, 1]):
+        t = np.sort(np.asarray(targets))
+        np.testing.assert_allclose(dense.matvec(mu, t), full[t], rtol=0, atol=1e-12 * np.abs(full).max())
+        # the chunked sum adds the same terms in another order; with the real
+        # pair blocks the literal form cancels strengths ~1e6 |mu|, so the
+        # two orders differ at ~1e-16 x 1e6 of the field
+        np.testing.assert_allclose(chunked.matvec(mu, t), full[t], rtol=0, atol=1e-9 * np.abs(full).max())
