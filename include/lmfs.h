@@ -188,7 +188,13 @@ int lmfs_get_solution(lmfs_handle h, double* mu_dev);
  * out [nt][2] (double).  No exclusions.  precision: LMFS_MIXED_DIRECT (or
  * LMFS_MIXED, the same): the series kernel, which rejects targets within 4
  * source-ring radii of a disk centre (LMFS_ERR_INVALID); LMFS_FP32_FAST: the
- * lean kernel, which rejects a target on a source (r = 0). */
+ * lean kernel, which rejects a target on a source (r = 0).  The lean kernel's
+ * launch shape (targets per thread, source disks per tile) is autotuned: the
+ * first call for a class of problem sizes (device, n_per_disk, log2 nt, log2
+ * nd) also times each candidate shape on a sample of the problem (all targets,
+ * at most 2048 source disks), writing scratch results to `out` before the
+ * final sum overwrites it; later calls of the class use the cached choice.
+ * `out` must not alias the inputs. */
 int lmfs_stokeslet_sum(const double* targets, int nt, const double* centres,
                        const double* offsets, const double* strengths, int nd,
                        int n_per_disk, double mu, int precision, void* stream, double* out);
