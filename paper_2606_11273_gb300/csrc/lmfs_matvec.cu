@@ -35,16 +35,6 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// Warp sum into every lane where only the lanes keeping a partial sum add
-// (31 FP64 lane operations instead of 5 x 32).
-__device__ __forceinline__ double lsum(double v) {
-  const int lane = threadIdx.x & 31;
-  for (int o = 16; o > 0; o >>= 1) {
-    const double t = __shfl_down_sync(0xffffffffu, v, o);
-    if (lane < o) v += t;
-  }
-  return __shfl_sync(0xffffffffu, v, 0);
-}
 
 // ---- Step 1a: lam_bar = Pi^+ mu, one block per disk, one thread per row ----
 // Pi^+ applied from its QR factors: t = W mu (W = first r rows of Q^T, stored
@@ -768,7 +758,8 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
             const T R = sqrt(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
             const T x = rho / R;
             const V2 a1 = cf[2];
-            const T lead = sqrt((T)a1.x * (T)a1.x + (T)a1.y * (T)a1.y) / R + B * x * (T)1e-6 + (T)1e-300;
+            const T lead = sqrt((T)a1.x * (T)a1.x + (T)a1.y * (T)a1.y) / R + B * x * (T)1e-6 +
+                           (sizeof(T) == 4 ? (T)0 : (T)1e-300);   // 1e-300 is 0 in FP32
             const T tol = (sizeof(T) == 4) ? (T)1e-9 : (T)1e-16;
             int need = MP_P;
             if (B > (T)0 && x < (T)1) {
