@@ -58,6 +58,41 @@ def test_single_disk_resistance_closed_form(a):
     assert np.allclose(ft[0], [0, 0, 4 * math.pi * a * a], rtol=1e-10, atol=1e-10)
 
 
+@pytest.mark.parametrize("a", [1.0, 0.8, 1.2])
+def test_single_disk_exterior_field_closed_form(a):
+    """Off the surface, the one-body MFS field of a rigid disk is the exact
+    one.  Translation with velocity V: a Stokeslet F at the centre plus the
+    potential dipole D = a^2 F / (8 pi mu), which cancels the Stokeslet's
+    (x.F) x / r^2 part on r = a, so u = V there with F = 4 pi mu V /
+    (1/2 - log a).  Rotation with omega: the rotlet u = a^2 omega (-y, x) / r^2.
+    The ring of coarse sources reproduces both at r = 1.5a .. 4a to rounding
+    (its aliasing terms decay like (R_c a / r)^N_c)."""
+    from oracle.onebody import OneBody
+    from oracle.system import stokes_sum
+    mu = PACKING.mu
+    ob = OneBody(a, PACKING, "resistance")
+    th = np.linspace(0.0, 2 * np.pi, 37, endpoint=False)
+    V = np.array([1.0, -0.5])
+    lam = ob.apply_pinv(np.tile(V, PACKING.Mc)).reshape(-1, 2)
+    F = lam.sum(0)
+    assert np.allclose(F, 4 * np.pi * mu * V / (0.5 - math.log(a)), rtol=1e-12)
+    for rr in (1.5, 2.0, 4.0):
+        X = np.stack([rr * a * np.cos(th), rr * a * np.sin(th)], 1)
+        r2 = (X ** 2).sum(1)[:, None]
+        xF = (X @ F)[:, None]
+        exact = (-0.5 * np.log(r2) * F + xF * X / r2) / (4 * np.pi * mu) \
+            + a * a / (8 * np.pi * mu) * (F / r2 - 2 * xF * X / r2 ** 2)
+        u = stokes_sum(X, ob.Y, lam, mu)
+        assert np.abs(u - exact).max() < 1e-12 * np.abs(exact).max(), rr
+    w_ = 1.0
+    lam = ob.apply_pinv(np.stack([-w_ * ob.X[:, 1], w_ * ob.X[:, 0]], 1).ravel()).reshape(-1, 2)
+    for rr in (1.5, 3.0):
+        X = np.stack([rr * a * np.cos(th), rr * a * np.sin(th)], 1)
+        exact = (a * a * w_ / (X ** 2).sum(1))[:, None] * np.stack([-X[:, 1], X[:, 0]], 1)
+        u = stokes_sum(X, ob.Y, lam, mu)
+        assert np.abs(u - exact).max() < 1e-12 * np.abs(exact).max(), rr
+
+
 @pytest.mark.parametrize("a", [1.0, 0.9])
 def test_single_disk_mobility_closed_form(a):
     """Inverse of the above: v = f (1/2 - log a)/(4 pi mu), omega = t/(4 pi mu a^2)."""
