@@ -370,3 +370,19 @@ def test_matvec_on_sampled_targets_equals_full_rows():
         # pair blocks the literal form cancels strengths ~1e6 |mu|, so the
         # two orders differ at ~1e-16 x 1e6 of the field
         np.testing.assert_allclose(chunked.matvec(mu, t), full[t], rtol=0, atol=1e-9 * np.abs(full).max())
+
+
+@pytest.mark.parametrize("problem", ["resistance", "mobility"])
+@pytest.mark.parametrize("gap", [1e-1, 1e-2, 1e-3])
+def test_pair_solves_have_small_residuals(problem, gap):
+    """The two least-squares problems of a close pair are solved, at the
+    paper's parameters: the fine local solve F Z = blkQ (eq. (bfm)) and the
+    peanut compression C A = -D Z (eq. (Amat)) leave relative residuals at the
+    discretisation level (measured 1e-12..2e-5 and 1e-8..2e-7 here), while a
+    sign, index or transposition error in Z, D or A leaves O(1)."""
+    from oracle.onebody import OneBody
+    from oracle.pairs import pair_blocks
+    ob = OneBody(1.0, PACKING, problem)
+    out = pair_blocks(np.array([0.0, 0.0]), 1.0, np.array([2.0 + gap, 0.0]), 1.0, ob, ob, PACKING, problem, 1.0)
+    assert out["fine_residual"] < 1e-4
+    assert out["peanut_residual"] < 1e-4
