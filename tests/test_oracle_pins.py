@@ -386,3 +386,47 @@ def test_pair_solves_have_small_residuals(problem, gap):
     out = pair_blocks(np.array([0.0, 0.0]), 1.0, np.array([2.0 + gap, 0.0]), 1.0, ob, ob, PACKING, problem, 1.0)
     assert out["fine_residual"] < 1e-4
     assert out["peanut_residual"] < 1e-4
+
+
+@pytest.mark.parametrize("problem", ["resistance", "mobility"])
+def test_exclusion_form_equals_literal_algorithm3(problem):
+    """Algorithm 3 adds every source in Step 2a and then, in Step 2b and the
+    identity step, takes out the self terms and the pair-internal terms.  The
+    same vector is reached without any cancellation: u^(i) = mu^(i) plus the
+    fields of the disks that are not close to i with their full strengths,
+    plus, for each close partner k, the field of k's corrections from its
+    other pairs only (its own lam_bar and the (i, k) correction are already
+    inside the two-body solve).  This exclusion form is the one the device
+    matvec evaluates; written out here directly from the definitions, it
+    agrees with the literal form to rounding, so a sign, index or swapped
+    operand in the oracle's Step 2b (or in the exclusion bookkeeping) fails."""
+    p = PAIR_SMALL
+    c = np.array([[0.0, 0.0], [2.05, 0.0], [4.2, 0.3], [0.5, 2.3], [2.7, 2.2]])
+    s = System(c, np.ones(5), p, problem)
+    P, n = s.P, 2 * p.Nc
+    assert len(s.pairs) >= 2
+    mu = w.smooth_surface_vector(P, p.Mc, 3).reshape(P, -1)
+    lb = s.lam_bar(mu)
+    lam = lb.copy()
+    corr = {}                      # corr[(a, b)]: correction that pair (a, b) adds to disk a
+    for (i, k), blk in zip(s.pairs, s.blocks):
+        t = blk["A"] @ np.concatenate([lb[i], lb[k]])
+        lam[i] += t[:n]
+        lam[k] += t[n:]
+        corr[(i, k)], corr[(k, i)] = t[:n], t[n:]
+    sig = [s.proj(i, lam[i]) for i in range(P)]
+    u = np.empty_like(mu)
+    for i in range(P):
+        acc = mu[i].copy()
+        for k in range(P):
+            if k == i:
+                continue
+            if (k, i) in corr:
+                own = sum((v for (a, b), v in corr.items() if a == k and b != i), np.zeros(n))
+                acc += stokeslet(s.X[i], s.Y[k], p.mu) @ s.proj(k, own)
+            else:
+                acc += stokeslet(s.X[i], s.Y[k], p.mu) @ sig[k]
+        u[i] = acc
+    lit = s.matvec(mu)
+    # the literal form cancels strengths up to ~1e4 |mu|: rounding ~1e-16 x 1e4
+    assert np.linalg.norm(u - lit) < 1e-11 * np.linalg.norm(lit)
