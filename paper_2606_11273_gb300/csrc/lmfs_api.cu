@@ -106,7 +106,10 @@ static void free_ctx(Ctx& c) {
 }
 
 static int validate_params(const lmfs_params& p) {
-  if (p.Nc < 2 || p.Mc < 2 || p.Nfp < 2 || p.Mp < 2 || p.Nell < 1) return LMFS_ERR_INVALID;
+  if (p.Nc < 2 || p.Mc < 2 || p.Nfp < 2 || p.Mp < 2 || p.Nell < 1) {
+    set_last_error("Nc, Mc, Nfp and Mp must be >= 2 and Nell >= 1");
+    return LMFS_ERR_INVALID;
+  }
   if (2 * p.Nc > 256) { set_last_error("Nc must be <= 128"); return LMFS_ERR_INVALID; }
   if (p.Mc % 2) { set_last_error("Mc must be even"); return LMFS_ERR_INVALID; }
   const double Rc = p.Rc > 0 ? p.Rc : 1.0 - std::log(1e12) / p.Nc;
@@ -117,8 +120,15 @@ static int validate_params(const lmfs_params& p) {
   }
   if (!(p.gamma > 0 && p.gamma < 1) || !(p.af > 0) || !(p.aell >= 0) || !(p.delta_c >= 0) ||
       !(p.eps_trunc > 0) || !(p.eps_trunc_fine > 0) || !(p.mu > 0) || !(p.tol > 0) || p.maxit < 1 ||
-      !(p.rho >= 0) || (p.precision != LMFS_FP64 && p.precision != LMFS_MIXED && p.precision != LMFS_MIXED_DIRECT))
+      !(p.rho >= 0)) {
+    set_last_error("need 0 < gamma < 1, af > 0, aell >= 0, delta_c >= 0, eps_trunc > 0, "
+                   "eps_trunc_fine > 0, mu > 0, tol > 0, maxit >= 1, rho >= 0");
     return LMFS_ERR_INVALID;
+  }
+  if (p.precision != LMFS_FP64 && p.precision != LMFS_MIXED && p.precision != LMFS_MIXED_DIRECT) {
+    set_last_error("unknown precision");
+    return LMFS_ERR_INVALID;
+  }
   return LMFS_OK;
 }
 
@@ -287,6 +297,7 @@ int lmfs_params_default(lmfs_params* p) {
 int lmfs_create(const double* centres, const double* radii, int P, const lmfs_params* p, lmfs_handle* out) {
   if (!out) return LMFS_ERR_INVALID;
   *out = nullptr;
+  set_last_error("");
   lmfs_params prm;
   if (p) prm = *p; else lmfs_params_default(&prm);
   auto* h = new (std::nothrow) lmfs_ctx();

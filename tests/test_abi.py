@@ -72,3 +72,43 @@ def test_missing_library_fails_loudly(tmp_path):
             % str(tmp_path / "nope.so"))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT).stdout
     assert "IMPORTERROR" in out
+
+
+@pytest.mark.parametrize("case,kw,msg", [
+    ("zero radius", dict(radii=[1.0, 0.0]), "non-positive radius"),
+    ("negative radius", dict(radii=[1.0, -1.0]), "non-positive radius"),
+    ("NaN centre", dict(centres=[[0.0, 0.0], [float("nan"), 0.0]]), "non-finite centre"),
+    ("infinite radius", dict(radii=[1.0, float("inf")]), "non-finite centre"),
+    ("too few sources", dict(params=dict(Nc=20)), "source radii"),
+    ("odd Mc", dict(params=dict(Mc=71)), "Mc must be even"),
+    ("Nc over 128", dict(params=dict(Nc=200, Mc=240)), "Nc must be <= 128"),
+    ("tiny Mp", dict(params=dict(Mp=1)), ">= 2"),
+    ("gamma out of range", dict(params=dict(gamma=1.5)), "0 < gamma < 1"),
+    ("zero tolerance", dict(params=dict(tol=0.0)), "tol > 0"),
+    ("zero viscosity", dict(params=dict(mu=0.0)), "mu > 0"),
+    ("unknown precision", dict(params=dict(precision=7)), "unknown precision"),
+])
+def test_create_rejects_bad_input_before_the_device(lib, case, kw, msg):
+    """lmfs_create checks the parameters, the radii and the centres on the
+    host before its first CUDA call, so each rejection is LMFS_ERR_INVALID
+    with its own reason, on a machine with or without a GPU."""
+    import paper_2606_11273_gb300 as L
+    centres = kw.get("centres", [[0.0, 0.0], [2.5, 0.0]])
+    radii = kw.get("radii", [1.0, 1.0])
+    params = L.Params(**kw.get("params", {}))
+    with pytest.raises(L.LmfsError) as e:
+        L.Solver(centres, radii, params)
+    assert e.value.code == -1, case
+    assert msg in str(e.value), (case, str(e.value))
+
+
+def test_valid_input_without_a_gpu_fails_loudly(lib):
+    """Past the host checks the library goes to the device; with no GPU it
+    returns the CUDA error code instead of computing anything on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2606_11273_gb300 as L
+    with pytest.raises(L.LmfsError) as e:
+        L.Solver([[0.0, 0.0], [2.5, 0.0]], [1.0, 1.0])
+    assert e.value.code == -2
