@@ -1,0 +1,113 @@
+"""The seeded input generators meet the recipes they state: the packings of
+Sec. 6.2 (box side set by the area fraction, disks inside the box, every
+gap at or above the minimum, the closest pair snapped to it), the rigid-body
+inputs (zero net force for mobility, Sec. 6.1) and the serving stream.  Gaps
+are checked by brute force over a KD-tree of centres, independently of the
+generator's own sort-based pair search."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+spatial = pytest.importorskip("scipy.spatial")
+
+
+def all_gaps(pk, cutoff):
+    """Every pair with gap < cutoff: (i, k, gap), i < k."""
+    c, r = pk.centres, pk.radii
+    tree = spatial.cKDTree(c)
+    pairs = np.array(sorted(tree.query_pairs(2 * r.max() + cutoff)), dtype=np.int64).reshape(-1, 2)
+    g = np.linalg.norm(c[pairs[:, 0]] - c[pairs[:, 1]], axis=1) - r[pairs[:, 0]] - r[pairs[:, 1]]
+    keep = g < cutoff
+    return pairs[keep], g[keep]
+
+
+def check_packing(pk, phi, gmin, snap, inside=True):
+    """inside: every disk lies in the box (the square-lattice and random
+    starts); otherwise only every centre does (the hexagonal start's edge
+    sites sit a quarter spacing from the wall, so its largest edge disks
+    cross it, which matters to no gap: the flow domain is all of the plane)."""
+    Lx, Ly = pk.box
+    r, c = pk.radii, pk.centres
+    assert c.shape == (pk.P, 2) and r.shape == (pk.P,)
+    assert math.pi * np.sum(r ** 2) / (Lx * Ly) == pytest.approx(phi, rel=1e-12)
+    m = r[:, None] if inside else np.zeros((pk.P, 1))
+    assert np.all(c - m >= 0) and np.all(c + m <= np.array([Lx, Ly]))
+    pairs, g = all_gaps(pk, 0.5)
+    # the snapped pair sits at exactly the target gap; every other gap >= the minimum
+    assert pk.meta["snapped"] is not None
+    i, k, gs = pk.meta["snapped"]
+    assert gs == snap
+    d = np.linalg.norm(c[i] - c[k]) - r[i] - r[k]
+    assert d == pytest.approx(snap, abs=1e-12)
+    assert g.min() == pytest.approx(min(gmin, snap), abs=1e-12)
+    assert np.all(g >= min(gmin, snap) * (1 - 1e-9))
+    return pairs, g
+
+
+def test_p100_packing_recipe():
+    pk = w.packing_p100()
+    pairs, g = check_packing(pk, 0.40, 1e-2, 1e-2)
+    n_close = int(np.sum(g <= 0.2))
+    assert 20 <= n_close <= 60                      # 37 close pairs at the fixed seed
+    again = w.packing_p100()
+    assert np.array_equal(again.centres, pk.centres)
+    assert not np.array_equal(w.packing_p100(seed=3).centres, pk.centres)
+
+
+def test_p1000_polydisperse_packing_recipe():
+    pk = w.packing_p1000_poly()
+    assert pk.radii.min() >= 0.8 and pk.radii.max() <= 1.2
+    # the radii are a permutation of the seeded U[0.8, 1.2] draw
+    rng = np.random.Generator(np.random.PCG64(3 + 1000))
+    assert np.array_equal(np.sort(pk.radii), np.sort(rng.uniform(0.8, 1.2, size=1000)))
+    pairs, g = check_packing(pk, 0.60, 1e-3, 1e-3, inside=False)
+    assert int(np.sum(g < 0.1)) > 50                # close pairs (gap < 0.1): 122 at the fixed seed
+
+
+def test_p10000_packing_is_the_papers_kind():
+    """The P = 10^4 packing has the parameters of the paper's large example
+    (unit disks, area fraction 0.65, minimum separation 1e-3, Sec. 1.1) on
+    the square-lattice start of Sec. 6.2 (spacing 2.198), and a close-pair
+    count (gap <= 0.2) within 10 % of the 9920 the paper reports for its own
+    random packing of that kind."""
+    pk = w.packing_p10000()
+    assert np.all(pk.radii == 1.0)
+    assert pk.box[0] / 100 == pytest.approx(2.198, abs=5e-4)
+    pairs, g = check_packing(pk, 0.65, 1e-3, 1e-3)
+    n_close = int(np.sum(g <= 0.2))
+    assert abs(n_close - 9920) <= 992
+
+
+def test_rigid_inputs():
+    v = w.rigid_velocities(50, 11)
+    assert v.shape == (50, 3) and np.array_equal(v, w.rigid_velocities(50, 11))
+    ft = w.forces_torques(500, 5)
+    assert np.abs(ft[:, :2].sum(axis=0)).max() < 1e-12       # zero net force (Sec. 6.1)
+    raw = np.random.Generator(np.random.PCG64(5)).standard_normal((500, 3))
+    assert np.array_equal(ft[:, 2], raw[:, 2])               # torques are not shifted
+    assert np.allclose(ft[:, :2] - raw[:, :2], ft[0, :2] - raw[0, :2])  # one common shift
+
+
+def test_smooth_surface_vector_is_band_limited():
+    Mc = 72
+    f = w.smooth_surface_vector(7, Mc, 3, modes=4)
+    spec = np.abs(np.fft.rfft(f, axis=1))
+    assert spec[:, 5:, :].max() < 1e-12 * spec.max()
+    assert spec[:, :5, :].max() > 0.1
+
+
+def test_serving_stream():
+    """Small disk counts at area fractions up to 0.65 included: the draw is
+    capped at what the square-lattice start admits."""
+    s = w.serving_stream(40, seed=1, pmin=20, pmax=200)
+    t = np.array([x[0] for x in s])
+    assert np.all(np.diff(t) > 0) and t[0] > 0
+    for arrival, pk, problem, data in s:
+        assert 20 <= pk.P <= 200 and 0.3 <= pk.meta["phi"] <= 0.65
+        check_packing(pk, pk.meta["phi"], pk.meta["gmin"], pk.meta["gmin"])
+        assert problem in (0, 1) and data.shape == (pk.P, 3)
+        if problem == 1:
+            assert np.abs(data[:, :2].sum(axis=0)).max() < 1e-12

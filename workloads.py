@@ -288,7 +288,11 @@ def serving_stream(n, seed=0, pmin=50, pmax=5000, mean_gap_s=0.02):
     square-lattice packing with P log-uniform in [pmin, pmax], area fraction
     uniform in [0.3, 0.65], minimum gap log-uniform in [1e-3, 1e-1] (the
     closest pair snapped to it), resistance or mobility with probability 1/2,
-    inputs N(0, 1) as rigid_velocities / forces_torques.
+    inputs N(0, 1) as rigid_velocities / forces_torques.  A square lattice of
+    ceil(sqrt(P))^2 sites reaches only area fraction P pi / ((2 + gmin)
+    ceil(sqrt(P)))^2 with every gap >= gmin, which is below 0.65 for small P
+    that are not squares; the drawn area fraction is capped there (a draw
+    under the cap is unchanged).
     Returns a list of (arrival_s, Packing, problem (0 resistance, 1 mobility),
     inputs [P, 3])."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -298,6 +302,8 @@ def serving_stream(n, seed=0, pmin=50, pmax=5000, mean_gap_s=0.02):
         P = int(round(math.exp(rng.uniform(math.log(pmin), math.log(pmax)))))
         phi = float(rng.uniform(0.3, 0.65))
         gmin = float(10 ** rng.uniform(-3, -1))
+        n_side = int(math.ceil(math.sqrt(P)))
+        phi = min(phi, (1 - 1e-9) * P * math.pi / ((2 + gmin) * n_side) ** 2)
         problem = int(rng.integers(0, 2))
         pk = packing(P, phi, 1000 + q, gmin=gmin, start="square", nsweep=3, snap_gap=gmin)
         data = rigid_velocities(P, 5000 + q) if problem == 0 else forces_torques(P, 5000 + q)
