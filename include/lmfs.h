@@ -18,8 +18,10 @@
  *     LMFS_MOBILITY (forces in, velocities out; Sec. 4).
  *
  * Threading: a handle may be used from one host thread at a time.  All GPU
- * work of a handle is ordered on the stream given in lmfs_params.stream (the
- * legacy default stream when NULL).
+ * work of a handle is ordered on the stream given in lmfs_params.stream; when
+ * that is NULL the handle creates a non-blocking stream of its own (GMRES
+ * steps are captured as CUDA graphs, which the legacy default stream cannot
+ * hold) and destroys it with the handle.
  */
 #ifndef LMFS_H
 #define LMFS_H
@@ -79,7 +81,7 @@ typedef struct lmfs_params {
   int    maxit;          /* GMRES iteration limit (300)                          */
   double rho;            /* peanut rolling radius; 0: smallest disk radius       */
   int    precision;      /* LMFS_FP64, LMFS_MIXED or LMFS_MIXED_DIRECT (lmfs_solve) */
-  void*  stream;         /* cudaStream_t for all work of the handle (NULL: default) */
+  void*  stream;         /* cudaStream_t for all work of the handle (NULL: own one) */
   int    device;         /* CUDA device ordinal (0)                              */
 } lmfs_params;
 
@@ -98,8 +100,10 @@ int lmfs_params_default(lmfs_params* p);
 
 /* Create a handle for P disks.  centres: host [P][2] (x, y), radii: host [P].
  * Validates P >= 1, finite positive radii, finite centres, every gap > 0, and
- * parameters (Nc, Mc, Nfp, Mp >= 2, source radii in (0, 1)); otherwise
- * LMFS_ERR_INVALID.  Runs contact detection (pairs with gap <= delta_c,
+ * parameters (Nc, Mc, Nfp, Mp >= 2, Nell >= 1, Nc <= 128, Mc even, source radii
+ * in (0, 1), positive tolerances and viscosity, a known precision); otherwise
+ * LMFS_ERR_INVALID, with the reason in lmfs_strerror's text.  Everything but
+ * the gap check runs on the host before the first CUDA call.  Runs contact detection (pairs with gap <= delta_c,
  * Algorithm 2, precomputation) on the device.  Allocates device memory. */
 int lmfs_create(const double* centres, const double* radii, int P,
                 const lmfs_params* p, lmfs_handle* out);
