@@ -58,7 +58,8 @@ struct lmfs_server {
   std::condition_variable cv_done;       // pollers wake on completion
   std::deque<std::shared_ptr<Request>> queue;
   std::map<uint64_t, std::shared_ptr<Request>> all;
-  std::vector<std::thread> slots;
+  std::vector<std::thread> slots;               // request threads not yet joined
+  std::vector<std::thread::id> finished;        // request threads that have returned
   std::thread dispatcher;
   size_t in_use = 0;
   int running = 0;
@@ -120,10 +121,22 @@ void release(Active& a) {
   a.h = nullptr; a.ev_pre = a.ev_step = nullptr; a.st = nullptr;
 }
 
+// Marks the calling request thread as returned, so that the dispatcher joins
+// it (and its stack is freed) instead of keeping it until the server ends.
+struct ReapOnExit {
+  lmfs_server* s;
+  ~ReapOnExit() {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->finished.push_back(std::this_thread::get_id());
+    s->cv_dispatch.notify_all();
+  }
+};
+
 // One admitted request: its handle on its own stream; then either the whole
 // solve here (streams engine) or the precompute, right-hand side and first
 // Krylov vector here and the Arnoldi steps on the engine.
 void run_request(lmfs_server* s, std::shared_ptr<Request> rq) {
+  ReapOnExit reap{s};                             // runs last, on either return
   cudaSetDevice(s->sp.device);
   auto a = std::make_unique<Active>();
   a->rq = rq;
@@ -250,14 +263,36 @@ void engine_loop(lmfs_server* s) {
   if (est) cudaStreamDestroy(est);
 }
 
+// Join the request threads that have returned (called with s->mu held through
+// lk; the joins run unlocked).  A thread's id is always in slots by the time it
+// is listed as finished: it is added under the lock it needs to list itself.
+void reap_finished(lmfs_server* s, std::unique_lock<std::mutex>& lk) {
+  std::vector<std::thread> done;
+  for (const std::thread::id id : s->finished) {
+    auto it = std::find_if(s->slots.begin(), s->slots.end(), [&](const std::thread& t) { return t.get_id() == id; });
+    if (it != s->slots.end()) {
+      done.push_back(std::move(*it));
+      s->slots.erase(it);
+    }
+  }
+  s->finished.clear();
+  lk.unlock();
+  for (auto& t : done) t.join();
+  lk.lock();
+}
+
 void dispatch_loop(lmfs_server* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     s->cv_dispatch.wait(lk, [&] {
-      if (s->stop) return true;
+      if (s->stop || !s->finished.empty()) return true;
       if (s->queue.empty() || s->running >= s->sp.max_slots) return false;
       return s->in_use + s->queue.front()->bytes <= s->sp.hbm_budget_bytes;
     });
+    if (!s->finished.empty()) {
+      reap_finished(s, lk);
+      continue;
+    }
     if (s->stop) break;
     // FIFO admission: the head waits until it fits (no starvation of large requests)
     auto rq = s->queue.front();
