@@ -22,6 +22,14 @@
  * that is NULL the handle creates a non-blocking stream of its own (GMRES
  * steps are captured as CUDA graphs, which the legacy default stream cannot
  * hold) and destroys it with the handle.
+ *
+ * Device memory: the library allocates from one stream-ordered pool per device
+ *   of its own (not from the caller's allocator), ordered on the handle's
+ *   stream.  Freed blocks stay in the pool for reuse by later handles and
+ *   requests, so after a handle is destroyed the process keeps the peak of
+ *   what the library used reserved until it exits; other allocators in the
+ *   process (e.g. PyTorch's caching allocator) cannot use that memory.
+ *   lmfs_stokeslet_sum_noalloc is the one entry point that never allocates.
  */
 #ifndef LMFS_H
 #define LMFS_H
