@@ -274,6 +274,13 @@ int lmfs_submit(lmfs_server* s, const double* centres, const double* radii, int 
  * wait expired, or the request's own error code. */
 int lmfs_poll(lmfs_server* s, uint64_t ticket, double* out, lmfs_solve_info* info,
               int timeout_us);
+/* The server keeps a finished request's result (out [P][3], info, status; its
+ * inputs are freed when it finishes) so that it can be polled any number of
+ * times, until the request is forgotten or the server is destroyed.  Forget
+ * drops that record: LMFS_OK, LMFS_ERR_STATE if the request has not finished
+ * (it stays), LMFS_ERR_INVALID for an unknown or already forgotten ticket.
+ * A long-running caller forgets each request once it has read the result. */
+int lmfs_server_forget(lmfs_server* s, uint64_t ticket);
 int lmfs_server_destroy(lmfs_server* s);
 
 #ifdef __cplusplus

@@ -187,6 +187,10 @@ class Server:
         rc = self.lib.lmfs_poll(self.s, ticket, _ptr(out), ctypes.byref(info), int(timeout_us))
         return rc, out, Solver._info(info, rc)
 
+    def forget(self, ticket):
+        """Drop a finished request's record; returns the status code."""
+        return self.lib.lmfs_server_forget(self.s, ticket)
+
     def close(self):
         if self.s:
             self.lib.lmfs_server_destroy(self.s)

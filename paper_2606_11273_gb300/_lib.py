@@ -90,6 +90,7 @@ SIGNATURES = {
     "lmfs_server_create": (_i, [_P(lmfs_server_params), _P(_vp)]),
     "lmfs_submit": (_i, [_vp, _vp, _vp, _i, _i, _vp, _P(lmfs_params), _P(ctypes.c_uint64)]),
     "lmfs_poll": (_i, [_vp, ctypes.c_uint64, _vp, _P(lmfs_solve_info), _i]),
+    "lmfs_server_forget": (_i, [_vp, ctypes.c_uint64]),
     "lmfs_server_destroy": (_i, [_vp]),
 }
 

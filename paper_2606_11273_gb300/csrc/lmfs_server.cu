@@ -105,6 +105,10 @@ size_t estimate_bytes(const double* c, const double* r, int P, const lmfs_params
 
 void complete(lmfs_server* s, const std::shared_ptr<Request>& rq, int rc) {
   std::lock_guard<std::mutex> lk(s->mu);
+  // the inputs are no longer read; the record keeps only the result
+  std::vector<double>().swap(rq->centres);
+  std::vector<double>().swap(rq->radii);
+  std::vector<double>().swap(rq->in);
   rq->rc = rc;
   rq->t_end = std::chrono::steady_clock::now();
   s->in_use -= rq->bytes;
@@ -364,6 +368,16 @@ int lmfs_poll(lmfs_server* s, uint64_t ticket, double* out, lmfs_solve_info* inf
     *info = rq->info;
   }
   return rq->rc;
+}
+
+int lmfs_server_forget(lmfs_server* s, uint64_t ticket) {
+  if (!s) return LMFS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return LMFS_ERR_INVALID;
+  if (it->second->rc == LMFS_PENDING) return LMFS_ERR_STATE;
+  s->all.erase(it);
+  return LMFS_OK;
 }
 
 int lmfs_server_destroy(lmfs_server* s) {

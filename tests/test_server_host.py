@@ -88,6 +88,11 @@ def test_submit_and_poll_error_codes(lib):
     assert rc == 0
     assert lib.lmfs_poll(s, tk, None, None, 10_000_000) == -2
     assert lib.lmfs_poll(s, tk, None, None, 0) == -2
+    # forgetting drops the finished record: the ticket is then unknown
+    assert lib.lmfs_server_forget(s, tk) == 0
+    assert lib.lmfs_poll(s, tk, None, None, 0) == -1
+    assert lib.lmfs_server_forget(s, tk) == -1
+    assert lib.lmfs_server_forget(None, tk) == -1
     assert lib.lmfs_server_destroy(s) == 0
     assert lib.lmfs_server_destroy(None) == -1
 
