@@ -281,6 +281,10 @@ int lmfs_poll(lmfs_server* s, uint64_t ticket, double* out, lmfs_solve_info* inf
  * (it stays), LMFS_ERR_INVALID for an unknown or already forgotten ticket.
  * A long-running caller forgets each request once it has read the result. */
 int lmfs_server_forget(lmfs_server* s, uint64_t ticket);
+/* Stop the server: waits for the requests already running to finish, drops
+ * the queued ones that have not started, joins every thread and frees all
+ * records; tickets are invalid afterwards.  No other call on `s` may run
+ * concurrently with it or follow it. */
 int lmfs_server_destroy(lmfs_server* s);
 
 #ifdef __cplusplus
