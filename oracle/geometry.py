@@ -45,8 +45,9 @@ def limiting_points(d, r1, r2):
     """Distances p1 (from c1) and p2 (from c2) of the two limiting points of
     the circles, i.e. where successive image reflections accumulate.  For
     r1 = r2 = 1, d = 2 + delta this is R_acc(delta) = 1 + delta/2 -
-    sqrt(delta + delta^2/4) (Sec. 5).  Unequal radii are this build's
-    extension (parity unpinned against the paper)."""
+    sqrt(delta + delta^2/4) (Sec. 5).  Unequal radii go beyond the paper,
+    which treats equal disks only: parity unpinned against it, pinned by the
+    two points being mutual inverses in both circles."""
     a = d * d + r1 * r1 - r2 * r2
     p1 = (a - math.sqrt(max(a * a - 4.0 * d * d * r1 * r1, 0.0))) / (2.0 * d)
     b = d * d + r2 * r2 - r1 * r1
