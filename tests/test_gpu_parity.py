@@ -236,8 +236,8 @@ def test_three_disk_chain_resistance(L):
 
 
 def test_polydisperse_mobility(L):
-    """Unequal radii (this build's extension: limiting points of unequal
-    circles, rolling radius = smallest radius)."""
+    """Unequal radii, beyond the paper's equal disks: limiting points of
+    unequal circles, rolling radius = smallest radius."""
     rng = np.random.default_rng(7)
     r = rng.uniform(0.8, 1.2, 8)
     pk = w.packing(8, 0.45, 11, gmin=1e-3, radii=r, start="hex", nsweep=10, snap_gap=2e-3)
