@@ -581,7 +581,7 @@ def main():
                     help="run one small bounded case for an ncu capture and exit")
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: served mixed precision against one-at-a-time FP64 (side report)")
-    ap.add_argument("--requests", type=int, default=64, help="serving: requests in the stream (config: 256)")
+    ap.add_argument("--requests", type=int, default=64, help="serving: requests in the stream (the full stream has 256)")
     ap.add_argument("--pmax", type=int, default=5000, help="serving: largest disk count")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent request slots")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 1],

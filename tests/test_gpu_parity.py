@@ -102,7 +102,7 @@ def test_single_disk_closed_forms(L, prec):
     assert np.allclose(v[0], [0.3 * m, 1.1 * m, -2.0 / (4 * math.pi)], rtol=1e-10, atol=1e-12)
 
 
-# ----------------------------------------------------------------- config 1
+# ------------------------------------------------- two unit disks at gap 1e-3
 @pytest.fixture(scope="module")
 def pair1():
     pk = w.two_disks(1e-3)
@@ -137,7 +137,7 @@ def test_two_disks_pair_blocks(L, pair1):
     assert np.array_equal(s.pairs(), np.array([[0, 1]]))
 
 
-# ----------------------------------------------------------------- config 2
+# ------------------------------------ P = 100 packing at area fraction 0.40
 @pytest.fixture(scope="module")
 def p100():
     pk = w.packing_p100()
