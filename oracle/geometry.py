@@ -13,6 +13,9 @@ def radius_rule(N, eps=1e-12):
 
 
 def ring(c, rad, n, offset=0.0):
+    """n equispaced points on the circle of radius rad about c, starting at
+    angle 2 pi offset / n in the global frame (the coarse and proxy rings of
+    Sec. 3 and Sec. 5)."""
     t = 2.0 * np.pi * (np.arange(n) + offset) / n
     return np.stack([c[0] + rad * np.cos(t), c[1] + rad * np.sin(t)], axis=1)
 

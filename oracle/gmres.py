@@ -5,6 +5,9 @@ import numpy as np
 
 
 def gmres(matvec, b, tol, maxit):
+    """Solve A x = b for the operator `matvec` (Algorithm 2's GMRES on the
+    two-body system, Algorithm 3 as the matvec).  Returns x and a record
+    with the iteration count, the final relative residual and its history."""
     n = b.size
     beta = np.linalg.norm(b)
     hist = [1.0]

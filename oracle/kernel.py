@@ -58,10 +58,13 @@ class TSVD:
         self.VSi = (Vt[:r].T / s[:r]).copy()
 
     def apply(self, b):
+        """x = V Sigma^+ (U^T b): U^T b first, as eq. (howG+) prescribes."""
         return self.VSi @ (self.Ut @ b)
 
 
 def blockdiag(*mats):
+    """Block-diagonal matrix of the given blocks (the blkdiag of the pair
+    systems, e.g. blockdiag(K^(1,2)T, K^(2,1)T) in eq. (force_ext))."""
     rows = sum(m.shape[0] for m in mats)
     cols = sum(m.shape[1] for m in mats)
     out = np.zeros((rows, cols))

@@ -35,4 +35,5 @@ class OneBody:
         self.pinv = TSVD(M, p.eps_trunc)
 
     def apply_pinv(self, mu):
+        """lam_bar = P^+ mu (resistance) or S_L^+ mu (mobility)."""
         return self.pinv.apply(mu)

@@ -66,6 +66,8 @@ class System:
         return np.stack([self.ob[i].apply_pinv(mu[i].ravel()) for i in range(self.P)])
 
     def proj(self, i, lam):
+        """Strengths fed to Stokeslet sums: lam itself for resistance,
+        (I - L) lam for mobility (Sec. 4.4)."""
         return self.ob[i].proj @ lam
 
     def far_field(self, sig, targets):
