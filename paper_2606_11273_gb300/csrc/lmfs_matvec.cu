@@ -37,6 +37,8 @@ __device__ __forceinline__ double wsum(double v) {
 
 
 // ---- Step 1a: lam_bar = Pi^+ mu, one block per disk, one thread per row ----
+// (Algorithm 3, Step 1a; Pi^+ = P^+ of eq. (howG+), or S_L^+ of eq. (SL) for
+// mobility.)
 // Pi^+ applied from its QR factors: t = W mu (W = first r rows of Q^T, stored
 // column by column, Wt[col][row], so that the rows read together are
 // contiguous), z = R^{-1} t with the triangular inverse formed once per
@@ -120,6 +122,7 @@ __global__ void onebody_rinv_kernel(const double* __restrict__ R, const int* __r
 }
 
 // ---- Step 1b: lam~ = A [lam_bar_i; lam_bar_k] per close pair ----------------
+// (Algorithm 3, Step 1b; eq. (correction), A from eq. (Amat).)
 // A is stored column by column ([C][col][row]).  Block (c, y) takes rows
 // 32 y .. 32 y + 31 of pair c: warp g sums the columns of group g (a strided
 // eighth of them) for its lane's row, so every load of A is a coalesced
@@ -291,6 +294,8 @@ __global__ void targets_as_disks(const double* __restrict__ t, int nt, float2* _
 }
 
 // ---- Step 2a far field, FP32 ------------------------------------------------
+// (Algorithm 3, Step 2a: the Stokeslet sum of eq. (stokes_sum) over coarse
+// sources, by direct tiles.)
 // Per (target x, source disk k) with X = x - c_k (double-float centres) and
 // R^2 = |X|^2, the disk's sum is split exactly as
 //   sum_j S(X - y_j) s_j = S_0(X) sum_j s_j + sum_j [ -1/2 log(r_j^2/R^2) s_j
@@ -493,6 +498,8 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
 }
 
 // ---- Step 2a far field by per-disk multipole expansions --------------------
+// (Algorithm 3, Step 2a: eq. (stokes_sum) with each disk's sources replaced by
+// their expansion about the disk centre outside the near zone.)
 // The coarse strengths of a disk that carries pair corrections have Fourier
 // modes that grow like (1/R_c)^m (the peanut least squares of eq. (peanut)
 // fits the fine field with coarse sources), so a direct sum over them in FP32
@@ -962,7 +969,9 @@ __global__ void near_kernel(int mode, const double* __restrict__ centres, const 
   }
 }
 
-// Per target node: the disk's near entries added in list order, and assembly.
+// Per target node: the disk's near entries added in list order, and assembly
+// of u = mu + far + near (Algorithm 3, Step 2b and the identity step, in the
+// exclusion form derived at the top of this file).
 __global__ void near_reduce(int mode, const int* __restrict__ near_off, const int4* __restrict__ near_ent,
                             const double* __restrict__ part, int P, int Mc, const double* __restrict__ mu,
                             const double* __restrict__ ufar, double cmu, double* __restrict__ u) {
@@ -1022,7 +1031,8 @@ __global__ void pair_E_kernel(const double* __restrict__ E, const int* __restric
   }
 }
 
-// out_i = sgn K^T lam_bar_i + sum over incident pairs of their E share;
+// out_i = sgn K^T lam_bar_i + sum over incident pairs of their E share
+// (eq. (two_force) with eq. (force_ext) for resistance, eq. (rbm2) for mobility);
 // segmented warp-shuffle reduction per disk.
 __global__ void post_kernel(const double* __restrict__ lb, const double* __restrict__ e6,
                             const int* __restrict__ csr_off, const int* __restrict__ csr_ent, int P, int Nc,

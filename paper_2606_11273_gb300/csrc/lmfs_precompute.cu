@@ -88,7 +88,8 @@ __global__ void fill_onebody(double* A, int ld, long long mstride, const double*
 }
 
 // Extract W (rank rows of Q^T, stored column by column: Wt[col][row]) and R
-// (upper 2Nc x 2Nc, column-major) from the factored [M | I].
+// (upper 2Nc x 2Nc, column-major) from the factored [M | I]: the factors of
+// the one-body pseudo-inverse P^+ (eq. (howG+)) or S_L^+ (eq. (SL)).
 __global__ void extract_onebody(const double* A, int ld, long long mstride, int Nc, int Mc,
                                 const int* rank, double* W, double* R) {
   const int b = blockIdx.y;
@@ -342,6 +343,8 @@ __global__ void project_FQ_mobility(PairDims pd, PairGeo g, const double* Yf, co
 // work.  Truncation is relative to each half's own largest column.
 __device__ __forceinline__ int sym_src(int b, int Nfp) { return b < Nfp ? (b + Nfp / 2) % Nfp : b; }
 
+// The fine pair system F Z = blkQ (eq. (bfm)) split by the half-turn symmetry
+// of an equal-radius pair into two half systems:
 // [A +- B | Q] for matrix 2b (+) and 2b + 1 (-): rows 2 nX (side-1 nodes),
 // columns 2 nY1 (side-1 sources) then 2 Nc (disk-2 coarse sources in image
 // order); column-major, leading dimension ld.
@@ -393,7 +396,8 @@ __global__ void fill_FQ_sym(PairDims pd, PairGeo g, const double* Yf, const doub
   }
 }
 
-// Mobility maps on the half problems: source columns times (I - L_f,1) plus
+// Mobility maps on the half problems (the mobility form of eq. (bfm), Sec. 4.3):
+// source columns times (I - L_f,1) plus
 // B_f,1 K_f,1^T (both halves), coarse columns times the ring projector.
 __global__ void project_FQ_mobility_sym(PairDims pd, PairGeo g, const double* Yf, const double* Xf, double* W,
                                         int ld, long long mstride, const double* Gf) {
@@ -503,7 +507,8 @@ __global__ void split_C_sym(int Nc, int Mp, const double* W2, int ldc, long long
 }
 
 // A = -1/2 [[Xp + Xm, Xp - Xm], [Xp - Xm, Xp + Xm]] in (disk 1, disk 2 image)
-// order, stored row-major [4Nc][4Nc] in the natural order.
+// order (eq. (Amat) assembled from its two half solutions), stored column by
+// column [4Nc cols][4Nc rows] in the natural order.
 __global__ void assemble_A_sym(int Nc, const double* X, int xld, long long xstride, double* A, int Cfirst) {
   const int b = blockIdx.y;
   const int n4 = 4 * Nc, nh = 2 * Nc;
@@ -642,7 +647,8 @@ __global__ void fill_DC(PairDims pd, PairGeo g, const double* Yf, const double* 
   }
 }
 
-// C (I - L^pair) in place: per row, per disk, ring projector.
+// C (I - L^pair) in place: per row, per disk, ring projector (the mobility
+// form of the peanut system of eq. (Amat), Sec. 4.4).
 __global__ void project_C(PairDims pd, PairGeo g, double* W2, int ld2, long long w2stride, int Mp) {
   const int b = blockIdx.y, q = g.first + b, Nc = pd.Nc;
   double* Cb = W2 + (long long)b * w2stride;
@@ -706,7 +712,7 @@ __global__ void gemm_batched(const double* Am, int lda, long long sa, const doub
   }
 }
 
-// A = -X (row-major [4Nc][4Nc]) from the column-major solution X.
+// A = -X (eq. (Amat): X solves C X = D Z), stored column by column like X.
 __global__ void store_A(const double* X, int xld, long long xstride, int n4, double* A, int Cfirst) {
   const int b = blockIdx.y;
   const double* Xb = X + (long long)b * xstride;
