@@ -4,9 +4,10 @@
 //   mu, u, b            [P][Mc][2]      surface vectors (x, y interleaved)
 //   lb, lam, sig        [P][Nc][2]      one-body, corrected and projected strengths
 //   tilde               [C][4Nc]        per-pair corrections  A [lb_i; lb_k]
-//   A                   [C][4Nc][4Nc]   row-major;  E [C][6][4Nc]
-//   one-body factors per radius class: W [2Nc][2Mc] (rows < rank used),
-//   R [2Nc][2Nc] column-major upper triangle, perm [2Nc], rank
+//   A                   [C][4Nc][4Nc]   column by column ([col][row]);  E [C][6][4Nc]
+//   one-body factors per radius class: W = rows < rank of Q^T, stored column
+//   by column (Wt [2Mc][2Nc]); R and R^{-1} [2Nc][2Nc] column-major upper
+//   triangles, perm [2Nc], rank
 //   far-field FP32 sources: src4 [P][Nc] float4 (y_x, y_y, |y|^2, y.sigma),
 //   src2 [P][Nc] float2 (sigma_x, sigma_y), disk data dsk [P] float4x2.
 #pragma once
