@@ -8,8 +8,8 @@
 //   one-body factors per radius class: W = rows < rank of Q^T, stored column
 //   by column (Wt [2Mc][2Nc]); R and R^{-1} [2Nc][2Nc] column-major upper
 //   triangles, perm [2Nc], rank
-//   far-field FP32 sources: src4 [P][Nc] float4 (y_x, y_y, |y|^2, y.sigma),
-//   src2 [P][Nc] float2 (sigma_x, sigma_y), disk data dsk [P] float4x2.
+//   far-field FP32 sources: src4 [P][Nc][2] float4, (y_x, y_y, |y|^2, y.sigma)
+//   and (sigma_x, sigma_y, 0, 0) per source; disk data dsk32 [P][2] float4.
 #pragma once
 #include <algorithm>
 #include <chrono>
@@ -136,7 +136,6 @@ struct Ctx {
   double* ufar = nullptr;
   double* lam0 = nullptr;
   float4* src4 = nullptr;
-  float2* src2 = nullptr;
   int far_split = 1;                 // largest source-range split of the far kernels
   int split_direct = 1, kchunk_direct = 1;   // far32_kernel (LMFS_MIXED_DIRECT)
   int split_m2p32 = 1, kchunk_m2p32 = 1;     // m2p_kernel<float> (LMFS_MIXED)
