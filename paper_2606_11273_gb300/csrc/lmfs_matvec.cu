@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
   for (int tile = 0; tile < ntile; ++tile) {
     const int buf = tile & 1;
     if (threadIdx.x == 0 && tile + 1 < ntile) issue(tile + 1);
-    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) { s_fail = 1; }
+    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) { s_fail = tile + 1; }
     __syncthreads();
     if (s_fail) break;
     const int kb = k_begin + tile * F_TILE;
@@ -485,7 +485,10 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
     }
     __syncthreads();
   }
-  if (s_fail) { if (threadIdx.x == 0) atomicExch(a.err, 1); return; }
+  if (s_fail) {
+    if (threadIdx.x == 0) { mbar_drain2(bars, s_fail - 1, ntile); atomicExch(a.err, 1); }
+    return;
+  }
   if (active) {
     double* o = a.out + blockIdx.y * a.out_stride;
 #pragma unroll
@@ -727,7 +730,7 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
   for (int tile = 0; tile < ntile; ++tile) {
     const int buf = tile & 1;
     if (threadIdx.x == 0 && tile + 1 < ntile) issue(tile + 1);
-    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = 1;
+    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = tile + 1;
     __syncthreads();
     if (s_fail) break;
     const int kb = k_begin + tile * M_TILE;
@@ -819,7 +822,10 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
     }
     __syncthreads();
   }
-  if (s_fail) { if (threadIdx.x == 0) atomicExch(a.err, 1); return; }
+  if (s_fail) {
+    if (threadIdx.x == 0) { mbar_drain2(bars, s_fail - 1, ntile); atomicExch(a.err, 1); }
+    return;
+  }
   if (active) {
     double* o = a.out + by * a.out_stride;
 #pragma unroll
@@ -1163,7 +1169,7 @@ __global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel
   for (int tile = 0; tile < ntile; ++tile) {
     const int buf = tile & 1;
     if (threadIdx.x == 0 && tile + 1 < ntile) issue(tile + 1);
-    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = 1;
+    if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = tile + 1;
     __syncthreads();
     if (s_fail) break;
     const int nd = min(FL, k_end - (k_begin + tile * FL));
@@ -1221,7 +1227,10 @@ __global__ void __launch_bounds__(F_THREADS, TPT == 2 ? 5 : 3) far32_lean_kernel
     }
     __syncthreads();
   }
-  if (s_fail) { if (threadIdx.x == 0) atomicExch(a.err, 1); return; }
+  if (s_fail) {
+    if (threadIdx.x == 0) { mbar_drain2(bars, s_fail - 1, ntile); atomicExch(a.err, 1); }
+    return;
+  }
   double* o = a.out + blockIdx.y * a.out_stride;
   bool bad = false;
 #pragma unroll

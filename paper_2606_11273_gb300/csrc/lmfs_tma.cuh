@@ -37,4 +37,12 @@ static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
   return false;
 }
 
+// After the wait on tile `failed` of a two-buffer pipeline (tile t + 1 issued
+// before tile t is waited on) ran out: wait, with the same bound, for the
+// copies that may still be landing in shared memory (tiles `failed` and
+// `failed` + 1), so that the block leaves none in flight when it returns.
+static __device__ __forceinline__ void mbar_drain2(uint64_t* bars, int failed, int ntile) {
+  for (int t = failed; t < ntile && t <= failed + 1; ++t) mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1));
+}
+
 }  // namespace lmfs
