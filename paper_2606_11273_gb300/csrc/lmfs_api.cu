@@ -206,6 +206,19 @@ static int ensure_precompute(Ctx& c, int problem) {
   return LMFS_OK;
 }
 
+// The far-field kernels' error flags (c.far_err: [0] a bounded wait expired,
+// [1] a target too close to an unexcluded source disk for the direct series)
+// are read once per solve, with the solve's final synchronisation.  The near
+// zone keeps [1] clear by construction; either flag means the result is void.
+static int sync_and_check_far_flags(Ctx& c) {
+  int herr[2] = {0, 0};
+  LMFS_CUDA(cudaMemcpyAsync(herr, c.far_err, sizeof(herr), cudaMemcpyDeviceToHost, c.stream));
+  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  if (herr[0]) { set_last_error("far field: a bounded wait expired"); return LMFS_ERR_CUDA; }
+  if (herr[1]) { set_last_error("far field: a target inside a source disk's series radius"); return LMFS_ERR_CUDA; }
+  return LMFS_OK;
+}
+
 static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
   if (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) return LMFS_ERR_INVALID;
   const auto t0 = std::chrono::steady_clock::now();
@@ -218,7 +231,7 @@ static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev,
   int rc = gmres_solve(c, problem, c.prm.precision, c.bvec, c.xsol, &loc);
   if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
   LMFS_TRY(post_device(c, problem, c.xsol, out_dev));
-  LMFS_CUDA(cudaStreamSynchronize(c.stream));
+  LMFS_TRY(sync_and_check_far_flags(c));
   c.have_solution = true;
   const auto t2 = std::chrono::steady_clock::now();
   if (info) {
@@ -266,6 +279,7 @@ int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* o
     rc = LMFS_ERR_CUDA;
   dfree(outd);
   if (rc != LMFS_OK) return rc;
+  LMFS_TRY(sync_and_check_far_flags(c));
   c.have_solution = true;
   const auto t2 = std::chrono::steady_clock::now();
   if (info) {
