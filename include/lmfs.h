@@ -51,7 +51,8 @@ extern "C" {
 #define LMFS_ERR_STATE         -5   /* call out of order (e.g. no precompute)   */
 #define LMFS_ERR_TIMEOUT       -6   /* lmfs_poll gave up after its time limit   */
 #define LMFS_ERR_TOO_LARGE     -7   /* request alone exceeds the memory budget  */
-#define LMFS_ERR_NUMERICAL     -8   /* a factorization produced a non-finite value */
+#define LMFS_ERR_NUMERICAL     -8   /* a factorization failed: a non-finite value,
+                                       or one of its bounded waits expired         */
 
 #define LMFS_RESISTANCE 0
 #define LMFS_MOBILITY   1

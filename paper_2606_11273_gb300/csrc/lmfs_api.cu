@@ -566,7 +566,7 @@ const char* lmfs_strerror(int code) {
     case LMFS_ERR_STATE: base = "call out of order"; break;
     case LMFS_ERR_TIMEOUT: base = "timed out"; break;
     case LMFS_ERR_TOO_LARGE: base = "request exceeds the memory budget"; break;
-    case LMFS_ERR_NUMERICAL: base = "non-finite value in a factorization"; break;
+    case LMFS_ERR_NUMERICAL: base = "factorization failed"; break;
   }
   s = base;
   if (code < 0 && !g_last_error.empty()) s += " (" + g_last_error + ")";

@@ -796,7 +796,7 @@ int onebody_finish(Ctx& c, OneBody& ob, cudaStream_t st) {
   ob.rank_h.assign(nb, 0);
   LMFS_CUDA(cudaMemcpy(ob.rank_h.data(), ob.rank, nb * sizeof(int), cudaMemcpyDeviceToHost));
   LMFS_CUDA(cudaMemcpy(&hbad, ob.bad, sizeof(int), cudaMemcpyDeviceToHost));
-  if (hbad) { set_last_error("non-finite value in a one-body factorization"); return LMFS_ERR_NUMERICAL; }
+  if (hbad) { set_last_error("non-finite value or expired wait in a one-body factorization"); return LMFS_ERR_NUMERICAL; }
   return LMFS_OK;
 }
 
@@ -1038,7 +1038,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   }
   if (cuda_failed(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
       cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
-  if (hbad) { set_last_error("non-finite value in a pair factorization"); rc = LMFS_ERR_NUMERICAL; goto done; }
+  if (hbad) { set_last_error("non-finite value or expired wait in a pair factorization"); rc = LMFS_ERR_NUMERICAL; goto done; }
   pb.min_rank_F = minr; pb.max_rank_F = maxr;
   pb.qr_ms = qr_ms; pb.qr_flops = qr_flops;
   pb.fac_ms = fac_ms; pb.fac_flops = fac_flops; pb.rhs_ms = rhs_ms; pb.rhs_flops = rhs_flops;
