@@ -349,7 +349,7 @@ def run_reference(args):
     if rank != 0:
         return
     pk, ft = workload()
-    for _ in range(min(args.warmup, 1)):
+    for _ in range(args.warmup):
         oracle_solve(pk, ft)
     t0 = time.perf_counter()
     for _ in range(args.steps):
