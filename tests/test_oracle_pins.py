@@ -319,6 +319,46 @@ def test_peanut_is_the_rolling_disk_envelope():
         assert np.std(seg) < 1e-3 * seg.mean()
 
 
+
+@pytest.mark.parametrize("r1,r2", [(0.8, 1.2), (1.2, 0.9), (1.0, 1.0)])
+def test_peanut_envelope_for_unequal_radii(r1, r2):
+    """The peanut of two disks of different radii with rolling radius rho =
+    min(r1, r2) (reading of Sec. 3.3 for unequal disks): the rolling disk
+    touches both disks at the two points W with |W - c_i| = r_i + rho (found
+    here as circle intersections).  Every node lies outside both disks and
+    outside both rolling disks, on a disk circle or on a rolling circle; the
+    nodes are uniform along one closed curve."""
+    for gap in (1e-3, 0.1):
+        rho = min(r1, r2)
+        c1 = np.array([0.4, -0.1])
+        d = r1 + r2 + gap
+        u = np.array([math.cos(-1.1), math.sin(-1.1)])
+        c2 = c1 + d * u
+        z = peanut(c1, r1, c2, r2, rho, 600)
+        # rolling centres: intersections of |W - c1| = r1 + rho and |W - c2| = r2 + rho
+        R1, R2 = r1 + rho, r2 + rho
+        a = (R1 ** 2 - R2 ** 2 + d ** 2) / (2 * d)
+        hh = math.sqrt(R1 ** 2 - a ** 2)
+        nrm = np.array([-u[1], u[0]])
+        W = [c1 + a * u + hh * nrm, c1 + a * u - hh * nrm]
+        for Wk in W:
+            assert abs(np.hypot(*(Wk - c1)) - R1) < 1e-12 and abs(np.hypot(*(Wk - c2)) - R2) < 1e-12
+        d1 = np.hypot(*(z - c1).T)
+        d2 = np.hypot(*(z - c2).T)
+        dw = [np.hypot(*(z - Wk).T) for Wk in W]
+        tol = 1e-12
+        assert np.all(d1 >= r1 - tol) and np.all(d2 >= r2 - tol)
+        assert np.all(dw[0] >= rho - tol) and np.all(dw[1] >= rho - tol)
+        on = (np.abs(d1 - r1) < tol) | (np.abs(d2 - r2) < tol) | (np.abs(dw[0] - rho) < tol) | \
+             (np.abs(dw[1] - rho) < tol)
+        assert np.all(on)
+        # both disks and both waists are represented
+        assert np.any(np.abs(d1 - r1) < tol) and np.any(np.abs(d2 - r2) < tol)
+        assert np.any(np.abs(dw[0] - rho) < tol) and np.any(np.abs(dw[1] - rho) < tol)
+        seg = np.hypot(*(np.roll(z, -1, axis=0) - z).T)
+        assert np.std(seg) < 1e-3 * seg.mean()
+
+
 def test_params_reject_nonpositive_source_radius():
     with pytest.raises(ValueError):
         PACKING.with_(Nc=24)
