@@ -266,6 +266,26 @@ def test_shield_ellipse_foci_and_tip():
     assert len(z) > 0 and np.all(np.abs(z) > Rf)
 
 
+
+@pytest.mark.parametrize("r1,r2", [(0.8, 1.2), (1.2, 0.8)])
+def test_shield_ellipse_for_unequal_radii(r1, r2):
+    """For a disk of radius r1 facing a disk of radius r2 at gap 1e-3, the
+    shielding nodes lie on one ellipse whose foci are the disk centre and the
+    limiting point a (constant sum of focal distances), stay outside r1 R_f,
+    and reach no further than a + gamma (r1 - a) toward the partner (Sec. 5,
+    with r1 for the unit radius)."""
+    d = r1 + r2 + 1e-3
+    a, _ = limiting_points(d, r1, r2)
+    Rf, gamma = 0.9309, 0.3
+    z = shield_ellipse(a, r1, Rf, 80, gamma)
+    assert len(z) > 0 and np.all(np.abs(z) > r1 * Rf)
+    s = np.abs(z) + np.abs(z - a)
+    assert np.allclose(s, s[0], rtol=1e-12)
+    tip = a + gamma * (r1 - a)
+    assert np.all(z.real <= tip + 1e-12) and z.real.max() > tip - 1e-3
+    assert 0 < a < r1
+
+
 def test_fine_sets_counts_and_orientation():
     p = PAIR_SMALL
     pk = w.two_disks(1e-3)
