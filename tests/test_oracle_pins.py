@@ -219,6 +219,24 @@ def test_isolated_pair_equals_fine_brute_force():
     assert np.linalg.norm(ft - fb) < 1e-8 * np.linalg.norm(fb)
 
 
+
+@pytest.mark.parametrize("problem", ["resistance", "mobility"])
+@pytest.mark.parametrize("gap", [1e-1, 1e-2, 1e-3])
+def test_unequal_pair_against_fine_brute_force(problem, gap):
+    """Disks of radii 0.8 and 1.2 (the unequal-radius extension: limiting
+    points of unequal circles, rolling radius 0.8): the two-body solution
+    matches the dense fine MFS of the pair within the 1e-5 solve target
+    (measured 4e-10 to 1e-5; equal radii give 3e-11 to 4e-6)."""
+    c = np.array([[0.0, 0.0], [0.8 + 1.2 + gap, 0.0]])
+    r = np.array([0.8, 1.2])
+    data = (np.array([[1.0, 0.3, 0.2], [-0.5, -0.3, 0.4]]) if problem == "resistance"
+            else np.array([[1.0, 0.3, 0.2], [-1.0, -0.3, -0.5]]))
+    p = PACKING.with_(Nfp=100)
+    fb = bruteforce.solve(c, r, p, problem, data)
+    out, _ = System(c, r, p, problem).solve(data, tol=1e-13)
+    assert np.linalg.norm(out - fb) < 3e-5 * np.linalg.norm(fb)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("problem,geom,tol", [
     ("resistance", "chain", 5e-6), ("mobility", "chain", 5e-6), ("mobility", "triangle", 5e-4)])
