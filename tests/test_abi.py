@@ -112,3 +112,21 @@ def test_valid_input_without_a_gpu_fails_loudly(lib):
     with pytest.raises(L.LmfsError) as e:
         L.Solver([[0.0, 0.0], [2.5, 0.0]], [1.0, 1.0])
     assert e.value.code == -2
+
+
+def test_product_does_not_use_the_oracle(lib):
+    """The library package neither imports nor names the CPU oracle: importing
+    it (and loading the library) leaves no oracle module loaded, and no source
+    file under the package mentions it."""
+    code = ("import sys\n"
+            "import paper_2606_11273_gb300 as L\n"
+            "L._lib.load()\n"
+            "print(sorted(m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')))\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip() == "[]"
+    pkg = os.path.join(ROOT, "paper_2606_11273_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                assert "oracle" not in open(os.path.join(dirpath, f)).read(), f
