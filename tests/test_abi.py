@@ -117,7 +117,7 @@ def test_valid_input_without_a_gpu_fails_loudly(lib):
 def test_product_does_not_use_the_oracle(lib):
     """The library package neither imports nor names the CPU oracle: importing
     it (and loading the library) leaves no oracle module loaded, and no source
-    file under the package mentions it."""
+    file under the package mentions it; nor does the oracle name the package."""
     code = ("import sys\n"
             "import paper_2606_11273_gb300 as L\n"
             "L._lib.load()\n"
@@ -130,3 +130,8 @@ def test_product_does_not_use_the_oracle(lib):
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
                 assert "oracle" not in open(os.path.join(dirpath, f)).read(), f
+    # and the other way round: the oracle names neither the package nor its library
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2606_11273_gb300" not in src and "lmfs" not in src, f
