@@ -111,3 +111,18 @@ def test_serving_stream():
         assert problem in (0, 1) and data.shape == (pk.P, 3)
         if problem == 1:
             assert np.abs(data[:, :2].sum(axis=0)).max() < 1e-12
+
+
+def test_generators_hold_no_method_arithmetic():
+    """The seeded generators are the one module both sides use: they import
+    neither the oracle nor the library, and compute no Stokeslet."""
+    import ast
+    src = open(w.__file__).read()
+    mods = set()
+    for node in ast.walk(ast.parse(src)):
+        if isinstance(node, ast.Import):
+            mods.update(a.name.split(".")[0] for a in node.names)
+        elif isinstance(node, ast.ImportFrom):
+            mods.add((node.module or "").split(".")[0])
+    assert mods <= {"__future__", "math", "dataclasses", "numpy"}, mods
+    assert "stokeslet" not in src.lower() and "lmfs" not in src
