@@ -125,4 +125,12 @@ def test_generators_hold_no_method_arithmetic():
         elif isinstance(node, ast.ImportFrom):
             mods.add((node.module or "").split(".")[0])
     assert mods <= {"__future__", "math", "dataclasses", "numpy"}, mods
-    assert "stokeslet" not in src.lower() and "lmfs" not in src
+    names = set()
+    for node in ast.walk(ast.parse(src)):
+        if isinstance(node, ast.Name):
+            names.add(node.id)
+        elif isinstance(node, ast.Attribute):
+            names.add(node.attr)
+        elif isinstance(node, (ast.FunctionDef, ast.ClassDef)):
+            names.add(node.name)
+    assert not any("stokeslet" in n.lower() or "lmfs" in n.lower() for n in names), names
