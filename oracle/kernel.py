@@ -25,6 +25,27 @@ def stokeslet(X, Y, mu=1.0):
     return S.reshape(2 * X.shape[0], 2 * Y.shape[0])
 
 
+def stokeslet_in(X, Y, mu=1.0, dtype=np.float64):
+    """The Stokeslet matrix of eq. (stokeslet2d) with every operation carried
+    out in `dtype` (np.float64, or np.longdouble for an extended-precision
+    reference: 80-bit on x86-64, IEEE binary128 on aarch64).  The inputs are
+    taken as exact values of that type."""
+    X = np.asarray(X).reshape(-1, 2).astype(dtype)
+    Y = np.asarray(Y).reshape(-1, 2).astype(dtype)
+    dx = X[:, None, 0] - Y[None, :, 0]
+    dy = X[:, None, 1] - Y[None, :, 1]
+    r2 = dx * dx + dy * dy
+    lg = np.log(r2) / dtype(2)
+    pi = dtype(4) * np.arctan(dtype(1))
+    c = dtype(1) / (dtype(4) * pi * dtype(mu))
+    S = np.empty((X.shape[0], 2, Y.shape[0], 2), dtype=dtype)
+    S[:, 0, :, 0] = c * (-lg + dx * dx / r2)
+    S[:, 0, :, 1] = c * (dx * dy / r2)
+    S[:, 1, :, 0] = S[:, 0, :, 1]
+    S[:, 1, :, 1] = c * (-lg + dy * dy / r2)
+    return S.reshape(2 * X.shape[0], 2 * Y.shape[0])
+
+
 def rigid_matrix(pts, c):
     """Rigid-body matrix of eq. (Kmat), Sec. 3.4: rows [I_2, (y - c)^perp] per
     point, with (a, b)^perp = (-b, a) (Sec. 1, after eq. (rigidbc)).  (2n, 3).  K^T lam gives (sum lam_x,

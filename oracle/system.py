@@ -4,7 +4,7 @@ import numpy as np
 
 from .geometry import coarse_nodes, coarse_sources, contacts
 from .gmres import gmres
-from .kernel import stokeslet
+from .kernel import stokeslet, stokeslet_in
 from .onebody import OneBody
 from .pairs import pair_blocks
 
@@ -109,6 +109,96 @@ class System:
         for i in targets:                                        # identity fix
             u[pos[int(i)]] -= self.ob[i].P @ self.proj(i, lb[i]) - mu[i]
         return u
+
+    def matvec_exclusion(self, mu, targets=None, dtype=np.float64):
+        """Algorithm 3 with Step 2b and the identity step carried out before
+        the Stokeslet sums instead of after them.  Expanding Step 2b, every
+        self term and every close partner's own one-body and pair-correction
+        strengths cancel exactly, which leaves
+
+          u^(i) = mu^(i) + sum_{k not in C(i), k != i} S^(ik) sigma^(k)
+                + sum_{k in C(i)} S^(ik) proj_k( sum_{n in C(k), n != i} lam~_k^(k-n) )
+
+        (C(i): the close partners of i; lam~_k^(k-n): the correction that pair
+        (k, n) adds to disk k in Step 1b; sigma = proj(lam)).  Nothing is
+        added and subtracted again.  Every operation after the one-body and
+        pair blocks (Step 1a, Step 1b, projections, the sums) runs in `dtype`;
+        with np.longdouble this is an extended-precision evaluation of the
+        same FP64 inputs (blocks, factors, points, mu).  Returns u at the
+        target disks (all by default) as float64."""
+        P, p = self.P, self.p
+        n = 2 * p.Nc
+        targets = np.arange(P) if targets is None else np.asarray(targets)
+        mu = np.asarray(mu, dtype=np.float64).reshape(P, 2 * p.Mc).astype(dtype)
+        lb = np.stack([self.ob[i].pinv.VSi.astype(dtype) @ (self.ob[i].pinv.Ut.astype(dtype) @ mu[i])
+                       for i in range(P)])                                  # Step 1a
+        lam = lb.copy()
+        corr = {}                                                            # corr[(a, b)]: pair (a, b)'s share on a
+        for (i, k), blk in zip(self.pairs, self.blocks):                     # Step 1b
+            t = blk["A"].astype(dtype) @ np.concatenate([lb[i], lb[k]])
+            lam[i] += t[:n]
+            lam[k] += t[n:]
+            corr[(i, k)], corr[(k, i)] = t[:n], t[n:]
+        prj = {float(r): ob.proj.astype(dtype) for r, ob in self.onebody.items()}
+        proj = lambda k, v: prj[float(self.radii[k])] @ v
+        partners = {i: set() for i in range(P)}
+        for i, k in self.pairs:
+            partners[i].add(k)
+            partners[k].add(i)
+        u = np.empty((len(targets), 2 * p.Mc), dtype=dtype)
+        for a, i in enumerate(targets):
+            i = int(i)
+            acc = mu[i].copy()
+            for k in range(P):
+                if k == i:
+                    continue
+                if k in partners[i]:
+                    own = np.zeros(n, dtype=dtype)
+                    for m in sorted(partners[k] - {i}):
+                        own = own + corr[(k, m)]
+                    s_k = proj(k, own)
+                else:
+                    s_k = proj(k, lam[k])
+                acc = acc + stokeslet_in(self.X[i], self.Y[k], p.mu, dtype) @ s_k
+            u[a] = acc
+        return u.astype(np.float64)
+
+    def exclusion_condition(self, mu, targets=None):
+        """Rounding scale of the exclusion form at the target disks: the
+        2-norm of the sum of |S^(ik)| |s_k| over the terms that form's sums
+        add, divided by the 2-norm of the result.  An FP64 evaluation of
+        those sums, in any order, errs by about eps_64 times this (relative);
+        so does an FP64 evaluation of the strengths s_k that feed them."""
+        P, p = self.P, self.p
+        n = 2 * p.Nc
+        targets = np.arange(P) if targets is None else np.asarray(targets)
+        mu = np.asarray(mu, dtype=np.float64).reshape(P, 2 * p.Mc)
+        lb = self.lam_bar(mu)
+        lam = lb.copy()
+        corr = {}
+        for (i, k), blk in zip(self.pairs, self.blocks):
+            t = blk["A"] @ np.concatenate([lb[i], lb[k]])
+            lam[i] += t[:n]
+            lam[k] += t[n:]
+            corr[(i, k)], corr[(k, i)] = t[:n], t[n:]
+        partners = {i: set() for i in range(P)}
+        for i, k in self.pairs:
+            partners[i].add(k)
+            partners[k].add(i)
+        absum = np.zeros((len(targets), 2 * p.Mc))
+        for a, i in enumerate(targets):
+            i = int(i)
+            absum[a] = np.abs(mu[i])
+            for k in range(P):
+                if k == i:
+                    continue
+                if k in partners[i]:
+                    s_k = self.proj(k, sum((corr[(k, m)] for m in partners[k] - {i}), np.zeros(n)))
+                else:
+                    s_k = self.proj(k, lam[k])
+                absum[a] += np.abs(stokeslet(self.X[i], self.Y[k], p.mu)) @ np.abs(s_k)
+        u = self.matvec_exclusion(mu, targets)
+        return float(np.linalg.norm(absum) / np.linalg.norm(u))
 
     # -- right-hand sides and post-processing ----------------------------
     def rhs_resistance(self, vel):

@@ -508,6 +508,57 @@ def test_exclusion_form_equals_literal_algorithm3(problem):
     lit = s.matvec(mu)
     # the literal form cancels strengths up to ~1e4 |mu|: rounding ~1e-16 x 1e4
     assert np.linalg.norm(u - lit) < 1e-11 * np.linalg.norm(lit)
+    # the oracle's own exclusion-form evaluation (the reference for the device
+    # matvec) is the same vector, in FP64 and in extended precision, on all
+    # disks and on a subset of target disks
+    for dt in (np.float64, np.longdouble):
+        ex = s.matvec_exclusion(mu, dtype=dt)
+        assert np.linalg.norm(ex - lit) < 1e-11 * np.linalg.norm(lit)
+        assert np.linalg.norm(ex - u) < 1e-13 * np.linalg.norm(u)
+    sub = s.matvec_exclusion(mu, targets=[1, 3], dtype=np.longdouble)
+    assert np.linalg.norm(sub - u[[1, 3]]) < 1e-13 * np.linalg.norm(u[[1, 3]])
+    assert 1.0 <= s.exclusion_condition(mu) < 1e6
+
+
+def test_extended_precision_stokeslet_sum_against_mpmath():
+    """The extended-precision reference evaluates cancelling sums that FP64
+    cannot: a ring of 60 Stokeslets whose strengths are one high Fourier mode
+    (m = 25) of amplitude 1e8 has a field that decays like (rho/|z|)^25 away
+    from the ring, so the direct sum cancels ~15 digits.  Against a 50-digit
+    mpmath evaluation of the same sum, np.longdouble reaches its own
+    eps x condition number while FP64 misses by orders of magnitude more."""
+    mpmath = pytest.importorskip("mpmath")
+    from oracle.kernel import stokeslet_in
+    mpmath.mp.dps = 50
+    N, m, rho, amp = 60, 25, 0.54, 1e8
+    th = 2 * np.pi * np.arange(N) / N
+    Y = np.stack([rho * np.cos(th), rho * np.sin(th)], -1)
+    s = np.stack([amp * np.cos(m * th), amp * np.sin(m * th)], -1).ravel()
+    X = np.array([[1.05, 0.3], [-0.7, 0.9]])
+    ref = []
+    for x in X:
+        ux = uy = mpmath.mpf(0)
+        for j in range(N):
+            dx = mpmath.mpf(x[0]) - mpmath.mpf(Y[j, 0])
+            dy = mpmath.mpf(x[1]) - mpmath.mpf(Y[j, 1])
+            r2 = dx * dx + dy * dy
+            lg = mpmath.log(r2) / 2
+            sx, sy = mpmath.mpf(s[2 * j]), mpmath.mpf(s[2 * j + 1])
+            dot = (dx * sx + dy * sy) / r2
+            ux += -lg * sx + dot * dx
+            uy += -lg * sy + dot * dy
+        c = 1 / (4 * mpmath.pi)
+        ref += [float(c * ux), float(c * uy)]
+    ref = np.array(ref)
+    scale = np.abs(stokeslet(X, Y)) @ np.abs(s)
+    cond = np.linalg.norm(scale) / np.linalg.norm(ref)
+    assert cond > 1e6                            # a badly conditioned sum
+    e64 = np.linalg.norm(stokeslet(X, Y) @ s - ref) / np.linalg.norm(ref)
+    ext = (stokeslet_in(X, Y, 1.0, np.longdouble) @ s.astype(np.longdouble)).astype(np.float64)
+    eext = np.linalg.norm(ext - ref) / np.linalg.norm(ref)
+    epsx = float(np.finfo(np.longdouble).eps)
+    assert eext < max(100 * epsx * cond, 1e-15)
+    assert e64 > 10 * eext
 
 
 @pytest.mark.parametrize("case", ["pair_1e-2", "pair_1e-3", "chain_resistance", "chain_mobility"])
