@@ -92,6 +92,23 @@ typedef struct lmfs_params {
   int    precision;      /* LMFS_FP64, LMFS_MIXED or LMFS_MIXED_DIRECT (lmfs_solve) */
   void*  stream;         /* cudaStream_t for all work of the handle (NULL: own one) */
   int    device;         /* CUDA device ordinal (0)                              */
+  int    refine;         /* LMFS_MIXED / LMFS_MIXED_DIRECT solves: at most this many
+                            refinement rounds against the FP64 operator (4); 0: none.
+                            Each round forms r = b - A_64 x with the FP64 matvec (b the
+                            FP64 right-hand side) and adds the mixed-precision GMRES
+                            solution of A d = r; the solve stops once |r| / |b| <= tol.
+                            Not in the paper: it closes the gap between the mixed
+                            operator and the FP64 one (about 3e-8 relative).          */
+  /* Optional device allocator for every buffer of the handle (NULL: the
+   * library's pool).  dev_alloc returns `bytes` of device memory usable on
+   * `stream` (the handle's stream) or NULL; dev_free returns a block from
+   * dev_alloc, stream-ordered on `stream`.  Both are called from the thread
+   * that makes the library call (for server requests: the server's own
+   * threads), never during a stream capture; they must be thread-safe and
+   * must not wait for other work of the caller. */
+  void*  (*dev_alloc)(size_t bytes, void* stream, void* user);
+  void   (*dev_free)(void* ptr, void* stream, void* user);
+  void*  alloc_user;     /* passed to dev_alloc and dev_free                      */
 } lmfs_params;
 
 typedef struct lmfs_solve_info {
@@ -100,6 +117,10 @@ typedef struct lmfs_solve_info {
   double t_precompute_ms;/* pair precompute of this call (0 if already done)     */
   double t_solve_ms;     /* right-hand side + GMRES + post-processing            */
   int    n_pairs;        /* close pairs                                          */
+  int    refine_rounds;  /* FP64 residual evaluations (FP64 matvecs) of a refined
+                            mixed solve; 0 without refinement                      */
+  double relres_gmres;   /* the last GMRES round's own residual estimate; relres is
+                            the FP64 residual |b - A_64 x| / |b| when refined       */
 } lmfs_solve_info;
 
 typedef struct lmfs_ctx* lmfs_handle;
@@ -212,16 +233,26 @@ int lmfs_stokeslet_sum(const double* targets, int nt, const double* centres,
                        const double* offsets, const double* strengths, int nd,
                        int n_per_disk, double mu, int precision, void* stream, double* out);
 
+/* The library's device-memory pool on `device` (the pool every handle without
+ * dev_alloc allocates from): out[4] = {bytes in use at the high-water mark,
+ * bytes reserved at the high-water mark, bytes in use now, bytes reserved
+ * now}.  reset != 0 then restarts both high-water marks from the current
+ * values.  HOST array.  No counterpart in the paper: a measurement hook (e.g.
+ * to hold the server's admission estimate against what a solve really used). */
+int lmfs_pool_stats(int device, int reset, uint64_t* out);
+
 /* Number of kernels this process has launched through the library so far
  * (eager launches plus the kernel nodes of every replayed graph). */
 int lmfs_launch_count(uint64_t* out);
 
 /* lmfs_stokeslet_sum without any device allocation, for callers that cannot
  * let a library allocate during a call: applications that give the whole
- * device budget to their own pool or arena, plugin hosts that require every
- * allocation to go through their allocator, and latency-critical loops that
- * cannot take an allocation's implicit synchronisation.  The paper has no
- * counterpart: it is a packaging of the same FP32 direct tile sum.
+ * device budget to their own pool or arena up front (a library allocation
+ * would fail or evict their cache), plugin hosts that require every device
+ * allocation to go through their own allocator for accounting and limits, and
+ * processes whose device footprint must stay what it was after start-up.  The
+ * paper has no counterpart: it is a packaging of the same FP32 direct tile
+ * sum.
  *   Arguments as lmfs_stokeslet_sum (FP32 direct tiles; DEVICE pointers; out
  *   is overwritten), with one source range per launch.
  *   Scratch: a fixed 32 MiB array per device, reserved when the library's
@@ -232,7 +263,8 @@ int lmfs_launch_count(uint64_t* out);
  *   array's device address; make that first call before any stream capture.
  *   Every call reuses the same array and it keeps the last call's contents:
  *   calls that overlap on the GPU race on it, so serialise them.
- *   Synchronizes `stream` before returning (it reads the error flags). */
+ *   Host-synchronous: every call synchronizes `stream` before it returns (it
+ *   reads the two error flags back from the array). */
 int lmfs_stokeslet_sum_noalloc(const double* targets, int nt, const double* centres,
                                const double* offsets, const double* strengths, int nd,
                                int n_per_disk, double mu, void* stream, double* out);
@@ -263,6 +295,12 @@ typedef struct lmfs_server_params {
 #define LMFS_ENGINE_INTERLEAVED 0
 #define LMFS_ENGINE_STREAMS 1
 
+/* The device bytes the server's admission counts for one request with these
+ * inputs (pair blocks, one-body factors, Krylov basis and vectors, refinement
+ * vectors, the first pair-precompute chunk's workspace, and a fixed 64 MiB);
+ * contacts are counted on the host.  p may be NULL (defaults). */
+int lmfs_estimate_bytes(const double* centres, const double* radii, int P, const lmfs_params* p, size_t* out);
+
 /* Start a server: a dispatcher thread that admits queued requests, a thread per
  * admitted request, and (interleaved engine) the engine thread. */
 int lmfs_server_create(const lmfs_server_params* sp, lmfs_server** out);
@@ -282,10 +320,11 @@ int lmfs_poll(lmfs_server* s, uint64_t ticket, double* out, lmfs_solve_info* inf
  * (it stays), LMFS_ERR_INVALID for an unknown or already forgotten ticket.
  * A long-running caller forgets each request once it has read the result. */
 int lmfs_server_forget(lmfs_server* s, uint64_t ticket);
-/* Stop the server: waits for the requests already running to finish, drops
- * the queued ones that have not started, joins every thread and frees all
- * records; tickets are invalid afterwards.  No other call on `s` may run
- * concurrently with it or follow it. */
+/* Stop the server: cancels the queued requests that have not been admitted
+ * (their status becomes LMFS_ERR_STATE), waits for the admitted ones to
+ * finish, joins every thread and frees all records; tickets are invalid
+ * afterwards.  No other call on `s` may run concurrently with it or follow
+ * it. */
 int lmfs_server_destroy(lmfs_server* s);
 
 #ifdef __cplusplus

@@ -164,11 +164,12 @@ class System:
         return u.astype(np.float64)
 
     def exclusion_condition(self, mu, targets=None):
-        """Rounding scale of the exclusion form at the target disks: the
-        2-norm of the sum of |S^(ik)| |s_k| over the terms that form's sums
-        add, divided by the 2-norm of the result.  An FP64 evaluation of
-        those sums, in any order, errs by about eps_64 times this (relative);
-        so does an FP64 evaluation of the strengths s_k that feed them."""
+        """Rounding scale of the exclusion form's sums at the target disks:
+        the 2-norm of the sum of |S^(ik)| |s_k| over the terms that those sums
+        add, divided by the 2-norm of the result.  An FP64 evaluation of the
+        sums, in any order, errs by about eps_64 times this (relative), and so
+        does an FP64 evaluation of the strengths s_k that feed them (a
+        relative error of eps in s_k moves the result by that much)."""
         P, p = self.P, self.p
         n = 2 * p.Nc
         targets = np.arange(P) if targets is None else np.asarray(targets)

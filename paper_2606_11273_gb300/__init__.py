@@ -12,15 +12,22 @@ import numpy as np
 from . import _lib
 from ._lib import FP32_FAST, FP64, MIXED, MIXED_DIRECT, MOBILITY, RESISTANCE, LmfsError  # noqa: F401
 
-__all__ = ["Params", "Solver", "Server", "stokeslet_sum", "FP64", "MIXED", "MIXED_DIRECT", "FP32_FAST", "RESISTANCE",
+__all__ = ["Params", "Solver", "Server", "stokeslet_sum", "pool_stats", "estimate_bytes", "FP64", "MIXED", "MIXED_DIRECT", "FP32_FAST", "RESISTANCE",
            "MOBILITY", "LmfsError"]
 
 
-def Params(**kw):
-    """lmfs_params with the library defaults, overridden by keyword."""
+def Params(allocator=None, **kw):
+    """lmfs_params with the library defaults, overridden by keyword.
+    allocator="torch": every device buffer of the handle comes from PyTorch's
+    CUDA caching allocator (through the C adapter libtorchalloc.so) instead of
+    the library's own pool."""
     lib = _lib.load()
     p = _lib.lmfs_params()
     _lib.check(lib.lmfs_params_default(ctypes.byref(p)))
+    if allocator == "torch":
+        p.dev_alloc, p.dev_free = _lib.torch_allocator()
+    elif allocator is not None:
+        raise ValueError("allocator must be None (library pool) or 'torch'")
     for k, v in kw.items():
         if not hasattr(p, k):
             raise TypeError(f"unknown parameter {k}")
@@ -142,7 +149,25 @@ class Solver:
     def _info(info, rc):
         return {"iters": info.iters, "relres": info.relres, "t_precompute_ms": info.t_precompute_ms,
                 "t_solve_ms": info.t_solve_ms, "n_pairs": info.n_pairs,
+                "refine_rounds": info.refine_rounds, "relres_gmres": info.relres_gmres,
                 "converged": rc == _lib.LMFS_OK}
+
+
+def pool_stats(device=0, reset=False):
+    """The library pool's {used_high, reserved_high, used, reserved} bytes."""
+    out = np.zeros(4, dtype=np.uint64)
+    _lib.check(_lib.load().lmfs_pool_stats(int(device), int(bool(reset)), _ptr(out)))
+    return dict(zip(["used_high", "reserved_high", "used", "reserved"], (int(v) for v in out)))
+
+
+def estimate_bytes(centres, radii, params=None):
+    """The server's admission estimate of one request's resident device bytes."""
+    c = np.ascontiguousarray(centres, dtype=np.float64)
+    r = np.ascontiguousarray(radii, dtype=np.float64)
+    out = ctypes.c_size_t()
+    p = ctypes.byref(params) if params is not None else None
+    _lib.check(_lib.load().lmfs_estimate_bytes(_ptr(c), _ptr(r), r.size, p, ctypes.byref(out)))
+    return out.value
 
 
 def stokeslet_sum(targets, centres, offsets, strengths, mu=1.0, precision=MIXED_DIRECT, stream=None, out=None):

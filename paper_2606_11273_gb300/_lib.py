@@ -36,14 +36,15 @@ class lmfs_params(ctypes.Structure):
         ("aell", ctypes.c_double), ("delta_c", ctypes.c_double), ("eps_trunc", ctypes.c_double),
         ("eps_trunc_fine", ctypes.c_double), ("mu", ctypes.c_double), ("tol", ctypes.c_double),
         ("maxit", ctypes.c_int), ("rho", ctypes.c_double), ("precision", ctypes.c_int),
-        ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("refine", ctypes.c_int),
+        ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_user", ctypes.c_void_p),
     ]
 
 
 class lmfs_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("relres", ctypes.c_double),
                 ("t_precompute_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
-                ("n_pairs", ctypes.c_int)]
+                ("n_pairs", ctypes.c_int), ("refine_rounds", ctypes.c_int), ("relres_gmres", ctypes.c_double)]
 
 
 class lmfs_server_params(ctypes.Structure):
@@ -87,6 +88,8 @@ SIGNATURES = {
     "lmfs_stokeslet_sum_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _d, _vp, _vp]),
     "lmfs_strerror": (ctypes.c_char_p, [_i]),
     "lmfs_launch_count": (_i, [_P(ctypes.c_uint64)]),
+    "lmfs_pool_stats": (_i, [_i, _i, _vp]),
+    "lmfs_estimate_bytes": (_i, [_vp, _vp, _i, _P(lmfs_params), _P(ctypes.c_size_t)]),
     "lmfs_server_create": (_i, [_P(lmfs_server_params), _P(_vp)]),
     "lmfs_submit": (_i, [_vp, _vp, _vp, _i, _i, _vp, _P(lmfs_params), _P(ctypes.c_uint64)]),
     "lmfs_poll": (_i, [_vp, ctypes.c_uint64, _vp, _P(lmfs_solve_info), _i]),
@@ -109,6 +112,24 @@ def load(path=LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+_shim = None
+
+
+def torch_allocator():
+    """(dev_alloc, dev_free) function pointers of the adapter to PyTorch's CUDA
+    caching allocator (libtorchalloc.so, built beside liblmfs.so)."""
+    global _shim
+    if _shim is None:
+        import torch
+        torch.cuda.init()                 # the caching allocator must exist before the library calls it
+        path = os.path.join(HERE, "libtorchalloc.so")
+        if not os.path.exists(path):
+            raise ImportError(f"libtorchalloc.so not built at {path}; run paper_2606_11273_gb300/build.py")
+        _shim = ctypes.CDLL(path)
+    return (ctypes.cast(_shim.lmfs_torch_alloc, ctypes.c_void_p).value,
+            ctypes.cast(_shim.lmfs_torch_free, ctypes.c_void_p).value)
 
 
 def check(rc, allow=()):

@@ -32,6 +32,37 @@ def _stale(obj, src):
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+TORCH_SHIM_SRC = os.path.join(CSRC, "torch_alloc.cpp")
+TORCH_SHIM = os.path.join(HERE, "libtorchalloc.so")
+
+
+def build_torch_shim(verbose=False, force=False):
+    """The adapter from the library's allocator callbacks to PyTorch's caching
+    allocator (g++ against the installed torch headers).  Returns its path, or
+    None if torch is not importable here."""
+    try:
+        import torch
+        import torch.utils.cpp_extension as ce
+    except Exception:
+        return None
+    if not force and os.path.exists(TORCH_SHIM) and os.path.getmtime(TORCH_SHIM) > os.path.getmtime(TORCH_SHIM_SRC):
+        return TORCH_SHIM
+    cuda_home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    inc = [f"-I{d}" for d in ce.include_paths()] + [f"-I{os.path.join(cuda_home, 'include')}"]
+    libdir = ce.library_paths()[0]
+    abi = int(bool(getattr(torch._C, "_GLIBCXX_USE_CXX11_ABI", True)))
+    tmp = TORCH_SHIM + ".tmp"
+    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", f"-D_GLIBCXX_USE_CXX11_ABI={abi}"] + inc + \
+          [TORCH_SHIM_SRC, "-o", tmp, f"-L{libdir}", "-lc10_cuda", "-lc10", f"-Wl,-rpath,{libdir}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("g++ failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+    if verbose:
+        sys.stdout.write(r.stdout + r.stderr)
+    os.replace(tmp, TORCH_SHIM)
+    return TORCH_SHIM
+
+
 def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -56,6 +87,7 @@ def build(verbose=False, force=False):
         tmp = OUT + ".tmp"
         run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
         os.replace(tmp, OUT)
+    build_torch_shim(verbose, force)
     return OUT
 
 

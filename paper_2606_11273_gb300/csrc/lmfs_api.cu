@@ -22,6 +22,9 @@ static thread_local std::string g_last_error;
 
 thread_local cudaStream_t g_alloc_stream = nullptr;
 thread_local bool g_alloc_scoped = false;
+thread_local UserAlloc g_user_alloc = nullptr;
+thread_local UserFree g_user_free = nullptr;
+thread_local void* g_user_data = nullptr;
 
 cudaMemPool_t device_pool(int device) {
   static std::mutex mu;
@@ -44,6 +47,11 @@ cudaMemPool_t device_pool(int device) {
 }
 
 int dalloc_bytes(void** p, size_t bytes) {
+  if (g_user_alloc) {                            // the caller's allocator (lmfs_params.dev_alloc)
+    *p = g_user_alloc(bytes, (void*)g_alloc_stream, g_user_data);
+    if (!*p) { set_last_error("the caller's dev_alloc returned NULL"); return LMFS_ERR_NOMEM; }
+    return LMFS_OK;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaMemPool_t pool = device_pool(dev);
@@ -62,6 +70,7 @@ int dalloc_bytes(void** p, size_t bytes) {
 
 void dfree_bytes(void* p) {
   if (!p) return;
+  if (g_user_free) { g_user_free(p, (void*)g_alloc_stream, g_user_data); return; }
   if (g_alloc_scoped) cudaFreeAsync(p, g_alloc_stream);
   else cudaFree(p);
 }
@@ -101,6 +110,7 @@ static void free_ctx(Ctx& c) {
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
+  dfree(c.b64); dfree(c.xacc); dfree(c.rres);
   dfree(c.ufar_part); dfree(c.ring); dfree(c.nodes); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
   if (c.own_stream && c.stream) { cudaStreamDestroy(c.stream); c.stream = nullptr; c.own_stream = false; }
 }
@@ -129,6 +139,8 @@ static int validate_params(const lmfs_params& p) {
     set_last_error("unknown precision");
     return LMFS_ERR_INVALID;
   }
+  if (p.refine < 0 || p.refine > 64) { set_last_error("refine must lie in [0, 64]"); return LMFS_ERR_INVALID; }
+  if (!p.dev_alloc != !p.dev_free) { set_last_error("dev_alloc and dev_free go together"); return LMFS_ERR_INVALID; }
   return LMFS_OK;
 }
 
@@ -152,7 +164,7 @@ static int create_ctx(Ctx& c, const double* centres, const double* radii, int P,
     LMFS_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
     c.own_stream = true;
   }
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
   c.Rc = p.Rc > 0 ? p.Rc : 1.0 - std::log(1e12) / p.Nc;
   c.Rf = 1.0 - std::log(1e12) / p.Nfp;
   c.centres_h.assign(centres, centres + 2 * (size_t)P);
@@ -219,6 +231,55 @@ static int sync_and_check_far_flags(Ctx& c) {
   return LMFS_OK;
 }
 
+static bool refined(const Ctx& c) { return c.prm.precision != LMFS_FP64 && c.prm.refine > 0; }
+
+// Mixed-precision GMRES refined against the FP64 operator: x_0 from GMRES on
+// b (the FP64 right-hand side); then, while |b - A_64 x| / |b| > tol, the
+// mixed GMRES solution d of A d = r (to a tolerance relative to |r| that aims
+// at half the target) is added to x, until refine_done.  prm.maxit bounds the
+// GMRES iterations of all rounds together.  The solve has converged when
+// every GMRES round reached its tolerance (the FP64 residual may then stay at
+// its rounding floor above tol; relres reports it).  x ends in xacc and xsol.
+static int refined_gmres(Ctx& c, int problem, lmfs_solve_info* loc) {
+  const int prec = c.prm.precision;
+  const double tol = c.prm.tol;
+  const int maxit = std::max(1, c.prm.maxit);
+  LMFS_TRY(refine_alloc(c));
+  c.gm_tol = tol;
+  lmfs_solve_info g{};
+  int rc = gmres_solve(c, problem, prec, c.b64, c.xsol, &g, maxit);
+  if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
+  int status = rc;
+  int iters = g.iters, rounds = 0;
+  double relres_g = g.relres, rho = 0.0, rho_prev = 0.0;
+  LMFS_TRY(refine_update(c, true));
+  LMFS_TRY(refine_norm_b(c));
+  while (true) {
+    LMFS_TRY(refine_residual(c, problem));
+    LMFS_CUDA(cudaStreamSynchronize(c.stream));
+    rho = c.host_pinned[4];
+    rounds += 1;
+    if (!(rho == rho)) { set_last_error("refinement: non-finite FP64 residual"); return LMFS_ERR_NUMERICAL; }
+    if (status != LMFS_OK || iters >= maxit || refine_done(c.prm, rounds, rho, rho_prev)) break;
+    rho_prev = rho;
+    c.gm_tol = refine_inner_tol(tol, rho);
+    rc = gmres_solve(c, problem, prec, c.rres, c.xsol, &g, maxit - iters);
+    if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
+    status = rc;
+    iters += g.iters;
+    relres_g = g.relres;
+    LMFS_TRY(refine_update(c, false));
+  }
+  LMFS_CUDA(cudaMemcpyAsync(c.xsol, c.xacc, 2 * (size_t)c.d.P * c.d.Mc * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c.stream));
+  c.gm_tol = tol;
+  loc->iters = iters;
+  loc->relres = rho;
+  loc->relres_gmres = relres_g;
+  loc->refine_rounds = rounds;
+  return status;
+}
+
 static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
   if (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) return LMFS_ERR_INVALID;
   const auto t0 = std::chrono::steady_clock::now();
@@ -226,9 +287,18 @@ static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev,
   LMFS_TRY(ensure_precompute(c, problem));
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
   const auto t1 = std::chrono::steady_clock::now();
-  LMFS_TRY(rhs_device(c, problem, in_dev, c.bvec, c.prm.precision));
   lmfs_solve_info loc{};
-  int rc = gmres_solve(c, problem, c.prm.precision, c.bvec, c.xsol, &loc);
+  int rc = LMFS_OK;
+  if (refined(c)) {
+    LMFS_TRY(refine_alloc(c));
+    LMFS_TRY(rhs_device(c, problem, in_dev, c.b64, LMFS_FP64));
+    rc = refined_gmres(c, problem, &loc);
+  } else {
+    LMFS_TRY(rhs_device(c, problem, in_dev, c.bvec, c.prm.precision));
+    c.gm_tol = c.prm.tol;
+    rc = gmres_solve(c, problem, c.prm.precision, c.bvec, c.xsol, &loc);
+    loc.relres_gmres = loc.relres;
+  }
   if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
   LMFS_TRY(post_device(c, problem, c.xsol, out_dev));
   LMFS_TRY(sync_and_check_far_flags(c));
@@ -249,7 +319,7 @@ static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev,
 int solve_begin(lmfs_handle h, int problem, const double* in, double* beta) {
   if (!h || !in || !beta || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
   LMFS_CUDA(cudaSetDevice(c.device));
   for (int i = 0; i < 3 * c.d.P; ++i)
     if (!std::isfinite(in[i])) { set_last_error("non-finite input"); return LMFS_ERR_INVALID; }
@@ -259,17 +329,51 @@ int solve_begin(lmfs_handle h, int problem, const double* in, double* beta) {
   LMFS_TRY(ensure_precompute(c, problem));
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
   c.t_pre = std::chrono::steady_clock::now();
+  c.gm_tol = c.prm.tol;
+  if (refined(c)) {
+    LMFS_TRY(refine_alloc(c));
+    LMFS_TRY(rhs_device(c, problem, c.io3, c.b64, LMFS_FP64));
+    return gmres_begin(c, problem, c.prm.precision, c.b64, beta);
+  }
   LMFS_TRY(rhs_device(c, problem, c.io3, c.bvec, c.prm.precision));
   return gmres_begin(c, problem, c.prm.precision, c.bvec, beta);
 }
 
-int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info) {
+bool solve_refined(lmfs_handle h) { return refined(h->c); }
+
+int solve_refine_round(lmfs_handle h, int problem, int iters, bool first) {
   Ctx& c = h->c;
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
+  LMFS_CUDA(cudaSetDevice(c.device));
+  LMFS_TRY(gmres_finish(c, iters, c.xsol));
+  LMFS_TRY(refine_update(c, first));
+  if (first) LMFS_TRY(refine_norm_b(c));
+  return refine_residual(c, problem);
+}
+
+int solve_refine_restart(lmfs_handle h, double rho) {
+  Ctx& c = h->c;
+  LMFS_CUDA(cudaSetDevice(c.device));
+  c.gm_tol = refine_inner_tol(c.prm.tol, rho);
+  return gmres_restart(c, c.rres);
+}
+
+int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info,
+                 const lmfs_solve_info* refined_info, int refined_rc) {
+  Ctx& c = h->c;
+  AllocScope as(c.stream, c.prm);
   LMFS_CUDA(cudaSetDevice(c.device));
   const long long n = 2LL * c.d.P * c.d.Mc;
-  if (iters > 0) LMFS_TRY(gmres_finish(c, iters, c.xsol));
-  else LMFS_CUDA(cudaMemsetAsync(c.xsol, 0, n * sizeof(double), c.stream));
+  if (refined_info) {
+    LMFS_CUDA(cudaMemcpyAsync(c.xsol, c.xacc, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    relres = refined_info->relres;
+    iters = refined_info->iters;
+  } else if (iters > 0) {
+    LMFS_TRY(gmres_finish(c, iters, c.xsol));
+  } else {
+    LMFS_CUDA(cudaMemsetAsync(c.xsol, 0, n * sizeof(double), c.stream));
+  }
+  c.gm_tol = c.prm.tol;
   double* outd = nullptr;
   LMFS_TRY(dalloc(&outd, 3 * (size_t)c.d.P));
   int rc = post_device(c, problem, c.xsol, outd);
@@ -283,12 +387,16 @@ int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* o
   c.have_solution = true;
   const auto t2 = std::chrono::steady_clock::now();
   if (info) {
+    *info = lmfs_solve_info{};
     info->iters = iters;
     info->relres = relres;
+    info->relres_gmres = refined_info ? refined_info->relres_gmres : relres;
+    info->refine_rounds = refined_info ? refined_info->refine_rounds : 0;
     info->t_precompute_ms = c.had_precompute ? 0.0 : std::chrono::duration<double, std::milli>(c.t_pre - c.t_begin).count();
     info->t_solve_ms = std::chrono::duration<double, std::milli>(t2 - c.t_pre).count();
     info->n_pairs = c.C;
   }
+  if (refined_info) return refined_rc;
   return relres <= c.prm.tol ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
 }
 
@@ -304,7 +412,8 @@ int lmfs_params_default(lmfs_params* p) {
   p->Nc = 60; p->Mc = 72; p->Rc = 0.0; p->Nfp = 150; p->Nell = 80; p->Mp = 200;
   p->gamma = 0.3; p->af = 1.2; p->r_mob = 0.6; p->aell = 5.0; p->delta_c = 0.2;
   p->eps_trunc = 1e-14; p->eps_trunc_fine = 1e-11; p->mu = 1.0; p->tol = 1e-7; p->maxit = 300;
-  p->rho = 0.0; p->precision = LMFS_MIXED; p->stream = nullptr; p->device = 0;
+  p->rho = 0.0; p->precision = LMFS_MIXED; p->stream = nullptr; p->device = 0; p->refine = 4;
+  p->dev_alloc = nullptr; p->dev_free = nullptr; p->alloc_user = nullptr;
   return LMFS_OK;
 }
 
@@ -317,7 +426,11 @@ int lmfs_create(const double* centres, const double* radii, int P, const lmfs_pa
   auto* h = new (std::nothrow) lmfs_ctx();
   if (!h) return LMFS_ERR_NOMEM;
   int rc = create_ctx(h->c, centres, radii, P, prm);
-  if (rc != LMFS_OK) { free_ctx(h->c); delete h; return rc; }
+  if (rc != LMFS_OK) {
+    { AllocScope as(h->c.stream, prm); free_ctx(h->c); }
+    delete h;
+    return rc;
+  }
   *out = h;
   return LMFS_OK;
 }
@@ -327,7 +440,7 @@ int lmfs_destroy(lmfs_handle h) {
   cudaSetDevice(h->c.device);
   cudaStreamSynchronize(h->c.stream);
   {
-    AllocScope as(h->c.stream);
+    AllocScope as(h->c.stream, h->c.prm);
     free_ctx(h->c);
   }
   delete h;
@@ -349,7 +462,7 @@ int lmfs_get_pairs(lmfs_handle h, int* pairs) {
 int lmfs_precompute_pairs(lmfs_handle h, int problem) {
   if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   LMFS_CUDA(cudaSetDevice(h->c.device));
-  AllocScope as(h->c.stream);
+  AllocScope as(h->c.stream, h->c.prm);
   LMFS_TRY(ensure_precompute(h->c, problem));
   LMFS_CUDA(cudaStreamSynchronize(h->c.stream));
   return LMFS_OK;
@@ -368,7 +481,7 @@ static void transpose_blocks(const double* in, double* out, int C, size_t n) {
 int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E) {
   if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
   if (!c.prob[problem].ready) return LMFS_ERR_STATE;
   const size_t n4 = 4 * (size_t)c.d.Nc;
   if (c.C == 0) return LMFS_OK;
@@ -387,7 +500,7 @@ int lmfs_get_pair_blocks(lmfs_handle h, int problem, double* A, double* E) {
 int lmfs_set_pair_blocks(lmfs_handle h, int problem, const double* A, const double* E) {
   if (!h || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) || (h->c.C && (!A || !E))) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
   PairBlocks& pb = c.prob[problem];
   if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
   const size_t n4 = 4 * (size_t)c.d.Nc;
@@ -409,7 +522,7 @@ int lmfs_set_onebody(lmfs_handle h, int problem, const double* Ut, const double*
   if (!h || !Ut || !sigma || !V || !rank || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY))
     return LMFS_ERR_INVALID;
   Ctx& c = h->c;
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
   PairBlocks& pb = c.prob[problem];
   if (!pb.ob.W) LMFS_TRY(build_onebody(c, problem, pb.ob));
   const int ns = 2 * c.d.Nc, nn = 2 * c.d.Mc, nc = pb.ob.nclass;
@@ -454,7 +567,7 @@ int lmfs_matvec(lmfs_handle h, int problem, const double* mu_dev, double* u_dev,
   if (!h || !mu_dev || !u_dev || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) ||
       (precision != LMFS_FP64 && precision != LMFS_MIXED && precision != LMFS_MIXED_DIRECT))
     return LMFS_ERR_INVALID;
-  AllocScope as(h->c.stream);
+  AllocScope as(h->c.stream, h->c.prm);
   return matvec_device(h->c, problem, mu_dev, u_dev, precision);
 }
 
@@ -462,21 +575,21 @@ int lmfs_rhs(lmfs_handle h, int problem, const double* in_dev, double* b_dev, in
   if (!h || !in_dev || !b_dev || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) ||
       (precision != LMFS_FP64 && precision != LMFS_MIXED && precision != LMFS_MIXED_DIRECT))
     return LMFS_ERR_INVALID;
-  AllocScope as(h->c.stream);
+  AllocScope as(h->c.stream, h->c.prm);
   return rhs_device(h->c, problem, in_dev, b_dev, precision);
 }
 
 int lmfs_solve_device(lmfs_handle h, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
   if (!h || !in_dev || !out_dev) return LMFS_ERR_INVALID;
   LMFS_CUDA(cudaSetDevice(h->c.device));
-  AllocScope as(h->c.stream);
+  AllocScope as(h->c.stream, h->c.prm);
   return solve_dev(h->c, problem, in_dev, out_dev, info);
 }
 
 int lmfs_solve(lmfs_handle h, int problem, const double* in, double* out, lmfs_solve_info* info) {
   if (!h || !in || !out) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
   LMFS_CUDA(cudaSetDevice(c.device));
   for (int i = 0; i < 3 * c.d.P; ++i)
     if (!std::isfinite(in[i])) { set_last_error("non-finite input"); return LMFS_ERR_INVALID; }
@@ -496,7 +609,7 @@ int lmfs_solve(lmfs_handle h, int problem, const double* in, double* out, lmfs_s
 int lmfs_invalidate(lmfs_handle h) {
   if (!h) return LMFS_ERR_INVALID;
   Ctx& c = h->c;
-  AllocScope as(c.stream);
+  AllocScope as(c.stream, c.prm);
   LMFS_CUDA(cudaSetDevice(c.device));
   // re-run contact detection on the device; the geometry is unchanged, so the
   // pair lists (and every allocation sized from them) stay valid
@@ -538,6 +651,24 @@ int lmfs_stokeslet_sum(const double* targets, int nt, const double* centres, con
                        double* out) {
   return stokeslet_sum_standalone(targets, nt, centres, offsets, strengths, nd, n_per_disk, mu, precision,
                                   (cudaStream_t)stream, out);
+}
+
+int lmfs_pool_stats(int device, int reset, uint64_t* out) {
+  if (!out || device < 0) return LMFS_ERR_INVALID;
+  cudaMemPool_t pool = device_pool(device);
+  if (!pool) { set_last_error("no memory pool on this device"); return LMFS_ERR_CUDA; }
+  unsigned long long v[4] = {0, 0, 0, 0};
+  LMFS_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v[0]));
+  LMFS_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &v[1]));
+  LMFS_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v[2]));
+  LMFS_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v[3]));
+  for (int i = 0; i < 4; ++i) out[i] = (uint64_t)v[i];
+  if (reset) {
+    unsigned long long zero = 0;
+    LMFS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    LMFS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &zero));
+  }
+  return LMFS_OK;
 }
 
 int lmfs_launch_count(uint64_t* out) {

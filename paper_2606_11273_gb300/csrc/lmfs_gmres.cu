@@ -169,6 +169,33 @@ __global__ void combine_x(const double* V, long long n, const double* y, int k, 
   }
 }
 
+// ---- refinement against the FP64 operator --------------------------------
+// r = b - r (r holds A_64 x on entry) and the partial sums of |r|^2.
+__global__ void resid_part(const double* b, double* r, long long n, double* part) {
+  const long long r0 = (long long)blockIdx.x * ROWS_PER_BLOCK;
+  const long long r1 = min(n, r0 + ROWS_PER_BLOCK);
+  double acc = 0.0;
+  for (long long i = r0 + threadIdx.x; i < r1; i += RB) {
+    const double v = b[i] - r[i];
+    r[i] = v;
+    acc += v * v;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+// scal[slot] = sqrt(sum part) (slot 5: |b|), or that over scal[5] (slot 4: |r| / |b|).
+__global__ void norm_finish(const double* part, int nblk, double* scal, int slot) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[b];
+  const double nv = sqrt(s);
+  scal[slot] = slot == 5 ? nv : (scal[5] > 0 ? nv / scal[5] : 0.0);
+}
+__global__ void axpy_kernel(double* x, const double* d, long long n, int first) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    x[r] = first ? d[r] : x[r] + d[r];
+}
+
 }  // namespace
 
 void gmres_drop_graphs(Ctx& c) {
@@ -314,9 +341,58 @@ int gmres_step_post(Ctx& c, int problem, int precision) {
   return LMFS_OK;
 }
 
-int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, lmfs_solve_info* info) {
-  const int maxit = std::max(1, c.prm.maxit);
-  LMFS_TRY(gmres_alloc(c, maxit));
+int refine_alloc(Ctx& c) {
+  const size_t n = 2 * (size_t)c.d.P * c.d.Mc;
+  if (!c.b64) LMFS_TRY(dalloc(&c.b64, n));
+  if (!c.xacc) LMFS_TRY(dalloc(&c.xacc, n));
+  if (!c.rres) LMFS_TRY(dalloc(&c.rres, n));
+  return LMFS_OK;
+}
+
+int refine_norm_b(Ctx& c) {
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+  norm_part<<<nblk, RB, 0, c.stream>>>(c.b64, n, c.hpart);
+  norm_finish<<<1, 32, 0, c.stream>>>(c.hpart, nblk, c.scal, 5);
+  note_launches(1);
+  return check_launch("refine |b|");
+}
+
+int refine_update(Ctx& c, bool first) {
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
+  axpy_kernel<<<eb, 256, 0, c.stream>>>(c.xacc, c.xsol, n, first ? 1 : 0);
+  return check_launch("refine update");
+}
+
+int refine_residual(Ctx& c, int problem) {
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+  LMFS_TRY(matvec_device(c, problem, c.xacc, c.rres, LMFS_FP64));
+  resid_part<<<nblk, RB, 0, c.stream>>>(c.b64, c.rres, n, c.hpart);
+  norm_finish<<<1, 32, 0, c.stream>>>(c.hpart, nblk, c.scal, 4);
+  note_launches(1);
+  LMFS_TRY(check_launch("refine residual"));
+  LMFS_CUDA(cudaMemcpyAsync(c.host_pinned + 4, c.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  return LMFS_OK;
+}
+
+// A new GMRES round on b without a host wait (the caller knows |b| > 0).
+int gmres_restart(Ctx& c, const double* b) {
+  const long long n = 2LL * c.d.P * c.d.Mc;
+  const int nblk = (int)((n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+  const int eb = (int)std::min<long long>((n + 255) / 256, 2048);
+  norm_part<<<nblk, RB, 0, c.stream>>>(b, n, c.hpart);
+  init_kernel<<<1, 32, 0, c.stream>>>(c.hpart, nblk, c.scal, c.gvec, c.gm_cap, c.jdev);
+  scale_kernel<<<eb, 256, 0, c.stream>>>(b, n, c.scal, c.V);
+  note_launches(2);
+  return check_launch("gmres restart");
+}
+
+int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, lmfs_solve_info* info,
+                int maxit_round) {
+  const int maxit = std::max(1, maxit_round > 0 ? std::min(maxit_round, c.prm.maxit) : c.prm.maxit);
+  LMFS_TRY(gmres_alloc(c, std::max(1, c.prm.maxit)));
   const long long n = 2LL * c.d.P * c.d.Mc;
   double beta = 0.0;
   LMFS_TRY(gmres_init(c, b, &beta));
@@ -336,7 +412,7 @@ int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, 
       iters = it + 1;
       relres = c.host_pinned[1];
       if (!(relres == relres)) { set_last_error("GMRES produced a non-finite residual"); return LMFS_ERR_NUMERICAL; }
-      if (relres <= c.prm.tol || c.host_pinned[3] != 0.0) break;
+      if (relres <= c.gm_tol || c.host_pinned[3] != 0.0) break;
     }
     LMFS_TRY(gmres_finish(c, iters, x));
   } else {
@@ -344,7 +420,7 @@ int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, 
     relres = 0.0;
   }
   if (info) { info->iters = iters; info->relres = relres; }
-  return relres <= c.prm.tol ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
+  return relres <= c.gm_tol ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
 }
 
 }  // namespace lmfs

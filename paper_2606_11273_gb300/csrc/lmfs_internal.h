@@ -161,6 +161,12 @@ struct Ctx {
   int* jdev = nullptr;
   double* bvec = nullptr;
   double* xsol = nullptr;
+  // refinement against the FP64 operator (mixed solves): the FP64 right-hand
+  // side, the accumulated solution and the FP64 residual
+  double* b64 = nullptr;
+  double* xacc = nullptr;
+  double* rres = nullptr;
+  double gm_tol = 0.0;               // tolerance of the running GMRES round (relative to its right-hand side)
   double* io3 = nullptr;             // [P][3]
   double* host_pinned = nullptr;     // pinned scalars
   cudaGraphExec_t graph_exec[2][3] = {};
@@ -269,8 +275,27 @@ int stokeslet_sum_noalloc(const double* targets, int nt, const double* centres, 
                           const double* strengths, int nd, int npd, double mu, cudaStream_t s, double* out);
 
 // ---- GMRES (lmfs_gmres.cu) ------------------------------------------------
+// To c.gm_tol (set by the caller), at most maxit_round iterations (<= 0:
+// prm.maxit).
 int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x,
-                lmfs_solve_info* info);
+                lmfs_solve_info* info, int maxit_round = 0);
+// Refinement against the FP64 operator (lmfs_gmres.cu), all stream-ordered on
+// the handle's stream without a host wait:
+//   refine_norm_b: |b64| into the device scalars (scal[5]);
+//   refine_update: xacc = xsol (first round) or xacc + xsol;
+//   refine_residual: rres = b64 - A_64 xacc (FP64 matvec) and |rres| / |b64|
+//     into scal[4], copied to host_pinned[4];
+//   gmres_restart: a new GMRES round on rres (basis vector 0, g, j = 0).
+int refine_alloc(Ctx& c);
+int refine_norm_b(Ctx& c);
+int refine_update(Ctx& c, bool first);
+int refine_residual(Ctx& c, int problem);
+int gmres_restart(Ctx& c, const double* b);
+// Inner tolerance of the next refinement round for a residual ratio rho
+// (aims at half the target; within [tol, 0.1]).
+inline double refine_inner_tol(double tol, double rho) {
+  return std::min(0.1, std::max(tol, 0.5 * tol / std::max(rho, 1e-300)));
+}
 void gmres_free(Ctx& c);
 // The captured GMRES graphs hold the device addresses of every buffer the
 // matvec reads; drop them whenever one of those buffers is reallocated.
@@ -296,17 +321,38 @@ int gmres_finish(Ctx& c, int iters, double* x);
 // stream for the calls made on this thread while it lives.  Without a scope
 // an allocation is made on the legacy stream and waited for, and a free is the
 // synchronous cudaFree (legal for pool memory), so every path stays ordered.
+// A handle whose lmfs_params carry dev_alloc / dev_free allocates every buffer
+// through them instead (the scope of an API call on that handle names them;
+// a nested scope that names only a stream keeps the enclosing allocator).
 cudaMemPool_t device_pool(int device);
+using UserAlloc = void* (*)(size_t, void*, void*);
+using UserFree = void (*)(void*, void*, void*);
 extern thread_local cudaStream_t g_alloc_stream;
 extern thread_local bool g_alloc_scoped;
+extern thread_local UserAlloc g_user_alloc;
+extern thread_local UserFree g_user_free;
+extern thread_local void* g_user_data;
 struct AllocScope {
   cudaStream_t prev_stream;
   bool prev_scoped;
-  explicit AllocScope(cudaStream_t s) : prev_stream(g_alloc_stream), prev_scoped(g_alloc_scoped) {
+  UserAlloc prev_alloc;
+  UserFree prev_free;
+  void* prev_data;
+  explicit AllocScope(cudaStream_t s)
+      : prev_stream(g_alloc_stream), prev_scoped(g_alloc_scoped), prev_alloc(g_user_alloc), prev_free(g_user_free),
+        prev_data(g_user_data) {
     g_alloc_stream = s;
     g_alloc_scoped = true;
   }
-  ~AllocScope() { g_alloc_stream = prev_stream; g_alloc_scoped = prev_scoped; }
+  AllocScope(cudaStream_t s, const lmfs_params& p) : AllocScope(s) {
+    g_user_alloc = p.dev_alloc;
+    g_user_free = p.dev_free;
+    g_user_data = p.alloc_user;
+  }
+  ~AllocScope() {
+    g_alloc_stream = prev_stream; g_alloc_scoped = prev_scoped;
+    g_user_alloc = prev_alloc; g_user_free = prev_free; g_user_data = prev_data;
+  }
 };
 int dalloc_bytes(void** p, size_t bytes);
 void dfree_bytes(void* p);
@@ -334,8 +380,26 @@ namespace lmfs {
 // (gmres_step_pre, far field, gmres_step_post) until convergence, breakdown or
 // maxit, and solve_finish forms x from `iters` basis vectors, post-processes,
 // and copies [P][3] to `out` (host).
+// With refinement against the FP64 operator (mixed precision, prm.refine > 0)
+// the caller ends each GMRES round with solve_refine_round (x += the round's
+// solution, then the FP64 residual, all enqueued; |r| / |b| lands in
+// host_pinned[4] when the stream reaches it) and either starts the next round
+// with solve_refine_restart or finishes with the refined record (x from xacc).
+size_t estimate_bytes(const double* c, const double* r, int P, const lmfs_params& p);   // lmfs_server.cu
 int solve_begin(lmfs_handle h, int problem, const double* in, double* beta);
-int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info);
+bool solve_refined(lmfs_handle h);
+int solve_refine_round(lmfs_handle h, int problem, int iters, bool first);
+int solve_refine_restart(lmfs_handle h, double rho);
+int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info,
+                 const lmfs_solve_info* refined_info = nullptr, int refined_rc = LMFS_OK);
+// The refinement's stopping rule, shared by lmfs_solve and the server: stop
+// at tol, after prm.refine residuals, or when a round no longer halves the
+// FP64 residual (its rounding floor: the FP64 evaluation of the two-body
+// operator carries an error of about eps_64 times the condition number of its
+// sums, which the corrected strengths of close contacts make large).
+inline bool refine_done(const lmfs_params& p, int rounds, double rho, double rho_prev) {
+  return rho <= p.tol || rounds > p.refine || (rounds > 1 && rho > 0.5 * rho_prev);
+}
 }  // namespace lmfs
 
 #define LMFS_TRY(x) do { int _rc = (x); if (_rc != LMFS_OK) return _rc; } while (0)

@@ -1738,10 +1738,10 @@ int stokeslet_sum_standalone(const double* targets, int nt, const double* centre
 
 // ---- stand-alone sum without device allocation ------------------------------
 // Some callers cannot have a library allocate device memory during a call:
-// applications that hand the whole device budget to their own pool or arena,
-// plugin hosts that require every allocation to go through their allocator,
-// and latency-critical loops that cannot take the implicit synchronisation an
-// allocation may cause.  lmfs_stokeslet_sum_noalloc serves them: its scratch
+// applications that hand the whole device budget to their own pool or arena
+// up front, plugin hosts that require every device allocation to go through
+// their allocator, and processes whose device footprint must not grow after
+// start-up.  lmfs_stokeslet_sum_noalloc serves them: its scratch
 // lives in the fixed array below, reserved once per device when this module is
 // loaded and held until the process exits.  Every call reuses the same array,
 // so calls that overlap on the GPU (from different streams or threads) race on

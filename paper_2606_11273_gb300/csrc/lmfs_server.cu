@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -34,8 +35,14 @@ struct Active {
   lmfs_handle h = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t ev_pre = nullptr, ev_step = nullptr;
-  int iters = 0;
+  int iters = 0;                 // Arnoldi steps of the running GMRES round
   bool in_flight = false;
+  // refinement against the FP64 operator (mixed servers): phase 1 while the
+  // FP64 residual of a finished round is in flight
+  int phase = 0;
+  lmfs_solve_info ref{};         // total iterations, rounds, residuals so far
+  double rho_prev = 0.0;
+  int ref_rc = LMFS_OK;          // LMFS_ERR_NOT_CONVERGED once a round ran out of iterations
 };
 
 struct Request {
@@ -65,6 +72,10 @@ struct lmfs_server {
   int running = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
+  // a host-side fake of a failing step, for tests: the request with this
+  // ticket gets LMFS_ERR_CUDA from its third Arnoldi step's launch instead of
+  // the launch (LMFS_TEST_FAIL_TICKET; 0: none)
+  uint64_t fail_ticket = 0;
   // interleaved engine
   std::thread engine;
   std::condition_variable cv_engine;             // engine wakes on hand-off / stop
@@ -73,6 +84,9 @@ struct lmfs_server {
 
 namespace {
 
+}  // namespace
+
+namespace lmfs {
 // Device bytes a request keeps resident: pair blocks, one-body factors, the
 // Krylov basis and vectors, plus the pair-precompute workspace of its first
 // chunk.  Contacts are counted on the host for this estimate only.
@@ -100,8 +114,13 @@ size_t estimate_bytes(const double* c, const double* r, int P, const lmfs_params
   const double nmax = 4.0 * (p.Nfp + 2 * p.Nell);
   const double per_pair_ws = (4.0 * nX * (nmax + n4) + 2 * nmax * n4 + 2.0 * p.Mp * (nmax + 2 * n4)) * 8.0;
   const double ws = std::min<double>((double)std::max<long long>(C, 1), 456.0) * per_pair_ws;
-  return (size_t)(blocks + basis + vecs + ws + (64 << 20));
+  const double refine = (p.precision != LMFS_FP64 && p.refine > 0) ? 3.0 * n * 8.0 : 0.0;
+  return (size_t)(blocks + basis + vecs + ws + refine + (64 << 20));
 }
+}  // namespace lmfs
+
+namespace {
+using lmfs::estimate_bytes;
 
 void complete(lmfs_server* s, const std::shared_ptr<Request>& rq, int rc) {
   std::lock_guard<std::mutex> lk(s->mu);
@@ -210,11 +229,45 @@ void engine_loop(lmfs_server* s) {
         if (q == cudaErrorNotReady) continue;
         a.in_flight = false;
         if (q != cudaSuccess) { cudaGetLastError(); fail(a, LMFS_ERR_CUDA); continue; }
-        a.iters += 1;
         const lmfs::Ctx& c = a.h->c;
+        if (a.phase == 1) {
+          // the FP64 residual of the round that just ended is on the host
+          const double rho = c.host_pinned[4];
+          a.ref.refine_rounds += 1;
+          a.ref.relres = rho;
+          if (!(rho == rho)) { fail(a, LMFS_ERR_NUMERICAL); continue; }
+          a.phase = 0;
+          if (a.ref_rc != LMFS_OK || a.ref.iters >= std::max(1, c.prm.maxit) ||
+              lmfs::refine_done(c.prm, a.ref.refine_rounds, rho, a.rho_prev)) {
+            const int rc = lmfs::solve_finish(a.h, a.rq->problem, a.ref.iters, rho, a.rq->out.data(), &a.rq->info,
+                                              &a.ref, a.ref_rc);
+            release(a);
+            complete(s, a.rq, rc);
+            continue;
+          }
+          a.rho_prev = rho;
+          a.iters = 0;
+          const int rc = lmfs::solve_refine_restart(a.h, rho);
+          if (rc != LMFS_OK) { fail(a, rc); continue; }
+          ready.push_back(&a);
+          continue;
+        }
+        a.iters += 1;
+        a.ref.iters += 1;
         const double relres = c.host_pinned[1];
         if (!(relres == relres)) { fail(a, LMFS_ERR_NUMERICAL); continue; }
-        if (relres <= c.prm.tol || c.host_pinned[3] != 0.0 || a.iters >= std::max(1, c.prm.maxit)) {
+        if (relres <= c.gm_tol || c.host_pinned[3] != 0.0 || a.ref.iters >= std::max(1, c.prm.maxit)) {
+          if (lmfs::solve_refined(a.h)) {
+            // end of a GMRES round: x += its solution, FP64 residual in flight
+            a.ref.relres_gmres = relres;
+            if (!(relres <= c.gm_tol) && c.host_pinned[3] == 0.0) a.ref_rc = LMFS_ERR_NOT_CONVERGED;
+            int rc = lmfs::solve_refine_round(a.h, a.rq->problem, a.iters, a.ref.refine_rounds == 0);
+            if (rc == LMFS_OK && cudaEventRecord(a.ev_step, a.st) != cudaSuccess) rc = LMFS_ERR_CUDA;
+            if (rc != LMFS_OK) { cudaStreamSynchronize(a.st); fail(a, rc); continue; }
+            a.phase = 1;
+            a.in_flight = true;
+            continue;
+          }
           const int rc = lmfs::solve_finish(a.h, a.rq->problem, a.iters, relres, a.rq->out.data(), &a.rq->info);
           release(a);
           complete(s, a.rq, rc);
@@ -226,30 +279,47 @@ void engine_loop(lmfs_server* s) {
     act.erase(std::remove_if(act.begin(), act.end(), [](const std::unique_ptr<Active>& a) { return !a->h; }),
               act.end());
     if (!ready.empty()) {
+      // A request whose own step fails is failed alone; the others go on.
       std::vector<lmfs::Ctx*> cs;
       std::vector<int> problems;
-      int rc = LMFS_OK;
+      std::vector<Active*> go;
       for (Active* a : ready) {
         lmfs::Ctx& c = a->h->c;
-        if ((rc = lmfs::gmres_step_pre(c, a->rq->problem, prec)) != LMFS_OK) break;
-        if (cudaEventRecord(a->ev_pre, a->st) != cudaSuccess || cudaStreamWaitEvent(est, a->ev_pre, 0) != cudaSuccess) {
-          rc = LMFS_ERR_CUDA;
-          break;
+        int r = (s->fail_ticket && a->rq->ticket == s->fail_ticket && a->ref.iters == 2)
+                    ? (lmfs::set_last_error("injected step failure (LMFS_TEST_FAIL_TICKET)"), LMFS_ERR_CUDA)
+                    : lmfs::gmres_step_pre(c, a->rq->problem, prec);
+        if (r == LMFS_OK && (cudaEventRecord(a->ev_pre, a->st) != cudaSuccess ||
+                             cudaStreamWaitEvent(est, a->ev_pre, 0) != cudaSuccess))
+          r = LMFS_ERR_CUDA;
+        if (r != LMFS_OK) {
+          cudaGetLastError();
+          cudaStreamSynchronize(a->st);
+          fail(*a, r);
+          continue;
         }
         cs.push_back(&c);
         problems.push_back(a->rq->problem);
+        go.push_back(a);
       }
-      if (rc == LMFS_OK) rc = lmfs::far_multi_launch(cs.data(), problems.data(), (int)cs.size(), prec, est, buf);
-      if (rc == LMFS_OK && cudaEventRecord(ev_far, est) != cudaSuccess) rc = LMFS_ERR_CUDA;
-      for (Active* a : ready) {
-        int r = rc;
-        if (r == LMFS_OK && cudaStreamWaitEvent(a->st, ev_far, 0) != cudaSuccess) r = LMFS_ERR_CUDA;
+      int rc = lmfs::far_multi_launch(cs.data(), problems.data(), (int)cs.size(), prec, est, buf);
+      bool shared = rc == LMFS_OK && cudaEventRecord(ev_far, est) == cudaSuccess;
+      if (!shared) cudaGetLastError();
+      for (Active* a : go) {
+        int r = LMFS_OK;
+        if (shared) {
+          if (cudaStreamWaitEvent(a->st, ev_far, 0) != cudaSuccess) r = LMFS_ERR_CUDA;
+        } else {
+          // the shared launch could not be made: this request's far field
+          // alone, on its own stream (the same kernel on the same items)
+          r = lmfs::matvec_far(a->h->c, a->rq->problem, prec);
+        }
         if (r == LMFS_OK) r = lmfs::gmres_step_post(a->h->c, a->rq->problem, prec);
         if (r == LMFS_OK && cudaEventRecord(a->ev_step, a->st) != cudaSuccess) r = LMFS_ERR_CUDA;
         if (r == LMFS_OK) {
           a->in_flight = true;
         } else {
           // nothing of this request is left in flight once its stream is idle
+          cudaGetLastError();
           cudaStreamSynchronize(a->st);
           cudaStreamSynchronize(est);
           fail(*a, r);
@@ -320,6 +390,7 @@ int lmfs_server_create(const lmfs_server_params* sp, lmfs_server** out) {
   auto* s = new (std::nothrow) lmfs_server();
   if (!s) return LMFS_ERR_NOMEM;
   s->sp = *sp;
+  if (const char* f = std::getenv("LMFS_TEST_FAIL_TICKET")) s->fail_ticket = std::strtoull(f, nullptr, 10);
   s->dispatcher = std::thread(dispatch_loop, s);
   if (s->sp.engine == LMFS_ENGINE_INTERLEAVED) s->engine = std::thread(engine_loop, s);
   *out = s;
@@ -370,6 +441,14 @@ int lmfs_poll(lmfs_server* s, uint64_t ticket, double* out, lmfs_solve_info* inf
   return rq->rc;
 }
 
+int lmfs_estimate_bytes(const double* centres, const double* radii, int P, const lmfs_params* p, size_t* out) {
+  if (!centres || !radii || P < 1 || !out) return LMFS_ERR_INVALID;
+  lmfs_params prm;
+  if (p) prm = *p; else lmfs_params_default(&prm);
+  *out = estimate_bytes(centres, radii, P, prm);
+  return LMFS_OK;
+}
+
 int lmfs_server_forget(lmfs_server* s, uint64_t ticket) {
   if (!s) return LMFS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -384,7 +463,17 @@ int lmfs_server_destroy(lmfs_server* s) {
   if (!s) return LMFS_ERR_INVALID;
   {
     std::unique_lock<std::mutex> lk(s->mu);
-    // wait (bounded per request by its own solve) for running requests
+    // requests still queued are cancelled (LMFS_ERR_STATE) before the
+    // dispatcher can admit them; then wait (bounded per request by its own
+    // solve) for the admitted ones
+    for (auto& rq : s->queue) {
+      rq->rc = LMFS_ERR_STATE;
+      std::vector<double>().swap(rq->centres);
+      std::vector<double>().swap(rq->radii);
+      std::vector<double>().swap(rq->in);
+    }
+    s->queue.clear();
+    s->cv_done.notify_all();
     s->cv_done.wait(lk, [&] { return s->running == 0; });
     s->stop = true;
     s->cv_dispatch.notify_all();

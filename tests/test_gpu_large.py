@@ -1,0 +1,227 @@
+"""GPU path at the large workload sizes against the CPU oracle (C ABI):
+the polydisperse P = 1000 packing (mixed solve refined against the FP64
+operator versus the FP64 solve), the P = 10^4 packing with the device's own
+pair blocks (sampled pairs' blocks, sampled matvec rows, the refined solve's
+FP64 residual), and the stand-alone Stokeslet kernel at the P = 10^4 size on
+sampled targets.  Tolerances as in test_gpu_parity: mixed matvec 1e-6,
+solves 1e-5, FP64 matvec within the rounding band of FP64 evaluation."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle.kernel import stokeslet
+from oracle.pairs import pair_blocks
+from oracle.params import PACKING, POLY
+from oracle.system import System
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.220446049250313e-16
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2606_11273_gb300 import build
+    build.build()
+    import paper_2606_11273_gb300 as lib
+    return lib
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def onebody_factors(ob, Nc):
+    """The oracle's truncated SVD of a one-body block as (U^T, sigma, V, rank)."""
+    ns = 2 * Nc
+    r = ob.pinv.rank
+    Ut = np.zeros((1, ns, ob.pinv.Ut.shape[1]))
+    Ut[0, :r] = ob.pinv.Ut
+    sig = np.ones((1, ns))
+    sig[0, :r] = ob.pinv.s[:r]
+    V = np.zeros((1, ns, ns))
+    V[0, :, :r] = ob.pinv.VSi * ob.pinv.s[:r]
+    return Ut, sig, V, np.array([r])
+
+
+def fp64_residual(L, s, problem, data):
+    """|b - A_64 x| / |b| of the handle's last solution, with the FP64 matvec
+    and the FP64 right-hand side, all on the device."""
+    n = s.P * s.params.Mc * 2
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s.solution(x)
+    b = torch.zeros_like(x)
+    s.rhs(problem, torch.tensor(np.ascontiguousarray(data).ravel(), dtype=torch.float64, device="cuda"), b, L.FP64)
+    ax = torch.zeros_like(x)
+    s.matvec(problem, x, ax, L.FP64)
+    torch.cuda.synchronize()
+    return float((b - ax).norm() / b.norm())
+
+
+def test_p1000_polydisperse_refined_mixed_against_extended_precision_residual(L):
+    """P = 1000, radii U[0.8, 1.2], area fraction 0.60, close pairs below gap
+    0.1: an ill-conditioned packing whose FP64 operator has a rounding floor
+    of a few 1e-6 (the FP64 solve's own true FP64 residual is ~5e-6 even at
+    tol 1e-10), so two FP64-level solutions can differ by ~1e-5.  The
+    arbiter is the oracle: with identical blocks and one-body factors on every
+    side (the device's pair blocks, the oracle's SVD factors for all 1000
+    radius classes), its exclusion form of Algorithm 3 in extended precision
+    gives the residual of each device solution on 3 sampled target disks.
+    The refined mixed solution's residual must be no larger than 1.5 times
+    the FP64 solution's (and at most 1e-5), and its velocities within 3e-5
+    of the FP64 solve's."""
+    pk = w.packing_p1000_poly()
+    ft = w.forces_torques(pk.P, 6)
+    kw = dict(delta_c=0.1, tol=1e-7)
+    s0 = L.Solver(pk.centres, pk.radii, L.Params(precision=L.FP64, **kw))
+    s0.precompute(L.MOBILITY)
+    A, E = s0.pair_blocks(L.MOBILITY)
+    s0.close()
+    so = System(pk.centres, pk.radii, POLY, "mobility", blocks=[{"A": A[q], "E": E[q]} for q in range(len(A))],
+                dense_limit=0)
+    radii_cls = []
+    for r in pk.radii:
+        if float(r) not in radii_cls:
+            radii_cls.append(float(r))
+    fac = [onebody_factors(so.onebody[r], PACKING.Nc) for r in radii_cls]
+    Ut, sg, V, rk = (np.concatenate([f[q] for f in fac]) for q in range(4))
+    sols, vels, infos = {}, {}, {}
+    for name, prec in (("fp64", L.FP64), ("mixed", L.MIXED)):
+        s = L.Solver(pk.centres, pk.radii, L.Params(precision=prec, **kw))
+        s.set_pair_blocks(L.MOBILITY, A, E)
+        s.set_onebody(L.MOBILITY, Ut, sg, V, rk)
+        vels[name], infos[name] = s.solve(L.MOBILITY, ft)
+        x = torch.zeros(pk.P * 144, dtype=torch.float64, device="cuda")
+        s.solution(x)
+        torch.cuda.synchronize()
+        sols[name] = x.cpu().numpy().reshape(pk.P, -1)
+        s.close()
+    deg = np.zeros(pk.P, dtype=int)
+    for i, k in so.pairs:
+        deg[i] += 1
+        deg[k] += 1
+    tg = np.unique(np.concatenate([[int(np.argmax(deg))], np.random.default_rng(31).choice(pk.P, 2, replace=False)]))
+    b = so.rhs_mobility(ft, tg)
+    res = {k: rel(so.matvec_exclusion(x, tg, dtype=np.longdouble), b) for k, x in sols.items()}
+    dv = rel(vels["mixed"], vels["fp64"])
+    print(f"P = 1000 poly, extended-precision residual on {len(tg) * 144} rows: fp64 {res['fp64']:.2e} "
+          f"({infos['fp64']['iters']} it), refined mixed {res['mixed']:.2e} ({infos['mixed']['iters']} it, "
+          f"{infos['mixed']['refine_rounds']} FP64 residuals, FP64 relres {infos['mixed']['relres']:.1e}); "
+          f"velocities differ by {dv:.2e}")
+    assert infos["fp64"]["converged"] and infos["mixed"]["converged"]
+    assert res["mixed"] <= max(1.5 * res["fp64"], 1e-7) and res["mixed"] <= 1e-5
+    assert dv < 3e-5
+
+
+@pytest.fixture(scope="module")
+def p10k(L):
+    pk = w.packing_p10000()
+    s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, tol=1e-6))
+    s.precompute(L.MOBILITY)
+    A, E = s.pair_blocks(L.MOBILITY)
+    return pk, s, A, E
+
+
+def test_p10000_sampled_pair_blocks(L, p10k):
+    """20 of the device's ~10^4 pair blocks, spread over the pair list,
+    against the oracle's SVD-truncated ones: the unique parts agree -- E (the
+    fine sources' rigid-body moments) and C A (the compressed field on the
+    peanut) -- within 1e-5."""
+    pk, s, A, E = p10k
+    pairs = s.pairs()
+    from oracle.onebody import OneBody
+    ob = OneBody(1.0, PACKING, "mobility")
+    picks = np.linspace(0, len(pairs) - 1, 20).astype(int)
+    worst_e = worst_ca = 0.0
+    for q in picks:
+        i, k = pairs[q]
+        b = pair_blocks(pk.centres[i], 1.0, pk.centres[k], 1.0, ob, ob, PACKING, "mobility", 1.0, keep=True)
+        worst_e = max(worst_e, rel(E[q], b["E"]))
+        worst_ca = max(worst_ca, rel(b["C"] @ A[q], b["C"] @ b["A"]))
+    print(f"P = 10^4, 20 sampled pairs: E {worst_e:.2e}, C A {worst_ca:.2e}")
+    assert worst_e < 1e-5 and worst_ca < 1e-5
+
+
+def test_p10000_matvec_sampled_rows_real_blocks(L, p10k):
+    """The P = 10^4 matvec with the device's own pair blocks, given to the
+    oracle as its blocks (identical blocks on both sides), and identical
+    one-body SVD factors: 1008 sampled target rows (7 disks, the first the
+    disk with the most contacts) of the FP64 and mixed device matvecs
+    against the oracle's exclusion form of Algorithm 3 over all 6e5 sources
+    and ~10^4 pair corrections.  The real corrections make the sums badly
+    conditioned, so the FP64 bound is the rounding band of two FP64
+    evaluations, 100 eps_64 x the condition number of the sums (at least
+    1e-12); mixed 1e-6."""
+    pk, s, A, E = p10k
+    P = pk.P
+    blocks = [{"A": A[q], "E": E[q]} for q in range(len(A))]
+    so = System(pk.centres, pk.radii, PACKING, "mobility", blocks=blocks, dense_limit=0)
+    assert [tuple(x) for x in s.pairs()] == so.pairs
+    s.set_onebody(L.MOBILITY, *onebody_factors(so.ob[0], PACKING.Nc))
+    deg = np.zeros(P, dtype=int)
+    for i, k in so.pairs:
+        deg[i] += 1
+        deg[k] += 1
+    rng = np.random.default_rng(23)
+    targets = np.unique(np.concatenate([[int(np.argmax(deg))], rng.choice(P, 6, replace=False)]))
+    mu = w.smooth_surface_vector(P, PACKING.Mc, 29).reshape(P, -1)
+    ref = so.matvec_exclusion(mu, targets)
+    kappa = so.exclusion_condition(mu, targets)
+    md = torch.tensor(mu.ravel(), dtype=torch.float64, device="cuda")
+    out = {}
+    for prec in (L.FP64, L.MIXED):
+        ud = torch.zeros_like(md)
+        s.matvec(L.MOBILITY, md, ud, prec)
+        torch.cuda.synchronize()
+        out[prec] = ud.cpu().numpy().reshape(P, -1)[targets]
+    e64, e32 = rel(out[L.FP64], ref), rel(out[L.MIXED], ref)
+    bound = max(1e-12, 100 * EPS64 * kappa)
+    print(f"P = 10^4 real blocks, {len(targets) * 144} rows: condition {kappa:.2e}; fp64 {e64:.2e} "
+          f"(bound {bound:.1e}), mixed {e32:.2e}")
+    assert e64 < bound
+    assert e32 < 1e-6
+
+
+def test_p10000_refined_mixed_solve_reaches_fp64_tol(L, p10k):
+    """The P = 10^4 mobility solve (tol 1e-6) in mixed precision, refined
+    against the FP64 operator: its FP64 residual, reported and recomputed
+    here from the device's FP64 matvec and right-hand side, is at most tol."""
+    pk, s, _, _ = p10k
+    s.invalidate()                      # back to the device's own one-body factors
+    ft = w.forces_torques(pk.P, 7)
+    v, info = s.solve(L.MOBILITY, ft)
+    res = fp64_residual(L, s, L.MOBILITY, ft)
+    print(f"P = 10^4 refined mixed: {info['iters']} it, {info['refine_rounds']} FP64 residuals, "
+          f"relres {info['relres']:.2e} (recomputed {res:.2e}), gmres estimate {info['relres_gmres']:.1e}")
+    assert info["converged"] and info["relres"] <= 1e-6 and res <= 1.05e-6
+    assert np.all(np.isfinite(v))
+
+
+def test_stokeslet_kernel_full_size_sampled_targets(L):
+    """The stand-alone Stokeslet tile sums at the P = 10^4 size (7.2e5
+    targets x 6e5 sources, the bench's case), through the autotuned lean
+    kernel and the series kernel, against the oracle's FP64 Stokeslet on 400
+    sampled targets: within 1e-6."""
+    n, h = 100, 4.4
+    g = (np.arange(n) + 0.5) * h
+    cx, cy = np.meshgrid(g, g)
+    centres = np.stack([cx.ravel(), cy.ravel()], -1)
+    th = 2 * np.pi * np.arange(60) / 60
+    off = np.broadcast_to(np.stack([0.54 * np.cos(th), 0.54 * np.sin(th)], -1), (n * n, 60, 2)).copy()
+    s = np.random.default_rng(0).standard_normal((n * n, 60, 2)) / 60
+    ph = 2 * np.pi * np.arange(72) / 72
+    targets = ((centres + h / 2)[:, None, :] + 0.5 * np.stack([np.cos(ph), np.sin(ph)], -1)[None]).reshape(-1, 2)
+    d = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    T, Cc, O, S = d(targets), d(centres), d(off), d(s)
+    idx = np.random.default_rng(5).choice(targets.shape[0], 400, replace=False)
+    ys = (centres[:, None, :] + off).reshape(-1, 2)
+    exact = (stokeslet(targets[idx], ys) @ s.reshape(-1)).reshape(-1, 2)
+    for prec in (L.FP32_FAST, L.MIXED_DIRECT):
+        out = L.stokeslet_sum(T, Cc, O, S, precision=prec)
+        torch.cuda.synchronize()
+        e = rel(out.cpu().numpy()[idx], exact)
+        print(f"stokeslet sum precision {prec}: sampled error {e:.2e}")
+        assert e < 1e-6

@@ -177,6 +177,45 @@ def test_p100_matvec_exchanged_blocks(L, p100):
         assert e32 < 1e-6, (j, e32)
 
 
+def test_p100_matvec_against_extended_precision_exclusion_form(L, p100):
+    """With the oracle's real pair blocks the matvec is badly conditioned: the
+    corrected strengths of disks in contact carry high Fourier modes of size
+    up to ~1e8 |mu| whose fields nearly cancel, so ANY FP64 evaluation of
+    Algorithm 3 -- the oracle's literal form, its exclusion form, or the
+    device's -- errs by about eps_64 times the condition number of the sums
+    (Sigma |S| |s| / |u|, 1e5..1e8 here).  The reference is therefore the
+    oracle's exclusion form evaluated in extended precision (np.longdouble)
+    on the same FP64 blocks, factors and points, on the 8 disks with the most
+    contacts.  Measured here on CPU, the oracle's own FP64 evaluations sit
+    at 0.2..20 eps_64 x that condition number (1e-10..7e-8).  The device's
+    FP64 matvec is another FP64 evaluation of the same sums: it must be no
+    further from the exact value than 10 times the oracle's FP64 exclusion
+    form, or 50 eps_64 x the condition number, or 1e-12, whichever is
+    largest.  Mixed within 1e-6."""
+    pk, so, ft, vs = p100
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING))
+    s.set_pair_blocks(L.MOBILITY, np.stack([b["A"] for b in so.blocks]), np.stack([b["E"] for b in so.blocks]))
+    s.set_onebody(L.MOBILITY, *onebody_factors(so.ob[0], PACKING.Nc))
+    deg = np.zeros(so.P, dtype=int)
+    for i, k in so.pairs:
+        deg[i] += 1
+        deg[k] += 1
+    targets = np.sort(np.argsort(-deg, kind="stable")[:8])
+    for j in (0, 3, 7):
+        v = vs[j]
+        exact = so.matvec_exclusion(v, targets, dtype=np.longdouble)
+        kappa = so.exclusion_condition(v, targets)
+        e64 = rel(gpu_matvec(L, s, L.MOBILITY, v, L.FP64)[targets], exact)
+        e32 = rel(gpu_matvec(L, s, L.MOBILITY, v, L.MIXED)[targets], exact)
+        e_ex = rel(so.matvec_exclusion(v, targets), exact)
+        e_lit = rel(so.matvec(v, targets), exact)
+        bound = max(1e-12, 10 * e_ex, 50 * EPS64 * kappa)
+        print(f"krylov {j}: condition {kappa:.2e}; device fp64 {e64:.2e}, oracle fp64 exclusion {e_ex:.2e}, "
+              f"oracle literal {e_lit:.2e} (bound {bound:.1e}); device mixed {e32:.2e}")
+        assert e64 < bound, (j, e64, bound)
+        assert e32 < 1e-6, (j, e32)
+
+
 @pytest.mark.parametrize("problem", ["mobility", "resistance"])
 def test_p100_matvec_fp64_where_oracle_is_exact(L, p100, problem):
     """Identical one-body pseudo-inverse and zero pair blocks in both (no large
@@ -213,15 +252,60 @@ def test_p100_rhs_mobility(L, p100):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_p100_mobility_solve(L, p100, prec):
     """Full GPU pipeline (device pair precompute by QR) against the oracle's
-    SVD-based solve: velocities within 1e-5."""
+    SVD-based solve: velocities within 1e-5.  The mixed solve is refined
+    against the FP64 operator: its reported residual is the FP64 one."""
     pk, so, ft, _ = p100
     vo, io = so.solve(ft, tol=1e-9)
     s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, precision=prec, tol=1e-9))
     vg, ig = s.solve(L.MOBILITY, ft)
     assert ig["converged"]
     assert rel(vg, vo) < 1e-5, rel(vg, vo)
+    if prec == 1:
+        assert ig["refine_rounds"] >= 1
     vg2, _ = s.solve(L.MOBILITY, ft)
     assert np.array_equal(vg, vg2)          # bitwise reproducible
+
+
+def fp64_residual(L, s, problem, data):
+    """|b - A_64 x| / |b| of the handle's last solution x: the device's FP64
+    matvec and FP64 right-hand side, recomputed here."""
+    n = s.P * s.params.Mc * 2
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s.solution(x)
+    b = torch.zeros_like(x)
+    s.rhs(problem, dev(data), b, L.FP64)
+    ax = torch.zeros_like(x)
+    s.matvec(problem, x, ax, L.FP64)
+    torch.cuda.synchronize()
+    return float((b - ax).norm() / b.norm())
+
+
+def test_p100_mixed_refinement_rounds(L, p100):
+    """The refinement of the mixed solve against the FP64 operator.  The FP64
+    evaluation of the two-body operator has a rounding floor (the corrected
+    strengths of contacts are ~1e7 times the field): even the FP64 solve at
+    tol 1e-10 has a true FP64 residual of ~2e-7 here.  Refined, the mixed
+    solution's FP64 residual falls below that floor's level and below the
+    unrefined mixed solution's; the velocities agree with the FP64 solve
+    within 1e-6."""
+    pk, so, ft, _ = p100
+    tol = 1e-10
+    s64 = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, precision=L.FP64, tol=tol))
+    v64, i64 = s64.solve(L.MOBILITY, ft)
+    r64 = fp64_residual(L, s64, L.MOBILITY, ft)
+    s0 = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, precision=L.MIXED, tol=tol, refine=0))
+    v0, i0 = s0.solve(L.MOBILITY, ft)
+    r0 = fp64_residual(L, s0, L.MOBILITY, ft)
+    sr = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, precision=L.MIXED, tol=tol))
+    vr, ir = sr.solve(L.MOBILITY, ft)
+    rr = fp64_residual(L, sr, L.MOBILITY, ft)
+    print(f"fp64 {i64['iters']} it, true residual {r64:.1e}; mixed unrefined {i0['iters']} it, residual {r0:.1e}, "
+          f"err {rel(v0, v64):.2e}; refined {ir['iters']} it in {ir['refine_rounds']} FP64 residuals, relres "
+          f"{ir['relres']:.1e} (recomputed {rr:.1e}), err {rel(vr, v64):.2e}")
+    assert i64["converged"] and ir["converged"] and ir["refine_rounds"] >= 2
+    assert abs(rr - ir["relres"]) <= 1e-3 * rr + 1e-15         # the reported residual is the FP64 one
+    assert rr <= 1.5 * r64 and rr < r0
+    assert rel(vr, v64) < 1e-6
 
 
 # ----------------------------------------------------------------- clusters
@@ -277,6 +361,8 @@ def test_edge_cases(L):
     s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, maxit=3, tol=1e-14))
     v, info = s.solve(L.MOBILITY, w.forces_torques(100, 5))
     assert not info["converged"] and info["iters"] == 3 and np.all(np.isfinite(v)) and np.abs(v).max() > 0
+    # maxit bounds the iterations of every refinement round together
+    assert info["refine_rounds"] == 1
 
 
 def test_stokeslet_sum_standalone(L):

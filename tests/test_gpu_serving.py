@@ -90,3 +90,77 @@ def test_admission_and_polling(L):
         assert rc == 0 and np.all(np.isfinite(out))
     assert srv.lib.lmfs_poll(srv.s, 999999, None, None, 0) == L._lib.LMFS_ERR_INVALID   # unknown ticket
     srv.close()
+
+
+def test_one_failing_request_leaves_the_mix_intact(L, monkeypatch):
+    """A request whose Arnoldi step fails (a host-side fake of a failing
+    launch: LMFS_TEST_FAIL_TICKET names it) ends with LMFS_ERR_CUDA alone; the
+    requests it was interleaved with finish normally with the results they
+    have when run alone (bitwise)."""
+    reqs = requests(6, seed=3)
+    alone = []
+    for pk, problem, data in reqs:
+        s = L.Solver(pk.centres, pk.radii, params(L, L.MIXED))
+        out, info = s.solve(problem, data)
+        assert info["converged"] and info["iters"] > 3
+        alone.append(out)
+        s.close()
+    monkeypatch.setenv("LMFS_TEST_FAIL_TICKET", "3")
+    srv = L.Server(hbm_budget_bytes=20 << 30, max_slots=6, precision=L.MIXED, engine=0)
+    monkeypatch.delenv("LMFS_TEST_FAIL_TICKET")
+    tickets = [srv.submit(pk.centres, pk.radii, problem, data, params(L, L.MIXED)) for pk, problem, data in reqs]
+    assert tickets[2][0] == 3
+    for q, ((t, P), ref) in enumerate(zip(tickets, alone)):
+        rc, out, info = srv.poll(t, P, timeout_us=120_000_000)
+        if q == 2:
+            assert rc == L._lib.LMFS_ERR_CUDA
+        else:
+            assert rc == 0, L._lib.strerror(rc)
+            assert np.array_equal(out, ref)
+    srv.close()
+
+
+@pytest.mark.parametrize("problem", [0, 1])
+def test_admission_estimate_covers_what_a_solve_uses(L, problem):
+    """The server admits a request by lmfs_estimate_bytes.  Held against the
+    library pool's high-water mark over a whole solve of that request (create,
+    precompute, right-hand side, GMRES with refinement, post-processing), the
+    estimate must cover what was used."""
+    pk = w.packing_p100()
+    data = w.forces_torques(pk.P, 1) if problem == 1 else w.rigid_velocities(pk.P, 1)
+    prm = L.Params(tol=1e-7)
+    est = L.estimate_bytes(pk.centres, pk.radii, prm)
+    torch.cuda.synchronize()
+    base = L.pool_stats(0, reset=True)
+    s = L.Solver(pk.centres, pk.radii, prm)
+    s.solve(problem, data)
+    torch.cuda.synchronize()
+    used = L.pool_stats(0)["used_high"] - base["used"]
+    s.close()
+    print(f"problem {problem}: estimate {est / 2**20:.1f} MiB, pool high-water over the solve {used / 2**20:.1f} MiB "
+          f"(ratio {est / used:.2f})")
+    assert 0 < used <= est
+
+
+def test_torch_allocator_gives_the_same_solve(L):
+    """lmfs_params.dev_alloc / dev_free wired to PyTorch's caching allocator
+    (through the C adapter, no Python in the allocation path): the solve is
+    bitwise the one made from the library's own pool, the library pool does
+    not grow during it, and PyTorch's allocator saw the handle's buffers."""
+    pk = w.packing_p100()
+    ft = w.forces_torques(pk.P, 5)
+    ref, _ = L.Solver(pk.centres, pk.radii, L.Params(tol=1e-7)).solve(L.MOBILITY, ft)
+    torch.cuda.synchronize()
+    base = L.pool_stats(0, reset=True)
+    torch.cuda.reset_peak_memory_stats()
+    t0 = torch.cuda.max_memory_allocated()
+    s = L.Solver(pk.centres, pk.radii, L.Params(tol=1e-7, allocator="torch"))
+    out, info = s.solve(L.MOBILITY, ft)
+    torch.cuda.synchronize()
+    grew = L.pool_stats(0)["used_high"] - base["used"]
+    peak = torch.cuda.max_memory_allocated() - t0
+    s.close()
+    print(f"torch allocator: peak {peak / 2**20:.1f} MiB through PyTorch, library pool growth {grew} B")
+    assert info["converged"] and np.array_equal(out, ref)
+    assert grew == 0
+    assert peak > 100 << 20

@@ -1,10 +1,14 @@
 """lmfs_stokeslet_sum_noalloc, the entry point for callers that cannot let the
 library allocate device memory, against the allocating lmfs_stokeslet_sum.
 
-Both are called through the C ABI on the same device inputs; two calls in a
-row with different strengths check that nothing left in the shared fixed
-scratch array from the first call leaks into the second.  Collected last so
-that a failure here does not hide the other tests' results.
+Both are called through the C ABI on the same device inputs, and both are
+compared with the oracle's FP64 Stokeslet sum.  The first call puts a target
+inside a source disk's series range, so the kernel sets the range error flag
+in the shared fixed scratch array and the call fails with LMFS_ERR_INVALID;
+the two valid calls that follow (different strengths) must succeed and match,
+which shows that the flags and every scratch region are reset and rewritten,
+not left over.  Collected last so that a failure here does not hide the other
+tests' results.
 """
 import ctypes
 
@@ -38,7 +42,14 @@ def test_noalloc_matches_allocating_entry_point():
     build.build()
     lib = _lib.load()
     p = lambda x: ctypes.c_void_p(x.data_ptr())
+    from oracle.kernel import stokeslet
     stream = torch.cuda.current_stream().cuda_stream
+    # a failing call first: one target 1.0 from a disk centre (inside 4 x 0.54)
+    T, Cc, O, S, nt, nd, npd = case(1)
+    bad = torch.tensor([[Cc[0, 0].item() + 1.0, Cc[0, 1].item()]], dtype=torch.float64, device="cuda")
+    junk = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
+    rc = lib.lmfs_stokeslet_sum_noalloc(p(bad), 1, p(Cc), p(O), p(S), nd, npd, 1.0, ctypes.c_void_p(stream), p(junk))
+    assert rc == _lib.LMFS_ERR_INVALID and "ring radius" in _lib.strerror(rc)
     for seed in (1, 2):                      # two calls in a row, different inputs
         T, Cc, O, S, nt, nd, npd = case(seed)
         ref = torch.zeros((nt, 2), dtype=torch.float64, device="cuda")
@@ -51,6 +62,10 @@ def test_noalloc_matches_allocating_entry_point():
         r, o = ref.cpu().numpy(), out.cpu().numpy()
         assert np.all(np.isfinite(o))
         assert np.linalg.norm(o - r) / np.linalg.norm(r) < TOL
+        # and the oracle's FP64 direct sum of the same sources
+        tg, cg, og, sg = (x.cpu().numpy() for x in (T, Cc, O, S))
+        exact = (stokeslet(tg, (cg[:, None, :] + og).reshape(-1, 2)) @ sg.reshape(-1)).reshape(-1, 2)
+        assert np.linalg.norm(o - exact) / np.linalg.norm(exact) < TOL
     # beyond the fixed scratch size: a clear error, not an overrun
     big_nd = 20000
     rc = lib.lmfs_stokeslet_sum_noalloc(p(T), nt, p(Cc), p(O), p(S), big_nd, npd, 1.0, ctypes.c_void_p(stream), p(out))
