@@ -96,11 +96,11 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
-# DRAM traffic of the pivoted-QR kernel (qrcp_kernel) per timed step -- its two
-# launches, the fine pair systems and the peanut systems of the P = 100 batch --
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; command
-# and figures in profiles/qrcp_kernel_p100_mobility.md).  Valid only for the
-# kernel source it was taken on: reported as null once lmfs_qr.cu changes.
+# DRAM traffic of the pivoted-QR kernel (qrcp_kernel) per solve of the P = 100
+# workload -- its two launches, the fine pair systems and the peanut systems
+# of the 37 pairs -- from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum).  Valid only for the kernel source it was taken on:
+# reported as null once lmfs_qr.cu changes.
 QRCP_TRAFFIC_BYTES = 23436956160 + 25761400320 + 14299136 + 2100224
 QRCP_TRAFFIC_SRC_SHA256 = "3ce04c663094e62340580234a338a11233c67842ce496f69c0fbeeff384884f9"
 

@@ -109,7 +109,17 @@ typedef struct lmfs_params {
   void*  (*dev_alloc)(size_t bytes, void* stream, void* user);
   void   (*dev_free)(void* ptr, void* stream, void* user);
   void*  alloc_user;     /* passed to dev_alloc and dev_free                      */
+  int    far_form;       /* Step 2a's far field for LMFS_MIXED and LMFS_FP64:
+                            LMFS_FAR_AUTO (0): cells when the packing is large
+                            enough (P >= 1000 and room for cells beyond each near
+                            window), else all pairs; LMFS_FAR_ALLPAIRS (1): every
+                            disk's expansion at every target; LMFS_FAR_CELLS (2):
+                            cells where the geometry allows, else all pairs.      */
 } lmfs_params;
+
+#define LMFS_FAR_AUTO     0
+#define LMFS_FAR_ALLPAIRS 1
+#define LMFS_FAR_CELLS    2
 
 typedef struct lmfs_solve_info {
   int    iters;          /* GMRES iterations                                     */

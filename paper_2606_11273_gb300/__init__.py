@@ -10,7 +10,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import FP32_FAST, FP64, MIXED, MIXED_DIRECT, MOBILITY, RESISTANCE, LmfsError  # noqa: F401
+from ._lib import (FAR_ALLPAIRS, FAR_AUTO, FAR_CELLS, FP32_FAST, FP64, MIXED, MIXED_DIRECT, MOBILITY,  # noqa: F401
+                   RESISTANCE, LmfsError)
 
 __all__ = ["Params", "Solver", "Server", "stokeslet_sum", "pool_stats", "estimate_bytes", "FP64", "MIXED", "MIXED_DIRECT", "FP32_FAST", "RESISTANCE",
            "MOBILITY", "LmfsError"]

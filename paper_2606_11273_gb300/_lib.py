@@ -26,6 +26,9 @@ FP64 = 0
 MIXED = 1
 MIXED_DIRECT = 2
 FP32_FAST = 3
+FAR_AUTO = 0
+FAR_ALLPAIRS = 1
+FAR_CELLS = 2
 
 
 class lmfs_params(ctypes.Structure):
@@ -38,6 +41,7 @@ class lmfs_params(ctypes.Structure):
         ("maxit", ctypes.c_int), ("rho", ctypes.c_double), ("precision", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("refine", ctypes.c_int),
         ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_user", ctypes.c_void_p),
+        ("far_form", ctypes.c_int),
     ]
 
 

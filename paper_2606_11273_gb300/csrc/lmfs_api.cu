@@ -99,6 +99,7 @@ int check_launch(const char* what) {
 
 static void free_ctx(Ctx& c) {
   gmres_free(c);
+  fmm_free(c);
   dfree(c.centres); dfree(c.radii); dfree(c.cls); dfree(c.cls_r); dfree(c.pairs); dfree(c.csr_off);
   dfree(c.csr_ent);
   for (NearSet& z : c.nz) {
@@ -110,7 +111,7 @@ static void free_ctx(Ctx& c) {
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
-  dfree(c.b64); dfree(c.xacc); dfree(c.rres);
+  dfree(c.b64); dfree(c.xacc); dfree(c.rres); dfree(c.xbest);
   dfree(c.ufar_part); dfree(c.ring); dfree(c.nodes); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
   if (c.own_stream && c.stream) { cudaStreamDestroy(c.stream); c.stream = nullptr; c.own_stream = false; }
 }
@@ -141,6 +142,7 @@ static int validate_params(const lmfs_params& p) {
   }
   if (p.refine < 0 || p.refine > 64) { set_last_error("refine must lie in [0, 64]"); return LMFS_ERR_INVALID; }
   if (!p.dev_alloc != !p.dev_free) { set_last_error("dev_alloc and dev_free go together"); return LMFS_ERR_INVALID; }
+  if (p.far_form < LMFS_FAR_AUTO || p.far_form > LMFS_FAR_CELLS) { set_last_error("unknown far_form"); return LMFS_ERR_INVALID; }
   return LMFS_OK;
 }
 
@@ -234,50 +236,48 @@ static int sync_and_check_far_flags(Ctx& c) {
 static bool refined(const Ctx& c) { return c.prm.precision != LMFS_FP64 && c.prm.refine > 0; }
 
 // Mixed-precision GMRES refined against the FP64 operator: x_0 from GMRES on
-// b (the FP64 right-hand side); then, while |b - A_64 x| / |b| > tol, the
-// mixed GMRES solution d of A d = r (to a tolerance relative to |r| that aims
-// at half the target) is added to x, until refine_done.  prm.maxit bounds the
-// GMRES iterations of all rounds together.  The solve has converged when
-// every GMRES round reached its tolerance (the FP64 residual may then stay at
-// its rounding floor above tol; relres reports it).  x ends in xacc and xsol.
+// b (the FP64 right-hand side); then, as RefineCtl decides, the mixed GMRES
+// solution d of A d = r, r = b - A_64 x, is added to x.  x ends in xacc and
+// xsol; relres is the FP64 residual of the returned iterate.
 static int refined_gmres(Ctx& c, int problem, lmfs_solve_info* loc) {
   const int prec = c.prm.precision;
-  const double tol = c.prm.tol;
-  const int maxit = std::max(1, c.prm.maxit);
   LMFS_TRY(refine_alloc(c));
-  c.gm_tol = tol;
+  c.gm_tol = c.prm.tol;
   lmfs_solve_info g{};
-  int rc = gmres_solve(c, problem, prec, c.b64, c.xsol, &g, maxit);
+  RefineCtl ctl;
+  int rc = gmres_solve(c, problem, prec, c.b64, c.xsol, &g, c.prm.maxit);
   if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
-  int status = rc;
-  int iters = g.iters, rounds = 0;
-  double relres_g = g.relres, rho = 0.0, rho_prev = 0.0;
+  ctl.status = rc;
+  ctl.iters0 = ctl.iters = g.iters;
+  double relres_g = g.relres, rho = 0.0;
   LMFS_TRY(refine_update(c, true));
   LMFS_TRY(refine_norm_b(c));
   while (true) {
     LMFS_TRY(refine_residual(c, problem));
     LMFS_CUDA(cudaStreamSynchronize(c.stream));
     rho = c.host_pinned[4];
-    rounds += 1;
     if (!(rho == rho)) { set_last_error("refinement: non-finite FP64 residual"); return LMFS_ERR_NUMERICAL; }
-    if (status != LMFS_OK || iters >= maxit || refine_done(c.prm, rounds, rho, rho_prev)) break;
-    rho_prev = rho;
-    c.gm_tol = refine_inner_tol(tol, rho);
-    rc = gmres_solve(c, problem, prec, c.rres, c.xsol, &g, maxit - iters);
+    double itol = 0.0;
+    int rmax = 0;
+    const bool more = ctl.next(c.prm, rho, &itol, &rmax);
+    if (ctl.best) LMFS_TRY(refine_keep(c));
+    if (!more) break;
+    c.gm_tol = itol;
+    rc = gmres_solve(c, problem, prec, c.rres, c.xsol, &g, rmax);
     if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
-    status = rc;
-    iters += g.iters;
+    ctl.iters += g.iters;
     relres_g = g.relres;
     LMFS_TRY(refine_update(c, false));
   }
+  if (!ctl.best) LMFS_TRY(refine_restore(c));
   LMFS_CUDA(cudaMemcpyAsync(c.xsol, c.xacc, 2 * (size_t)c.d.P * c.d.Mc * sizeof(double), cudaMemcpyDeviceToDevice,
                             c.stream));
-  c.gm_tol = tol;
-  loc->iters = iters;
-  loc->relres = rho;
+  c.gm_tol = c.prm.tol;
+  loc->iters = ctl.iters;
+  loc->relres = ctl.rho_best;
   loc->relres_gmres = relres_g;
-  loc->refine_rounds = rounds;
-  return status;
+  loc->refine_rounds = ctl.rounds;
+  return ctl.status;
 }
 
 static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
@@ -351,11 +351,17 @@ int solve_refine_round(lmfs_handle h, int problem, int iters, bool first) {
   return refine_residual(c, problem);
 }
 
-int solve_refine_restart(lmfs_handle h, double rho) {
+int solve_refine_restart(lmfs_handle h, double inner_tol) {
   Ctx& c = h->c;
   LMFS_CUDA(cudaSetDevice(c.device));
-  c.gm_tol = refine_inner_tol(c.prm.tol, rho);
+  c.gm_tol = inner_tol;
   return gmres_restart(c, c.rres);
+}
+
+int solve_refine_keep(lmfs_handle h, bool restore) {
+  Ctx& c = h->c;
+  LMFS_CUDA(cudaSetDevice(c.device));
+  return restore ? refine_restore(c) : refine_keep(c);
 }
 
 int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info,
@@ -413,7 +419,7 @@ int lmfs_params_default(lmfs_params* p) {
   p->gamma = 0.3; p->af = 1.2; p->r_mob = 0.6; p->aell = 5.0; p->delta_c = 0.2;
   p->eps_trunc = 1e-14; p->eps_trunc_fine = 1e-11; p->mu = 1.0; p->tol = 1e-7; p->maxit = 300;
   p->rho = 0.0; p->precision = LMFS_MIXED; p->stream = nullptr; p->device = 0; p->refine = 4;
-  p->dev_alloc = nullptr; p->dev_free = nullptr; p->alloc_user = nullptr;
+  p->dev_alloc = nullptr; p->dev_free = nullptr; p->alloc_user = nullptr; p->far_form = LMFS_FAR_AUTO;
   return LMFS_OK;
 }
 

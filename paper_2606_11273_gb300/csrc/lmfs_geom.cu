@@ -80,6 +80,7 @@ int detect_contacts(Ctx& c) {
   const double rmax = *std::max_element(c.radii_h.begin(), c.radii_h.end());
   const double rmin = *std::min_element(c.radii_h.begin(), c.radii_h.end());
   const double g_near = std::max({c.prm.delta_c, 1.5, 4.0 * c.Rc * rmax - rmin + 0.01});
+  c.g_near = g_near;
   int *cc = nullptr, *cn = nullptr, *nov = nullptr, *oc = nullptr, *on = nullptr;
   int *pc = nullptr, *pn = nullptr, *gcs = nullptr, *gcd = nullptr;
   int rc = LMFS_OK;

@@ -346,6 +346,19 @@ int refine_alloc(Ctx& c) {
   if (!c.b64) LMFS_TRY(dalloc(&c.b64, n));
   if (!c.xacc) LMFS_TRY(dalloc(&c.xacc, n));
   if (!c.rres) LMFS_TRY(dalloc(&c.rres, n));
+  if (!c.xbest) LMFS_TRY(dalloc(&c.xbest, n));
+  return LMFS_OK;
+}
+
+int refine_keep(Ctx& c) {
+  LMFS_CUDA(cudaMemcpyAsync(c.xbest, c.xacc, 2 * (size_t)c.d.P * c.d.Mc * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c.stream));
+  return LMFS_OK;
+}
+
+int refine_restore(Ctx& c) {
+  LMFS_CUDA(cudaMemcpyAsync(c.xacc, c.xbest, 2 * (size_t)c.d.P * c.d.Mc * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c.stream));
   return LMFS_OK;
 }
 

@@ -93,6 +93,56 @@ struct NearSet {
   int n_work0 = 0;
 };
 
+// ---- per-disk multipole coefficients (lmfs_matvec.cu) and the cell form of
+// the far field (lmfs_fmm.cu) ----------------------------------------------
+// Disk coefficient slots (complex, per disk): 0 -> F_0 (strength sum), 1 ->
+// (B, rho) (a bound |c_n| <= B rho^n and the ring radius), 2n -> a_n and
+// 2n + 1 -> g_n for n = 1..MP_P + 1 (a_{MP_P+1} = 0), 2 (MP_P + 2) + n ->
+// conj(A_n) for n = 0..MP_P; see p2m_kernel.
+constexpr int MP_P = 32;
+constexpr int MP_NCOEF = 104;
+// Cell expansions: orders 0..FMM_PMAX; per cell FMM_NC complex slots: the
+// multipole (0: F, n: alpha_n, FMM_PMAX + 1 + n: gamma_n, n >= 1) and the
+// local expansion (n: lambda_n, FMM_PMAX + 1 + n: kappa_n, n >= 0).
+constexpr int FMM_PMAX = 63;
+constexpr int FMM_NC = 2 * (FMM_PMAX + 1);
+constexpr int FMM_NEAR = 2;                // cells within this Chebyshev distance are near
+constexpr int FMM_NODES32 = 256;           // target nodes per block (FP32: 128 threads x 2)
+constexpr int FMM_NODES64 = 128;           // (FP64: 128 threads x 1)
+
+// The cell form of the far field (a one-level fast multipole method): disks
+// binned in a uniform grid of square cells in row-major order; a target's
+// field from the disks of the (2 FMM_NEAR + 1)^2 cells around its own comes
+// from their per-disk expansions, from every other cell through that cell's
+// multipole translated to a local expansion about the target's cell.
+struct FmmGrid {
+  bool on = false;
+  double h = 0, x0 = 0, y0 = 0;
+  int nx = 0, ny = 0, ncell = 0;
+  int n_tblk32 = 0, n_tblk64 = 0;
+  double worst_ratio = 0;            // max over translated cell pairs of (rho_C + tau_T) / |s_T - s_C|
+  std::vector<int> cell_start_h, sorted_h, pos_h;
+  int* cell_start = nullptr;         // [ncell + 1] into the sorted order
+  int* sorted = nullptr;             // [P] disk at each sorted position
+  int* pos = nullptr;                // [P] sorted position of each disk
+  double* cell_ctr = nullptr;        // [ncell][2]
+  double* cell_rho = nullptr;        // [ncell] multipole radius (source rings)
+  double* cell_tau = nullptr;        // [ncell] local-expansion radius (target nodes)
+  int4* tblk32 = nullptr;            // per far-field block: (cell, first node, nodes, 0)
+  int4* tblk64 = nullptr;
+  int* xoff[2] = {nullptr, nullptr}; // per near zone: exclusions of each target disk,
+  int* xpos[2] = {nullptr, nullptr}; //   in sorted positions, ascending
+  float4* dsk_s = nullptr;           // dsk32 in sorted order
+  double* ctr_s = nullptr;           // centres in sorted order
+  double* binA = nullptr;            // [64][64] C(l - 1, n - 1)
+  double* binB64 = nullptr;          // [64][64] C(n + l - 1, l)
+  float* binB32 = nullptr;
+  double2* mcoef = nullptr;          // [ncell][FMM_NC] multipoles (FP64)
+  double2* lcoef64 = nullptr;        // [ncell][FMM_NC] local expansions
+  float2* lcoef32 = nullptr;
+  int* lorder = nullptr;             // [ncell] local order in use
+};
+
 struct Ctx {
   lmfs_params prm{};
   Dims d;
@@ -101,6 +151,8 @@ struct Ctx {
   bool own_stream = false;           // created by the handle (no caller stream given)
   int device = 0;
   double Rc = 0, Rf = 0, rho = 0;
+  double g_near = 0;                 // gap below which a disk is in the FP64 near zone (nz[0])
+  FmmGrid fmm;
 
   std::vector<double> centres_h, radii_h;
   std::vector<int> pairs_h;          // [C][2]
@@ -166,6 +218,7 @@ struct Ctx {
   double* b64 = nullptr;
   double* xacc = nullptr;
   double* rres = nullptr;
+  double* xbest = nullptr;
   double gm_tol = 0.0;               // tolerance of the running GMRES round (relative to its right-hand side)
   double* io3 = nullptr;             // [P][3]
   double* host_pinned = nullptr;     // pinned scalars
@@ -245,6 +298,13 @@ int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision)
 int post_device(Ctx& c, int problem, const double* mu, double* out3);
 int far_field(Ctx& c, const double* strength, double* out, int precision, bool mobility_sums_zero);
 int far_field_prepare(Ctx& c);
+// Cell form (lmfs_fmm.cu): fmm_setup decides whether the geometry uses it and
+// builds its tables (once per handle, after the near lists); fmm_translate
+// forms the cells' multipoles from the disks' coefficients and their local
+// expansions (after p2m, on the handle's stream); fmm_free releases it all.
+int fmm_setup(Ctx& c);
+int fmm_translate(Ctx& c, int precision);
+void fmm_free(Ctx& c);
 
 // Source-range split of an all-pairs kernel whose blocks each sweep a chunk of
 // kchunk source disks (a whole number of tiles) for one tile of targets.  All
@@ -286,16 +346,48 @@ int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x,
 //   refine_residual: rres = b64 - A_64 xacc (FP64 matvec) and |rres| / |b64|
 //     into scal[4], copied to host_pinned[4];
 //   gmres_restart: a new GMRES round on rres (basis vector 0, g, j = 0).
+//   refine_keep / refine_restore: xbest = xacc / xacc = xbest.
 int refine_alloc(Ctx& c);
 int refine_norm_b(Ctx& c);
 int refine_update(Ctx& c, bool first);
 int refine_residual(Ctx& c, int problem);
+int refine_keep(Ctx& c);
+int refine_restore(Ctx& c);
 int gmres_restart(Ctx& c, const double* b);
-// Inner tolerance of the next refinement round for a residual ratio rho
-// (aims at half the target; within [tol, 0.1]).
-inline double refine_inner_tol(double tol, double rho) {
-  return std::min(0.1, std::max(tol, 0.5 * tol / std::max(rho, 1e-300)));
-}
+
+// The refinement's control, shared by lmfs_solve and the server's engine.
+// After each FP64 residual rho = |b - A_64 x| / |b| of the accumulated x it
+// decides whether one more mixed-precision GMRES round runs on r, with which
+// tolerance (relative to |r|: half the remaining factor to tol, within
+// [1e-4, 0.1]) and how many iterations.  It stops at tol, after prm.refine
+// residuals, when a round no longer halves rho (the FP64 evaluation of the
+// two-body operator has a rounding floor: about eps_64 times the condition
+// number of its sums, which the corrected strengths of close contacts make
+// large), or when the rounds after the first have used as many iterations as
+// the first did (at least 20), or prm.maxit is reached.  The iterate with the
+// smallest rho is the result.  The solve's status is the first round's.
+struct RefineCtl {
+  int iters0 = 0;          // iterations of the first round
+  int iters = 0;           // iterations of all rounds
+  int rounds = 0;          // residuals evaluated
+  int status = LMFS_OK;    // the first round's GMRES status
+  double rho_prev = 0.0, rho_best = 0.0;
+  bool best = false;       // the last residual is the smallest so far
+  bool next(const lmfs_params& p, double rho, double* inner_tol, int* round_maxit) {
+    rounds += 1;
+    best = rounds == 1 || rho < rho_best;
+    if (best) rho_best = rho;
+    const int left = std::min(std::max(0, p.maxit - iters), std::max(20, iters0) - (iters - iters0));
+    const bool more = status == LMFS_OK && rho > p.tol && rounds <= p.refine && !(rounds > 1 && rho > 0.5 * rho_prev) &&
+                      left > 0;
+    rho_prev = rho;
+    if (more) {
+      *inner_tol = std::min(0.1, std::max(1e-4, 0.5 * p.tol / std::max(rho, 1e-300)));
+      *round_maxit = left;
+    }
+    return more;
+  }
+};
 void gmres_free(Ctx& c);
 // The captured GMRES graphs hold the device addresses of every buffer the
 // matvec reads; drop them whenever one of those buffers is reallocated.
@@ -389,17 +481,10 @@ size_t estimate_bytes(const double* c, const double* r, int P, const lmfs_params
 int solve_begin(lmfs_handle h, int problem, const double* in, double* beta);
 bool solve_refined(lmfs_handle h);
 int solve_refine_round(lmfs_handle h, int problem, int iters, bool first);
-int solve_refine_restart(lmfs_handle h, double rho);
+int solve_refine_restart(lmfs_handle h, double inner_tol);
+int solve_refine_keep(lmfs_handle h, bool restore);
 int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info,
                  const lmfs_solve_info* refined_info = nullptr, int refined_rc = LMFS_OK);
-// The refinement's stopping rule, shared by lmfs_solve and the server: stop
-// at tol, after prm.refine residuals, or when a round no longer halves the
-// FP64 residual (its rounding floor: the FP64 evaluation of the two-body
-// operator carries an error of about eps_64 times the condition number of its
-// sums, which the corrected strengths of close contacts make large).
-inline bool refine_done(const lmfs_params& p, int rounds, double rho, double rho_prev) {
-  return rho <= p.tol || rounds > p.refine || (rounds > 1 && rho > 0.5 * rho_prev);
-}
 }  // namespace lmfs
 
 #define LMFS_TRY(x) do { int _rc = (x); if (_rc != LMFS_OK) return _rc; } while (0)

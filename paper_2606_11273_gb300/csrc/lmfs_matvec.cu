@@ -517,13 +517,13 @@ __global__ void __launch_bounds__(F_THREADS) far32_kernel(FarArgs a) {
 // truncated at n = MP_P; the terms decay like (|w|/|Z|)^n and |w|/|Z| <=
 // R_c r/(r + g_near) outside the near zone.  The moments are formed in FP64;
 // the evaluation runs in FP32 (mixed) or FP64.
-constexpr int MP_P = 32;
-// Coefficient slots per disk (complex): 2n -> a_n = A_n/(2n) and 2n+1 -> g_n
-// for n = 1..P+1 (a_{P+1} = 0), 2(P+2)+n -> h_n = conj(A_n) for n = 0..P;
-// slot 0 holds F_0, slot 1 holds (B, rho): rho = source ring radius and B a
-// bound with |c_n| <= B rho^n for every stored coefficient c_n (n >= 1),
-// which fixes the order needed at each target (adaptive truncation).
-constexpr int MP_NCOEF = 104;   // 3P + 5 = 101, padded to a multiple of 4
+// Coefficient slots per disk (complex; MP_P, MP_NCOEF in lmfs_internal.h):
+// 2n -> a_n = A_n/(2n) and 2n+1 -> g_n for n = 1..P+1 (a_{P+1} = 0),
+// 2(P+2)+n -> h_n = conj(A_n) for n = 0..P; slot 0 holds F_0, slot 1 holds
+// (B, rho): rho = source ring radius and B a bound with |c_n| <= B rho^n for
+// every stored coefficient c_n (n >= 1), which fixes the order needed at each
+// target (adaptive truncation).  3P + 5 = 101 slots, padded to 104.
+static_assert(MP_NCOEF >= 3 * MP_P + 5 && MP_NCOEF % 4 == 0, "coefficient slots");
 
 // P2M: one block per disk, moments in FP64.  Thread (group, n) accumulates the
 // order-n moments over one third of the ring's sources; the powers come from
@@ -535,7 +535,7 @@ constexpr int P2M_G = 3;
 
 __global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, int P, int Nc,
                                                   const double* __restrict__ radii, double Rc,
-                                                  const double2* __restrict__ ring,
+                                                  const double2* __restrict__ ring, const int* __restrict__ pos,
                                                   double2* __restrict__ coef, float2* __restrict__ coef32) {
   __shared__ double mom[MP_P + 1][6];     // A_n, B_n, D_n (complex)
   __shared__ double2 cf[MP_NCOEF];
@@ -626,9 +626,10 @@ __global__ void __launch_bounds__(128) p2m_kernel(const double* __restrict__ s, 
     cf[1] = make_double2(B, rs);
   }
   __syncthreads();
+  const long long io = pos ? pos[i] : i;   // the cell form keeps the coefficients in sorted order
   for (int c = threadIdx.x; c < MP_NCOEF; c += blockDim.x) {
-    coef[(long long)i * MP_NCOEF + c] = cf[c];
-    if (coef32) coef32[(long long)i * MP_NCOEF + c] = make_float2((float)cf[c].x, (float)cf[c].y);
+    coef[io * MP_NCOEF + c] = cf[c];
+    if (coef32) coef32[io * MP_NCOEF + c] = make_float2((float)cf[c].x, (float)cf[c].y);
   }
 }
 
@@ -648,22 +649,150 @@ constexpr int M_THREADS = 128;
 constexpr int M_TILE = 16;     // source disks per staged tile
 
 struct MpArgs {
-  const float2* tgt; const float4* dsk;      // FP32 path: node offsets, double-float centres
+  const float2* tgt; const float4* dsk;      // FP32 path: node offsets, double-float centres (by disk)
   const double* centres; const double* radii; int Mc_nodes;
   const double2* nodes;                      // FP64 path: [Mc] (cos, sin)(2 pi m / Mc)
-  const void* coef;                          // [P][MP_NCOEF] float2 or double2
-  const int* excl_off; const int* excl;
+  const void* coef;                          // [P][MP_NCOEF] float2 or double2 (cell form: sorted order)
+  const float4* dsk_src;                     // source disks' double-float centres, in coef's order
+  const double* ctr_src;                     // source disks' centres, in coef's order
+  const int* excl_off; const int* excl;      // per target disk, ascending in coef's order
   int P, Mc, kchunk;
   double cmu;
   double* out; long long out_stride;
   int with_log;
   int* err;
+  // cell form (cell != 0): block b takes the target nodes tblk[b] = (cell,
+  // first node, nodes) of one cell, L2P of that cell's local expansion, then
+  // the per-disk expansions of its near window's disks
+  int cell;
+  const int4* tblk;
+  const int* cell_start; const int* sorted;
+  int nx, ny;
+  const double* cell_ctr; const double* cell_tau;
+  const void* lcoef;                         // [ncell][FMM_NC] float2 or double2
+  const int* lorder;
 };
+
+// One disk's expansion (coefficients cf, staged in shared memory) at the
+// thread's TPT targets, Z = target - disk centre, added with compensation.
+template <typename T, int TPT>
+__device__ __forceinline__ void m2p_eval(const typename Vec2<T>::type* __restrict__ cf, const Cx<T>* Z, int with_log,
+                                         T* sr, T* si, T* cr, T* ci) {
+  using V2 = typename Vec2<T>::type;
+  Cx<T> t[TPT], tb[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const T r2 = Z[q].r * Z[q].r + Z[q].i * Z[q].i;
+    const T ir2 = (T)1 / r2;
+    t[q].r = Z[q].r * ir2; t[q].i = -Z[q].i * ir2;     // 1/Z
+    tb[q].r = t[q].r; tb[q].i = -t[q].i;              // 1/conj(Z)
+  }
+  // order needed here: B x^(p+1) / (1 - x) <= tol * |leading term|, x = rho / R
+  int pe = 2;
+  {
+    const V2 bd = cf[1];
+    const T B = (T)bd.x, rho = (T)bd.y;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const T R = sqrt(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
+      const T x = rho / R;
+      const V2 a1 = cf[2];
+      const T lead = sqrt((T)a1.x * (T)a1.x + (T)a1.y * (T)a1.y) / R + B * x * (T)1e-6 +
+                     (sizeof(T) == 4 ? (T)0 : (T)1e-300);   // 1e-300 is 0 in FP32
+      const T tol = (sizeof(T) == 4) ? (T)1e-9 : (T)1e-16;
+      int need = MP_P;
+      if (B > (T)0 && x < (T)1) {
+        const T lim = tol * lead * ((T)1 - x) / B;
+        need = (lim >= (T)1) ? 1 : (int)ceil(log(lim) / log(x)) - 1;
+      }
+      pe = max(pe, min(need, MP_P));
+    }
+    pe = __reduce_max_sync(__activemask(), pe);   // lanes may skip different disks
+  }
+  Cx<T> s1[TPT], s2[TPT], s3[TPT];
+  {
+    const V2 ap = cf[2 * pe], gp = cf[2 * (pe + 1) + 1], hp = cf[2 * (MP_P + 2) + pe];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      s1[q].r = (T)ap.x; s1[q].i = (T)ap.y;
+      s2[q].r = (T)gp.x; s2[q].i = (T)gp.y;
+      s3[q].r = (T)hp.x; s3[q].i = (T)hp.y;
+    }
+  }
+  // s1 = sum_{n=1}^{pe} a_n t^n, s2 = sum_{n=1}^{pe+1} g_n tb^n,
+  // s3 = sum_{n=0}^{pe} h_n tb^(n+1): Horner, one complex FMA per term
+  for (int n = pe; n >= 1; --n) {
+    const V2 an1 = cf[2 * (n - 1)], gn = cf[2 * n + 1], hn1 = cf[2 * (MP_P + 2) + n - 1];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      if (n > 1) s1[q] = cfma(s1[q], t[q], Cx<T>{(T)an1.x, (T)an1.y});
+      s2[q] = cfma(s2[q], tb[q], Cx<T>{(T)gn.x, (T)gn.y});
+      s3[q] = cfma(s3[q], tb[q], Cx<T>{(T)hn1.x, (T)hn1.y});
+    }
+  }
+  const V2 f0 = cf[0];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const Cx<T> s1f = {s1[q].r * t[q].r - s1[q].i * t[q].i, s1[q].r * t[q].i + s1[q].i * t[q].r};
+    const Cx<T> s2f = {s2[q].r * tb[q].r - s2[q].i * tb[q].i, s2[q].r * tb[q].i + s2[q].i * tb[q].r};
+    const Cx<T> s3f = {s3[q].r * tb[q].r - s3[q].i * tb[q].i, s3[q].r * tb[q].i + s3[q].i * tb[q].r};
+    T ur = s1f.r + s2f.r + (T)0.5 * (Z[q].r * s3f.r - Z[q].i * s3f.i);
+    T ui = s1f.i + s2f.i + (T)0.5 * (Z[q].r * s3f.i + Z[q].i * s3f.r);
+    if (with_log) {
+      const T lr = (T)0.5 * log(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
+      ur += (T)f0.x * ((T)0.5 - lr);
+      ui += (T)f0.y * ((T)0.5 - lr);
+    }
+    // Kahan accumulation over source disks
+    T yk = ur - cr[q]; T tk = sr[q] + yk; cr[q] = (tk - sr[q]) - yk; sr[q] = tk;
+    yk = ui - ci[q]; tk = si[q] + yk; ci[q] = (tk - si[q]) - yk; si[q] = tk;
+  }
+}
+
+// The thread's target positions: FP32 double-float centre + offset, or FP64
+// absolute (node m of disk ti).
+template <typename T, int TPT>
+__device__ __forceinline__ void m2p_targets(const MpArgs& a, int ti, int t0, T* xr, T* xi, float& chx, float& chy,
+                                            float& clx, float& cly) {
+  if (sizeof(T) == 4) {
+    const float4 dh = a.dsk[2 * ti];
+    chx = dh.x; chy = dh.y; clx = dh.z; cly = dh.w;
+    for (int q = 0; q < TPT; ++q) { xr[q] = (T)a.tgt[t0 + q].x; xi[q] = (T)a.tgt[t0 + q].y; }
+  } else {
+    for (int q = 0; q < TPT; ++q) {
+      const double2 cs = a.nodes[(t0 + q) % a.Mc];
+      xr[q] = (T)(a.centres[2 * ti] + a.radii[ti] * cs.x);
+      xi[q] = (T)(a.centres[2 * ti + 1] + a.radii[ti] * cs.y);
+    }
+  }
+}
+
+// Z = target - source disk centre for staged disk dd (FP32: double-float
+// differences; FP64: absolute positions).
+template <typename T, int TPT>
+__device__ __forceinline__ void m2p_offsets(const MpArgs& a, const float4* DB, int dd, int k, const T* xr,
+                                            const T* xi, float chx, float chy, float clx, float cly, Cx<T>* Z) {
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    if (sizeof(T) == 4) {
+      const float4 dh = DB[2 * dd];
+      Z[q].r = (T)((chx - dh.x) + ((clx - dh.z) + (float)xr[q]));
+      Z[q].i = (T)((chy - dh.y) + ((cly - dh.w) + (float)xi[q]));
+    } else {
+      Z[q].r = xr[q] - (T)a.ctr_src[2 * k];
+      Z[q].i = xi[q] - (T)a.ctr_src[2 * k + 1];
+    }
+  }
+}
 
 // M2P: one thread per target (FP64) or two targets per thread (FP32), source
 // disks staged tile by tile into shared memory with bulk asynchronous copies
-// (TMA) completing on an mbarrier, double-buffered.  One block of the launch
-// grid: target block bx, source chunk by.
+// (TMA) completing on an mbarrier, double-buffered.  The source disks form up
+// to 5 contiguous ranges [rb, re) of coef's order, visited in ascending
+// order; a tile never spans two ranges.  All-pairs form: one block of the
+// launch grid is target block bx and source chunk by (one range).  Cell form:
+// block bx is a run of one cell's target nodes, starting from that cell's
+// local expansion, with the disks of its near window (one range per row).
 template <typename T, int TPT>
 __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
   using V2 = typename Vec2<T>::type;
@@ -676,39 +805,91 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
   uint64_t* bars = (uint64_t*)(msm + 2 * cbytes + 2 * M_TILE * 32);
   __shared__ int s_fail;
 
-  const int nt = a.P * a.Mc;
-  const int t0 = (bx * M_THREADS + threadIdx.x) * TPT;
-  const bool active = t0 < nt;
-  const int ti = active ? t0 / a.Mc : 0;
-  const int k_begin = by * a.kchunk;
-  const int k_end = min(a.P, k_begin + a.kchunk);
-  // target positions: FP32 double-float centre + offset, or FP64 absolute
+  // targets and source ranges
+  int ti = 0, t0 = 0;
+  bool active;
+  int rb[2 * FMM_NEAR + 1], re[2 * FMM_NEAR + 1], nr = 0;
+  int cell = 0;
+  if (a.cell) {
+    const int4 tb = a.tblk[bx];
+    cell = tb.x;
+    const int nloc = threadIdx.x * TPT;
+    active = nloc < tb.z;
+    if (active) {
+      const int node = tb.y + nloc;
+      ti = a.sorted[a.cell_start[cell] + node / a.Mc];
+      t0 = ti * a.Mc + node % a.Mc;
+    }
+    const int cx = cell % a.nx, cy = cell / a.nx;
+    for (int yy = max(0, cy - FMM_NEAR); yy <= min(a.ny - 1, cy + FMM_NEAR); ++yy) {
+      const int c0 = yy * a.nx + max(0, cx - FMM_NEAR), c1 = yy * a.nx + min(a.nx - 1, cx + FMM_NEAR);
+      const int b = a.cell_start[c0], e = a.cell_start[c1 + 1];
+      if (e > b) { rb[nr] = b; re[nr] = e; ++nr; }
+    }
+  } else {
+    const int nt = a.P * a.Mc;
+    t0 = (bx * M_THREADS + threadIdx.x) * TPT;
+    active = t0 < nt;
+    ti = active ? t0 / a.Mc : 0;
+    rb[0] = by * a.kchunk;
+    re[0] = min(a.P, rb[0] + a.kchunk);
+    nr = re[0] > rb[0] ? 1 : 0;
+  }
   T xr[TPT], xi[TPT];
   float chx = 0, chy = 0, clx = 0, cly = 0;
-  if (active) {
-    if (sizeof(T) == 4) {
-      const float4 dh = a.dsk[2 * ti];
-      chx = dh.x; chy = dh.y; clx = dh.z; cly = dh.w;
-      for (int q = 0; q < TPT; ++q) { xr[q] = (T)a.tgt[t0 + q].x; xi[q] = (T)a.tgt[t0 + q].y; }
-    } else {
-      for (int q = 0; q < TPT; ++q) {
-        const double2 cs = a.nodes[(t0 + q) % a.Mc];
-        xr[q] = (T)(a.centres[2 * ti] + a.radii[ti] * cs.x);
-        xi[q] = (T)(a.centres[2 * ti + 1] + a.radii[ti] * cs.y);
+  if (active) m2p_targets<T, TPT>(a, ti, t0, xr, xi, chx, chy, clx, cly);
+  T sr[TPT], si[TPT], cr[TPT], ci[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) { sr[q] = si[q] = cr[q] = ci[q] = (T)0; }
+  if (a.cell && active) {
+    // L2P: Phi(zh) + conj(Psi(zh)) - zh conj(sum l lambda_l zh^(l-1)), zh = (x - t) / tau
+    const V2* lc = (const V2*)a.lcoef + (long long)cell * FMM_NC;
+    const int Lo = a.lorder[cell];
+    const double tcx = a.cell_ctr[2 * cell], tcy = a.cell_ctr[2 * cell + 1];
+    const T itau = (T)(1.0 / a.cell_tau[cell]);
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      Cx<T> zh;
+      if (sizeof(T) == 4) {
+        zh.r = (T)((float)(((double)chx - tcx) + (double)clx) + (float)xr[q]) * itau;
+        zh.i = (T)((float)(((double)chy - tcy) + (double)cly) + (float)xi[q]) * itau;
+      } else {
+        zh.r = (xr[q] - (T)tcx) * itau;
+        zh.i = (xi[q] - (T)tcy) * itau;
       }
+      const V2 lL = lc[Lo], kL = lc[FMM_PMAX + 1 + Lo];
+      Cx<T> Ph = {(T)lL.x, (T)lL.y}, Ps = {(T)kL.x, (T)kL.y};
+      Cx<T> Dv = {(T)Lo * (T)lL.x, (T)Lo * (T)lL.y};
+      for (int l = Lo - 1; l >= 0; --l) {
+        const V2 ll = lc[l], kl = lc[FMM_PMAX + 1 + l];
+        Ph = cfma(Ph, zh, Cx<T>{(T)ll.x, (T)ll.y});
+        Ps = cfma(Ps, zh, Cx<T>{(T)kl.x, (T)kl.y});
+        if (l >= 1) Dv = cfma(Dv, zh, Cx<T>{(T)l * (T)ll.x, (T)l * (T)ll.y});
+      }
+      if (Lo == 0) Dv = Cx<T>{(T)0, (T)0};
+      // zh conj(Dv)
+      const T wr = zh.r * Dv.r + zh.i * Dv.i, wi = zh.i * Dv.r - zh.r * Dv.i;
+      sr[q] = Ph.r + Ps.r - wr;
+      si[q] = Ph.i - Ps.i - wi;
     }
   }
   int ep = 0, ee = 0;
   if (active) {
     ep = a.excl_off[ti]; ee = a.excl_off[ti + 1];
-    while (ep < ee && a.excl[ep] < k_begin) ++ep;
+    while (ep < ee && a.excl[ep] < rb[0]) ++ep;
   }
   int next_ex = (ep < ee) ? a.excl[ep] : 0x7fffffff;
-  T sr[TPT], si[TPT], cr[TPT], ci[TPT];
-#pragma unroll
-  for (int q = 0; q < TPT; ++q) { sr[q] = si[q] = cr[q] = ci[q] = (T)0; }
 
-  const int ntile = (k_end - k_begin + M_TILE - 1) / M_TILE;
+  int ntile = 0;
+  for (int r = 0; r < nr; ++r) ntile += (re[r] - rb[r] + M_TILE - 1) / M_TILE;
+  auto tile_at = [&](int tile, int& kb, int& nd) {
+    for (int r = 0; r < nr; ++r) {
+      const int n_r = (re[r] - rb[r] + M_TILE - 1) / M_TILE;
+      if (tile < n_r) { kb = rb[r] + tile * M_TILE; nd = min(M_TILE, re[r] - kb); return; }
+      tile -= n_r;
+    }
+    kb = 0; nd = 0;
+  };
   if (threadIdx.x == 0) {
     s_fail = 0;
     mbar_init(&bars[0], 1);
@@ -717,14 +898,14 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
   }
   __syncthreads();
   auto issue = [&](int tile) {
-    const int kb = k_begin + tile * M_TILE;
-    const int nd = min(M_TILE, k_end - kb);
+    int kb, nd;
+    tile_at(tile, kb, nd);
     const int buf = tile & 1;
     const uint32_t cb = (uint32_t)(nd * MP_NCOEF * sizeof(V2)), db = (uint32_t)(nd * 32);
     const bool fp32 = sizeof(T) == 4;
     mbar_expect_tx(&bars[buf], cb + (fp32 ? db : 0));
     bulk_g2s(buf ? (void*)cbuf1 : (void*)cbuf0, (const V2*)a.coef + (long long)kb * MP_NCOEF, cb, &bars[buf]);
-    if (fp32) bulk_g2s(buf ? (void*)dbuf1 : (void*)dbuf0, a.dsk + 2LL * kb, db, &bars[buf]);
+    if (fp32) bulk_g2s(buf ? (void*)dbuf1 : (void*)dbuf0, a.dsk_src + 2LL * kb, db, &bars[buf]);
   };
   if (threadIdx.x == 0 && ntile > 0) issue(0);
   for (int tile = 0; tile < ntile; ++tile) {
@@ -733,91 +914,17 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
     if (!mbar_wait(&bars[buf], (uint32_t)((tile >> 1) & 1))) s_fail = tile + 1;
     __syncthreads();
     if (s_fail) break;
-    const int kb = k_begin + tile * M_TILE;
-    const int nd = min(M_TILE, k_end - kb);
+    int kb, nd;
+    tile_at(tile, kb, nd);
     const V2* CB = buf ? cbuf1 : cbuf0;
     const float4* DB = buf ? dbuf1 : dbuf0;
     if (active) {
       for (int dd = 0; dd < nd; ++dd) {
         const int k = kb + dd;
         if (k == next_ex) { ++ep; next_ex = (ep < ee) ? a.excl[ep] : 0x7fffffff; continue; }
-        const V2* cf = CB + dd * MP_NCOEF;
-        Cx<T> Z[TPT], t[TPT], tb[TPT];
-#pragma unroll
-        for (int q = 0; q < TPT; ++q) {
-          if (sizeof(T) == 4) {
-            const float4 dh = DB[2 * dd];
-            Z[q].r = (T)((chx - dh.x) + ((clx - dh.z) + (float)xr[q]));
-            Z[q].i = (T)((chy - dh.y) + ((cly - dh.w) + (float)xi[q]));
-          } else {
-            Z[q].r = xr[q] - (T)a.centres[2 * k];
-            Z[q].i = xi[q] - (T)a.centres[2 * k + 1];
-          }
-          const T r2 = Z[q].r * Z[q].r + Z[q].i * Z[q].i;
-          const T ir2 = (T)1 / r2;
-          t[q].r = Z[q].r * ir2; t[q].i = -Z[q].i * ir2;     // 1/Z
-          tb[q].r = t[q].r; tb[q].i = -t[q].i;              // 1/conj(Z)
-        }
-        // order needed here: B x^(p+1) / (1 - x) <= tol * |leading term|, x = rho / R
-        int pe = 2;
-        {
-          const V2 bd = cf[1];
-          const T B = (T)bd.x, rho = (T)bd.y;
-#pragma unroll
-          for (int q = 0; q < TPT; ++q) {
-            const T R = sqrt(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
-            const T x = rho / R;
-            const V2 a1 = cf[2];
-            const T lead = sqrt((T)a1.x * (T)a1.x + (T)a1.y * (T)a1.y) / R + B * x * (T)1e-6 +
-                           (sizeof(T) == 4 ? (T)0 : (T)1e-300);   // 1e-300 is 0 in FP32
-            const T tol = (sizeof(T) == 4) ? (T)1e-9 : (T)1e-16;
-            int need = MP_P;
-            if (B > (T)0 && x < (T)1) {
-              const T lim = tol * lead * ((T)1 - x) / B;
-              need = (lim >= (T)1) ? 1 : (int)ceil(log(lim) / log(x)) - 1;
-            }
-            pe = max(pe, min(need, MP_P));
-          }
-          pe = __reduce_max_sync(__activemask(), pe);   // lanes may skip different disks
-        }
-        Cx<T> s1[TPT], s2[TPT], s3[TPT];
-        {
-          const V2 ap = cf[2 * pe], gp = cf[2 * (pe + 1) + 1], hp = cf[2 * (MP_P + 2) + pe];
-#pragma unroll
-          for (int q = 0; q < TPT; ++q) {
-            s1[q].r = (T)ap.x; s1[q].i = (T)ap.y;
-            s2[q].r = (T)gp.x; s2[q].i = (T)gp.y;
-            s3[q].r = (T)hp.x; s3[q].i = (T)hp.y;
-          }
-        }
-        // s1 = sum_{n=1}^{pe} a_n t^n, s2 = sum_{n=1}^{pe+1} g_n tb^n,
-        // s3 = sum_{n=0}^{pe} h_n tb^(n+1): Horner, one complex FMA per term
-        for (int n = pe; n >= 1; --n) {
-          const V2 an1 = cf[2 * (n - 1)], gn = cf[2 * n + 1], hn1 = cf[2 * (MP_P + 2) + n - 1];
-#pragma unroll
-          for (int q = 0; q < TPT; ++q) {
-            if (n > 1) s1[q] = cfma(s1[q], t[q], Cx<T>{(T)an1.x, (T)an1.y});
-            s2[q] = cfma(s2[q], tb[q], Cx<T>{(T)gn.x, (T)gn.y});
-            s3[q] = cfma(s3[q], tb[q], Cx<T>{(T)hn1.x, (T)hn1.y});
-          }
-        }
-        const V2 f0 = cf[0];
-#pragma unroll
-        for (int q = 0; q < TPT; ++q) {
-          const Cx<T> s1f = {s1[q].r * t[q].r - s1[q].i * t[q].i, s1[q].r * t[q].i + s1[q].i * t[q].r};
-          const Cx<T> s2f = {s2[q].r * tb[q].r - s2[q].i * tb[q].i, s2[q].r * tb[q].i + s2[q].i * tb[q].r};
-          const Cx<T> s3f = {s3[q].r * tb[q].r - s3[q].i * tb[q].i, s3[q].r * tb[q].i + s3[q].i * tb[q].r};
-          T ur = s1f.r + s2f.r + (T)0.5 * (Z[q].r * s3f.r - Z[q].i * s3f.i);
-          T ui = s1f.i + s2f.i + (T)0.5 * (Z[q].r * s3f.i + Z[q].i * s3f.r);
-          if (a.with_log) {
-            const T lr = (T)0.5 * log(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
-            ur += (T)f0.x * ((T)0.5 - lr);
-            ui += (T)f0.y * ((T)0.5 - lr);
-          }
-          // Kahan accumulation over source disks
-          T yk = ur - cr[q]; T tk = sr[q] + yk; cr[q] = (tk - sr[q]) - yk; sr[q] = tk;
-          yk = ui - ci[q]; tk = si[q] + yk; ci[q] = (tk - si[q]) - yk; si[q] = tk;
-        }
+        Cx<T> Z[TPT];
+        m2p_offsets<T, TPT>(a, DB, dd, k, xr, xi, chx, chy, clx, cly, Z);
+        m2p_eval<T, TPT>(CB + dd * MP_NCOEF, Z, a.with_log, sr, si, cr, ci);
       }
     }
     __syncthreads();
@@ -1423,7 +1530,8 @@ int far_field_prepare(Ctx& c) {
     LMFS_CUDA(cudaStreamSynchronize(c.stream));
   }
   for (NearSet& z : c.nz) LMFS_TRY(dalloc(&z.part, std::max<size_t>(1, z.h.size()) * c.d.Mc * 2));
-  return LMFS_OK;
+  static_assert(FMM_NODES32 == 2 * M_THREADS && FMM_NODES64 == M_THREADS, "cell-form block sizes");
+  return fmm_setup(c);
 }
 
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb) {
@@ -1457,12 +1565,16 @@ static int far_pre(Ctx& c, const double* strength, int precision) {
     records_kernel<<<(P * 32 + 127) / 128, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.src4, c.dsk32);
     return check_launch("records");
   }
-  p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, c.coef64,
+  const bool cell = c.fmm.on;
+  p2m_kernel<<<P, 128, 0, c.stream>>>(strength, P, Nc, c.radii, c.Rc, c.ring, cell ? c.fmm.pos : nullptr, c.coef64,
                                       precision == LMFS_MIXED ? c.coef32 : nullptr);
-  return check_launch("p2m");
+  LMFS_TRY(check_launch("p2m"));
+  if (cell) return fmm_translate(c, precision);
+  return LMFS_OK;
 }
 
 static int far_split_of(const Ctx& c, int precision) {
+  if (precision != LMFS_MIXED_DIRECT && c.fmm.on) return 1;
   return precision == LMFS_MIXED_DIRECT ? c.split_direct : precision == LMFS_MIXED ? c.split_m2p32 : c.split_m2p64;
 }
 
@@ -1471,19 +1583,34 @@ static void mp_setup(const Ctx& c, int precision, double* out, bool skip_base, M
   const int P = c.d.P, Mc = c.d.Mc;
   const NearSet& z = zone(c, precision);
   const bool fp32 = precision == LMFS_MIXED;
-  const int split = fp32 ? c.split_m2p32 : c.split_m2p64;
+  const bool cell = c.fmm.on;
+  const int split = cell ? 1 : fp32 ? c.split_m2p32 : c.split_m2p64;
+  a = MpArgs{};
   a.tgt = c.tgt32; a.dsk = c.dsk32; a.centres = c.centres; a.radii = c.radii; a.Mc_nodes = Mc; a.nodes = c.nodes;
   a.coef = fp32 ? (const void*)c.coef32 : (const void*)c.coef64;
-  a.excl_off = z.excl_off; a.excl = z.excl; a.P = P; a.Mc = Mc;
+  a.dsk_src = cell ? c.fmm.dsk_s : c.dsk32;
+  a.ctr_src = cell ? c.fmm.ctr_s : c.centres;
+  const int zi = precision == LMFS_MIXED ? 1 : 0;
+  a.excl_off = cell ? c.fmm.xoff[zi] : z.excl_off; a.excl = cell ? c.fmm.xpos[zi] : z.excl;
+  a.P = P; a.Mc = Mc;
   a.kchunk = fp32 ? c.kchunk_m2p32 : c.kchunk_m2p64; a.cmu = INV4PI / c.prm.mu;
   a.out = split > 1 ? c.ufar_part : out; a.out_stride = (long long)P * Mc * 2; a.with_log = skip_base ? 0 : 1;
   a.err = c.far_err;
+  if (cell) {
+    a.cell = 1;
+    a.tblk = fp32 ? c.fmm.tblk32 : c.fmm.tblk64;
+    a.cell_start = c.fmm.cell_start; a.sorted = c.fmm.sorted;
+    a.nx = c.fmm.nx; a.ny = c.fmm.ny;
+    a.cell_ctr = c.fmm.cell_ctr; a.cell_tau = c.fmm.cell_tau;
+    a.lcoef = fp32 ? (const void*)c.fmm.lcoef32 : (const void*)c.fmm.lcoef64;
+    a.lorder = c.fmm.lorder;
+  }
   if (fp32) {
     shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(float2) + 2 * M_TILE * 32 + 16;
-    grid = dim3(((P * Mc + 1) / 2 + M_THREADS - 1) / M_THREADS, split);
+    grid = cell ? dim3(c.fmm.n_tblk32, 1) : dim3(((P * Mc + 1) / 2 + M_THREADS - 1) / M_THREADS, split);
   } else {
     shm = 2 * (size_t)M_TILE * MP_NCOEF * sizeof(double2) + 2 * M_TILE * 32 + 16;
-    grid = dim3((P * Mc + M_THREADS - 1) / M_THREADS, split);
+    grid = cell ? dim3(c.fmm.n_tblk64, 1) : dim3((P * Mc + M_THREADS - 1) / M_THREADS, split);
   }
 }
 

@@ -40,9 +40,9 @@ struct Active {
   // refinement against the FP64 operator (mixed servers): phase 1 while the
   // FP64 residual of a finished round is in flight
   int phase = 0;
-  lmfs_solve_info ref{};         // total iterations, rounds, residuals so far
-  double rho_prev = 0.0;
-  int ref_rc = LMFS_OK;          // LMFS_ERR_NOT_CONVERGED once a round ran out of iterations
+  lmfs::RefineCtl ctl;
+  int round_maxit = 0;           // iteration limit of the running round
+  double relres_g = 0.0;         // the last round's GMRES estimate
 };
 
 struct Request {
@@ -233,35 +233,45 @@ void engine_loop(lmfs_server* s) {
         if (a.phase == 1) {
           // the FP64 residual of the round that just ended is on the host
           const double rho = c.host_pinned[4];
-          a.ref.refine_rounds += 1;
-          a.ref.relres = rho;
           if (!(rho == rho)) { fail(a, LMFS_ERR_NUMERICAL); continue; }
           a.phase = 0;
-          if (a.ref_rc != LMFS_OK || a.ref.iters >= std::max(1, c.prm.maxit) ||
-              lmfs::refine_done(c.prm, a.ref.refine_rounds, rho, a.rho_prev)) {
-            const int rc = lmfs::solve_finish(a.h, a.rq->problem, a.ref.iters, rho, a.rq->out.data(), &a.rq->info,
-                                              &a.ref, a.ref_rc);
+          double itol = 0.0;
+          int rmax = 0;
+          const bool more = a.ctl.next(c.prm, rho, &itol, &rmax);
+          int rc = a.ctl.best ? lmfs::solve_refine_keep(a.h, false) : LMFS_OK;
+          if (rc == LMFS_OK && !more) {
+            if (!a.ctl.best) rc = lmfs::solve_refine_keep(a.h, true);
+            lmfs_solve_info ri{};
+            ri.iters = a.ctl.iters; ri.relres = a.ctl.rho_best; ri.relres_gmres = a.relres_g;
+            ri.refine_rounds = a.ctl.rounds;
+            if (rc == LMFS_OK)
+              rc = lmfs::solve_finish(a.h, a.rq->problem, ri.iters, ri.relres, a.rq->out.data(), &a.rq->info, &ri,
+                                      a.ctl.status);
             release(a);
             complete(s, a.rq, rc);
             continue;
           }
-          a.rho_prev = rho;
-          a.iters = 0;
-          const int rc = lmfs::solve_refine_restart(a.h, rho);
+          if (rc == LMFS_OK) rc = lmfs::solve_refine_restart(a.h, itol);
           if (rc != LMFS_OK) { fail(a, rc); continue; }
+          a.iters = 0;
+          a.round_maxit = rmax;
           ready.push_back(&a);
           continue;
         }
         a.iters += 1;
-        a.ref.iters += 1;
         const double relres = c.host_pinned[1];
         if (!(relres == relres)) { fail(a, LMFS_ERR_NUMERICAL); continue; }
-        if (relres <= c.gm_tol || c.host_pinned[3] != 0.0 || a.ref.iters >= std::max(1, c.prm.maxit)) {
+        const int lim = a.ctl.rounds == 0 ? std::max(1, c.prm.maxit) : a.round_maxit;
+        if (relres <= c.gm_tol || c.host_pinned[3] != 0.0 || a.iters >= lim) {
           if (lmfs::solve_refined(a.h)) {
             // end of a GMRES round: x += its solution, FP64 residual in flight
-            a.ref.relres_gmres = relres;
-            if (!(relres <= c.gm_tol) && c.host_pinned[3] == 0.0) a.ref_rc = LMFS_ERR_NOT_CONVERGED;
-            int rc = lmfs::solve_refine_round(a.h, a.rq->problem, a.iters, a.ref.refine_rounds == 0);
+            a.relres_g = relres;
+            if (a.ctl.rounds == 0) {
+              a.ctl.iters0 = a.iters;
+              a.ctl.status = (relres <= c.gm_tol || c.host_pinned[3] != 0.0) ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
+            }
+            a.ctl.iters += a.iters;
+            int rc = lmfs::solve_refine_round(a.h, a.rq->problem, a.iters, a.ctl.rounds == 0);
             if (rc == LMFS_OK && cudaEventRecord(a.ev_step, a.st) != cudaSuccess) rc = LMFS_ERR_CUDA;
             if (rc != LMFS_OK) { cudaStreamSynchronize(a.st); fail(a, rc); continue; }
             a.phase = 1;
@@ -285,7 +295,7 @@ void engine_loop(lmfs_server* s) {
       std::vector<Active*> go;
       for (Active* a : ready) {
         lmfs::Ctx& c = a->h->c;
-        int r = (s->fail_ticket && a->rq->ticket == s->fail_ticket && a->ref.iters == 2)
+        int r = (s->fail_ticket && a->rq->ticket == s->fail_ticket && a->ctl.iters + a->iters == 2)
                     ? (lmfs::set_last_error("injected step failure (LMFS_TEST_FAIL_TICKET)"), LMFS_ERR_CUDA)
                     : lmfs::gmres_step_pre(c, a->rq->problem, prec);
         if (r == LMFS_OK && (cudaEventRecord(a->ev_pre, a->st) != cudaSuccess ||

@@ -178,11 +178,14 @@ def test_p10000_matvec_sampled_rows_real_blocks(L, p10k):
         torch.cuda.synchronize()
         out[prec] = ud.cpu().numpy().reshape(P, -1)[targets]
     e64, e32 = rel(out[L.FP64], ref), rel(out[L.MIXED], ref)
+    e3264 = rel(out[L.MIXED], out[L.FP64])
     bound = max(1e-12, 100 * EPS64 * kappa)
     print(f"P = 10^4 real blocks, {len(targets) * 144} rows: condition {kappa:.2e}; fp64 {e64:.2e} "
-          f"(bound {bound:.1e}), mixed {e32:.2e}")
+          f"(bound {bound:.1e}), mixed {e32:.2e}, mixed vs device fp64 {e3264:.2e}")
     assert e64 < bound
-    assert e32 < 1e-6
+    # the oracle's FP64 reference itself carries ~eps_64 x condition: mixed is
+    # held to 1e-6 against it where that allows, and against the device's FP64
+    assert e32 < max(1e-6, bound) and e3264 < 1e-6
 
 
 def test_p10000_refined_mixed_solve_reaches_fp64_tol(L, p10k):
@@ -225,3 +228,46 @@ def test_stokeslet_kernel_full_size_sampled_targets(L):
         e = rel(out.cpu().numpy()[idx], exact)
         print(f"stokeslet sum precision {prec}: sampled error {e:.2e}")
         assert e < 1e-6
+
+
+@pytest.mark.parametrize("case", ["p10000_mobility", "p1000_poly_resistance"])
+def test_cell_form_matches_all_pairs(L, case):
+    """The far field's cell form (per-disk expansions in each near window,
+    cell multipoles translated to local expansions elsewhere) against the
+    all-pairs form (every disk's expansion at every target), on the same
+    handle data (zero pair blocks, the device's one-body factors): FP64
+    within 1e-11 (the translations are truncated at 1e-17; the two forms sum
+    in different orders), mixed precision within 5e-7 of each other (FP32
+    translations), and mixed within 1e-6 of the FP64 all-pairs result.  The resistance case has
+    strength sums (the logarithmic terms of the expansions)."""
+    if case == "p10000_mobility":
+        pk, problem, kw = w.packing_p10000(), L.MOBILITY, {}
+    else:
+        pk, problem, kw = w.packing_p1000_poly(), L.RESISTANCE, dict(delta_c=0.1)
+    n4 = 4 * PACKING.Nc
+    out = {}
+    for form in (L.FAR_ALLPAIRS, L.FAR_CELLS):
+        s = L.Solver(pk.centres, pk.radii, L.Params(far_form=form, **kw))
+        C = s.n_pairs
+        s.set_pair_blocks(problem, np.zeros((C, n4, n4)), np.zeros((C, 6, n4)))
+        mu = torch.tensor(w.smooth_surface_vector(pk.P, PACKING.Mc, 41).ravel(), dtype=torch.float64, device="cuda")
+        for prec in (L.FP64, L.MIXED):
+            u = torch.zeros_like(mu)
+            s.matvec(problem, mu, u, prec)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            s.matvec(problem, mu, u, prec)
+            ev[1].record()
+            torch.cuda.synchronize()
+            out[(form, prec)] = (u.cpu().numpy(), ev[0].elapsed_time(ev[1]))
+        s.close()
+    ref = out[(L.FAR_ALLPAIRS, L.FP64)][0]
+    e64 = rel(out[(L.FAR_CELLS, L.FP64)][0], ref)
+    e32 = rel(out[(L.FAR_CELLS, L.MIXED)][0], out[(L.FAR_ALLPAIRS, L.MIXED)][0])
+    e32r = rel(out[(L.FAR_CELLS, L.MIXED)][0], ref)
+    ms = {k: round(v[1], 2) for k, v in out.items()}
+    print(f"{case}: cells vs all pairs fp64 {e64:.2e}, mixed {e32:.2e} (mixed cells vs fp64 {e32r:.2e}); "
+          f"matvec ms (form, precision): {ms}")
+    assert e64 < 1e-11
+    assert e32 < 5e-7 and e32r < 1e-6
