@@ -788,6 +788,8 @@ def run_profile_case(case):
         u = torch.zeros_like(mu)
         for _ in range(2):
             s.matvec(L.MOBILITY, mu, u, L.MIXED)
+        if case == "matvec_large":
+            s.matvec(L.MOBILITY, mu, u, L.FP64)
         torch.cuda.synchronize()
     elif case in ("qr", "matvec"):
         pk, ft = workload()

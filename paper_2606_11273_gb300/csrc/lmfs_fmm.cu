@@ -56,6 +56,9 @@ template <typename T> __device__ __forceinline__ C2<T> cpow(C2<T> a, int n) {
   return r;
 }
 __device__ __forceinline__ C2<double> ld(double2 v) { return {v.x, v.y}; }
+template <typename T> struct Vec2T;
+template <> struct Vec2T<float> { using type = float2; };
+template <> struct Vec2T<double> { using type = double2; };
 
 // M2M: the multipole of each cell (FP64), one block of FMM_PMAX + 1 threads
 // per cell, thread l forming order l.  Disks are visited in sorted order, so
@@ -75,6 +78,8 @@ __global__ void __launch_bounds__(FMM_PMAX + 1) m2m_kernel(const double2* __rest
   const double sx = cell_ctr[2 * cell], sy = cell_ctr[2 * cell + 1];
   const double rho = cell_rho[cell];
   const double irho = rho > 0 ? 1.0 / rho : 0.0;
+  __shared__ double spw[FMM_PMAX + 1];      // rho_C^-n
+  spw[l] = pow(irho, (double)l);
   C2<double> acc_a = {0, 0}, acc_g = {0, 0}, F = {0, 0};
   for (int q = b; q < e; ++q) {
     for (int j = l; j < MP_NCOEF; j += FMM_PMAX + 1) cf[j] = coef[(long long)q * MP_NCOEF + j];
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(FMM_PMAX + 1) m2m_kernel(const double2* __rest
       const C2<double> dc = cconj(d);
       if (n == 1) en = cadd(en, cscale(cmul(dc, F0), -0.5));
       else en = cadd(en, cscale(cmul(dc, ld(cf[2 * (n - 1)])), -(double)(n - 1)));
-      const double sc = pow(irho, (double)n);
+      const double sc = spw[n];
       as[n] = cscale(an, sc);
       es[n] = cscale(en, sc);
     }
@@ -118,77 +123,68 @@ __global__ void __launch_bounds__(FMM_PMAX + 1) m2m_kernel(const double2* __rest
   out[FMM_PMAX + 1 + l] = l == 0 ? make_double2(0.0, 0.0) : make_double2(acc_g.r, acc_g.i);
 }
 
-// M2L: the local expansion of each target cell from every cell outside its
-// near window, one block of FMM_PMAX + 1 threads per target cell, thread l
-// forming order l; source cells in row-major order, compensated sums.  T is
-// the precision of the translation (float for the mixed-precision far field,
-// double for FP64); cell geometry and the order choice stay in FP64.
-template <typename T, typename V2>
-__global__ void __launch_bounds__(FMM_PMAX + 1) m2l_kernel(const double2* __restrict__ mcoef,
-                                                             const int* __restrict__ cell_start,
-                                                             const double* __restrict__ cell_ctr,
-                                                             const double* __restrict__ cell_rho,
-                                                             const double* __restrict__ cell_tau, int nx, int ny,
-                                                             double tol, const T* __restrict__ binB,
-                                                             V2* __restrict__ lcoef, int* __restrict__ lorder) {
-  const int tc = blockIdx.x, l = threadIdx.x;
-  V2* out = lcoef + (long long)tc * FMM_NC;
-  if (cell_start[tc + 1] == cell_start[tc]) {
-    out[l] = V2{(T)0, (T)0};
-    out[FMM_PMAX + 1 + l] = V2{(T)0, (T)0};
-    if (l == 0) lorder[tc] = 0;
-    return;
-  }
-  __shared__ C2<T> ab[FMM_PMAX + 1], cb[FMM_PMAX + 1];
-  const int tx = tc % nx, ty = tc / nx;
-  const double ttx = cell_ctr[2 * tc], tty = cell_ctr[2 * tc + 1];
-  const double tau = cell_tau[tc];
-  const double ltol = log(tol);
+// M2L: the local expansion of each target cell from its interaction list
+// (every non-empty cell outside its near window, with the translation's
+// geometric factors and order precomputed on the host in FP64), one block of
+// M2L_G groups of FMM_PMAX + 1 threads per target cell: group g takes the
+// list's entries g, g + M2L_G, ..., thread l of a group forms order l, and the
+// groups' compensated sums are added in group order.  T is the precision of
+// the translation (float for the mixed-precision far field, double for FP64).
+constexpr int M2L_G = 4;
+
+template <typename T, typename R>
+__global__ void __launch_bounds__(M2L_G * (FMM_PMAX + 1)) m2l_kernel(const double2* __restrict__ mcoef,
+                                                                      const int* __restrict__ ilist_off,
+                                                                      const R* __restrict__ ilist,
+                                                                      const T* __restrict__ binB,
+                                                                      typename Vec2T<T>::type* __restrict__ lcoef,
+                                                                      const int* __restrict__ lorder_in,
+                                                                      int* __restrict__ lorder) {
+  using V2 = typename Vec2T<T>::type;
+  const int tc = blockIdx.x;
+  const int l = threadIdx.x % (FMM_PMAX + 1), g = threadIdx.x / (FMM_PMAX + 1);
+  __shared__ C2<T> ab[M2L_G][FMM_PMAX + 1], cb[M2L_G][FMM_PMAX + 1];
+  __shared__ C2<T> part[M2L_G][FMM_PMAX + 1][2];
+  const int b = ilist_off[tc], e = ilist_off[tc + 1];
   const T* bl = binB + l * (FMM_PMAX + 1);
   C2<T> la = {0, 0}, lac = {0, 0}, ka = {0, 0}, kac = {0, 0};   // sums and compensations
-  int pseen = 0;
-  const int ncell = nx * ny;
-  for (int sc = 0; sc < ncell; ++sc) {
-    const int sx = sc % nx, sy = sc / nx;
-    if (abs(sx - tx) <= FMM_NEAR && abs(sy - ty) <= FMM_NEAR) continue;
-    if (cell_start[sc + 1] == cell_start[sc]) continue;
-    const double Dx = ttx - cell_ctr[2 * sc], Dy = tty - cell_ctr[2 * sc + 1];
-    const double R2 = Dx * Dx + Dy * Dy, R = sqrt(R2);
-    const double rho = cell_rho[sc];
-    const double x = (rho + tau) / R;
-    int pc = (int)ceil(ltol / log(x));
-    pc = max(2, min(FMM_PMAX, pc));
-    pseen = max(pseen, pc);
-    const double2* m = mcoef + (long long)sc * FMM_NC;
-    const C2<double> F = ld(m[0]);
-    if (l >= 1 && l <= pc) {
+  const int rounds = (e - b + M2L_G - 1) / M2L_G;
+  for (int r = 0; r < rounds; ++r) {
+    const int q = b + r * M2L_G + g;
+    const bool have = q < e;
+    R it;
+    int pc = 0;
+    if (have) { it = ilist[q]; pc = it.pc; }
+    const double2* m = mcoef + (long long)(have ? it.src : 0) * FMM_NC;
+    if (have && l >= 1 && l <= pc) {
       // psi_C - conj(D) phi_C' in the scaled Laurent series about s:
       // c_1 = gamma_1 + conj(D) F / (2 rho), c_n = gamma_n + conj(D) (n-1) alpha_{n-1} / rho
-      const C2<double> Dc = {Dx / rho, -Dy / rho};
-      C2<double> cn = ld(m[FMM_PMAX + 1 + l]);
-      cn = cadd(cn, l == 1 ? cscale(cmul(Dc, F), 0.5) : cscale(cmul(Dc, ld(m[l - 1])), (double)(l - 1)));
-      // u = rho / D
-      const C2<T> u = {(T)(rho * Dx / R2), (T)(-rho * Dy / R2)};
-      const C2<T> ul = cpow(u, l);
-      const C2<double> al = ld(m[l]);
-      ab[l] = cmul(C2<T>{(T)al.r, (T)al.i}, ul);
-      cb[l] = cmul(C2<T>{(T)cn.r, (T)cn.i}, ul);
+      const C2<T> Dc = {(T)it.dcr, (T)it.dci};
+      const double2 gl = m[FMM_PMAX + 1 + l];
+      const double2 prev = m[l - 1];
+      C2<T> cn = {(T)gl.x, (T)gl.y};
+      const C2<T> pv = {(T)prev.x, (T)prev.y};
+      cn = cadd(cn, l == 1 ? cscale(cmul(Dc, pv), (T)0.5) : cscale(cmul(Dc, pv), (T)(l - 1)));
+      const C2<T> ul = cpow(C2<T>{(T)it.ur, (T)it.ui}, l);
+      const double2 al = m[l];
+      ab[g][l] = cmul(C2<T>{(T)al.x, (T)al.y}, ul);
+      cb[g][l] = cmul(cn, ul);
     }
     __syncthreads();
-    if (l <= pc) {
+    if (have && l <= pc) {
       C2<T> sa = {0, 0}, sg = {0, 0};
       for (int n = 1; n <= pc; ++n) {
         const T bc = bl[n];
-        sa.r = fma(bc, ab[n].r, sa.r); sa.i = fma(bc, ab[n].i, sa.i);
-        sg.r = fma(bc, cb[n].r, sg.r); sg.i = fma(bc, cb[n].i, sg.i);
+        sa.r = fma(bc, ab[g][n].r, sa.r); sa.i = fma(bc, ab[g][n].i, sa.i);
+        sg.r = fma(bc, cb[g][n].r, sg.r); sg.i = fma(bc, cb[g][n].i, sg.i);
       }
-      const C2<T> mv = {(T)(-tau * Dx / R2), (T)(tau * Dy / R2)};     // -v = -tau / D
-      const C2<T> mvl = cpow(mv, l);
+      const C2<T> mvl = cpow(C2<T>{(T)it.vr, (T)it.vi}, l);   // (-tau / D)^l
       C2<T> ta = cmul(mvl, sa), tg = cmul(mvl, sg);
-      const C2<T> Fh = {(T)(0.5 * F.r), (T)(0.5 * F.i)};
+      const double2 F = m[0];
+      const C2<T> Fh = {(T)(0.5 * F.x), (T)(0.5 * F.y)};
       if (l == 0) {
         // -F/2 log D + F/2 (the strengths' constant), -conj(F)/2 log D
-        const C2<T> lg = {(T)(0.5 * log(R2)), (T)atan2(Dy, Dx)};
+        const C2<T> lg = {(T)it.lr, (T)it.li};
         ta = cadd(ta, cadd(cmul(C2<T>{-Fh.r, -Fh.i}, lg), Fh));
         tg = cadd(tg, cmul(C2<T>{-Fh.r, Fh.i}, lg));
       } else {
@@ -196,7 +192,6 @@ __global__ void __launch_bounds__(FMM_PMAX + 1) m2l_kernel(const double2* __rest
         ta = cadd(ta, cscale(cmul(Fh, mvl), il));
         tg = cadd(tg, cscale(cmul(cconj(Fh), mvl), il));
       }
-      // compensated accumulation over source cells
       T y = ta.r - lac.r; T t = la.r + y; lac.r = (t - la.r) - y; la.r = t;
       y = ta.i - lac.i; t = la.i + y; lac.i = (t - la.i) - y; la.i = t;
       y = tg.r - kac.r; t = ka.r + y; kac.r = (t - ka.r) - y; ka.r = t;
@@ -204,9 +199,17 @@ __global__ void __launch_bounds__(FMM_PMAX + 1) m2l_kernel(const double2* __rest
     }
     __syncthreads();
   }
-  out[l] = V2{la.r - lac.r, la.i - lac.i};
-  out[FMM_PMAX + 1 + l] = V2{ka.r - kac.r, ka.i - kac.i};
-  if (l == 0) lorder[tc] = pseen;
+  part[g][l][0] = C2<T>{la.r - lac.r, la.i - lac.i};
+  part[g][l][1] = C2<T>{ka.r - kac.r, ka.i - kac.i};
+  __syncthreads();
+  if (g == 0) {
+    C2<T> sl = part[0][l][0], sk = part[0][l][1];
+    for (int q = 1; q < M2L_G; ++q) { sl = cadd(sl, part[q][l][0]); sk = cadd(sk, part[q][l][1]); }
+    V2* out = lcoef + (long long)tc * FMM_NC;
+    out[l] = V2{sl.r, sl.i};
+    out[FMM_PMAX + 1 + l] = V2{sk.r, sk.i};
+    if (l == 0) lorder[tc] = lorder_in[tc];
+  }
 }
 
 }  // namespace
@@ -217,7 +220,10 @@ void fmm_free(Ctx& c) {
   dfree(g.tblk32); dfree(g.tblk64);
   for (int z = 0; z < 2; ++z) { dfree(g.xoff[z]); dfree(g.xpos[z]); }
   dfree(g.dsk_s); dfree(g.ctr_s); dfree(g.binA); dfree(g.binB64); dfree(g.binB32);
-  dfree(g.mcoef); dfree(g.lcoef64); dfree(g.lcoef32); dfree(g.lorder);
+  dfree(g.mcoef); dfree(g.lcoef64); dfree(g.lcoef32); dfree(g.lorder); dfree(g.lorder32); dfree(g.lorder64);
+  dfree(g.ilist_off);
+  if (g.ilist32) dfree_bytes(g.ilist32);
+  if (g.ilist64) dfree_bytes(g.ilist64);
   g = FmmGrid{};
 }
 
@@ -285,6 +291,41 @@ int fmm_setup(Ctx& c) {
     }
   }
   if (worst > FMM_MAX_RATIO) return LMFS_OK;
+  // interaction lists: per target cell every non-empty cell outside its near
+  // window, with u = rho_C / D, -tau_T / D, log D, conj(D) / rho_C (FP64 on the
+  // host) and the order that reaches the tolerance at x = (rho_C + tau_T) / |D|
+  std::vector<int> ioff(ncell + 1, 0), lord32(ncell, 0), lord64(ncell, 0);
+  std::vector<M2LItem<float>> il32;
+  std::vector<M2LItem<double>> il64;
+  for (int t = 0; t < ncell; ++t) {
+    if (start[t + 1] > start[t]) {
+      for (int sc = 0; sc < ncell; ++sc) {
+        if (start[sc + 1] == start[sc]) continue;
+        if (std::abs(t % nx - sc % nx) <= FMM_NEAR && std::abs(t / nx - sc / nx) <= FMM_NEAR) continue;
+        const double Dx = ctr[2 * t] - ctr[2 * sc], Dy = ctr[2 * t + 1] - ctr[2 * sc + 1];
+        const double R2 = Dx * Dx + Dy * Dy, R = std::sqrt(R2);
+        const double x = (rho[sc] + tau[t]) / R;
+        const int p32 = std::max(2, std::min(FMM_PMAX, (int)std::ceil(std::log(1e-10) / std::log(x))));
+        const int p64 = std::max(2, std::min(FMM_PMAX, (int)std::ceil(std::log(1e-17) / std::log(x))));
+        lord32[t] = std::max(lord32[t], p32);
+        lord64[t] = std::max(lord64[t], p64);
+        M2LItem<double> d;
+        d.src = sc;
+        d.ur = rho[sc] * Dx / R2; d.ui = -rho[sc] * Dy / R2;
+        d.vr = -tau[t] * Dx / R2; d.vi = tau[t] * Dy / R2;
+        d.lr = 0.5 * std::log(R2); d.li = std::atan2(Dy, Dx);
+        d.dcr = Dx / rho[sc]; d.dci = -Dy / rho[sc];
+        d.pc = p64;
+        il64.push_back(d);
+        M2LItem<float> f;
+        f.src = sc; f.pc = p32;
+        f.ur = (float)d.ur; f.ui = (float)d.ui; f.vr = (float)d.vr; f.vi = (float)d.vi;
+        f.lr = (float)d.lr; f.li = (float)d.li; f.dcr = (float)d.dcr; f.dci = (float)d.dci;
+        il32.push_back(f);
+      }
+    }
+    ioff[t + 1] = (int)il64.size();
+  }
   // far-field blocks: each cell's target nodes in runs of FMM_NODES32 / FMM_NODES64
   auto blocks = [&](int per) {
     std::vector<int4> v;
@@ -357,6 +398,11 @@ int fmm_setup(Ctx& c) {
   LMFS_TRY(dalloc(&g.lcoef64, (size_t)ncell * FMM_NC));
   LMFS_TRY(dalloc(&g.lcoef32, (size_t)ncell * FMM_NC));
   LMFS_TRY(dalloc(&g.lorder, (size_t)ncell));
+  LMFS_TRY(dalloc(&g.lorder32, (size_t)ncell));
+  LMFS_TRY(dalloc(&g.lorder64, (size_t)ncell));
+  LMFS_TRY(dalloc(&g.ilist_off, (size_t)ncell + 1));
+  LMFS_TRY(dalloc_bytes((void**)&g.ilist32, std::max<size_t>(1, il32.size()) * sizeof(M2LItem<float>)));
+  LMFS_TRY(dalloc_bytes((void**)&g.ilist64, std::max<size_t>(1, il64.size()) * sizeof(M2LItem<double>)));
   LMFS_CUDA(cudaMemcpyAsync(g.cell_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   LMFS_CUDA(cudaMemcpyAsync(g.sorted, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   LMFS_CUDA(cudaMemcpyAsync(g.pos, pos.data(), pos.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -375,6 +421,13 @@ int fmm_setup(Ctx& c) {
   LMFS_CUDA(cudaMemcpyAsync(g.binA, bA.data(), bA.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   LMFS_CUDA(cudaMemcpyAsync(g.binB64, bB.data(), bB.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   LMFS_CUDA(cudaMemcpyAsync(g.binB32, bB32.data(), bB32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  LMFS_CUDA(cudaMemcpyAsync(g.lorder32, lord32.data(), lord32.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  LMFS_CUDA(cudaMemcpyAsync(g.lorder64, lord64.data(), lord64.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  LMFS_CUDA(cudaMemcpyAsync(g.ilist_off, ioff.data(), ioff.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!il32.empty()) {
+    LMFS_CUDA(cudaMemcpyAsync(g.ilist32, il32.data(), il32.size() * sizeof(M2LItem<float>), cudaMemcpyHostToDevice, st));
+    LMFS_CUDA(cudaMemcpyAsync(g.ilist64, il64.data(), il64.size() * sizeof(M2LItem<double>), cudaMemcpyHostToDevice, st));
+  }
   LMFS_CUDA(cudaStreamSynchronize(st));   // the host vectors go out of scope
   g.h = h; g.x0 = x0; g.y0 = y0; g.nx = nx; g.ny = ny; g.ncell = ncell;
   g.n_tblk32 = (int)b32.size(); g.n_tblk64 = (int)b64.size();
@@ -392,14 +445,14 @@ int fmm_translate(Ctx& c, int precision) {
   m2m_kernel<<<g.ncell, FMM_PMAX + 1, 0, c.stream>>>(c.coef64, g.cell_start, g.ctr_s, g.cell_ctr, g.cell_rho, g.binA,
                                                       g.mcoef);
   LMFS_TRY(check_launch("m2m"));
+  constexpr int threads = M2L_G * (FMM_PMAX + 1);
   if (precision == LMFS_MIXED)
-    m2l_kernel<float, float2><<<g.ncell, FMM_PMAX + 1, 0, c.stream>>>(g.mcoef, g.cell_start, g.cell_ctr, g.cell_rho,
-                                                                       g.cell_tau, g.nx, g.ny, 1e-10, g.binB32,
-                                                                       g.lcoef32, g.lorder);
+    m2l_kernel<float, M2LItem<float>><<<g.ncell, threads, 0, c.stream>>>(g.mcoef, g.ilist_off, (const M2LItem<float>*)g.ilist32, g.binB32,
+                                                                          g.lcoef32, g.lorder32, g.lorder);
   else
-    m2l_kernel<double, double2><<<g.ncell, FMM_PMAX + 1, 0, c.stream>>>(g.mcoef, g.cell_start, g.cell_ctr,
-                                                                         g.cell_rho, g.cell_tau, g.nx, g.ny, 1e-17,
-                                                                         g.binB64, g.lcoef64, g.lorder);
+    m2l_kernel<double, M2LItem<double>><<<g.ncell, threads, 0, c.stream>>>(g.mcoef, g.ilist_off, (const M2LItem<double>*)g.ilist64,
+                                                                            g.binB64, g.lcoef64, g.lorder64,
+                                                                            g.lorder);
   return check_launch("m2l");
 }
 

@@ -115,6 +115,15 @@ constexpr int FMM_NODES64 = 128;           // (FP64: 128 threads x 1)
 // field from the disks of the (2 FMM_NEAR + 1)^2 cells around its own comes
 // from their per-disk expansions, from every other cell through that cell's
 // multipole translated to a local expansion about the target's cell.
+// One entry of a target cell's M2L interaction list: the source cell, the
+// translation's order, and its geometric factors (u = rho_C / D, v = -tau_T /
+// D, log D, conj(D) / rho_C; D = s_T - s_C), in the translation's precision.
+template <typename T>
+struct M2LItem {
+  int src, pc;
+  T ur, ui, vr, vi, lr, li, dcr, dci;
+};
+
 struct FmmGrid {
   bool on = false;
   double h = 0, x0 = 0, y0 = 0;
@@ -141,6 +150,11 @@ struct FmmGrid {
   double2* lcoef64 = nullptr;        // [ncell][FMM_NC] local expansions
   float2* lcoef32 = nullptr;
   int* lorder = nullptr;             // [ncell] local order in use
+  int* lorder32 = nullptr;           // [ncell] the local order of each precision
+  int* lorder64 = nullptr;
+  int* ilist_off = nullptr;          // [ncell + 1] interaction lists
+  void* ilist32 = nullptr;           // M2LItem<float>[]
+  void* ilist64 = nullptr;           // M2LItem<double>[]
 };
 
 struct Ctx {

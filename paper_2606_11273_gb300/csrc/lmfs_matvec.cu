@@ -675,35 +675,42 @@ struct MpArgs {
 
 // One disk's expansion (coefficients cf, staged in shared memory) at the
 // thread's TPT targets, Z = target - disk centre, added with compensation.
+// The FP64 form takes 1/r^2 from the Newton reciprocal and the logarithm from
+// the table form (lmfs_fp64.cuh, ltab), and chooses the order in FP32.
 template <typename T, int TPT>
 __device__ __forceinline__ void m2p_eval(const typename Vec2<T>::type* __restrict__ cf, const Cx<T>* Z, int with_log,
-                                         T* sr, T* si, T* cr, T* ci) {
+                                         const double* ltab, T* sr, T* si, T* cr, T* ci) {
   using V2 = typename Vec2<T>::type;
   Cx<T> t[TPT], tb[TPT];
+  float r2f[TPT];
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
     const T r2 = Z[q].r * Z[q].r + Z[q].i * Z[q].i;
-    const T ir2 = (T)1 / r2;
+    T ir2;
+    if constexpr (sizeof(T) == 8) ir2 = rcp_pos(r2);
+    else ir2 = (T)1 / r2;
+    r2f[q] = (float)r2;
     t[q].r = Z[q].r * ir2; t[q].i = -Z[q].i * ir2;     // 1/Z
     tb[q].r = t[q].r; tb[q].i = -t[q].i;              // 1/conj(Z)
   }
   // order needed here: B x^(p+1) / (1 - x) <= tol * |leading term|, x = rho / R
+  // (an estimate: evaluated in FP32 for both forms)
   int pe = 2;
   {
     const V2 bd = cf[1];
-    const T B = (T)bd.x, rho = (T)bd.y;
+    const float B = (float)bd.x, rho = (float)bd.y;
+    const V2 a1 = cf[2];
+    const float a1n = sqrtf((float)a1.x * (float)a1.x + (float)a1.y * (float)a1.y);
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
-      const T R = sqrt(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
-      const T x = rho / R;
-      const V2 a1 = cf[2];
-      const T lead = sqrt((T)a1.x * (T)a1.x + (T)a1.y * (T)a1.y) / R + B * x * (T)1e-6 +
-                     (sizeof(T) == 4 ? (T)0 : (T)1e-300);   // 1e-300 is 0 in FP32
-      const T tol = (sizeof(T) == 4) ? (T)1e-9 : (T)1e-16;
+      const float iR = rsqrtf(r2f[q]);
+      const float x = rho * iR;
+      const float lead = a1n * iR + B * x * 1e-6f + 1e-37f;
+      const float tol = (sizeof(T) == 4) ? 1e-9f : 1e-16f;
       int need = MP_P;
-      if (B > (T)0 && x < (T)1) {
-        const T lim = tol * lead * ((T)1 - x) / B;
-        need = (lim >= (T)1) ? 1 : (int)ceil(log(lim) / log(x)) - 1;
+      if (B > 0.f && x < 1.f) {
+        const float lim = fmaxf(tol * lead * (1.f - x) / B, 1e-37f);
+        need = (lim >= 1.f) ? 1 : (int)fminf((float)MP_P, ceilf(__logf(lim) / __logf(x))) - 1 + (sizeof(T) == 8);
       }
       pe = max(pe, min(need, MP_P));
     }
@@ -739,7 +746,9 @@ __device__ __forceinline__ void m2p_eval(const typename Vec2<T>::type* __restric
     T ur = s1f.r + s2f.r + (T)0.5 * (Z[q].r * s3f.r - Z[q].i * s3f.i);
     T ui = s1f.i + s2f.i + (T)0.5 * (Z[q].r * s3f.i + Z[q].i * s3f.r);
     if (with_log) {
-      const T lr = (T)0.5 * log(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
+      T lr;
+      if constexpr (sizeof(T) == 8) lr = 0.5 * log_pos(Z[q].r * Z[q].r + Z[q].i * Z[q].i, ltab);
+      else lr = (T)0.5 * log(Z[q].r * Z[q].r + Z[q].i * Z[q].i);
       ur += (T)f0.x * ((T)0.5 - lr);
       ui += (T)f0.y * ((T)0.5 - lr);
     }
@@ -804,6 +813,8 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
   float4* dbuf1 = (float4*)(msm + 2 * cbytes + M_TILE * 32);
   uint64_t* bars = (uint64_t*)(msm + 2 * cbytes + 2 * M_TILE * 32);
   __shared__ int s_fail;
+  __shared__ double ltab[sizeof(T) == 8 ? 3 * LOG_TAB : 1];
+  if constexpr (sizeof(T) == 8) log_table_init(ltab);     // read after the first barrier
 
   // targets and source ranges
   int ti = 0, t0 = 0;
@@ -924,7 +935,7 @@ __device__ __forceinline__ void m2p_block(const MpArgs& a, int bx, int by) {
         if (k == next_ex) { ++ep; next_ex = (ep < ee) ? a.excl[ep] : 0x7fffffff; continue; }
         Cx<T> Z[TPT];
         m2p_offsets<T, TPT>(a, DB, dd, k, xr, xi, chx, chy, clx, cly, Z);
-        m2p_eval<T, TPT>(CB + dd * MP_NCOEF, Z, a.with_log, sr, si, cr, ci);
+        m2p_eval<T, TPT>(CB + dd * MP_NCOEF, Z, a.with_log, ltab, sr, si, cr, ci);
       }
     }
     __syncthreads();
