@@ -87,7 +87,8 @@ typedef struct lmfs_params {
   double eps_trunc_fine; /* truncation of the fine pair solve (1e-11)            */
   double mu;             /* viscosity (1)                                        */
   double tol;            /* GMRES relative residual tolerance (1e-7)             */
-  int    maxit;          /* GMRES iteration limit (300)                          */
+  int    maxit;          /* GMRES iteration limit (300): of a plain solve, and of a
+                            refined one's mixed rounds together                    */
   double rho;            /* peanut rolling radius; 0: smallest disk radius       */
   int    precision;      /* LMFS_FP64, LMFS_MIXED or LMFS_MIXED_DIRECT (lmfs_solve) */
   void*  stream;         /* cudaStream_t for all work of the handle (NULL: own one) */
@@ -96,9 +97,17 @@ typedef struct lmfs_params {
                             refinement rounds against the FP64 operator (4); 0: none.
                             Each round forms r = b - A_64 x with the FP64 matvec (b the
                             FP64 right-hand side) and adds the mixed-precision GMRES
-                            solution of A d = r; the solve stops once |r| / |b| <= tol.
-                            Not in the paper: it closes the gap between the mixed
-                            operator and the FP64 one (about 3e-8 relative).          */
+                            solution of A d = r (each to a tolerance relative to |r|);
+                            it stops at |r| / |b| <= tol, when a round no longer halves
+                            |r| (the FP64 operator's rounding floor), or when the
+                            rounds after the first have used as many iterations as the
+                            first.  If |r| / |b| then exceeds max(1e-4, 1e3 tol), one
+                            FP64 GMRES round on r follows (up to maxit iterations of
+                            its own).  The result is the iterate with the smallest
+                            FP64 residual; lmfs_solve_info.relres reports it.  Not in
+                            the paper: it closes the gap between the mixed operator
+                            and the FP64 one (about 3e-8 relative on smooth vectors,
+                            far more on ill-conditioned resistance clusters).        */
   /* Optional device allocator for every buffer of the handle (NULL: the
    * library's pool).  dev_alloc returns `bytes` of device memory usable on
    * `stream` (the handle's stream) or NULL; dev_free returns a block from

@@ -269,7 +269,27 @@ static int refined_gmres(Ctx& c, int problem, lmfs_solve_info* loc) {
     relres_g = g.relres;
     LMFS_TRY(refine_update(c, false));
   }
-  if (!ctl.best) LMFS_TRY(refine_restore(c));
+  double itol = 0.0;
+  int rmax = 0;
+  if (ctl.fp64_next(c.prm, &itol, &rmax)) {
+    // the mixed operator did not reach the FP64 solution: FP64 GMRES from x = 0
+    LMFS_TRY(refine_from_zero(c));
+    c.gm_tol = itol;
+    rc = gmres_solve(c, problem, LMFS_FP64, c.rres, c.xsol, &g, rmax);
+    if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
+    ctl.fp64_round = true;
+    ctl.status = rc;
+    ctl.iters += g.iters;
+    relres_g = g.relres;
+    LMFS_TRY(refine_update(c, false));
+    LMFS_TRY(refine_residual(c, problem));
+    LMFS_CUDA(cudaStreamSynchronize(c.stream));
+    rho = c.host_pinned[4];
+    ctl.rounds += 1;
+    ctl.rho_best = rho;
+  } else if (!ctl.best) {
+    LMFS_TRY(refine_restore(c));
+  }
   LMFS_CUDA(cudaMemcpyAsync(c.xsol, c.xacc, 2 * (size_t)c.d.P * c.d.Mc * sizeof(double), cudaMemcpyDeviceToDevice,
                             c.stream));
   c.gm_tol = c.prm.tol;
@@ -356,6 +376,15 @@ int solve_refine_restart(lmfs_handle h, double inner_tol) {
   LMFS_CUDA(cudaSetDevice(c.device));
   c.gm_tol = inner_tol;
   return gmres_restart(c, c.rres);
+}
+
+int solve_refine_fp64_prepare(lmfs_handle h, int problem) {
+  Ctx& c = h->c;
+  AllocScope as(c.stream, c.prm);
+  LMFS_CUDA(cudaSetDevice(c.device));
+  LMFS_TRY(refine_from_zero(c));
+  // the FP64 step graphs, captured outside any running capture
+  return gmres_begin_graphs(c, problem, LMFS_FP64);
 }
 
 int solve_refine_keep(lmfs_handle h, bool restore) {

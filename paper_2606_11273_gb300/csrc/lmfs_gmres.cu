@@ -316,6 +316,11 @@ int gmres_finish(Ctx& c, int iters, double* x) {
 int gmres_begin(Ctx& c, int problem, int precision, const double* b, double* beta) {
   LMFS_TRY(gmres_alloc(c, std::max(1, c.prm.maxit)));
   LMFS_TRY(gmres_init(c, b, beta));
+  return gmres_begin_graphs(c, problem, precision);
+}
+
+int gmres_begin_graphs(Ctx& c, int problem, int precision) {
+  LMFS_TRY(gmres_alloc(c, std::max(1, c.prm.maxit)));
   if (!c.step_pre[problem][precision]) {
     c.step_nodes[problem][precision] = 0;
     LMFS_TRY(capture(c, [&] { return arnoldi_pre(c, problem, precision); }, &c.step_pre[problem][precision],
@@ -353,6 +358,13 @@ int refine_alloc(Ctx& c) {
 int refine_keep(Ctx& c) {
   LMFS_CUDA(cudaMemcpyAsync(c.xbest, c.xacc, 2 * (size_t)c.d.P * c.d.Mc * sizeof(double), cudaMemcpyDeviceToDevice,
                             c.stream));
+  return LMFS_OK;
+}
+
+int refine_from_zero(Ctx& c) {
+  const size_t n = 2 * (size_t)c.d.P * c.d.Mc;
+  LMFS_CUDA(cudaMemsetAsync(c.xacc, 0, n * sizeof(double), c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(c.rres, c.b64, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
   return LMFS_OK;
 }
 

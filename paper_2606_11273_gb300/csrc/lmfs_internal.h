@@ -360,13 +360,15 @@ int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x,
 //   refine_residual: rres = b64 - A_64 xacc (FP64 matvec) and |rres| / |b64|
 //     into scal[4], copied to host_pinned[4];
 //   gmres_restart: a new GMRES round on rres (basis vector 0, g, j = 0).
-//   refine_keep / refine_restore: xbest = xacc / xacc = xbest.
+//   refine_keep / refine_restore: xbest = xacc / xacc = xbest;
+//   refine_from_zero: xacc = 0, rres = b64 (the FP64 round starts over).
 int refine_alloc(Ctx& c);
 int refine_norm_b(Ctx& c);
 int refine_update(Ctx& c, bool first);
 int refine_residual(Ctx& c, int problem);
 int refine_keep(Ctx& c);
 int refine_restore(Ctx& c);
+int refine_from_zero(Ctx& c);
 int gmres_restart(Ctx& c, const double* b);
 
 // The refinement's control, shared by lmfs_solve and the server's engine.
@@ -380,20 +382,43 @@ int gmres_restart(Ctx& c, const double* b);
 // large), or when the rounds after the first have used as many iterations as
 // the first did (at least 20), or prm.maxit is reached.  The iterate with the
 // smallest rho is the result.  The solve's status is the first round's.
+//
+// Where the mixed operator is too far from the FP64 one for the problem's
+// conditioning (ill-conditioned resistance clusters: the mixed GMRES converges
+// in its own operator while the FP64 residual of its solution stays large),
+// the refinement ends with an FP64 GMRES solve of A x = b from x = 0 (the
+// residual of a poor mixed iterate has rough components that the FP64
+// operator's rounding swamps, so a correction from it does not converge), with
+// up to prm.maxit iterations of its own: when rho_best > max(1e-4, 1e3 tol)
+// after the mixed rounds (which stop at once if the first residual is above
+// 1e-2), unless the first round ran out of iterations.  The solve's status and
+// result are then that solve's.
 struct RefineCtl {
   int iters0 = 0;          // iterations of the first round
   int iters = 0;           // iterations of all rounds
   int rounds = 0;          // residuals evaluated
-  int status = LMFS_OK;    // the first round's GMRES status
+  int status = LMFS_OK;    // the first round's GMRES status (or the FP64 round's)
   double rho_prev = 0.0, rho_best = 0.0;
   bool best = false;       // the last residual is the smallest so far
+  bool fp64_round = false; // the FP64 round has run
+  static double fp64_threshold(const lmfs_params& p) { return std::max(1e-4, 1e3 * p.tol); }
+  // after the mixed rounds (next returned false): whether the FP64 round runs,
+  // with its tolerance relative to |r| of the best iterate and its iterations
+  bool fp64_next(const lmfs_params& p, double* inner_tol, int* round_maxit) const {
+    if (fp64_round || status != LMFS_OK || rho_best <= fp64_threshold(p)) return false;
+    *inner_tol = p.tol;
+    *round_maxit = std::max(1, p.maxit);
+    return true;
+  }
   bool next(const lmfs_params& p, double rho, double* inner_tol, int* round_maxit) {
     rounds += 1;
     best = rounds == 1 || rho < rho_best;
     if (best) rho_best = rho;
     const int left = std::min(std::max(0, p.maxit - iters), std::max(20, iters0) - (iters - iters0));
+    // a first residual above 1e-2: the mixed operator is far from the FP64 one
+    // for this problem, and the FP64 round follows at once
     const bool more = status == LMFS_OK && rho > p.tol && rounds <= p.refine && !(rounds > 1 && rho > 0.5 * rho_prev) &&
-                      left > 0;
+                      !(rounds == 1 && rho > 1e-2) && left > 0;
     rho_prev = rho;
     if (more) {
       *inner_tol = std::min(0.1, std::max(1e-4, 0.5 * p.tol / std::max(rho, 1e-300)));
@@ -414,6 +439,7 @@ void gmres_drop_graphs(Ctx& c);
 //   copy of (relres, -, breakdown) to host_pinned[1..3];
 //   gmres_finish: x from the first `iters` basis vectors.
 int gmres_begin(Ctx& c, int problem, int precision, const double* b, double* beta);
+int gmres_begin_graphs(Ctx& c, int problem, int precision);   // the two step graphs, if not captured yet
 int gmres_step_pre(Ctx& c, int problem, int precision);
 int gmres_step_post(Ctx& c, int problem, int precision);
 int gmres_finish(Ctx& c, int iters, double* x);
@@ -496,6 +522,9 @@ int solve_begin(lmfs_handle h, int problem, const double* in, double* beta);
 bool solve_refined(lmfs_handle h);
 int solve_refine_round(lmfs_handle h, int problem, int iters, bool first);
 int solve_refine_restart(lmfs_handle h, double inner_tol);
+// the FP64 round: x = 0, r = b (enqueued) and the FP64 step graphs; then
+// solve_refine_restart starts the round on r
+int solve_refine_fp64_prepare(lmfs_handle h, int problem);
 int solve_refine_keep(lmfs_handle h, bool restore);
 int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* out, lmfs_solve_info* info,
                  const lmfs_solve_info* refined_info = nullptr, int refined_rc = LMFS_OK);

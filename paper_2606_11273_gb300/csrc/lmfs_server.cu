@@ -43,6 +43,7 @@ struct Active {
   lmfs::RefineCtl ctl;
   int round_maxit = 0;           // iteration limit of the running round
   double relres_g = 0.0;         // the last round's GMRES estimate
+  bool fp64 = false;             // in the refinement's FP64 round: steps run alone, in FP64
 };
 
 struct Request {
@@ -237,8 +238,27 @@ void engine_loop(lmfs_server* s) {
           a.phase = 0;
           double itol = 0.0;
           int rmax = 0;
-          const bool more = a.ctl.next(c.prm, rho, &itol, &rmax);
-          int rc = a.ctl.best ? lmfs::solve_refine_keep(a.h, false) : LMFS_OK;
+          int rc = LMFS_OK;
+          bool more = false;
+          if (a.fp64) {
+            a.ctl.rounds += 1;            // the residual after the FP64 round: the result
+            a.ctl.rho_best = rho;
+            a.ctl.best = true;
+          } else {
+            more = a.ctl.next(c.prm, rho, &itol, &rmax);
+            if (a.ctl.best) rc = lmfs::solve_refine_keep(a.h, false);
+            if (rc == LMFS_OK && !more && a.ctl.fp64_next(c.prm, &itol, &rmax)) {
+              rc = lmfs::solve_refine_fp64_prepare(a.h, a.rq->problem);
+              if (rc == LMFS_OK) rc = lmfs::solve_refine_restart(a.h, itol);
+              if (rc != LMFS_OK) { cudaStreamSynchronize(a.st); fail(a, rc); continue; }
+              a.fp64 = true;
+              a.ctl.fp64_round = true;
+              a.iters = 0;
+              a.round_maxit = rmax;
+              ready.push_back(&a);
+              continue;
+            }
+          }
           if (rc == LMFS_OK && !more) {
             if (!a.ctl.best) rc = lmfs::solve_refine_keep(a.h, true);
             lmfs_solve_info ri{};
@@ -266,10 +286,9 @@ void engine_loop(lmfs_server* s) {
           if (lmfs::solve_refined(a.h)) {
             // end of a GMRES round: x += its solution, FP64 residual in flight
             a.relres_g = relres;
-            if (a.ctl.rounds == 0) {
-              a.ctl.iters0 = a.iters;
+            if (a.ctl.rounds == 0) a.ctl.iters0 = a.iters;
+            if (a.ctl.rounds == 0 || a.fp64)
               a.ctl.status = (relres <= c.gm_tol || c.host_pinned[3] != 0.0) ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
-            }
             a.ctl.iters += a.iters;
             int rc = lmfs::solve_refine_round(a.h, a.rq->problem, a.iters, a.ctl.rounds == 0);
             if (rc == LMFS_OK && cudaEventRecord(a.ev_step, a.st) != cudaSuccess) rc = LMFS_ERR_CUDA;
@@ -295,6 +314,16 @@ void engine_loop(lmfs_server* s) {
       std::vector<Active*> go;
       for (Active* a : ready) {
         lmfs::Ctx& c = a->h->c;
+        if (a->fp64) {
+          // the refinement's FP64 round: this request's step alone, on its stream
+          int r = lmfs::gmres_step_pre(c, a->rq->problem, LMFS_FP64);
+          if (r == LMFS_OK) r = lmfs::matvec_far(c, a->rq->problem, LMFS_FP64);
+          if (r == LMFS_OK) r = lmfs::gmres_step_post(c, a->rq->problem, LMFS_FP64);
+          if (r == LMFS_OK && cudaEventRecord(a->ev_step, a->st) != cudaSuccess) r = LMFS_ERR_CUDA;
+          if (r != LMFS_OK) { cudaGetLastError(); cudaStreamSynchronize(a->st); fail(*a, r); continue; }
+          a->in_flight = true;
+          continue;
+        }
         int r = (s->fail_ticket && a->rq->ticket == s->fail_ticket && a->ctl.iters + a->iters == 2)
                     ? (lmfs::set_last_error("injected step failure (LMFS_TEST_FAIL_TICKET)"), LMFS_ERR_CUDA)
                     : lmfs::gmres_step_pre(c, a->rq->problem, prec);
