@@ -39,11 +39,13 @@ def fine_cluster(centres, radii, p):
     return Ys, Xs
 
 
-def solve(centres, radii, p, problem, data, eps=1e-11):
+def solve(centres, radii, p, problem, data, eps=1e-11, points=None):
     """Resistance: S lam = g at all fine nodes, forces f = sum lam, torques
     sum lam . (y - c)^perp (eq. (force_eq)).  Mobility: [S (I - L) + B K^T]
     lam_bar = -S lam_0 with fine K, B, L per disk and [v; w] = -K^T lam_bar
-    (eqs. (tosolve), (u0_def), (rbm_ansatz))."""
+    (eqs. (tosolve), (u0_def), (rbm_ansatz)).  With points (n, 2), also the
+    flow field there: sum S(x, Y) lam (resistance) or sum S(x, Y) [(I - L)
+    lam_bar + lam_0] (mobility, eq. (mob)); returns (result, field)."""
     centres = np.asarray(centres, dtype=np.float64)
     radii = np.asarray(radii, dtype=np.float64)
     Ys, Xs = fine_cluster(centres, radii, p)
@@ -58,10 +60,17 @@ def solve(centres, radii, p, problem, data, eps=1e-11):
     if problem == "resistance":
         g = np.concatenate([Bs[i] @ data[i] for i in range(P)])
         lam = TSVD(S, eps).apply(g)
-        return (K.T @ lam).reshape(P, 3)
+        out = (K.T @ lam).reshape(P, 3)
+        if points is None:
+            return out
+        return out, (stokeslet(points, Y, p.mu) @ lam).reshape(-1, 2)
     L = blockdiag(*[rigid_projector(Ki) for Ki in Ks])
     B = blockdiag(*Bs)
     M = S @ (np.eye(L.shape[0]) - L) + B @ K.T
     lam0 = np.concatenate([Ks[i] @ np.linalg.solve(Ks[i].T @ Ks[i], data[i]) for i in range(P)])
     lb = TSVD(M, eps).apply(-S @ lam0)
-    return (-(K.T @ lb)).reshape(P, 3)
+    out = (-(K.T @ lb)).reshape(P, 3)
+    if points is None:
+        return out
+    strength = (np.eye(L.shape[0]) - L) @ lb + lam0
+    return out, (stokeslet(points, Y, p.mu) @ strength).reshape(-1, 2)

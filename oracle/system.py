@@ -33,10 +33,12 @@ class System:
     """Geometry, one-body factors and pair blocks of one problem.
 
     problem: "resistance" or "mobility".  blocks: optional list of
-    {"A", "E"} per contact to use instead of computing them.
+    {"A", "E"} per contact to use instead of computing them.  keep_fine:
+    also keep each pair's fine solution Z, fine sources Yf and fine rigid
+    matrix Kf (the flowEval data of Algorithm 2, for oracle.flow).
     """
 
-    def __init__(self, centres, radii, p, problem, blocks=None, dense_limit=2.5e9):
+    def __init__(self, centres, radii, p, problem, blocks=None, dense_limit=2.5e9, keep_fine=False):
         self.p = p
         self.problem = problem
         self.centres = np.asarray(centres, dtype=np.float64)
@@ -52,8 +54,11 @@ class System:
         self.rho = p.rho if p.rho > 0 else float(self.radii.min())
         if blocks is None:
             blocks = [pair_blocks(self.centres[i], self.radii[i], self.centres[k], self.radii[k],
-                                  self.ob[i], self.ob[k], p, problem, self.rho)
+                                  self.ob[i], self.ob[k], p, problem, self.rho, keep=keep_fine)
                       for i, k in self.pairs]
+            if keep_fine:
+                keys = ("A", "E", "Z", "Yf", "Kf", "rank_F", "rank_C")
+                blocks = [{q: b[q] for q in keys} for b in blocks]
         self.blocks = blocks
         nbytes = (2 * P * p.Mc) * (2 * P * p.Nc) * 8
         self.S_all = None

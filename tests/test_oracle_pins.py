@@ -591,3 +591,50 @@ def test_fine_brute_force_converges_under_refinement(case):
     assert err[0] > 1e3 * err[-1], err               # and the coarsest level is far from them
     if case == "pair_1e-3":
         assert err[levels.index(80)] < 1e-6, err
+
+
+# ------------------------------------------------- flow evaluation (flowEval)
+@pytest.mark.parametrize("problem", ["resistance", "mobility"])
+def test_boundary_flow_single_disk_is_rigid(problem):
+    """A single disk: the one-body MFS reproduces the exact rigid-body flow,
+    so the pointwise residual (eq. (residual_x)) at new boundary nodes is at
+    rounding level."""
+    from oracle import flow
+    s = System(np.zeros((1, 2)), np.array([1.0]), PACKING, problem, keep_fine=True)
+    data = np.array([[1.0, -0.5, 0.3]])
+    _, info = s.solve(data, tol=1e-13)
+    _, rel = flow.boundary_residual(s, info["mu"], data, 100)
+    assert rel < 1e-12
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("problem,gap", [("resistance", 1e-1), ("resistance", 1e-3), ("mobility", 1e-2),
+                                         ("mobility", 1e-3)])
+def test_boundary_flow_of_a_pair_matches_fine_brute_force(problem, gap):
+    """Two unit disks at the paper's parameters: the two-body flow at 100 new
+    nodes per boundary (one-body fields, the other pairs' compressed
+    corrections, the pair's own fine sources beta = -Z lam_bar) equals the
+    flow of the dense fine MFS of the same pair (no compression, no
+    preconditioner) to 5e-6, and its relative boundary residual (eq.
+    (residual)) is within 5 times the brute force's own (plus 1e-8): the
+    peanut compression and the one-body stand-in of Step 2b add their own error.  Leaving
+    out the fine sources, or taking them with the wrong sign, breaks both."""
+    from oracle import bruteforce, flow
+    pk = w.two_disks(gap)
+    s = System(pk.centres, pk.radii, PACKING, problem, keep_fine=True)
+    data = np.array([[1.0, 0.3, 0.2], [-0.5, -0.3, 0.4]])
+    _, info = s.solve(data, tol=1e-13)
+    u, g = flow.boundary_flow(s, info["mu"], data, 100)
+    X = np.concatenate([flow.eval_nodes(pk.centres[i], 1.0, 100) for i in range(2)])
+    _, ubf = bruteforce.solve(pk.centres, pk.radii, PACKING, problem, data, points=X)
+    err = np.linalg.norm(u.reshape(-1, 2) - ubf) / np.linalg.norm(ubf)
+    assert err < 5e-6
+    _, rel = flow.boundary_residual(s, info["mu"], data, 100)
+    gv = g.reshape(-1, 2)
+    rel_bf = np.hypot(*(ubf - gv).T).max() / np.hypot(*gv.T).max()
+    assert rel <= 5 * rel_bf + 1e-8
+    # planted: the pair's fine sources with the wrong sign
+    for b in s.blocks:
+        b["Z"] = -b["Z"]
+    u2, _ = flow.boundary_flow(s, info["mu"], data, 100)
+    assert np.linalg.norm(u2.reshape(-1, 2) - ubf) / np.linalg.norm(ubf) > 1e-2
