@@ -124,6 +124,11 @@ typedef struct lmfs_params {
                             window), else all pairs; LMFS_FAR_ALLPAIRS (1): every
                             disk's expansion at every target; LMFS_FAR_CELLS (2):
                             cells where the geometry allows, else all pairs.      */
+  int    keep_fine;      /* 1: the pair precompute also keeps every close pair's
+                            fine solution (the coarse-to-fine map of eq. (bfm)) and
+                            fine sources, about 2.4 MB per pair at the default
+                            parameters, for lmfs_flow_boundary (Algorithm 2 with
+                            flowEval); 0 (default): they are discarded.             */
 } lmfs_params;
 
 #define LMFS_FAR_AUTO     0
@@ -228,6 +233,23 @@ int lmfs_stats(lmfs_handle h, int problem, double* out);
  * substitution)}.  HOST array; zeros before the first precompute.  No
  * counterpart in the paper: a measurement hook. */
 int lmfs_qr_stats(lmfs_handle h, int problem, double* out);
+
+/* The flow of the last solve of `problem` at m_eval new nodes on every
+ * boundary, x = c_i + r_i (cos, sin)(2 pi (j + 1/2) / m_eval) (Algorithm 2
+ * with flowEval; Sec. 6.1): u(x) from every disk's coarse strengths
+ * (corrected, with the completion flow for mobility), minus the compressed
+ * corrections of the pairs that contain the node's disk, plus those pairs'
+ * fine sources beta = -F^+ blkQ lam_bar (eq. (bfm)); and the boundary data
+ * g(x) = v + omega (x - c)^perp (prescribed velocities for resistance,
+ * computed ones for mobility).  All in FP64 (per-disk and cell expansions
+ * beyond the FP64 near zone, direct sums inside it).  Needs keep_fine = 1
+ * before the precompute, and a solve of `problem` (LMFS_ERR_STATE
+ * otherwise).  Outputs, each optional (NULL): u_dev DEVICE [P][m_eval][2];
+ * res_disk HOST [P], the largest pointwise residual |u - g| (eq.
+ * (residual_x)) on each boundary; rel HOST scalar, the relative boundary
+ * residual of eq. (residual), max |u - g| / max |g|.  1 <= m_eval <= 1024.
+ * Synchronizes the handle's stream. */
+int lmfs_flow_boundary(lmfs_handle h, int problem, int m_eval, double* u_dev, double* res_disk, double* rel);
 
 /* Diagnostics of the last solve on the device: the GMRES solution mu
  * (DEVICE [P][Mc][2] copy destination) for parity checks. */

@@ -143,6 +143,16 @@ class Solver:
         d.update(zip(["factor_ms", "factor_flops", "rhs_ms", "rhs_flops"], q.tolist()))
         return d
 
+    def flow_boundary(self, problem, m_eval, u_dev=None):
+        """The last solve's flow at m_eval new nodes per boundary (needs
+        keep_fine=1): returns (per-disk max residual [P], relative boundary
+        residual); u_dev (CUDA float64, P*m_eval*2) receives the velocities."""
+        res = np.zeros(self.P)
+        rel = ctypes.c_double()
+        _lib.check(self.lib.lmfs_flow_boundary(self.h, problem, int(m_eval), _ptr(u_dev), _ptr(res),
+                                               ctypes.byref(rel)))
+        return res, rel.value
+
     def solution(self, mu_dev):
         _lib.check(self.lib.lmfs_get_solution(self.h, _ptr(mu_dev)))
 

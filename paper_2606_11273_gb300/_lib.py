@@ -41,7 +41,7 @@ class lmfs_params(ctypes.Structure):
         ("maxit", ctypes.c_int), ("rho", ctypes.c_double), ("precision", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("refine", ctypes.c_int),
         ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_user", ctypes.c_void_p),
-        ("far_form", ctypes.c_int),
+        ("far_form", ctypes.c_int), ("keep_fine", ctypes.c_int),
     ]
 
 
@@ -93,6 +93,7 @@ SIGNATURES = {
     "lmfs_strerror": (ctypes.c_char_p, [_i]),
     "lmfs_launch_count": (_i, [_P(ctypes.c_uint64)]),
     "lmfs_pool_stats": (_i, [_i, _i, _vp]),
+    "lmfs_flow_boundary": (_i, [_vp, _i, _i, _vp, _vp, _P(_d)]),
     "lmfs_estimate_bytes": (_i, [_vp, _vp, _i, _P(lmfs_params), _P(ctypes.c_size_t)]),
     "lmfs_server_create": (_i, [_P(lmfs_server_params), _P(_vp)]),
     "lmfs_submit": (_i, [_vp, _vp, _vp, _i, _i, _vp, _P(lmfs_params), _P(ctypes.c_uint64)]),

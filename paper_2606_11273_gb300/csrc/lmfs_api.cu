@@ -107,11 +107,13 @@ static void free_ctx(Ctx& c) {
   }
   dfree(c.tgt32); dfree(c.dsk32);
   for (auto& pb : c.prob) {
+    dfree(pb.Zf); dfree(pb.Yf); dfree(pb.nenh);
     dfree(pb.A); dfree(pb.E); dfree(pb.ob.W); dfree(pb.ob.R); dfree(pb.ob.perm); dfree(pb.ob.rank); dfree(pb.ob.V); dfree(pb.ob.Rinv); dfree(pb.ob.bad);
     pb.ready = false;
   }
   dfree(c.lb); dfree(c.lam); dfree(c.sig); dfree(c.tilde); dfree(c.ufar); dfree(c.lam0); dfree(c.src4);
   dfree(c.b64); dfree(c.xacc); dfree(c.rres); dfree(c.xbest);
+  for (int q = 0; q < 2; ++q) { dfree(c.in_last[q]); dfree(c.out_last[q]); c.solved[q] = false; }
   dfree(c.ufar_part); dfree(c.ring); dfree(c.nodes); dfree(c.bvec); dfree(c.xsol); dfree(c.io3); dfree(c.far_err); dfree(c.coef64); dfree(c.coef32);
   if (c.own_stream && c.stream) { cudaStreamDestroy(c.stream); c.stream = nullptr; c.own_stream = false; }
 }
@@ -321,6 +323,15 @@ static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev,
   }
   if (rc != LMFS_OK && rc != LMFS_ERR_NOT_CONVERGED) return rc;
   LMFS_TRY(post_device(c, problem, c.xsol, out_dev));
+  // the solve's data, for lmfs_flow_boundary
+  if (!c.in_last[problem]) LMFS_TRY(dalloc(&c.in_last[problem], 3 * (size_t)c.d.P));
+  if (!c.out_last[problem]) LMFS_TRY(dalloc(&c.out_last[problem], 3 * (size_t)c.d.P));
+  LMFS_CUDA(cudaMemcpyAsync(c.in_last[problem], in_dev, 3 * (size_t)c.d.P * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c.stream));
+  LMFS_CUDA(cudaMemcpyAsync(c.out_last[problem], out_dev, 3 * (size_t)c.d.P * sizeof(double),
+                            cudaMemcpyDeviceToDevice, c.stream));
+  c.solved[problem] = true;
+  c.solved[1 - problem] = false;     // the solution vector now belongs to this problem
   LMFS_TRY(sync_and_check_far_flags(c));
   c.have_solution = true;
   const auto t2 = std::chrono::steady_clock::now();
@@ -448,7 +459,7 @@ int lmfs_params_default(lmfs_params* p) {
   p->gamma = 0.3; p->af = 1.2; p->r_mob = 0.6; p->aell = 5.0; p->delta_c = 0.2;
   p->eps_trunc = 1e-14; p->eps_trunc_fine = 1e-11; p->mu = 1.0; p->tol = 1e-7; p->maxit = 300;
   p->rho = 0.0; p->precision = LMFS_MIXED; p->stream = nullptr; p->device = 0; p->refine = 4;
-  p->dev_alloc = nullptr; p->dev_free = nullptr; p->alloc_user = nullptr; p->far_form = LMFS_FAR_AUTO;
+  p->dev_alloc = nullptr; p->dev_free = nullptr; p->alloc_user = nullptr; p->far_form = LMFS_FAR_AUTO; p->keep_fine = 0;
   return LMFS_OK;
 }
 
@@ -654,6 +665,7 @@ int lmfs_invalidate(lmfs_handle h) {
   if (c.C != C0 || c.pairs_h != pairs0) { set_last_error("contact list changed"); return LMFS_ERR_STATE; }
   for (auto& pb : c.prob) pb.ready = false;
   c.have_solution = false;
+  c.solved[0] = c.solved[1] = false;
   return LMFS_OK;
 }
 

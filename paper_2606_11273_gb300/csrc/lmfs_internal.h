@@ -64,6 +64,16 @@ struct PairBlocks {
   double fac_ms = 0.0, fac_flops = 0.0;   // of which the pivoted factorizations (qrcp_kernel)
   double rhs_ms = 0.0, rhs_flops = 0.0;   // and the right-hand sides (apply_qt_kernel)
   int max_rank_F = 0, min_rank_F = 0;
+  // kept with lmfs_params.keep_fine (flowEval of Algorithm 2): per pair the
+  // fine solution Z (mobility: (I - L_f) Z), column-major [4Nc cols][fine_ld
+  // rows], rows 2 s + component of fine source s; the fine sources [fine_sy][2]
+  // (side 1's N_fp + kept ellipse sources, then side 2's); the kept ellipse
+  // sources per side
+  double* Zf = nullptr;
+  double* Yf = nullptr;
+  int* nenh = nullptr;
+  int fine_ld = 0, fine_sy = 0;
+  bool fine_kept = false;
 };
 
 // Near-interaction list: for each target disk i, the source disks handled in
@@ -166,6 +176,9 @@ struct Ctx {
   int device = 0;
   double Rc = 0, Rf = 0, rho = 0;
   double g_near = 0;                 // gap below which a disk is in the FP64 near zone (nz[0])
+  double* in_last[2] = {nullptr, nullptr};    // [P][3] input and output of the last solve per problem
+  double* out_last[2] = {nullptr, nullptr};
+  bool solved[2] = {false, false};
   FmmGrid fmm;
 
   std::vector<double> centres_h, radii_h;
@@ -310,7 +323,10 @@ int far_multi_launch(Ctx* const* cs, const int* problems, int n, int precision, 
 void multi_far_free(MultiFar& buf);
 int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision);
 int post_device(Ctx& c, int problem, const double* mu, double* out3);
+int completion_strengths(Ctx& c, const double* in3, double* lam0);   // lam_0 = K (K^T K)^{-1} [f; t]
 int far_field(Ctx& c, const double* strength, double* out, int precision, bool mobility_sums_zero);
+int far_field_at_nodes(Ctx& c, const double* strength, int m, const double2* enodes, const int4* tblk_eval,
+                       int n_tblk_eval, double* out);
 int far_field_prepare(Ctx& c);
 // Cell form (lmfs_fmm.cu): fmm_setup decides whether the geometry uses it and
 // builds its tables (once per handle, after the near lists); fmm_translate

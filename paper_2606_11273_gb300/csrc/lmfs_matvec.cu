@@ -1667,6 +1667,34 @@ int far_field(Ctx& c, const double* strength, double* out, int precision, bool s
   return far_post(c, out, precision);
 }
 
+// The FP64 far field of `strength` at m nodes per disk (x = c_i + r_i
+// enodes[j]) instead of the collocation nodes: every source disk outside the
+// FP64 near zone of the target disk, by per-disk expansions (and cell
+// expansions in the cell form, whose blocks tblk_eval the caller lays out for
+// m nodes per disk).  out [P][m][2], scaled by 1/(4 pi mu).
+int far_field_at_nodes(Ctx& c, const double* strength, int m, const double2* enodes, const int4* tblk_eval,
+                       int n_tblk_eval, double* out) {
+  LMFS_TRY(far_pre(c, strength, LMFS_FP64));
+  MpArgs a;
+  dim3 grid;
+  size_t shm = 0;
+  mp_setup(c, LMFS_FP64, out, false, a, grid, shm);
+  a.Mc = m;
+  a.Mc_nodes = m;
+  a.nodes = enodes;
+  a.out = out;
+  a.out_stride = (long long)c.d.P * m * 2;
+  if (a.cell) {
+    a.tblk = tblk_eval;
+    grid = dim3(n_tblk_eval, 1);
+  } else {
+    a.kchunk = c.d.P;
+    grid = dim3((c.d.P * m + M_THREADS - 1) / M_THREADS, 1);
+  }
+  m2p_kernel<double, 1><<<grid, M_THREADS, shm, c.stream>>>(a);
+  return check_launch("m2p at new nodes");
+}
+
 int far_multi_launch(Ctx* const* cs, const int* problems, int n, int precision, cudaStream_t st, MultiFar& buf) {
   if (n <= 0) return LMFS_OK;
   if (precision != LMFS_MIXED && precision != LMFS_FP64) {
@@ -1783,6 +1811,11 @@ int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision)
   LMFS_TRY(check_launch("lam0"));
   LMFS_TRY(far_field(c, c.lam0, c.ufar, precision, false));
   return near_field(c, 1, c.lam0, nullptr, c.ufar, b, problem, precision);
+}
+
+int completion_strengths(Ctx& c, const double* in3, double* lam0) {
+  lam0_kernel<<<(c.d.P * c.d.Nc + 127) / 128, 128, 0, c.stream>>>(in3, c.radii, c.Rc, c.d.P, c.d.Nc, lam0);
+  return check_launch("lam0");
 }
 
 int post_device(Ctx& c, int problem, const double* mu, double* out3) {

@@ -858,6 +858,14 @@ int build_pair_blocks(Ctx& c, int problem) {
   };
   for (auto& e : ev) cudaEventCreate(&e);
   int minr = 1 << 30, maxr = 0;
+  pb.fine_kept = false;
+  if (c.prm.keep_fine) {
+    if (!pb.Zf) LMFS_TRY(dalloc(&pb.Zf, (size_t)C * nmax * k));
+    if (!pb.Yf) LMFS_TRY(dalloc(&pb.Yf, (size_t)C * SYmax * 2));
+    if (!pb.nenh) LMFS_TRY(dalloc(&pb.nenh, (size_t)2 * C));
+    pb.fine_ld = nmax;
+    pb.fine_sy = SYmax;
+  }
   if ((rc = dalloc(&ws1, (size_t)chunk * s1)) || (rc = dalloc(&Z, (size_t)chunk * nmax * k)) ||
       (mob && (rc = dalloc(&Zp, (size_t)chunk * nmax * k))) || (rc = dalloc(&D, (size_t)chunk * ld2 * nmax)) ||
       (rc = dalloc(&ws2, (size_t)chunk * s2)) || (rc = dalloc(&X2, (size_t)chunk * n4 * k)) ||
@@ -957,6 +965,15 @@ int build_pair_blocks(Ctx& c, int problem) {
     extract_E<<<dim3((k * 32 + 255) / 256, nb), 256, 0, c.stream>>>(pd, g, Yf, Z, nmax, (long long)nmax * k, k,
                                                                    mob ? 1.0 : -1.0, pb.E, first, Gf, mob ? Zp : nullptr);
     if ((rc = check_launch("extract_E"))) goto done;
+    if (c.prm.keep_fine &&
+        (cuda_failed(cudaMemcpyAsync(pb.Zf + (long long)first * nmax * k, mob ? Zp : Z, (size_t)nb * nmax * k * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c.stream), "keep Z") ||
+         cuda_failed(cudaMemcpyAsync(pb.Yf + (long long)first * SYmax * 2, Yf, (size_t)nb * SYmax * 2 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c.stream), "keep Yf") ||
+         cuda_failed(cudaMemcpyAsync(pb.nenh + 2LL * first, nenh, 2 * (size_t)nb * sizeof(int), cudaMemcpyDeviceToDevice,
+                                     c.stream), "keep nenh"))) {
+      rc = LMFS_ERR_CUDA; goto done;
+    }
     // the symmetric split of the peanut system reads only the first half of
     // the peanut nodes: fill, project and multiply only those rows
     const bool symC = sym && (Mp % 2 == 0);
@@ -1039,6 +1056,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   if (cuda_failed(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
       cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
   if (hbad) { set_last_error("non-finite value or expired wait in a pair factorization"); rc = LMFS_ERR_NUMERICAL; goto done; }
+  pb.fine_kept = c.prm.keep_fine != 0;
   pb.min_rank_F = minr; pb.max_rank_F = maxr;
   pb.qr_ms = qr_ms; pb.qr_flops = qr_flops;
   pb.fac_ms = fac_ms; pb.fac_flops = fac_flops; pb.rhs_ms = rhs_ms; pb.rhs_flops = rhs_flops;

@@ -501,3 +501,44 @@ def test_p10000_matvec_sampled_rows(L):
     assert e64 < 1e-10
     assert e32 < 1e-6
     s.close()
+
+
+# ------------------------------------------------------------ flow evaluation
+@pytest.mark.parametrize("case", ["pair_resistance", "p100_mobility"])
+def test_flow_at_new_boundary_nodes_matches_oracle(L, case):
+    """The flow of a solve at 100 new nodes per boundary (Algorithm 2 with
+    flowEval: coarse strengths, the compressed corrections of other pairs,
+    each pair's own fine sources beta = -Z lam_bar) against the oracle's
+    evaluation of its own solve: the velocity fields agree within 1e-5 (the
+    solve target; the two solutions differ by about that), and the device's
+    relative boundary residual (eq. (residual)) is within twice the oracle's
+    (plus 1e-8) and below 1e-4."""
+    from oracle import flow
+    if case == "pair_resistance":
+        pk, prm, problem, data = w.two_disks(1e-3), PAIR_SMALL, L.RESISTANCE, w.rigid_velocities(2, 11)
+        name = "resistance"
+    else:
+        pk, prm, problem, data = w.packing_p100(), PACKING, L.MOBILITY, w.forces_torques(100, 5)
+        name = "mobility"
+    so = System(pk.centres, pk.radii, prm, name, keep_fine=True)
+    _, info = so.solve(data, tol=1e-10)
+    u_or, _ = flow.boundary_flow(so, info["mu"], data, 100)
+    res_or, rel_or = flow.boundary_residual(so, info["mu"], data, 100)
+    for prec in (L.FP64, L.MIXED):
+        s = L.Solver(pk.centres, pk.radii, gparams(L, prm, precision=prec, tol=1e-10, keep_fine=1))
+        _, ig = s.solve(problem, data)
+        assert ig["converged"]
+        u = torch.zeros(pk.P * 100 * 2, dtype=torch.float64, device="cuda")
+        res, relg = s.flow_boundary(problem, 100, u)
+        torch.cuda.synchronize()
+        e = rel(u.cpu().numpy().reshape(pk.P, 100, 2), u_or)
+        print(f"{case} precision {prec}: flow vs oracle {e:.2e}; relative boundary residual device {relg:.2e}, "
+              f"oracle {rel_or:.2e}; worst disk device {res.max():.2e} oracle {res_or.max():.2e}")
+        assert e < 1e-5
+        assert relg <= 2 * rel_or + 1e-8 and relg < 1e-4
+        s.close()
+    # without the fine factors the call is refused
+    s = L.Solver(pk.centres, pk.radii, gparams(L, prm, tol=1e-8))
+    s.solve(problem, data)
+    with pytest.raises(L.LmfsError):
+        s.flow_boundary(problem, 100)
