@@ -220,6 +220,25 @@ int lmfs_solve_device(lmfs_handle h, int problem, const double* in_dev, double* 
  * Used to time the whole path repeatedly on one handle. */
 int lmfs_invalidate(lmfs_handle h);
 
+/* Move the disks (one step of a time-dependent simulation; the paper's Sec. 1
+ * names dynamic geometries, where the geometry changes every step, as the
+ * setting that rules out costly per-step precomputation).  centres: HOST
+ * [P][2], the new positions of the same P disks (radii and parameters stay).
+ * Contact detection and the far-field tables run anew.  A close pair's blocks
+ * (A, E; with keep_fine its fine solution and sources) depend only on the two
+ * radii and c_k - c_i (Sec. 3.2-3.3, Sec. 5): every pair (i, k) of the new
+ * geometry that was a pair before and whose vector c_k - c_i moved by at most
+ * tol |c_k - c_i| (tol = 0: bitwise equal) keeps its blocks, and only the
+ * others are precomputed (FP64 QR, as lmfs_precompute_pairs), for each
+ * problem that was precomputed; the one-body factors are kept.  tol > 0
+ * trades the kept blocks' exactness (their error grows with tol) for fewer
+ * recomputed pairs.  *recomputed (optional) = the number of pair blocks
+ * computed anew, summed over the problems.  The last solve's solution and the
+ * flowEval state are dropped.  On an error (LMFS_ERR_INVALID for a bad centre
+ * or overlapping disks, LMFS_ERR_NOMEM, LMFS_ERR_CUDA) the handle keeps its
+ * old geometry and blocks.  Synchronizes the handle's stream. */
+int lmfs_update_geometry(lmfs_handle h, const double* centres, double tol, int* recomputed);
+
 /* Diagnostics of the last pair precompute of `problem`: out[8] =
  * {wall ms, QR kernel ms (CUDA events on the handle's stream), algorithmic
  * FP64 flops of those QR launches, min rank of F, max rank of F, C, far-field

@@ -132,6 +132,16 @@ class Solver:
     def invalidate(self):
         _lib.check(self.lib.lmfs_invalidate(self.h))
 
+    def update_geometry(self, centres, tol=0.0):
+        """Move the disks to centres [P][2], keeping the blocks of every close
+        pair whose relative position moved by at most tol |c_k - c_i|; returns
+        the number of pair blocks computed anew."""
+        centres = np.ascontiguousarray(centres, dtype=np.float64).reshape(self.P, 2)
+        n = ctypes.c_int()
+        _lib.check(self.lib.lmfs_update_geometry(self.h, _ptr(centres), float(tol), ctypes.byref(n)))
+        self.centres = centres
+        return n.value
+
     def stats(self, problem):
         out = np.zeros(8)
         _lib.check(self.lib.lmfs_stats(self.h, problem, _ptr(out)))

@@ -446,6 +446,180 @@ int solve_finish(lmfs_handle h, int problem, int iters, double relres, double* o
   return relres <= c.prm.tol ? LMFS_OK : LMFS_ERR_NOT_CONVERGED;
 }
 
+// Dynamic geometry (Sec. 1: in a time-dependent simulation the geometry
+// changes every step): the blocks of a close pair (i, k) depend only on the two
+// radii, the vector c_k - c_i and the parameters (the Stokeslet depends on
+// differences of points only, and every point set of the pair -- the unrotated
+// fine proxy rings and the ellipse segments along the pair axis of Sec. 5 -- is
+// placed relative to the two centres), and the one-body factors only on the
+// radius.  update_geometry keeps, for every pair of the new
+// geometry whose vector is within tol |c_k - c_i| of its old value (bitwise
+// equal for tol = 0), the pair's A and E (and its kept fine solution, with the
+// fine sources moved with disk i); only the other pairs are precomputed.
+// to[dst[b]] = from[src[b]] (+ shift[b] on x, y components), len doubles a row
+__global__ void gather_rows(const double* __restrict__ from, double* __restrict__ to, const int* __restrict__ src,
+                            const int* __restrict__ dst, long long len, const double* __restrict__ shift) {
+  const long long a = (long long)src[blockIdx.x] * len, b = (long long)dst[blockIdx.x] * len;
+  const double sx = shift ? shift[2 * blockIdx.x] : 0.0, sy = shift ? shift[2 * blockIdx.x + 1] : 0.0;
+  for (long long t = threadIdx.x; t < len; t += blockDim.x) to[b + t] = from[a + t] + ((t & 1) ? sy : sx);
+}
+
+static int gather_rows_host(Ctx& c, const void* from, void* to, const std::vector<int>& src,
+                            const std::vector<int>& dst, long long len, const std::vector<double>* shift) {
+  if (src.empty()) return LMFS_OK;
+  int *ds = nullptr, *dd = nullptr;
+  double* dsh = nullptr;
+  int rc = LMFS_OK;
+  if ((rc = dalloc(&ds, src.size())) || (rc = dalloc(&dd, dst.size())) ||
+      (shift && (rc = dalloc(&dsh, shift->size()))))
+    goto out;
+  if (cuda_failed(cudaMemcpyAsync(ds, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+      cuda_failed(cudaMemcpyAsync(dd, dst.data(), dst.size() * sizeof(int), cudaMemcpyHostToDevice, c.stream), "h2d") ||
+      (shift && cuda_failed(cudaMemcpyAsync(dsh, shift->data(), shift->size() * sizeof(double),
+                                            cudaMemcpyHostToDevice, c.stream), "h2d"))) {
+    rc = LMFS_ERR_CUDA;
+    goto out;
+  }
+  gather_rows<<<(unsigned)src.size(), 256, 0, c.stream>>>((const double*)from, (double*)to, ds, dd, len, dsh);
+  rc = check_launch("gather_rows");
+  // the index vectors are the caller's host memory: done before they go
+  if (rc == LMFS_OK && cuda_failed(cudaStreamSynchronize(c.stream), "sync")) rc = LMFS_ERR_CUDA;
+out:
+  dfree(ds); dfree(dd); dfree(dsh);
+  return rc;
+}
+
+// The new context nc (same P, radii and parameters as oc) gets problem's
+// blocks: kept pairs gathered from oc, the others precomputed on a sub-list.
+static int carry_pair_blocks(Ctx& nc, Ctx& oc, int problem, double tol, int* recomputed) {
+  PairBlocks& nb = nc.prob[problem];
+  PairBlocks& ob = oc.prob[problem];
+  const int C = nc.C, n4 = 4 * nc.d.Nc;
+  const bool fine = nc.prm.keep_fine != 0;
+  std::map<std::pair<int, int>, int> old_idx;
+  for (int q = 0; q < oc.C; ++q) old_idx[{oc.pairs_h[2 * q], oc.pairs_h[2 * q + 1]}] = q;
+  std::vector<int> src, dst, chg, sub;
+  std::vector<double> shift;
+  for (int q = 0; q < C; ++q) {
+    const int i = nc.pairs_h[2 * q], k = nc.pairs_h[2 * q + 1];
+    auto it = old_idx.find({i, k});
+    bool keep = it != old_idx.end() && (!fine || ob.fine_kept);
+    if (keep) {
+      const double ox = oc.centres_h[2 * k] - oc.centres_h[2 * i], oy = oc.centres_h[2 * k + 1] - oc.centres_h[2 * i + 1];
+      const double nx = nc.centres_h[2 * k] - nc.centres_h[2 * i], ny = nc.centres_h[2 * k + 1] - nc.centres_h[2 * i + 1];
+      keep = tol > 0 ? std::hypot(nx - ox, ny - oy) <= tol * std::hypot(ox, oy) : (nx == ox && ny == oy);
+    }
+    if (keep) {
+      src.push_back(it->second);
+      dst.push_back(q);
+      shift.push_back(nc.centres_h[2 * i] - oc.centres_h[2 * i]);
+      shift.push_back(nc.centres_h[2 * i + 1] - oc.centres_h[2 * i + 1]);
+    } else {
+      chg.push_back(q);
+      sub.push_back(i);
+      sub.push_back(k);
+    }
+  }
+  // the changed pairs: the pair precompute on their sub-list, with blocks of
+  // its own, into the new context's blocks afterwards
+  PairBlocks part;
+  if (!chg.empty()) {
+    int* dsub = nullptr;
+    LMFS_TRY(dalloc(&dsub, sub.size()));
+    if (cuda_failed(cudaMemcpyAsync(dsub, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice, nc.stream),
+                    "h2d") ||
+        cuda_failed(cudaStreamSynchronize(nc.stream), "sync")) {
+      dfree(dsub);
+      return LMFS_ERR_CUDA;
+    }
+    const int C0 = nc.C;
+    int* pairs0 = nc.pairs;
+    std::swap(nc.pairs_h, sub);
+    nc.C = (int)chg.size();
+    nc.pairs = dsub;
+    std::swap(nc.prob[problem], part);
+    const int rc = build_pair_blocks(nc, problem);
+    std::swap(nc.prob[problem], part);
+    nc.C = C0;
+    nc.pairs = pairs0;
+    std::swap(nc.pairs_h, sub);
+    dfree(dsub);
+    if (rc != LMFS_OK) {
+      dfree(part.A); dfree(part.E); dfree(part.Zf); dfree(part.Yf); dfree(part.nenh);
+      return rc;
+    }
+  }
+  int rc = LMFS_OK;
+  const int ld = fine ? (ob.fine_kept ? ob.fine_ld : part.fine_ld) : 0;
+  const int sy = fine ? (ob.fine_kept ? ob.fine_sy : part.fine_sy) : 0;
+  std::vector<int> id(chg.size());
+  for (size_t q = 0; q < chg.size(); ++q) id[q] = (int)q;
+  if ((rc = dalloc(&nb.A, (size_t)std::max(C, 1) * n4 * n4)) || (rc = dalloc(&nb.E, (size_t)std::max(C, 1) * 6 * n4)))
+    goto done;
+  if (fine && C > 0 &&
+      ((rc = dalloc(&nb.Zf, (size_t)C * ld * n4)) || (rc = dalloc(&nb.Yf, (size_t)C * sy * 2)) ||
+       (rc = dalloc(&nb.nenh, 2 * (size_t)C))))
+    goto done;
+  if ((rc = gather_rows_host(nc, ob.A, nb.A, src, dst, (long long)n4 * n4, nullptr)) ||
+      (rc = gather_rows_host(nc, ob.E, nb.E, src, dst, 6LL * n4, nullptr)) ||
+      (rc = gather_rows_host(nc, part.A, nb.A, id, chg, (long long)n4 * n4, nullptr)) ||
+      (rc = gather_rows_host(nc, part.E, nb.E, id, chg, 6LL * n4, nullptr)))
+    goto done;
+  // the kept ellipse-source counts are two ints a pair: one 8-byte row
+  if (fine && ((rc = gather_rows_host(nc, ob.Zf, nb.Zf, src, dst, (long long)ld * n4, nullptr)) ||
+               (rc = gather_rows_host(nc, ob.Yf, nb.Yf, src, dst, 2LL * sy, &shift)) ||
+               (rc = gather_rows_host(nc, ob.nenh, nb.nenh, src, dst, 1, nullptr)) ||
+               (rc = gather_rows_host(nc, part.Zf, nb.Zf, id, chg, (long long)ld * n4, nullptr)) ||
+               (rc = gather_rows_host(nc, part.Yf, nb.Yf, id, chg, 2LL * sy, nullptr)) ||
+               (rc = gather_rows_host(nc, part.nenh, nb.nenh, id, chg, 1, nullptr))))
+    goto done;
+  nb.fine_ld = ld;
+  nb.fine_sy = sy;
+  nb.fine_kept = fine;
+  nb.t_ms = part.t_ms; nb.qr_ms = part.qr_ms; nb.qr_flops = part.qr_flops;
+  nb.fac_ms = part.fac_ms; nb.fac_flops = part.fac_flops; nb.rhs_ms = part.rhs_ms; nb.rhs_flops = part.rhs_flops;
+  nb.min_rank_F = chg.empty() ? ob.min_rank_F : part.min_rank_F;
+  nb.max_rank_F = chg.empty() ? ob.max_rank_F : part.max_rank_F;
+  if (recomputed) *recomputed += (int)chg.size();
+done:
+  dfree(part.A); dfree(part.E); dfree(part.Zf); dfree(part.Yf); dfree(part.nenh);
+  return rc;
+}
+
+static int update_geometry(Ctx& oc, const double* centres, double tol, int* recomputed) {
+  LMFS_CUDA(cudaStreamSynchronize(oc.stream));
+  // the new context runs on the old one's stream, which it takes over
+  lmfs_params prm = oc.prm;
+  prm.stream = oc.stream;
+  Ctx nc;
+  int rc = create_ctx(nc, centres, oc.radii_h.data(), oc.d.P, prm);
+  int count = 0;
+  for (int q = 0; q < 2 && rc == LMFS_OK; ++q) {
+    if (!oc.prob[q].ready) continue;
+    rc = carry_pair_blocks(nc, oc, q, tol, &count);
+    if (rc == LMFS_OK) {
+      // equal radii, equal classes: the one-body factors move over as they are
+      std::swap(nc.prob[q].ob, oc.prob[q].ob);
+      nc.prob[q].ready = true;
+    }
+  }
+  if (rc == LMFS_OK) rc = cuda_failed(cudaStreamSynchronize(nc.stream), "sync") ? LMFS_ERR_CUDA : LMFS_OK;
+  if (rc != LMFS_OK) {
+    // the handle keeps its old geometry (and one-body factors moved back)
+    for (int q = 0; q < 2; ++q)
+      if (nc.prob[q].ready) std::swap(nc.prob[q].ob, oc.prob[q].ob);
+    free_ctx(nc);
+    return rc;
+  }
+  nc.prm.stream = oc.prm.stream;
+  nc.own_stream = oc.own_stream;
+  oc.own_stream = false;
+  std::swap(oc, nc);
+  free_ctx(nc);
+  if (recomputed) *recomputed = count;
+  return LMFS_OK;
+}
+
 }  // namespace lmfs
 
 using namespace lmfs;
@@ -479,6 +653,17 @@ int lmfs_create(const double* centres, const double* radii, int P, const lmfs_pa
   }
   *out = h;
   return LMFS_OK;
+}
+
+int lmfs_update_geometry(lmfs_handle h, const double* centres, double tol, int* recomputed) {
+  if (!h || !centres || !(tol >= 0)) {
+    set_last_error("a handle, centres and tol >= 0 required");
+    return LMFS_ERR_INVALID;
+  }
+  set_last_error("");
+  LMFS_CUDA(cudaSetDevice(h->c.device));
+  AllocScope as(h->c.stream, h->c.prm);
+  return update_geometry(h->c, centres, tol, recomputed);
 }
 
 int lmfs_destroy(lmfs_handle h) {

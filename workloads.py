@@ -255,6 +255,25 @@ def packing_p10000(seed=4, nsweep=6):
     return packing(10000, 0.65, seed, gmin=1e-3, nsweep=nsweep, snap_gap=1e-3)
 
 
+def move_disks(pk: Packing, n_move, seed, frac=0.3, shift=(0.0, 0.0)):
+    """One step of a moving geometry: n_move distinct disks (drawn without
+    replacement) each displaced, one after the other, in a uniform random
+    direction by frac times its current smallest gap to any other disk (so
+    every gap stays >= (1 - frac) times what it was), then every centre
+    shifted by `shift`.  Returns (new centres [P, 2], moved disk indices)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = pk.centres.copy()
+    r = pk.radii
+    idx = rng.choice(pk.P, size=n_move, replace=False)
+    for j in idx:
+        d = np.hypot(c[:, 0] - c[j, 0], c[:, 1] - c[j, 1]) - r - r[j]
+        d[j] = np.inf
+        a = rng.uniform(0.0, 2.0 * np.pi)
+        c[j] += frac * d.min() * np.array([np.cos(a), np.sin(a)])
+    c += np.asarray(shift, dtype=np.float64)
+    return c, np.sort(idx)
+
+
 def rigid_velocities(P, seed):
     """(v_x, v_y, omega) per disk, each N(0,1)."""
     rng = np.random.Generator(np.random.PCG64(seed))
