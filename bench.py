@@ -708,6 +708,135 @@ def run_large(args):
     print(json.dumps(res))
 
 
+def _stats(xs):
+    xs = [float(x) for x in xs]
+    return {"mean": float(np.mean(xs)), "min": float(np.min(xs)), "max": float(np.max(xs))}
+
+
+def _solve_case(L, pk, prm, code, data, m_eval):
+    """One solve through the library: iterations, the relative boundary
+    residual at m_eval new nodes per boundary, close pairs, solve time."""
+    s = L.Solver(pk.centres, pk.radii, prm)
+    t0 = time.perf_counter()
+    out, info = s.solve(code, data)
+    t = time.perf_counter() - t0
+    _, rel_res = s.flow_boundary(code, m_eval)
+    r = {"iters": info["iters"], "converged": info["converged"], "residual": rel_res, "n_pairs": int(s.n_pairs),
+         "solve_s": t}
+    return s, out, r
+
+
+def experiment_delta(L, w, runs):
+    """Sec. 6.1: random clusters with every disk at separation delta from a
+    neighbour; the two-body solver against one-body preconditioning at the
+    same coarse discretization (no pair blocks: delta_c = 0), and the
+    two-way error (mobility output fed to the resistance solve)."""
+    # peanut nodes: Mp = 10 N_c / 3 (rounded to even) keeps the peanut fit as
+    # overdetermined as Sec. 6.2's M_p = 200 at N_c = 60; at N_c = 128 the
+    # default 200 nodes give fewer equations (400) than unknowns (512)
+    cases = {
+        "mobility": (50, dict(Nc=80, Mc=96, Nfp=60, Nell=100, Mp=268), L.MOBILITY, (1e-1, 1e-2, 1e-3, 1e-4)),
+        "resistance": (20, dict(Nc=128, Mc=154, Nfp=120, Nell=100, Mp=428), L.RESISTANCE, (1e-1, 1e-2, 1e-3)),
+    }
+    out = {}
+    for name, (P, kw, code, deltas) in cases.items():
+        rows = []
+        for delta in deltas:
+            agg = {"two_body": [], "one_body": [], "two_way": [], "pairs_per_body": []}
+            for q in range(runs):
+                pk = w.cluster(P, delta, seed=100 * q + 7)
+                data = w.forces_torques(P, q) if code == L.MOBILITY else w.rigid_velocities(P, q)
+                m_eval = 2 * kw["Mc"]
+                prm = L.Params(precision=L.FP64, tol=1e-7, keep_fine=1, **kw)
+                s, res, r2 = _solve_case(L, pk, prm, code, data, m_eval)
+                s.close()
+                if code == L.MOBILITY:
+                    # two-way error (Sec. 6.1): the resistance output (forces
+                    # of N(0, 1) velocities) fed to the mobility solve, against
+                    # those velocities; GMRES at 1e-11 so that its tolerance
+                    # does not hide the discretization's share, and both
+                    # solves' boundary residuals beside it
+                    s2 = L.Solver(pk.centres, pk.radii,
+                                  L.Params(precision=L.FP64, tol=1e-11, maxit=1000, keep_fine=1, **kw))
+                    uv = w.rigid_velocities(P, 50 + q)
+                    f, i_r = s2.solve(L.RESISTANCE, uv)
+                    _, res_r = s2.flow_boundary(L.RESISTANCE, m_eval)
+                    v2, i_m = s2.solve(L.MOBILITY, f)
+                    _, res_m = s2.flow_boundary(L.MOBILITY, m_eval)
+                    s2.close()
+                    agg["two_way"].append({"error": float(np.linalg.norm(v2 - uv) / np.linalg.norm(uv)),
+                                           "residual_resistance": res_r, "residual_mobility": res_m,
+                                           "iters": [i_r["iters"], i_m["iters"]],
+                                           "converged": bool(i_r["converged"] and i_m["converged"])})
+                s1, _, r1 = _solve_case(L, pk, L.Params(precision=L.FP64, tol=1e-7, keep_fine=1, delta_c=0.0, **kw),
+                                        code, data, m_eval)
+                s1.close()
+                agg["two_body"].append(r2)
+                agg["one_body"].append(r1)
+                agg["pairs_per_body"].append(2.0 * r2["n_pairs"] / P)
+            row = {"delta": delta, "runs": runs, "pairs_per_body": _stats(agg["pairs_per_body"])}
+            for k in ("two_body", "one_body"):
+                row[k] = {"iters": _stats([r["iters"] for r in agg[k]]),
+                          "residual": _stats([r["residual"] for r in agg[k]]),
+                          "solve_s": _stats([r["solve_s"] for r in agg[k]]),
+                          "not_converged": sum(1 for r in agg[k] if not r["converged"])}
+            if agg["two_way"]:
+                tw = agg["two_way"]
+                row["two_way"] = {"error": _stats([r["error"] for r in tw]),
+                                  "over_residual": _stats([r["error"] / max(r["residual_resistance"],
+                                                                            r["residual_mobility"]) for r in tw]),
+                                  "tol": 1e-11, "per_run": tw}
+            row["per_run"] = {k: [{"iters": r["iters"], "residual": r["residual"]} for r in agg[k]]
+                              for k in ("two_body", "one_body")}
+            rows.append(row)
+        out[name] = {"P": P, "params": kw, "tol": 1e-7, "precision": "fp64", "m_eval": 2 * kw["Mc"], "rows": rows}
+    return out
+
+
+def experiment_packing(L, w, sweep, runs):
+    """Sec. 6.2: mobility on random packings (square lattice + Metropolis
+    sweeps, minimum gap 1e-3), GMRES tol 1e-7: iterations, close neighbours
+    per body and the relative boundary residual, over `runs` packings per
+    point; sweep "phi" fixes P = 500, sweep "P" fixes phi = 0.65."""
+    pts = ([(500, phi) for phi in (0.30, 0.40, 0.50, 0.60, 0.65)] if sweep == "phi"
+           else [(P, 0.65) for P in (100, 300, 1000, 3000, 10000)])
+    rows = []
+    for P, phi in pts:
+        n = runs if P <= 1000 else max(1, runs // (3 if P <= 3000 else 10))
+        rs = []
+        for q in range(n):
+            pk = w.packing(P, phi, seed=1000 + q, gmin=1e-3, nsweep=10 if P <= 3000 else 6)
+            ft = w.forces_torques(P, q)
+            prm = L.Params(precision=L.FP64, tol=1e-7, keep_fine=1)
+            s, _, r = _solve_case(L, pk, prm, L.MOBILITY, ft, 144)
+            s.close()
+            r["pairs_per_body"] = 2.0 * r["n_pairs"] / P
+            rs.append(r)
+        rows.append({"P": P, "phi": phi, "runs": n, "iters": _stats([r["iters"] for r in rs]),
+                     "pairs_per_body": _stats([r["pairs_per_body"] for r in rs]),
+                     "residual": _stats([r["residual"] for r in rs]),
+                     "solve_s": _stats([r["solve_s"] for r in rs]),
+                     "not_converged": sum(1 for r in rs if not r["converged"])})
+    return {"sweep": sweep, "precision": "fp64", "tol": 1e-7, "m_eval": 144, "rows": rows}
+
+
+def run_experiment(args):
+    """The paper's experiments through the library on the GPU (side reports,
+    one JSON line): --experiment delta (Sec. 6.1), phi or P (Sec. 6.2)."""
+    from paper_2606_11273_gb300 import build as b
+    b.build()
+    import paper_2606_11273_gb300 as L
+    import workloads as w
+    t0 = time.perf_counter()
+    if args.experiment == "delta":
+        res = experiment_delta(L, w, args.runs if args.runs else 5)
+    else:
+        res = experiment_packing(L, w, args.experiment, args.runs if args.runs else 10)
+    res["experiment"] = args.experiment
+    res["wall_s"] = time.perf_counter() - t0
+    print(json.dumps(res))
+
+
 def run_serving(args):
     """Serving stream (Poisson arrivals, mixed disk counts and problems)
     through the continuous-batching server in the mixed-precision form,
@@ -877,7 +1006,14 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="default run: leave out the bounded serving key")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="non-default workloads print timings and full-size checks, not the contract line")
+    ap.add_argument("--experiment", default=None, choices=["delta", "phi", "P"],
+                    help="the paper's experiments on the GPU: delta-sweep clusters (Sec. 6.1), phi- or P-sweep "
+                         "packings (Sec. 6.2); prints one JSON line")
+    ap.add_argument("--runs", type=int, default=0, help="experiment: runs per point (default 5 delta, 10 sweeps)")
     args = ap.parse_args()
+    if args.experiment:
+        run_experiment(args)
+        return
     if args.profile_case:
         run_profile_case(args.profile_case)
         return

@@ -137,3 +137,28 @@ def test_generators_hold_no_method_arithmetic():
         elif isinstance(node, (ast.FunctionDef, ast.ClassDef)):
             names.add(node.name)
     assert not any("stokeslet" in n.lower() or "lmfs" in n.lower() for n in names), names
+
+
+@pytest.mark.parametrize("delta", [1e-1, 1e-3, 1e-4])
+def test_cluster_every_disk_at_separation_delta(delta):
+    """Sec. 6.1 clusters: every disk has a neighbour at separation delta
+    (to rounding) and no separation is below it."""
+    pk = w.cluster(50, delta, 3)
+    c = pk.centres
+    g = np.hypot(c[:, None, 0] - c[None, :, 0], c[:, None, 1] - c[None, :, 1]) - 2.0
+    np.fill_diagonal(g, np.inf)
+    assert np.all(np.abs(g.min(axis=1) - delta) <= 1e-12 + 1e-9 * delta)
+    assert g.min() >= delta * (1 - 1e-9)
+
+
+def test_moved_disks_keep_positive_gaps():
+    pk = w.packing_p100()
+    c, idx = w.move_disks(pk, 10, seed=1)
+    assert len(set(idx.tolist())) == 10
+    moved = np.any(c != pk.centres, axis=1)
+    assert set(np.flatnonzero(moved).tolist()) == set(idx.tolist())
+    g = np.hypot(c[:, None, 0] - c[None, :, 0], c[:, None, 1] - c[None, :, 1]) - pk.radii[:, None] - pk.radii[None, :]
+    np.fill_diagonal(g, np.inf)
+    g0 = np.hypot(*(pk.centres[:, None, :] - pk.centres[None, :, :]).transpose(2, 0, 1)) - 2.0
+    np.fill_diagonal(g0, np.inf)
+    assert g.min() >= (1 - 0.3) ** 2 * g0.min() * (1 - 1e-12)      # at worst two moves close one gap

@@ -255,12 +255,38 @@ def packing_p10000(seed=4, nsweep=6):
     return packing(10000, 0.65, seed, gmin=1e-3, nsweep=nsweep, snap_gap=1e-3)
 
 
+def cluster(P, delta, seed, max_tries=200000):
+    """Random cluster of P unit disks in which every disk has separation
+    exactly delta from at least one other (Sec. 6.1): disk 0 at the origin;
+    each next disk at distance 2 + delta from a uniformly drawn earlier disk,
+    in a uniform random direction, kept only if every other separation is at
+    least delta.  Returns a Packing whose box bounds the cluster."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = np.zeros((P, 2))
+    n, tries = 1, 0
+    while n < P:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("cluster: no admissible placement found")
+        j = int(rng.integers(n))
+        a = rng.uniform(0.0, 2.0 * np.pi)
+        x = c[j] + (2.0 + delta) * np.array([np.cos(a), np.sin(a)])
+        d = np.hypot(c[:n, 0] - x[0], c[:n, 1] - x[1]) - 2.0
+        d[j] = delta
+        if d.min() >= delta * (1.0 - 1e-12):
+            c[n] = x
+            n += 1
+    lo, hi = c.min(axis=0) - 1.0, c.max(axis=0) + 1.0
+    return Packing(centres=c, radii=np.ones(P), box=(float(hi[0] - lo[0]), float(hi[1] - lo[1])),
+                   meta={"P": P, "delta": delta, "seed": seed, "tries": tries})
+
+
 def move_disks(pk: Packing, n_move, seed, frac=0.3, shift=(0.0, 0.0)):
     """One step of a moving geometry: n_move distinct disks (drawn without
     replacement) each displaced, one after the other, in a uniform random
     direction by frac times its current smallest gap to any other disk (so
-    every gap stays >= (1 - frac) times what it was), then every centre
-    shifted by `shift`.  Returns (new centres [P, 2], moved disk indices)."""
+    its gaps stay >= (1 - frac) times their values just before its move),
+    then every centre shifted by `shift`.  Returns (new centres [P, 2], moved disk indices)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     c = pk.centres.copy()
     r = pk.radii
