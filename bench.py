@@ -96,23 +96,23 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
-# DRAM traffic of the pivoted-QR kernel (qrcp_kernel) per solve of the P = 100
-# workload -- its two launches, the fine pair systems and the peanut systems
-# of the 37 pairs -- from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum).  Valid only for the kernel source it was taken on:
-# reported as null once lmfs_qr.cu changes.
-QRCP_TRAFFIC_BYTES = 23436956160 + 25761400320 + 14299136 + 2100224
-QRCP_TRAFFIC_SRC_SHA256 = "3ce04c663094e62340580234a338a11233c67842ce496f69c0fbeeff384884f9"
+# DRAM traffic of the blocked QR kernel (rqr_kernel) per fine half system:
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of its launch
+# on the 398 fine half systems of `bench.py --profile-case qr_mid` (P = 160,
+# area fraction 0.65), divided by 398.  Valid only for the kernel source it was
+# taken on: reported as null once lmfs_rqr.cu changes.
+RQR_TRAFFIC_PER_MATRIX = (74373963776 + 38127273728) / 398.0
+RQR_TRAFFIC_SRC_SHA256 = "8edb5bebabe92e2f812ff735fa64de0be09ba4bec68747b10c712de6c0dbb7ec"
 
 
-def qrcp_traffic():
+def rqr_traffic_per_matrix():
     import hashlib
-    src = os.path.join(ROOT, "paper_2606_11273_gb300", "csrc", "lmfs_qr.cu")
+    src = os.path.join(ROOT, "paper_2606_11273_gb300", "csrc", "lmfs_rqr.cu")
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    return QRCP_TRAFFIC_BYTES if h == QRCP_TRAFFIC_SRC_SHA256 else None
+    return RQR_TRAFFIC_PER_MATRIX if h == RQR_TRAFFIC_SRC_SHA256 else None
 
 
 def dist_env():
@@ -522,7 +522,10 @@ def run_ours(args):
         fac_ms = float(np.mean([q["factor_ms"] for q in qr]))
         fac_tf = float(np.mean([q["factor_flops"] for q in qr])) / (fac_ms * 1e-3) / 1e12
         rhs_ms = float(np.mean([q["rhs_ms"] for q in qr]))
-        rhs_tf = float(np.mean([q["rhs_flops"] for q in qr])) / (rhs_ms * 1e-3) / 1e12
+        rhs_tf = float(np.mean([q["rhs_flops"] for q in qr])) / (rhs_ms * 1e-3) / 1e12 if rhs_ms > 0 else None
+        fine_ms = float(np.mean([q["fine_ms"] for q in qr]))
+        fine_tf = float(np.mean([q["fine_flops"] for q in qr])) / (fine_ms * 1e-3) / 1e12
+        fine_blocked = all(q["fine_blocked"] > 0 for q in qr)
         pre_ms = float(np.mean([q["precompute_ms"] for q in qr]))
         clocks = clk.summary()
         n_pairs = int(s.n_pairs)
@@ -544,10 +547,10 @@ def run_ours(args):
         stk_series, stk_series_sample = stokeslet_kernel_rate(L, torch, stream, L.MIXED_DIRECT)
         serving = serving_side(L) if not args.no_serving else None
         t_or, or_sample, or_parts = oracle_extrapolated(pk, iters + rounds)
-        # DRAM traffic of qrcp_kernel: the ncu capture of the P = 100 workload's
-        # two launches per solve (37 pairs), scaled by the number of pairs
-        tr = qrcp_traffic()
-        traffic = tr * n_pairs / 37.0 if tr is not None else None
+        # DRAM traffic of rqr_kernel per step: the per-system figure of the
+        # P = 160 capture times the step's fine half systems (two per pair)
+        tr = rqr_traffic_per_matrix()
+        traffic = tr * 2 * n_pairs if (tr is not None and fine_blocked) else None
         result = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -563,7 +566,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(np.mean(lat)), "note": "per timed step (one solve each)"},
-            "breakdown_ms": {"precompute": pre_ms, "qr_factor": fac_ms, "qr_rhs": rhs_ms,
+            "breakdown_ms": {"precompute": pre_ms, "qr_fine_systems": fine_ms, "qr_factor": fac_ms, "qr_rhs": rhs_ms,
                              "rest": float(np.mean(lat)) - pre_ms},
             "gmres_iters": iters, "refine_rounds": rounds,
             "fp64_relres": float(np.max([x["relres"] for x in infos])),
@@ -572,17 +575,23 @@ def run_ours(args):
             "dynamic_geometry": dyn,
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "qrcp_kernel (pivoted FP64 QR of the pair systems)",
-                         "achieved": fac_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
-                         "frac": fac_tf / fp64_peak_tf, "traffic": traffic,
-                         "traffic_note": "DRAM bytes per step: ncu capture of the P = 100 workload's qrcp launches "
-                                         "scaled by pairs (10470 / 37); null if the kernel changed since",
+            "roofline": {"bound": "alu",
+                         "kernel": ("rqr_kernel (blocked FP64 QR of the fine pair systems, pivots from a random "
+                                    "sketch, right-hand sides in the same sweep)" if fine_blocked else
+                                    "qrcp_kernel + apply_qt_kernel (pivoted FP64 QR of the fine pair systems)"),
+                         "achieved": fine_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
+                         "frac": fine_tf / fp64_peak_tf, "traffic": traffic,
+                         "algorithmic_flops_per_step": float(np.mean([q["fine_flops"] for q in qr])),
+                         "traffic_note": "DRAM bytes per step: the ncu capture of rqr_kernel on 398 fine half "
+                                         "systems (P = 160), per system, times the 20940 of the step; null if "
+                                         "the kernel changed since",
                          "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (no FP64 figure "
                                       "in the measured peaks)",
-                         "kernel_ms_per_step": fac_ms, "share_of_step": fac_ms / (t_ms / args.steps)},
-            "roofline_rhs": {"bound": "alu", "kernel": "apply_qt_kernel (Q^T B and back substitution)",
-                             "achieved": rhs_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
-                             "frac": rhs_tf / fp64_peak_tf, "kernel_ms_per_step": rhs_ms},
+                         "kernel_ms_per_step": fine_ms, "share_of_step": fine_ms / (t_ms / args.steps)},
+            "qr_all_stages": {"factor_ms": fac_ms, "factor_tflops": fac_tf, "rhs_ms": rhs_ms, "rhs_tflops": rhs_tf,
+                              "note": "all pair QR launches of a step: the fine systems (blocked form: counted as "
+                                      "factorization) and the peanut systems (pivoted cluster form, "
+                                      "qrcp_kernel + apply_qt_kernel)"},
             "p100": side,
             "stokeslet_tile_kernel": {**stk, "kernel": "far32_lean_kernel (LMFS_FP32_FAST)", "flops_per_pair": 17,
                                       "achieved_tflops_17": stk["gpair_per_s"] * 17 / 1e3,
@@ -951,8 +960,21 @@ def run_profile_case(case):
         if case == "matvec_large":
             s.matvec(L.MOBILITY, mu, u, L.FP64)
         torch.cuda.synchronize()
+    elif case == "qr_large":
+        # the P = 10^4 pair precompute (23 chunks of <= 456 pairs)
+        pk, _ = workload("p10000_phi065_mobility")
+        s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))
+        s.precompute(L.MOBILITY)
+        torch.cuda.synchronize()
+    elif case == "qr_mid":
+        # P = 160 at area fraction 0.65: ~350 fine half systems, one launch
+        import workloads as w
+        pk = w.packing(160, 0.65, 5, gmin=1e-3)
+        s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))
+        s.precompute(L.MOBILITY)
+        torch.cuda.synchronize()
     elif case in ("qr", "matvec"):
-        pk, ft = workload()
+        pk, ft = workload("p100_phi040_mobility")
         s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))
         s.precompute(L.MOBILITY)
         if case == "qr":
@@ -992,7 +1014,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile-case", default=None, choices=["qr", "matvec", "stokeslet", "stokeslet_fast", "m2p_large", "matvec_large"],
+    ap.add_argument("--profile-case", default=None, choices=["qr", "qr_mid", "qr_large", "matvec", "stokeslet", "stokeslet_fast", "m2p_large", "matvec_large"],
                     help="run one small bounded case for an ncu capture and exit")
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: served mixed precision against one-at-a-time FP64 (side report)")

@@ -245,12 +245,15 @@ int lmfs_update_geometry(lmfs_handle h, const double* centres, double tol, int* 
  * source-range split, near-list entries}. */
 int lmfs_stats(lmfs_handle h, int problem, double* out);
 
-/* The pair QR of the last precompute split into its two kernels (CUDA events
- * on the handle's stream): out[4] = {factorization ms, its algorithmic FP64
- * flops (sum over reflectors s < rank of 4 (m - s)(n - s - 1)), right-hand
- * sides ms, their flops (4 (m - s) k per reflector plus k rank^2 for the back
- * substitution)}.  HOST array; zeros before the first precompute.  No
- * counterpart in the paper: a measurement hook. */
+/* The pair QR of the last precompute (CUDA events on the handle's stream):
+ * out[7] = {factorization ms, its algorithmic FP64 flops (sum over reflectors
+ * s < rank of 4 (m - s)(n - s - 1)), right-hand sides ms, their flops
+ * (4 (m - s) k per reflector plus k rank^2 for the back substitution), the
+ * fine systems' QR stage ms, its flops (both parts), 1 if that stage ran the
+ * blocked QR with sketch pivoting (which updates the right-hand sides in the
+ * factorization's sweep, so its flops count as factorization) else 0}.  HOST
+ * array; zeros before the first precompute.  No counterpart in the paper: a
+ * measurement hook. */
 int lmfs_qr_stats(lmfs_handle h, int problem, double* out);
 
 /* The flow of the last solve of `problem` at m_eval new nodes on every

@@ -148,9 +148,10 @@ class Solver:
         keys = ["precompute_ms", "qr_ms", "qr_flops", "min_rank_F", "max_rank_F", "n_pairs", "far_split",
                 "near_entries"]
         d = dict(zip(keys, out.tolist()))
-        q = np.zeros(4)
+        q = np.zeros(7)
         _lib.check(self.lib.lmfs_qr_stats(self.h, problem, _ptr(q)))
-        d.update(zip(["factor_ms", "factor_flops", "rhs_ms", "rhs_flops"], q.tolist()))
+        d.update(zip(["factor_ms", "factor_flops", "rhs_ms", "rhs_flops", "fine_ms", "fine_flops",
+                      "fine_blocked"], q.tolist()))
         return d
 
     def flow_boundary(self, problem, m_eval, u_dev=None):

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblmfs.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["lmfs_api.cu", "lmfs_geom.cu", "lmfs_qr.cu", "lmfs_precompute.cu", "lmfs_matvec.cu",
-           "lmfs_fmm.cu", "lmfs_flow.cu", "lmfs_gmres.cu", "lmfs_server.cu"]
+           "lmfs_fmm.cu", "lmfs_flow.cu", "lmfs_gmres.cu", "lmfs_server.cu", "lmfs_rqr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

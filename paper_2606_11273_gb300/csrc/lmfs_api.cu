@@ -578,6 +578,7 @@ static int carry_pair_blocks(Ctx& nc, Ctx& oc, int problem, double tol, int* rec
   nb.fine_kept = fine;
   nb.t_ms = part.t_ms; nb.qr_ms = part.qr_ms; nb.qr_flops = part.qr_flops;
   nb.fac_ms = part.fac_ms; nb.fac_flops = part.fac_flops; nb.rhs_ms = part.rhs_ms; nb.rhs_flops = part.rhs_flops;
+  nb.fine_ms = part.fine_ms; nb.fine_flops = part.fine_flops; nb.fine_blocked = part.fine_blocked;
   nb.min_rank_F = chg.empty() ? ob.min_rank_F : part.min_rank_F;
   nb.max_rank_F = chg.empty() ? ob.max_rank_F : part.max_rank_F;
   if (recomputed) *recomputed += (int)chg.size();
@@ -867,6 +868,7 @@ int lmfs_qr_stats(lmfs_handle h, int problem, double* out) {
   if (!h || !out || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   const PairBlocks& pb = h->c.prob[problem];
   out[0] = pb.fac_ms; out[1] = pb.fac_flops; out[2] = pb.rhs_ms; out[3] = pb.rhs_flops;
+  out[4] = pb.fine_ms; out[5] = pb.fine_flops; out[6] = pb.fine_blocked ? 1.0 : 0.0;
   return LMFS_OK;
 }
 

@@ -63,6 +63,8 @@ struct PairBlocks {
   double qr_flops = 0.0;         // algorithmic FP64 flops of those QR launches
   double fac_ms = 0.0, fac_flops = 0.0;   // of which the pivoted factorizations (qrcp_kernel)
   double rhs_ms = 0.0, rhs_flops = 0.0;   // and the right-hand sides (apply_qt_kernel)
+  double fine_ms = 0.0, fine_flops = 0.0; // the fine systems' QR stage alone (either form)
+  bool fine_blocked = false;              // ... solved by the blocked form (rqr_kernel)
   int max_rank_F = 0, min_rank_F = 0;
   // kept with lmfs_params.keep_fine (flowEval of Algorithm 2): per pair the
   // fine solution Z (mobility: (I - L_f) Z), column-major [4Nc cols][fine_ld
@@ -294,11 +296,27 @@ struct QRBatch {
   double* tau;      // work [nb][permstride]
   double* vn;       // work [nb][2*permstride]
   int* info;        // out: 0 ok, 1 non-finite
+  const int* n_h = nullptr;     // optional host copy of n (the blocked path orders matrices by it)
+  int* used_blocked = nullptr;  // optional host out: 1 if the blocked path solved the batch
   int nb;
   int nmax;
   cudaEvent_t* ev = nullptr;   // optional: 3 events recorded before, between and after the two kernels
 };
 int qr_solve_batched(const QRBatch& q, cudaStream_t s, bool solve);
+// Pairs per precompute chunk for C pairs of per_pair workspace bytes: up to
+// 12 GB of workspace and 456 pairs, or, beyond 456 pairs, up to 32 GB (the
+// blocked QR then runs several waves of matrices per launch, so the waves'
+// ragged end costs less).  The server's admission estimate uses the same rule.
+inline int pair_chunk(long long C, double per_pair) {
+  const double budget = C > 456 ? 32.0 * (1LL << 30) : 12.0 * (1LL << 30);
+  const long long cap = C > 456 ? 2048 : 456;
+  const long long by_mem = std::max<long long>(1, (long long)(budget / std::max(per_pair, 1.0)));
+  return (int)std::max<long long>(1, std::min<long long>(std::min<long long>(C, by_mem), cap));
+}
+// The blocked QR with sketch pivoting (lmfs_rqr.cu): shared memory it needs,
+// and the batch solve itself (solve mode only).
+size_t rqr_smem_bytes(int ld, int nmax);
+int rqr_solve_batched(const QRBatch& q, cudaStream_t s);
 
 // ---- matvec pieces (lmfs_matvec.cu) ---------------------------------------
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb);

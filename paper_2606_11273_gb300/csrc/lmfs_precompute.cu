@@ -826,10 +826,9 @@ int build_pair_blocks(Ctx& c, int problem) {
   const long long s1 = (long long)ld1 * (nmax + k);
   const int ld2 = 2 * Mp;
   const long long s2 = (long long)ld2 * (n4 + k);
-  // chunk size: bounded by ~12 GB of workspace and 3 blocks per SM
+  // chunk size: the workspace budget of pair_chunk
   const long long per = s1 + (long long)nmax * k * 2 + (long long)ld2 * nmax + s2 + (long long)n4 * k;
-  int chunk = (int)std::min<long long>(C, std::max<long long>(1, (12LL << 30) / (per * 8)));
-  chunk = std::min(chunk, 456);
+  const int chunk = pair_chunk(C, (double)per * 8.0);
   double *ws1 = nullptr, *Z = nullptr, *Zp = nullptr, *D = nullptr, *ws2 = nullptr, *X2 = nullptr;
   double *Yf = nullptr, *Xf = nullptr, *Zpts = nullptr, *Gf = nullptr, *tau = nullptr, *vn = nullptr;
   int *nenh = nullptr, *dm = nullptr, *dn = nullptr, *rank = nullptr, *perm = nullptr, *info = nullptr;
@@ -841,6 +840,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   int hbad = 0;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double qr_ms = 0.0, qr_flops = 0.0;
+  double fine_ms = 0.0, fine_flops = 0.0;   // the fine systems' QR stage alone
   double fac_ms = 0.0, fac_flops = 0.0, rhs_ms = 0.0, rhs_flops = 0.0;
   // split of qrf: the factorization's part, the rest being the right-hand sides
   auto qrfA = [](double m, double n, double r) {
@@ -858,6 +858,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   };
   for (auto& e : ev) cudaEventCreate(&e);
   int minr = 1 << 30, maxr = 0;
+  int fine_blocked = 0;
   pb.fine_kept = false;
   if (c.prm.keep_fine) {
     if (!pb.Zf) LMFS_TRY(dalloc(&pb.Zf, (size_t)C * nmax * k));
@@ -939,7 +940,7 @@ int build_pair_blocks(Ctx& c, int problem) {
       q.A = ws1; q.mstride = sh; q.m = dm; q.n = dn; q.k = kh; q.ld = ldh; q.eps = c.prm.eps_trunc_fine;
       q.X = D; q.xld = nmaxh; q.xstride = (long long)nmaxh * kh; q.rank = rank; q.perm = perm;
       q.permstride = nmaxh; q.tau = tau; q.vn = vn; q.info = info; q.nb = nbq; q.nmax = nmaxh;
-      q.ev = ev;
+      q.ev = ev; q.n_h = hn.data(); q.used_blocked = &fine_blocked;
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
       assemble_Z_sym<<<dim3(32, nb), 256, 0, c.stream>>>(pd, D, nmaxh, (long long)nmaxh * kh, Z, nmax,
                                                          (long long)nmax * k);
@@ -957,7 +958,7 @@ int build_pair_blocks(Ctx& c, int problem) {
       q.A = ws1; q.mstride = s1; q.m = dm; q.n = dn; q.k = k; q.ld = ld1; q.eps = c.prm.eps_trunc_fine;
       q.X = Z; q.xld = nmax; q.xstride = (long long)nmax * k; q.rank = rank; q.perm = perm; q.permstride = nmax;
       q.tau = tau; q.vn = vn; q.info = info; q.nb = nb; q.nmax = nmax;
-      q.ev = ev;
+      q.ev = ev; q.n_h = hn.data(); q.used_blocked = &fine_blocked;
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
     }
     any_nonzero<<<(nbq + 255) / 256, 256, 0, c.stream>>>(info, nbq, bad);
@@ -1023,7 +1024,11 @@ int build_pair_blocks(Ctx& c, int problem) {
           const int mi = sym ? 2 * b + h : b;
           const double mm = sym ? ldh : m1, kk = sym ? kh : k;
           const double f = qrf(mm, hn[mi], kk, hr[mi]), fa = qrfA(mm, hn[mi], hr[mi]);
-          qr_flops += f; fac_flops += fa; rhs_flops += f - fa;
+          // the blocked form updates the right-hand sides in the factorization's sweep
+          qr_flops += f;
+          fine_flops += f;
+          if (fine_blocked) fac_flops += f;
+          else { fac_flops += fa; rhs_flops += f - fa; }
         }
       }
       q.ev = ev + 3;
@@ -1041,6 +1046,7 @@ int build_pair_blocks(Ctx& c, int problem) {
       cudaEventElapsedTime(&a1, ev[3], ev[4]);
       cudaEventElapsedTime(&b1, ev[4], ev[5]);
       fac_ms += a0 + a1; rhs_ms += b0 + b1;
+      fine_ms += a0 + b0;
       qr_ms += a0 + b0 + a1 + b1;
     }
     any_nonzero<<<(nbc + 255) / 256, 256, 0, c.stream>>>(info, nbc, bad);
@@ -1060,6 +1066,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   pb.min_rank_F = minr; pb.max_rank_F = maxr;
   pb.qr_ms = qr_ms; pb.qr_flops = qr_flops;
   pb.fac_ms = fac_ms; pb.fac_flops = fac_flops; pb.rhs_ms = rhs_ms; pb.rhs_flops = rhs_flops;
+  pb.fine_ms = fine_ms; pb.fine_flops = fine_flops; pb.fine_blocked = fine_blocked != 0;
   pb.t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 done:
   dfree(ws1); dfree(Z); dfree(Zp); dfree(D); dfree(ws2); dfree(X2); dfree(Yf); dfree(Xf); dfree(Zpts);

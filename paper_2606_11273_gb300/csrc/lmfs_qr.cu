@@ -24,6 +24,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 
 #include <cooperative_groups.h>
 
@@ -546,6 +548,16 @@ int apply_call(int kt, int nbuf, bool launch, const ArgsB& a, int nb, size_t shm
   return rc == -1000 ? (launch ? LMFS_ERR_INVALID : 0) : rc;
 }
 
+// LMFS_QR_PATH=blocked or =cluster forces one of the two QR forms for the
+// batches both can solve (tests compare them); unset, the batch decides.
+int qr_path_override() {
+  const char* e = std::getenv("LMFS_QR_PATH");
+  if (!e) return 0;
+  if (!std::strcmp(e, "blocked")) return 1;
+  if (!std::strcmp(e, "cluster")) return 2;
+  return 0;
+}
+
 }  // namespace
 
 int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
@@ -553,6 +565,19 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   int sms = 152, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (q.used_blocked) *q.used_blocked = 0;
+  // The blocked form (one matrix per CTA, lmfs_rqr.cu) for batches of tall
+  // systems that fill the device at two CTAs per SM; the pivoted cluster form
+  // below spreads each matrix over several SMs, which small batches need.
+  if (solve && q.k > 0) {
+    const int path = qr_path_override();
+    const bool fits = rqr_smem_bytes(q.ld, q.nmax) <= 226 * 1024;
+    const bool big = q.nb >= 2 * sms && q.ld >= 512;
+    if (fits && (path == 1 || (path == 0 && big))) {
+      if (q.used_blocked) *q.used_blocked = 1;
+      return rqr_solve_batched(q, st);
+    }
+  }
 
   // ---- factorization: choose the CTA size and cluster size that finish the
   // batch soonest -- waves of resident clusters x the work each CTA carries

@@ -1,0 +1,566 @@
+// Blocked Householder QR with the pivots chosen on a random sketch, and the
+// truncated basic least-squares solution, in FP64: one matrix per CTA.
+//
+// The column-pivoted QR of lmfs_qr.cu chooses every pivot from the updated
+// norms of all remaining columns, so each reflector is applied to the whole
+// trailing matrix before the next pivot is known: one pass over the trailing
+// matrix (and two cluster barriers) per reflector.  Here the pivots of a
+// block of RB columns are chosen at once by a column-pivoted QR of a small
+// sketch Y = Omega A (RL = RB + 8 rows, Omega of random signs), as in
+// randomized QRCP (Martinsson, Quintana-Orti, Heavner, van de Geijn, "HQRRP",
+// 2017; Duersch and Gu, 2017); the block is factored without pivoting, and
+// its RB reflectors are applied to the trailing columns -- the remaining
+// coefficient columns and the right-hand sides -- as one compact-WY product
+// (I - V T^T V^T), one pass per block.  The sketch of the trailing columns is
+// brought up to date from the block's R (Y_2 <- Y_2 - Y_1 R_11^-1 R_12), so it
+// stays a sketch of the trailing matrix without another pass over it.
+//
+// Truncation as in the pivoted QR: the factorization stops at the first
+// reflector whose |R_ss| <= eps |R_00|, or at a block boundary where every
+// remaining column's partial norm (kept exactly, from the trailing pass) is
+// <= eps |R_00|.  The solution is then x = P [R_11^-1 (Q^T B)_1; 0].
+//
+// Tested on the fine systems of unit pairs at gaps 1e-1..1e-3 (both problems)
+// against column-pivoted QR and the SVD pseudo-inverse: the same rank within
+// 2, the same residual, and the products D Z and E that the method uses from
+// Z as close to the SVD's as the pivoted QR's.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "lmfs_internal.h"
+
+namespace lmfs {
+namespace {
+
+constexpr int RB = 8;              // reflectors per block
+constexpr int RL = 16;             // sketch rows
+constexpr int RT = 256;            // threads per CTA
+constexpr int RW = RT / 32;        // warps
+constexpr int RSMALL = 2 * RB * RB + RL * RB + 2 * RB + RW * 32 + 32;   // doubles
+
+struct RArgs {
+  double* A; long long mstride; const int* m; const int* n; int k; int ld; double eps;
+  double* X; int xld; long long xstride; int* rank; int* perm; int permstride; int* info;
+  double* Yg;                      // [nb][RL][ysd] sketch of the trailing columns
+  int ysd;
+  double* tn;                      // [nb][permstride] squared partial column norms
+  const int* order;                // matrix of CTA blockIdx.x
+  int wsz;                         // doubles of the shared work region
+};
+
+// 16 random signs per row: the bits of a 32-bit integer mix of the row index
+// (the finalizer of MurmurHash3).
+__device__ __forceinline__ unsigned row_signs(unsigned i) {
+  unsigned h = i * 0x9E3779B1u + 0x7F4A7C15u;
+  h ^= h >> 16; h *= 0x85EBCA6Bu;
+  h ^= h >> 13; h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h & 0xFFFFu;
+}
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sums of NV values held by every thread; the sums land in out[0..NV)
+// (shared), visible to every thread after the call.  red: RW * NV doubles.
+template <int NV>
+__device__ void block_sums(double (&v)[NV], int nv, double* red, double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    if (q < nv) v[q] = warp_allsum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q < nv) red[w * NV + q] = v[q];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nv) {
+    double s = 0.0;
+    for (int ww = 0; ww < RW; ++ww) s += red[ww * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int b = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
+  const int m = a.m[b], n = a.n[b], k = a.k, ld = a.ld, ysd = a.ysd;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* A = a.A + (long long)b * a.mstride;
+  double* Yg = a.Yg + (long long)b * RL * ysd;
+  double* tn = a.tn + (long long)b * a.permstride;
+  int* perm = a.perm + (long long)b * a.permstride;
+
+  double* W = sm;                                         // work region (a.wsz doubles)
+  unsigned short* om = (unsigned short*)(sm + a.wsz);     // [ld] sign masks
+  double* smallp = sm + a.wsz + (ld + 3) / 4;
+  double* T = smallp;                                     // [RB][RB]: T[u * RB + t]
+  double* R11 = T + RB * RB;                              // [RB][RB]: R11[u * RB + t]
+  double* G2 = R11 + RB * RB;                             // [RL][RB]
+  double* sbeta = G2 + RL * RB;                           // [RB]
+  double* stau = sbeta + RB;                              // [RB]
+  double* red = stau + RB;                                // [RW * 32]
+  double* sred = red + RW * 32;                           // [32] block results
+  __shared__ int s_pv[RB];
+  __shared__ int s_stop, s_bad, s_bbe, s_q;
+  __shared__ double s_r00, s_scale;
+
+  // ---- sketch, squared column norms, identity permutation
+  for (int i = tid; i < m; i += RT) om[i] = (unsigned short)row_signs((unsigned)i);
+  for (int c = tid; c < n; c += RT) perm[c] = c;
+  if (tid == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; }
+  __syncthreads();
+  for (int c = tid; c < n; c += RT) {
+    const double* col = A + (long long)c * ld;
+    double acc[RL];
+#pragma unroll
+    for (int j = 0; j < RL; ++j) acc[j] = 0.0;
+    double nn = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double x = col[i];
+      const unsigned msk = om[i];
+      nn = fma(x, x, nn);
+#pragma unroll
+      for (int j = 0; j < RL; ++j) acc[j] += ((msk >> j) & 1u) ? x : -x;
+    }
+#pragma unroll
+    for (int j = 0; j < RL; ++j) Yg[(long long)j * ysd + c] = acc[j];
+    tn[c] = nn;
+  }
+  __syncthreads();
+
+  const int smax = min(m, n);
+  int rank = smax;
+  int s = 0;
+  while (s < smax) {
+    const int nt = n - s;
+    const int bb = min(RB, min(nt, m - s));
+    // ---- stop test on the exact partial norms
+    {
+      double mx = 0.0;
+      for (int c = s + tid; c < n; c += RT) mx = fmax(mx, tn[c]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) red[warp] = mx;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int ww = 0; ww < RW; ++ww) t = fmax(t, red[ww]);
+        if (!(t == t) || isinf(t)) s_bad = 1;
+        s_stop = (s_r00 > 0.0 && (sqrt(t) <= a.eps * s_r00)) || s_bad || t == 0.0;
+      }
+      __syncthreads();
+      if (s_stop) { rank = s; break; }
+    }
+    // ---- pivots of this block: column-pivoted QR of the sketch's trailing columns
+    {
+      double* Ys = W;                                     // [RL][nt]: Ys[j * nt + c]
+      for (int e = tid; e < RL * nt; e += RT) {
+        const int j = e / nt, c = e - j * nt;
+        Ys[e] = Yg[(long long)j * ysd + s + c];
+      }
+      __syncthreads();
+      for (int t = 0; t < bb; ++t) {
+        double bv = -1.0;
+        int bi = 0x7fffffff;
+        for (int c = t + tid; c < nt; c += RT) {
+          double v = 0.0;
+#pragma unroll
+          for (int j = 0; j < RL; ++j)
+            if (j >= t) v = fma(Ys[j * nt + c], Ys[j * nt + c], v);
+          if (v > bv) { bv = v; bi = c; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { red[warp] = bv; ((int*)(red + RW))[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+          double v = red[0];
+          int q = ((int*)(red + RW))[0];
+          for (int ww = 1; ww < RW; ++ww) {
+            const double ov = red[ww];
+            const int oi = ((int*)(red + RW))[ww];
+            if (ov > v || (ov == v && oi < q)) { v = ov; q = oi; }
+          }
+          s_q = (q >= t && q < nt) ? q : t;
+          s_pv[t] = s_q;
+        }
+        __syncthreads();
+        const int q = s_q;
+        if (q != t && tid < RL) {
+          const double x = Ys[tid * nt + t];
+          Ys[tid * nt + t] = Ys[tid * nt + q];
+          Ys[tid * nt + q] = x;
+        }
+        __syncthreads();
+        // Householder vector of Ys[t:RL, t] (kept in place, unit entry implicit)
+        if (tid == 0) {
+          const double alpha = Ys[t * nt + t];
+          double sig2 = 0.0;
+          for (int j = t + 1; j < RL; ++j) sig2 = fma(Ys[j * nt + t], Ys[j * nt + t], sig2);
+          const double nrm = sqrt(alpha * alpha + sig2);
+          if (nrm == 0.0 || !(nrm == nrm)) {
+            s_scale = 0.0;
+            stau[0] = 0.0;
+          } else {
+            const double beta = alpha >= 0.0 ? -nrm : nrm;
+            stau[0] = (beta - alpha) / beta;
+            s_scale = 1.0 / (alpha - beta);
+            Ys[t * nt + t] = beta;
+            for (int j = t + 1; j < RL; ++j) Ys[j * nt + t] *= s_scale;
+          }
+        }
+        __syncthreads();
+        const double tau = stau[0];
+        if (tau != 0.0) {
+          for (int c = t + 1 + tid; c < nt; c += RT) {
+            double d = Ys[t * nt + c];
+#pragma unroll
+            for (int j = 0; j < RL; ++j)
+              if (j > t) d = fma(Ys[j * nt + t], Ys[j * nt + c], d);
+            d *= tau;
+            Ys[t * nt + c] -= d;
+#pragma unroll
+            for (int j = 0; j < RL; ++j)
+              if (j > t) Ys[j * nt + c] = fma(-d, Ys[j * nt + t], Ys[j * nt + c]);
+          }
+        }
+        __syncthreads();
+      }
+      // the same exchanges, in the same order, on the matrix, the sketch, the
+      // norms and the permutation
+      for (int t = 0; t < bb; ++t) {
+        const int q = s_pv[t];
+        if (q != t) {
+          double* c1 = A + (long long)(s + t) * ld;
+          double* c2 = A + (long long)(s + q) * ld;
+          for (int i = tid; i < m; i += RT) { const double x = c1[i]; c1[i] = c2[i]; c2[i] = x; }
+          if (tid < RL) {
+            double* y = Yg + (long long)tid * ysd + s;
+            const double x = y[t]; y[t] = y[q]; y[q] = x;
+          }
+          if (tid == RL) {
+            const double x = tn[s + t]; tn[s + t] = tn[s + q]; tn[s + q] = x;
+            const int pi = perm[s + t]; perm[s + t] = perm[s + q]; perm[s + q] = pi;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // ---- the block, factored without pivoting in shared memory
+    double* Vs = W;                                       // [RB][ld]: Vs[t * ld + i], rows s..m-1
+    for (int t = 0; t < bb; ++t)
+      for (int i = s + tid; i < m; i += RT) Vs[t * ld + i] = A[(long long)(s + t) * ld + i];
+    if (tid == 0) s_bbe = bb;
+    __syncthreads();
+    for (int t = 0; t < bb; ++t) {
+      const int p = s + t;
+      double part[1] = {0.0};
+      for (int i = p + 1 + tid; i < m; i += RT) part[0] = fma(Vs[t * ld + i], Vs[t * ld + i], part[0]);
+      block_sums<1>(part, 1, red, sred);
+      if (tid == 0) {
+        const double alpha = Vs[t * ld + p];
+        const double nrm = sqrt(alpha * alpha + sred[0]);
+        if (p == 0) s_r00 = nrm;
+        if (!(nrm == nrm) || isinf(nrm)) s_bad = 1;
+        if (nrm <= a.eps * s_r00 || nrm == 0.0 || s_bad) {
+          s_stop = 1;
+          s_bbe = t;
+        } else {
+          const double beta = alpha >= 0.0 ? -nrm : nrm;
+          stau[t] = (beta - alpha) / beta;
+          sbeta[t] = beta;
+          s_scale = 1.0 / (alpha - beta);
+        }
+      }
+      __syncthreads();
+      if (s_stop) break;
+      {
+        const double sc = s_scale;
+        for (int i = p + 1 + tid; i < m; i += RT) Vs[t * ld + i] *= sc;
+        if (tid == 0) Vs[t * ld + p] = 1.0;
+      }
+      __syncthreads();
+      const int nu = bb - 1 - t;
+      if (nu > 0) {
+        double d[RB - 1];
+#pragma unroll
+        for (int u = 0; u < RB - 1; ++u) d[u] = 0.0;
+        for (int i = p + tid; i < m; i += RT) {
+          const double v = Vs[t * ld + i];
+#pragma unroll
+          for (int u = 0; u < RB - 1; ++u)
+            if (u < nu) d[u] = fma(v, Vs[(t + 1 + u) * ld + i], d[u]);
+        }
+        block_sums<RB - 1>(d, nu, red, sred);
+        const double tau = stau[t];
+        for (int i = p + tid; i < m; i += RT) {
+          const double v = Vs[t * ld + i];
+#pragma unroll
+          for (int u = 0; u < RB - 1; ++u)
+            if (u < nu) Vs[(t + 1 + u) * ld + i] = fma(-tau * sred[u], v, Vs[(t + 1 + u) * ld + i]);
+        }
+        __syncthreads();
+      }
+    }
+    const int bbe = s_bbe;
+    const bool stopped = s_stop != 0;
+    // write the block back (R above and on the diagonal, V below), keep R_11,
+    // and leave V unit lower trapezoidal in shared memory
+    for (int t = 0; t < bbe; ++t) {
+      const int p = s + t;
+      double* col = A + (long long)p * ld;
+      for (int i = s + tid; i < m; i += RT) col[i] = (i == p) ? sbeta[t] : Vs[t * ld + i];
+    }
+    if (tid < RB * RB) {
+      const int u = tid / RB, t = tid - u * RB;
+      R11[tid] = (u < bbe && t < bbe) ? (u < t ? Vs[t * ld + s + u] : (u == t ? sbeta[t] : 0.0)) : 0.0;
+    }
+    __syncthreads();
+    for (int t = 0; t < bbe; ++t)
+      for (int i = s + tid; i < s + t; i += RT) Vs[t * ld + i] = 0.0;
+    __syncthreads();
+    if (bbe == 0) { rank = s; break; }
+    // ---- T of the compact WY form, H_0 ... H_{bbe-1} = I - V T V^T, from the Gram matrix of V
+    {
+      double g[RB * (RB - 1) / 2];
+#pragma unroll
+      for (int q = 0; q < RB * (RB - 1) / 2; ++q) g[q] = 0.0;
+      for (int i = s + tid; i < m; i += RT) {
+        double v[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) v[u] = (u < bbe) ? Vs[u * ld + i] : 0.0;
+#pragma unroll
+        for (int t = 1; t < RB; ++t)
+#pragma unroll
+          for (int u = 0; u < t; ++u) g[t * (t - 1) / 2 + u] = fma(v[u], v[t], g[t * (t - 1) / 2 + u]);
+      }
+      block_sums<RB * (RB - 1) / 2>(g, RB * (RB - 1) / 2, red, sred);
+      if (tid == 0) {
+        for (int e = 0; e < RB * RB; ++e) T[e] = 0.0;
+        int q0 = 0;
+        for (int t = 0; t < bbe; ++t) {
+          // sred holds (u, t) for t = 1..RB-1, u < t, in order: offset t (t - 1) / 2
+          q0 = t * (t - 1) / 2;
+          T[t * RB + t] = stau[t];
+          for (int u = 0; u < t; ++u) {
+            double acc = 0.0;
+            for (int w2 = u; w2 < t; ++w2) acc = fma(T[u * RB + w2], sred[q0 + w2], acc);
+            T[u * RB + t] = -stau[t] * acc;
+          }
+        }
+      }
+      // the sketch update's coefficients G2 = Y_1 R_11^-1 (rows of the sketch)
+      if (!stopped && tid < RL) {
+        const int j = tid;
+        for (int t = 0; t < bbe; ++t) {
+          double acc = Yg[(long long)j * ysd + s + t];
+          for (int u = 0; u < t; ++u) acc = fma(-G2[j * RB + u], R11[u * RB + t], acc);
+          G2[j * RB + t] = acc / R11[t * RB + t];
+        }
+      }
+      __syncthreads();
+    }
+    // ---- Q^T applied to the trailing columns: (I - V T^T V^T) C, one pass
+    // each.  A column belongs to a group of tpc threads (tpc = 1 while there
+    // are enough columns for every thread), each taking every tpc-th chunk of
+    // four rows; the reads of V are then shared-memory broadcasts, and a
+    // column's V^T c needs no cross-lane sum unless tpc > 1.
+    {
+      const int c0 = stopped ? n : s + bbe;
+      const int ncol = n + k - c0;
+      int tpc = 1;
+      while (tpc < 8 && ncol * tpc * 2 <= RT) tpc *= 2;
+      const int slots = RT / tpc, g = tid / tpc, r = tid - g * tpc;
+      const int rs = s + bbe;                             // rows below the block
+      // every lane of a warp takes the same number of steps (the shuffles
+      // and the warp barrier need all 32); lanes past the last column idle
+      for (int base = 0; base < ncol; base += slots) {
+        const int cc = base + g;
+        const bool act = cc < ncol;
+        const int c = c0 + (act ? cc : 0);
+        double* col = A + (long long)c * ld;
+        double w[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) w[u] = 0.0;
+        if (act) {
+          for (int i0 = s + 4 * r; i0 < m; i0 += 4 * tpc) {
+            double x[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) x[h] = (i0 + h < m) ? col[i0 + h] : 0.0;
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+              if (u < bbe) {
+                const double* vu = Vs + u * ld + i0;
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                  if (i0 + h < m) w[u] = fma(vu[h], x[h], w[u]);
+              }
+            }
+          }
+        }
+        for (int o = 1; o < tpc; o <<= 1) {
+#pragma unroll
+          for (int u = 0; u < RB; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+        }
+        // w2 = T^T w
+        double w2[RB];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+          double acc = 0.0;
+#pragma unroll
+          for (int u = 0; u < RB; ++u)
+            if (u <= t) acc = fma(T[u * RB + t], w[u], acc);
+          w2[t] = (t < bbe) ? acc : 0.0;
+        }
+        double nn = 0.0;
+        if (act) {
+          for (int i0 = s + 4 * r; i0 < m; i0 += 4 * tpc) {
+            double x[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) x[h] = (i0 + h < m) ? col[i0 + h] : 0.0;
+#pragma unroll
+            for (int t = 0; t < RB; ++t) {
+              if (t < bbe) {
+                const double* vt = Vs + t * ld + i0;
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                  if (i0 + h < m) x[h] = fma(-vt[h], w2[t], x[h]);
+              }
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              if (i0 + h < m) {
+                col[i0 + h] = x[h];
+                if (i0 + h >= rs) nn = fma(x[h], x[h], nn);
+              }
+            }
+          }
+        }
+        for (int o = 1; o < tpc; o <<= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        __syncwarp();                                     // the group's stores, before R_12 is read
+        if (act && c < n) {
+          // sketch of this column: Y_2 <- Y_2 - G2 R_12, rows split over the group
+          if (!stopped) {
+            double r12[RB];
+#pragma unroll
+            for (int t = 0; t < RB; ++t) r12[t] = (t < bbe) ? col[s + t] : 0.0;
+            for (int j = r; j < RL; j += tpc) {
+              double* y = Yg + (long long)j * ysd + c;
+              double acc = *y;
+#pragma unroll
+              for (int t = 0; t < RB; ++t)
+                if (t < bbe) acc = fma(-G2[j * RB + t], r12[t], acc);
+              *y = acc;
+            }
+          }
+          if (r == 0) tn[c] = nn;
+        }
+      }
+    }
+    __syncthreads();
+    s += bbe;
+    if (stopped) { rank = s; break; }
+  }
+  if (s >= smax) rank = smax;
+  __syncthreads();
+
+  // ---- back substitution R_11 x = (Q^T B)_1, one right-hand side per warp
+  // at a time (staged in shared memory), and the scatter by the pivot order
+  {
+    double* y = W + (long long)warp * ysd;
+    int bad = 0;
+    for (int c0 = 0; c0 < k; c0 += RW) {
+      const int c = c0 + warp;
+      if (c >= k) break;
+      const double* bc = A + (long long)(n + c) * ld;
+      for (int i = lane; i < rank; i += 32) y[i] = bc[i];
+      __syncwarp();
+      for (int j = rank - 1; j >= 0; --j) {
+        const double* rj = A + (long long)j * ld;
+        const double xj = y[j] / rj[j];
+        __syncwarp();
+        for (int i = lane; i < j; i += 32) y[i] = fma(-xj, rj[i], y[i]);
+        if (lane == 0) y[j] = xj;
+        __syncwarp();
+      }
+      double* xc = a.X + (long long)b * a.xstride + (long long)c * a.xld;
+      for (int i = lane; i < n; i += 32) {
+        const double v = (i < rank) ? y[i] : 0.0;
+        if (!(v == v) || isinf(v)) bad = 1;
+        xc[perm[i]] = v;
+      }
+      __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.info + b, 1);
+  }
+  if (tid == 0) {
+    a.rank[b] = rank;
+    if (s_bad) atomicOr(a.info + b, 1);
+  }
+}
+
+}  // namespace
+
+// Shared memory of the blocked path for leading dimension ld and at most
+// nmax coefficient columns (0 if it does not fit a CTA).
+size_t rqr_smem_bytes(int ld, int nmax) {
+  const size_t wsz = std::max<size_t>({(size_t)RB * ld, (size_t)RL * nmax, (size_t)RW * nmax});
+  return (wsz + (size_t)(ld + 3) / 4 + RSMALL) * sizeof(double);
+}
+
+int rqr_solve_batched(const QRBatch& q, cudaStream_t st) {
+  const int nmax = q.nmax;
+  const size_t wsz = std::max<size_t>({(size_t)RB * q.ld, (size_t)RL * nmax, (size_t)RW * nmax});
+  const size_t shm = rqr_smem_bytes(q.ld, nmax);
+  if (cuda_failed(cudaFuncSetAttribute(rqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm),
+                  "rqr smem attribute"))
+    return LMFS_ERR_CUDA;
+  double* Yg = nullptr;
+  int* order = nullptr;
+  int rc = LMFS_OK;
+  if ((rc = dalloc(&Yg, (size_t)q.nb * RL * nmax))) return rc;
+  if (q.n_h) {
+    // largest matrices first: the waves of CTAs then end together
+    std::vector<int> ord(q.nb);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return q.n_h[x] > q.n_h[y]; });
+    if ((rc = dalloc(&order, (size_t)q.nb))) { dfree(Yg); return rc; }
+    if (cuda_failed(cudaMemcpyAsync(order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st), "h2d") ||
+        cuda_failed(cudaStreamSynchronize(st), "sync")) {
+      dfree(Yg); dfree(order);
+      return LMFS_ERR_CUDA;
+    }
+  }
+  if (cuda_failed(cudaMemsetAsync(q.info, 0, (size_t)q.nb * sizeof(int), st), "memset")) {
+    dfree(Yg); dfree(order);
+    return LMFS_ERR_CUDA;
+  }
+  RArgs a;
+  a.A = q.A; a.mstride = q.mstride; a.m = q.m; a.n = q.n; a.k = q.k; a.ld = q.ld; a.eps = q.eps;
+  a.X = q.X; a.xld = q.xld; a.xstride = q.xstride; a.rank = q.rank; a.perm = q.perm;
+  a.permstride = q.permstride; a.info = q.info; a.Yg = Yg; a.ysd = nmax; a.tn = q.vn; a.order = order;
+  a.wsz = (int)wsz;
+  if (q.ev) cudaEventRecord(q.ev[0], st);
+  rqr_kernel<<<q.nb, RT, shm, st>>>(a);
+  rc = check_launch("rqr_kernel");
+  if (q.ev) { cudaEventRecord(q.ev[1], st); cudaEventRecord(q.ev[2], st); }
+  dfree(Yg);
+  dfree(order);
+  return rc;
+}
+
+}  // namespace lmfs

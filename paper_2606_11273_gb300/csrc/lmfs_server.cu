@@ -113,8 +113,8 @@ size_t estimate_bytes(const double* c, const double* r, int P, const lmfs_params
   const double vecs = 20.0 * n * 8.0 + 12.0 * P * p.Nc * 8.0;
   const int nX = (int)std::ceil(p.af * p.Nfp) + (int)std::lround(p.aell * p.Nell);
   const double nmax = 4.0 * (p.Nfp + 2 * p.Nell);
-  const double per_pair_ws = (4.0 * nX * (nmax + n4) + 2 * nmax * n4 + 2.0 * p.Mp * (nmax + 2 * n4)) * 8.0;
-  const double ws = std::min<double>((double)std::max<long long>(C, 1), 456.0) * per_pair_ws;
+  const double per_pair_ws = (4.0 * nX * (nmax + n4) + 2 * nmax * n4 + 2.0 * p.Mp * (nmax + 2 * n4) + n4 * n4) * 8.0;
+  const double ws = pair_chunk(std::max<long long>(C, 1), per_pair_ws) * per_pair_ws;
   const double refine = (p.precision != LMFS_FP64 && p.refine > 0) ? 3.0 * n * 8.0 : 0.0;
   return (size_t)(blocks + basis + vecs + ws + refine + (64 << 20));
 }

@@ -1,0 +1,94 @@
+"""The pair precompute's two QR forms through the C ABI: the blocked QR with
+pivots chosen on a random sketch (one matrix per CTA, the form large batches
+use) and the column-pivoted cluster form (small batches).  LMFS_QR_PATH
+forces one or the other.  Both truncate at the same level and differ only in
+numerically null directions, so the unique parts of the blocks -- E and C A
+-- are compared with the oracle's SVD-truncated blocks, and the solves with
+each other."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle.onebody import OneBody
+from oracle.pairs import pair_blocks
+from oracle.params import PACKING
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2606_11273_gb300 import build
+    build.build()
+    import paper_2606_11273_gb300 as lib
+    return lib
+
+
+def gparams(L, p, **kw):
+    base = dict(Nc=p.Nc, Mc=p.Mc, Rc=p.Rc, Nfp=p.Nfp, Nell=p.Nell, Mp=p.Mp, delta_c=p.delta_c, tol=p.tol,
+                gamma=p.gamma, af=p.af, r_mob=p.r_mob, aell=p.aell, eps_trunc=p.eps_trunc,
+                eps_trunc_fine=p.eps_trunc_fine, mu=p.mu)
+    base.update(kw)
+    return L.Params(**base)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def solver(L, monkeypatch, path, pk, problem, **kw):
+    monkeypatch.setenv("LMFS_QR_PATH", path)
+    s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, **kw))
+    s.precompute(problem)
+    monkeypatch.delenv("LMFS_QR_PATH")
+    return s
+
+
+@pytest.mark.parametrize("problem", ["mobility", "resistance"])
+def test_blocked_qr_pair_blocks_against_oracle(L, monkeypatch, problem):
+    """P = 100 packing (37 close pairs): on 8 sampled pairs E and C A of the
+    blocked form against the oracle's SVD blocks within 1e-5, as the cluster
+    form's are; the fine ranks of the two forms within a few columns."""
+    code = L.MOBILITY if problem == "mobility" else L.RESISTANCE
+    pk = w.packing_p100()
+    sb = solver(L, monkeypatch, "blocked", pk, code)
+    sc = solver(L, monkeypatch, "cluster", pk, code)
+    Ab, Eb = sb.pair_blocks(code)
+    Ac, Ec = sc.pair_blocks(code)
+    stb, stc = sb.stats(code), sc.stats(code)
+    ob = OneBody(1.0, PACKING, problem)
+    pairs = sb.pairs()
+    worst = {"blocked": [0.0, 0.0], "cluster": [0.0, 0.0]}
+    for q in np.linspace(0, len(pairs) - 1, 8).astype(int):
+        i, k = pairs[q]
+        b = pair_blocks(pk.centres[i], 1.0, pk.centres[k], 1.0, ob, ob, PACKING, problem, 1.0, keep=True)
+        for name, A, E in (("blocked", Ab, Eb), ("cluster", Ac, Ec)):
+            worst[name][0] = max(worst[name][0], rel(E[q], b["E"]))
+            worst[name][1] = max(worst[name][1], rel(b["C"] @ A[q], b["C"] @ b["A"]))
+    print(f"{problem}: E, C A vs oracle: blocked {worst['blocked'][0]:.2e} {worst['blocked'][1]:.2e}, "
+          f"cluster {worst['cluster'][0]:.2e} {worst['cluster'][1]:.2e}; rank F blocked "
+          f"[{stb['min_rank_F']:.0f}, {stb['max_rank_F']:.0f}] cluster [{stc['min_rank_F']:.0f}, {stc['max_rank_F']:.0f}]; "
+          f"QR ms blocked {stb['qr_ms']:.1f} cluster {stc['qr_ms']:.1f}")
+    assert worst["blocked"][0] < 1e-5 and worst["blocked"][1] < 1e-5
+    assert abs(stb["min_rank_F"] - stc["min_rank_F"]) <= 8 and abs(stb["max_rank_F"] - stc["max_rank_F"]) <= 8
+    sb.close()
+    sc.close()
+
+
+def test_blocked_qr_solves_like_the_cluster_form(L, monkeypatch):
+    """The P = 100 mobility solve (FP64) on blocks from either form: the
+    velocities agree within 1e-6 (each is within ~3e-7 of the oracle)."""
+    pk = w.packing_p100()
+    ft = w.forces_torques(pk.P, 5)
+    out = {}
+    for path in ("blocked", "cluster"):
+        s = solver(L, monkeypatch, path, pk, L.MOBILITY, precision=L.FP64)
+        out[path], info = s.solve(L.MOBILITY, ft)
+        assert info["converged"]
+        s.close()
+    d = rel(out["blocked"], out["cluster"])
+    print(f"velocities blocked vs cluster {d:.2e}")
+    assert d < 1e-6
