@@ -567,12 +567,14 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (q.used_blocked) *q.used_blocked = 0;
   // The blocked form (one matrix per CTA, lmfs_rqr.cu) for batches of tall
-  // systems that fill the device at two CTAs per SM; the pivoted cluster form
-  // below spreads each matrix over several SMs, which small batches need.
+  // systems that fill at least four waves of two CTAs per SM (measured on the
+  // P = 10^4 fine systems: 2.1 waves per launch 10.2 s against the cluster
+  // form's 9.4 s, 5.7 waves 8.8 s); the pivoted cluster form below spreads
+  // each matrix over several SMs, which smaller batches need.
   if (solve && q.k > 0) {
     const int path = qr_path_override();
     const bool fits = rqr_smem_bytes(q.ld, q.nmax) <= 226 * 1024;
-    const bool big = q.nb >= 2 * sms && q.ld >= 512;
+    const bool big = q.nb >= 8 * sms && q.ld >= 512;
     if (fits && (path == 1 || (path == 0 && big))) {
       if (q.used_blocked) *q.used_blocked = 1;
       return rqr_solve_batched(q, st);
