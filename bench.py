@@ -98,11 +98,11 @@ class Clocks:
 
 # DRAM traffic of the blocked QR kernel (rqr_kernel) per fine half system:
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of its launch
-# on the 398 fine half systems of `bench.py --profile-case qr_mid` (P = 160,
-# area fraction 0.65), divided by 398.  Valid only for the kernel source it was
+# on the 398 fine half systems of `LMFS_QR_PATH=blocked bench.py --profile-case
+# qr_mid` (P = 160, area fraction 0.65), divided by 398.  Valid only for the kernel source it was
 # taken on: reported as null once lmfs_rqr.cu changes.
-RQR_TRAFFIC_PER_MATRIX = (74373963776 + 38127273728) / 398.0
-RQR_TRAFFIC_SRC_SHA256 = "8edb5bebabe92e2f812ff735fa64de0be09ba4bec68747b10c712de6c0dbb7ec"
+RQR_TRAFFIC_PER_MATRIX = (74.73e9 + 38.24e9) / 398.0
+RQR_TRAFFIC_SRC_SHA256 = "a22c720c89f7e0840e0a59f531118cfdea43f6fd1f5c7644a06d3a75aab6a40a"
 
 
 def rqr_traffic_per_matrix():

@@ -47,7 +47,6 @@ struct RArgs {
   double* X; int xld; long long xstride; int* rank; int* perm; int permstride; int* info;
   double* Yg;                      // [nb][RL][ysd] sketch of the trailing columns
   int ysd;
-  double* tn;                      // [nb][permstride] squared partial column norms
   const int* order;                // matrix of CTA blockIdx.x
   int wsz;                         // doubles of the shared work region
 };
@@ -66,6 +65,13 @@ __device__ __forceinline__ double warp_allsum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Warp maximum of v; lane 0 stores it at red[warp] (as an integer).
+__device__ __forceinline__ void warp_max_to(unsigned long long v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) ((unsigned long long*)red)[threadIdx.x >> 5] = v;
 }
 
 // Block sums of NV values held by every thread; the sums land in out[0..NV)
@@ -97,7 +103,6 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* A = a.A + (long long)b * a.mstride;
   double* Yg = a.Yg + (long long)b * RL * ysd;
-  double* tn = a.tn + (long long)b * a.permstride;
   int* perm = a.perm + (long long)b * a.permstride;
 
   double* W = sm;                                         // work region (a.wsz doubles)
@@ -112,13 +117,17 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   double* sred = red + RW * 32;                           // [32] block results
   __shared__ int s_pv[RB];
   __shared__ int s_stop, s_bad, s_bbe, s_q;
-  __shared__ double s_r00, s_scale;
+  __shared__ double s_r00, s_scale, s_thr2;
 
   // ---- sketch, squared column norms, identity permutation
   for (int i = tid; i < m; i += RT) om[i] = (unsigned short)row_signs((unsigned)i);
   for (int c = tid; c < n; c += RT) perm[c] = c;
-  if (tid == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; }
+  if (tid == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; s_thr2 = 0.0; }
   __syncthreads();
+  // squared partial norms are >= 0, so their bit patterns order as integers:
+  // the block maximum of the norms below the current block is kept without
+  // FP64 instructions (nmx per thread, then per warp in red)
+  unsigned long long nmx = 0ull;
   for (int c = tid; c < n; c += RT) {
     const double* col = A + (long long)c * ld;
     double acc[RL];
@@ -134,8 +143,9 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     }
 #pragma unroll
     for (int j = 0; j < RL; ++j) Yg[(long long)j * ysd + c] = acc[j];
-    tn[c] = nn;
+    nmx = max(nmx, (unsigned long long)__double_as_longlong(nn));
   }
+  warp_max_to(nmx, red);
   __syncthreads();
 
   const int smax = min(m, n);
@@ -144,19 +154,15 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   while (s < smax) {
     const int nt = n - s;
     const int bb = min(RB, min(nt, m - s));
-    // ---- stop test on the exact partial norms
+    // ---- stop test on the exact partial norms (their maximum from the last
+    // pass; a NaN or infinity has the largest bit patterns)
     {
-      double mx = 0.0;
-      for (int c = s + tid; c < n; c += RT) mx = fmax(mx, tn[c]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) red[warp] = mx;
-      __syncthreads();
       if (tid == 0) {
-        double t = 0.0;
-        for (int ww = 0; ww < RW; ++ww) t = fmax(t, red[ww]);
-        if (!(t == t) || isinf(t)) s_bad = 1;
-        s_stop = (s_r00 > 0.0 && (sqrt(t) <= a.eps * s_r00)) || s_bad || t == 0.0;
+        const unsigned long long* redu = (const unsigned long long*)red;
+        unsigned long long t = 0ull;
+        for (int ww = 0; ww < RW; ++ww) t = max(t, redu[ww]);
+        if (t >= 0x7FF0000000000000ull) s_bad = 1;
+        s_stop = (s_r00 > 0.0 && t <= (unsigned long long)__double_as_longlong(s_thr2)) || s_bad || t == 0ull;
       }
       __syncthreads();
       if (s_stop) { rank = s; break; }
@@ -240,8 +246,8 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
         }
         __syncthreads();
       }
-      // the same exchanges, in the same order, on the matrix, the sketch, the
-      // norms and the permutation
+      // the same exchanges, in the same order, on the matrix, the sketch and
+      // the permutation
       for (int t = 0; t < bb; ++t) {
         const int q = s_pv[t];
         if (q != t) {
@@ -253,7 +259,6 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
             const double x = y[t]; y[t] = y[q]; y[q] = x;
           }
           if (tid == RL) {
-            const double x = tn[s + t]; tn[s + t] = tn[s + q]; tn[s + q] = x;
             const int pi = perm[s + t]; perm[s + t] = perm[s + q]; perm[s + q] = pi;
           }
         }
@@ -274,7 +279,10 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
       if (tid == 0) {
         const double alpha = Vs[t * ld + p];
         const double nrm = sqrt(alpha * alpha + sred[0]);
-        if (p == 0) s_r00 = nrm;
+        if (p == 0) {
+          s_r00 = nrm;
+          s_thr2 = (a.eps * nrm) * (a.eps * nrm);
+        }
         if (!(nrm == nrm) || isinf(nrm)) s_bad = 1;
         if (nrm <= a.eps * s_r00 || nrm == 0.0 || s_bad) {
           s_stop = 1;
@@ -382,6 +390,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     {
       const int c0 = stopped ? n : s + bbe;
       const int ncol = n + k - c0;
+      nmx = 0ull;
       int tpc = 1;
       while (tpc < 8 && ncol * tpc * 2 <= RT) tpc *= 2;
       const int slots = RT / tpc, g = tid / tpc, r = tid - g * tpc;
@@ -397,10 +406,15 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
 #pragma unroll
         for (int u = 0; u < RB; ++u) w[u] = 0.0;
         if (act) {
-          for (int i0 = s + 4 * r; i0 < m; i0 += 4 * tpc) {
-            double x[4];
+          // the next chunk's loads are issued before this chunk's FMAs
+          double x[4], xn[4];
+          int i0 = s + 4 * r;
 #pragma unroll
-            for (int h = 0; h < 4; ++h) x[h] = (i0 + h < m) ? col[i0 + h] : 0.0;
+          for (int h = 0; h < 4; ++h) x[h] = (i0 + h < m) ? col[i0 + h] : 0.0;
+          for (; i0 < m; i0 += 4 * tpc) {
+            const int i1 = i0 + 4 * tpc;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) xn[h] = (i1 + h < m) ? col[i1 + h] : 0.0;
 #pragma unroll
             for (int u = 0; u < RB; ++u) {
               if (u < bbe) {
@@ -410,6 +424,8 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
                   if (i0 + h < m) w[u] = fma(vu[h], x[h], w[u]);
               }
             }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) x[h] = xn[h];
           }
         }
         for (int o = 1; o < tpc; o <<= 1) {
@@ -428,10 +444,17 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
         }
         double nn = 0.0;
         if (act) {
-          for (int i0 = s + 4 * r; i0 < m; i0 += 4 * tpc) {
+          double xn[4];
+          int i0 = s + 4 * r;
+#pragma unroll
+          for (int h = 0; h < 4; ++h) xn[h] = (i0 + h < m) ? col[i0 + h] : 0.0;
+          for (; i0 < m; i0 += 4 * tpc) {
             double x[4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) x[h] = (i0 + h < m) ? col[i0 + h] : 0.0;
+            for (int h = 0; h < 4; ++h) x[h] = xn[h];
+            const int i1 = i0 + 4 * tpc;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) xn[h] = (i1 + h < m) ? col[i1 + h] : 0.0;
 #pragma unroll
             for (int t = 0; t < RB; ++t) {
               if (t < bbe) {
@@ -467,10 +490,11 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
               *y = acc;
             }
           }
-          if (r == 0) tn[c] = nn;
+          nmx = max(nmx, (unsigned long long)__double_as_longlong(nn));
         }
       }
     }
+    warp_max_to(nmx, red);
     __syncthreads();
     s += bbe;
     if (stopped) { rank = s; break; }
@@ -478,30 +502,63 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   if (s >= smax) rank = smax;
   __syncthreads();
 
-  // ---- back substitution R_11 x = (Q^T B)_1, one right-hand side per warp
-  // at a time (staged in shared memory), and the scatter by the pivot order
+  // ---- back substitution R_11 x = (Q^T B)_1 for RW right-hand sides at a
+  // time, one per warp (in shared memory); R's columns are staged chunk by
+  // chunk in shared memory for all warps, with the reciprocals of its
+  // diagonal, so the chain of each solve waits on neither global memory nor a
+  // division; then the scatter by the pivot order
   {
-    double* y = W + (long long)warp * ysd;
+    const int rpad = (rank + 1) & ~1;
+    double* y = W + (long long)warp * ysd;                // RW * ysd doubles
+    double* rinv = W + (long long)RW * ysd;               // [rank]
+    double* Rs = rinv + rpad;                             // the rest of the work region
+    const int cap = a.wsz - RW * ysd - rpad;              // >= 7 nmax >= rank (wsz >= RL nmax)
+    for (int j = tid; j < rank; j += RT) rinv[j] = 1.0 / A[(long long)j * ld + j];
     int bad = 0;
     for (int c0 = 0; c0 < k; c0 += RW) {
       const int c = c0 + warp;
-      if (c >= k) break;
-      const double* bc = A + (long long)(n + c) * ld;
-      for (int i = lane; i < rank; i += 32) y[i] = bc[i];
-      __syncwarp();
-      for (int j = rank - 1; j >= 0; --j) {
-        const double* rj = A + (long long)j * ld;
-        const double xj = y[j] / rj[j];
-        __syncwarp();
-        for (int i = lane; i < j; i += 32) y[i] = fma(-xj, rj[i], y[i]);
-        if (lane == 0) y[j] = xj;
-        __syncwarp();
+      const bool act = c < k;
+      if (act) {
+        const double* bc = A + (long long)(n + c) * ld;
+        for (int i = lane; i < rank; i += 32) y[i] = bc[i];
       }
-      double* xc = a.X + (long long)b * a.xstride + (long long)c * a.xld;
-      for (int i = lane; i < n; i += 32) {
-        const double v = (i < rank) ? y[i] : 0.0;
-        if (!(v == v) || isinf(v)) bad = 1;
-        xc[perm[i]] = v;
+      int j = rank - 1;
+      while (j >= 0) {
+        // columns j, j - 1, ..., j - ch + 1, rows above the diagonal
+        int ch = 0, used = 0;
+        while (j - ch >= 0 && used + (j - ch) <= cap) { used += j - ch; ++ch; }
+        __syncthreads();                                  // the previous chunk is consumed
+        {
+          int off = 0;
+          for (int q = 0; q < ch; ++q) {
+            const int jj = j - q;
+            const double* rc = A + (long long)jj * ld;
+            for (int i = tid; i < jj; i += RT) Rs[off + i] = rc[i];
+            off += jj;
+          }
+        }
+        __syncthreads();
+        if (act) {
+          int off = 0;
+          for (int q = 0; q < ch; ++q) {
+            const int jj = j - q;
+            const double xj = y[jj] * rinv[jj];
+            __syncwarp();
+            for (int i = lane; i < jj; i += 32) y[i] = fma(-xj, Rs[off + i], y[i]);
+            if (lane == 0) y[jj] = xj;
+            __syncwarp();
+            off += jj;
+          }
+        }
+        j -= ch;
+      }
+      if (act) {
+        double* xc = a.X + (long long)b * a.xstride + (long long)c * a.xld;
+        for (int i = lane; i < n; i += 32) {
+          const double v = (i < rank) ? y[i] : 0.0;
+          if (!(v == v) || isinf(v)) bad = 1;
+          xc[perm[i]] = v;
+        }
       }
       __syncwarp();
     }
@@ -549,10 +606,10 @@ int rqr_solve_batched(const QRBatch& q, cudaStream_t st) {
     dfree(Yg); dfree(order);
     return LMFS_ERR_CUDA;
   }
-  RArgs a;
+  RArgs a{};
   a.A = q.A; a.mstride = q.mstride; a.m = q.m; a.n = q.n; a.k = q.k; a.ld = q.ld; a.eps = q.eps;
   a.X = q.X; a.xld = q.xld; a.xstride = q.xstride; a.rank = q.rank; a.perm = q.perm;
-  a.permstride = q.permstride; a.info = q.info; a.Yg = Yg; a.ysd = nmax; a.tn = q.vn; a.order = order;
+  a.permstride = q.permstride; a.info = q.info; a.Yg = Yg; a.ysd = nmax; a.order = order;
   a.wsz = (int)wsz;
   if (q.ev) cudaEventRecord(q.ev[0], st);
   rqr_kernel<<<q.nb, RT, shm, st>>>(a);
