@@ -306,12 +306,17 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t s, bool solve);
 // Pairs per precompute chunk for C pairs of per_pair workspace bytes: up to
 // 12 GB of workspace and 456 pairs, or, beyond 456 pairs, up to 32 GB (the
 // blocked QR then runs several waves of matrices per launch, so the waves'
-// ragged end costs less).  The server's admission estimate uses the same rule.
+// ragged end costs less), split into chunks of equal size.  The server's
+// admission estimate uses the same rule.
 inline int pair_chunk(long long C, double per_pair) {
   const double budget = C > 456 ? 32.0 * (1LL << 30) : 12.0 * (1LL << 30);
   const long long cap = C > 456 ? 2048 : 456;
   const long long by_mem = std::max<long long>(1, (long long)(budget / std::max(per_pair, 1.0)));
-  return (int)std::max<long long>(1, std::min<long long>(std::min<long long>(C, by_mem), cap));
+  const long long lim = std::max<long long>(1, std::min<long long>(std::min<long long>(C, by_mem), cap));
+  // chunks of equal size (no small last chunk, whose QR batch would leave
+  // most of the device idle or fall back to the form for small batches)
+  const long long nchunk = (std::max<long long>(C, 1) + lim - 1) / lim;
+  return (int)((std::max<long long>(C, 1) + nchunk - 1) / nchunk);
 }
 // The blocked QR with sketch pivoting (lmfs_rqr.cu): shared memory it needs,
 // and the batch solve itself (solve mode only).

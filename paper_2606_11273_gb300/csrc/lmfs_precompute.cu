@@ -1032,13 +1032,17 @@ int build_pair_blocks(Ctx& c, int problem) {
         }
       }
       q.ev = ev + 3;
+      int pea_blocked = 0;
+      q.used_blocked = &pea_blocked;
       if ((rc = qr_solve_batched(q, c.stream, true))) goto done;
       if (cuda_failed(cudaMemcpyAsync(hr2.data(), rank, nbc * sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h") ||
           cuda_failed(cudaStreamSynchronize(c.stream), "sync")) { rc = LMFS_ERR_CUDA; goto done; }
       for (int b = 0; b < nbc; ++b) {
         const double mm = symC ? Mp : 2 * Mp, nn = symC ? 2 * Nc : n4, kk = symC ? 2 * Nc : k;
         const double f = qrf(mm, nn, kk, hr2[b]), fa = qrfA(mm, nn, hr2[b]);
-        qr_flops += f; fac_flops += fa; rhs_flops += f - fa;
+        qr_flops += f;
+        if (pea_blocked) fac_flops += f;
+        else { fac_flops += fa; rhs_flops += f - fa; }
       }
       float a0 = 0, a1 = 0, b0 = 0, b1 = 0;
       cudaEventElapsedTime(&a0, ev[0], ev[1]);

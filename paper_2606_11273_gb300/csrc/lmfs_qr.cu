@@ -566,15 +566,16 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (q.used_blocked) *q.used_blocked = 0;
-  // The blocked form (one matrix per CTA, lmfs_rqr.cu) for batches of tall
-  // systems that fill at least four waves of two CTAs per SM (measured on the
-  // P = 10^4 fine systems: 2.1 waves per launch 10.2 s against the cluster
-  // form's 9.4 s, 5.7 waves 8.8 s); the pivoted cluster form below spreads
-  // each matrix over several SMs, which smaller batches need.
+  // The blocked form (one matrix per CTA, lmfs_rqr.cu) for batches that fill
+  // at least four waves of two CTAs per SM (measured on the P = 10^4 fine
+  // systems: 2.1 waves per launch 10.2 s against the cluster form's 9.4 s,
+  // 5.7 waves 8.8 s; on its 1746 peanut systems of 200 rows 46 ms against
+  // 67 ms per launch); the pivoted cluster form below spreads each matrix over
+  // several SMs, which smaller batches need.
   if (solve && q.k > 0) {
     const int path = qr_path_override();
     const bool fits = rqr_smem_bytes(q.ld, q.nmax) <= 226 * 1024;
-    const bool big = q.nb >= 8 * sms && q.ld >= 512;
+    const bool big = q.nb >= 8 * sms && q.ld >= 128;
     if (fits && (path == 1 || (path == 0 && big))) {
       if (q.used_blocked) *q.used_blocked = 1;
       return rqr_solve_batched(q, st);
