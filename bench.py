@@ -589,9 +589,9 @@ def run_ours(args):
                                       "in the measured peaks)",
                          "kernel_ms_per_step": fine_ms, "share_of_step": fine_ms / (t_ms / args.steps)},
             "qr_all_stages": {"factor_ms": fac_ms, "factor_tflops": fac_tf, "rhs_ms": rhs_ms, "rhs_tflops": rhs_tf,
-                              "note": "all pair QR launches of a step: the fine systems (blocked form: counted as "
-                                      "factorization) and the peanut systems (pivoted cluster form, "
-                                      "qrcp_kernel + apply_qt_kernel)"},
+                              "note": "all pair QR launches of a step, fine and peanut systems: the blocked form "
+                                      "(rqr_kernel, launches of >= 1216 systems; counted as factorization) or the "
+                                      "pivoted cluster form (qrcp_kernel + apply_qt_kernel)"},
             "p100": side,
             "stokeslet_tile_kernel": {**stk, "kernel": "far32_lean_kernel (LMFS_FP32_FAST)", "flops_per_pair": 17,
                                       "achieved_tflops_17": stk["gpair_per_s"] * 17 / 1e3,
