@@ -357,6 +357,7 @@ def p100_side(L, torch, stream, local, n=10):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / n
     v = out_d.cpu().numpy()
+    tune = tune_summary(s.tune_report())
     s.close()
     t0 = time.perf_counter()
     ref, oinfo = oracle_solve(pk, ft)
@@ -364,7 +365,7 @@ def p100_side(L, torch, stream, local, n=10):
     return {"workload": "p100_phi040_mobility", "P": pk.P, "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
             "gmres_iters": info["iters"], "refine_rounds": info["refine_rounds"], "fp64_relres": info["relres"],
             "velocity_err_vs_oracle": float(np.linalg.norm(v - ref) / np.linalg.norm(ref)),
-            "oracle_solve_s": t_or, "oracle_gmres_iters": oinfo["iters"]}
+            "oracle_solve_s": t_or, "oracle_gmres_iters": oinfo["iters"], "autotune": tune}
 
 
 def serving_side(L, n=24, pmax=600, slots=8, seed=0):
@@ -539,6 +540,7 @@ def run_ours(args):
                 "median_disk": float(np.median(res_disk)), "m_eval": 144, "eval_s": time.perf_counter() - t0,
                 "definition": "max |u - g| over 144 new nodes per boundary / max |g| (u: two-body flow with each "
                               "pair's fine sources; g: v + omega (x - c)^perp)"}
+        tune = tune_summary(s.tune_report())
         checks = oracle_checks(L, torch, s, pk, ft)
         dyn = dynamic_side(L, s, pk, ft, pre_ms)
         s.close()
@@ -573,6 +575,7 @@ def run_ours(args):
             "err_vs_oracle": checks,
             "boundary_residual": flow,
             "dynamic_geometry": dyn,
+            "autotune": tune,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu",
@@ -611,6 +614,24 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return result
+
+
+def tune_summary(rows):
+    """Per (kernel, precision): candidates timed, the occupancy model's shape
+    and time, the chosen shape and time (the handle's first solve tunes)."""
+    out = {}
+    for r in rows:
+        key = f"{r['kind']}_{'fp64' if r['precision'] == 0 else 'mixed'}"
+        g = out.setdefault(key, {"candidates": 0})
+        g["candidates"] += 1
+        if r["model"]:
+            g["model"] = [r["p1"], r["p2"], r["ms"]]
+        if r["chosen"]:
+            g["chosen"] = [r["p1"], r["p2"], r["ms"]]
+    for g in out.values():
+        if "model" in g and "chosen" in g and g["chosen"][2] > 0:
+            g["speedup_vs_model"] = g["model"][2] / g["chosen"][2]
+    return out or None
 
 
 def dynamic_side(L, s, pk, ft, pre_ms):

@@ -273,6 +273,23 @@ int lmfs_qr_stats(lmfs_handle h, int problem, double* out);
  * Synchronizes the handle's stream. */
 int lmfs_flow_boundary(lmfs_handle h, int problem, int m_eval, double* u_dev, double* res_disk, double* rel);
 
+/* The matvec autotuner's measurements on this handle.  Before the first GMRES
+ * iteration of each precision is captured as a CUDA graph, the handle times
+ * (CUDA events on its stream, one untimed and one timed run each, on the
+ * solve's own right-hand side as input) the candidate launch shapes of the
+ * near-field kernel -- target split Y in {1, 2, 4} x source groups G in
+ * {1, 2, 4, 8, 16}, within the kernel's limits -- and, for the all-pairs far
+ * field, the source splits 1, 2, 4, .. that its partial buffer allows, and
+ * keeps the fastest; the choice is cached per size class for the process
+ * (later handles of that class reuse it without timing).  Rows of out (HOST,
+ * 7 doubles each, up to cap rows): {kind (0 near kernel, 1 far field),
+ * precision, first parameter (Y or split), second (G or source disks per
+ * chunk), ms, 1 if chosen, 1 if the occupancy model's choice}; *nrows = the
+ * number of rows the handle holds.  Results
+ * with different shapes differ by rounding (the order of partial sums).  No
+ * counterpart in the paper. */
+int lmfs_tune_report(lmfs_handle h, double* out, int cap, int* nrows);
+
 /* Diagnostics of the last solve on the device: the GMRES solution mu
  * (DEVICE [P][Mc][2] copy destination) for parity checks. */
 int lmfs_get_solution(lmfs_handle h, double* mu_dev);

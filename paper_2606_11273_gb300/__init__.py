@@ -164,6 +164,17 @@ class Solver:
                                                ctypes.byref(rel)))
         return res, rel.value
 
+    def tune_report(self):
+        """The matvec autotuner's rows on this handle: dicts of kind ("near" or
+        "far"), precision, the two shape parameters, ms, chosen and model (the
+        occupancy model's choice)."""
+        n = ctypes.c_int()
+        _lib.check(self.lib.lmfs_tune_report(self.h, None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 7))
+        _lib.check(self.lib.lmfs_tune_report(self.h, _ptr(out), n.value, ctypes.byref(n)))
+        return [{"kind": "near" if r[0] == 0 else "far", "precision": int(r[1]), "p1": int(r[2]), "p2": int(r[3]),
+                 "ms": float(r[4]), "chosen": bool(r[5]), "model": bool(r[6])} for r in out[:n.value]]
+
     def solution(self, mu_dev):
         _lib.check(self.lib.lmfs_get_solution(self.h, _ptr(mu_dev)))
 

@@ -87,6 +87,7 @@ SIGNATURES = {
     "lmfs_get_solution": (_i, [_vp, _vp]),
     "lmfs_invalidate": (_i, [_vp]),
     "lmfs_update_geometry": (_i, [_vp, _vp, _d, _P(_i)]),
+    "lmfs_tune_report": (_i, [_vp, _vp, _i, _P(_i)]),
     "lmfs_stats": (_i, [_vp, _i, _vp]),
     "lmfs_qr_stats": (_i, [_vp, _i, _vp]),
     "lmfs_stokeslet_sum": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _d, _i, _vp, _vp]),

@@ -302,11 +302,25 @@ static int refined_gmres(Ctx& c, int problem, lmfs_solve_info* loc) {
   return ctl.status;
 }
 
+// The matvec autotuner for every precision a solve uses, before the solve's
+// first far field (so that all of its evaluations, and every later solve's,
+// use the same launch shapes): input the resistance right-hand side of the
+// solve's input read as rigid velocities, a smooth vector of the right size.
+static int tune_for_solve(Ctx& c, int problem, const double* in3) {
+  const bool ref = c.prm.precision != LMFS_FP64 && c.prm.refine > 0;
+  if (c.tuned[c.prm.precision] && (!ref || c.tuned[LMFS_FP64])) return LMFS_OK;
+  LMFS_TRY(rhs_device(c, LMFS_RESISTANCE, in3, c.bvec, c.prm.precision));
+  LMFS_TRY(autotune_matvec(c, problem, c.prm.precision, c.bvec));
+  if (ref) LMFS_TRY(autotune_matvec(c, problem, LMFS_FP64, c.bvec));
+  return LMFS_OK;
+}
+
 static int solve_dev(Ctx& c, int problem, const double* in_dev, double* out_dev, lmfs_solve_info* info) {
   if (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY) return LMFS_ERR_INVALID;
   const auto t0 = std::chrono::steady_clock::now();
   const bool had = c.prob[problem].ready;
   LMFS_TRY(ensure_precompute(c, problem));
+  LMFS_TRY(tune_for_solve(c, problem, in_dev));
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
   const auto t1 = std::chrono::steady_clock::now();
   lmfs_solve_info loc{};
@@ -358,6 +372,7 @@ int solve_begin(lmfs_handle h, int problem, const double* in, double* beta) {
   c.t_begin = std::chrono::steady_clock::now();
   c.had_precompute = c.prob[problem].ready;
   LMFS_TRY(ensure_precompute(c, problem));
+  LMFS_TRY(tune_for_solve(c, problem, c.io3));
   LMFS_CUDA(cudaStreamSynchronize(c.stream));
   c.t_pre = std::chrono::steady_clock::now();
   c.gm_tol = c.prm.tol;
@@ -395,7 +410,7 @@ int solve_refine_fp64_prepare(lmfs_handle h, int problem) {
   LMFS_CUDA(cudaSetDevice(c.device));
   LMFS_TRY(refine_from_zero(c));
   // the FP64 step graphs, captured outside any running capture
-  return gmres_begin_graphs(c, problem, LMFS_FP64);
+  return gmres_begin_graphs(c, problem, LMFS_FP64, c.b64);
 }
 
 int solve_refine_keep(lmfs_handle h, bool restore) {
@@ -869,6 +884,18 @@ int lmfs_qr_stats(lmfs_handle h, int problem, double* out) {
   const PairBlocks& pb = h->c.prob[problem];
   out[0] = pb.fac_ms; out[1] = pb.fac_flops; out[2] = pb.rhs_ms; out[3] = pb.rhs_flops;
   out[4] = pb.fine_ms; out[5] = pb.fine_flops; out[6] = pb.fine_blocked ? 1.0 : 0.0;
+  return LMFS_OK;
+}
+
+int lmfs_tune_report(lmfs_handle h, double* out, int cap, int* nrows) {
+  if (!h || !nrows || cap < 0 || (cap > 0 && !out)) return LMFS_ERR_INVALID;
+  const auto& log = h->c.tune_log;
+  *nrows = (int)log.size();
+  for (int r = 0; r < std::min(cap, (int)log.size()); ++r) {
+    double* o = out + 7 * r;
+    o[0] = log[r].kind; o[1] = log[r].precision; o[2] = log[r].p1; o[3] = log[r].p2; o[4] = log[r].ms;
+    o[5] = log[r].chosen; o[6] = log[r].model;
+  }
   return LMFS_OK;
 }
 

@@ -316,12 +316,13 @@ int gmres_finish(Ctx& c, int iters, double* x) {
 int gmres_begin(Ctx& c, int problem, int precision, const double* b, double* beta) {
   LMFS_TRY(gmres_alloc(c, std::max(1, c.prm.maxit)));
   LMFS_TRY(gmres_init(c, b, beta));
-  return gmres_begin_graphs(c, problem, precision);
+  return gmres_begin_graphs(c, problem, precision, b);
 }
 
-int gmres_begin_graphs(Ctx& c, int problem, int precision) {
+int gmres_begin_graphs(Ctx& c, int problem, int precision, const double* b) {
   LMFS_TRY(gmres_alloc(c, std::max(1, c.prm.maxit)));
   if (!c.step_pre[problem][precision]) {
+    LMFS_TRY(autotune_matvec(c, problem, precision, b));       // before the capture
     c.step_nodes[problem][precision] = 0;
     LMFS_TRY(capture(c, [&] { return arnoldi_pre(c, problem, precision); }, &c.step_pre[problem][precision],
                      &c.step_nodes[problem][precision]));
@@ -426,6 +427,7 @@ int gmres_solve(Ctx& c, int problem, int precision, const double* b, double* x, 
   if (beta > 0.0) {
     cudaGraphExec_t& ge = c.graph_exec[problem][precision];  // precision < 3
     if (!ge) {
+      LMFS_TRY(autotune_matvec(c, problem, precision, b));     // before the capture
       c.graph_nodes[problem][precision] = 0;
       LMFS_TRY(capture(c, [&] { return arnoldi_step(c, problem, precision); }, &ge, &c.graph_nodes[problem][precision]));
     }

@@ -223,6 +223,13 @@ struct Ctx {
   int split_m2p64 = 1, kchunk_m2p64 = 1;     // m2p_kernel<double> (LMFS_FP64)
   double* ufar_part = nullptr;       // [far_split][P][Mc][2]
   int sms = 152;                     // multiprocessors of the handle's device
+  // the matvec's autotuned launch shapes (0: the occupancy models' choice):
+  // near_kernel's target split Y and source groups G per near zone, and the
+  // all-pairs multipole kernels' source split per precision (FP64, mixed)
+  int near_Y[2] = {0, 0}, near_G[2] = {0, 0};
+  bool tuned[3] = {false, false, false};
+  struct TuneRow { int kind, precision, p1, p2; double ms; int chosen, model; };
+  std::vector<TuneRow> tune_log;
   double2* ring = nullptr;           // [Nc] (cos, sin)(2 pi j / Nc) of the source rings
   double2* nodes = nullptr;          // [Mc] (cos, sin)(2 pi m / Mc) of the collocation nodes
   int* far_err = nullptr;            // set by the far kernel if a bounded wait expired
@@ -348,6 +355,12 @@ int rhs_device(Ctx& c, int problem, const double* in3, double* b, int precision)
 int post_device(Ctx& c, int problem, const double* mu, double* out3);
 int completion_strengths(Ctx& c, const double* in3, double* lam0);   // lam_0 = K (K^T K)^{-1} [f; t]
 int far_field(Ctx& c, const double* strength, double* out, int precision, bool mobility_sums_zero);
+// Autotuner of the matvec's launch shapes for (problem, precision): times the
+// near kernel's (Y, G) candidates and, for the all-pairs far field, the
+// source splits that its partial buffer allows, with CUDA events on one
+// matvec's real inputs; the choices are cached per size class for the
+// process.  Not during a stream capture (returns without tuning).
+int autotune_matvec(Ctx& c, int problem, int precision, const double* mu);
 int far_field_at_nodes(Ctx& c, const double* strength, int m, const double2* enodes, const int4* tblk_eval,
                        int n_tblk_eval, double* out);
 int far_field_prepare(Ctx& c);
@@ -478,7 +491,7 @@ void gmres_drop_graphs(Ctx& c);
 //   copy of (relres, -, breakdown) to host_pinned[1..3];
 //   gmres_finish: x from the first `iters` basis vectors.
 int gmres_begin(Ctx& c, int problem, int precision, const double* b, double* beta);
-int gmres_begin_graphs(Ctx& c, int problem, int precision);   // the two step graphs, if not captured yet
+int gmres_begin_graphs(Ctx& c, int problem, int precision, const double* b);   // the two step graphs, if not captured yet
 int gmres_step_pre(Ctx& c, int problem, int precision);
 int gmres_step_post(Ctx& c, int problem, int precision);
 int gmres_finish(Ctx& c, int iters, double* x);

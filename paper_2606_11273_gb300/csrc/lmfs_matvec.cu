@@ -1751,9 +1751,11 @@ int near_field(Ctx& c, int mode, const double* strength, const double* mu, const
   // others only, so that no SM gets several working blocks while others idle
   const int* work = mode == 0 ? z.work0 : nullptr;
   const int ne = mode == 0 ? z.n_work0 : (int)z.h.size();
-  const int Y = std::max(1, std::min(4, (2 * c.sms + std::max(ne, 1) - 1) / std::max(ne, 1)));
+  int Y = std::max(1, std::min(4, (2 * c.sms + std::max(ne, 1) - 1) / std::max(ne, 1)));
+  int G = std::max(1, std::min({4 * Y, 1024 / ((Mc + Y - 1) / Y), c.d.Nc}));
+  const int zi = precision == LMFS_MIXED ? 1 : 0;
+  if (mode == 0 && c.near_Y[zi] > 0) { Y = c.near_Y[zi]; G = c.near_G[zi]; }    // autotuned
   const int Mt = (Mc + Y - 1) / Y;
-  const int G = std::max(1, std::min({4 * Y, 1024 / Mt, c.d.Nc}));
   const int threads = ((G * Mt + 31) / 32) * 32;
   const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mt * 2) * sizeof(double);
   if (ne > 0) {
@@ -1766,6 +1768,139 @@ int near_field(Ctx& c, int mode, const double* strength, const double* mu, const
   near_reduce<<<(n + 127) / 128, 128, 0, c.stream>>>(mode, z.off, z.ent, z.part, c.d.P, Mc, mu, ufar,
                                                      INV4PI / c.prm.mu, u);
   return check_launch("near_reduce");
+}
+
+// ---- autotuner of the matvec's launch shapes ------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::mutex g_tune_run_mu;
+// near kernel: (device, Mc, Nc, zone, log2 entries) -> (Y, G)
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_near_best;
+// all-pairs multipole kernels: (device, precision, P, allocated split) -> (split, kchunk)
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_far_best;
+
+bool near_shape_ok(const Ctx& c, int Y, int G) {
+  const int Mt = (c.d.Mc + Y - 1) / Y;
+  const int threads = ((G * Mt + 31) / 32) * 32;
+  const size_t shm = ((size_t)c.d.Nc * 4 + (size_t)G * Mt * 2) * sizeof(double);
+  return Y >= 1 && Y <= 4 && G >= 1 && G <= c.d.Nc && threads <= 1024 && shm <= 48 * 1024;
+}
+}  // namespace
+
+int autotune_matvec(Ctx& c, int problem, int precision, const double* mu) {
+  if (precision != LMFS_FP64 && precision != LMFS_MIXED) return LMFS_OK;
+  if (c.tuned[precision] || !c.prob[problem].ready) return LMFS_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c.stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return LMFS_OK;
+  }
+  c.tuned[precision] = true;
+  // one tuning at a time in the process: handles of one size class (the
+  // server's concurrent requests) then all take the first one's choice
+  std::lock_guard<std::mutex> run_lock(g_tune_run_mu);
+  const int zi = precision == LMFS_MIXED ? 1 : 0;
+  const NearSet& z = zone(c, precision);
+  const int ne = z.n_work0;
+  const bool allpairs = !c.fmm.on;
+  int& sp = precision == LMFS_MIXED ? c.split_m2p32 : c.split_m2p64;
+  int& kc = precision == LMFS_MIXED ? c.kchunk_m2p32 : c.kchunk_m2p64;
+  const auto nkey = std::make_tuple(c.device, c.d.Mc, c.d.Nc, zi, ilog2(std::max(ne, 1)));
+  const auto fkey = std::make_tuple(c.device, precision, c.d.P, c.far_split);
+  bool have_near = false, have_far = !allpairs;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_near_best.find(nkey);
+    if (it != g_near_best.end()) { c.near_Y[zi] = it->second.first; c.near_G[zi] = it->second.second; have_near = true; }
+    auto jt = g_far_best.find(fkey);
+    if (allpairs && jt != g_far_best.end()) { sp = jt->second.first; kc = jt->second.second; have_far = true; }
+  }
+  if (have_near && have_far) return LMFS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cuda_failed(cudaEventCreate(&e0), "event") || cuda_failed(cudaEventCreate(&e1), "event")) {
+    if (e0) cudaEventDestroy(e0);
+    return LMFS_ERR_CUDA;
+  }
+  int rc = LMFS_OK;
+  // one timed run on the handle's stream (after one untimed run of the first candidate)
+  auto timed = [&](auto&& run, double* ms, bool warm) {
+    int r = warm ? run() : LMFS_OK;
+    if (r == LMFS_OK && cuda_failed(cudaEventRecord(e0, c.stream), "event")) r = LMFS_ERR_CUDA;
+    if (r == LMFS_OK) r = run();
+    if (r == LMFS_OK && (cuda_failed(cudaEventRecord(e1, c.stream), "event") || cuda_failed(cudaEventSynchronize(e1), "sync")))
+      r = LMFS_ERR_CUDA;
+    float f = 0.f;
+    if (r == LMFS_OK) cudaEventElapsedTime(&f, e0, e1);
+    *ms = f;
+    return r;
+  };
+  double* out = c.xsol;                                  // scratch: GMRES writes its own solution there later
+  rc = matvec_pre(c, problem, mu, precision);
+  if (rc == LMFS_OK && !have_far) {
+    // candidate source splits: 1, 2, 4, 8, 16 within the partial-sum buffer, and the model's
+    std::vector<std::pair<int, int>> cand;
+    for (int q = 1; q <= c.far_split; q *= 2) {
+      const int kq = (c.d.P + q - 1) / q;
+      if ((c.d.P + kq - 1) / kq == q) cand.push_back({q, kq});
+    }
+    if (std::find(cand.begin(), cand.end(), std::make_pair(sp, kc)) == cand.end()) cand.push_back({sp, kc});
+    const int msp = sp, mkc = kc;
+    double best = 1e30;
+    std::pair<int, int> pick{sp, kc};
+    std::vector<std::pair<std::pair<int, int>, double>> rows;
+    for (const auto& q : cand) {
+      sp = q.first; kc = q.second;
+      double ms = 0.0;
+      rc = timed([&] {
+        int r = far_main(c, c.ufar, precision, problem == LMFS_MOBILITY);
+        return r == LMFS_OK ? far_post(c, c.ufar, precision) : r;
+      }, &ms, rows.empty());
+      if (rc != LMFS_OK) break;
+      rows.push_back({q, ms});
+      if (ms < best * (1.0 - 1e-9)) { best = ms; pick = q; }
+    }
+    sp = rc == LMFS_OK ? pick.first : msp;
+    kc = rc == LMFS_OK ? pick.second : mkc;
+    for (const auto& r : rows)
+      c.tune_log.push_back({1, precision, r.first.first, r.first.second, r.second, r.first == pick ? 1 : 0,
+                            (r.first.first == msp && r.first.second == mkc) ? 1 : 0});
+    if (rc == LMFS_OK) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_far_best[fkey] = pick;
+    }
+  }
+  if (rc == LMFS_OK) rc = far_main(c, c.ufar, precision, problem == LMFS_MOBILITY);
+  if (rc == LMFS_OK) rc = far_post(c, c.ufar, precision);
+  if (rc == LMFS_OK && !have_near && ne > 0) {
+    // candidate (Y, G): target splits 1, 2, 4 x source groups 1..16, within the kernel's limits
+    const int mY = std::max(1, std::min(4, (2 * c.sms + std::max(ne, 1) - 1) / std::max(ne, 1)));
+    const int mG = std::max(1, std::min({4 * mY, 1024 / ((c.d.Mc + mY - 1) / mY), c.d.Nc}));
+    std::vector<std::pair<int, int>> cand = {{mY, mG}};
+    for (int Y : {1, 2, 4})
+      for (int G : {1, 2, 4, 8, 16})
+        if (near_shape_ok(c, Y, G) && !(Y == mY && G == mG)) cand.push_back({Y, G});
+    double best = 1e30;
+    std::pair<int, int> pick{mY, mG};
+    for (const auto& q : cand) {
+      c.near_Y[zi] = q.first; c.near_G[zi] = q.second;
+      double ms = 0.0;
+      rc = timed([&] { return near_field(c, 0, c.sig, mu, c.ufar, out, problem, precision); }, &ms, &q == &cand[0]);
+      if (rc != LMFS_OK) break;
+      c.tune_log.push_back({0, precision, q.first, q.second, ms, 0, (q.first == mY && q.second == mG) ? 1 : 0});
+      if (ms < best * (1.0 - 1e-9)) { best = ms; pick = q; }
+    }
+    c.near_Y[zi] = rc == LMFS_OK ? pick.first : 0;
+    c.near_G[zi] = rc == LMFS_OK ? pick.second : 0;
+    for (auto& r : c.tune_log)
+      if (r.kind == 0 && r.precision == precision) r.chosen = (r.p1 == pick.first && r.p2 == pick.second) ? 1 : 0;
+    if (rc == LMFS_OK) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_near_best[nkey] = pick;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 // The matvec in three steps around the far field's evaluation (the server's
