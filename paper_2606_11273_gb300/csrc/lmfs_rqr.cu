@@ -51,8 +51,11 @@ struct RArgs {
   int wsz;                         // doubles of the shared work region
 };
 
-// 16 random signs per row: the bits of a 32-bit integer mix of the row index
-// (the finalizer of MurmurHash3).
+// The sketch's entries of row i: one of each group of four sketch rows
+// (bits 2g..2g+1 select row 4g + q) with a sign (bit 8 + g), so that each
+// row adds into four of the sixteen sketch rows (a sparse sign sketch); the
+// bits come from a 32-bit integer mix of the row index (the finalizer of
+// MurmurHash3).
 __device__ __forceinline__ unsigned row_signs(unsigned i) {
   unsigned h = i * 0x9E3779B1u + 0x7F4A7C15u;
   h ^= h >> 16; h *= 0x85EBCA6Bu;
@@ -118,6 +121,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   __shared__ int s_pv[RB];
   __shared__ int s_stop, s_bad, s_bbe, s_q;
   __shared__ double s_r00, s_scale, s_thr2;
+  __shared__ double s_rdi[RB];
 
   // ---- sketch, squared column norms, identity permutation
   for (int i = tid; i < m; i += RT) om[i] = (unsigned short)row_signs((unsigned)i);
@@ -136,10 +140,17 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     double nn = 0.0;
     for (int i = 0; i < m; ++i) {
       const double x = col[i];
-      const unsigned msk = om[i];
+      const unsigned msk = om[i];                         // the same for every lane: uniform branches
       nn = fma(x, x, nn);
 #pragma unroll
-      for (int j = 0; j < RL; ++j) acc[j] += ((msk >> j) & 1u) ? x : -x;
+      for (int g = 0; g < 4; ++g) {
+        const double sx = ((msk >> (8 + g)) & 1u) ? x : -x;
+        const unsigned q = (msk >> (2 * g)) & 3u;
+        if (q == 0) acc[4 * g] += sx;
+        else if (q == 1) acc[4 * g + 1] += sx;
+        else if (q == 2) acc[4 * g + 2] += sx;
+        else acc[4 * g + 3] += sx;
+      }
     }
 #pragma unroll
     for (int j = 0; j < RL; ++j) Yg[(long long)j * ysd + c] = acc[j];
@@ -162,42 +173,47 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
         unsigned long long t = 0ull;
         for (int ww = 0; ww < RW; ++ww) t = max(t, redu[ww]);
         if (t >= 0x7FF0000000000000ull) s_bad = 1;
-        s_stop = (s_r00 > 0.0 && t <= (unsigned long long)__double_as_longlong(s_thr2)) || s_bad || t == 0ull;
+        s_stop = (__double_as_longlong(s_r00) > 0 && t <= (unsigned long long)__double_as_longlong(s_thr2)) ||
+                 s_bad || t == 0ull;
       }
       __syncthreads();
       if (s_stop) { rank = s; break; }
     }
-    // ---- pivots of this block: column-pivoted QR of the sketch's trailing columns
+    // ---- pivots of this block: column-pivoted QR of the sketch's trailing
+    // columns, on an FP32 copy (the pivot order needs no more; the FP64 pipe
+    // stays with the other CTA's updates)
     {
-      double* Ys = W;                                     // [RL][nt]: Ys[j * nt + c]
+      float* Ys = (float*)W;                              // [RL][nt]: Ys[j * nt + c]
       for (int e = tid; e < RL * nt; e += RT) {
         const int j = e / nt, c = e - j * nt;
-        Ys[e] = Yg[(long long)j * ysd + s + c];
+        Ys[e] = (float)Yg[(long long)j * ysd + s + c];
       }
       __syncthreads();
+      __shared__ float s_taup, s_scalep;
       for (int t = 0; t < bb; ++t) {
-        double bv = -1.0;
+        float bv = -1.0f;
         int bi = 0x7fffffff;
         for (int c = t + tid; c < nt; c += RT) {
-          double v = 0.0;
+          float v = 0.0f;
 #pragma unroll
           for (int j = 0; j < RL; ++j)
-            if (j >= t) v = fma(Ys[j * nt + c], Ys[j * nt + c], v);
+            if (j >= t) v = fmaf(Ys[j * nt + c], Ys[j * nt + c], v);
           if (v > bv) { bv = v; bi = c; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
-        if (lane == 0) { red[warp] = bv; ((int*)(red + RW))[warp] = bi; }
+        float* redf = (float*)red;
+        if (lane == 0) { redf[warp] = bv; ((int*)(red + RW))[warp] = bi; }
         __syncthreads();
         if (tid == 0) {
-          double v = red[0];
+          float v = redf[0];
           int q = ((int*)(red + RW))[0];
           for (int ww = 1; ww < RW; ++ww) {
-            const double ov = red[ww];
+            const float ov = redf[ww];
             const int oi = ((int*)(red + RW))[ww];
             if (ov > v || (ov == v && oi < q)) { v = ov; q = oi; }
           }
@@ -207,41 +223,40 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
         __syncthreads();
         const int q = s_q;
         if (q != t && tid < RL) {
-          const double x = Ys[tid * nt + t];
+          const float x = Ys[tid * nt + t];
           Ys[tid * nt + t] = Ys[tid * nt + q];
           Ys[tid * nt + q] = x;
         }
         __syncthreads();
         // Householder vector of Ys[t:RL, t] (kept in place, unit entry implicit)
         if (tid == 0) {
-          const double alpha = Ys[t * nt + t];
-          double sig2 = 0.0;
-          for (int j = t + 1; j < RL; ++j) sig2 = fma(Ys[j * nt + t], Ys[j * nt + t], sig2);
-          const double nrm = sqrt(alpha * alpha + sig2);
-          if (nrm == 0.0 || !(nrm == nrm)) {
-            s_scale = 0.0;
-            stau[0] = 0.0;
+          const float alpha = Ys[t * nt + t];
+          float sig2 = 0.0f;
+          for (int j = t + 1; j < RL; ++j) sig2 = fmaf(Ys[j * nt + t], Ys[j * nt + t], sig2);
+          const float nrm = sqrtf(alpha * alpha + sig2);
+          if (nrm == 0.0f || !(nrm == nrm) || isinf(nrm)) {
+            s_taup = 0.0f;
           } else {
-            const double beta = alpha >= 0.0 ? -nrm : nrm;
-            stau[0] = (beta - alpha) / beta;
-            s_scale = 1.0 / (alpha - beta);
+            const float beta = alpha >= 0.0f ? -nrm : nrm;
+            s_taup = (beta - alpha) / beta;
+            s_scalep = 1.0f / (alpha - beta);
             Ys[t * nt + t] = beta;
-            for (int j = t + 1; j < RL; ++j) Ys[j * nt + t] *= s_scale;
+            for (int j = t + 1; j < RL; ++j) Ys[j * nt + t] *= s_scalep;
           }
         }
         __syncthreads();
-        const double tau = stau[0];
-        if (tau != 0.0) {
+        const float tau = s_taup;
+        if (tau != 0.0f) {
           for (int c = t + 1 + tid; c < nt; c += RT) {
-            double d = Ys[t * nt + c];
+            float d = Ys[t * nt + c];
 #pragma unroll
             for (int j = 0; j < RL; ++j)
-              if (j > t) d = fma(Ys[j * nt + t], Ys[j * nt + c], d);
+              if (j > t) d = fmaf(Ys[j * nt + t], Ys[j * nt + c], d);
             d *= tau;
             Ys[t * nt + c] -= d;
 #pragma unroll
             for (int j = 0; j < RL; ++j)
-              if (j > t) Ys[j * nt + c] = fma(-d, Ys[j * nt + t], Ys[j * nt + c]);
+              if (j > t) Ys[j * nt + c] = fmaf(-d, Ys[j * nt + t], Ys[j * nt + c]);
           }
         }
         __syncthreads();
@@ -357,27 +372,33 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
           for (int u = 0; u < t; ++u) g[t * (t - 1) / 2 + u] = fma(v[u], v[t], g[t * (t - 1) / 2 + u]);
       }
       block_sums<RB * (RB - 1) / 2>(g, RB * (RB - 1) / 2, red, sred);
-      if (tid == 0) {
-        for (int e = 0; e < RB * RB; ++e) T[e] = 0.0;
-        int q0 = 0;
-        for (int t = 0; t < bbe; ++t) {
-          // sred holds (u, t) for t = 1..RB-1, u < t, in order: offset t (t - 1) / 2
-          q0 = t * (t - 1) / 2;
-          T[t * RB + t] = stau[t];
-          for (int u = 0; u < t; ++u) {
-            double acc = 0.0;
-            for (int w2 = u; w2 < t; ++w2) acc = fma(T[u * RB + w2], sred[q0 + w2], acc);
-            T[u * RB + t] = -stau[t] * acc;
-          }
+      // T column by column on warp 0 (lane u < t: T[u][t] = -tau_t sum_{w=u}^{t-1}
+      // T[u][w] (v_w . v_t)); G2 row by row on warp 1, with the reciprocal diagonal
+      if (warp == 0) {
+        if (lane < RB) {
+          for (int e = lane; e < RB * RB; e += RB) T[e] = 0.0;
         }
-      }
-      // the sketch update's coefficients G2 = Y_1 R_11^-1 (rows of the sketch)
-      if (!stopped && tid < RL) {
-        const int j = tid;
+        __syncwarp();
         for (int t = 0; t < bbe; ++t) {
-          double acc = Yg[(long long)j * ysd + s + t];
-          for (int u = 0; u < t; ++u) acc = fma(-G2[j * RB + u], R11[u * RB + t], acc);
-          G2[j * RB + t] = acc / R11[t * RB + t];
+          const int q0 = t * (t - 1) / 2;
+          if (lane < t) {
+            double acc = 0.0;
+            for (int w2 = lane; w2 < t; ++w2) acc = fma(T[lane * RB + w2], sred[q0 + w2], acc);
+            T[lane * RB + t] = -stau[t] * acc;
+          }
+          if (lane == t) T[t * RB + t] = stau[t];
+          __syncwarp();
+        }
+      } else if (warp == 1 && !stopped) {
+        if (lane < bbe) s_rdi[lane] = 1.0 / R11[lane * RB + lane];
+        __syncwarp();
+        if (lane < RL) {
+          const int j = lane;
+          for (int t = 0; t < bbe; ++t) {
+            double acc = Yg[(long long)j * ysd + s + t];
+            for (int u = 0; u < t; ++u) acc = fma(-G2[j * RB + u], R11[u * RB + t], acc);
+            G2[j * RB + t] = acc * s_rdi[t];
+          }
         }
       }
       __syncthreads();
