@@ -166,18 +166,20 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     const int nt = n - s;
     const int bb = min(RB, min(nt, m - s));
     // ---- stop test on the exact partial norms (their maximum from the last
-    // pass; a NaN or infinity has the largest bit patterns)
+    // pass, read by every thread: no barrier; a NaN or infinity has the
+    // largest bit patterns).  red is next written after the sketch copy's
+    // barrier, so every thread has read it by then.
     {
-      if (tid == 0) {
-        const unsigned long long* redu = (const unsigned long long*)red;
-        unsigned long long t = 0ull;
-        for (int ww = 0; ww < RW; ++ww) t = max(t, redu[ww]);
-        if (t >= 0x7FF0000000000000ull) s_bad = 1;
-        s_stop = (__double_as_longlong(s_r00) > 0 && t <= (unsigned long long)__double_as_longlong(s_thr2)) ||
-                 s_bad || t == 0ull;
-      }
-      __syncthreads();
-      if (s_stop) { rank = s; break; }
+      const unsigned long long* redu = (const unsigned long long*)red;
+      unsigned long long t = 0ull;
+      for (int ww = 0; ww < RW; ++ww) t = max(t, redu[ww]);
+      // (every thread decides from the same values: red, s_r00 and s_thr2 were
+      // written before the last barrier; s_bad is not read for it)
+      const bool bad = t >= 0x7FF0000000000000ull;
+      const bool stop = (__double_as_longlong(s_r00) > 0 && t <= (unsigned long long)__double_as_longlong(s_thr2)) ||
+                        bad || t == 0ull;
+      if (bad && tid == 0) s_bad = 1;
+      if (stop) { rank = s; break; }
     }
     // ---- pivots of this block: column-pivoted QR of the sketch's trailing
     // columns, on an FP32 copy (the pivot order needs no more; the FP64 pipe
