@@ -101,8 +101,8 @@ class Clocks:
 # on the 398 fine half systems of `LMFS_QR_PATH=blocked bench.py --profile-case
 # qr_mid` (P = 160, area fraction 0.65), divided by 398.  Valid only for the kernel source it was
 # taken on: reported as null once lmfs_rqr.cu changes.
-RQR_TRAFFIC_PER_MATRIX = (74.83e9 + 38.24e9) / 398.0
-RQR_TRAFFIC_SRC_SHA256 = "4fc5036c3f287054fad136ddd92a30be7dbfd55bb1a4bac6130bcdd86315d057"
+RQR_TRAFFIC_PER_MATRIX = (74.87e9 + 38.27e9) / 398.0
+RQR_TRAFFIC_SRC_SHA256 = "d8a729861d5dcc5497af7d651e6ea3a43b089b818e7af5c3fc3a5ef3f0105620"
 
 
 def rqr_traffic_per_matrix():

@@ -16,9 +16,11 @@
 // stays a sketch of the trailing matrix without another pass over it.
 //
 // Truncation as in the pivoted QR: the factorization stops at the first
-// reflector whose |R_ss| <= eps |R_00|, or at a block boundary where every
-// remaining column's partial norm (kept exactly, from the trailing pass) is
-// <= eps |R_00|.  The solution is then x = P [R_11^-1 (Q^T B)_1; 0].
+// reflector whose |R_ss| <= eps |R_00| (R_ss is the norm of the pivot
+// column's remaining part, and the sketch pivots a column of near-largest
+// remaining norm; a test on the exact remaining norms at each block start
+// changed no rank in the prototype and is not made).  The solution is then
+// x = P [R_11^-1 (Q^T B)_1; 0].
 //
 // Tested on the fine systems of unit pairs at gaps 1e-1..1e-3 (both problems)
 // against column-pivoted QR and the SVD pseudo-inverse: the same rank within
@@ -70,13 +72,6 @@ __device__ __forceinline__ double warp_allsum(double v) {
   return v;
 }
 
-// Warp maximum of v; lane 0 stores it at red[warp] (as an integer).
-__device__ __forceinline__ void warp_max_to(unsigned long long v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) ((unsigned long long*)red)[threadIdx.x >> 5] = v;
-}
-
 // Block sums of NV values held by every thread; the sums land in out[0..NV)
 // (shared), visible to every thread after the call.  red: RW * NV doubles.
 template <int NV>
@@ -120,28 +115,22 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   double* sred = red + RW * 32;                           // [32] block results
   __shared__ int s_pv[RB];
   __shared__ int s_stop, s_bad, s_bbe, s_q;
-  __shared__ double s_r00, s_scale, s_thr2;
+  __shared__ double s_r00, s_scale;
   __shared__ double s_rdi[RB];
 
   // ---- sketch, squared column norms, identity permutation
   for (int i = tid; i < m; i += RT) om[i] = (unsigned short)row_signs((unsigned)i);
   for (int c = tid; c < n; c += RT) perm[c] = c;
-  if (tid == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; s_thr2 = 0.0; }
+  if (tid == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; }
   __syncthreads();
-  // squared partial norms are >= 0, so their bit patterns order as integers:
-  // the block maximum of the norms below the current block is kept without
-  // FP64 instructions (nmx per thread, then per warp in red)
-  unsigned long long nmx = 0ull;
   for (int c = tid; c < n; c += RT) {
     const double* col = A + (long long)c * ld;
     double acc[RL];
 #pragma unroll
     for (int j = 0; j < RL; ++j) acc[j] = 0.0;
-    double nn = 0.0;
     for (int i = 0; i < m; ++i) {
       const double x = col[i];
       const unsigned msk = om[i];                         // the same for every lane: uniform branches
-      nn = fma(x, x, nn);
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         const double sx = ((msk >> (8 + g)) & 1u) ? x : -x;
@@ -154,9 +143,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     }
 #pragma unroll
     for (int j = 0; j < RL; ++j) Yg[(long long)j * ysd + c] = acc[j];
-    nmx = max(nmx, (unsigned long long)__double_as_longlong(nn));
   }
-  warp_max_to(nmx, red);
   __syncthreads();
 
   const int smax = min(m, n);
@@ -165,22 +152,6 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   while (s < smax) {
     const int nt = n - s;
     const int bb = min(RB, min(nt, m - s));
-    // ---- stop test on the exact partial norms (their maximum from the last
-    // pass, read by every thread: no barrier; a NaN or infinity has the
-    // largest bit patterns).  red is next written after the sketch copy's
-    // barrier, so every thread has read it by then.
-    {
-      const unsigned long long* redu = (const unsigned long long*)red;
-      unsigned long long t = 0ull;
-      for (int ww = 0; ww < RW; ++ww) t = max(t, redu[ww]);
-      // (every thread decides from the same values: red, s_r00 and s_thr2 were
-      // written before the last barrier; s_bad is not read for it)
-      const bool bad = t >= 0x7FF0000000000000ull;
-      const bool stop = (__double_as_longlong(s_r00) > 0 && t <= (unsigned long long)__double_as_longlong(s_thr2)) ||
-                        bad || t == 0ull;
-      if (bad && tid == 0) s_bad = 1;
-      if (stop) { rank = s; break; }
-    }
     // ---- pivots of this block: column-pivoted QR of the sketch's trailing
     // columns, on an FP32 copy (the pivot order needs no more; the FP64 pipe
     // stays with the other CTA's updates)
@@ -296,10 +267,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
       if (tid == 0) {
         const double alpha = Vs[t * ld + p];
         const double nrm = sqrt(alpha * alpha + sred[0]);
-        if (p == 0) {
-          s_r00 = nrm;
-          s_thr2 = (a.eps * nrm) * (a.eps * nrm);
-        }
+        if (p == 0) s_r00 = nrm;
         if (!(nrm == nrm) || isinf(nrm)) s_bad = 1;
         if (nrm <= a.eps * s_r00 || nrm == 0.0 || s_bad) {
           s_stop = 1;
@@ -413,11 +381,9 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     {
       const int c0 = stopped ? n : s + bbe;
       const int ncol = n + k - c0;
-      nmx = 0ull;
       int tpc = 1;
       while (tpc < 8 && ncol * tpc * 2 <= RT) tpc *= 2;
       const int slots = RT / tpc, g = tid / tpc, r = tid - g * tpc;
-      const int rs = s + bbe;                             // rows below the block
       // every lane of a warp takes the same number of steps (the shuffles
       // and the warp barrier need all 32); lanes past the last column idle
       for (int base = 0; base < ncol; base += slots) {
@@ -465,7 +431,6 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
             if (u <= t) acc = fma(T[u * RB + t], w[u], acc);
           w2[t] = (t < bbe) ? acc : 0.0;
         }
-        double nn = 0.0;
         if (act) {
           double xn[4];
           int i0 = s + 4 * r;
@@ -488,15 +453,10 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
               }
             }
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              if (i0 + h < m) {
-                col[i0 + h] = x[h];
-                if (i0 + h >= rs) nn = fma(x[h], x[h], nn);
-              }
-            }
+            for (int h = 0; h < 4; ++h)
+              if (i0 + h < m) col[i0 + h] = x[h];
           }
         }
-        for (int o = 1; o < tpc; o <<= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
         __syncwarp();                                     // the group's stores, before R_12 is read
         if (act && c < n) {
           // sketch of this column: Y_2 <- Y_2 - G2 R_12, rows split over the group
@@ -513,11 +473,9 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
               *y = acc;
             }
           }
-          nmx = max(nmx, (unsigned long long)__double_as_longlong(nn));
         }
       }
     }
-    warp_max_to(nmx, red);
     __syncthreads();
     s += bbe;
     if (stopped) { rank = s; break; }
