@@ -90,3 +90,52 @@ def test_wave_split_fills_waves(harness):
     assert split > 1 and cost <= 1.01 * ideal
     (s1, c1), = run(harness, [(704, 456, 10000, 8, 1)])
     assert s1 == 1 and -(-704 // 456) * c1 > cost
+
+
+CHUNK_HARNESS = r"""
+#include <cstdio>
+#include "lmfs_internal.h"
+int main() {
+  long long C; double per;
+  while (std::scanf("%lld %lf", &C, &per) == 2) std::printf("%d\n", lmfs::pair_chunk(C, per));
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def chunk_harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if not cxx or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    d = tmp_path_factory.mktemp("chunk")
+    src = d / "chunk.cpp"
+    src.write_text(CHUNK_HARNESS)
+    exe = d / "chunk"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2606_11273_gb300", "csrc"),
+                    "-I", CUDA_INC, str(src), "-o", str(exe)], check=True, capture_output=True)
+    return exe
+
+
+def test_pair_chunks_are_equal_and_within_budget(chunk_harness):
+    """The precompute's chunk rule: chunks of equal size (the last shorter by
+    fewer pairs than there are chunks) that cover all C pairs in the fewest
+    chunks the workspace budget allows (12 GB and 456 pairs up to 456 pairs,
+    32 GB and 2048 pairs beyond)."""
+    rng = np.random.default_rng(5)
+    per = 38.2e6                                  # bytes of workspace per pair at the default parameters
+    cases = [(10470, per), (456, per), (457, per), (400, per), (1, per), (122, per), (1100, per), (5000, 1e5)]
+    cases += [(int(rng.integers(1, 30000)), float(rng.uniform(1e5, 8e7))) for _ in range(300)]
+    inp = "".join(f"{c} {p}\n" for c, p in cases)
+    out = subprocess.run([str(chunk_harness)], input=inp, capture_output=True, text=True, check=True).stdout.split()
+    assert len(out) == len(cases)
+    for (C, p), got in zip(cases, out):
+        chunk = int(got)
+        budget, cap = (32 * 2 ** 30, 2048) if C > 456 else (12 * 2 ** 30, 456)
+        lim = max(1, min(C, int(budget / p), cap))
+        nchunk = -(-C // lim)
+        assert chunk == -(-C // nchunk), (C, p, chunk)
+        assert chunk <= lim and -(-C // chunk) == nchunk
+        # the last chunk is shorter than the others by fewer pairs than there are chunks
+        assert C - (nchunk - 1) * chunk >= chunk - nchunk
+    assert int(out[0]) == 873                     # the P = 10^4 packing: 12 chunks
