@@ -328,7 +328,8 @@ inline int pair_chunk(long long C, double per_pair) {
 // The blocked QR with sketch pivoting (lmfs_rqr.cu): shared memory it needs,
 // and the batch solve itself (solve mode only).
 size_t rqr_smem_bytes(int ld, int nmax);
-int rqr_solve_batched(const QRBatch& q, cudaStream_t s);
+int rqr_active_clusters(size_t shm, int cs, int nb);
+int rqr_solve_batched(const QRBatch& q, cudaStream_t s, int cs);
 
 // ---- matvec pieces (lmfs_matvec.cu) ---------------------------------------
 int onebody_apply(Ctx& c, const OneBody& ob, const double* mu, double* lb);

@@ -566,19 +566,27 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (q.used_blocked) *q.used_blocked = 0;
-  // The blocked form (one matrix per CTA, lmfs_rqr.cu) for batches that fill
-  // at least four waves of two CTAs per SM (measured on the P = 10^4 fine
-  // systems: 2.1 waves per launch 10.2 s against the cluster form's 9.4 s,
-  // 5.7 waves 8.8 s; on its 1746 peanut systems of 200 rows 46 ms against
-  // 67 ms per launch); the pivoted cluster form below spreads each matrix over
-  // several SMs, which smaller batches need.
+  // The blocked form (lmfs_rqr.cu) with one matrix per CTA for batches that
+  // fill at least four waves of two CTAs per SM (measured on the P = 10^4 fine
+  // systems: 2.1 waves per launch 10.2 s against the pivoted cluster form's
+  // 9.4 s, 5.7 waves 8.8 s; on its 1746 peanut systems of 200 rows 46 ms
+  // against 67 ms per launch), with two CTAs (a cluster) per matrix from one
+  // wave (P = 160 and 300 packings, 398 and 434 systems: 192 and 396 ms
+  // against 200 and 428 ms; one CTA 224 and 448 ms); below that the pivoted
+  // cluster form (P = 100, 74 systems: 40 ms, the blocked form 41 ms at best,
+  // with four CTAs per matrix).  LMFS_QR_PATH=blocked|cluster and
+  // LMFS_QR_CS=n override the choice (tests compare the forms).
   if (solve && q.k > 0) {
     const int path = qr_path_override();
-    const bool fits = rqr_smem_bytes(q.ld, q.nmax) <= 226 * 1024;
-    const bool big = q.nb >= 8 * sms && q.ld >= 128;
-    if (fits && (path == 1 || (path == 0 && big))) {
+    const size_t shm = rqr_smem_bytes(q.ld, q.nmax);
+    const bool fits = shm <= 226 * 1024;
+    int cs = q.nb >= 8 * sms ? 1 : (q.nb >= 2 * sms ? 2 : 0);
+    if (const char* e = std::getenv("LMFS_QR_CS")) cs = std::max(1, std::min(8, std::atoi(e)));
+    if (path == 1 && cs == 0) cs = 1;
+    if (cs > 1 && rqr_active_clusters(shm, cs, q.nb) <= 0) cs = path == 1 ? 1 : 0;
+    if (fits && q.ld >= 128 && path != 2 && cs > 0) {
       if (q.used_blocked) *q.used_blocked = 1;
-      return rqr_solve_batched(q, st);
+      return rqr_solve_batched(q, st, cs);
     }
   }
 

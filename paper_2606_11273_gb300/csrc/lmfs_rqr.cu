@@ -33,6 +33,8 @@
 #include <numeric>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "lmfs_internal.h"
 
 namespace lmfs {
@@ -49,8 +51,9 @@ struct RArgs {
   double* X; int xld; long long xstride; int* rank; int* perm; int permstride; int* info;
   double* Yg;                      // [nb][RL][ysd] sketch of the trailing columns
   int ysd;
-  const int* order;                // matrix of CTA blockIdx.x
+  const int* order;                // matrix of cluster blockIdx.x / cs
   int wsz;                         // doubles of the shared work region
+  int cs;                          // CTAs per matrix (a thread-block cluster when > 1)
 };
 
 // The sketch's entries of row i: one of each group of four sketch rows
@@ -95,8 +98,20 @@ __device__ void block_sums(double (&v)[NV], int nv, double* red, double* out) {
 }
 
 __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
+  namespace cg = cooperative_groups;
   extern __shared__ __align__(16) double sm[];
-  const int b = a.order ? a.order[blockIdx.x] : (int)blockIdx.x;
+  // cs CTAs per matrix: CTA 0 of the cluster runs each block's serial stages
+  // (pivots, exchanges, the block's factorization, T) while the others wait;
+  // all of them share the trailing updates and the back substitution.  Every
+  // CTA passes the same cluster barriers: the decisions (the block size and
+  // the stop) are CTA 0's, read by all after a barrier.
+  const int cs = a.cs;
+  const int crank = cs > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  auto csync = [&] {
+    if (cs > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+  const int b = a.order ? a.order[blockIdx.x / cs] : (int)(blockIdx.x / cs);
   const int m = a.m[b], n = a.n[b], k = a.k, ld = a.ld, ysd = a.ysd;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* A = a.A + (long long)b * a.mstride;
@@ -120,10 +135,11 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
 
   // ---- sketch, squared column norms, identity permutation
   for (int i = tid; i < m; i += RT) om[i] = (unsigned short)row_signs((unsigned)i);
-  for (int c = tid; c < n; c += RT) perm[c] = c;
+  if (crank == 0)
+    for (int c = tid; c < n; c += RT) perm[c] = c;
   if (tid == 0) { s_stop = 0; s_bad = 0; s_r00 = 0.0; }
   __syncthreads();
-  for (int c = tid; c < n; c += RT) {
+  for (int c = crank * RT + tid; c < n; c += cs * RT) {
     const double* col = A + (long long)c * ld;
     double acc[RL];
 #pragma unroll
@@ -144,7 +160,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
 #pragma unroll
     for (int j = 0; j < RL; ++j) Yg[(long long)j * ysd + c] = acc[j];
   }
-  __syncthreads();
+  csync();
 
   const int smax = min(m, n);
   int rank = smax;
@@ -152,6 +168,8 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   while (s < smax) {
     const int nt = n - s;
     const int bb = min(RB, min(nt, m - s));
+    double* Vs = W;                                       // [RB][ld]: Vs[t * ld + i], rows s..m-1
+    if (crank == 0) {
     // ---- pivots of this block: column-pivoted QR of the sketch's trailing
     // columns, on an FP32 copy (the pivot order needs no more; the FP64 pipe
     // stays with the other CTA's updates)
@@ -254,7 +272,6 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
       }
     }
     // ---- the block, factored without pivoting in shared memory
-    double* Vs = W;                                       // [RB][ld]: Vs[t * ld + i], rows s..m-1
     for (int t = 0; t < bb; ++t)
       for (int i = s + tid; i < m; i += RT) Vs[t * ld + i] = A[(long long)(s + t) * ld + i];
     if (tid == 0) s_bbe = bb;
@@ -326,9 +343,8 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     for (int t = 0; t < bbe; ++t)
       for (int i = s + tid; i < s + t; i += RT) Vs[t * ld + i] = 0.0;
     __syncthreads();
-    if (bbe == 0) { rank = s; break; }
     // ---- T of the compact WY form, H_0 ... H_{bbe-1} = I - V T V^T, from the Gram matrix of V
-    {
+    if (bbe > 0) {
       double g[RB * (RB - 1) / 2];
 #pragma unroll
       for (int q = 0; q < RB * (RB - 1) / 2; ++q) g[q] = 0.0;
@@ -373,6 +389,29 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
       }
       __syncthreads();
     }
+    }  // CTA 0's stages
+    csync();
+    // every CTA: CTA 0's block size and stop, then its V, T and G2
+    int bbe = s_bbe, stop_i = s_stop;
+    if (cs > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      bbe = *cl.map_shared_rank(&s_bbe, 0);
+      stop_i = *cl.map_shared_rank(&s_stop, 0);
+    }
+    const bool stopped = stop_i != 0;
+    if (bbe == 0) { rank = s; break; }
+    if (crank != 0) {
+      for (int t = 0; t < bbe; ++t) {
+        const double* col = A + (long long)(s + t) * ld;
+        for (int i = s + tid; i < m; i += RT) Vs[t * ld + i] = i < s + t ? 0.0 : (i == s + t ? 1.0 : col[i]);
+      }
+      cg::cluster_group cl = cg::this_cluster();
+      const double* T0 = cl.map_shared_rank(T, 0);
+      const double* G0 = cl.map_shared_rank(G2, 0);
+      for (int e = tid; e < RB * RB; e += RT) T[e] = T0[e];
+      for (int e = tid; e < RL * RB; e += RT) G2[e] = G0[e];
+      __syncthreads();
+    }
     // ---- Q^T applied to the trailing columns: (I - V T^T V^T) C, one pass
     // each.  A column belongs to a group of tpc threads (tpc = 1 while there
     // are enough columns for every thread), each taking every tpc-th chunk of
@@ -380,7 +419,8 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     // column's V^T c needs no cross-lane sum unless tpc > 1.
     {
       const int c0 = stopped ? n : s + bbe;
-      const int ncol = n + k - c0;
+      // this CTA's columns: c0 + crank + cs j
+      const int ncol = std::max(0, (n + k - c0 - crank + cs - 1) / cs);
       int tpc = 1;
       while (tpc < 8 && ncol * tpc * 2 <= RT) tpc *= 2;
       const int slots = RT / tpc, g = tid / tpc, r = tid - g * tpc;
@@ -389,7 +429,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
       for (int base = 0; base < ncol; base += slots) {
         const int cc = base + g;
         const bool act = cc < ncol;
-        const int c = c0 + (act ? cc : 0);
+        const int c = c0 + (act ? crank + cs * cc : 0);
         double* col = A + (long long)c * ld;
         double w[RB];
 #pragma unroll
@@ -476,7 +516,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
         }
       }
     }
-    __syncthreads();
+    csync();
     s += bbe;
     if (stopped) { rank = s; break; }
   }
@@ -496,9 +536,10 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     const int cap = a.wsz - RW * ysd - rpad;              // >= 7 nmax >= rank (wsz >= RL nmax)
     for (int j = tid; j < rank; j += RT) rinv[j] = 1.0 / A[(long long)j * ld + j];
     int bad = 0;
-    for (int c0 = 0; c0 < k; c0 += RW) {
-      const int c = c0 + warp;
-      const bool act = c < k;
+    const int kc = std::max(0, (k - crank + cs - 1) / cs);  // this CTA's right-hand sides: crank + cs j
+    for (int c0 = 0; c0 < kc; c0 += RW) {
+      const bool act = c0 + warp < kc;
+      const int c = crank + cs * (c0 + warp);
       if (act) {
         const double* bc = A + (long long)(n + c) * ld;
         for (int i = lane; i < rank; i += 32) y[i] = bc[i];
@@ -545,10 +586,12 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.info + b, 1);
   }
-  if (tid == 0) {
+  if (crank == 0 && tid == 0) {
     a.rank[b] = rank;
     if (s_bad) atomicOr(a.info + b, 1);
   }
+  // no CTA leaves while another may still read CTA 0's shared memory
+  if (cs > 1) cg::this_cluster().sync();
 }
 
 }  // namespace
@@ -560,10 +603,36 @@ size_t rqr_smem_bytes(int ld, int nmax) {
   return (wsz + (size_t)(ld + 3) / 4 + RSMALL) * sizeof(double);
 }
 
-int rqr_solve_batched(const QRBatch& q, cudaStream_t st) {
+// Clusters of cs CTAs of the blocked kernel that fit on the device at once.
+int rqr_active_clusters(size_t shm, int cs, int nb) {
+  if (cudaFuncSetAttribute(rqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(std::max(nb, 1) * cs));
+  cfg.blockDim = dim3(RT);
+  cfg.dynamicSmemBytes = shm;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int act = 0;
+  if (cudaOccupancyMaxActiveClusters(&act, rqr_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return act;
+}
+
+int rqr_solve_batched(const QRBatch& q, cudaStream_t st, int cs) {
   const int nmax = q.nmax;
   const size_t wsz = std::max<size_t>({(size_t)RB * q.ld, (size_t)RL * nmax, (size_t)RW * nmax});
   const size_t shm = rqr_smem_bytes(q.ld, nmax);
+  if (cs < 1 || cs > 8) { set_last_error("blocked QR: cluster size must lie in 1..8"); return LMFS_ERR_INVALID; }
   if (cuda_failed(cudaFuncSetAttribute(rqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm),
                   "rqr smem attribute"))
     return LMFS_ERR_CUDA;
@@ -592,9 +661,27 @@ int rqr_solve_batched(const QRBatch& q, cudaStream_t st) {
   a.X = q.X; a.xld = q.xld; a.xstride = q.xstride; a.rank = q.rank; a.perm = q.perm;
   a.permstride = q.permstride; a.info = q.info; a.Yg = Yg; a.ysd = nmax; a.order = order;
   a.wsz = (int)wsz;
+  a.cs = cs;
   if (q.ev) cudaEventRecord(q.ev[0], st);
-  rqr_kernel<<<q.nb, RT, shm, st>>>(a);
-  rc = check_launch("rqr_kernel");
+  if (cs == 1) {
+    rqr_kernel<<<q.nb, RT, shm, st>>>(a);
+    rc = check_launch("rqr_kernel");
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(q.nb * cs));
+    cfg.blockDim = dim3(RT);
+    cfg.dynamicSmemBytes = shm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    rc = cuda_failed(cudaLaunchKernelEx(&cfg, rqr_kernel, a), "rqr cluster launch") ? LMFS_ERR_CUDA
+                                                                                      : check_launch("rqr_kernel");
+  }
   if (q.ev) { cudaEventRecord(q.ev[1], st); cudaEventRecord(q.ev[2], st); }
   dfree(Yg);
   dfree(order);

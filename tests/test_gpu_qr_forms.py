@@ -39,22 +39,29 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def solver(L, monkeypatch, path, pk, problem, **kw):
+def solver(L, monkeypatch, path, pk, problem, cs=None, **kw):
     monkeypatch.setenv("LMFS_QR_PATH", path)
+    if cs:
+        monkeypatch.setenv("LMFS_QR_CS", cs)
     s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, **kw))
     s.precompute(problem)
     monkeypatch.delenv("LMFS_QR_PATH")
+    if cs:
+        monkeypatch.delenv("LMFS_QR_CS")
     return s
 
 
+@pytest.mark.parametrize("cs", ["1", "2"])
 @pytest.mark.parametrize("problem", ["mobility", "resistance"])
-def test_blocked_qr_pair_blocks_against_oracle(L, monkeypatch, problem):
+def test_blocked_qr_pair_blocks_against_oracle(L, monkeypatch, problem, cs):
     """P = 100 packing (37 close pairs): on 8 sampled pairs E and C A of the
-    blocked form against the oracle's SVD blocks within 1e-5, as the cluster
-    form's are; the fine ranks of the two forms within a few columns."""
+    blocked form -- one CTA per system, and two CTAs (a cluster) per system,
+    the form of mid-size batches -- against the oracle's SVD blocks within
+    1e-5, as the cluster form's are; the fine ranks of the forms within a few
+    columns."""
     code = L.MOBILITY if problem == "mobility" else L.RESISTANCE
     pk = w.packing_p100()
-    sb = solver(L, monkeypatch, "blocked", pk, code)
+    sb = solver(L, monkeypatch, "blocked", pk, code, cs=cs)
     sc = solver(L, monkeypatch, "cluster", pk, code)
     Ab, Eb = sb.pair_blocks(code)
     Ac, Ec = sc.pair_blocks(code)
@@ -68,7 +75,7 @@ def test_blocked_qr_pair_blocks_against_oracle(L, monkeypatch, problem):
         for name, A, E in (("blocked", Ab, Eb), ("cluster", Ac, Ec)):
             worst[name][0] = max(worst[name][0], rel(E[q], b["E"]))
             worst[name][1] = max(worst[name][1], rel(b["C"] @ A[q], b["C"] @ b["A"]))
-    print(f"{problem}: E, C A vs oracle: blocked {worst['blocked'][0]:.2e} {worst['blocked'][1]:.2e}, "
+    print(f"{problem}, {cs} CTA(s) per system: E, C A vs oracle: blocked {worst['blocked'][0]:.2e} {worst['blocked'][1]:.2e}, "
           f"cluster {worst['cluster'][0]:.2e} {worst['cluster'][1]:.2e}; rank F blocked "
           f"[{stb['min_rank_F']:.0f}, {stb['max_rank_F']:.0f}] cluster [{stc['min_rank_F']:.0f}, {stc['max_rank_F']:.0f}]; "
           f"QR ms blocked {stb['qr_ms']:.1f} cluster {stc['qr_ms']:.1f}")
