@@ -1,12 +1,13 @@
 // Blocked Householder QR with the pivots chosen on a random sketch, and the
-// truncated basic least-squares solution, in FP64: one matrix per CTA.
+// truncated basic least-squares solution, in FP64: one matrix per CTA, or per
+// thread-block cluster of cs CTAs.
 //
 // The column-pivoted QR of lmfs_qr.cu chooses every pivot from the updated
 // norms of all remaining columns, so each reflector is applied to the whole
 // trailing matrix before the next pivot is known: one pass over the trailing
 // matrix (and two cluster barriers) per reflector.  Here the pivots of a
 // block of RB columns are chosen at once by a column-pivoted QR of a small
-// sketch Y = Omega A (RL = RB + 8 rows, Omega of random signs), as in
+// sketch Y = Omega A (RL = RB + 8 rows, Omega a sparse sign matrix), as in
 // randomized QRCP (Martinsson, Quintana-Orti, Heavner, van de Geijn, "HQRRP",
 // 2017; Duersch and Gu, 2017); the block is factored without pivoting, and
 // its RB reflectors are applied to the trailing columns -- the remaining
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   __shared__ double s_r00, s_scale;
   __shared__ double s_rdi[RB];
 
-  // ---- sketch, squared column norms, identity permutation
+  // ---- sketch and identity permutation
   for (int i = tid; i < m; i += RT) om[i] = (unsigned short)row_signs((unsigned)i);
   if (crank == 0)
     for (int c = tid; c < n; c += RT) perm[c] = c;
@@ -170,225 +171,225 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     const int bb = min(RB, min(nt, m - s));
     double* Vs = W;                                       // [RB][ld]: Vs[t * ld + i], rows s..m-1
     if (crank == 0) {
-    // ---- pivots of this block: column-pivoted QR of the sketch's trailing
-    // columns, on an FP32 copy (the pivot order needs no more; the FP64 pipe
-    // stays with the other CTA's updates)
-    {
-      float* Ys = (float*)W;                              // [RL][nt]: Ys[j * nt + c]
-      for (int e = tid; e < RL * nt; e += RT) {
-        const int j = e / nt, c = e - j * nt;
-        Ys[e] = (float)Yg[(long long)j * ysd + s + c];
-      }
-      __syncthreads();
-      __shared__ float s_taup, s_scalep;
-      for (int t = 0; t < bb; ++t) {
-        float bv = -1.0f;
-        int bi = 0x7fffffff;
-        for (int c = t + tid; c < nt; c += RT) {
-          float v = 0.0f;
-#pragma unroll
-          for (int j = 0; j < RL; ++j)
-            if (j >= t) v = fmaf(Ys[j * nt + c], Ys[j * nt + c], v);
-          if (v > bv) { bv = v; bi = c; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-        }
-        float* redf = (float*)red;
-        if (lane == 0) { redf[warp] = bv; ((int*)(red + RW))[warp] = bi; }
-        __syncthreads();
-        if (tid == 0) {
-          float v = redf[0];
-          int q = ((int*)(red + RW))[0];
-          for (int ww = 1; ww < RW; ++ww) {
-            const float ov = redf[ww];
-            const int oi = ((int*)(red + RW))[ww];
-            if (ov > v || (ov == v && oi < q)) { v = ov; q = oi; }
-          }
-          s_q = (q >= t && q < nt) ? q : t;
-          s_pv[t] = s_q;
-        }
-        __syncthreads();
-        const int q = s_q;
-        if (q != t && tid < RL) {
-          const float x = Ys[tid * nt + t];
-          Ys[tid * nt + t] = Ys[tid * nt + q];
-          Ys[tid * nt + q] = x;
-        }
-        __syncthreads();
-        // Householder vector of Ys[t:RL, t] (kept in place, unit entry implicit)
-        if (tid == 0) {
-          const float alpha = Ys[t * nt + t];
-          float sig2 = 0.0f;
-          for (int j = t + 1; j < RL; ++j) sig2 = fmaf(Ys[j * nt + t], Ys[j * nt + t], sig2);
-          const float nrm = sqrtf(alpha * alpha + sig2);
-          if (nrm == 0.0f || !(nrm == nrm) || isinf(nrm)) {
-            s_taup = 0.0f;
-          } else {
-            const float beta = alpha >= 0.0f ? -nrm : nrm;
-            s_taup = (beta - alpha) / beta;
-            s_scalep = 1.0f / (alpha - beta);
-            Ys[t * nt + t] = beta;
-            for (int j = t + 1; j < RL; ++j) Ys[j * nt + t] *= s_scalep;
-          }
-        }
-        __syncthreads();
-        const float tau = s_taup;
-        if (tau != 0.0f) {
-          for (int c = t + 1 + tid; c < nt; c += RT) {
-            float d = Ys[t * nt + c];
-#pragma unroll
-            for (int j = 0; j < RL; ++j)
-              if (j > t) d = fmaf(Ys[j * nt + t], Ys[j * nt + c], d);
-            d *= tau;
-            Ys[t * nt + c] -= d;
-#pragma unroll
-            for (int j = 0; j < RL; ++j)
-              if (j > t) Ys[j * nt + c] = fmaf(-d, Ys[j * nt + t], Ys[j * nt + c]);
-          }
-        }
-        __syncthreads();
-      }
-      // the same exchanges, in the same order, on the matrix, the sketch and
-      // the permutation
-      for (int t = 0; t < bb; ++t) {
-        const int q = s_pv[t];
-        if (q != t) {
-          double* c1 = A + (long long)(s + t) * ld;
-          double* c2 = A + (long long)(s + q) * ld;
-          for (int i = tid; i < m; i += RT) { const double x = c1[i]; c1[i] = c2[i]; c2[i] = x; }
-          if (tid < RL) {
-            double* y = Yg + (long long)tid * ysd + s;
-            const double x = y[t]; y[t] = y[q]; y[q] = x;
-          }
-          if (tid == RL) {
-            const int pi = perm[s + t]; perm[s + t] = perm[s + q]; perm[s + q] = pi;
-          }
-        }
-        __syncthreads();
-      }
-    }
-    // ---- the block, factored without pivoting in shared memory
-    for (int t = 0; t < bb; ++t)
-      for (int i = s + tid; i < m; i += RT) Vs[t * ld + i] = A[(long long)(s + t) * ld + i];
-    if (tid == 0) s_bbe = bb;
-    __syncthreads();
-    for (int t = 0; t < bb; ++t) {
-      const int p = s + t;
-      double part[1] = {0.0};
-      for (int i = p + 1 + tid; i < m; i += RT) part[0] = fma(Vs[t * ld + i], Vs[t * ld + i], part[0]);
-      block_sums<1>(part, 1, red, sred);
-      if (tid == 0) {
-        const double alpha = Vs[t * ld + p];
-        const double nrm = sqrt(alpha * alpha + sred[0]);
-        if (p == 0) s_r00 = nrm;
-        if (!(nrm == nrm) || isinf(nrm)) s_bad = 1;
-        if (nrm <= a.eps * s_r00 || nrm == 0.0 || s_bad) {
-          s_stop = 1;
-          s_bbe = t;
-        } else {
-          const double beta = alpha >= 0.0 ? -nrm : nrm;
-          stau[t] = (beta - alpha) / beta;
-          sbeta[t] = beta;
-          s_scale = 1.0 / (alpha - beta);
-        }
-      }
-      __syncthreads();
-      if (s_stop) break;
+      // ---- pivots of this block: column-pivoted QR of the sketch's trailing
+      // columns, on an FP32 copy (the pivot order needs no more; the FP64 pipe
+      // stays with the other CTA's updates)
       {
-        const double sc = s_scale;
-        for (int i = p + 1 + tid; i < m; i += RT) Vs[t * ld + i] *= sc;
-        if (tid == 0) Vs[t * ld + p] = 1.0;
+        float* Ys = (float*)W;                              // [RL][nt]: Ys[j * nt + c]
+        for (int e = tid; e < RL * nt; e += RT) {
+          const int j = e / nt, c = e - j * nt;
+          Ys[e] = (float)Yg[(long long)j * ysd + s + c];
+        }
+        __syncthreads();
+        __shared__ float s_taup, s_scalep;
+        for (int t = 0; t < bb; ++t) {
+          float bv = -1.0f;
+          int bi = 0x7fffffff;
+          for (int c = t + tid; c < nt; c += RT) {
+            float v = 0.0f;
+  #pragma unroll
+            for (int j = 0; j < RL; ++j)
+              if (j >= t) v = fmaf(Ys[j * nt + c], Ys[j * nt + c], v);
+            if (v > bv) { bv = v; bi = c; }
+          }
+  #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+          }
+          float* redf = (float*)red;
+          if (lane == 0) { redf[warp] = bv; ((int*)(red + RW))[warp] = bi; }
+          __syncthreads();
+          if (tid == 0) {
+            float v = redf[0];
+            int q = ((int*)(red + RW))[0];
+            for (int ww = 1; ww < RW; ++ww) {
+              const float ov = redf[ww];
+              const int oi = ((int*)(red + RW))[ww];
+              if (ov > v || (ov == v && oi < q)) { v = ov; q = oi; }
+            }
+            s_q = (q >= t && q < nt) ? q : t;
+            s_pv[t] = s_q;
+          }
+          __syncthreads();
+          const int q = s_q;
+          if (q != t && tid < RL) {
+            const float x = Ys[tid * nt + t];
+            Ys[tid * nt + t] = Ys[tid * nt + q];
+            Ys[tid * nt + q] = x;
+          }
+          __syncthreads();
+          // Householder vector of Ys[t:RL, t] (kept in place, unit entry implicit)
+          if (tid == 0) {
+            const float alpha = Ys[t * nt + t];
+            float sig2 = 0.0f;
+            for (int j = t + 1; j < RL; ++j) sig2 = fmaf(Ys[j * nt + t], Ys[j * nt + t], sig2);
+            const float nrm = sqrtf(alpha * alpha + sig2);
+            if (nrm == 0.0f || !(nrm == nrm) || isinf(nrm)) {
+              s_taup = 0.0f;
+            } else {
+              const float beta = alpha >= 0.0f ? -nrm : nrm;
+              s_taup = (beta - alpha) / beta;
+              s_scalep = 1.0f / (alpha - beta);
+              Ys[t * nt + t] = beta;
+              for (int j = t + 1; j < RL; ++j) Ys[j * nt + t] *= s_scalep;
+            }
+          }
+          __syncthreads();
+          const float tau = s_taup;
+          if (tau != 0.0f) {
+            for (int c = t + 1 + tid; c < nt; c += RT) {
+              float d = Ys[t * nt + c];
+  #pragma unroll
+              for (int j = 0; j < RL; ++j)
+                if (j > t) d = fmaf(Ys[j * nt + t], Ys[j * nt + c], d);
+              d *= tau;
+              Ys[t * nt + c] -= d;
+  #pragma unroll
+              for (int j = 0; j < RL; ++j)
+                if (j > t) Ys[j * nt + c] = fmaf(-d, Ys[j * nt + t], Ys[j * nt + c]);
+            }
+          }
+          __syncthreads();
+        }
+        // the same exchanges, in the same order, on the matrix, the sketch and
+        // the permutation
+        for (int t = 0; t < bb; ++t) {
+          const int q = s_pv[t];
+          if (q != t) {
+            double* c1 = A + (long long)(s + t) * ld;
+            double* c2 = A + (long long)(s + q) * ld;
+            for (int i = tid; i < m; i += RT) { const double x = c1[i]; c1[i] = c2[i]; c2[i] = x; }
+            if (tid < RL) {
+              double* y = Yg + (long long)tid * ysd + s;
+              const double x = y[t]; y[t] = y[q]; y[q] = x;
+            }
+            if (tid == RL) {
+              const int pi = perm[s + t]; perm[s + t] = perm[s + q]; perm[s + q] = pi;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      // ---- the block, factored without pivoting in shared memory
+      for (int t = 0; t < bb; ++t)
+        for (int i = s + tid; i < m; i += RT) Vs[t * ld + i] = A[(long long)(s + t) * ld + i];
+      if (tid == 0) s_bbe = bb;
+      __syncthreads();
+      for (int t = 0; t < bb; ++t) {
+        const int p = s + t;
+        double part[1] = {0.0};
+        for (int i = p + 1 + tid; i < m; i += RT) part[0] = fma(Vs[t * ld + i], Vs[t * ld + i], part[0]);
+        block_sums<1>(part, 1, red, sred);
+        if (tid == 0) {
+          const double alpha = Vs[t * ld + p];
+          const double nrm = sqrt(alpha * alpha + sred[0]);
+          if (p == 0) s_r00 = nrm;
+          if (!(nrm == nrm) || isinf(nrm)) s_bad = 1;
+          if (nrm <= a.eps * s_r00 || nrm == 0.0 || s_bad) {
+            s_stop = 1;
+            s_bbe = t;
+          } else {
+            const double beta = alpha >= 0.0 ? -nrm : nrm;
+            stau[t] = (beta - alpha) / beta;
+            sbeta[t] = beta;
+            s_scale = 1.0 / (alpha - beta);
+          }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        {
+          const double sc = s_scale;
+          for (int i = p + 1 + tid; i < m; i += RT) Vs[t * ld + i] *= sc;
+          if (tid == 0) Vs[t * ld + p] = 1.0;
+        }
+        __syncthreads();
+        const int nu = bb - 1 - t;
+        if (nu > 0) {
+          double d[RB - 1];
+  #pragma unroll
+          for (int u = 0; u < RB - 1; ++u) d[u] = 0.0;
+          for (int i = p + tid; i < m; i += RT) {
+            const double v = Vs[t * ld + i];
+  #pragma unroll
+            for (int u = 0; u < RB - 1; ++u)
+              if (u < nu) d[u] = fma(v, Vs[(t + 1 + u) * ld + i], d[u]);
+          }
+          block_sums<RB - 1>(d, nu, red, sred);
+          const double tau = stau[t];
+          for (int i = p + tid; i < m; i += RT) {
+            const double v = Vs[t * ld + i];
+  #pragma unroll
+            for (int u = 0; u < RB - 1; ++u)
+              if (u < nu) Vs[(t + 1 + u) * ld + i] = fma(-tau * sred[u], v, Vs[(t + 1 + u) * ld + i]);
+          }
+          __syncthreads();
+        }
+      }
+      const int bbe = s_bbe;
+      const bool stopped = s_stop != 0;
+      // write the block back (R above and on the diagonal, V below), keep R_11,
+      // and leave V unit lower trapezoidal in shared memory
+      for (int t = 0; t < bbe; ++t) {
+        const int p = s + t;
+        double* col = A + (long long)p * ld;
+        for (int i = s + tid; i < m; i += RT) col[i] = (i == p) ? sbeta[t] : Vs[t * ld + i];
+      }
+      if (tid < RB * RB) {
+        const int u = tid / RB, t = tid - u * RB;
+        R11[tid] = (u < bbe && t < bbe) ? (u < t ? Vs[t * ld + s + u] : (u == t ? sbeta[t] : 0.0)) : 0.0;
       }
       __syncthreads();
-      const int nu = bb - 1 - t;
-      if (nu > 0) {
-        double d[RB - 1];
-#pragma unroll
-        for (int u = 0; u < RB - 1; ++u) d[u] = 0.0;
-        for (int i = p + tid; i < m; i += RT) {
-          const double v = Vs[t * ld + i];
-#pragma unroll
-          for (int u = 0; u < RB - 1; ++u)
-            if (u < nu) d[u] = fma(v, Vs[(t + 1 + u) * ld + i], d[u]);
+      for (int t = 0; t < bbe; ++t)
+        for (int i = s + tid; i < s + t; i += RT) Vs[t * ld + i] = 0.0;
+      __syncthreads();
+      // ---- T of the compact WY form, H_0 ... H_{bbe-1} = I - V T V^T, from the Gram matrix of V
+      if (bbe > 0) {
+        double g[RB * (RB - 1) / 2];
+  #pragma unroll
+        for (int q = 0; q < RB * (RB - 1) / 2; ++q) g[q] = 0.0;
+        for (int i = s + tid; i < m; i += RT) {
+          double v[RB];
+  #pragma unroll
+          for (int u = 0; u < RB; ++u) v[u] = (u < bbe) ? Vs[u * ld + i] : 0.0;
+  #pragma unroll
+          for (int t = 1; t < RB; ++t)
+  #pragma unroll
+            for (int u = 0; u < t; ++u) g[t * (t - 1) / 2 + u] = fma(v[u], v[t], g[t * (t - 1) / 2 + u]);
         }
-        block_sums<RB - 1>(d, nu, red, sred);
-        const double tau = stau[t];
-        for (int i = p + tid; i < m; i += RT) {
-          const double v = Vs[t * ld + i];
-#pragma unroll
-          for (int u = 0; u < RB - 1; ++u)
-            if (u < nu) Vs[(t + 1 + u) * ld + i] = fma(-tau * sred[u], v, Vs[(t + 1 + u) * ld + i]);
+        block_sums<RB * (RB - 1) / 2>(g, RB * (RB - 1) / 2, red, sred);
+        // T column by column on warp 0 (lane u < t: T[u][t] = -tau_t sum_{w=u}^{t-1}
+        // T[u][w] (v_w . v_t)); G2 row by row on warp 1, with the reciprocal diagonal
+        if (warp == 0) {
+          if (lane < RB) {
+            for (int e = lane; e < RB * RB; e += RB) T[e] = 0.0;
+          }
+          __syncwarp();
+          for (int t = 0; t < bbe; ++t) {
+            const int q0 = t * (t - 1) / 2;
+            if (lane < t) {
+              double acc = 0.0;
+              for (int w2 = lane; w2 < t; ++w2) acc = fma(T[lane * RB + w2], sred[q0 + w2], acc);
+              T[lane * RB + t] = -stau[t] * acc;
+            }
+            if (lane == t) T[t * RB + t] = stau[t];
+            __syncwarp();
+          }
+        } else if (warp == 1 && !stopped) {
+          if (lane < bbe) s_rdi[lane] = 1.0 / R11[lane * RB + lane];
+          __syncwarp();
+          if (lane < RL) {
+            const int j = lane;
+            for (int t = 0; t < bbe; ++t) {
+              double acc = Yg[(long long)j * ysd + s + t];
+              for (int u = 0; u < t; ++u) acc = fma(-G2[j * RB + u], R11[u * RB + t], acc);
+              G2[j * RB + t] = acc * s_rdi[t];
+            }
+          }
         }
         __syncthreads();
       }
-    }
-    const int bbe = s_bbe;
-    const bool stopped = s_stop != 0;
-    // write the block back (R above and on the diagonal, V below), keep R_11,
-    // and leave V unit lower trapezoidal in shared memory
-    for (int t = 0; t < bbe; ++t) {
-      const int p = s + t;
-      double* col = A + (long long)p * ld;
-      for (int i = s + tid; i < m; i += RT) col[i] = (i == p) ? sbeta[t] : Vs[t * ld + i];
-    }
-    if (tid < RB * RB) {
-      const int u = tid / RB, t = tid - u * RB;
-      R11[tid] = (u < bbe && t < bbe) ? (u < t ? Vs[t * ld + s + u] : (u == t ? sbeta[t] : 0.0)) : 0.0;
-    }
-    __syncthreads();
-    for (int t = 0; t < bbe; ++t)
-      for (int i = s + tid; i < s + t; i += RT) Vs[t * ld + i] = 0.0;
-    __syncthreads();
-    // ---- T of the compact WY form, H_0 ... H_{bbe-1} = I - V T V^T, from the Gram matrix of V
-    if (bbe > 0) {
-      double g[RB * (RB - 1) / 2];
-#pragma unroll
-      for (int q = 0; q < RB * (RB - 1) / 2; ++q) g[q] = 0.0;
-      for (int i = s + tid; i < m; i += RT) {
-        double v[RB];
-#pragma unroll
-        for (int u = 0; u < RB; ++u) v[u] = (u < bbe) ? Vs[u * ld + i] : 0.0;
-#pragma unroll
-        for (int t = 1; t < RB; ++t)
-#pragma unroll
-          for (int u = 0; u < t; ++u) g[t * (t - 1) / 2 + u] = fma(v[u], v[t], g[t * (t - 1) / 2 + u]);
-      }
-      block_sums<RB * (RB - 1) / 2>(g, RB * (RB - 1) / 2, red, sred);
-      // T column by column on warp 0 (lane u < t: T[u][t] = -tau_t sum_{w=u}^{t-1}
-      // T[u][w] (v_w . v_t)); G2 row by row on warp 1, with the reciprocal diagonal
-      if (warp == 0) {
-        if (lane < RB) {
-          for (int e = lane; e < RB * RB; e += RB) T[e] = 0.0;
-        }
-        __syncwarp();
-        for (int t = 0; t < bbe; ++t) {
-          const int q0 = t * (t - 1) / 2;
-          if (lane < t) {
-            double acc = 0.0;
-            for (int w2 = lane; w2 < t; ++w2) acc = fma(T[lane * RB + w2], sred[q0 + w2], acc);
-            T[lane * RB + t] = -stau[t] * acc;
-          }
-          if (lane == t) T[t * RB + t] = stau[t];
-          __syncwarp();
-        }
-      } else if (warp == 1 && !stopped) {
-        if (lane < bbe) s_rdi[lane] = 1.0 / R11[lane * RB + lane];
-        __syncwarp();
-        if (lane < RL) {
-          const int j = lane;
-          for (int t = 0; t < bbe; ++t) {
-            double acc = Yg[(long long)j * ysd + s + t];
-            for (int u = 0; u < t; ++u) acc = fma(-G2[j * RB + u], R11[u * RB + t], acc);
-            G2[j * RB + t] = acc * s_rdi[t];
-          }
-        }
-      }
-      __syncthreads();
-    }
     }  // CTA 0's stages
     csync();
     // every CTA: CTA 0's block size and stop, then its V, T and G2
