@@ -99,10 +99,11 @@ class Clocks:
 # DRAM traffic of the blocked QR kernel (rqr_kernel) per fine half system:
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of its launch
 # on the 398 fine half systems of `LMFS_QR_PATH=blocked bench.py --profile-case
-# qr_mid` (P = 160, area fraction 0.65), divided by 398.  Valid only for the kernel source it was
+# qr_mid` (P = 160, area fraction 0.65; LMFS_QR_CS=1, one CTA per system as in
+# the P = 10^4 launches), divided by 398.  Valid only for the kernel source it was
 # taken on: reported as null once lmfs_rqr.cu changes.
-RQR_TRAFFIC_PER_MATRIX = (74.87e9 + 38.27e9) / 398.0
-RQR_TRAFFIC_SRC_SHA256 = "d8a729861d5dcc5497af7d651e6ea3a43b089b818e7af5c3fc3a5ef3f0105620"
+RQR_TRAFFIC_PER_MATRIX = (75.00e9 + 38.36e9) / 398.0
+RQR_TRAFFIC_SRC_SHA256 = "5c5d3b172db11fb05cfe5408d8b7f6fc4a79bbd90a8fca10683cf75dbfca73f5"
 
 
 def rqr_traffic_per_matrix():
