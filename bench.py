@@ -96,24 +96,34 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
-# DRAM traffic of the blocked QR kernel (rqr_kernel) per fine half system:
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of its launch
-# on the 398 fine half systems of `LMFS_QR_PATH=blocked bench.py --profile-case
-# qr_mid` (P = 160, area fraction 0.65; LMFS_QR_CS=1, one CTA per system as in
-# the P = 10^4 launches), divided by 398.  Valid only for the kernel source it was
-# taken on: reported as null once lmfs_rqr.cu changes.
-RQR_TRAFFIC_PER_MATRIX = (75.00e9 + 38.36e9) / 398.0
-RQR_TRAFFIC_SRC_SHA256 = "5c5d3b172db11fb05cfe5408d8b7f6fc4a79bbd90a8fca10683cf75dbfca73f5"
+# Counters of the blocked QR kernel (rqr_kernel, trailing updates on the
+# tensor cores) from one ncu capture of its launch on the 398 fine half
+# systems of `bench.py --profile-case qr_mid` (P = 160, area fraction 0.65,
+# one CTA per system as in the P = 10^4 launches): DRAM bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum) per system, and the launch's
+# algorithmic FP64 flops per ALU-pipe warp instruction
+# (sm__inst_executed_pipe_alu.sum), the pipe that carries the digit work.
+# Valid only for the kernel source they were taken on (lmfs_rqr.cu and
+# lmfs_emu64.cuh): reported as null once either changes.
+RQR_TRAFFIC_PER_MATRIX = (81.69e9 + 40.07e9) / 398.0
+RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.4696552e10
+RQR_SRC_SHA256 = "e93424e09edb2dfb903381467820d3e7315bdd35708283fd98c70c883e9edb4f"
+ALU_WARP_INST_PER_CLK = 2          # 64 results per clock per SM for 32-bit integer add, logic and shift
+
+
+def rqr_counters_valid():
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in ("lmfs_rqr.cu", "lmfs_emu64.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2606_11273_gb300", "csrc", f), "rb").read())
+    except OSError:
+        return False
+    return h.hexdigest() == RQR_SRC_SHA256
 
 
 def rqr_traffic_per_matrix():
-    import hashlib
-    src = os.path.join(ROOT, "paper_2606_11273_gb300", "csrc", "lmfs_rqr.cu")
-    try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    return RQR_TRAFFIC_PER_MATRIX if h == RQR_TRAFFIC_SRC_SHA256 else None
+    return RQR_TRAFFIC_PER_MATRIX if rqr_counters_valid() else None
 
 
 def dist_env():
@@ -528,6 +538,7 @@ def run_ours(args):
         fine_ms = float(np.mean([q["fine_ms"] for q in qr]))
         fine_tf = float(np.mean([q["fine_flops"] for q in qr])) / (fine_ms * 1e-3) / 1e12
         fine_blocked = all(q["fine_blocked"] > 0 for q in qr)
+        fine_emu = all(q["fine_blocked"] == 2 for q in qr)
         pre_ms = float(np.mean([q["precompute_ms"] for q in qr]))
         clocks = clk.summary()
         n_pairs = int(s.n_pairs)
@@ -579,19 +590,8 @@ def run_ours(args):
             "autotune": tune,
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu",
-                         "kernel": ("rqr_kernel (blocked FP64 QR of the fine pair systems, pivots from a random "
-                                    "sketch, right-hand sides in the same sweep)" if fine_blocked else
-                                    "qrcp_kernel + apply_qt_kernel (pivoted FP64 QR of the fine pair systems)"),
-                         "achieved": fine_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s (FP64)",
-                         "frac": fine_tf / fp64_peak_tf, "traffic": traffic,
-                         "algorithmic_flops_per_step": float(np.mean([q["fine_flops"] for q in qr])),
-                         "traffic_note": "DRAM bytes per step: the ncu capture of rqr_kernel on 398 fine half "
-                                         "systems (P = 160), per system, times the 20940 of the step; null if "
-                                         "the kernel changed since",
-                         "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (no FP64 figure "
-                                      "in the measured peaks)",
-                         "kernel_ms_per_step": fine_ms, "share_of_step": fine_ms / (t_ms / args.steps)},
+            "roofline": rqr_roofline(fine_emu, fine_blocked, fine_tf, fp64_peak_tf, sm_max, traffic,
+                                     float(np.mean([q["fine_flops"] for q in qr])), fine_ms, t_ms / args.steps),
             "qr_all_stages": {"factor_ms": fac_ms, "factor_tflops": fac_tf, "rhs_ms": rhs_ms, "rhs_tflops": rhs_tf,
                               "note": "all pair QR launches of a step, fine and peanut systems: the blocked form "
                                       "(rqr_kernel, launches of >= 1216 systems; counted as factorization) or the "
@@ -615,6 +615,38 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return result
+
+
+def rqr_roofline(fine_emu, fine_blocked, fine_tf, fp64_peak_tf, sm_max, traffic, flops, fine_ms, step_ms):
+    """Roofline of the fine systems' QR.  With FP64 trailing updates it is
+    bound by the FP64 pipe; with the updates as exact bf16 digit products on
+    the tensor cores the FP64 pipe no longer bounds it (it runs above that
+    pipe's peak in FP64-equivalent flops), and the bound is the ALU pipe,
+    which carries the digit extraction and the integer assembly of the
+    products: the ceiling is the algorithm's flops per ALU warp instruction
+    (from the capture) at the ALU pipe's full rate."""
+    base = {"achieved": fine_tf, "traffic": traffic, "algorithmic_flops_per_step": flops,
+            "traffic_note": "DRAM bytes per step: the ncu capture of rqr_kernel on 398 fine half systems "
+                            "(P = 160), per system, times the 20940 of the step; null if the kernel changed since",
+            "kernel_ms_per_step": fine_ms, "share_of_step": fine_ms / step_ms}
+    if fine_emu:
+        fpi = RQR_FLOPS_PER_ALU_INST if rqr_counters_valid() else None
+        peak = fpi * 152 * ALU_WARP_INST_PER_CLK * sm_max * 1e6 / 1e12 if fpi else None
+        return {"bound": "alu", "kernel": "rqr_kernel (blocked QR of the fine pair systems, pivots from a random "
+                                          "sketch; trailing updates as exact bf16 digit products on the tensor "
+                                          "cores, FP64-class)",
+                "unit": "TFLOP/s (FP64-equivalent: the algorithm's FP64 flops)", "peak": peak,
+                "frac": fine_tf / peak if peak else None, **base,
+                "vs_fp64_pipe_peak": fine_tf / fp64_peak_tf,
+                "peak_note": "derived: the launch's algorithmic flops per ALU-pipe warp instruction (ncu, P = 160 "
+                             "capture) x 152 SMs x 2 ALU warp instructions per clock x max SM clock; "
+                             "vs_fp64_pipe_peak compares with the FP64 pipe (152 x 2 FMA/clk x 2 x max clock)"}
+    return {"bound": "alu", "kernel": ("rqr_kernel (blocked FP64 QR of the fine pair systems, pivots from a random "
+                                       "sketch, right-hand sides in the same sweep)" if fine_blocked else
+                                       "qrcp_kernel + apply_qt_kernel (pivoted FP64 QR of the fine pair systems)"),
+            "unit": "TFLOP/s (FP64)", "peak": fp64_peak_tf, "frac": fine_tf / fp64_peak_tf, **base,
+            "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (no FP64 figure in the "
+                         "measured peaks)"}
 
 
 def tune_summary(rows):
@@ -989,12 +1021,15 @@ def run_profile_case(case):
         s.precompute(L.MOBILITY)
         torch.cuda.synchronize()
     elif case == "qr_mid":
-        # P = 160 at area fraction 0.65: ~350 fine half systems, one launch
+        # P = 160 at area fraction 0.65: 398 fine half systems, one launch
         import workloads as w
         pk = w.packing(160, 0.65, 5, gmin=1e-3)
         s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))
         s.precompute(L.MOBILITY)
         torch.cuda.synchronize()
+        st = s.stats(L.MOBILITY)
+        print(f"qr_mid: {2 * s.n_pairs} fine half systems, fine QR {st['fine_ms']:.2f} ms, "
+              f"{st['fine_flops']:.6e} algorithmic flops, form {st['fine_blocked']:.0f}")
     elif case in ("qr", "matvec"):
         pk, ft = workload("p100_phi040_mobility")
         s = L.Solver(pk.centres, pk.radii, L.Params(precision=L.MIXED, stream=stream.cuda_stream))

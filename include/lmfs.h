@@ -251,7 +251,9 @@ int lmfs_stats(lmfs_handle h, int problem, double* out);
  * (4 (m - s) k per reflector plus k rank^2 for the back substitution), the
  * fine systems' QR stage ms, its flops (both parts), 1 if that stage ran the
  * blocked QR with sketch pivoting (which updates the right-hand sides in the
- * factorization's sweep, so its flops count as factorization) else 0}.  HOST
+ * factorization's sweep, so its flops count as factorization) with FP64
+ * trailing updates, 2 if with the trailing updates as exact digit products on
+ * the tensor cores, else 0 (the pivoted cluster form)}.  HOST
  * array; zeros before the first precompute.  No counterpart in the paper: a
  * measurement hook. */
 int lmfs_qr_stats(lmfs_handle h, int problem, double* out);

@@ -883,7 +883,7 @@ int lmfs_qr_stats(lmfs_handle h, int problem, double* out) {
   if (!h || !out || (problem != LMFS_RESISTANCE && problem != LMFS_MOBILITY)) return LMFS_ERR_INVALID;
   const PairBlocks& pb = h->c.prob[problem];
   out[0] = pb.fac_ms; out[1] = pb.fac_flops; out[2] = pb.rhs_ms; out[3] = pb.rhs_flops;
-  out[4] = pb.fine_ms; out[5] = pb.fine_flops; out[6] = pb.fine_blocked ? 1.0 : 0.0;
+  out[4] = pb.fine_ms; out[5] = pb.fine_flops; out[6] = (double)pb.fine_blocked;
   return LMFS_OK;
 }
 

@@ -64,7 +64,8 @@ struct PairBlocks {
   double fac_ms = 0.0, fac_flops = 0.0;   // of which the pivoted factorizations (qrcp_kernel)
   double rhs_ms = 0.0, rhs_flops = 0.0;   // and the right-hand sides (apply_qt_kernel)
   double fine_ms = 0.0, fine_flops = 0.0; // the fine systems' QR stage alone (either form)
-  bool fine_blocked = false;              // ... solved by the blocked form (rqr_kernel)
+  int fine_blocked = 0;                   // ... solved by the blocked form (rqr_kernel): 1 with FP64
+                                          // trailing updates, 2 with them on the tensor cores
   int max_rank_F = 0, min_rank_F = 0;
   // kept with lmfs_params.keep_fine (flowEval of Algorithm 2): per pair the
   // fine solution Z (mobility: (I - L_f) Z), column-major [4Nc cols][fine_ld
@@ -327,7 +328,8 @@ inline int pair_chunk(long long C, double per_pair) {
 }
 // The blocked QR with sketch pivoting (lmfs_rqr.cu): shared memory it needs,
 // and the batch solve itself (solve mode only).
-size_t rqr_smem_bytes(int ld, int nmax);
+size_t rqr_smem_bytes(int ld, int nmax, int k);
+bool rqr_emu_ok(const QRBatch& q);        // trailing updates on the tensor cores possible (one CTA per matrix)
 int rqr_active_clusters(size_t shm, int cs, int nb);
 int rqr_solve_batched(const QRBatch& q, cudaStream_t s, int cs);
 

@@ -1070,7 +1070,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   pb.min_rank_F = minr; pb.max_rank_F = maxr;
   pb.qr_ms = qr_ms; pb.qr_flops = qr_flops;
   pb.fac_ms = fac_ms; pb.fac_flops = fac_flops; pb.rhs_ms = rhs_ms; pb.rhs_flops = rhs_flops;
-  pb.fine_ms = fine_ms; pb.fine_flops = fine_flops; pb.fine_blocked = fine_blocked != 0;
+  pb.fine_ms = fine_ms; pb.fine_flops = fine_flops; pb.fine_blocked = fine_blocked;
   pb.t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 done:
   dfree(ws1); dfree(Z); dfree(Zp); dfree(D); dfree(ws2); dfree(X2); dfree(Yf); dfree(Xf); dfree(Zpts);

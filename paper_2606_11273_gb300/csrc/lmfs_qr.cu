@@ -566,21 +566,24 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (q.used_blocked) *q.used_blocked = 0;
-  // The blocked form (lmfs_rqr.cu) with one matrix per CTA for batches that
-  // fill at least four waves of two CTAs per SM (measured on the P = 10^4 fine
-  // systems: 2.1 waves per launch 10.2 s against the pivoted cluster form's
-  // 9.4 s, 5.7 waves 8.8 s; on its 1746 peanut systems of 200 rows 46 ms
-  // against 67 ms per launch), with two CTAs (a cluster) per matrix from one
-  // wave (P = 160 and 300 packings, 398 and 434 systems: 192 and 396 ms
-  // against 200 and 428 ms; one CTA 224 and 448 ms); below that the pivoted
-  // cluster form (P = 100, 74 systems: 40 ms, the blocked form 41 ms at best,
-  // with four CTAs per matrix).  LMFS_QR_PATH=blocked|cluster and
-  // LMFS_QR_CS=n override the choice (tests compare the forms).
+  // The blocked form (lmfs_rqr.cu).  With its trailing updates on the tensor
+  // cores (one matrix per CTA) it is the faster form from one matrix per SM
+  // (P = 160 packing, 398 fine systems: 94 ms against 192 ms for two FP64
+  // CTAs per matrix and 211 ms for one; P = 10^4: 3.5 s against 7.9 s); on
+  // smaller batches the pivoted cluster form (P = 100, 74 systems: 40 ms
+  // against 47 ms).  With FP64 updates: one matrix per CTA from four waves of
+  // two CTAs per SM (P = 10^4 fine systems: 2.1 waves per launch 10.2 s
+  // against the pivoted cluster form's 9.4 s, 5.7 waves 8.8 s), two CTAs (a
+  // cluster) per matrix from one wave (P = 160 and 300, 398 and 434 systems:
+  // 192 and 396 ms against 200 and 428 ms), and below that the pivoted cluster
+  // form.  LMFS_QR_PATH=blocked|cluster, LMFS_QR_CS=n and LMFS_QR_EMU=0
+  // override the choice (tests compare the forms).
   if (solve && q.k > 0) {
     const int path = qr_path_override();
-    const size_t shm = rqr_smem_bytes(q.ld, q.nmax);
+    const size_t shm = rqr_smem_bytes(q.ld, q.nmax, q.k);
     const bool fits = shm <= 226 * 1024;
-    int cs = q.nb >= 8 * sms ? 1 : (q.nb >= 2 * sms ? 2 : 0);
+    const bool emu = rqr_emu_ok(q);
+    int cs = emu ? (q.nb >= sms ? 1 : 0) : (q.nb >= 8 * sms ? 1 : (q.nb >= 2 * sms ? 2 : 0));
     if (const char* e = std::getenv("LMFS_QR_CS")) cs = std::max(1, std::min(8, std::atoi(e)));
     if (path == 1 && cs == 0) cs = 1;
     if (cs > 1 && rqr_active_clusters(shm, cs, q.nb) <= 0) cs = path == 1 ? 1 : 0;

@@ -36,6 +36,7 @@
 
 #include <cooperative_groups.h>
 
+#include "lmfs_emu64.cuh"
 #include "lmfs_internal.h"
 
 namespace lmfs {
@@ -55,6 +56,9 @@ struct RArgs {
   const int* order;                // matrix of cluster blockIdx.x / cs
   int wsz;                         // doubles of the shared work region
   int cs;                          // CTAs per matrix (a thread-block cluster when > 1)
+  int emu;                         // trailing updates on the tensor cores (lmfs_emu64.cuh); cs == 1
+  int64_t* Wsc;                    // [nb][16][wld] their scratch
+  int wld;                         // >= n + k
 };
 
 // The sketch's entries of row i: one of each group of four sketch rows
@@ -129,6 +133,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   double* stau = sbeta + RB;                              // [RB]
   double* red = stau + RB;                                // [RW * 32]
   double* sred = red + RW * 32;                           // [32] block results
+  int* cex = (int*)(smallp + RSMALL);                     // [n + k] column exponent bounds (emu)
   __shared__ int s_pv[RB];
   __shared__ int s_stop, s_bad, s_bbe, s_q;
   __shared__ double s_r00, s_scale;
@@ -145,8 +150,10 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     double acc[RL];
 #pragma unroll
     for (int j = 0; j < RL; ++j) acc[j] = 0.0;
+    int mx = 0;
     for (int i = 0; i < m; ++i) {
       const double x = col[i];
+      if (a.emu) mx = max(mx, emu::bexp(x));
       const unsigned msk = om[i];                         // the same for every lane: uniform branches
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
@@ -160,7 +167,15 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     }
 #pragma unroll
     for (int j = 0; j < RL; ++j) Yg[(long long)j * ysd + c] = acc[j];
+    if (a.emu) cex[c] = mx;
   }
+  if (a.emu)
+    for (int c = n + tid; c < n + k; c += RT) {
+      const double* col = A + (long long)c * ld;
+      int mx = 0;
+      for (int i = 0; i < m; ++i) mx = max(mx, emu::bexp(col[i]));
+      cex[c] = mx;
+    }
   csync();
 
   const int smax = min(m, n);
@@ -267,6 +282,9 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
             }
             if (tid == RL) {
               const int pi = perm[s + t]; perm[s + t] = perm[s + q]; perm[s + q] = pi;
+            }
+            if (tid == RL + 1 && a.emu) {
+              const int e = cex[s + t]; cex[s + t] = cex[s + q]; cex[s + q] = e;
             }
           }
           __syncthreads();
@@ -418,7 +436,28 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     // are enough columns for every thread), each taking every tpc-th chunk of
     // four rows; the reads of V are then shared-memory broadcasts, and a
     // column's V^T c needs no cross-lane sum unless tpc > 1.
-    {
+    if (a.emu) {
+      // the same product with exact digit products on the tensor cores
+      const int c0 = stopped ? n : s + bbe;
+      emu::block_update<RT>(A, ld, m, s, bbe, c0, n + k - c0, T, cex, a.Wsc + (long long)b * 16 * a.wld, a.wld,
+                            (uint32_t*)W, (int*)((uint32_t*)W + emu::UPD_DG));
+      if (!stopped)
+        for (int c = c0 + tid; c < n; c += RT) {
+          // sketch of this column: Y_2 <- Y_2 - G2 R_12
+          const double* col = A + (long long)c * ld;
+          double r12[RB];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) r12[t] = (t < bbe) ? col[s + t] : 0.0;
+          for (int j = 0; j < RL; ++j) {
+            double* y = Yg + (long long)j * ysd + c;
+            double acc = *y;
+#pragma unroll
+            for (int t = 0; t < RB; ++t)
+              if (t < bbe) acc = fma(-G2[j * RB + t], r12[t], acc);
+            *y = acc;
+          }
+        }
+    } else {
       const int c0 = stopped ? n : s + bbe;
       // this CTA's columns: c0 + crank + cs j
       const int ncol = std::max(0, (n + k - c0 - crank + cs - 1) / cs);
@@ -599,9 +638,9 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
 
 // Shared memory of the blocked path for leading dimension ld and at most
 // nmax coefficient columns (0 if it does not fit a CTA).
-size_t rqr_smem_bytes(int ld, int nmax) {
+size_t rqr_smem_bytes(int ld, int nmax, int k) {
   const size_t wsz = std::max<size_t>({(size_t)RB * ld, (size_t)RL * nmax, (size_t)RW * nmax});
-  return (wsz + (size_t)(ld + 3) / 4 + RSMALL) * sizeof(double);
+  return (wsz + (size_t)(ld + 3) / 4 + RSMALL + (size_t)(nmax + k + 1) / 2) * sizeof(double);
 }
 
 // Clusters of cs CTAs of the blocked kernel that fit on the device at once.
@@ -629,32 +668,49 @@ int rqr_active_clusters(size_t shm, int cs, int nb) {
   return act;
 }
 
+// Whether the trailing updates of a batch can run on the tensor cores
+// (lmfs_emu64.cuh): even leading dimension and matrix stride (16-byte row
+// pairs), at most 3072 rows (the exact sums' range), and room for the digit
+// tiles in the work region; LMFS_QR_EMU=0 turns them off.  They need one CTA
+// per matrix.
+bool rqr_emu_ok(const QRBatch& q) {
+  if (const char* e = std::getenv("LMFS_QR_EMU"))
+    if (std::atoi(e) == 0) return false;
+  const size_t wsz = std::max<size_t>({(size_t)RB * q.ld, (size_t)RL * q.nmax, (size_t)RW * q.nmax});
+  return q.ld % 2 == 0 && q.mstride % 2 == 0 && q.ld <= 3072 &&
+         wsz * sizeof(double) >= emu::update_smem_bytes(q.nmax + q.k);
+}
+
 int rqr_solve_batched(const QRBatch& q, cudaStream_t st, int cs) {
   const int nmax = q.nmax;
   const size_t wsz = std::max<size_t>({(size_t)RB * q.ld, (size_t)RL * nmax, (size_t)RW * nmax});
-  const size_t shm = rqr_smem_bytes(q.ld, nmax);
+  const size_t shm = rqr_smem_bytes(q.ld, nmax, q.k);
+  const bool use_emu = cs == 1 && rqr_emu_ok(q);
+  const int wld = nmax + q.k;
   if (cs < 1 || cs > 8) { set_last_error("blocked QR: cluster size must lie in 1..8"); return LMFS_ERR_INVALID; }
   if (cuda_failed(cudaFuncSetAttribute(rqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm),
                   "rqr smem attribute"))
     return LMFS_ERR_CUDA;
   double* Yg = nullptr;
   int* order = nullptr;
+  int64_t* Wsc = nullptr;
   int rc = LMFS_OK;
   if ((rc = dalloc(&Yg, (size_t)q.nb * RL * nmax))) return rc;
+  if (use_emu && (rc = dalloc(&Wsc, (size_t)q.nb * 16 * wld))) { dfree(Yg); return rc; }
   if (q.n_h) {
     // largest matrices first: the waves of CTAs then end together
     std::vector<int> ord(q.nb);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return q.n_h[x] > q.n_h[y]; });
-    if ((rc = dalloc(&order, (size_t)q.nb))) { dfree(Yg); return rc; }
+    if ((rc = dalloc(&order, (size_t)q.nb))) { dfree(Yg); dfree(Wsc); return rc; }
     if (cuda_failed(cudaMemcpyAsync(order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st), "h2d") ||
         cuda_failed(cudaStreamSynchronize(st), "sync")) {
-      dfree(Yg); dfree(order);
+      dfree(Yg); dfree(order); dfree(Wsc);
       return LMFS_ERR_CUDA;
     }
   }
   if (cuda_failed(cudaMemsetAsync(q.info, 0, (size_t)q.nb * sizeof(int), st), "memset")) {
-    dfree(Yg); dfree(order);
+    dfree(Yg); dfree(order); dfree(Wsc);
     return LMFS_ERR_CUDA;
   }
   RArgs a{};
@@ -663,6 +719,10 @@ int rqr_solve_batched(const QRBatch& q, cudaStream_t st, int cs) {
   a.permstride = q.permstride; a.info = q.info; a.Yg = Yg; a.ysd = nmax; a.order = order;
   a.wsz = (int)wsz;
   a.cs = cs;
+  a.emu = use_emu ? 1 : 0;
+  if (use_emu && q.used_blocked) *q.used_blocked = 2;
+  a.Wsc = Wsc;
+  a.wld = wld;
   if (q.ev) cudaEventRecord(q.ev[0], st);
   if (cs == 1) {
     rqr_kernel<<<q.nb, RT, shm, st>>>(a);
@@ -686,6 +746,7 @@ int rqr_solve_batched(const QRBatch& q, cudaStream_t st, int cs) {
   if (q.ev) { cudaEventRecord(q.ev[1], st); cudaEventRecord(q.ev[2], st); }
   dfree(Yg);
   dfree(order);
+  dfree(Wsc);
   return rc;
 }
 

@@ -1,7 +1,8 @@
 """The pair precompute's two QR forms through the C ABI: the blocked QR with
 pivots chosen on a random sketch (one matrix per CTA, the form large batches
-use) and the column-pivoted cluster form (small batches).  LMFS_QR_PATH
-forces one or the other.  Both truncate at the same level and differ only in
+use, with its trailing updates as exact digit products on the tensor cores or
+in FP64; two CTAs per matrix in FP64) and the column-pivoted cluster form
+(small batches).  LMFS_QR_PATH, LMFS_QR_CS and LMFS_QR_EMU force a form.  Both truncate at the same level and differ only in
 numerically null directions, so the unique parts of the blocks -- E and C A
 -- are compared with the oracle's SVD-truncated blocks, and the solves with
 each other."""
@@ -39,29 +40,34 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def solver(L, monkeypatch, path, pk, problem, cs=None, **kw):
+def solver(L, monkeypatch, path, pk, problem, cs=None, emu=None, **kw):
     monkeypatch.setenv("LMFS_QR_PATH", path)
     if cs:
         monkeypatch.setenv("LMFS_QR_CS", cs)
+    if emu is not None:
+        monkeypatch.setenv("LMFS_QR_EMU", emu)
     s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, **kw))
     s.precompute(problem)
     monkeypatch.delenv("LMFS_QR_PATH")
     if cs:
         monkeypatch.delenv("LMFS_QR_CS")
+    if emu is not None:
+        monkeypatch.delenv("LMFS_QR_EMU")
     return s
 
 
-@pytest.mark.parametrize("cs", ["1", "2"])
+@pytest.mark.parametrize("cs,emu", [("1", "1"), ("1", "0"), ("2", None)])
 @pytest.mark.parametrize("problem", ["mobility", "resistance"])
-def test_blocked_qr_pair_blocks_against_oracle(L, monkeypatch, problem, cs):
+def test_blocked_qr_pair_blocks_against_oracle(L, monkeypatch, problem, cs, emu):
     """P = 100 packing (37 close pairs): on 8 sampled pairs E and C A of the
-    blocked form -- one CTA per system, and two CTAs (a cluster) per system,
-    the form of mid-size batches -- against the oracle's SVD blocks within
-    1e-5, as the cluster form's are; the fine ranks of the forms within a few
-    columns."""
+    blocked form -- one CTA per system with the trailing updates on the tensor
+    cores or in FP64, and two CTAs (a cluster) per system in FP64, the form of
+    mid-size batches without the tensor-core updates -- against the oracle's
+    SVD blocks within 1e-5, as the cluster form's are; the fine ranks of the
+    forms within a few columns."""
     code = L.MOBILITY if problem == "mobility" else L.RESISTANCE
     pk = w.packing_p100()
-    sb = solver(L, monkeypatch, "blocked", pk, code, cs=cs)
+    sb = solver(L, monkeypatch, "blocked", pk, code, cs=cs, emu=emu)
     sc = solver(L, monkeypatch, "cluster", pk, code)
     Ab, Eb = sb.pair_blocks(code)
     Ac, Ec = sc.pair_blocks(code)
@@ -75,7 +81,7 @@ def test_blocked_qr_pair_blocks_against_oracle(L, monkeypatch, problem, cs):
         for name, A, E in (("blocked", Ab, Eb), ("cluster", Ac, Ec)):
             worst[name][0] = max(worst[name][0], rel(E[q], b["E"]))
             worst[name][1] = max(worst[name][1], rel(b["C"] @ A[q], b["C"] @ b["A"]))
-    print(f"{problem}, {cs} CTA(s) per system: E, C A vs oracle: blocked {worst['blocked'][0]:.2e} {worst['blocked'][1]:.2e}, "
+    print(f"{problem}, {cs} CTA(s) per system, tensor-core updates {emu}: E, C A vs oracle: blocked {worst['blocked'][0]:.2e} {worst['blocked'][1]:.2e}, "
           f"cluster {worst['cluster'][0]:.2e} {worst['cluster'][1]:.2e}; rank F blocked "
           f"[{stb['min_rank_F']:.0f}, {stb['max_rank_F']:.0f}] cluster [{stc['min_rank_F']:.0f}, {stc['max_rank_F']:.0f}]; "
           f"QR ms blocked {stb['qr_ms']:.1f} cluster {stc['qr_ms']:.1f}")
@@ -99,3 +105,32 @@ def test_blocked_qr_solves_like_the_cluster_form(L, monkeypatch):
     d = rel(out["blocked"], out["cluster"])
     print(f"velocities blocked vs cluster {d:.2e}")
     assert d < 1e-6
+
+
+@pytest.mark.parametrize("problem", ["mobility", "resistance"])
+def test_tensor_core_updates_match_fp64_updates(L, monkeypatch, problem):
+    """The blocked form with its trailing updates as exact digit products on
+    the tensor cores against the same form with FP64 updates, P = 100: the
+    same fine ranks on every pair, every E within 1e-9 (measured 1.9e-11 and
+    3.6e-13: the two differ by rounding, the digit products being exact), and
+    the FP64 mobility solve on either set of blocks within 1e-6."""
+    code = L.MOBILITY if problem == "mobility" else L.RESISTANCE
+    pk = w.packing_p100()
+    se = solver(L, monkeypatch, "blocked", pk, code, cs="1", emu="1", precision=L.FP64)
+    sf = solver(L, monkeypatch, "blocked", pk, code, cs="1", emu="0", precision=L.FP64)
+    Ae, Ee = se.pair_blocks(code)
+    Af, Ef = sf.pair_blocks(code)
+    ste, stf = se.stats(code), sf.stats(code)
+    assert ste["min_rank_F"] == stf["min_rank_F"] and ste["max_rank_F"] == stf["max_rank_F"]
+    dE = max(rel(Ee[q], Ef[q]) for q in range(len(Ee)))
+    print(f"{problem}: E tensor-core vs FP64 updates, worst pair {dE:.2e}; fine QR ms {ste['fine_ms']:.1f} "
+          f"against {stf['fine_ms']:.1f}")
+    assert dE < 1e-9
+    if code == L.MOBILITY:
+        ft = w.forces_torques(pk.P, 5)
+        ve, ie = se.solve(code, ft)
+        vf, if_ = sf.solve(code, ft)
+        assert ie["converged"] and if_["converged"]
+        assert rel(ve, vf) < 1e-6
+    se.close()
+    sf.close()

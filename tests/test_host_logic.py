@@ -139,3 +139,144 @@ def test_pair_chunks_are_equal_and_within_budget(chunk_harness):
         # the last chunk is shorter than the others by fewer pairs than there are chunks
         assert C - (nchunk - 1) * chunk >= chunk - nchunk
     assert int(out[0]) == 873                     # the P = 10^4 packing: 12 chunks
+
+
+EMU_HARNESS = r"""
+#include <cstdio>
+#include <cmath>
+#include <random>
+#include <vector>
+#include "lmfs_emu64.cuh"
+using namespace lmfs::emu;
+typedef __int128 i128;
+static i128 exact_fix(double x, int E) {
+  const long double v = std::ldexp((long double)std::fabs(x), 1076 - E);
+  const i128 r = (i128)std::floor(v + 0.5L);
+  return x < 0 ? -r : r;
+}
+int main() {
+  std::mt19937_64 rng(11);
+  std::uniform_real_distribution<double> U(-1, 1);
+  long bad_fix = 0, bad_range = 0, bad_pair = 0, bad_ldexp = 0, bad_bound = 0;
+  for (int it = 0; it < 50000; ++it) {
+    double x = U(rng) * std::ldexp(1.0, (int)(rng() % 80) - 40);
+    if (it % 9 == 0) x = std::ldexp(1.0, (int)(rng() % 40) - 20) * (it % 2 ? -1 : 1);
+    if (it % 97 == 0) x = 0.0;
+    const int E = bexp(x) + (int)(rng() % 60);
+    const uint64_t y = fixpt(x, E);
+    i128 X = 0;
+    for (int i = 7; i >= 0; --i) {
+      const int d = digit(y, i);
+      if (d < -64 || d > 63) ++bad_range;
+      X = X * 128 + d;
+    }
+    if (X != exact_fix(x, E)) ++bad_fix;
+    const int sh = 7 * (int)(rng() % 8);
+    const uint32_t p = dpair(y, fixpt(-x, E), sh);
+    if ((int)bitsf(p << 16) != digit(y, sh / 7) || (int)bitsf(p & 0xFFFF0000u) != digit(fixpt(-x, E), sh / 7)) ++bad_pair;
+  }
+  for (int it = 0; it < 50000; ++it) {
+    const int64_t v = (int64_t)(rng() >> (rng() % 63)) * ((rng() & 1) ? -1 : 1);
+    const int e = (int)(rng() % 300) - 150;
+    const double got = i64_ldexp(v, e);
+    const long double ref = std::ldexp((long double)v, e);
+    if (std::fabs((long double)got - ref) > 0.5000001L * std::ldexp(1.0L, std::ilogb((double)ref) - 52)) ++bad_ldexp;
+  }
+  double worst_w = 0, worst_w64 = 0, worst_p = 0;
+  for (int it = 0; it < 120; ++it) {
+    const int m = 1 + (int)(rng() % 1400);
+    std::vector<double> v(m), c(m);
+    for (int i = 0; i < m; ++i) {
+      v[i] = U(rng) * (i % 11 == 0 ? 1e-9 : 1.0);
+      c[i] = U(rng) * std::ldexp(1.0, (int)(rng() % 24) - 12);
+    }
+    v[0] = 1.0;
+    int E = 0;
+    for (double x : c) E = std::max(E, bexp(x));
+    // the accumulator scheme of the device's W = V^T C: per flush of 192 rows,
+    // accumulator q holds level q from the even places of v and level q + 1
+    // from the odd ones (v's place 2p with c's place q - 2p)
+    int64_t H = 0, Lw = 0;
+    for (int r0 = 0; r0 < m; r0 += 192) {
+      long long Se[9] = {0}, So[9] = {0};
+      for (int i = r0; i < std::min(m, r0 + 192); ++i) {
+        const uint64_t yv = fixpt(v[i], 1023), yc = fixpt(c[i], E);
+        for (int q = 0; q < 9; ++q)
+          for (int p = 0; p < 4 && 2 * p <= q; ++p) {
+            if (q - 2 * p > 7) continue;
+            Se[q] += (long long)digit(yv, 7 - 2 * p) * digit(yc, 7 - (q - 2 * p));
+            So[q] += (long long)digit(yv, 6 - 2 * p) * digit(yc, 7 - (q - 2 * p));
+          }
+      }
+      for (int q = 0; q < 9; ++q) {
+        if (std::llabs(Se[q]) >= (1 << 22) || std::llabs(So[q]) >= (1 << 22)) ++bad_bound;
+        w_add(H, Lw, q, acc_pair(MAGIC + (float)Se[q], MAGIC + (float)So[q]));
+      }
+    }
+    const double W = w_value(H, Lw, E);
+    long double ref = 0, vs = 0;
+    for (int i = 0; i < m; ++i) { ref += (long double)v[i] * c[i]; vs += std::fabs((long double)v[i]); }
+    const long double bnd = vs * std::ldexp(1.0L, E - 1023);
+    double f64 = 0;
+    for (int i = 0; i < m; ++i) f64 = std::fma(v[i], c[i], f64);
+    worst_w = std::max(worst_w, (double)(std::fabs((long double)W - ref) / bnd));
+    worst_w64 = std::max(worst_w64, (double)(std::fabs((long double)f64 - ref) / bnd));
+    // P = sum_t v_t w_t over 8 reflectors, one accumulator per level (w's place a, v's place l - a)
+    double vv[8], ww[8];
+    int F = 0;
+    for (int t = 0; t < 8; ++t) {
+      vv[t] = U(rng);
+      ww[t] = U(rng) * std::ldexp(1.0, (int)(rng() % 40) - 20);
+      F = std::max(F, bexp(ww[t]));
+    }
+    float acc[9];
+    for (int l = 0; l < 9; ++l) {
+      long long S = 0;
+      for (int a = 0; a <= l; ++a)
+        if (a <= 7 && l - a <= 7)
+          for (int t = 0; t < 8; ++t) S += (long long)digit(fixpt(ww[t], F), 7 - a) * digit(fixpt(vv[t], 1023), 7 - (l - a));
+      if (std::llabs(S) >= (1 << 22)) ++bad_bound;
+      acc[l] = MAGIC + (float)S;
+    }
+    const double P = i64_ldexp(comb_p(acc), F - 1079);
+    long double pr = 0, pa = 0;
+    for (int t = 0; t < 8; ++t) { pr += (long double)vv[t] * ww[t]; pa += std::fabs((long double)vv[t]); }
+    worst_p = std::max(worst_p, (double)(std::fabs((long double)P - pr) / (pa * std::ldexp(1.0L, F - 1023))));
+  }
+  std::printf("%ld %ld %ld %ld %ld %.6e %.6e %.6e\n", bad_fix, bad_range, bad_pair, bad_ldexp, bad_bound,
+              worst_w, worst_w64, worst_p);
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def emu_harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("needs g++")
+    d = tmp_path_factory.mktemp("emu")
+    src = d / "emu.cpp"
+    src.write_text(EMU_HARNESS)
+    exe = d / "emu"
+    subprocess.run([cxx, "-std=c++17", "-O2", "-I", os.path.join(ROOT, "paper_2606_11273_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True, capture_output=True)
+    return exe
+
+
+def test_digit_products_reproduce_fp64_dot_products(emu_harness):
+    """The scalar steps of the tensor-core trailing update, on the host,
+    against exact arithmetic: the eight balanced base-128 digits of each
+    fixed-point value are in [-64, 63] and sum (as a 128-bit integer) to the
+    correctly rounded x 2^(1076 - E); every bf16 digit pair decodes to the same
+    digits; int64 -> double rounds to nearest; no accumulator of the device's
+    level scheme (192 rows per flush, up to 1400 rows) leaves the exact range;
+    and the assembled W = v . c and P = sum_t v_t w_t lie as close to the
+    exact (extended-precision) values, measured against the sum of |v| times
+    the bound, as an FP64 fused-multiply-add loop does (below 2^-53)."""
+    out = subprocess.run([str(emu_harness)], capture_output=True, text=True, check=True).stdout.split()
+    bad_fix, bad_range, bad_pair, bad_ldexp, bad_bound = (int(v) for v in out[:5])
+    worst_w, worst_w64, worst_p = (float(v) for v in out[5:])
+    assert (bad_fix, bad_range, bad_pair, bad_ldexp, bad_bound) == (0, 0, 0, 0, 0)
+    assert worst_w < 2.0 ** -53 and worst_p < 2.0 ** -53
+    assert worst_w <= 2 * worst_w64
