@@ -105,9 +105,9 @@ class Clocks:
 # (sm__inst_executed_pipe_alu.sum), the pipe that carries the digit work.
 # Valid only for the kernel source they were taken on (lmfs_rqr.cu and
 # lmfs_emu64.cuh): reported as null once either changes.
-RQR_TRAFFIC_PER_MATRIX = (81.69e9 + 40.07e9) / 398.0
-RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.4696552e10
-RQR_SRC_SHA256 = "e93424e09edb2dfb903381467820d3e7315bdd35708283fd98c70c883e9edb4f"
+RQR_TRAFFIC_PER_MATRIX = (80.89e9 + 40.48e9) / 398.0
+RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.2765054e10
+RQR_SRC_SHA256 = "514fbf2d0ea02ccf7dd7b61d9814954483e8b2e364f2ca34c91a7c2d24ff1fa5"
 ALU_WARP_INST_PER_CLK = 2          # 64 results per clock per SM for 32-bit integer add, logic and shift
 
 

@@ -24,6 +24,9 @@
 
 #include <cstdint>
 #include <cstring>
+#ifdef __CUDACC__
+#include <cuda_bf16.h>
+#endif
 
 #ifdef __CUDACC__
 #define EMU_HD __host__ __device__ __forceinline__
@@ -80,13 +83,14 @@ EMU_HD int clz64(uint64_t v) {
 EMU_HD int bexp(double x) { return (int)((dbits(x) >> 52) & 0x7FF); }
 
 // x against the bound 2^(E - 1023) (E a biased exponent no smaller than
-// x's): X = round(x 2^(1076 - E)) with ties away from zero, |X| < 2^54,
-// returned as DBIAS + X, whose eight 7-bit fields are the digits plus 64.
-// Subnormals count as zero.
+// x's, and at least 64): X = round(x 2^(1076 - E)) with ties away from
+// zero, |X| < 2^54, returned as DBIAS + X, whose eight 7-bit fields are the
+// digits plus 64.  Zero and subnormals (biased exponent 0) give 0: with
+// E >= 64 their shift reaches past all 55 bits.
 EMU_HD uint64_t fixpt(double x, int E) {
   const uint64_t b = dbits(x);
   const int ex = (int)((b >> 52) & 0x7FF);
-  const uint64_t m4 = ex ? (((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 2) : 0ull;
+  const uint64_t m4 = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 2;
   int d = E - ex;
   d = d < 0 ? 0 : (d > 63 ? 63 : d);
   const uint64_t mag = ((m4 >> d) + 1ull) >> 1;
@@ -96,14 +100,30 @@ EMU_HD uint64_t fixpt(double x, int E) {
 // Digit (0 = least significant .. 7) of a biased fixed-point value.
 EMU_HD int digit(uint64_t y, int i) { return (int)((y >> (7 * i)) & 127u) - 64; }
 
-// The digits at bit offset sh of two biased values as a bf16 pair (y0 in the
-// low half): u - 64 formed exactly in FP32 from the bits of 2^23 + u, whose
-// upper half is then the bf16 of the same integer.
+// The digits at bit offset sh (a multiple of 7, below 56) of two biased
+// values as a bf16 pair (y0 in the low half).  On the device: the bits
+// 0x4300 | u are the bf16 of 128 + u (exponent 2^7, the 7 digit bits as
+// mantissa), so two digits placed in the two halves and one packed bf16
+// subtraction of 192 give u - 64 in both halves, exactly.  On the host the
+// same integers are formed in FP32 (u - 64 from the bits of 2^23 + u, whose
+// upper half is then its bf16).
 EMU_HD uint32_t dpair(uint64_t y0, uint64_t y1, int sh) {
+#ifdef __CUDA_ARCH__
+  const uint32_t a = (uint32_t)(y0 >> sh);
+  const uint32_t b = sh >= 16 ? (uint32_t)(y1 >> (sh - 16)) : (uint32_t)(y1 << (16 - sh));
+  const uint32_t w = ((a & 0x7Fu) | 0x43004300u) | (b & 0x007F0000u);
+  __nv_bfloat162 v;
+  std::memcpy(&v, &w, 4);
+  const __nv_bfloat162 r = __hsub2(v, __floats2bfloat162_rn(192.0f, 192.0f));
+  uint32_t out;
+  std::memcpy(&out, &r, 4);
+  return out;
+#else
   const uint32_t u0 = (uint32_t)(y0 >> sh) & 127u, u1 = (uint32_t)(y1 >> sh) & 127u;
   const float f0 = bitsf(0x4B000000u + u0) - 8388672.0f;
   const float f1 = bitsf(0x4B000000u + u1) - 8388672.0f;
   return (fbits(f0) >> 16) | (fbits(f1) & 0xFFFF0000u);
+#endif
 }
 
 // The integer held by an accumulator that started at MAGIC.
@@ -140,8 +160,9 @@ EMU_HD int64_t shl(int64_t v, int sh) { return sh >= 0 ? v * ((int64_t)1 << sh) 
 // rows).  With V against 2^0 (E = 1023) and C against its column bound E,
 // W = W_fix 2^(E - 1129).
 EMU_HD void w_add(int64_t& H, int64_t& L, int q, int32_t u) {
-  if (q <= 3) H += shl(u, 21 - 7 * q);
-  else L += shl(u, 56 - 7 * q);
+  // both weights fit 32 bits: one widening multiply-add
+  if (q <= 3) H += (int64_t)u * (int32_t)(1 << (21 - 7 * q));
+  else L += (int64_t)u * (int32_t)(1 << (56 - 7 * q));
 }
 EMU_HD double w_value(int64_t H, int64_t L, int E) {
   return i64_ldexp(H, E - 1059) + i64_ldexp(L, E - 1094);
@@ -150,19 +171,28 @@ EMU_HD double w_value(int64_t H, int64_t L, int E) {
 // Level sums of P = V W2 (one accumulator per level lambda = 0..8) as
 // P_int = (sum_lambda S_lambda 128^(14 - lambda)) / 2^50; with W2 against
 // its column bound F, P = P_int 2^(F - 1079).
+// The three heaviest levels fit one int32 (a most significant digit is at
+// most 33 in magnitude, so over 8 reflectors their sums stay below 2^13.1,
+// 2^15.1 and 2^16.1), the rest in pairs; the
+// weights in units of P_int are 2^34 (levels 0-2), 2^20 (3-4), 2^6 (5-6) and
+// 2^-8 (7-8).
 EMU_HD int64_t comb_p(const float* acc) {
-  const int32_t u01 = acc_pair(acc[0], acc[1]), u23 = acc_pair(acc[2], acc[3]);
-  const int32_t u45 = acc_pair(acc[4], acc[5]), u67 = acc_pair(acc[6], acc[7]);
-  return shl(u01, 41) + shl(u23, 27) + shl(u45, 13) + shl(u67, -1) + shl(acc_int(acc[8]), -8);
+  const int32_t u012 = (int32_t)(fbits(acc[0]) * 16384u + fbits(acc[1]) * 128u + fbits(acc[2]) - 16513u * MAGIC_BITS);
+  const int32_t u34 = acc_pair(acc[3], acc[4]), u56 = acc_pair(acc[5], acc[6]), u78 = acc_pair(acc[7], acc[8]);
+  int64_t t = (int64_t)u012 * 16384 + u34;
+  t = t * 16384 + u56;
+  return t * 64 + (u78 >> 8);
 }
 
 #ifdef __CUDACC__
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
 }
+// (not volatile: a pure function of its operands, so the compiler may
+// schedule the digit work around it)
 __device__ __forceinline__ void mma16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                       uint32_t b0, uint32_t b1) {
-  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                "{%0,%1,%2,%3};\n"
                : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
@@ -230,11 +260,12 @@ __device__ void block_update(double* __restrict__ A, int ld, int m, int s, int b
       const int lc = 8 * j8 + g;                          // the column this lane loads
       const bool cv = lc < ncol;
       const double* col = A + (long long)(c0 + (cv ? lc : 0)) * ld;
-      const int E = cv ? cex[c0 + lc] : 0;
+      const int E = cv ? max(cex[c0 + lc], 64) : 64;
       if (cv) {
-        // the first two k-steps' lines; each step then asks for the one two ahead
+        // the first three k-steps' lines; each step then asks for the one three ahead
         if (rb + 2 * t4 < m) prefetch_l1(col + rb + 2 * t4);
         if (rb + 16 + 2 * t4 < m) prefetch_l1(col + rb + 16 + 2 * t4);
+        if (rb + 32 + 2 * t4 < m) prefetch_l1(col + rb + 32 + 2 * t4);
       }
       // this lane: reflector g, tile columns 2 t4 and 2 t4 + 1
       int64_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
@@ -245,7 +276,7 @@ __device__ void block_update(double* __restrict__ A, int ld, int m, int s, int b
       const int k1 = min(kss, k0 + KF);
       for (int ks = k0; ks < k1; ++ks) {
         const int r = rb + 16 * ks + 2 * t4;
-        if (cv && r + 32 < m) prefetch_l1(col + r + 32);
+        if (cv && r + 48 < m) prefetch_l1(col + r + 48);
         double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
         if (cv) {
           if (r + 1 < m) { const double2 v = *reinterpret_cast<const double2*>(col + r); x0 = v.x; x1 = v.y; }
@@ -302,7 +333,7 @@ __device__ void block_update(double* __restrict__ A, int ld, int m, int s, int b
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       w[u] = u < bbe ? w_value(WH[(long long)u * wld + lc], WL[(long long)u * wld + lc], E) : 0.0;
-    int F = 0;
+    int F = 64;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       double acc = 0.0;
@@ -337,7 +368,7 @@ __device__ void block_update(double* __restrict__ A, int ld, int m, int s, int b
     for (int j16 = warp; j16 < nt16; j16 += NW) {
       const int la = 16 * j16 + g, lb = la + 8;
       const bool va = la < ncol, vb = lb < ncol;
-      const int fa = va ? fcx[la] : 0, fb = vb ? fcx[lb] : 0;
+      const int fa = va ? fcx[la] : 64, fb = vb ? fcx[lb] : 64;
       const int t0 = 2 * t4;
       uint32_t Ra[8], Rb[8];
       {
@@ -428,6 +459,153 @@ __device__ void block_update(double* __restrict__ A, int ld, int m, int s, int b
     }
   }
   __syncthreads();
+}
+
+// Shared memory (bytes) of backsub inside the caller's work region: the
+// reciprocal diagonal, one block of solved rows (8 x k), the digit tiles of
+// one row chunk, the chunk's row bounds and the block's column bounds.
+__host__ __device__ constexpr size_t backsub_smem_bytes(int r, int k) {
+  return (size_t)8 * r + (size_t)64 * k + (size_t)UPD_DG * 4 + (size_t)4 * UPD_CH + (size_t)4 * k;
+}
+
+// Back substitution R X = Y for the k right-hand sides in columns n .. n+k-1
+// of A (rows 0 .. r-1, overwritten by X), R the upper triangle of A's first r
+// columns: blocks of 8 rows from the bottom, each solved in FP64 (a thread
+// per right-hand side, the reciprocal diagonal), then taken out of the rows
+// above, Y[0:j0] -= R[0:j0, j0:j0+8] X_b, as exact digit products on the
+// tensor cores like GEMM2 of block_update -- R's digits against the largest
+// entry of their row in the block, X_b's against its column's.  smw: the
+// work region, backsub_smem_bytes(r, k) bytes.
+template <int NT>
+__device__ void backsub(double* __restrict__ A, int ld, int r, int n, int k, double* smw) {
+  constexpr int NW = NT / 32, CH = UPD_CH, NR8 = CH / 8;
+  static_assert((NR8 * 32) % NT == 0, "staging loop: every lane takes the same number of steps");
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+  double* rinv = smw;                                     // [r]
+  double* Xb = rinv + r;                                  // [8][k]
+  uint32_t* Dg = reinterpret_cast<uint32_t*>(Xb + 8 * k); // UPD_DG words
+  int* Ei = reinterpret_cast<int*>(Dg + UPD_DG);          // [CH]
+  int* fcx = Ei + CH;                                     // [k]
+  for (int j = tid; j < r; j += NT) rinv[j] = 1.0 / A[(long long)j * ld + j];
+  __syncthreads();
+  const int nt16 = (k + 15) >> 4;
+  for (int j1 = r; j1 > 0;) {
+    const int j0 = max(0, j1 - 8), bw = j1 - j0;
+    // the block's rows of X, per right-hand side
+    for (int c = tid; c < k; c += NT) {
+      double* yc = A + (long long)(n + c) * ld;
+      double y[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) y[t] = t < bw ? yc[j0 + t] : 0.0;
+#pragma unroll
+      for (int t = 7; t >= 0; --t) {
+        if (t < bw) {
+          const double x = y[t] * rinv[j0 + t];
+          y[t] = x;
+          const double* rc = A + (long long)(j0 + t) * ld + j0;
+#pragma unroll
+          for (int u = 0; u < t; ++u) y[u] = fma(-rc[u], x, y[u]);
+        }
+      }
+      int F = 64;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        Xb[t * k + c] = t < bw ? y[t] : 0.0;
+        if (t < bw) {
+          yc[j0 + t] = y[t];
+          F = max(F, bexp(y[t]));
+        }
+      }
+      fcx[c] = F;
+    }
+    __syncthreads();
+    for (int rb = 0; rb < j0; rb += CH) {
+      // R's digits for rows rb .. rb + CH - 1 in the B-fragment order, each
+      // row against its largest entry among the block's columns
+      for (int u = tid; u < NR8 * 32; u += NT) {
+        const int nt = u >> 5, ln = u & 31, gg = ln >> 2, tt = ln & 3;
+        const int i = rb + 8 * nt + gg;
+        const double v0 = (i < j0 && 2 * tt < bw) ? A[(long long)(j0 + 2 * tt) * ld + i] : 0.0;
+        const double v1 = (i < j0 && 2 * tt + 1 < bw) ? A[(long long)(j0 + 2 * tt + 1) * ld + i] : 0.0;
+        int e = max(max(bexp(v0), bexp(v1)), 64);
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+        if (tt == 0) Ei[8 * nt + gg] = e;
+        const uint64_t y0 = fixpt(v0, e), y1 = fixpt(v1, e);
+        uint32_t* D = Dg + nt * 256 + ln;
+#pragma unroll
+        for (int sl = 0; sl < 8; ++sl) D[sl * 32] = dpair(y0, y1, 7 * (7 - sl));
+      }
+      __syncthreads();
+      const int nts = min(NR8, (j0 - rb + 7) >> 3);
+      for (int j16 = warp; j16 < nt16; j16 += NW) {
+        const int la = 16 * j16 + g, lb = la + 8;
+        const bool va = la < k, vb = lb < k;
+        const int fa = va ? fcx[la] : 64, fb = vb ? fcx[lb] : 64;
+        const int t0 = 2 * t4;
+        uint32_t Ra[8], Rb[8];
+        {
+          const double wa0 = va ? Xb[t0 * k + la] : 0.0, wa1 = va ? Xb[(t0 + 1) * k + la] : 0.0;
+          const double wb0 = vb ? Xb[t0 * k + lb] : 0.0, wb1 = vb ? Xb[(t0 + 1) * k + lb] : 0.0;
+          const uint64_t ya0 = fixpt(wa0, fa), ya1 = fixpt(wa1, fa), yb0 = fixpt(wb0, fb), yb1 = fixpt(wb1, fb);
+#pragma unroll
+          for (int sl = 0; sl < 8; ++sl) {
+            Ra[sl] = dpair(ya0, ya1, 7 * (7 - sl));
+            Rb[sl] = dpair(yb0, yb1, 7 * (7 - sl));
+          }
+        }
+        double* cola = A + (long long)(n + (va ? la : 0)) * ld;
+        double* colb = A + (long long)(n + (vb ? lb : 0)) * ld;
+        for (int nt = 0; nt < nts; ++nt) {
+          const int i = rb + 8 * nt + 2 * t4;             // this lane's rows i, i + 1
+          double2 xa = make_double2(0.0, 0.0), xb = make_double2(0.0, 0.0);
+          if (i + 1 < j0) {
+            if (va) xa = *reinterpret_cast<const double2*>(cola + i);
+            if (vb) xb = *reinterpret_cast<const double2*>(colb + i);
+          } else if (i < j0) {
+            if (va) xa.x = cola[i];
+            if (vb) xb.x = colb[i];
+          }
+          const uint32_t* D = Dg + nt * 256 + lane;
+          uint32_t Q[8];
+#pragma unroll
+          for (int sl = 0; sl < 8; ++sl) Q[sl] = D[sl * 32];
+          float acc[9][4];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = MAGIC;
+#pragma unroll
+          for (int lam = 0; lam < 9; ++lam) {
+            const int alo = lam > 7 ? lam - 7 : 0, ahi = lam < 7 ? lam : 7;
+#pragma unroll
+            for (int a = alo; a <= ahi; a += 2) {
+              if (a + 1 <= ahi) mma16(acc[lam], Ra[a], Rb[a], Ra[a + 1], Rb[a + 1], Q[lam - a], Q[lam - a - 1]);
+              else mma16(acc[lam], Ra[a], Rb[a], 0u, 0u, Q[lam - a], 0u);
+            }
+          }
+          auto pval = [&](int e, int f) {
+            float av[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) av[q] = acc[q][e];
+            return i64_ldexp(comb_p(av), f - 2102);
+          };
+          const int e0 = Ei[i - rb], e1 = Ei[i + 1 - rb];
+          if (i < j0) {
+            if (va) xa.x -= pval(0, fa + e0);
+            if (vb) xb.x -= pval(2, fb + e0);
+            if (i + 1 < j0) {
+              if (va) { xa.y -= pval(1, fa + e1); *reinterpret_cast<double2*>(cola + i) = xa; }
+              if (vb) { xb.y -= pval(3, fb + e1); *reinterpret_cast<double2*>(colb + i) = xb; }
+            } else {
+              if (va) cola[i] = xa.x;
+              if (vb) colb[i] = xb.x;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    j1 = j0;
+  }
 }
 #endif
 

@@ -563,12 +563,26 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
   if (s >= smax) rank = smax;
   __syncthreads();
 
-  // ---- back substitution R_11 x = (Q^T B)_1 for RW right-hand sides at a
-  // time, one per warp (in shared memory); R's columns are staged chunk by
-  // chunk in shared memory for all warps, with the reciprocals of its
-  // diagonal, so the chain of each solve waits on neither global memory nor a
-  // division; then the scatter by the pivot order
-  {
+  // ---- back substitution R_11 x = (Q^T B)_1 and the scatter by the pivot
+  // order.  With the tensor-core updates: blocks of 8 rows, each taken out of
+  // the rows above as digit products (lmfs_emu64.cuh), in place in B.
+  if (a.emu) {
+    emu::backsub<RT>(A, ld, rank, n, k, W);
+    __syncthreads();
+    int bad = 0;
+    double* X0 = a.X + (long long)b * a.xstride;
+    for (long long e = tid; e < (long long)n * k; e += RT) {
+      const int c = (int)(e / n), i = (int)(e - (long long)c * n);
+      const double v = i < rank ? A[(long long)(n + c) * ld + i] : 0.0;
+      if (!(v == v) || isinf(v)) bad = 1;
+      X0[(long long)c * a.xld + perm[i]] = v;
+    }
+    if (bad) atomicOr(a.info + b, 1);
+  } else {
+    // FP64: RW right-hand sides at a time, one per warp (in shared memory);
+    // R's columns are staged chunk by chunk in shared memory for all warps,
+    // with the reciprocals of its diagonal, so the chain of each solve waits
+    // on neither global memory nor a division
     const int rpad = (rank + 1) & ~1;
     double* y = W + (long long)warp * ysd;                // RW * ysd doubles
     double* rinv = W + (long long)RW * ysd;               // [rank]
@@ -678,7 +692,8 @@ bool rqr_emu_ok(const QRBatch& q) {
     if (std::atoi(e) == 0) return false;
   const size_t wsz = std::max<size_t>({(size_t)RB * q.ld, (size_t)RL * q.nmax, (size_t)RW * q.nmax});
   return q.ld % 2 == 0 && q.mstride % 2 == 0 && q.ld <= 3072 &&
-         wsz * sizeof(double) >= emu::update_smem_bytes(q.nmax + q.k);
+         wsz * sizeof(double) >= emu::update_smem_bytes(q.nmax + q.k) &&
+         wsz * sizeof(double) >= emu::backsub_smem_bytes(q.nmax, q.k);
 }
 
 int rqr_solve_batched(const QRBatch& q, cudaStream_t st, int cs) {

@@ -162,7 +162,7 @@ int main() {
     double x = U(rng) * std::ldexp(1.0, (int)(rng() % 80) - 40);
     if (it % 9 == 0) x = std::ldexp(1.0, (int)(rng() % 40) - 20) * (it % 2 ? -1 : 1);
     if (it % 97 == 0) x = 0.0;
-    const int E = bexp(x) + (int)(rng() % 60);
+    const int E = std::max(64, bexp(x) + (int)(rng() % 60));
     const uint64_t y = fixpt(x, E);
     i128 X = 0;
     for (int i = 7; i >= 0; --i) {
@@ -191,7 +191,7 @@ int main() {
       c[i] = U(rng) * std::ldexp(1.0, (int)(rng() % 24) - 12);
     }
     v[0] = 1.0;
-    int E = 0;
+    int E = 64;
     for (double x : c) E = std::max(E, bexp(x));
     // the accumulator scheme of the device's W = V^T C: per flush of 192 rows,
     // accumulator q holds level q from the even places of v and level q + 1
@@ -223,7 +223,7 @@ int main() {
     worst_w64 = std::max(worst_w64, (double)(std::fabs((long double)f64 - ref) / bnd));
     // P = sum_t v_t w_t over 8 reflectors, one accumulator per level (w's place a, v's place l - a)
     double vv[8], ww[8];
-    int F = 0;
+    int F = 64;
     for (int t = 0; t < 8; ++t) {
       vv[t] = U(rng);
       ww[t] = U(rng) * std::ldexp(1.0, (int)(rng() % 40) - 20);
