@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "lmfs_emu64.cuh"
 #include "lmfs_geom.cuh"
 #include "lmfs_internal.h"
 #include "lmfs_fp64.cuh"
@@ -712,6 +713,142 @@ __global__ void gemm_batched(const double* Am, int lda, long long sa, const doub
   }
 }
 
+// The same product as exact digit products on the tensor cores
+// (lmfs_emu64.cuh): every row of A against its largest entry, every column
+// of B against its, eight 7-bit digits each; the products of the 43 digit
+// pairs of levels 0..8 are summed exactly (one FP32 accumulator per level
+// over a chunk of 64 terms, then into two int64 words per output) and the
+// result rounded once.  digit_bounds finds the bounds (a block per matrix);
+// gemm_digits_batched: a 32 x 32 tile of Out per CTA, 16 x 8 per warp, the
+// chunk's digits staged in shared memory in the fragment order.  ldb and the
+// matrix strides of B even (pairs of B's rows load as 16-byte words).
+__global__ void digit_bounds(const double* Am, int lda, long long sa, const double* Bm, int ldb, long long sb,
+                             int M, int N, const int* Kb, int kfixed, const PairDims* pdp, int* bounds) {
+  const int b = blockIdx.x;
+  int K = kfixed;
+  if (Kb) K = 2 * (2 * pdp->Nfp + Kb[2 * b] + Kb[2 * b + 1]);
+  const double* A_ = Am + (long long)b * sa;
+  const double* B_ = Bm + (long long)b * sb;
+  int* eb = bounds + (long long)b * (M + N);
+  for (int r = threadIdx.x; r < M; r += blockDim.x) {
+    int e = 64;
+    for (int kk = 0; kk < K; ++kk) e = max(e, emu::bexp(A_[(long long)kk * lda + r]));
+    eb[r] = e;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < N; c += nw) {
+    int e = 64;
+    for (int kk = lane; kk < K; kk += 32) e = max(e, emu::bexp(B_[(long long)c * ldb + kk]));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) eb[M + c] = e;
+  }
+}
+
+constexpr int DG_AW = 2 * 4 * 8 * 32 * 4;   // A digit words per chunk: [m tile][k step][place][lane][4]
+constexpr int DG_BW = 4 * 4 * 8 * 32 * 2;   // B digit words per chunk: [n tile][k step][place][lane][2]
+constexpr size_t DG_SMEM = (size_t)(DG_AW + DG_BW + 64) * 4;
+
+__global__ void __launch_bounds__(256, 2) gemm_digits_batched(const double* Am, int lda, long long sa, const double* Bm,
+                                                              int ldb, long long sb, double* Out, int ldo, long long so,
+                                                              int M, int N, const int* Kb, int kfixed,
+                                                              const PairDims* pdp, const int* bounds) {
+  using namespace emu;
+  extern __shared__ __align__(16) uint32_t dsm[];
+  uint32_t* Ad = dsm;
+  uint32_t* Bd = dsm + DG_AW;
+  int* er = reinterpret_cast<int*>(Bd + DG_BW);
+  int* ec = er + 32;
+  const int b = blockIdx.z;
+  int K = kfixed;
+  if (Kb) K = 2 * (2 * pdp->Nfp + Kb[2 * b] + Kb[2 * b + 1]);
+  const double* A_ = Am + (long long)b * sa;
+  const double* B_ = Bm + (long long)b * sb;
+  double* O = Out + (long long)b * so;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+  const int row0 = blockIdx.x * 32, col0 = blockIdx.y * 32;
+  if (tid < 32) er[tid] = row0 + tid < M ? bounds[(long long)b * (M + N) + row0 + tid] : 64;
+  else if (tid < 64) ec[tid - 32] = col0 + tid - 32 < N ? bounds[(long long)b * (M + N) + M + col0 + tid - 32] : 64;
+  const int mt = warp & 1, nt = warp >> 1;                // this warp's 16 x 8 tile
+  int64_t H[4] = {0, 0, 0, 0}, L[4] = {0, 0, 0, 0};
+  for (int kb = 0; kb < K; kb += 64) {
+    __syncthreads();
+    // A: 32 rows x 64 terms, a pair of consecutive terms per word
+    for (int p = tid; p < 1024; p += 256) {
+      const int row = p & 31, kk2 = p >> 5, kk = kb + 2 * kk2, ar = row0 + row;
+      double v0 = 0.0, v1 = 0.0;
+      if (ar < M) {
+        if (kk < K) v0 = A_[(long long)kk * lda + ar];
+        if (kk + 1 < K) v1 = A_[(long long)(kk + 1) * lda + ar];
+      }
+      const uint64_t y0 = fixpt(v0, er[row]), y1 = fixpt(v1, er[row]);
+      const int r16 = row & 15, k16 = (2 * kk2) & 15;
+      const int reg = (r16 >> 3) + 2 * (k16 >> 3), ln = 4 * (r16 & 7) + ((k16 & 7) >> 1);
+      uint32_t* dst = Ad + ((((row >> 4) * 4 + (kk2 >> 3)) * 8) * 32 + ln) * 4 + reg;
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl) dst[sl * 128] = dpair(y0, y1, 7 * (7 - sl));
+    }
+    // B: 64 terms x 32 columns
+    for (int p = tid; p < 1024; p += 256) {
+      const int kk2 = p & 31, col = p >> 5, kk = kb + 2 * kk2, bc = col0 + col;
+      double v0 = 0.0, v1 = 0.0;
+      if (bc < N) {
+        const double* bp = B_ + (long long)bc * ldb + kk;
+        if (kk + 1 < K) { const double2 v = *reinterpret_cast<const double2*>(bp); v0 = v.x; v1 = v.y; }
+        else if (kk < K) v0 = bp[0];
+      }
+      const uint64_t y0 = fixpt(v0, ec[col]), y1 = fixpt(v1, ec[col]);
+      const int k16 = (2 * kk2) & 15;
+      const int reg = k16 >> 3, ln = 4 * (col & 7) + ((k16 & 7) >> 1);
+      uint32_t* dst = Bd + ((((col >> 3) * 4 + (kk2 >> 3)) * 8) * 32 + ln) * 2 + reg;
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl) dst[sl * 64] = dpair(y0, y1, 7 * (7 - sl));
+    }
+    __syncthreads();
+    float acc[9][4];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = MAGIC;
+    const int kss = min(4, (K - kb + 15) >> 4);
+    for (int ks = 0; ks < kss; ++ks) {
+      uint32_t bq[8][2];
+      const uint32_t* Bp = Bd + (((nt * 4 + ks) * 8) * 32 + lane) * 2;
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl) {
+        const uint2 v = *reinterpret_cast<const uint2*>(Bp + sl * 64);
+        bq[sl][0] = v.x; bq[sl][1] = v.y;
+      }
+      const uint32_t* Ap = Ad + (((mt * 4 + ks) * 8) * 32 + lane) * 4;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const uint4 av = *reinterpret_cast<const uint4*>(Ap + a * 128);
+#pragma unroll
+        for (int bs = 0; bs < 8; ++bs)
+          if (a + bs <= 8) mma16(acc[a + bs], av.x, av.y, av.z, av.w, bq[bs][0], bq[bs][1]);
+      }
+    }
+    // at most 8 digit-pair products per level and k-step, 4 k-steps: |sum| < 2^21
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int32_t S = acc_int(acc[q][e]);
+        if (q <= 4) H[e] += (int64_t)S * (int32_t)(1 << (28 - 7 * q));
+        else L[e] += (int64_t)S * (int32_t)(1 << (63 - 7 * q));
+      }
+    }
+  }
+  // out = (H 2^70 + L 2^35) 2^(er - 1076) 2^(ec - 1076)
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int rl = 16 * mt + g + 8 * (e >> 1), cl = 8 * nt + 2 * t4 + (e & 1);
+    const int row = row0 + rl, col = col0 + cl;
+    if (row < M && col < N) {
+      const int sc = er[rl] + ec[cl];
+      O[(long long)col * ldo + row] = i64_ldexp(H[e], sc - 2082) + i64_ldexp(L[e], sc - 2117);
+    }
+  }
+}
+
 // A = -X (eq. (Amat): X solves C X = D Z), stored column by column like X.
 __global__ void store_A(const double* X, int xld, long long xstride, int n4, double* A, int Cfirst) {
   const int b = blockIdx.y;
@@ -832,7 +969,7 @@ int build_pair_blocks(Ctx& c, int problem) {
   double *ws1 = nullptr, *Z = nullptr, *Zp = nullptr, *D = nullptr, *ws2 = nullptr, *X2 = nullptr;
   double *Yf = nullptr, *Xf = nullptr, *Zpts = nullptr, *Gf = nullptr, *tau = nullptr, *vn = nullptr;
   int *nenh = nullptr, *dm = nullptr, *dn = nullptr, *rank = nullptr, *perm = nullptr, *info = nullptr;
-  int *dm2 = nullptr, *dn2 = nullptr, *bad = nullptr;
+  int *dm2 = nullptr, *dn2 = nullptr, *bad = nullptr, *dzb = nullptr;
   PairDims* pdd = nullptr;
   int rc = LMFS_OK;
   const bool mob = problem == LMFS_MOBILITY;
@@ -877,7 +1014,7 @@ int build_pair_blocks(Ctx& c, int problem) {
       (rc = dalloc(&rank, 2 * chunk)) || (rc = dalloc(&perm, (size_t)chunk * nmax)) ||
       (rc = dalloc(&info, 2 * chunk)) ||
       (rc = dalloc(&dm2, 2 * chunk)) || (rc = dalloc(&dn2, 2 * chunk)) || (rc = dalloc(&bad, 1)) ||
-      (rc = dalloc(&pdd, 1)))
+      (rc = dalloc(&pdd, 1)) || (rc = dalloc(&dzb, (size_t)chunk * (ld2 + k))))
     goto done;
   if (cuda_failed(cudaMemsetAsync(bad, 0, sizeof(int), c.stream), "memset")) { rc = LMFS_ERR_CUDA; goto done; }
   for (int first = 0; first < C; first += chunk) {
@@ -985,12 +1122,29 @@ int build_pair_blocks(Ctx& c, int problem) {
       project_C<<<dim3((2 * Mrow + 127) / 128, nb), 128, 0, c.stream>>>(pd, g, ws2, ld2, s2, Mrow);
       if ((rc = check_launch("project_C"))) goto done;
     }
-    // DZ into the right-hand-side columns of the second workspace
+    // DZ into the right-hand-side columns of the second workspace: as digit
+    // products on the tensor cores (LMFS_DZ_EMU=0: the FP64 kernel)
     {
+      const char* de = std::getenv("LMFS_DZ_EMU");
+      const bool digits = (!de || std::atoi(de) != 0) && nmax % 2 == 0;
       dim3 grid((2 * Mrow + GT - 1) / GT, (k + GT - 1) / GT, nb);
-      gemm_batched<<<grid, 256, 0, c.stream>>>(D, ld2, (long long)ld2 * nmax, mob ? Zp : Z, nmax, (long long)nmax * k,
-                                               ws2 + (long long)n4 * ld2, ld2, s2, 2 * Mrow, k, nenh, 0, pdd);
-      if ((rc = check_launch("gemm DZ"))) goto done;
+      if (digits) {
+        digit_bounds<<<nb, 256, 0, c.stream>>>(D, ld2, (long long)ld2 * nmax, mob ? Zp : Z, nmax, (long long)nmax * k,
+                                               2 * Mrow, k, nenh, 0, pdd, dzb);
+        if ((rc = check_launch("digit bounds DZ"))) goto done;
+        if (cuda_failed(cudaFuncSetAttribute(gemm_digits_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)DG_SMEM), "digit gemm smem")) {
+          rc = LMFS_ERR_CUDA; goto done;
+        }
+        gemm_digits_batched<<<grid, 256, DG_SMEM, c.stream>>>(D, ld2, (long long)ld2 * nmax, mob ? Zp : Z, nmax,
+                                                             (long long)nmax * k, ws2 + (long long)n4 * ld2, ld2, s2,
+                                                             2 * Mrow, k, nenh, 0, pdd, dzb);
+        if ((rc = check_launch("digit gemm DZ"))) goto done;
+      } else {
+        gemm_batched<<<grid, 256, 0, c.stream>>>(D, ld2, (long long)ld2 * nmax, mob ? Zp : Z, nmax, (long long)nmax * k,
+                                                 ws2 + (long long)n4 * ld2, ld2, s2, 2 * Mrow, k, nenh, 0, pdd);
+        if ((rc = check_launch("gemm DZ"))) goto done;
+      }
     }
     const int nbc = symC ? 2 * nb : nb;
     const long long shc = (long long)Mp * n4;             // half: Mp rows x (2Nc + 2Nc)
@@ -1075,7 +1229,7 @@ int build_pair_blocks(Ctx& c, int problem) {
 done:
   dfree(ws1); dfree(Z); dfree(Zp); dfree(D); dfree(ws2); dfree(X2); dfree(Yf); dfree(Xf); dfree(Zpts);
   dfree(Gf); dfree(tau); dfree(vn); dfree(nenh); dfree(dm); dfree(dn); dfree(rank); dfree(perm);
-  dfree(info); dfree(dm2); dfree(dn2); dfree(bad); dfree(pdd);
+  dfree(info); dfree(dm2); dfree(dn2); dfree(bad); dfree(pdd); dfree(dzb);
   for (auto& e : ev) if (e) cudaEventDestroy(e);
   return rc;
 }

@@ -134,3 +134,37 @@ def test_tensor_core_updates_match_fp64_updates(L, monkeypatch, problem):
         assert rel(ve, vf) < 1e-6
     se.close()
     sf.close()
+
+
+def test_digit_dz_matches_fp64_dz(L, monkeypatch):
+    """The pair precompute's D Z product as exact digit products on the
+    tensor cores (the default) against the FP64 kernel (LMFS_DZ_EMU=0),
+    P = 100 mobility: C A -- the part of A the method uses, A being unique
+    only up to C's null directions -- on 4 sampled pairs within 1e-9 (the two
+    products differ by rounding), E unchanged, and the FP64 solves on either
+    set of blocks within 1e-6."""
+    pk = w.packing_p100()
+    ft = w.forces_torques(pk.P, 5)
+    out = {}
+    for dz in ("1", "0"):
+        monkeypatch.setenv("LMFS_DZ_EMU", dz)
+        s = L.Solver(pk.centres, pk.radii, gparams(L, PACKING, precision=L.FP64))
+        s.precompute(L.MOBILITY)
+        monkeypatch.delenv("LMFS_DZ_EMU")
+        A, E = s.pair_blocks(L.MOBILITY)
+        v, info = s.solve(L.MOBILITY, ft)
+        assert info["converged"]
+        out[dz] = (A, E, v, s.pairs().copy())
+        s.close()
+    (Ad, Ed, vd, pairs), (Af, Ef, vf, _) = out["1"], out["0"]
+    assert np.array_equal(Ed, Ef)
+    ob = OneBody(1.0, PACKING, "mobility")
+    worst = 0.0
+    for q in np.linspace(0, len(pairs) - 1, 4).astype(int):
+        i, k = pairs[q]
+        b = pair_blocks(pk.centres[i], 1.0, pk.centres[k], 1.0, ob, ob, PACKING, "mobility", 1.0, keep=True)
+        worst = max(worst, rel(b["C"] @ Ad[q], b["C"] @ Af[q]))
+    dv = rel(vd, vf)
+    print(f"C A digit vs FP64 D Z: worst sampled pair {worst:.2e}; FP64 velocities {dv:.2e}")
+    assert worst < 1e-9
+    assert dv < 1e-6
