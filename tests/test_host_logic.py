@@ -243,8 +243,46 @@ int main() {
     for (int t = 0; t < 8; ++t) { pr += (long double)vv[t] * ww[t]; pa += std::fabs((long double)vv[t]); }
     worst_p = std::max(worst_p, (double)(std::fabs((long double)P - pr) / (pa * std::ldexp(1.0L, F - 1023))));
   }
-  std::printf("%ld %ld %ld %ld %ld %.6e %.6e %.6e\n", bad_fix, bad_range, bad_pair, bad_ldexp, bad_bound,
-              worst_w, worst_w64, worst_p);
+  // the batched GEMM's scheme (one accumulator per level over 64 terms, levels 0-4 into H in
+  // units of 2^70, 5-8 into L in units of 2^35), each side against its own bound
+  double worst_g = 0, worst_g64 = 0;
+  for (int it = 0; it < 120; ++it) {
+    const int K = 1 + (int)(rng() % 1300);
+    std::vector<double> x(K), z(K);
+    for (int i = 0; i < K; ++i) {
+      x[i] = U(rng) * std::ldexp(1.0, (int)(rng() % 30) - 15);
+      z[i] = U(rng) * std::ldexp(1.0, (int)(rng() % 30) - 15);
+    }
+    int ea = 64, eb = 64;
+    for (int i = 0; i < K; ++i) { ea = std::max(ea, bexp(x[i])); eb = std::max(eb, bexp(z[i])); }
+    int64_t H = 0, Lg = 0;
+    for (int k0 = 0; k0 < K; k0 += 64) {
+      long long S[9] = {0};
+      for (int i = k0; i < std::min(K, k0 + 64); ++i) {
+        const uint64_t ya = fixpt(x[i], ea), yb = fixpt(z[i], eb);
+        for (int a = 0; a < 8; ++a)
+          for (int b = 0; b < 8; ++b)
+            if (a + b <= 8) S[a + b] += (long long)digit(ya, 7 - a) * digit(yb, 7 - b);
+      }
+      for (int q = 0; q < 9; ++q) {
+        if (std::llabs(S[q]) >= (1 << 22)) ++bad_bound;
+        const int32_t v = acc_int(MAGIC + (float)S[q]);
+        if (q <= 4) H += (int64_t)v * (int32_t)(1 << (28 - 7 * q));
+        else Lg += (int64_t)v * (int32_t)(1 << (63 - 7 * q));
+      }
+    }
+    const int sc = ea + eb;
+    const double got = i64_ldexp(H, sc - 2082) + i64_ldexp(Lg, sc - 2117);
+    long double ref = 0;
+    for (int i = 0; i < K; ++i) ref += (long double)x[i] * z[i];
+    const long double bnd = K * std::ldexp(1.0L, ea - 1023) * std::ldexp(1.0L, eb - 1023);
+    double f64 = 0;
+    for (int i = 0; i < K; ++i) f64 = std::fma(x[i], z[i], f64);
+    worst_g = std::max(worst_g, (double)(std::fabs((long double)got - ref) / bnd));
+    worst_g64 = std::max(worst_g64, (double)(std::fabs((long double)f64 - ref) / bnd));
+  }
+  std::printf("%ld %ld %ld %ld %ld %.6e %.6e %.6e %.6e %.6e\n", bad_fix, bad_range, bad_pair, bad_ldexp, bad_bound,
+              worst_w, worst_w64, worst_p, worst_g, worst_g64);
   return 0;
 }
 """
@@ -271,12 +309,14 @@ def test_digit_products_reproduce_fp64_dot_products(emu_harness):
     correctly rounded x 2^(1076 - E); every bf16 digit pair decodes to the same
     digits; int64 -> double rounds to nearest; no accumulator of the device's
     level scheme (192 rows per flush, up to 1400 rows) leaves the exact range;
-    and the assembled W = v . c and P = sum_t v_t w_t lie as close to the
-    exact (extended-precision) values, measured against the sum of |v| times
-    the bound, as an FP64 fused-multiply-add loop does (below 2^-53)."""
+    and the assembled W = v . c and P = sum_t v_t w_t, and the batched
+    GEMM's x . z (one accumulator per level, both sides against their own
+    bounds), lie as close to the exact (extended-precision) values, measured
+    against the bounds, as an FP64 fused-multiply-add loop does (below
+    2^-53)."""
     out = subprocess.run([str(emu_harness)], capture_output=True, text=True, check=True).stdout.split()
     bad_fix, bad_range, bad_pair, bad_ldexp, bad_bound = (int(v) for v in out[:5])
-    worst_w, worst_w64, worst_p = (float(v) for v in out[5:])
+    worst_w, worst_w64, worst_p, worst_g, worst_g64 = (float(v) for v in out[5:])
     assert (bad_fix, bad_range, bad_pair, bad_ldexp, bad_bound) == (0, 0, 0, 0, 0)
-    assert worst_w < 2.0 ** -53 and worst_p < 2.0 ** -53
-    assert worst_w <= 2 * worst_w64
+    assert worst_w < 2.0 ** -53 and worst_p < 2.0 ** -53 and worst_g < 2.0 ** -53
+    assert worst_w <= 2 * worst_w64 and worst_g <= 2 * worst_g64
