@@ -107,7 +107,7 @@ class Clocks:
 # lmfs_emu64.cuh): reported as null once either changes.
 RQR_TRAFFIC_PER_MATRIX = (80.89e9 + 40.48e9) / 398.0
 RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.2765054e10
-RQR_SRC_SHA256 = "514fbf2d0ea02ccf7dd7b61d9814954483e8b2e364f2ca34c91a7c2d24ff1fa5"
+RQR_SRC_SHA256 = "49bed31b533886044e6b3d957d770fcd16384e04abe96afae6035341432b1b82"
 ALU_WARP_INST_PER_CLK = 2          # 64 results per clock per SM for 32-bit integer add, logic and shift
 
 

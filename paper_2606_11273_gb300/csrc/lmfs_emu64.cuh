@@ -3,9 +3,13 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59, 2012).
 //
+// Used for the blocked QR's trailing updates and back substitution
+// (block_update, backsub) and for the pair precompute's D Z product.
+//
 // A double x is written against a power-of-two bound 2^E shared by the
 // entries that one dot product combines (a column of the trailing matrix, a
-// reflector, a column of T^T W) as an integer X = round(x 2^(1076 - E)),
+// reflector, a column of T^T W, a row of R's block, a row of D, a column of
+// Z) as an integer X = round(x 2^(1076 - E)),
 // |X| < 2^54, and X as eight balanced base-128 digits d_0..d_7 in [-64, 63]
 // (X = sum_i d_i 128^i).  Every digit is an integer that bf16 holds exactly,
 // every digit product is below 2^12, and a sum of them below 2^22 is exact in
@@ -149,9 +153,6 @@ EMU_HD double i64_ldexp(int64_t v, int e) {
   return bitsd(sgn | (((uint64_t)(eb - 1) << 52) + r));
 }
 
-// Shift an int64 by 2^sh (sh may be negative: arithmetic shift right).
-EMU_HD int64_t shl(int64_t v, int sh) { return sh >= 0 ? v * ((int64_t)1 << sh) : (v >> (-sh)); }
-
 // Level sums of W = V^T C, exactly: accumulator q = 0..8 holds level q from
 // the even digits of V and level q + 1 from the odd ones, so acc_pair gives
 // their sum in units of level q + 1, weight 128^(13 - q).  W_fix =
@@ -173,9 +174,8 @@ EMU_HD double w_value(int64_t H, int64_t L, int E) {
 // its column bound F, P = P_int 2^(F - 1079).
 // The three heaviest levels fit one int32 (a most significant digit is at
 // most 33 in magnitude, so over 8 reflectors their sums stay below 2^13.1,
-// 2^15.1 and 2^16.1), the rest in pairs; the
-// weights in units of P_int are 2^34 (levels 0-2), 2^20 (3-4), 2^6 (5-6) and
-// 2^-8 (7-8).
+// 2^15.1 and 2^16.1), the rest in pairs; the weights in units of P_int are
+// 2^34 (levels 0-2), 2^20 (3-4), 2^6 (5-6) and 2^-8 (7-8).
 EMU_HD int64_t comb_p(const float* acc) {
   const int32_t u012 = (int32_t)(fbits(acc[0]) * 16384u + fbits(acc[1]) * 128u + fbits(acc[2]) - 16513u * MAGIC_BITS);
   const int32_t u34 = acc_pair(acc[3], acc[4]), u56 = acc_pair(acc[5], acc[6]), u78 = acc_pair(acc[7], acc[8]);
