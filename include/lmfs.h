@@ -342,11 +342,12 @@ int lmfs_launch_count(uint64_t* out);
  *   44 bytes per target + 32 bytes per source + 32 bytes per disk (each part
  *   rounded up to 256 bytes); larger problems get LMFS_ERR_INVALID.
  *   The first call on a device (with that device current) looks up the
- *   array's device address; make that first call before any stream capture.
- *   Every call reuses the same array and it keeps the last call's contents:
- *   calls that overlap on the GPU race on it, so serialise them.
- *   Host-synchronous: every call synchronizes `stream` before it returns (it
- *   reads the two error flags back from the array). */
+ *   array's device address.  Every call reuses the same array and it keeps
+ *   the last call's contents: calls that overlap on the GPU race on it, so
+ *   serialise them.
+ *   Host-synchronous and not capturable: every call synchronizes `stream`
+ *   before it returns (it reads the two error flags back from the array), so
+ *   it cannot be enqueued inside a CUDA graph capture. */
 int lmfs_stokeslet_sum_noalloc(const double* targets, int nt, const double* centres,
                                const double* offsets, const double* strengths, int nd,
                                int n_per_disk, double mu, void* stream, double* out);
