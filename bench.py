@@ -107,7 +107,7 @@ class Clocks:
 # lmfs_emu64.cuh): reported as null once either changes.
 RQR_TRAFFIC_PER_MATRIX = (80.89e9 + 40.48e9) / 398.0
 RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.2765054e10
-RQR_SRC_SHA256 = "49bed31b533886044e6b3d957d770fcd16384e04abe96afae6035341432b1b82"
+RQR_SRC_SHA256 = "c5a71397a85d2340877b781ad2d383c3f1554c3bf19893203cb598df219bf7b6"
 ALU_WARP_INST_PER_CLK = 2          # 64 results per clock per SM for 32-bit integer add, logic and shift
 
 

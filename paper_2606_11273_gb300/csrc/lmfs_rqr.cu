@@ -1,6 +1,12 @@
 // Blocked Householder QR with the pivots chosen on a random sketch, and the
-// truncated basic least-squares solution, in FP64: one matrix per CTA, or per
-// thread-block cluster of cs CTAs.
+// truncated basic least-squares solution, FP64-class: one matrix per CTA, or
+// per thread-block cluster of cs CTAs.
+//
+// With one CTA per matrix (the default for large batches, emu = 1) the
+// trailing updates and the back substitution -- nearly all of the flops --
+// are exact products of fixed-point digits on the bf16 tensor cores, rounded
+// once (lmfs_emu64.cuh); the blocks' own factorization, T, the sketch and its
+// update stay in FP64.  Otherwise every step is FP64.
 //
 // The column-pivoted QR of lmfs_qr.cu chooses every pivot from the updated
 // norms of all remaining columns, so each reflector is applied to the whole
