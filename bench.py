@@ -107,7 +107,7 @@ class Clocks:
 # lmfs_emu64.cuh): reported as null once either changes.
 RQR_TRAFFIC_PER_MATRIX = (80.89e9 + 40.48e9) / 398.0
 RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.2765054e10
-RQR_SRC_SHA256 = "c5a71397a85d2340877b781ad2d383c3f1554c3bf19893203cb598df219bf7b6"
+RQR_SRC_SHA256 = "1c189e703fa01490bc816157a55e1e4a2598ace863fabc72e62af987a06631bf"
 ALU_WARP_INST_PER_CLK = 2          # 64 results per clock per SM for 32-bit integer add, logic and shift
 
 

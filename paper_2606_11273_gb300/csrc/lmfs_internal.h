@@ -328,7 +328,7 @@ inline int pair_chunk(long long C, double per_pair) {
 }
 // The blocked QR with sketch pivoting (lmfs_rqr.cu): shared memory it needs,
 // and the batch solve itself (solve mode only).
-size_t rqr_smem_bytes(int ld, int nmax, int k);
+size_t rqr_smem_bytes(int ld, int nmax, int k, bool emu = false);
 bool rqr_emu_ok(const QRBatch& q);        // trailing updates on the tensor cores possible (one CTA per matrix)
 int rqr_active_clusters(size_t shm, int cs, int nb);
 int rqr_solve_batched(const QRBatch& q, cudaStream_t s, int cs);

@@ -580,9 +580,9 @@ int qr_solve_batched(const QRBatch& q, cudaStream_t st, bool solve) {
   // override the choice (tests compare the forms).
   if (solve && q.k > 0) {
     const int path = qr_path_override();
-    const size_t shm = rqr_smem_bytes(q.ld, q.nmax, q.k);
-    const bool fits = shm <= 226 * 1024;
     const bool emu = rqr_emu_ok(q);
+    const size_t shm = rqr_smem_bytes(q.ld, q.nmax, q.k);   // FP64 stages (clusters)
+    const bool fits = rqr_smem_bytes(q.ld, q.nmax, q.k, emu) <= 226 * 1024;
     int cs = emu ? (q.nb >= sms ? 1 : 0) : (q.nb >= 8 * sms ? 1 : (q.nb >= 2 * sms ? 2 : 0));
     if (const char* e = std::getenv("LMFS_QR_CS")) cs = std::max(1, std::min(8, std::atoi(e)));
     if (path == 1 && cs == 0) cs = 1;

@@ -658,8 +658,20 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
 
 // Shared memory of the blocked path for leading dimension ld and at most
 // nmax coefficient columns (0 if it does not fit a CTA).
-size_t rqr_smem_bytes(int ld, int nmax, int k) {
-  const size_t wsz = std::max<size_t>({(size_t)RB * ld, (size_t)RL * nmax, (size_t)RW * nmax});
+// Doubles of the shared work region: the block's V, the sketch's FP32 copy
+// and the back substitution's right-hand sides, and, with the tensor-core
+// stages, their digit tiles (the larger need for short systems).
+static size_t rqr_work_doubles(int ld, int nmax, int k, bool emu) {
+  size_t wsz = std::max<size_t>({(size_t)RB * ld, (size_t)RL * nmax, (size_t)RW * nmax});
+  if (emu) {
+    const size_t need = std::max(emu::update_smem_bytes(nmax + k), emu::backsub_smem_bytes(nmax, k));
+    wsz = std::max(wsz, (need + sizeof(double) - 1) / sizeof(double));
+  }
+  return wsz;
+}
+
+size_t rqr_smem_bytes(int ld, int nmax, int k, bool emu) {
+  const size_t wsz = rqr_work_doubles(ld, nmax, k, emu);
   return (wsz + (size_t)(ld + 3) / 4 + RSMALL + (size_t)(nmax + k + 1) / 2) * sizeof(double);
 }
 
@@ -688,25 +700,23 @@ int rqr_active_clusters(size_t shm, int cs, int nb) {
   return act;
 }
 
-// Whether the trailing updates of a batch can run on the tensor cores
-// (lmfs_emu64.cuh): even leading dimension and matrix stride (16-byte row
-// pairs), at most 3072 rows (the exact sums' range), and room for the digit
-// tiles in the work region; LMFS_QR_EMU=0 turns them off.  They need one CTA
-// per matrix.
+// Whether the trailing updates and the back substitution of a batch can run
+// on the tensor cores (lmfs_emu64.cuh): even leading dimension and matrix
+// stride (16-byte row pairs), at most 3072 rows (the exact sums' range), and
+// shared memory for two CTAs per SM with the digit tiles; LMFS_QR_EMU=0
+// turns them off.  They need one CTA per matrix.
 bool rqr_emu_ok(const QRBatch& q) {
   if (const char* e = std::getenv("LMFS_QR_EMU"))
     if (std::atoi(e) == 0) return false;
-  const size_t wsz = std::max<size_t>({(size_t)RB * q.ld, (size_t)RL * q.nmax, (size_t)RW * q.nmax});
   return q.ld % 2 == 0 && q.mstride % 2 == 0 && q.ld <= 3072 &&
-         wsz * sizeof(double) >= emu::update_smem_bytes(q.nmax + q.k) &&
-         wsz * sizeof(double) >= emu::backsub_smem_bytes(q.nmax, q.k);
+         rqr_smem_bytes(q.ld, q.nmax, q.k, true) <= 112 * 1024;
 }
 
 int rqr_solve_batched(const QRBatch& q, cudaStream_t st, int cs) {
   const int nmax = q.nmax;
-  const size_t wsz = std::max<size_t>({(size_t)RB * q.ld, (size_t)RL * nmax, (size_t)RW * nmax});
-  const size_t shm = rqr_smem_bytes(q.ld, nmax, q.k);
   const bool use_emu = cs == 1 && rqr_emu_ok(q);
+  const size_t wsz = rqr_work_doubles(q.ld, nmax, q.k, use_emu);
+  const size_t shm = rqr_smem_bytes(q.ld, nmax, q.k, use_emu);
   const int wld = nmax + q.k;
   if (cs < 1 || cs > 8) { set_last_error("blocked QR: cluster size must lie in 1..8"); return LMFS_ERR_INVALID; }
   if (cuda_failed(cudaFuncSetAttribute(rqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm),
