@@ -45,3 +45,26 @@ def test_clock_summary_without_samples():
     c = bench.Clocks()
     s = c.summary()
     assert s == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_qr_roofline_forms(monkeypatch):
+    """The bench's roofline of the fine systems' QR: with the tensor-core
+    stages, bound by the ALU pipe at the capture's flops per ALU instruction
+    x 152 SMs x 2 instructions per clock x the clock (null once the kernel
+    sources no longer hash to the capture's), with the FP64 pipe's peak beside
+    it; with FP64 stages, bound by the FP64 peak."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fp64 = 152 * 2 * 2 * 2070e6 / 1e12
+    r = bench.rqr_roofline(True, True, 2.5, fp64, 2070.0, 6.4e12, 7.7e12, 3000.0, 4600.0)
+    assert r["bound"] == "alu"
+    if bench.rqr_counters_valid():
+        peak = bench.RQR_FLOPS_PER_ALU_INST * 152 * 2 * 2070e6 / 1e12
+        assert abs(r["peak"] - peak) < 1e-12 and abs(r["frac"] - 2.5 / peak) < 1e-12
+    assert abs(r["vs_fp64_pipe_peak"] - 2.5 / fp64) < 1e-12
+    assert abs(r["share_of_step"] - 3000.0 / 4600.0) < 1e-12
+    monkeypatch.setattr(bench, "RQR_SRC_SHA256", "0" * 64)
+    r = bench.rqr_roofline(True, True, 2.5, fp64, 2070.0, None, 7.7e12, 3000.0, 4600.0)
+    assert r["peak"] is None and r["frac"] is None
+    r = bench.rqr_roofline(False, True, 0.98, fp64, 2070.0, None, 7.7e12, 7800.0, 10000.0)
+    assert r["unit"] == "TFLOP/s (FP64)" and abs(r["frac"] - 0.98 / fp64) < 1e-12
