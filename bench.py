@@ -106,8 +106,8 @@ class Clocks:
 # Valid only for the kernel source they were taken on (lmfs_rqr.cu and
 # lmfs_emu64.cuh): reported as null once either changes.
 RQR_TRAFFIC_PER_MATRIX = (80.89e9 + 40.48e9) / 398.0
-RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.2765054e10
-RQR_SRC_SHA256 = "1c189e703fa01490bc816157a55e1e4a2598ace863fabc72e62af987a06631bf"
+RQR_FLOPS_PER_ALU_INST = 1.481730e11 / 1.2765068e10
+RQR_SRC_SHA256 = "a2a29986564be4e7d583bf76d76ce2cae6d9c529f2da6d5be8c65efb76e31f1b"
 ALU_WARP_INST_PER_CLK = 2          # 64 results per clock per SM for 32-bit integer add, logic and shift
 
 

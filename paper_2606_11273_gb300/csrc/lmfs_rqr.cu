@@ -173,7 +173,10 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
     }
 #pragma unroll
     for (int j = 0; j < RL; ++j) Yg[(long long)j * ysd + c] = acc[j];
-    if (a.emu) cex[c] = mx;
+    if (a.emu) {
+      cex[c] = mx;
+      if (mx == 2047) s_bad = 1;                          // Inf or NaN: digits would hide it
+    }
   }
   if (a.emu)
     for (int c = n + tid; c < n + k; c += RT) {
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(RT, 2) rqr_kernel(RArgs a) {
       int mx = 0;
       for (int i = 0; i < m; ++i) mx = max(mx, emu::bexp(col[i]));
       cex[c] = mx;
+      if (mx == 2047) s_bad = 1;
     }
   csync();
 
