@@ -172,7 +172,14 @@ int lmfs_get_pairs(lmfs_handle h, int* pairs);
  * pair's coarse-to-coarse correction A (4N_c x 4N_c, eq. (Amat)) and
  * extraction matrix E (6 x 4N_c, eq. (force_ext) resistance, eq. (rbm2)
  * mobility), computed on the device by batched column-pivoted Householder QR
- * (FP64).  Idempotent per problem. */
+ * (FP64-class).  Idempotent per problem.
+ *   Large batches (152 systems or more per launch) take the blocked QR with
+ *   sketch pivoting, whose trailing updates and back substitution, and the D Z
+ *   product of eq. (Amat), are exact digit products on the tensor cores,
+ *   rounded once; smaller batches the column-pivoted QR in FP64.  Environment
+ *   overrides, read at every precompute: LMFS_QR_EMU=0 (the blocked QR in
+ *   FP64), LMFS_DZ_EMU=0 (D Z in FP64), LMFS_QR_PATH=blocked|cluster and
+ *   LMFS_QR_CS=n (the QR form and CTAs per system). */
 int lmfs_precompute_pairs(lmfs_handle h, int problem);
 
 /* Export / import the pair blocks: host double A[C][4Nc][4Nc] (row-major),
